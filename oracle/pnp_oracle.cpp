@@ -1,0 +1,799 @@
+// pnp_oracle.cpp -- plain FP64 CPU oracle for the VMS-stabilised PNP block.
+//
+// TEST INFRASTRUCTURE.  This file is the independent reference that the CUDA path is
+// checked against.  Only the tests, the smoke check and the CPU-baseline leg of the
+// benchmark load it; the library's product path never calls, links or includes it,
+// and it shares no code, header or table with the CUDA sources.
+//
+// What it computes (Kim et al., "Direct numerical simulation of electrokinetic
+// transport phenomena in fluids: variational multi-scale stabilization and
+// octree-based mesh refinement", arXiv 2301.05985):
+//   * the non-dimensional Poisson and Nernst-Planck equations of Sec. 2.2
+//     (Eqs. nondim_poisson, nondim_np): -2 Lambda^2 lap(phi) = sum_s z_s c_s and
+//     dc/dt + v.grad c = div(grad c + z c grad phi);
+//   * BDF time discretisation with coefficients beta0..beta2 (Def. 1 of Sec. 3);
+//   * the fully discrete VMS form of Def. 3 (Poisson and Nernst-Planck rows), with
+//     the fine-scale closure c^f = -tau_c R_c and tau_c of Sec. 3.1 (C_I = 6,
+//     G_ij = (2/h)^2 delta_ij on cubes);
+//   * the analytic Jacobian of that residual (Sec. 4.1, Eq. newton_linear_system);
+//   * Q1 elements on a 2:1-balanced octree (Sec. 4.2) with conforming hanging-node
+//     constraints (the paper does not describe them; face-centre = mean of 4 face
+//     corners, edge-midpoint = mean of 2 edge ends).
+//
+// Everything is written out plainly: std::map on integer coordinates for the mesh,
+// direct evaluation of the tensor-product shape functions at each Gauss point,
+// element-by-element assembly.  No sum factorisation, no blocking, no reordering.
+
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <set>
+#include <utility>
+#include <vector>
+
+namespace {
+
+typedef std::array<int64_t, 3> IPt;
+
+struct Mesh {
+  int dim = 0;
+  int L = 0;                                   // max level: coordinates in units of 2^-L
+  std::vector<IPt> el_anchor;
+  std::vector<int> el_level;
+  std::vector<std::vector<int64_t>> el_nodes;  // 2^dim corner node ids (lexicographic corner order)
+  std::vector<IPt> node_xyz;
+  std::map<IPt, int64_t> node_of;
+  // constraint rows: node -> list of (independent node, weight).  Identity for free nodes.
+  std::vector<std::vector<std::pair<int64_t, double>>> cons;
+  std::vector<char> hanging;
+};
+
+// Parameters of one residual evaluation.  Must match the ctypes mirror in oracle.py.
+struct Params {
+  double eps;      // Lambda, the non-dimensional Debye length
+  double dt;       // time step
+  double beta0, beta1, beta2;  // BDF coefficients
+  double C_I;      // tau_c constant (6 in the paper)
+  double t;        // time level of the unknown (manufactured-solution forcing only)
+  int32_t steady;  // 1: drop the time-derivative terms (and 4/dt^2 in tau_c)
+  int32_t vms;     // 0: tau_c := 0 (plain Galerkin; used by the exact-integration checks)
+  int32_t mms;     // 1: add manufactured-solution forcing and use its Dirichlet values
+  int32_t pad;
+  int32_t bc_type[6][3];  // per face, per field: 0 natural, 1 Dirichlet
+  double bc_val[6][3];
+};
+
+const double kZ[2] = {+1.0, -1.0};  // valences of c+ and c-
+
+// ------------------------------------------------------------------ manufactured solution
+// Sec. 5.1, Eq. manufac_sol (2D); in 3D every field is multiplied by cos(pi z) and the
+// third velocity component is zero (still divergence-free).  Returns, for fields
+// [c+, c-, phi, u, v, w], the value, gradient and Laplacian at (x, t); "steady"
+// freezes the time factor at 1.
+struct MmsField { double val; double grad[3]; double lap; double dval_dt; };
+
+void mms_fields(int dim, const double* x, double t, int steady, MmsField out[6]) {
+  const double k = 2.0 * M_PI;
+  const double T = steady ? 1.0 : std::cos(2.0 * t);
+  const double Tp = steady ? 0.0 : -2.0 * std::sin(2.0 * t);
+  const double sx = std::sin(k * x[0]), cx = std::cos(k * x[0]);
+  const double sy = std::sin(k * x[1]), cy = std::cos(k * x[1]);
+  // A = cos(kx) sin(ky), B = sin(kx) cos(ky)
+  const double A = cx * sy, B = sx * cy;
+  const double Ag[2] = {-k * sx * sy, k * cx * cy};
+  const double Bg[2] = {k * cx * cy, -k * sx * sy};
+  const double Alap = -2.0 * k * k * A, Blap = -2.0 * k * k * B;
+  double Z = 1.0, Zp = 0.0, Zpp = 0.0;
+  if (dim == 3) {
+    Z = std::cos(M_PI * x[2]);
+    Zp = -M_PI * std::sin(M_PI * x[2]);
+    Zpp = -M_PI * M_PI * Z;
+  }
+  // sign * T * {A or B} * Z
+  const int which[5] = {0, 1, 0, 1, 0};   // A, B, A, B, A  for c+, c-, phi, u, v
+  const double sgn[5] = {+1, +1, -1, +1, -1};
+  for (int f = 0; f < 5; ++f) {
+    const double g = which[f] ? B : A;
+    const double* gg = which[f] ? Bg : Ag;
+    const double gl = which[f] ? Blap : Alap;
+    const double s = sgn[f];
+    out[f].val = s * T * g * Z;
+    out[f].dval_dt = s * Tp * g * Z;
+    out[f].grad[0] = s * T * gg[0] * Z;
+    out[f].grad[1] = s * T * gg[1] * Z;
+    out[f].grad[2] = s * T * g * Zp;
+    out[f].lap = s * T * (gl * Z + g * Zpp);
+  }
+  out[5] = MmsField{0.0, {0.0, 0.0, 0.0}, 0.0, 0.0};
+}
+
+// Forcing that makes the manufactured fields an exact solution of
+//   dc_s/dt + v.grad c_s - div(grad c_s + z_s c_s grad phi) = f_s,
+//   -2 Lambda^2 lap(phi) - sum_s z_s c_s = f_phi.
+void mms_forcing(int dim, const double* x, double t, double eps, int steady, double f[3]) {
+  MmsField m[6];
+  mms_fields(dim, x, t, steady, m);
+  const MmsField& ph = m[2];
+  for (int s = 0; s < 2; ++s) {
+    const MmsField& c = m[s];
+    double adv = 0.0, gcgp = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      adv += m[3 + a].val * c.grad[a];
+      gcgp += c.grad[a] * ph.grad[a];
+    }
+    // div(z c grad phi) = z (grad c . grad phi + c lap phi)
+    f[s] = c.dval_dt + adv - c.lap - kZ[s] * (gcgp + c.val * ph.lap);
+  }
+  f[2] = -2.0 * eps * eps * ph.lap - (m[0].val - m[1].val);
+}
+
+// ------------------------------------------------------------------ mesh construction
+int corner_count(int dim) { return 1 << dim; }
+
+IPt corner_point(const Mesh& m, const IPt& a, int64_t s, int c) {
+  IPt p = a;
+  for (int k = 0; k < m.dim; ++k)
+    if ((c >> k) & 1) p[k] += s;
+  return p;
+}
+
+// Error codes (same meaning as the library's public codes where they overlap).
+enum { ORA_OK = 0, ORA_ERR_ARG = 1, ORA_ERR_UNBALANCED = 3 };
+
+int build_mesh(Mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels) {
+  if (dim != 2 && dim != 3) return ORA_ERR_ARG;
+  if (L < 0 || L > 20 || n <= 0) return ORA_ERR_ARG;
+  m.dim = dim;
+  m.L = L;
+  const int64_t size = int64_t(1) << L;
+  std::map<IPt, int> leaf;  // anchor -> level
+  for (int64_t e = 0; e < n; ++e) {
+    IPt a = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) a[k] = anchors[e * dim + k];
+    const int l = levels[e];
+    if (l > L) return ORA_ERR_ARG;
+    const int64_t s = int64_t(1) << (L - l);
+    for (int k = 0; k < dim; ++k)
+      if (a[k] < 0 || a[k] % s != 0 || a[k] + s > size) return ORA_ERR_ARG;
+    if (leaf.count(a)) return ORA_ERR_ARG;  // duplicate anchor (same or different level)
+    leaf[a] = l;
+  }
+  // Two octants overlap only if one is an ancestor of the other.
+  long double vol = 0;
+  for (auto& kv : leaf) {
+    const IPt& a = kv.first;
+    const int l = kv.second;
+    for (int lc = 0; lc < l; ++lc) {
+      const int64_t sc = int64_t(1) << (L - lc);
+      IPt b = {0, 0, 0};
+      for (int k = 0; k < dim; ++k) b[k] = (a[k] / sc) * sc;
+      auto it = leaf.find(b);
+      if (it != leaf.end() && it->second == lc) return ORA_ERR_ARG;
+    }
+    vol += std::pow((long double)2.0, -(long double)(dim * l));
+  }
+  if (std::fabs((double)(vol - 1.0L)) > 1e-12) return ORA_ERR_ARG;  // not a complete cover
+
+  // 2:1 balance across faces, edges and corners: the leaf containing the same-size
+  // neighbour region of every leaf must be at most one level coarser.
+  for (auto& kv : leaf) {
+    const IPt& a = kv.first;
+    const int l = kv.second;
+    const int64_t s = int64_t(1) << (L - l);
+    const int nd = dim == 3 ? 27 : 9;
+    for (int d = 0; d < nd; ++d) {
+      int off[3] = {d % 3 - 1, (d / 3) % 3 - 1, (d / 9) % 3 - 1};
+      if (dim == 2) off[2] = 0;
+      if (off[0] == 0 && off[1] == 0 && off[2] == 0) continue;
+      IPt r = a;
+      bool inside = true;
+      for (int k = 0; k < dim; ++k) {
+        r[k] = a[k] + off[k] * s;
+        if (r[k] < 0 || r[k] >= size) inside = false;
+      }
+      if (!inside) continue;
+      for (int lc = l; lc >= 0; --lc) {
+        const int64_t sc = int64_t(1) << (L - lc);
+        IPt b = {0, 0, 0};
+        for (int k = 0; k < dim; ++k) b[k] = (r[k] / sc) * sc;
+        auto it = leaf.find(b);
+        if (it != leaf.end() && it->second == lc) {
+          if (lc < l - 1) return ORA_ERR_UNBALANCED;
+          break;
+        }
+      }
+    }
+  }
+
+  // Elements in the given input order; nodes numbered in order of first appearance.
+  const int nc = corner_count(dim);
+  m.el_anchor.resize(n);
+  m.el_level.resize(n);
+  m.el_nodes.assign(n, std::vector<int64_t>(nc));
+  for (int64_t e = 0; e < n; ++e) {
+    IPt a = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) a[k] = anchors[e * dim + k];
+    m.el_anchor[e] = a;
+    m.el_level[e] = levels[e];
+    const int64_t s = int64_t(1) << (L - levels[e]);
+    for (int c = 0; c < nc; ++c) {
+      IPt p = corner_point(m, a, s, c);
+      auto it = m.node_of.find(p);
+      int64_t id;
+      if (it == m.node_of.end()) {
+        id = (int64_t)m.node_xyz.size();
+        m.node_of[p] = id;
+        m.node_xyz.push_back(p);
+      } else {
+        id = it->second;
+      }
+      m.el_nodes[e][c] = id;
+    }
+  }
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  m.hanging.assign(nn, 0);
+  m.cons.assign(nn, {});
+  // A node that sits at the midpoint of an edge, or the centre of a face, of some
+  // element is hanging; its value is the mean of that edge's ends / face's corners.
+  for (int64_t e = 0; e < n; ++e) {
+    const int64_t s = int64_t(1) << (L - m.el_level[e]);
+    if (s < 2) continue;
+    const IPt& a = m.el_anchor[e];
+    // enumerate points of {0, s/2, s}^dim with 1 (edge midpoint) or 2 (face centre, 3D) mid coords
+    const int np = dim == 3 ? 27 : 9;
+    for (int q = 0; q < np; ++q) {
+      int t3[3] = {q % 3, (q / 3) % 3, (q / 9) % 3};
+      if (dim == 2) t3[2] = 0;
+      int nmid = 0;
+      for (int k = 0; k < dim; ++k) nmid += (t3[k] == 1);
+      if (nmid == 0 || nmid == dim) continue;  // a corner, or the element centre
+      IPt p = a;
+      for (int k = 0; k < dim; ++k) p[k] = a[k] + t3[k] * (s / 2);
+      auto it = m.node_of.find(p);
+      if (it == m.node_of.end()) continue;
+      const int64_t h = it->second;
+      // parents: replace each mid coordinate by 0 or s
+      std::vector<std::pair<int64_t, double>> par;
+      const int npar = 1 << nmid;
+      for (int pc = 0; pc < npar; ++pc) {
+        IPt pp = a;
+        int bit = 0;
+        for (int k = 0; k < dim; ++k) {
+          if (t3[k] == 1) {
+            pp[k] = a[k] + (((pc >> bit) & 1) ? s : 0);
+            ++bit;
+          } else {
+            pp[k] = a[k] + t3[k] * (s / 2);
+          }
+        }
+        auto pit = m.node_of.find(pp);
+        if (pit == m.node_of.end()) return ORA_ERR_UNBALANCED;
+        par.push_back({pit->second, 1.0 / npar});
+      }
+      if (m.hanging[h]) {
+        // found again from another coarse element: must agree on the parent set
+        std::set<int64_t> s1, s2;
+        for (auto& pw : m.cons[h]) s1.insert(pw.first);
+        for (auto& pw : par) s2.insert(pw.first);
+        if (s1 != s2) return ORA_ERR_UNBALANCED;
+        continue;
+      }
+      m.hanging[h] = 1;
+      m.cons[h] = par;
+    }
+  }
+  for (int64_t i = 0; i < nn; ++i) {
+    if (!m.hanging[i]) {
+      m.cons[i] = {{i, 1.0}};
+    } else {
+      for (auto& pw : m.cons[i])
+        if (m.hanging[pw.first]) return ORA_ERR_UNBALANCED;  // chained constraints
+    }
+  }
+  return ORA_OK;
+}
+
+// ------------------------------------------------------------------ boundary rows
+// Dirichlet value of (node, field), if any: faces are scanned in increasing index and
+// the last Dirichlet face that contains the node wins.  Hanging nodes are never
+// Dirichlet rows (they stay constrained).
+bool dirichlet(const Mesh& m, const Params& p, int64_t i, int f, double* g) {
+  if (m.hanging[i]) return false;
+  const int64_t size = int64_t(1) << m.L;
+  bool is = false;
+  for (int face = 0; face < 2 * m.dim; ++face) {
+    const int ax = face / 2;
+    const int64_t want = (face & 1) ? size : 0;
+    if (m.node_xyz[i][ax] != want) continue;
+    if (p.bc_type[face][f] != 1) continue;
+    is = true;
+    if (p.mms) {
+      double x[3] = {0, 0, 0};
+      for (int k = 0; k < m.dim; ++k) x[k] = (double)m.node_xyz[i][k] / (double)size;
+      MmsField mf[6];
+      mms_fields(m.dim, x, p.t, p.steady, mf);
+      *g = mf[f].val;
+    } else {
+      *g = p.bc_val[face][f];
+    }
+  }
+  return is;
+}
+
+// ------------------------------------------------------------------ quadrature-point state
+struct Qp {
+  double N[8];        // shape functions
+  double dN[8][3];    // physical gradients
+  double w;           // quadrature weight (h/2)^dim
+  double x[3];        // physical coordinates
+};
+
+// Tensor-product Q1 shape functions at the Gauss point with sign pattern q, in the
+// element of anchor a and edge h (coordinates in [0,1]).
+void eval_qp(const Mesh& m, int64_t e, int q, Qp& Q) {
+  const int dim = m.dim;
+  const double size = (double)(int64_t(1) << m.L);
+  const double h = std::ldexp(1.0, -m.el_level[e]);
+  const double g = 1.0 / std::sqrt(3.0);
+  double xi[3] = {0, 0, 0};
+  for (int k = 0; k < dim; ++k) {
+    xi[k] = ((q >> k) & 1) ? g : -g;
+    Q.x[k] = (double)m.el_anchor[e][k] / size + 0.5 * h * (xi[k] + 1.0);
+  }
+  if (dim == 2) Q.x[2] = 0.0;
+  Q.w = std::pow(0.5 * h, dim);
+  const int nc = corner_count(dim);
+  for (int c = 0; c < nc; ++c) {
+    double f1[3], d1[3];
+    for (int k = 0; k < dim; ++k) {
+      const double sk = ((c >> k) & 1) ? 1.0 : -1.0;
+      f1[k] = 0.5 * (1.0 + sk * xi[k]);
+      d1[k] = 0.5 * sk;
+    }
+    double N = 1.0;
+    for (int k = 0; k < dim; ++k) N *= f1[k];
+    Q.N[c] = N;
+    for (int a = 0; a < 3; ++a) Q.dN[c][a] = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      double d = d1[a] * (2.0 / h);
+      for (int k = 0; k < dim; ++k)
+        if (k != a) d *= f1[k];
+      Q.dN[c][a] = d;
+    }
+  }
+}
+
+// Element nodal values of a node-major 3-field vector through the constraints.
+void gather3(const Mesh& m, int64_t e, const double* U, double out[8][3]) {
+  const int nc = corner_count(m.dim);
+  for (int c = 0; c < nc; ++c) {
+    const int64_t i = m.el_nodes[e][c];
+    for (int f = 0; f < 3; ++f) out[c][f] = 0.0;
+    for (auto& pw : m.cons[i])
+      for (int f = 0; f < 3; ++f) out[c][f] += pw.second * U[3 * pw.first + f];
+  }
+}
+
+void gatherd(const Mesh& m, int64_t e, const double* V, double out[8][3]) {
+  // velocity: node-major with 3 slots per node (the last is ignored in 2D)
+  gather3(m, e, V, out);
+}
+
+struct QpPhys {
+  double c[2], gc[2][3], gp[3], va[3], hs[2], f[3];
+  double tau, R[2], P[2][3];
+  double kappa;
+};
+
+// State at one Gauss point: interpolated fields, tau_c, strong residual R_s and the
+// transport vector P_s = v - z_s grad(phi).
+void qp_state(const Mesh& m, const Params& p, int64_t e, const Qp& Q, const double Ue[8][3],
+              const double Uke[8][3], const double Ukm1e[8][3], const double Ve[8][3], QpPhys& S) {
+  const int dim = m.dim, nc = corner_count(dim);
+  const double h = std::ldexp(1.0, -m.el_level[e]);
+  for (int s = 0; s < 2; ++s) {
+    S.c[s] = 0; S.hs[s] = 0;
+    for (int a = 0; a < 3; ++a) S.gc[s][a] = 0;
+  }
+  for (int a = 0; a < 3; ++a) { S.gp[a] = 0; S.va[a] = 0; }
+  for (int c = 0; c < nc; ++c) {
+    for (int s = 0; s < 2; ++s) {
+      S.c[s] += Q.N[c] * Ue[c][s];
+      for (int a = 0; a < dim; ++a) S.gc[s][a] += Q.dN[c][a] * Ue[c][s];
+      if (!p.steady) S.hs[s] += Q.N[c] * (p.beta1 * Uke[c][s] + p.beta2 * Ukm1e[c][s]) / p.dt;
+    }
+    for (int a = 0; a < dim; ++a) {
+      S.gp[a] += Q.dN[c][a] * Ue[c][2];
+      S.va[a] += Q.N[c] * Ve[c][a];
+    }
+  }
+  S.kappa = p.steady ? 0.0 : p.beta0 / p.dt;
+  if (p.mms) {
+    mms_forcing(dim, Q.x, p.t, p.eps, p.steady, S.f);
+  } else {
+    S.f[0] = S.f[1] = S.f[2] = 0.0;
+  }
+  // tau_c = (4/dt^2 + v.G.v + C_I G:G)^(-1/2), G = (2/h)^2 I  (Sec. 3.1)
+  double vv = 0;
+  for (int a = 0; a < dim; ++a) vv += S.va[a] * S.va[a];
+  const double G = (2.0 / h) * (2.0 / h);
+  const double arg = (p.steady ? 0.0 : 4.0 / (p.dt * p.dt)) + G * vv + p.C_I * dim * G * G;
+  S.tau = p.vms ? 1.0 / std::sqrt(arg) : 0.0;
+  for (int s = 0; s < 2; ++s) {
+    // R_s = (beta0 c + beta1 c^k + beta2 c^{k-1})/dt + v.grad c - div(grad c + z c grad phi) - f.
+    // On an axis-aligned Q1 cube lap(c) = lap(phi) = 0, so the divergence reduces to
+    // z grad c . grad phi.
+    double adv = 0, mig = 0;
+    for (int a = 0; a < dim; ++a) {
+      adv += S.va[a] * S.gc[s][a];
+      mig += S.gc[s][a] * S.gp[a];
+    }
+    S.R[s] = S.kappa * S.c[s] + S.hs[s] + adv - kZ[s] * mig - S.f[s];
+    for (int a = 0; a < 3; ++a) S.P[s][a] = (a < dim) ? S.va[a] - kZ[s] * S.gp[a] : 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ residual
+void element_residual(const Mesh& m, const Params& p, int64_t e, const double* U, const double* Uk,
+                      const double* Ukm1, const double* adv, double Fe[8][3]) {
+  const int dim = m.dim, nc = corner_count(dim);
+  double Ue[8][3], Uke[8][3], Ukm1e[8][3], Ve[8][3];
+  gather3(m, e, U, Ue);
+  gather3(m, e, Uk, Uke);
+  gather3(m, e, Ukm1, Ukm1e);
+  gatherd(m, e, adv, Ve);
+  for (int c = 0; c < nc; ++c)
+    for (int f = 0; f < 3; ++f) Fe[c][f] = 0.0;
+  const double lam2 = 2.0 * p.eps * p.eps;
+  for (int q = 0; q < nc; ++q) {
+    Qp Q;
+    eval_qp(m, e, q, Q);
+    QpPhys S;
+    qp_state(m, p, e, Q, Ue, Uke, Ukm1e, Ve, S);
+    for (int i = 0; i < nc; ++i) {
+      // Nernst-Planck rows (Def. 3):
+      // (q, (b0 c + b1 c^k + b2 c^{k-1})/dt) + (q, v.grad c) - (q, f)
+      //   + (grad q, grad c + z c grad phi + tau R (v - z grad phi))
+      for (int s = 0; s < 2; ++s) {
+        double adv_s = 0, flux = 0;
+        for (int a = 0; a < dim; ++a) adv_s += S.va[a] * S.gc[s][a];
+        for (int a = 0; a < dim; ++a)
+          flux += Q.dN[i][a] * (S.gc[s][a] + kZ[s] * S.c[s] * S.gp[a] + S.tau * S.R[s] * S.P[s][a]);
+        Fe[i][s] += Q.w * (Q.N[i] * (S.kappa * S.c[s] + S.hs[s] + adv_s - S.f[s]) + flux);
+      }
+      // Poisson row (Def. 3): 2 Lambda^2 (grad q, grad phi) - (q, sum z c) + (q, sum z tau R) - (q, f_phi)
+      double gg = 0;
+      for (int a = 0; a < dim; ++a) gg += Q.dN[i][a] * S.gp[a];
+      double charge = 0, fine = 0;
+      for (int s = 0; s < 2; ++s) {
+        charge += kZ[s] * S.c[s];
+        fine += kZ[s] * S.tau * S.R[s];
+      }
+      Fe[i][2] += Q.w * (lam2 * gg - Q.N[i] * charge + Q.N[i] * fine - Q.N[i] * S.f[2]);
+    }
+  }
+}
+
+void residual(const Mesh& m, const Params& p, const double* U, const double* Uk, const double* Ukm1,
+              const double* adv, double* F) {
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  const int nc = corner_count(m.dim);
+  for (int64_t i = 0; i < 3 * nn; ++i) F[i] = 0.0;
+  for (int64_t e = 0; e < (int64_t)m.el_nodes.size(); ++e) {
+    double Fe[8][3];
+    element_residual(m, p, e, U, Uk, Ukm1, adv, Fe);
+    // assemble with the transpose of the constraints
+    for (int c = 0; c < nc; ++c)
+      for (auto& pw : m.cons[m.el_nodes[e][c]])
+        for (int f = 0; f < 3; ++f) F[3 * pw.first + f] += pw.second * Fe[c][f];
+  }
+  for (int64_t i = 0; i < nn; ++i) {
+    if (m.hanging[i]) {
+      // constraint row: U_h - sum_p w_p U_p
+      for (int f = 0; f < 3; ++f) {
+        double v = U[3 * i + f];
+        for (auto& pw : m.cons[i]) v -= pw.second * U[3 * pw.first + f];
+        F[3 * i + f] = v;
+      }
+      continue;
+    }
+    for (int f = 0; f < 3; ++f) {
+      double g;
+      if (dirichlet(m, p, i, f, &g)) F[3 * i + f] = U[3 * i + f] - g;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ analytic Jacobian
+// Element Jacobian J[(i,fi),(j,fj)] = d Fe[i][fi] / d Ue[j][fj] (before constraints).
+void element_jacobian(const Mesh& m, const Params& p, int64_t e, const double* U, const double* Uk,
+                      const double* Ukm1, const double* adv, double Je[24][24]) {
+  const int dim = m.dim, nc = corner_count(dim);
+  double Ue[8][3], Uke[8][3], Ukm1e[8][3], Ve[8][3];
+  gather3(m, e, U, Ue);
+  gather3(m, e, Uk, Uke);
+  gather3(m, e, Ukm1, Ukm1e);
+  gatherd(m, e, adv, Ve);
+  std::memset(Je, 0, sizeof(double) * 24 * 24);
+  const double lam2 = 2.0 * p.eps * p.eps;
+  for (int q = 0; q < nc; ++q) {
+    Qp Q;
+    eval_qp(m, e, q, Q);
+    QpPhys S;
+    qp_state(m, p, e, Q, Ue, Uke, Ukm1e, Ve, S);
+    for (int j = 0; j < nc; ++j) {
+      // derivatives of R_s with respect to the trial functions of node j
+      double dRdc[2], dRdp[2];
+      for (int s = 0; s < 2; ++s) {
+        double pg = 0, gcg = 0;
+        for (int a = 0; a < dim; ++a) {
+          pg += S.P[s][a] * Q.dN[j][a];
+          gcg += S.gc[s][a] * Q.dN[j][a];
+        }
+        dRdc[s] = S.kappa * Q.N[j] + pg;
+        dRdp[s] = -kZ[s] * gcg;
+      }
+      for (int i = 0; i < nc; ++i) {
+        double gij = 0, gip = 0, vgj = 0;
+        for (int a = 0; a < dim; ++a) {
+          gij += Q.dN[i][a] * Q.dN[j][a];
+          gip += Q.dN[i][a] * S.gp[a];
+          vgj += S.va[a] * Q.dN[j][a];
+        }
+        for (int s = 0; s < 2; ++s) {
+          double giP = 0;
+          for (int a = 0; a < dim; ++a) giP += Q.dN[i][a] * S.P[s][a];
+          // d F_s,i / d c_s,j
+          Je[3 * i + s][3 * j + s] +=
+              Q.w * (Q.N[i] * (S.kappa * Q.N[j] + vgj) + gij + kZ[s] * Q.N[j] * gip + S.tau * dRdc[s] * giP);
+          // d F_s,i / d phi_j
+          Je[3 * i + s][3 * j + 2] +=
+              Q.w * (kZ[s] * S.c[s] * gij + S.tau * dRdp[s] * giP - S.tau * S.R[s] * kZ[s] * gij);
+          // d F_phi,i / d c_s,j
+          Je[3 * i + 2][3 * j + s] += Q.w * (-Q.N[i] * kZ[s] * Q.N[j] + Q.N[i] * kZ[s] * S.tau * dRdc[s]);
+        }
+        Je[3 * i + 2][3 * j + 2] +=
+            Q.w * (lam2 * gij + Q.N[i] * (kZ[0] * S.tau * dRdp[0] + kZ[1] * S.tau * dRdp[1]));
+      }
+    }
+  }
+}
+
+// Triplets of the global Jacobian (duplicates to be summed by the caller).
+int64_t jacobian_triplets(const Mesh& m, const Params& p, const double* U, const double* Uk,
+                          const double* Ukm1, const double* adv, int64_t* I, int64_t* J, double* X) {
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  const int nc = corner_count(m.dim);
+  // row kind: 0 = PDE row, 1 = Dirichlet, 2 = hanging
+  std::vector<char> kind(3 * nn, 0);
+  for (int64_t i = 0; i < nn; ++i)
+    for (int f = 0; f < 3; ++f) {
+      double g;
+      if (m.hanging[i]) kind[3 * i + f] = 2;
+      else if (dirichlet(m, p, i, f, &g)) kind[3 * i + f] = 1;
+    }
+  int64_t k = 0;
+  auto put = [&](int64_t r, int64_t c, double v) {
+    if (I) { I[k] = r; J[k] = c; X[k] = v; }
+    ++k;
+  };
+  for (int64_t e = 0; e < (int64_t)m.el_nodes.size(); ++e) {
+    double Je[24][24];
+    if (I) element_jacobian(m, p, e, U, Uk, Ukm1, adv, Je);
+    for (int ci = 0; ci < nc; ++ci)
+      for (auto& pi : m.cons[m.el_nodes[e][ci]])
+        for (int fi = 0; fi < 3; ++fi) {
+          const int64_t r = 3 * pi.first + fi;
+          if (kind[r] != 0) continue;
+          for (int cj = 0; cj < nc; ++cj)
+            for (auto& pj : m.cons[m.el_nodes[e][cj]])
+              for (int fj = 0; fj < 3; ++fj)
+                put(r, 3 * pj.first + fj, I ? pi.second * pj.second * Je[3 * ci + fi][3 * cj + fj] : 0.0);
+        }
+  }
+  for (int64_t i = 0; i < nn; ++i)
+    for (int f = 0; f < 3; ++f) {
+      const int64_t r = 3 * i + f;
+      if (kind[r] == 1) put(r, r, 1.0);
+      if (kind[r] == 2) {
+        put(r, r, 1.0);
+        for (auto& pw : m.cons[i]) put(r, 3 * pw.first + f, -pw.second);
+      }
+    }
+  return k;
+}
+
+// ------------------------------------------------------------------ matrix-free Jv
+// Directional derivative of the residual written from the linearised Gauss-point
+// expressions (an independent derivation from element_jacobian).
+void jv(const Mesh& m, const Params& p, const double* U, const double* Uk, const double* Ukm1,
+        const double* adv, const double* V, double* JV) {
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  const int dim = m.dim, nc = corner_count(dim);
+  const double lam2 = 2.0 * p.eps * p.eps;
+  for (int64_t i = 0; i < 3 * nn; ++i) JV[i] = 0.0;
+  for (int64_t e = 0; e < (int64_t)m.el_nodes.size(); ++e) {
+    double Ue[8][3], Uke[8][3], Ukm1e[8][3], Ve[8][3], De[8][3], Fe[8][3];
+    gather3(m, e, U, Ue);
+    gather3(m, e, Uk, Uke);
+    gather3(m, e, Ukm1, Ukm1e);
+    gatherd(m, e, adv, Ve);
+    gather3(m, e, V, De);
+    for (int c = 0; c < nc; ++c)
+      for (int f = 0; f < 3; ++f) Fe[c][f] = 0.0;
+    for (int q = 0; q < nc; ++q) {
+      Qp Q;
+      eval_qp(m, e, q, Q);
+      QpPhys S;
+      qp_state(m, p, e, Q, Ue, Uke, Ukm1e, Ve, S);
+      double dc[2] = {0, 0}, dgc[2][3] = {{0, 0, 0}, {0, 0, 0}}, dgp[3] = {0, 0, 0};
+      for (int c = 0; c < nc; ++c) {
+        for (int s = 0; s < 2; ++s) {
+          dc[s] += Q.N[c] * De[c][s];
+          for (int a = 0; a < dim; ++a) dgc[s][a] += Q.dN[c][a] * De[c][s];
+        }
+        for (int a = 0; a < dim; ++a) dgp[a] += Q.dN[c][a] * De[c][2];
+      }
+      double dR[2], mass[2];
+      for (int s = 0; s < 2; ++s) {
+        double vdg = 0, a1 = 0, a2 = 0;
+        for (int a = 0; a < dim; ++a) {
+          vdg += S.va[a] * dgc[s][a];
+          a1 += dgc[s][a] * S.gp[a];
+          a2 += S.gc[s][a] * dgp[a];
+        }
+        mass[s] = S.kappa * dc[s] + vdg;
+        dR[s] = mass[s] - kZ[s] * (a1 + a2);
+      }
+      for (int i = 0; i < nc; ++i) {
+        for (int s = 0; s < 2; ++s) {
+          double flux = 0;
+          for (int a = 0; a < dim; ++a)
+            flux += Q.dN[i][a] * (dgc[s][a] + kZ[s] * (dc[s] * S.gp[a] + S.c[s] * dgp[a]) +
+                                  S.tau * dR[s] * S.P[s][a] - S.tau * S.R[s] * kZ[s] * dgp[a]);
+          Fe[i][s] += Q.w * (Q.N[i] * mass[s] + flux);
+        }
+        double gg = 0;
+        for (int a = 0; a < dim; ++a) gg += Q.dN[i][a] * dgp[a];
+        const double charge = kZ[0] * dc[0] + kZ[1] * dc[1];
+        const double fine = S.tau * (kZ[0] * dR[0] + kZ[1] * dR[1]);
+        Fe[i][2] += Q.w * (lam2 * gg - Q.N[i] * charge + Q.N[i] * fine);
+      }
+    }
+    for (int c = 0; c < nc; ++c)
+      for (auto& pw : m.cons[m.el_nodes[e][c]])
+        for (int f = 0; f < 3; ++f) JV[3 * pw.first + f] += pw.second * Fe[c][f];
+  }
+  for (int64_t i = 0; i < nn; ++i) {
+    if (m.hanging[i]) {
+      for (int f = 0; f < 3; ++f) {
+        double v = V[3 * i + f];
+        for (auto& pw : m.cons[i]) v -= pw.second * V[3 * pw.first + f];
+        JV[3 * i + f] = v;
+      }
+      continue;
+    }
+    for (int f = 0; f < 3; ++f) {
+      double g;
+      if (dirichlet(m, p, i, f, &g)) JV[3 * i + f] = V[3 * i + f];
+    }
+  }
+}
+
+}  // namespace
+
+// ================================================================== C interface
+extern "C" {
+
+void* ora_mesh_build(int dim, int max_level, int64_t n, const int32_t* anchors, const uint8_t* levels,
+                     int32_t* err) {
+  Mesh* m = new Mesh();
+  const int rc = build_mesh(*m, dim, max_level, n, anchors, levels);
+  *err = rc;
+  if (rc != ORA_OK) {
+    delete m;
+    return nullptr;
+  }
+  return m;
+}
+
+void ora_mesh_free(void* h) { delete static_cast<Mesh*>(h); }
+
+void ora_mesh_sizes(void* h, int64_t* ne, int64_t* nn, int64_t* nh) {
+  const Mesh& m = *static_cast<Mesh*>(h);
+  *ne = (int64_t)m.el_nodes.size();
+  *nn = (int64_t)m.node_xyz.size();
+  int64_t c = 0;
+  for (char x : m.hanging) c += x;
+  *nh = c;
+}
+
+// Integer node coordinates [nn][dim], hanging flags [nn], element corner ids [ne][2^dim].
+void ora_mesh_nodes(void* h, int64_t* xyz, int32_t* hanging, int64_t* el_nodes) {
+  const Mesh& m = *static_cast<Mesh*>(h);
+  for (size_t i = 0; i < m.node_xyz.size(); ++i) {
+    for (int k = 0; k < m.dim; ++k) xyz[i * m.dim + k] = m.node_xyz[i][k];
+    hanging[i] = m.hanging[i];
+  }
+  const int nc = corner_count(m.dim);
+  for (size_t e = 0; e < m.el_nodes.size(); ++e)
+    for (int c = 0; c < nc; ++c) el_nodes[e * nc + c] = m.el_nodes[e][c];
+}
+
+// Constraint triplets (row node, parent node, weight) of the hanging nodes.
+int64_t ora_mesh_constraints(void* h, int64_t* rows, int64_t* cols, double* w) {
+  const Mesh& m = *static_cast<Mesh*>(h);
+  int64_t k = 0;
+  for (size_t i = 0; i < m.node_xyz.size(); ++i) {
+    if (!m.hanging[i]) continue;
+    for (auto& pw : m.cons[i]) {
+      if (rows) { rows[k] = (int64_t)i; cols[k] = pw.first; w[k] = pw.second; }
+      ++k;
+    }
+  }
+  return k;
+}
+
+void ora_residual(void* h, const Params* p, const double* U, const double* Uk, const double* Ukm1,
+                  const double* adv, double* F) {
+  residual(*static_cast<Mesh*>(h), *p, U, Uk, Ukm1, adv, F);
+}
+
+int64_t ora_jacobian(void* h, const Params* p, const double* U, const double* Uk, const double* Ukm1,
+                     const double* adv, int64_t* I, int64_t* J, double* X) {
+  return jacobian_triplets(*static_cast<Mesh*>(h), *p, U, Uk, Ukm1, adv, I, J, X);
+}
+
+void ora_jv(void* h, const Params* p, const double* U, const double* Uk, const double* Ukm1,
+            const double* adv, const double* V, double* JV) {
+  jv(*static_cast<Mesh*>(h), *p, U, Uk, Ukm1, adv, V, JV);
+}
+
+// Strong residuals R_+, R_- and tau_c at one Gauss point of element e (for the
+// strong-form check): out = [R+, R-, tau].
+void ora_qp_eval(void* h, const Params* p, int64_t e, int q, const double* U, const double* Uk,
+                 const double* Ukm1, const double* adv, double* out) {
+  const Mesh& m = *static_cast<Mesh*>(h);
+  double Ue[8][3], Uke[8][3], Ukm1e[8][3], Ve[8][3];
+  gather3(m, e, U, Ue);
+  gather3(m, e, Uk, Uke);
+  gather3(m, e, Ukm1, Ukm1e);
+  gatherd(m, e, adv, Ve);
+  Qp Q;
+  eval_qp(m, e, q, Q);
+  QpPhys S;
+  qp_state(m, *p, e, Q, Ue, Uke, Ukm1e, Ve, S);
+  out[0] = S.R[0];
+  out[1] = S.R[1];
+  out[2] = S.tau;
+}
+
+// Row kinds [nn][3] (0 = PDE row, 1 = Dirichlet, 2 = hanging) and Dirichlet values.
+void ora_bc_rows(void* h, const Params* p, int32_t* kind, double* g) {
+  const Mesh& m = *static_cast<Mesh*>(h);
+  for (size_t i = 0; i < m.node_xyz.size(); ++i)
+    for (int f = 0; f < 3; ++f) {
+      double v = 0.0;
+      int k = 0;
+      if (m.hanging[i]) k = 2;
+      else if (dirichlet(m, *p, (int64_t)i, f, &v)) k = 1;
+      kind[3 * i + f] = k;
+      g[3 * i + f] = v;
+    }
+}
+
+// Manufactured solution at points x [n][3]: out [n][6] = (c+, c-, phi, u, v, w) and
+// forcing [n][3] = (f+, f-, f_phi).
+void ora_mms(int dim, double eps, double t, int steady, int64_t n, const double* x, double* vals,
+             double* forcing) {
+  for (int64_t i = 0; i < n; ++i) {
+    MmsField mf[6];
+    mms_fields(dim, x + 3 * i, t, steady, mf);
+    for (int f = 0; f < 6; ++f) vals[6 * i + f] = mf[f].val;
+    mms_forcing(dim, x + 3 * i, t, eps, steady, forcing + 3 * i);
+  }
+}
+
+}  // extern "C"
