@@ -1,0 +1,334 @@
+"""Benchmark: BDF time steps of the VMS PNP block on the 3D near-membrane octree.
+
+Workload (the transient membrane configuration): unit cube, octree base level 5,
+level 8 for every octant with z_min < 0.05, 2:1 graded (971,776 elements, 1,047,407
+nodes, 3.14 M unknowns c+, c-, phi); Lambda = 1e-3, V = 20, dt = 1e-3; membrane
+at z = 0 (phi = 0, c+ = 2, c- zero flux), reservoir at z = 1 (phi = V, c+- = 1),
+zero-flux side walls; c+- = 1 + seeded uniform noise of amplitude 1e-3, phi linear.
+The velocity is zero (no Navier-Stokes block in this library).
+
+One step = one pnp_time_step: BDF2 (BDF1 first), Newton to ||F|| <= 1e-8 ||F0||,
+GMRES(30) with 3x3 block-Jacobi on the exact Jacobian action.  Modes:
+  mixed : FP32 J V inside an inexact Newton (Eisenstat-Walker), FP64 residual, dots,
+          orthogonalisation; learned start if a trained network is supplied, else
+          the extrapolated start 2 U^k - U^{k-1}.
+  plain : FP64 J V, GMRES rtol 1e-8 per Newton step, previous-step start (the paper's).
+
+value = unknowns advanced per second = 3 N x steps / time (GDoF/s), timed with CUDA
+events on the library's stream.  The dominant kernel's roofline comes from the
+library's own event timing of each launch class during the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+for _p in (ROOT, os.path.join(ROOT, "oracle")):
+    if _p not in sys.path:
+        sys.path.insert(0, _p)
+
+METRIC = "PNP Jv GDoF/s (% HBM peak); s per PNP–NS step at rel-resid 1e-8, plain vs mixed+learned"
+EPS, VOLT, DT = 1e-3, 20.0, 1e-3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "plain"])
+    ap.add_argument("--small", action="store_true", help="level 4-7 miniature (profiling captures)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-mode comparison step")
+    return ap.parse_args()
+
+
+def workload_octants(small: bool):
+    from paper_2301_05985_gb300 import workloads as W
+    return W.membrane_band_octants(4, 7, 0.05) if small else W.membrane_band_octants(5, 8, 0.05)
+
+
+def mode_params(pnp, mode):
+    if mode == "mixed":
+        return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F32, start_mode=pnp.PNP_START_LEARNED,
+                                  newton_rtol=1e-8, gmres_restart=30, gmres_max_it=3000)
+    return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F64, start_mode=pnp.PNP_START_PREVIOUS,
+                              newton_rtol=1e-8, gmres_rtol=1e-8, gmres_restart=100, gmres_max_it=4000)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks / throttle reasons while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 4 + i and "Active" in r[4 + i]
+                          and "Not" not in r[4 + i]})
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(self.rows), "reasons": reasons}
+
+
+def setup_ctx(pnp, W, torch, oc, mode):
+    mesh = pnp.Mesh(oc)
+    ctx = pnp.Context(mesh, mode_params(pnp, mode), torch.cuda.current_stream().cuda_stream)
+    ctx.set_bcs(W.membrane_bcs(3, VOLT, 2.0))
+    U0 = W.noisy_state(mesh.ijk, oc.max_level, seed=0, amp=1e-3, phi_bottom=0.0, phi_top=VOLT)
+    ctx.set_field(pnp.PNP_FIELD_U, U0)
+    ctx.make_consistent()
+    ctx.reset_history()
+    return mesh, ctx
+
+
+def cpu_baseline_oracle(n_steps: int = 1):
+    """The FP64 oracle (single-threaded C++ + SciPy sparse direct solve) on a bounded
+    sample: the same physics on the level 3-5 miniature of the membrane octree."""
+    import oracle as O
+    from paper_2301_05985_gb300 import workloads as W
+    oc = W.membrane_band_octants(3, 5, 0.05)
+    m = O.OracleMesh(oc)
+    bcs = W.membrane_bcs(3, VOLT, 2.0)
+    U = W.noisy_state(m.ijk, oc.max_level, seed=0, amp=1e-3, phi_bottom=0.0, phi_top=VOLT)
+    p = O.Params(eps=EPS, dt=DT, beta=(1.0, -1.0, 0.0), bc_type=bcs.types, bc_val=bcs.values)
+    U = m.make_consistent(U, p)
+    Uk = Ukm1 = U
+    t0 = time.perf_counter()
+    for k in range(n_steps):
+        beta = O.bdf_coefficients(k)
+        p = O.Params(eps=EPS, dt=DT, beta=beta, bc_type=bcs.types, bc_val=bcs.values)
+        res = O.newton(m, p, Uk, Uk, Ukm1, None, rtol=1e-8)
+        Ukm1, Uk = Uk, res.U
+    t = time.perf_counter() - t0
+    return {"value": 3 * m.n_nodes * n_steps / t / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_steps} BDF step(s) of the same physics on the level 3-5 miniature of the membrane "
+                      f"octree ({m.n_elem} elements, {m.n_nodes} nodes), oracle Newton with direct sparse "
+                      f"solves, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass  # the oracle has nothing to warm up
+    vals = []
+    t0 = time.perf_counter()
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline_oracle(1)
+        vals.append(cb["value"])
+    t = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    out = {"metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "membrane-band octree level 3-5 miniature (oracle sample)", "eps": EPS,
+                      "V": VOLT, "dt": DT},
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": v},
+           "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def roofline(prof, peaks, jv_traffic):
+    best = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, d = best
+    if d["count"] == 0 or d["ms"] <= 0:
+        return None, None
+    gbs = d["alg_bytes"] / (d["ms"] * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = jv_traffic.get(name)
+    rl = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+          "traffic": traffic, "kernel": name, "launches": d["count"],
+          "avg_launch_ms": d["ms"] / d["count"],
+          "alg_bytes_per_launch": d["alg_bytes"] / d["count"],
+          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback"}
+    return rl, name
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_2301_05985_gb300 import pnp
+    from paper_2301_05985_gb300 import workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pnp.lib()
+    oc = workload_octants(args.small)
+    mesh, ctx = setup_ctx(pnp, W, torch, oc, args.mode)
+    N = mesh.n_nodes
+    stream = torch.cuda.current_stream()
+
+    stats = []
+    for _ in range(args.warmup):
+        ctx.time_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = pnp.kernel_launches()
+    ctx.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(ctx.time_step().as_dict())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    launches = pnp.kernel_launches() - launches0
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = 3.0 * N * args.steps * world / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with the state held in pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hU = [torch.empty((N, 3), dtype=torch.float64, pin_memory=True) for _ in range(3)]
+        ctx.get_field(pnp.PNP_FIELD_U_PREV, hU[0], pnp.PNP_HOST)
+        ctx.get_field(pnp.PNP_FIELD_U_PREV2, hU[1], pnp.PNP_HOST)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.set_field(pnp.PNP_FIELD_U_PREV, hU[0], pnp.PNP_HOST)
+            ctx.set_field(pnp.PNP_FIELD_U_PREV2, hU[1], pnp.PNP_HOST)
+            ctx.time_step()
+            ctx.get_field(pnp.PNP_FIELD_U, hU[2], pnp.PNP_HOST)
+            hU = [hU[2], hU[0], hU[1]]
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": 3.0 * N * args.steps * world / t_e2e / 1e9, "unit": "GDoF/s",
+               "h2d_bytes_per_step": 2 * 24 * N, "d2h_bytes_per_step": 24 * N,
+               "ms_per_step": 1e3 * t_e2e / args.steps}
+
+    # plain-mode comparison (one step from the same state; not part of the timed value)
+    plain = None
+    if not args.no_plain and rank == 0:
+        mesh_p, ctx_p = setup_ctx(pnp, W, torch, oc, "plain")
+        for _ in range(2):
+            ctx_p.time_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ctx_p.time_step().as_dict()
+        torch.cuda.synchronize()
+        plain = {"s_per_step": time.perf_counter() - t0, "newton_its": st["newton_its"],
+                 "krylov_its": st["krylov_its"], "after_steps": 2}
+        ctx_p.close()
+
+    peaks = measured_peaks()
+    traffic = {}
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            tj = json.load(open(tp))
+            import hashlib
+            src = open(os.path.join(ROOT, "paper_2301_05985_gb300", "csrc", "element_kernels.cu"), "rb").read()
+            if tj.get("element_kernels_sha256") == hashlib.sha256(src).hexdigest() and \
+                    tj.get("workload") == ("small" if args.small else "full"):
+                traffic = tj.get("traffic_per_launch", {})
+        except Exception:
+            traffic = {}
+    rl, dom = roofline(prof, peaks, traffic)
+    jv_name = "jv32" if args.mode == "mixed" else "jv64"
+    jv = prof[jv_name]
+    jv_gdofs = 3.0 * N * jv["count"] / (jv["ms"] * 1e-3) / 1e9 if jv["ms"] > 0 else None
+    jv_gbs = jv["alg_bytes"] / (jv["ms"] * 1e-3) / 1e9 if jv["ms"] > 0 else None
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline_oracle(2)
+    nt = sum(s["newton_its"] for s in stats)
+    kt = sum(s["krylov_its"] for s in stats)
+    out = {
+        "metric": METRIC, "value": round(value, 6), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": ("membrane-band octree L4-7 miniature" if args.small else
+                                "3D membrane-band octree, base level 5, level 8 for z<0.05 (2:1 graded)"),
+                   "n_elem": mesh.n_elem, "n_nodes": N, "n_hanging": mesh.n_hanging, "dofs": 3 * N,
+                   "eps": EPS, "V": VOLT, "dt": DT, "mode": args.mode, "velocity": "zero (no NS block)",
+                   "l2": "working set > L2 (3.1M-dof vectors, 31-vector Krylov basis = 780 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": rl,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "newton_its_per_step": nt / args.steps, "krylov_its_per_step": kt / args.steps,
+        "s_per_step": ms * 1e-3 / args.steps,
+        "jv_kernel": {"name": jv_name, "gdofs": jv_gdofs, "alg_gbs": jv_gbs,
+                      "avg_ms": jv["ms"] / jv["count"] if jv["count"] else None},
+        "time_share": {k: round(v["ms"] / ms, 4) for k, v in prof.items()},
+        "plain_step": plain,
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * pnp.h -- C ABI of the GB300 library for the VMS-stabilised Poisson-Nernst-Planck block
+ * on 2:1-balanced octrees (Kim, Saurabh, Khanwale, Mani, Anand,
+ * Ganapathysubramanian, arXiv 2301.05985).
+ *
+ * What the library computes
+ * -------------------------
+ * Unknowns per mesh node: c+, c-, phi (valences +1, -1).  Non-dimensional PNP of
+ * Sec. 2.2 (Eqs. nondim_poisson, nondim_np):
+ *     -2 eps^2 lap(phi) = c+ - c-,      dc/dt + v.grad c = div(grad c + z c grad phi),
+ * eps = Lambda (Debye length / domain length).  Time discretisation: BDF with
+ * coefficients beta0..beta2 (Def. 1, Sec. 3).  Space: trilinear (bilinear in 2D) Q1
+ * elements on octree leaves, 2x2x2 Gauss quadrature, VMS fine-scale closure
+ * c^f = -tau_c R_c with tau_c = (4/dt^2 + (2/h)^2 |v|^2 + C_I d (2/h)^4)^(-1/2)
+ * (Sec. 3.1), giving the discrete residual of Def. 3 (Poisson and Nernst-Planck rows).
+ * Newton's method with the analytic Jacobian (Sec. 4.1, Eq. newton_linear_system) is
+ * applied matrix-free: the library evaluates J(U) V directly.
+ *
+ * Conventions
+ * -----------
+ * - Domain: unit square (dim 2) or cube (dim 3).  Octant anchors and node coordinates
+ *   are integers in units of 2^-max_level.  Faces: 2*axis + side (x-=0, x+=1, y-=2,
+ *   y+=3, z-=4, z+=5).  Fields: c+ = 0, c- = 1, phi = 2.
+ * - Vectors of unknowns are node-major FP64 arrays [n_nodes][3] (c+, c-, phi
+ *   interleaved) in the library's node order (Morton order of node coordinates; use
+ *   pnp_mesh_node_coords to map).  Velocities are [n_nodes][dim].
+ * - Hanging nodes (edge midpoints / face centres of a coarser neighbour) are kept in
+ *   every vector; their rows are the constraints U_h - sum_p w_p U_p (weights 1/2 or
+ *   1/4) and their values never enter element computations.  Dirichlet rows are
+ *   U_i - g_i in the residual and V_i in J V.  A node on several Dirichlet faces takes
+ *   the value of the highest-numbered one; hanging nodes are never Dirichlet rows.
+ * - Pointers marked "device" must be CUDA device pointers valid on the context's
+ *   device; "host" pointers are ordinary host memory.  The caller owns every pointer it
+ *   passes; the library owns its handles and internal scratch, released by the
+ *   *_destroy calls.  All device work of a context is issued on the stream given at
+ *   pnp_ctx_create; calls return after that work is complete unless stated otherwise.
+ * - Every call returns PNP_OK (0) or an error code; nothing aborts.  After a CUDA
+ *   error the context is latched: later calls on it return PNP_ERR_CUDA.
+ *   pnp_last_error() gives a message for the calling thread's last failure.
+ * - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef PNP_H
+#define PNP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum pnp_status {
+  PNP_OK = 0,
+  PNP_ERR_ARG = 1,               /* bad argument (null pointer, size, enum value) */
+  PNP_ERR_MESH = 2,              /* octants overlap, leave gaps or are misaligned */
+  PNP_ERR_MESH_UNBALANCED = 3,   /* neighbours (face, edge or corner) differ by > 1 level */
+  PNP_ERR_NAN = 4,               /* a norm became NaN or Inf */
+  PNP_ERR_KRYLOV_MAXIT = 5,      /* GMRES hit its iteration limit */
+  PNP_ERR_NEWTON_DIVERGED = 6,   /* Newton hit its iteration limit or line search failed */
+  PNP_ERR_CUDA = 7,              /* a CUDA call failed; the context is latched */
+  PNP_ERR_DEVICE_FLAG = 8,       /* a kernel's own check failed (bad index / input) */
+  PNP_ERR_NOMEM = 9,             /* host or device allocation failed */
+  PNP_ERR_STATE = 10             /* call not valid in the current state */
+};
+
+enum { PNP_C_PLUS = 0, PNP_C_MINUS = 1, PNP_PHI = 2 };
+enum { PNP_NATURAL = 0, PNP_DIRICHLET = 1 };
+enum { PNP_F64 = 0, PNP_F32 = 1 };
+enum { PNP_DEVICE = 0, PNP_HOST = 1 };
+enum {
+  PNP_FIELD_U = 0,             /* U^{k+1} iterate / current state      [n][3] */
+  PNP_FIELD_U_PREV = 1,        /* U^k                                  [n][3] */
+  PNP_FIELD_U_PREV2 = 2,       /* U^{k-1}                              [n][3] */
+  PNP_FIELD_ADVECTION = 3,     /* advection velocity v~ of the residual [n][dim] */
+  PNP_FIELD_VELOCITY = 4,      /* fluid velocity v^k                    [n][dim] */
+  PNP_FIELD_VELOCITY_PREV = 5  /* fluid velocity v^{k-1}                [n][dim] */
+};
+enum { PNP_START_PREVIOUS = 0, PNP_START_EXTRAPOLATE = 1, PNP_START_LEARNED = 2 };
+
+typedef struct pnp_mesh pnp_mesh;
+typedef struct pnp_ctx pnp_ctx;
+
+/* Parameters.  Fill with pnp_params_default, then override. */
+typedef struct pnp_params {
+  double eps;            /* Lambda; Poisson coefficient is 2*eps^2 (Eq. nondim_poisson) */
+  double dt;             /* time step (ignored when steady) */
+  double C_I;            /* tau_c constant (6, Sec. 3.1) */
+  double beta0, beta1, beta2; /* BDF coefficients used by pnp_residual / pnp_jv /
+                                 pnp_newton_solve; pnp_time_step sets them itself */
+  int32_t steady;        /* 1: drop the d/dt terms and the 4/dt^2 term of tau_c */
+  int32_t bdf_order;     /* pnp_time_step: 1 or 2 (first step is always BDF1) */
+  double newton_rtol;    /* stop when ||F(U^m)||_2 <= newton_rtol ||F(U^0)||_2 */
+  double newton_atol;    /* ... or ||F(U^m)||_2 <= newton_atol */
+  int32_t newton_max_it;
+  int32_t line_search;   /* 1: backtracking (halving, Armijo 1e-4) on ||F||_2 */
+  int32_t gmres_restart; /* Krylov basis size m (<= 200) */
+  int32_t gmres_max_it;  /* total Krylov iterations per linear solve */
+  double gmres_rtol;     /* linear tolerance (plain mode) */
+  int32_t precision;     /* PNP_F64: FP64 J V in Krylov (plain); PNP_F32: FP32 J V
+                            inside an inexact Newton (Eisenstat-Walker forcing) */
+  int32_t start_mode;    /* pnp_time_step Newton start: PNP_START_* */
+  double ew_eta_max;     /* Eisenstat-Walker: largest forcing term (0.9) */
+  double ew_eta_min;     /* Eisenstat-Walker: smallest forcing term (1e-4) */
+  int32_t monitor;       /* 1: one line per Newton iteration on stderr */
+  int32_t f64_fallback;  /* 1: when an FP32-J V Newton iteration fails to decrease
+                            ||F||, redo it with FP64 J V (default 1) */
+} pnp_params;
+
+typedef struct pnp_solve_stats {
+  int32_t status;        /* pnp_status of the solve */
+  int32_t newton_its;
+  int32_t krylov_its;    /* total over the Newton iterations */
+  int32_t residual_evals;
+  int32_t jv_evals;
+  int32_t start_used;    /* PNP_START_* actually used (learned start may fall back) */
+  int32_t f64_fallbacks; /* Newton iterations redone with FP64 J V */
+  int32_t pad_;
+  double res0;           /* ||F(U^0)||_2 */
+  double res_final;      /* ||F(U^m)||_2 */
+  double res_start_extrapolated; /* learned start only: ||F|| of the extrapolated start */
+  double res_start_learned;      /* learned start only: ||F|| of the network's start */
+  double wall_ms;        /* host wall time of the call */
+} pnp_solve_stats;
+
+/* Message for the calling thread's most recent failure ("" if none).  Static storage. */
+const char* pnp_last_error(void);
+
+/* Library version string. */
+const char* pnp_version(void);
+
+void pnp_params_default(pnp_params* p);
+
+/* ---------------------------------------------------------------- mesh (host) ---- */
+/* Build the Q1 mesh of a complete linear octree (Sec. 4.2: octree leaves are the
+ * elements).  anchors: host int32 [n_oct][dim] (units of 2^-max_level, aligned to the
+ * octant size), levels: host uint8 [n_oct] (0..max_level), max_level <= 16.  The
+ * octants must tile the unit domain without overlap (PNP_ERR_MESH) and be 2:1 balanced
+ * across faces, edges and corners (PNP_ERR_MESH_UNBALANCED).  Elements are reordered
+ * by Morton order; nodes are the unique element corners in Morton order.  *out is
+ * owned by the caller and released by pnp_mesh_destroy. */
+int pnp_mesh_create(int dim, int max_level, int64_t n_oct, const int32_t* anchors,
+                    const uint8_t* levels, pnp_mesh** out);
+void pnp_mesh_destroy(pnp_mesh* m);
+int pnp_mesh_info(const pnp_mesh* m, int* dim, int* max_level, int64_t* n_elem,
+                  int64_t* n_nodes, int64_t* n_hanging);
+/* Integer node coordinates, host int32 [n_nodes][dim]. */
+int pnp_mesh_node_coords(const pnp_mesh* m, int32_t* ijk);
+/* Hanging flags, host uint8 [n_nodes] (1 = hanging). */
+int pnp_mesh_hanging(const pnp_mesh* m, uint8_t* flags);
+/* Element anchors host int32 [n_elem][dim] and levels host uint8 [n_elem] in the
+ * library's (Morton) element order. */
+int pnp_mesh_elements(const pnp_mesh* m, int32_t* anchors, uint8_t* levels);
+
+/* ---------------------------------------------------------------- context -------- */
+/* Create a context on the current CUDA device: uploads the mesh (the mesh may be
+ * destroyed afterwards), allocates fields and solver scratch.  stream: a cudaStream_t
+ * (NULL = legacy default stream) on which all of this context's work runs.  All
+ * fields start at zero; all faces start with natural (zero-flux) conditions. */
+int pnp_ctx_create(const pnp_mesh* m, const pnp_params* p, void* stream, pnp_ctx** out);
+void pnp_ctx_destroy(pnp_ctx* c);
+int pnp_set_params(pnp_ctx* c, const pnp_params* p);
+int pnp_get_params(const pnp_ctx* c, pnp_params* p);
+/* Boundary condition of one field on one face (Table tab:BC-AliMani style): type
+ * PNP_DIRICHLET (value g) or PNP_NATURAL (zero total flux for c+-, zero normal
+ * derivative for phi). */
+int pnp_set_bc(pnp_ctx* c, int face, int field, int type, double value);
+/* Copy a field in (set) or out (get).  where = PNP_DEVICE or PNP_HOST selects the kind
+ * of pointer; layout per the PNP_FIELD_* comments, FP64. */
+int pnp_set_field(pnp_ctx* c, int which, const double* src, int where);
+int pnp_get_field(pnp_ctx* c, int which, double* dst, int where);
+/* Impose Dirichlet values and hanging-node interpolation on PNP_FIELD_U. */
+int pnp_make_consistent(pnp_ctx* c);
+
+/* ---------------------------------------------------------------- operators ------ */
+/* F = residual of Def. 3 at U (device [n][3] FP64 each), using the context's
+ * U_PREV / U_PREV2 (BDF history), ADVECTION, parameters and boundary conditions. */
+int pnp_residual(pnp_ctx* c, const double* U, double* F);
+/* JV = J(U) V, the directional derivative of the residual (device pointers).
+ * precision PNP_F64: V, JV are FP64 [n][3]; PNP_F32: V, JV are FP32 [n][3] and the
+ * element arithmetic runs in FP32 (U is rounded to FP32 once per call). */
+int pnp_jv(pnp_ctx* c, const double* U, const void* V, void* JV, int precision);
+/* 3x3 diagonal blocks of J(U): D device FP64 [n][3][3] (row-major per node), exact
+ * for the assembled operator including hanging-node coupling. */
+int pnp_block_diag(pnp_ctx* c, const double* U, double* D);
+
+/* ---------------------------------------------------------------- solvers -------- */
+/* Solve J(U) x = b by right-preconditioned GMRES(m) (3x3 block-Jacobi preconditioner,
+ * classical Gram-Schmidt with reorthogonalisation, FP64 basis and dot products).
+ * U, b, x: device FP64 [n][3]; x is the initial guess on entry.  rtol relative to
+ * ||b||; precision selects the J V arithmetic. */
+int pnp_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol,
+              int precision, pnp_solve_stats* st);
+/* Newton solve of F(U) = 0 for PNP_FIELD_U in place, starting from its current
+ * value (made consistent first), with the context's parameters. */
+int pnp_newton_solve(pnp_ctx* c, pnp_solve_stats* st);
+/* One BDF time step (Def. 1): BDF1 on the first step, then bdf_order; advection
+ * v~ = 2 v^k - v^{k-1} (Eq. averaging1) from the VELOCITY fields; Newton start per
+ * start_mode; on success U_PREV2 <- U_PREV <- U^{k+1} = U and VELOCITY_PREV <-
+ * VELOCITY.  The BDF coefficients used are left in the context's parameters. */
+int pnp_time_step(pnp_ctx* c, pnp_solve_stats* st);
+/* Number of steps taken so far by pnp_time_step (0 after pnp_ctx_create or
+ * pnp_reset_history). */
+int pnp_step_count(const pnp_ctx* c, int64_t* k);
+/* Start a new trajectory: U_PREV and U_PREV2 <- U, step count <- 0. */
+int pnp_reset_history(pnp_ctx* c);
+
+/* ---------------------------------------------------------------- profiling ------ */
+/* Kernel classes timed with CUDA events recorded on the context's stream around each
+ * launch while profiling is on. */
+enum {
+  PNP_PROF_RESIDUAL = 0,   /* FP64 residual element kernel */
+  PNP_PROF_JV64 = 1,       /* FP64 J V element kernel */
+  PNP_PROF_JV32 = 2,       /* FP32 J V element kernel */
+  PNP_PROF_BLOCKDIAG = 3,  /* block-diagonal element kernel + 3x3 inversion */
+  PNP_PROF_ORTHO = 4,      /* Gram-Schmidt multi-dot / multi-axpy / norms */
+  PNP_PROF_PRECOND = 5,    /* block-Jacobi apply (and FP32 conversion) */
+  PNP_PROF_MLP = 6,        /* learned-start network kernels */
+  PNP_PROF_KINDS = 7
+};
+/* on != 0: clear the accumulated times and start recording; on == 0: stop. */
+int pnp_profile_enable(pnp_ctx* c, int on);
+/* Accumulated device time (ms), number of timed regions and algorithmic HBM bytes
+ * (each operand read once and each result written once, as the launches' sizes
+ * dictate) of one class since profiling was enabled; synchronises the stream.  Any
+ * output pointer may be NULL. */
+int pnp_profile_read(pnp_ctx* c, int kind, double* total_ms, int64_t* count, double* alg_bytes);
+/* Kernels launched by this process through the library since it was loaded. */
+int64_t pnp_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PNP_H */

@@ -1,0 +1,483 @@
+// capi.cu -- the extern "C" entry points declared in include/pnp.h: argument checks,
+// handle management, uploads and field copies.  Work runs on the context's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+
+static thread_local char g_err[512] = "";
+
+void pnp_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int ctx_check(pnp_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PNP_OK;
+  if (c && c->latched == cudaSuccess) c->latched = e;
+  pnp_set_error("%s: CUDA error %d (%s)", what, (int)e, cudaGetErrorString(e));
+  return PNP_ERR_CUDA;
+}
+
+#define CTX_GUARD(c)                                                                            \
+  do {                                                                                          \
+    if (!(c)) PNP_FAIL(PNP_ERR_ARG, "null context");                                            \
+    if ((c)->latched != cudaSuccess)                                                            \
+      PNP_FAIL(PNP_ERR_CUDA, "context latched after CUDA error %d (%s)", (int)(c)->latched,     \
+               cudaGetErrorString((c)->latched));                                               \
+  } while (0)
+
+#define CK(call)                                      \
+  do {                                                \
+    int _rc = ctx_check(c, (call), #call);            \
+    if (_rc) return _rc;                              \
+  } while (0)
+
+extern "C" {
+
+const char* pnp_last_error(void) { return g_err; }
+const char* pnp_version(void) { return "pnp-gb300 0.1 (sm_103a)"; }
+
+void pnp_params_default(pnp_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eps = 1e-2;
+  p->dt = 1e-3;
+  p->C_I = 6.0;
+  p->beta0 = 1.0;
+  p->beta1 = -1.0;
+  p->beta2 = 0.0;
+  p->steady = 0;
+  p->bdf_order = 2;
+  p->newton_rtol = 1e-8;
+  p->newton_atol = 0.0;
+  p->newton_max_it = 30;
+  p->line_search = 1;
+  p->gmres_restart = 30;
+  p->gmres_max_it = 2000;
+  p->gmres_rtol = 1e-8;
+  p->precision = PNP_F64;
+  p->start_mode = PNP_START_EXTRAPOLATE;
+  p->ew_eta_max = 0.9;
+  p->ew_eta_min = 1e-4;
+  p->monitor = 0;
+  p->f64_fallback = 1;
+}
+
+// ------------------------------------------------------------------ mesh
+int pnp_mesh_create(int dim, int max_level, int64_t n_oct, const int32_t* anchors, const uint8_t* levels,
+                    pnp_mesh** out) {
+  if (!out) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_create: out is null");
+  *out = nullptr;
+  pnp_mesh* m = new (std::nothrow) pnp_mesh();
+  if (!m) PNP_FAIL(PNP_ERR_NOMEM, "pnp_mesh_create: out of host memory");
+  int rc;
+  try {
+    rc = pnp_build_mesh(*m, dim, max_level, n_oct, anchors, levels);
+  } catch (const std::bad_alloc&) {
+    pnp_set_error("pnp_mesh_create: out of host memory");
+    rc = PNP_ERR_NOMEM;
+  }
+  if (rc != PNP_OK) {
+    delete m;
+    return rc;
+  }
+  *out = m;
+  return PNP_OK;
+}
+
+void pnp_mesh_destroy(pnp_mesh* m) { delete m; }
+
+int pnp_mesh_info(const pnp_mesh* m, int* dim, int* max_level, int64_t* n_elem, int64_t* n_nodes,
+                  int64_t* n_hanging) {
+  if (!m) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_info: null mesh");
+  if (dim) *dim = m->dim;
+  if (max_level) *max_level = m->L;
+  if (n_elem) *n_elem = m->n_elem;
+  if (n_nodes) *n_nodes = m->n_nodes;
+  if (n_hanging) *n_hanging = m->n_hanging;
+  return PNP_OK;
+}
+
+int pnp_mesh_node_coords(const pnp_mesh* m, int32_t* ijk) {
+  if (!m || !ijk) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_node_coords: null argument");
+  std::memcpy(ijk, m->node_ijk.data(), m->node_ijk.size() * sizeof(int32_t));
+  return PNP_OK;
+}
+
+int pnp_mesh_hanging(const pnp_mesh* m, uint8_t* flags) {
+  if (!m || !flags) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_hanging: null argument");
+  for (int64_t i = 0; i < m->n_nodes; ++i) flags[i] = m->node_hang[i] >= 0;
+  return PNP_OK;
+}
+
+int pnp_mesh_elements(const pnp_mesh* m, int32_t* anchors, uint8_t* levels) {
+  if (!m) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_elements: null mesh");
+  if (anchors) std::memcpy(anchors, m->el_anchor.data(), m->el_anchor.size() * sizeof(int32_t));
+  if (levels) std::memcpy(levels, m->el_level.data(), m->el_level.size());
+  return PNP_OK;
+}
+
+// ------------------------------------------------------------------ context
+static int check_params(const pnp_params* p) {
+  if (!p) PNP_FAIL(PNP_ERR_ARG, "null params");
+  if (!(p->eps > 0) || !std::isfinite(p->eps)) PNP_FAIL(PNP_ERR_ARG, "params: eps must be > 0");
+  if (!p->steady && (!(p->dt > 0) || !std::isfinite(p->dt))) PNP_FAIL(PNP_ERR_ARG, "params: dt must be > 0");
+  if (!(p->C_I > 0)) PNP_FAIL(PNP_ERR_ARG, "params: C_I must be > 0");
+  if (p->gmres_restart < 1 || p->gmres_restart > 200) PNP_FAIL(PNP_ERR_ARG, "params: gmres_restart in 1..200");
+  if (p->gmres_max_it < 1) PNP_FAIL(PNP_ERR_ARG, "params: gmres_max_it >= 1");
+  if (p->newton_max_it < 0) PNP_FAIL(PNP_ERR_ARG, "params: newton_max_it >= 0");
+  if (p->precision != PNP_F64 && p->precision != PNP_F32) PNP_FAIL(PNP_ERR_ARG, "params: bad precision");
+  if (p->start_mode < 0 || p->start_mode > 2) PNP_FAIL(PNP_ERR_ARG, "params: bad start_mode");
+  if (p->bdf_order != 1 && p->bdf_order != 2) PNP_FAIL(PNP_ERR_ARG, "params: bdf_order must be 1 or 2");
+  return PNP_OK;
+}
+
+static void free_ctx_memory(pnp_ctx* c) {
+  void* ptrs[] = {c->d_conn, c->d_level, c->d_faces, c->d_hnode, c->d_hpar, c->d_hnp, c->U, c->Uk, c->Ukm1,
+                  c->adv, c->vel, c->vel_prev, c->hs, c->U32, c->adv32, c->hs32, c->V32, c->JV32, c->F,
+                  c->dU, c->Ut, c->Ft, c->rhs, c->Dinv, c->basis, c->w, c->z, c->r, c->part, c->dsc, c->dflag};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->hpin) cudaFreeHost(c->hpin);
+}
+
+int pnp_ctx_create(const pnp_mesh* m, const pnp_params* p, void* stream, pnp_ctx** out) {
+  if (!out) PNP_FAIL(PNP_ERR_ARG, "pnp_ctx_create: out is null");
+  *out = nullptr;
+  if (!m) PNP_FAIL(PNP_ERR_ARG, "pnp_ctx_create: null mesh");
+  if (int rc = check_params(p)) return rc;
+  pnp_ctx* c = new (std::nothrow) pnp_ctx();
+  if (!c) PNP_FAIL(PNP_ERR_NOMEM, "pnp_ctx_create: out of host memory");
+  c->dim = m->dim;
+  c->L = m->L;
+  c->n_elem = m->n_elem;
+  c->n_nodes = m->n_nodes;
+  c->n_hanging = m->n_hanging;
+  c->prm = *p;
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  const int nc = 1 << m->dim;
+  const int64_t N = m->n_nodes;
+  auto fail = [&](int rc) {
+    free_ctx_memory(c);
+    delete c;
+    return rc;
+  };
+#define ALLOC(ptr, bytes)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 16);               \
+    if (e_ != cudaSuccess) {                                                               \
+      pnp_set_error("pnp_ctx_create: cudaMalloc(%zu) failed: %s", (size_t)(bytes),         \
+                    cudaGetErrorString(e_));                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? PNP_ERR_NOMEM : PNP_ERR_CUDA);         \
+    }                                                                                      \
+  } while (0)
+  ALLOC(c->d_conn, sizeof(int32_t) * m->n_elem * nc);
+  ALLOC(c->d_level, m->n_elem);
+  ALLOC(c->d_faces, N);
+  ALLOC(c->d_hnode, sizeof(int32_t) * m->n_hanging);
+  ALLOC(c->d_hpar, sizeof(int32_t) * 4 * m->n_hanging);
+  ALLOC(c->d_hnp, m->n_hanging);
+  const size_t v3 = sizeof(double) * 3 * N;
+  ALLOC(c->U, v3);
+  ALLOC(c->Uk, v3);
+  ALLOC(c->Ukm1, v3);
+  ALLOC(c->adv, v3);
+  ALLOC(c->vel, v3);
+  ALLOC(c->vel_prev, v3);
+  ALLOC(c->hs, sizeof(double) * 2 * N);
+  ALLOC(c->U32, sizeof(float) * 3 * N);
+  ALLOC(c->adv32, sizeof(float) * 3 * N);
+  ALLOC(c->hs32, sizeof(float) * 2 * N);
+  ALLOC(c->V32, sizeof(float) * 3 * N);
+  ALLOC(c->JV32, sizeof(float) * 3 * N);
+  ALLOC(c->F, v3);
+  ALLOC(c->dU, v3);
+  ALLOC(c->Ut, v3);
+  ALLOC(c->Ft, v3);
+  ALLOC(c->rhs, v3);
+  ALLOC(c->Dinv, sizeof(double) * 9 * N);
+  ALLOC(c->w, v3);
+  ALLOC(c->z, v3);
+  ALLOC(c->r, v3);
+  ALLOC(c->dflag, sizeof(int) * 4);
+#undef ALLOC
+  std::vector<uint8_t> faces(m->node_faces);
+  for (int64_t i = 0; i < N; ++i)
+    if (m->node_hang[i] >= 0) faces[i] |= 0x80;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (bytes && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  up(c->d_conn, m->el_conn.data(), sizeof(int32_t) * m->el_conn.size());
+  up(c->d_level, m->el_level.data(), m->el_level.size());
+  up(c->d_faces, faces.data(), faces.size());
+  up(c->d_hnode, m->hang_node.data(), sizeof(int32_t) * m->hang_node.size());
+  up(c->d_hpar, m->hang_par.data(), sizeof(int32_t) * m->hang_par.size());
+  up(c->d_hnp, m->hang_np.data(), m->hang_np.size());
+  for (double* f : {c->U, c->Uk, c->Ukm1, c->adv, c->vel, c->vel_prev})
+    if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, v3, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    pnp_set_error("pnp_ctx_create: upload failed: %s", cudaGetErrorString(e));
+    return fail(PNP_ERR_CUDA);
+  }
+  if (int rc = ctx_alloc_krylov(c, p->gmres_restart)) return fail(rc);
+  *out = c;
+  return PNP_OK;
+}
+
+}  // extern "C"
+
+int ctx_alloc_krylov(pnp_ctx* c, int m) {
+  if (m <= c->m_alloc) return PNP_OK;
+  if (c->basis) cudaFree(c->basis);
+  if (c->part) cudaFree(c->part);
+  if (c->dsc) cudaFree(c->dsc);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  c->basis = nullptr;
+  c->part = nullptr;
+  c->dsc = nullptr;
+  c->hpin = nullptr;
+  c->m_alloc = 0;
+  const size_t bb = sizeof(double) * (size_t)(m + 1) * (size_t)c->n3();
+  cudaError_t e = cudaMalloc((void**)&c->basis, bb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, sizeof(double) * (size_t)kRedBlocks * (m + 2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->dsc, sizeof(double) * (2 * (m + 2) + 16));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hpin, sizeof(double) * (2 * (m + 2) + 16));
+  if (e != cudaSuccess) {
+    pnp_set_error("Krylov scratch allocation (%zu bytes) failed: %s", bb, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PNP_ERR_NOMEM : PNP_ERR_CUDA;
+  }
+  c->basis_bytes = (int64_t)bb;
+  c->m_alloc = m;
+  return PNP_OK;
+}
+
+extern "C" {
+
+void pnp_ctx_destroy(pnp_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  pnp_mlp_release(c);
+  for (auto& pe : c->ev_pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  free_ctx_memory(c);
+  delete c;
+}
+
+int pnp_set_params(pnp_ctx* c, const pnp_params* p) {
+  CTX_GUARD(c);
+  if (int rc = check_params(p)) return rc;
+  if (int rc = ctx_alloc_krylov(c, p->gmres_restart)) return rc;
+  c->prm = *p;
+  return PNP_OK;
+}
+
+int pnp_get_params(const pnp_ctx* c, pnp_params* p) {
+  if (!c || !p) PNP_FAIL(PNP_ERR_ARG, "pnp_get_params: null argument");
+  *p = c->prm;
+  return PNP_OK;
+}
+
+int pnp_set_bc(pnp_ctx* c, int face, int field, int type, double value) {
+  CTX_GUARD(c);
+  if (face < 0 || face >= 2 * c->dim) PNP_FAIL(PNP_ERR_ARG, "pnp_set_bc: face %d out of range", face);
+  if (field < 0 || field > 2) PNP_FAIL(PNP_ERR_ARG, "pnp_set_bc: field %d out of range", field);
+  if (type != PNP_NATURAL && type != PNP_DIRICHLET) PNP_FAIL(PNP_ERR_ARG, "pnp_set_bc: bad type %d", type);
+  if (!std::isfinite(value)) PNP_FAIL(PNP_ERR_ARG, "pnp_set_bc: value not finite");
+  c->bc_type[face][field] = type;
+  c->bc_val[face][field] = value;
+  return PNP_OK;
+}
+
+static double* field_ptr(pnp_ctx* c, int which) {
+  switch (which) {
+    case PNP_FIELD_U: return c->U;
+    case PNP_FIELD_U_PREV: return c->Uk;
+    case PNP_FIELD_U_PREV2: return c->Ukm1;
+    case PNP_FIELD_ADVECTION: return c->adv;
+    case PNP_FIELD_VELOCITY: return c->vel;
+    case PNP_FIELD_VELOCITY_PREV: return c->vel_prev;
+  }
+  return nullptr;
+}
+
+int pnp_set_field(pnp_ctx* c, int which, const double* src, int where) {
+  CTX_GUARD(c);
+  double* dst = field_ptr(c, which);
+  if (!dst || !src) PNP_FAIL(PNP_ERR_ARG, "pnp_set_field: bad field %d or null source", which);
+  if (where != PNP_DEVICE && where != PNP_HOST) PNP_FAIL(PNP_ERR_ARG, "pnp_set_field: bad where");
+  const bool is_vel = which >= PNP_FIELD_ADVECTION;
+  const int64_t N = c->n_nodes;
+  const cudaMemcpyKind kind = where == PNP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (!is_vel || c->dim == 3) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * 3 * N, kind, c->stream));
+  } else {
+    // [N][dim] -> [N][3] through scratch (w)
+    CK(cudaMemcpyAsync(c->w, src, sizeof(double) * c->dim * N, kind, c->stream));
+    CK(launch_vel_pack(N, c->dim, c->w, dst, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_get_field(pnp_ctx* c, int which, double* dstp, int where) {
+  CTX_GUARD(c);
+  double* src = field_ptr(c, which);
+  if (!src || !dstp) PNP_FAIL(PNP_ERR_ARG, "pnp_get_field: bad field %d or null destination", which);
+  if (where != PNP_DEVICE && where != PNP_HOST) PNP_FAIL(PNP_ERR_ARG, "pnp_get_field: bad where");
+  const bool is_vel = which >= PNP_FIELD_ADVECTION;
+  const int64_t N = c->n_nodes;
+  const cudaMemcpyKind kind = where == PNP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (!is_vel || c->dim == 3) {
+    CK(cudaMemcpyAsync(dstp, src, sizeof(double) * 3 * N, kind, c->stream));
+  } else {
+    CK(launch_vel_unpack(N, c->dim, src, c->w, c->stream));
+    CK(cudaMemcpyAsync(dstp, c->w, sizeof(double) * c->dim * N, kind, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_make_consistent(pnp_ctx* c) {
+  CTX_GUARD(c);
+  CK(launch_make_consistent(c->rows(), c->U, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+// ------------------------------------------------------------------ operators
+int pnp_residual(pnp_ctx* c, const double* U, double* F) {
+  CTX_GUARD(c);
+  if (!U || !F) PNP_FAIL(PNP_ERR_ARG, "pnp_residual: null pointer");
+  if (int rc = ctx_prepare_history(c)) return rc;
+  if (int rc = ctx_residual(c, U, F)) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_jv(pnp_ctx* c, const double* U, const void* V, void* JV, int precision) {
+  CTX_GUARD(c);
+  if (!U || !V || !JV) PNP_FAIL(PNP_ERR_ARG, "pnp_jv: null pointer");
+  if (int rc = ctx_prepare_history(c)) return rc;
+  if (precision == PNP_F64) {
+    if (int rc = ctx_jv64(c, U, (const double*)V, (double*)JV)) return rc;
+  } else if (precision == PNP_F32) {
+    if (int rc = ctx_prepare_f32(c, U)) return rc;
+    if (int rc = ctx_jv32(c, (const float*)V, (float*)JV)) return rc;
+  } else {
+    PNP_FAIL(PNP_ERR_ARG, "pnp_jv: bad precision %d", precision);
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_block_diag(pnp_ctx* c, const double* U, double* D) {
+  CTX_GUARD(c);
+  if (!U || !D) PNP_FAIL(PNP_ERR_ARG, "pnp_block_diag: null pointer");
+  if (int rc = ctx_prepare_history(c)) return rc;
+  if (int rc = ctx_block_diag(c, U, D)) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int precision,
+              pnp_solve_stats* st) {
+  CTX_GUARD(c);
+  if (!U || !b || !x) PNP_FAIL(PNP_ERR_ARG, "pnp_gmres: null pointer");
+  if (precision != PNP_F64 && precision != PNP_F32) PNP_FAIL(PNP_ERR_ARG, "pnp_gmres: bad precision");
+  if (!(rtol > 0)) PNP_FAIL(PNP_ERR_ARG, "pnp_gmres: rtol must be > 0");
+  if (int rc = ctx_prepare_history(c)) return rc;
+  int its = 0;
+  double rel = 0;
+  c->jv_count = 0;
+  const int rc = ctx_gmres(c, U, b, x, rtol, precision, c->prm.gmres_max_it, &its, &rel, false);
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->status = rc;
+    st->krylov_its = its;
+    st->jv_evals = c->jv_count;
+    st->res_final = rel;
+  }
+  return rc;
+}
+
+int pnp_newton_solve(pnp_ctx* c, pnp_solve_stats* st) {
+  CTX_GUARD(c);
+  pnp_solve_stats local;
+  return ctx_newton(c, st ? st : &local);
+}
+
+int pnp_time_step(pnp_ctx* c, pnp_solve_stats* st) {
+  CTX_GUARD(c);
+  pnp_solve_stats local;
+  return ctx_time_step(c, st ? st : &local);
+}
+
+int pnp_step_count(const pnp_ctx* c, int64_t* k) {
+  if (!c || !k) PNP_FAIL(PNP_ERR_ARG, "pnp_step_count: null argument");
+  *k = c->step;
+  return PNP_OK;
+}
+
+static void resolve_events(pnp_ctx* c) {
+  for (auto& pe : c->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+      c->prof_ms[pe.first] += ms;
+      c->prof_cnt[pe.first] += 1;
+    }
+    c->ev_pool.push_back(pe.second.first);
+    c->ev_pool.push_back(pe.second.second);
+  }
+  c->ev_pending.clear();
+}
+
+int pnp_profile_enable(pnp_ctx* c, int on) {
+  CTX_GUARD(c);
+  CK(cudaStreamSynchronize(c->stream));
+  resolve_events(c);
+  if (on) {
+    for (int k = 0; k < PNP_PROF_KINDS; ++k) {
+      c->prof_ms[k] = 0;
+      c->prof_cnt[k] = 0;
+      c->prof_bytes[k] = 0;
+    }
+  }
+  c->prof_on = on != 0;
+  return PNP_OK;
+}
+
+int pnp_profile_read(pnp_ctx* c, int kind, double* total_ms, int64_t* count, double* alg_bytes) {
+  CTX_GUARD(c);
+  if (kind < 0 || kind >= PNP_PROF_KINDS) PNP_FAIL(PNP_ERR_ARG, "pnp_profile_read: bad kind %d", kind);
+  CK(cudaStreamSynchronize(c->stream));
+  resolve_events(c);
+  if (total_ms) *total_ms = c->prof_ms[kind];
+  if (count) *count = c->prof_cnt[kind];
+  if (alg_bytes) *alg_bytes = c->prof_bytes[kind];
+  return PNP_OK;
+}
+
+int pnp_reset_history(pnp_ctx* c) {
+  CTX_GUARD(c);
+  CK(cudaMemcpyAsync(c->Uk, c->U, sizeof(double) * c->n3(), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->Ukm1, c->U, sizeof(double) * c->n3(), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->step = 0;
+  return PNP_OK;
+}
+
+}  // extern "C"

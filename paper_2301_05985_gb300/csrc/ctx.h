@@ -1,0 +1,143 @@
+// ctx.h -- the context object behind the opaque pnp_ctx handle.
+#pragma once
+
+#include "kernels.h"
+
+struct pnp_ctx {
+  int dim = 0, L = 0;
+  int64_t n_elem = 0, n_nodes = 0, n_hanging = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  pnp_params prm{};
+  int bc_type[6][3] = {};
+  double bc_val[6][3] = {};
+  cudaError_t latched = cudaSuccess;
+  int64_t step = 0;
+
+  // mesh (device)
+  int32_t* d_conn = nullptr;
+  uint8_t* d_level = nullptr;
+  uint8_t* d_faces = nullptr;  // boundary-face bits, bit 7 = hanging
+  int32_t* d_hnode = nullptr;
+  int32_t* d_hpar = nullptr;
+  uint8_t* d_hnp = nullptr;
+
+  // fields, FP64, [N][3]
+  double *U = nullptr, *Uk = nullptr, *Ukm1 = nullptr;
+  double *adv = nullptr, *vel = nullptr, *vel_prev = nullptr;
+  double* hs = nullptr;  // [N][2]
+
+  // FP32 mirrors for the mixed-precision Jv
+  float *U32 = nullptr, *adv32 = nullptr, *hs32 = nullptr, *V32 = nullptr, *JV32 = nullptr;
+
+  // Newton / Krylov scratch
+  double *F = nullptr, *dU = nullptr, *Ut = nullptr, *Ft = nullptr, *rhs = nullptr;
+  double* Dinv = nullptr;  // [N][9]
+  double* basis = nullptr; // [(m+1)][3N]
+  double *w = nullptr, *z = nullptr, *r = nullptr;
+  double* part = nullptr;  // reduction partials [kRedBlocks][m+2]
+  double* dsc = nullptr;   // small device scalars [2*(m+2) + 8]
+  double* hpin = nullptr;  // pinned host mirror of dsc
+  int* dflag = nullptr;
+  int m_alloc = 0;
+  int64_t basis_bytes = 0;
+
+  // statistics of the last solve (for the time stepper)
+  int jv_count = 0, res_count = 0;
+
+  // learned start (optional)
+  struct Mlp* mlp = nullptr;
+
+  // profiling: event pairs per kernel class, resolved on read
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double prof_ms[PNP_PROF_KINDS] = {};
+  int64_t prof_cnt[PNP_PROF_KINDS] = {};
+  double prof_bytes[PNP_PROF_KINDS] = {};
+  // algorithmic bytes of one element-kernel launch: connectivity + level (+ hanging tables)
+  double conn_bytes() const {
+    return (double)n_elem * (4.0 * (1 << dim) + 1.0) + (double)n_hanging * 17.0;
+  }
+  cudaEvent_t take_event() {
+    cudaEvent_t e = nullptr;
+    if (!ev_pool.empty()) {
+      e = ev_pool.back();
+      ev_pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+
+  int64_t n3() const { return 3 * n_nodes; }
+  RowArgs rows() const {
+    RowArgs R;
+    R.n_nodes = n_nodes;
+    R.n_hanging = n_hanging;
+    R.faces = d_faces;
+    R.hnode = d_hnode;
+    R.hpar = d_hpar;
+    R.hnp = d_hnp;
+    R.bc = bc_table();
+    return R;
+  }
+  BcTable bc_table() const {
+    BcTable t{};
+    for (int f = 0; f < 3; ++f) {
+      uint8_t m = 0;
+      for (int face = 0; face < 2 * dim; ++face)
+        if (bc_type[face][f] == PNP_DIRICHLET) m |= (uint8_t)(1u << face);
+      t.dir_faces[f] = m;
+    }
+    for (int face = 0; face < 6; ++face)
+      for (int f = 0; f < 3; ++f) t.val[face][f] = bc_val[face][f];
+    return t;
+  }
+  PhysParams phys() const {
+    PhysParams P;
+    P.eps2x2 = 2.0 * prm.eps * prm.eps;
+    P.kappa = prm.steady ? 0.0 : prm.beta0 / prm.dt;
+    P.tau_t = prm.steady ? 0.0 : 4.0 / (prm.dt * prm.dt);
+    P.C_I = prm.C_I;
+    P.steady = prm.steady;
+    return P;
+  }
+};
+
+// Records a CUDA event pair around the enclosed launches when profiling is on.
+struct ProfScope {
+  pnp_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr;
+  ProfScope(pnp_ctx* c_, int k, double bytes) : c(c_), kind(k) {
+    if (c->prof_on) {
+      c->prof_bytes[kind] += bytes;
+      a = c->take_event();
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = c->take_event();
+      cudaEventRecord(b, c->stream);
+      c->ev_pending.push_back({kind, {a, b}});
+    }
+  }
+};
+
+// Internal operations (return pnp_status).
+int ctx_check(pnp_ctx* c, cudaError_t e, const char* what);
+int ctx_prepare_history(pnp_ctx* c);
+int ctx_residual(pnp_ctx* c, const double* U, double* F);
+int ctx_jv64(pnp_ctx* c, const double* U, const double* V, double* JV);
+int ctx_prepare_f32(pnp_ctx* c, const double* U);
+int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32);
+int ctx_block_diag(pnp_ctx* c, const double* U, double* D);
+int ctx_norm(pnp_ctx* c, const double* x, double* out);
+int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int precision, int max_it,
+              int* its, double* relres, bool have_precond);
+int ctx_newton(pnp_ctx* c, pnp_solve_stats* st);
+int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st);
+int ctx_alloc_krylov(pnp_ctx* c, int m);
+void pnp_mlp_release(pnp_ctx* c);

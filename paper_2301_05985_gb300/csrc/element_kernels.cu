@@ -1,0 +1,461 @@
+// element_kernels.cu -- fused gather / Gauss-point physics / test contraction / scatter
+// for the VMS PNP residual and its Jacobian action, plus the exact 3x3 block diagonal.
+//
+// Physics per Gauss point (Def. 3 of arXiv 2301.05985 with c^f = -tau_c R_c, Sec. 3.1):
+//   P_s  = v - z_s grad(phi)
+//   R_s  = kappa c_s + h_s + P_s . grad c_s          (lap of a Q1 field on a cube is 0)
+//   Nernst-Planck row:  q [kappa c_s + h_s + v.grad c_s] + grad q . [grad c_s + z_s c_s grad phi + tau R_s P_s]
+//   Poisson row:        2 eps^2 grad q . grad phi - q sum_s z_s c_s + q sum_s z_s tau R_s
+// with kappa = beta0/dt, h_s = (beta1 c_s^k + beta2 c_s^{k-1})/dt (both 0 when steady) and
+// tau = (4/dt^2 + (2/h)^2 |v|^2 + C_I d (2/h)^4)^(-1/2).  J V is the exact directional
+// derivative (the residual is cubic in U; tau does not depend on U).
+#include <cstdio>
+
+#include "element_kernels.cuh"
+#include "kernels.h"
+
+using namespace pnpk;
+
+namespace {
+
+template <int Q, int NQ, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (Q < NQ) {
+    f(std::integral_constant<int, Q>{});
+    static_for<Q + 1, NQ>(f);
+  }
+}
+
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+
+template <typename T, int NF, int NC>
+__device__ __forceinline__ void gather(const ElemArgs<T>& A, const int32_t (&conn)[NC], const T* __restrict__ src,
+                                       int stride, T (&dst)[NF][NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int32_t id = conn[c];
+    if (id >= 0) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) dst[f][c] = __ldg(src + (int64_t)stride * id + f);
+    } else {
+      const int32_t hidx = -id - 1;
+      const int np = A.hang_np[hidx];
+      const T wgt = np == 2 ? T(0.5) : T(0.25);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) dst[f][c] = T(0);
+      for (int p = 0; p < np; ++p) {
+        const int32_t pid = A.hang_par[4 * hidx + p];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) dst[f][c] += wgt * __ldg(src + (int64_t)stride * pid + f);
+      }
+    }
+  }
+}
+
+template <typename T, int NC>
+__device__ __forceinline__ void scatter(const ElemArgs<T>& A, const int32_t (&conn)[NC], T (&r)[3][NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int32_t id = conn[c];
+    if (id >= 0) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)id + f, r[f][c]);
+    } else {
+      const int32_t hidx = -id - 1;
+      const int np = A.hang_np[hidx];
+      const T wgt = np == 2 ? T(0.5) : T(0.25);
+      for (int p = 0; p < np; ++p) {
+        const int32_t pid = A.hang_par[4 * hidx + p];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)pid + f, wgt * r[f][c]);
+      }
+    }
+  }
+}
+
+template <typename T, int D, bool JV>
+__global__ void __launch_bounds__(128) k_element(ElemArgs<T> A) {
+  constexpr int NC = 1 << D;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= A.n_elem) return;
+  int32_t conn[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) conn[c] = __ldg(A.conn + e * NC + c);
+  const int lev = A.level[e];
+  const T h = T(ldexp(1.0, -lev));
+  const T inv_h = T(ldexp(1.0, lev));
+  const T Gs = T(2.0 / kGauss) * inv_h;     // 2 / (h g)
+  const T G2 = T(4.0) * inv_h * inv_h;      // (2/h)^2
+  T w = T(1);
+#pragma unroll
+  for (int k = 0; k < D; ++k) w *= T(0.5) * h;
+  const T kappa = T(A.P.kappa);
+  const T tau0 = T(A.P.tau_t) + T(A.P.C_I * D) * G2 * G2;
+  const T e2 = T(A.P.eps2x2);
+
+  T u[3][NC], va[3][NC], hs[2][NC];
+  gather<T, 3, NC>(A, conn, A.U, 3, u);
+  gather<T, 3, NC>(A, conn, A.adv, 3, va);
+  gather<T, 2, NC>(A, conn, A.hs, 2, hs);
+#pragma unroll
+  for (int f = 0; f < 3; ++f) to_modal<T, D>(u[f]);
+#pragma unroll
+  for (int f = 0; f < D; ++f) to_modal<T, D>(va[f]);
+#pragma unroll
+  for (int f = 0; f < 2; ++f) to_modal<T, D>(hs[f]);
+  T du[3][NC];
+  if constexpr (JV) {
+    gather<T, 3, NC>(A, conn, A.V, 3, du);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) to_modal<T, D>(du[f]);
+  }
+  T acc[3][NC];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int m = 0; m < NC; ++m) acc[f][m] = T(0);
+
+  static_for<0, NC>([&](auto qc) {
+    constexpr int Q = decltype(qc)::value;
+    T cv[2], gc[2][3], gp[3], v[3] = {T(0), T(0), T(0)}, hq[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      qp_value_grad<T, D, Q>(u[s], Gs, cv[s], gc[s]);
+      hq[s] = qp_value<T, D, Q>(hs[s]);
+    }
+    qp_grad<T, D, Q>(u[2], Gs, gp);
+    T vv = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[k] = qp_value<T, D, Q>(va[k]);
+      vv += v[k] * v[k];
+    }
+    const T tau = rsq(tau0 + G2 * vv);
+    T R[2], P[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const T z = s == 0 ? T(1) : T(-1);
+      T pg = T(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        P[s][k] = v[k] - z * gp[k];
+        pg += P[s][k] * gc[s][k];
+      }
+      R[s] = kappa * cv[s] + hq[s] + pg;
+    }
+    if constexpr (!JV) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const T z = s == 0 ? T(1) : T(-1);
+        T vg = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) vg += v[k] * gc[s][k];
+        const T S = kappa * cv[s] + hq[s] + vg;
+        const T tR = tau * R[s];
+        const T zc = z * cv[s];
+        T Phi[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Phi[k] = gc[s][k] + zc * gp[k] + tR * P[s][k];
+        qp_test_acc<T, D, Q>(acc[s], S, Phi, Gs);
+      }
+      const T S = -(cv[0] - cv[1]) + tau * (R[0] - R[1]);
+      T Phi[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Phi[k] = e2 * gp[k];
+      qp_test_acc<T, D, Q>(acc[2], S, Phi, Gs);
+    } else {
+      T dcv[2], dgc[2][3], dgp[3];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) qp_value_grad<T, D, Q>(du[s], Gs, dcv[s], dgc[s]);
+      qp_grad<T, D, Q>(du[2], Gs, dgp);
+      T dR[2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const T z = s == 0 ? T(1) : T(-1);
+        T vg = T(0), pg = T(0), gcd = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          vg += v[k] * dgc[s][k];
+          pg += P[s][k] * dgc[s][k];
+          gcd += gc[s][k] * dgp[k];
+        }
+        dR[s] = kappa * dcv[s] + pg - z * gcd;
+        const T S = kappa * dcv[s] + vg;
+        const T tdR = tau * dR[s];
+        const T zdc = z * dcv[s];
+        const T zc_tR = z * (cv[s] - tau * R[s]);
+        T Phi[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Phi[k] = dgc[s][k] + zdc * gp[k] + zc_tR * dgp[k] + tdR * P[s][k];
+        qp_test_acc<T, D, Q>(acc[s], S, Phi, Gs);
+      }
+      const T S = -(dcv[0] - dcv[1]) + tau * (dR[0] - dR[1]);
+      T Phi[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Phi[k] = e2 * dgp[k];
+      qp_test_acc<T, D, Q>(acc[2], S, Phi, Gs);
+    }
+  });
+#pragma unroll
+  for (int f = 0; f < 3; ++f) from_modal<T, D>(acc[f], w);
+  scatter<T, NC>(A, conn, acc);
+}
+
+// ------------------------------------------------------------------ block diagonal
+// 3x3 block (test corner I, trial corner J) of the element Jacobian at Gauss point Q.
+template <int D, int Q>
+__device__ __forceinline__ void jac_block(int I, int J, double h, double kappa, double e2, double tau,
+                                          const double (&cv)[2], const double (&gc)[2][3], const double (&gp)[3],
+                                          const double (&v)[3], const double (&R)[2], const double (&P)[2][3],
+                                          double w, double (&B)[9]) {
+  double Ni = 1, Nj = 1, dNi[3] = {0, 0, 0}, dNj[3] = {0, 0, 0};
+  double fi[3], fj[3];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double sg = ((Q >> k) & 1) ? kGauss : -kGauss;
+    const double si = ((I >> k) & 1) ? 1.0 : -1.0, sj = ((J >> k) & 1) ? 1.0 : -1.0;
+    fi[k] = 0.5 * (1.0 + si * sg);
+    fj[k] = 0.5 * (1.0 + sj * sg);
+    Ni *= fi[k];
+    Nj *= fj[k];
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double si = ((I >> k) & 1) ? 1.0 : -1.0, sj = ((J >> k) & 1) ? 1.0 : -1.0;
+    double a = si / h, b = sj / h;  // (2/h)(s/2)
+#pragma unroll
+    for (int l = 0; l < D; ++l)
+      if (l != k) {
+        a *= fi[l];
+        b *= fj[l];
+      }
+    dNi[k] = a;
+    dNj[k] = b;
+  }
+  double gij = 0, gip = 0, vgj = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gij += dNi[k] * dNj[k];
+    gip += dNi[k] * gp[k];
+    vgj += v[k] * dNj[k];
+  }
+  double pp_sum = 0;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const double z = s == 0 ? 1.0 : -1.0;
+    double pgj = 0, giP = 0, gcj = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      pgj += P[s][k] * dNj[k];
+      giP += dNi[k] * P[s][k];
+      gcj += gc[s][k] * dNj[k];
+    }
+    const double dRdc = kappa * Nj + pgj;
+    const double dRdp = -z * gcj;
+    B[3 * s + s] += w * (Ni * (kappa * Nj + vgj) + gij + z * Nj * gip + tau * dRdc * giP);
+    B[3 * s + 2] += w * (z * cv[s] * gij + tau * dRdp * giP - tau * R[s] * z * gij);
+    B[6 + s] += w * (-Ni * z * Nj + Ni * z * tau * dRdc);
+    pp_sum += z * tau * dRdp;
+  }
+  B[8] += w * (e2 * gij + Ni * pp_sum);
+}
+
+template <int D>
+__global__ void __launch_bounds__(64) k_block_diag(ElemArgs<double> A, double* __restrict__ Dout) {
+  constexpr int NC = 1 << D;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= A.n_elem) return;
+  int32_t conn[NC];
+  bool any_h = false;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    conn[c] = A.conn[e * NC + c];
+    any_h |= conn[c] < 0;
+  }
+  const int lev = A.level[e];
+  const double h = ldexp(1.0, -lev), inv_h = ldexp(1.0, lev);
+  const double Gs = (2.0 / kGauss) * inv_h, G2 = 4.0 * inv_h * inv_h;
+  double w = 1;
+  for (int k = 0; k < D; ++k) w *= 0.5 * h;
+  const double kappa = A.P.kappa, tau0 = A.P.tau_t + A.P.C_I * D * G2 * G2, e2 = A.P.eps2x2;
+  double u[3][NC], va[3][NC], hs[2][NC];
+  gather<double, 3, NC>(A, conn, A.U, 3, u);
+  gather<double, 3, NC>(A, conn, A.adv, 3, va);
+  gather<double, 2, NC>(A, conn, A.hs, 2, hs);
+  for (int f = 0; f < 3; ++f) to_modal<double, D>(u[f]);
+  for (int f = 0; f < D; ++f) to_modal<double, D>(va[f]);
+  for (int f = 0; f < 2; ++f) to_modal<double, D>(hs[f]);
+
+  // targets of each corner: (node, weight)
+  int32_t tgt[NC][4];
+  double tw[NC][4];
+  int nt[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (conn[c] >= 0) {
+      tgt[c][0] = conn[c];
+      tw[c][0] = 1.0;
+      nt[c] = 1;
+    } else {
+      const int32_t hidx = -conn[c] - 1;
+      nt[c] = A.hang_np[hidx];
+      for (int p = 0; p < nt[c]; ++p) {
+        tgt[c][p] = A.hang_par[4 * hidx + p];
+        tw[c][p] = nt[c] == 2 ? 0.5 : 0.25;
+      }
+    }
+  }
+
+  double Dacc[NC][9];
+  for (int c = 0; c < NC; ++c)
+    for (int k = 0; k < 9; ++k) Dacc[c][k] = 0;
+
+  static_for<0, NC>([&](auto qc) {
+    constexpr int Q = decltype(qc)::value;
+    double cv[2], gc[2][3], gp[3], v[3] = {0, 0, 0}, hq[2];
+    for (int s = 0; s < 2; ++s) {
+      qp_value_grad<double, D, Q>(u[s], Gs, cv[s], gc[s]);
+      hq[s] = qp_value<double, D, Q>(hs[s]);
+    }
+    qp_grad<double, D, Q>(u[2], Gs, gp);
+    double vv = 0;
+    for (int k = 0; k < D; ++k) {
+      v[k] = qp_value<double, D, Q>(va[k]);
+      vv += v[k] * v[k];
+    }
+    const double tau = 1.0 / sqrt(tau0 + G2 * vv);
+    double R[2], P[2][3];
+    for (int s = 0; s < 2; ++s) {
+      const double z = s == 0 ? 1.0 : -1.0;
+      double pg = 0;
+      for (int k = 0; k < 3; ++k) {
+        P[s][k] = v[k] - z * gp[k];
+        pg += P[s][k] * gc[s][k];
+      }
+      R[s] = kappa * cv[s] + hq[s] + pg;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) jac_block<D, Q>(c, c, h, kappa, e2, tau, cv, gc, gp, v, R, P, w, Dacc[c]);
+    if (any_h) {
+      // cross pairs that share a target node through the constraints
+      for (int i = 0; i < NC; ++i)
+        for (int j = 0; j < NC; ++j) {
+          if (i == j) continue;
+          double B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+          bool computed = false;
+          for (int a = 0; a < nt[i]; ++a)
+            for (int b = 0; b < nt[j]; ++b)
+              if (tgt[i][a] == tgt[j][b]) {
+                if (!computed) {
+                  jac_block<D, Q>(i, j, h, kappa, e2, tau, cv, gc, gp, v, R, P, w, B);
+                  computed = true;
+                }
+                const double ww = tw[i][a] * tw[j][b];
+                for (int k = 0; k < 9; ++k) atomicAdd(Dout + 9 * (int64_t)tgt[i][a] + k, ww * B[k]);
+              }
+        }
+    }
+  });
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    for (int a = 0; a < nt[c]; ++a) {
+      const double ww = tw[c][a] * tw[c][a];
+      for (int k = 0; k < 9; ++k) atomicAdd(Dout + 9 * (int64_t)tgt[c][a] + k, ww * Dacc[c][k]);
+    }
+}
+
+// ------------------------------------------------------------------ row fix-ups
+// mode 0: F = U - g on Dirichlet rows;  mode 1: out = V on Dirichlet rows.
+template <typename T>
+__global__ void k_dirichlet_rows(int64_t N, const uint8_t* __restrict__ faces, BcTable bc, const T* __restrict__ in,
+                                 T* __restrict__ out, int mode) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint8_t fm = faces[i];
+  if (fm & 0x80) return;  // hanging: constraint row written separately
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const unsigned msk = fm & bc.dir_faces[f] & 0x3F;
+    if (msk) {
+      const int face = 31 - __clz(msk);
+      out[3 * i + f] = mode == 0 ? T(double(in[3 * i + f]) - bc.val[face][f]) : in[3 * i + f];
+    }
+  }
+}
+
+// out_h = in_h - sum_p w_p in_p  (constraint rows of hanging nodes)
+template <typename T>
+__global__ void k_hanging_rows(int64_t H, const int32_t* __restrict__ hnode, const int32_t* __restrict__ hpar,
+                               const uint8_t* __restrict__ hnp, const T* __restrict__ in, T* __restrict__ out) {
+  const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  const int np = hnp[h];
+  const T wgt = np == 2 ? T(0.5) : T(0.25);
+  const int64_t id = hnode[h];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    T s = in[3 * id + f];
+    for (int p = 0; p < np; ++p) s -= wgt * in[3 * (int64_t)hpar[4 * h + p] + f];
+    out[3 * id + f] = s;
+  }
+}
+
+// Dirichlet / hanging rows of the block diagonal.
+__global__ void k_diag_rows(int64_t N, const uint8_t* __restrict__ faces, BcTable bc, double* __restrict__ Dg) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint8_t fm = faces[i];
+  double* B = Dg + 9 * i;
+  if (fm & 0x80) {
+    for (int k = 0; k < 9; ++k) B[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    return;
+  }
+  for (int f = 0; f < 3; ++f)
+    if (fm & bc.dir_faces[f] & 0x3F)
+      for (int g = 0; g < 3; ++g) B[3 * f + g] = (f == g) ? 1.0 : 0.0;
+}
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+cudaError_t launch_element(int dim, bool jv, const ElemArgs<T>& A, cudaStream_t s) {
+  if (A.n_elem == 0) return cudaSuccess;
+  const int t = 128;
+  if (dim == 2) {
+    if (jv) { k_element<T, 2, true><<<nblk(A.n_elem, t), t, 0, s>>>(A); note_launch(); }
+    else { k_element<T, 2, false><<<nblk(A.n_elem, t), t, 0, s>>>(A); note_launch(); }
+  } else {
+    if (jv) { k_element<T, 3, true><<<nblk(A.n_elem, t), t, 0, s>>>(A); note_launch(); }
+    else { k_element<T, 3, false><<<nblk(A.n_elem, t), t, 0, s>>>(A); note_launch(); }
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_element<double>(int, bool, const ElemArgs<double>&, cudaStream_t);
+template cudaError_t launch_element<float>(int, bool, const ElemArgs<float>&, cudaStream_t);
+
+cudaError_t launch_block_diag(int dim, const ElemArgs<double>& A, double* Dout, cudaStream_t s) {
+  if (A.n_elem == 0) return cudaSuccess;
+  const int t = 64;
+  if (dim == 2) { k_block_diag<2><<<nblk(A.n_elem, t), t, 0, s>>>(A, Dout); note_launch(); }
+  else { k_block_diag<3><<<nblk(A.n_elem, t), t, 0, s>>>(A, Dout); note_launch(); }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_row_fixups(const RowArgs& R, const T* in, T* out, int mode, cudaStream_t s) {
+  const int t = 256;
+  if (R.n_nodes) { k_dirichlet_rows<T><<<nblk(R.n_nodes, t), t, 0, s>>>(R.n_nodes, R.faces, R.bc, in, out, mode); note_launch(); }
+  if (R.n_hanging) { k_hanging_rows<T><<<nblk(R.n_hanging, t), t, 0, s>>>(R.n_hanging, R.hnode, R.hpar, R.hnp, in, out); note_launch(); }
+  return cudaGetLastError();
+}
+template cudaError_t launch_row_fixups<double>(const RowArgs&, const double*, double*, int, cudaStream_t);
+template cudaError_t launch_row_fixups<float>(const RowArgs&, const float*, float*, int, cudaStream_t);
+
+cudaError_t launch_diag_rows(const RowArgs& R, double* Dg, cudaStream_t s) {
+  if (R.n_nodes) { k_diag_rows<<<nblk(R.n_nodes, 256), 256, 0, s>>>(R.n_nodes, R.faces, R.bc, Dg); note_launch(); }
+  return cudaGetLastError();
+}

@@ -1,0 +1,76 @@
+// kernels.h -- launch interfaces of the library's CUDA kernels.
+#pragma once
+
+#include "pnp_internal.h"
+
+// Arguments of the fused element kernels (residual / Jv / block diagonal).
+template <typename T>
+struct ElemArgs {
+  int64_t n_elem;
+  const int32_t* conn;     // [E][2^dim]
+  const uint8_t* level;    // [E]
+  const int32_t* hang_par; // [H][4]
+  const uint8_t* hang_np;  // [H]
+  const T* U;              // [N][3]
+  const T* V;              // [N][3] direction (Jv only)
+  const T* hs;             // [N][2] (beta1 c^k + beta2 c^{k-1}) / dt
+  const T* adv;            // [N][3] advection velocity
+  T* out;                  // [N][3] accumulated (must be zeroed first)
+  PhysParams P;
+};
+
+// Arguments of the Dirichlet / hanging row kernels.
+struct RowArgs {
+  int64_t n_nodes, n_hanging;
+  const uint8_t* faces;    // [N] boundary-face bits; bit 7 = hanging
+  const int32_t* hnode;
+  const int32_t* hpar;
+  const uint8_t* hnp;
+  BcTable bc;
+};
+
+// Counts every kernel the library launches (read by pnp_kernel_launches).
+void note_launch();
+
+template <typename T>
+cudaError_t launch_element(int dim, bool jv, const ElemArgs<T>& A, cudaStream_t s);
+cudaError_t launch_block_diag(int dim, const ElemArgs<double>& A, double* Dout, cudaStream_t s);
+template <typename T>
+cudaError_t launch_row_fixups(const RowArgs& R, const T* in, T* out, int mode, cudaStream_t s);
+cudaError_t launch_diag_rows(const RowArgs& R, double* Dg, cudaStream_t s);
+
+// ------------------------------------------------------------------ vector kernels
+// All reductions are deterministic: fixed grid, per-block partials, one final block.
+constexpr int kRedBlocks = 608;  // 4 x 152 SMs
+constexpr int kRedThreads = 256;
+
+// history h_s = (b1 c^k + b2 c^{k-1}) / dt, [N][2]
+cudaError_t launch_history(int64_t N, const double* Uk, const double* Ukm1, double b1, double b2, double dt,
+                           double* hs, cudaStream_t s);
+// y[i] = (float) x[i]
+cudaError_t launch_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);
+cudaError_t launch_to_f64(int64_t n, const float* x, double* y, cudaStream_t s);
+// y = a x + b y
+cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t s);
+// z = a x + b y
+cudaError_t launch_axpbyz(int64_t n, double a, const double* x, double b, const double* y, double* z, cudaStream_t s);
+// partial sums of x.y into part[kRedBlocks], then result[0] = sum (device)
+cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* part, double* result, cudaStream_t s);
+cudaError_t launch_norm2(int64_t n, const double* x, double* part, double* result, cudaStream_t s);
+// h[i] = sum_n Vb[i*ld + n] w[n], i < k  (part: [kRedBlocks][k] scratch)
+cudaError_t launch_multi_dot(int64_t n, int k, const double* Vb, int64_t ld, const double* w, double* part, double* h,
+                             cudaStream_t s);
+// w -= sum_i h[i] Vb[i*ld + .], i < k ; optionally hacc[i] += h[i]
+cudaError_t launch_multi_axpy(int64_t n, int k, const double* Vb, int64_t ld, const double* h, double* w,
+                              double* hacc, cudaStream_t s);
+// v = w / nrm[0]
+cudaError_t launch_scale_by_inv(int64_t n, const double* w, const double* nrm, double* v, cudaStream_t s);
+// z_i = Dinv_i v_i per node (3x3 blocks); optionally also a float copy z32 (may be null)
+cudaError_t launch_block_apply(int64_t N, const double* Dinv, const double* v, double* z, float* z32, cudaStream_t s);
+// invert 3x3 blocks in place (Gauss-Jordan with partial pivoting); flag[0] |= 1 on a singular block
+cudaError_t launch_block_invert(int64_t N, double* D, int* flag, cudaStream_t s);
+// hanging interpolation + Dirichlet values on U
+cudaError_t launch_make_consistent(const RowArgs& R, double* U, cudaStream_t s);
+// copy with layout change: [N][dim] <-> [N][3]
+cudaError_t launch_vel_pack(int64_t N, int dim, const double* src, double* dst3, cudaStream_t s);
+cudaError_t launch_vel_unpack(int64_t N, int dim, const double* src3, double* dst, cudaStream_t s);

@@ -1,0 +1,66 @@
+// pnp_internal.h -- internal data structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pnp.h"
+
+// ------------------------------------------------------------------ errors
+void pnp_set_error(const char* fmt, ...);
+#define PNP_FAIL(code, ...)       \
+  do {                            \
+    pnp_set_error(__VA_ARGS__);   \
+    return (code);                \
+  } while (0)
+
+// ------------------------------------------------------------------ host mesh
+// Elements are Morton-ordered octree leaves; nodes are their unique corners in Morton
+// order of the (integer) coordinates.  Corner c of an element sits at anchor + h * bits(c)
+// (bit k of c = +1 along axis k).
+struct pnp_mesh {
+  int dim = 0;
+  int L = 0;
+  int64_t n_elem = 0, n_nodes = 0, n_hanging = 0;
+  std::vector<int32_t> el_anchor;   // [E][dim]
+  std::vector<uint8_t> el_level;    // [E]
+  std::vector<int32_t> el_conn;     // [E][2^dim]: node id, or -(h+1) for hanging node h
+  std::vector<int32_t> node_ijk;    // [N][dim]
+  std::vector<uint8_t> node_faces;  // [N] bit f set: node lies on boundary face f
+  std::vector<int32_t> node_hang;   // [N] hanging index or -1
+  std::vector<int32_t> hang_node;   // [H] node id of each hanging node
+  std::vector<int32_t> hang_par;    // [H][4] parent node ids (-1 padded)
+  std::vector<uint8_t> hang_np;     // [H] number of parents (2 or 4)
+};
+
+int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels);
+
+// ------------------------------------------------------------------ device views
+struct DevMesh {
+  int dim;
+  int64_t n_elem, n_nodes, n_hanging;
+  const int32_t* conn;       // [E][2^dim]
+  const uint8_t* level;      // [E]
+  const uint8_t* node_faces; // [N]
+  const int32_t* hang_node;  // [H]
+  const int32_t* hang_par;   // [H][4]
+  const uint8_t* hang_np;    // [H]
+};
+
+// Physics constants of one residual / Jv evaluation (passed by value to kernels).
+struct PhysParams {
+  double eps2x2;   // 2 Lambda^2
+  double kappa;    // beta0 / dt (0 when steady)
+  double tau_t;    // 4 / dt^2 (0 when steady)
+  double C_I;
+  int steady;
+};
+
+// Boundary-condition description for the row fix-up kernels.
+struct BcTable {
+  uint8_t dir_faces[3];  // per field: bit f set = Dirichlet on face f
+  double val[6][3];      // Dirichlet values
+};

@@ -1,0 +1,419 @@
+// solver.cu -- residual / Jv drivers, GMRES(m) with classical Gram-Schmidt and
+// reorthogonalisation, Newton's method (Sec. 4.1 of arXiv 2301.05985) with optional
+// Eisenstat-Walker forcing for the FP32-Jv inexact mode, and the BDF time step (Def. 1).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+#include "ctx.h"
+
+#define CK(call)                                 \
+  do {                                           \
+    int _rc = ctx_check(c, (call), #call);       \
+    if (_rc) return _rc;                         \
+  } while (0)
+#define RC(call)              \
+  do {                        \
+    int _rc = (call);         \
+    if (_rc) return _rc;      \
+  } while (0)
+
+namespace {
+
+template <typename T>
+ElemArgs<T> elem_args(const pnp_ctx* c, const T* U, const T* V, const T* hs, const T* adv, T* out) {
+  ElemArgs<T> A;
+  A.n_elem = c->n_elem;
+  A.conn = c->d_conn;
+  A.level = c->d_level;
+  A.hang_par = c->d_hpar;
+  A.hang_np = c->d_hnp;
+  A.U = U;
+  A.V = V;
+  A.hs = hs;
+  A.adv = adv;
+  A.out = out;
+  A.P = c->phys();
+  return A;
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+int ctx_prepare_history(pnp_ctx* c) {
+  if (c->prm.steady) {
+    CK(cudaMemsetAsync(c->hs, 0, sizeof(double) * 2 * c->n_nodes, c->stream));
+  } else {
+    CK(launch_history(c->n_nodes, c->Uk, c->Ukm1, c->prm.beta1, c->prm.beta2, c->prm.dt, c->hs, c->stream));
+  }
+  return PNP_OK;
+}
+
+int ctx_residual(pnp_ctx* c, const double* U, double* F) {
+  CK(cudaMemsetAsync(F, 0, sizeof(double) * c->n3(), c->stream));
+  {
+    ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes());
+    CK(launch_element<double>(c->dim, false, elem_args<double>(c, U, nullptr, c->hs, c->adv, F), c->stream));
+  }
+  CK(launch_row_fixups<double>(c->rows(), U, F, 0, c->stream));
+  c->res_count++;
+  return PNP_OK;
+}
+
+int ctx_jv64(pnp_ctx* c, const double* U, const double* V, double* JV) {
+  CK(cudaMemsetAsync(JV, 0, sizeof(double) * c->n3(), c->stream));
+  {
+    ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes());
+    CK(launch_element<double>(c->dim, true, elem_args<double>(c, U, V, c->hs, c->adv, JV), c->stream));
+  }
+  CK(launch_row_fixups<double>(c->rows(), V, JV, 1, c->stream));
+  c->jv_count++;
+  return PNP_OK;
+}
+
+int ctx_prepare_f32(pnp_ctx* c, const double* U) {
+  CK(launch_to_f32(c->n3(), U, c->U32, c->stream));
+  CK(launch_to_f32(2 * c->n_nodes, c->hs, c->hs32, c->stream));
+  CK(launch_to_f32(c->n3(), c->adv, c->adv32, c->stream));
+  return PNP_OK;
+}
+
+int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32) {
+  CK(cudaMemsetAsync(JV32, 0, sizeof(float) * c->n3(), c->stream));
+  {
+    ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes());
+    CK(launch_element<float>(c->dim, true, elem_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32), c->stream));
+  }
+  CK(launch_row_fixups<float>(c->rows(), V32, JV32, 1, c->stream));
+  c->jv_count++;
+  return PNP_OK;
+}
+
+int ctx_block_diag(pnp_ctx* c, const double* U, double* D) {
+  CK(cudaMemsetAsync(D, 0, sizeof(double) * 9 * c->n_nodes, c->stream));
+  {
+    ProfScope ps(c, PNP_PROF_BLOCKDIAG, 136.0 * c->n_nodes + c->conn_bytes());
+    CK(launch_block_diag(c->dim, elem_args<double>(c, U, nullptr, c->hs, c->adv, nullptr), D, c->stream));
+  }
+  CK(launch_diag_rows(c->rows(), D, c->stream));
+  return PNP_OK;
+}
+
+int ctx_norm(pnp_ctx* c, const double* x, double* out) {
+  double* slot = c->dsc + 2 * (c->m_alloc + 2) + 8;
+  CK(launch_norm2(c->n3(), x, c->part, slot, c->stream));
+  CK(cudaMemcpyAsync(c->hpin, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = c->hpin[0];
+  return PNP_OK;
+}
+
+static int build_preconditioner(pnp_ctx* c, const double* U) {
+  RC(ctx_block_diag(c, U, c->Dinv));
+  CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream));
+  CK(launch_block_invert(c->n_nodes, c->Dinv, c->dflag, c->stream));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (flag) PNP_FAIL(PNP_ERR_NAN, "block-Jacobi preconditioner: singular or non-finite 3x3 block");
+  return PNP_OK;
+}
+
+// w = J x  in the requested precision (FP32 path: U32/hs32/adv32 must be prepared)
+static int apply_op(pnp_ctx* c, const double* U, const double* x, double* w, int prec) {
+  if (prec == PNP_F64) return ctx_jv64(c, U, x, w);
+  CK(launch_to_f32(c->n3(), x, c->V32, c->stream));
+  RC(ctx_jv32(c, c->V32, c->JV32));
+  CK(launch_to_f64(c->n3(), c->JV32, w, c->stream));
+  return PNP_OK;
+}
+
+int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int prec, int max_it, int* its_out,
+              double* rel_out, bool have_precond) {
+  const int m = c->prm.gmres_restart;
+  RC(ctx_alloc_krylov(c, m));
+  const int64_t n = c->n3();
+  cudaStream_t s = c->stream;
+  if (!have_precond) RC(build_preconditioner(c, U));
+  if (prec == PNP_F32) RC(ctx_prepare_f32(c, U));
+  double* V = c->basis;
+  double* dh = c->dsc;                  // [m+2] projections of one pass
+  double* dacc = c->dsc + (m + 2);      // [m+2] accumulated column, then the norm
+  double* dnrm = c->dsc + 2 * (m + 2);  // [1]
+  double* hp = c->hpin;
+  *its_out = 0;
+  double bn;
+  RC(ctx_norm(c, b, &bn));
+  if (!std::isfinite(bn)) PNP_FAIL(PNP_ERR_NAN, "gmres: right-hand side is not finite");
+  if (bn == 0.0) {
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    *rel_out = 0;
+    return PNP_OK;
+  }
+  const double tol = rtol * bn;
+  // r = b - J x
+  RC(apply_op(c, U, x, c->w, prec));
+  CK(launch_axpbyz(n, 1.0, b, -1.0, c->w, c->r, s));
+  double beta;
+  RC(ctx_norm(c, c->r, &beta));
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  int total = 0;
+  while (true) {
+    if (!std::isfinite(beta)) PNP_FAIL(PNP_ERR_NAN, "gmres: residual norm is not finite");
+    if (beta <= tol) break;
+    if (total >= max_it) {
+      *its_out = total;
+      *rel_out = beta / bn;
+      PNP_FAIL(PNP_ERR_KRYLOV_MAXIT, "gmres: %d iterations, relative residual %.3e > %.3e", total, beta / bn, rtol);
+    }
+    CK(launch_axpbyz(n, 1.0 / beta, c->r, 0.0, c->r, V, s));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    double res = beta;
+    bool breakdown = false;
+    for (int j = 0; j < m && total < max_it; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* vj1 = V + (size_t)(j + 1) * n;
+      // z = M^-1 v_j ; w = J z
+      if (prec == PNP_F64) {
+        {
+          ProfScope ps(c, PNP_PROF_PRECOND, 120.0 * c->n_nodes);
+          CK(launch_block_apply(c->n_nodes, c->Dinv, vj, c->z, nullptr, s));
+        }
+        RC(ctx_jv64(c, U, c->z, c->w));
+      } else {
+        {
+          ProfScope ps(c, PNP_PROF_PRECOND, 108.0 * c->n_nodes);
+          CK(launch_block_apply(c->n_nodes, c->Dinv, vj, nullptr, c->V32, s));
+        }
+        RC(ctx_jv32(c, c->V32, c->JV32));
+        ProfScope ps(c, PNP_PROF_PRECOND, 36.0 * c->n_nodes);
+        CK(launch_to_f64(n, c->JV32, c->w, s));
+      }
+      {
+        // classical Gram-Schmidt, twice
+        ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (double)n * (4.0 * (j + 1) + 9.0));
+        CK(cudaMemsetAsync(dacc, 0, sizeof(double) * (j + 1), s));
+        for (int pass = 0; pass < 2; ++pass) {
+          CK(launch_multi_dot(n, j + 1, V, n, c->w, c->part, dh, s));
+          CK(launch_multi_axpy(n, j + 1, V, n, dh, c->w, dacc, s));
+        }
+        CK(launch_norm2(n, c->w, c->part, dnrm, s));
+        CK(launch_scale_by_inv(n, c->w, dnrm, vj1, s));
+      }
+      CK(cudaMemcpyAsync(hp, dacc, sizeof(double) * (m + 3), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const double nrm = hp[m + 2];
+      for (int i = 0; i <= j; ++i) Hij(i, j) = hp[i];
+      Hij(j + 1, j) = nrm;
+      if (!std::isfinite(nrm)) PNP_FAIL(PNP_ERR_NAN, "gmres: Krylov vector norm is not finite");
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double rr = std::hypot(Hij(j, j), Hij(j + 1, j));
+      if (rr == 0.0) PNP_FAIL(PNP_ERR_NAN, "gmres: singular Hessenberg matrix");
+      cs[j] = Hij(j, j) / rr;
+      sn[j] = Hij(j + 1, j) / rr;
+      Hij(j, j) = rr;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      res = std::fabs(g[j + 1]);
+      ++total;
+      k = j + 1;
+      if (nrm <= 1e-300 * bn) breakdown = true;
+      if (res <= tol || breakdown) break;
+    }
+    // y = H^-1 g ; x += M^-1 (V y)
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
+      y[i] = t / Hij(i, i);
+    }
+    for (int i = 0; i < k; ++i) hp[i] = -y[i];
+    CK(cudaMemcpyAsync(dh, hp, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->w, 0, sizeof(double) * n, s));
+    CK(launch_multi_axpy(n, k, V, n, dh, c->w, nullptr, s));
+    CK(launch_block_apply(c->n_nodes, c->Dinv, c->w, c->z, nullptr, s));
+    CK(launch_axpby(n, 1.0, c->z, 1.0, x, s));
+    if (res <= tol || breakdown) {
+      beta = res;
+      break;
+    }
+    // restart from the true residual
+    RC(apply_op(c, U, x, c->w, prec));
+    CK(launch_axpbyz(n, 1.0, b, -1.0, c->w, c->r, s));
+    RC(ctx_norm(c, c->r, &beta));
+  }
+  *its_out = total;
+  *rel_out = beta / bn;
+  return PNP_OK;
+}
+
+int ctx_newton(pnp_ctx* c, pnp_solve_stats* st) {
+  const double t0 = now_ms();
+  std::memset(st, 0, sizeof(*st));
+  const pnp_params& p = c->prm;
+  const int64_t n = c->n3();
+  cudaStream_t s = c->stream;
+  c->jv_count = 0;
+  c->res_count = 0;
+  RC(ctx_prepare_history(c));
+  CK(launch_make_consistent(c->rows(), c->U, s));
+  RC(ctx_residual(c, c->U, c->F));
+  double f0;
+  RC(ctx_norm(c, c->F, &f0));
+  st->res0 = f0;
+  if (!std::isfinite(f0)) {
+    st->status = PNP_ERR_NAN;
+    PNP_FAIL(PNP_ERR_NAN, "newton: initial residual is not finite");
+  }
+  const double target = std::max(p.newton_rtol * f0, p.newton_atol);
+  double f = f0, f_prev = f0, eta_prev = p.ew_eta_max;
+  int it = 0, kry = 0;
+  int rc = PNP_OK;
+  while (f > target) {
+    if (it >= p.newton_max_it) {
+      rc = PNP_ERR_NEWTON_DIVERGED;
+      pnp_set_error("newton: %d iterations, ||F|| = %.3e > target %.3e", it, f, target);
+      break;
+    }
+    RC(build_preconditioner(c, c->U));
+    CK(launch_axpby(n, -1.0, c->F, 0.0, c->rhs, s));
+    double eta;
+    if (p.precision == PNP_F64) {
+      eta = p.gmres_rtol;
+    } else {
+      // Eisenstat-Walker, choice 2 (gamma = 0.9, alpha = 2) with safeguards
+      if (it == 0) {
+        eta = 0.5;
+      } else {
+        eta = 0.9 * (f / f_prev) * (f / f_prev);
+        const double sg = 0.9 * eta_prev * eta_prev;
+        if (sg > 0.1) eta = std::max(eta, sg);
+      }
+      eta = std::max(eta, 0.5 * target / f);
+      eta = std::min(std::max(eta, p.ew_eta_min), p.ew_eta_max);
+    }
+    eta_prev = eta;
+    // one attempt = linear solve in precision `prec` + backtracking line search on ||F||;
+    // returns 0 accepted, 1 no decrease, <0 hard error (-status)
+    double alpha = 1.0, ft = 0.0;
+    int its = 0, lrc = PNP_OK;
+    double rel = 0;
+    auto attempt = [&](int prec, double tol) -> int {
+      CK(cudaMemsetAsync(c->dU, 0, sizeof(double) * n, s));
+      its = 0;
+      lrc = ctx_gmres(c, c->U, c->rhs, c->dU, tol, prec, p.gmres_max_it, &its, &rel, true);
+      kry += its;
+      if (lrc != PNP_OK && lrc != PNP_ERR_KRYLOV_MAXIT) return -lrc;
+      alpha = 1.0;
+      while (true) {
+        CK(launch_axpbyz(n, 1.0, c->U, alpha, c->dU, c->Ut, s));
+        RC(ctx_residual(c, c->Ut, c->Ft));
+        RC(ctx_norm(c, c->Ft, &ft));
+        if (!p.line_search) return std::isfinite(ft) ? 0 : 1;
+        if (std::isfinite(ft) && ft <= (1.0 - 1e-4 * alpha) * f) return 0;
+        alpha *= 0.5;
+        if (alpha < 1.0 / 1024) return 1;
+      }
+    };
+    int prec_used = p.precision;
+    int ar = attempt(p.precision, eta);
+    if (ar > 0 && p.precision == PNP_F32 && p.f64_fallback) {
+      if (p.monitor)
+        fprintf(stderr, "[pnp newton %2d] FP32 step rejected (gmres its %d rel %.2e alpha %.3g ||F_t|| %.3e)\n",
+                it, its, rel, alpha, ft);
+      prec_used = PNP_F64;
+      st->f64_fallbacks++;
+      ar = attempt(PNP_F64, std::min(eta, p.gmres_rtol > 0 ? std::max(p.gmres_rtol, 1e-12) : 1e-8));
+    }
+    if (p.monitor)
+      fprintf(stderr, "[pnp newton %2d] ||F|| %.6e -> %.6e  eta %.2e  %s gmres its %4d rel %.2e  alpha %.4g\n", it,
+              f, ft, eta, prec_used == PNP_F32 ? "f32" : "f64", its, rel, alpha);
+    if (ar < 0) {
+      rc = -ar;
+      break;
+    }
+    if (ar > 0) {
+      rc = std::isfinite(ft) ? PNP_ERR_NEWTON_DIVERGED : PNP_ERR_NAN;
+      pnp_set_error("newton: %s at iteration %d (||F|| = %.3e)",
+                    std::isfinite(ft) ? "line search failed" : "residual became non-finite", it + 1, f);
+      break;
+    }
+    std::swap(c->U, c->Ut);
+    std::swap(c->F, c->Ft);
+    f_prev = f;
+    f = ft;
+    ++it;
+  }
+  CK(cudaStreamSynchronize(s));
+  st->status = rc;
+  st->newton_its = it;
+  st->krylov_its = kry;
+  st->res_final = f;
+  st->jv_evals = c->jv_count;
+  st->residual_evals = c->res_count;
+  st->wall_ms = now_ms() - t0;
+  return rc;
+}
+
+int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st);  // mlp.cu
+
+int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st) {
+  const double t0 = now_ms();
+  const int64_t n = c->n3();
+  cudaStream_t s = c->stream;
+  pnp_params& p = c->prm;
+  if (c->step == 0 || p.bdf_order == 1) {
+    p.beta0 = 1.0; p.beta1 = -1.0; p.beta2 = 0.0;
+  } else {
+    p.beta0 = 1.5; p.beta1 = -2.0; p.beta2 = 0.5;
+  }
+  // advection at t^{k+1}: v~ = 2 v^k - v^{k-1} (Eq. averaging1)
+  CK(launch_axpbyz(n, 2.0, c->vel, -1.0, c->vel_prev, c->adv, s));
+  int start = p.start_mode;
+  double r_extra = 0, r_learn = 0;
+  if (start == PNP_START_LEARNED) {
+    pnp_solve_stats tmp;
+    std::memset(&tmp, 0, sizeof(tmp));
+    const int lrc = pnp_learned_start(c, &tmp);
+    if (lrc == PNP_OK) {
+      start = tmp.start_used;
+      r_extra = tmp.res_start_extrapolated;
+      r_learn = tmp.res_start_learned;
+    } else if (lrc == PNP_ERR_STATE) {
+      start = PNP_START_EXTRAPOLATE;  // no trained network: plain extrapolation
+    } else {
+      return lrc;
+    }
+  }
+  if (start == PNP_START_PREVIOUS || (start == PNP_START_EXTRAPOLATE && c->step == 0)) {
+    CK(cudaMemcpyAsync(c->U, c->Uk, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else if (start == PNP_START_EXTRAPOLATE) {
+    CK(launch_axpbyz(n, 2.0, c->Uk, -1.0, c->Ukm1, c->U, s));
+  }  // learned: U already holds the judged start
+  const int rc = ctx_newton(c, st);
+  st->start_used = start;
+  st->res_start_extrapolated = r_extra;
+  st->res_start_learned = r_learn;
+  if (rc != PNP_OK) return rc;
+  CK(cudaMemcpyAsync(c->Ukm1, c->Uk, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c->Uk, c->U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c->vel_prev, c->vel, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  c->step++;
+  st->wall_ms = now_ms() - t0;
+  return PNP_OK;
+}

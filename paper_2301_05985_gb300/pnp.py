@@ -1,0 +1,316 @@
+"""Thin ctypes binding of the C ABI in ``include/pnp.h`` (argument marshalling only).
+
+Every computation runs in ``_build/libpnp_gb300.so``; this module only converts Python
+arguments (numpy arrays on the host, torch CUDA tensors on the device) into pointers
+and sizes, checks status codes and raises ``PnpError`` with the library's message.
+There is no fallback: if the library is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpnp_gb300.so")
+
+# enums (include/pnp.h)
+PNP_OK, PNP_ERR_ARG, PNP_ERR_MESH, PNP_ERR_MESH_UNBALANCED, PNP_ERR_NAN = 0, 1, 2, 3, 4
+PNP_ERR_KRYLOV_MAXIT, PNP_ERR_NEWTON_DIVERGED, PNP_ERR_CUDA, PNP_ERR_DEVICE_FLAG = 5, 6, 7, 8
+PNP_ERR_NOMEM, PNP_ERR_STATE = 9, 10
+PNP_C_PLUS, PNP_C_MINUS, PNP_PHI = 0, 1, 2
+PNP_NATURAL, PNP_DIRICHLET = 0, 1
+PNP_F64, PNP_F32 = 0, 1
+PNP_DEVICE, PNP_HOST = 0, 1
+PNP_FIELD_U, PNP_FIELD_U_PREV, PNP_FIELD_U_PREV2 = 0, 1, 2
+PNP_FIELD_ADVECTION, PNP_FIELD_VELOCITY, PNP_FIELD_VELOCITY_PREV = 3, 4, 5
+PNP_START_PREVIOUS, PNP_START_EXTRAPOLATE, PNP_START_LEARNED = 0, 1, 2
+
+
+class PnpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[pnp status {code}] {msg}")
+        self.code = code
+
+
+class pnp_params(C.Structure):
+    _fields_ = [
+        ("eps", C.c_double), ("dt", C.c_double), ("C_I", C.c_double),
+        ("beta0", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+        ("steady", C.c_int32), ("bdf_order", C.c_int32),
+        ("newton_rtol", C.c_double), ("newton_atol", C.c_double),
+        ("newton_max_it", C.c_int32), ("line_search", C.c_int32),
+        ("gmres_restart", C.c_int32), ("gmres_max_it", C.c_int32),
+        ("gmres_rtol", C.c_double),
+        ("precision", C.c_int32), ("start_mode", C.c_int32),
+        ("ew_eta_max", C.c_double), ("ew_eta_min", C.c_double),
+        ("monitor", C.c_int32), ("f64_fallback", C.c_int32),
+    ]
+
+
+class pnp_solve_stats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("newton_its", C.c_int32), ("krylov_its", C.c_int32),
+        ("residual_evals", C.c_int32), ("jv_evals", C.c_int32), ("start_used", C.c_int32),
+        ("f64_fallbacks", C.c_int32), ("pad_", C.c_int32),
+        ("res0", C.c_double), ("res_final", C.c_double),
+        ("res_start_extrapolated", C.c_double), ("res_start_learned", C.c_double),
+        ("wall_ms", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+_P = C.POINTER
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "pnp_last_error": (C.c_char_p, []),
+    "pnp_version": (C.c_char_p, []),
+    "pnp_params_default": (None, [_P(pnp_params)]),
+    "pnp_mesh_create": (C.c_int, [C.c_int, C.c_int, _i64, _vp, _vp, _P(_vp)]),
+    "pnp_mesh_destroy": (None, [_vp]),
+    "pnp_mesh_info": (C.c_int, [_vp, _P(C.c_int), _P(C.c_int), _P(_i64), _P(_i64), _P(_i64)]),
+    "pnp_mesh_node_coords": (C.c_int, [_vp, _vp]),
+    "pnp_mesh_hanging": (C.c_int, [_vp, _vp]),
+    "pnp_mesh_elements": (C.c_int, [_vp, _vp, _vp]),
+    "pnp_ctx_create": (C.c_int, [_vp, _P(pnp_params), _vp, _P(_vp)]),
+    "pnp_ctx_destroy": (None, [_vp]),
+    "pnp_set_params": (C.c_int, [_vp, _P(pnp_params)]),
+    "pnp_get_params": (C.c_int, [_vp, _P(pnp_params)]),
+    "pnp_set_bc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _d]),
+    "pnp_set_field": (C.c_int, [_vp, C.c_int, _vp, C.c_int]),
+    "pnp_get_field": (C.c_int, [_vp, C.c_int, _vp, C.c_int]),
+    "pnp_make_consistent": (C.c_int, [_vp]),
+    "pnp_residual": (C.c_int, [_vp, _vp, _vp]),
+    "pnp_jv": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int]),
+    "pnp_block_diag": (C.c_int, [_vp, _vp, _vp]),
+    "pnp_gmres": (C.c_int, [_vp, _vp, _vp, _vp, _d, C.c_int, _P(pnp_solve_stats)]),
+    "pnp_newton_solve": (C.c_int, [_vp, _P(pnp_solve_stats)]),
+    "pnp_time_step": (C.c_int, [_vp, _P(pnp_solve_stats)]),
+    "pnp_step_count": (C.c_int, [_vp, _P(_i64)]),
+    "pnp_reset_history": (C.c_int, [_vp]),
+    "pnp_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "pnp_profile_read": (C.c_int, [_vp, C.c_int, _P(_d), _P(_i64), _P(_d)]),
+    "pnp_kernel_launches": (_i64, []),
+}
+
+PNP_PROF_RESIDUAL, PNP_PROF_JV64, PNP_PROF_JV32, PNP_PROF_BLOCKDIAG = 0, 1, 2, 3
+PNP_PROF_ORTHO, PNP_PROF_PRECOND, PNP_PROF_MLP, PNP_PROF_KINDS = 4, 5, 6, 7
+PROF_NAMES = ["residual64", "jv64", "jv32", "blockdiag", "ortho", "precond", "mlp"]
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            if hasattr(L, name):
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def register(name, restype, argtypes):
+    """Declare the signature of an additional entry point (used by sibling modules)."""
+    SIGNATURES[name] = (restype, argtypes)
+    if _lib is not None and hasattr(_lib, name):
+        fn = getattr(_lib, name)
+        fn.restype = restype
+        fn.argtypes = argtypes
+
+
+def check(rc: int):
+    if rc != PNP_OK:
+        raise PnpError(rc, lib().pnp_last_error().decode())
+
+
+def default_params(**kw) -> pnp_params:
+    p = pnp_params()
+    lib().pnp_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"pnp_params has no field {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(x):
+    """Pointer of a torch tensor (device or host) or numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr()
+
+
+class Mesh:
+    """Q1 mesh of a 2:1-balanced octree (owns a pnp_mesh handle)."""
+
+    def __init__(self, octants):
+        a = np.ascontiguousarray(octants.anchors, dtype=np.int32)
+        lv = np.ascontiguousarray(octants.levels, dtype=np.uint8)
+        h = C.c_void_p()
+        check(lib().pnp_mesh_create(octants.dim, octants.max_level, octants.n, a.ctypes.data, lv.ctypes.data,
+                                    C.byref(h)))
+        self.h = h
+        d, L = C.c_int(), C.c_int()
+        ne, nn, nh = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().pnp_mesh_info(h, C.byref(d), C.byref(L), C.byref(ne), C.byref(nn), C.byref(nh)))
+        self.dim, self.max_level = d.value, L.value
+        self.n_elem, self.n_nodes, self.n_hanging = ne.value, nn.value, nh.value
+        self.ijk = np.zeros((self.n_nodes, self.dim), np.int32)
+        check(lib().pnp_mesh_node_coords(h, self.ijk.ctypes.data))
+        hf = np.zeros(self.n_nodes, np.uint8)
+        check(lib().pnp_mesh_hanging(h, hf.ctypes.data))
+        self.hanging = hf.astype(bool)
+
+    def elements(self):
+        a = np.zeros((self.n_elem, self.dim), np.int32)
+        lv = np.zeros(self.n_elem, np.uint8)
+        check(lib().pnp_mesh_elements(self.h, a.ctypes.data, lv.ctypes.data))
+        return a, lv
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pnp_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """A solver context on the current CUDA device (owns a pnp_ctx handle).
+
+    ``stream`` is a raw cudaStream_t handle (int); torch users pass
+    ``torch.cuda.current_stream().cuda_stream``.
+    """
+
+    def __init__(self, mesh: Mesh, params: pnp_params, stream: int = 0):
+        h = C.c_void_p()
+        check(lib().pnp_ctx_create(mesh.h, C.byref(params), C.c_void_p(stream), C.byref(h)))
+        self.h = h
+        self.mesh = mesh
+        self.dim = mesh.dim
+        self.n_nodes = mesh.n_nodes
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pnp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # parameters / BCs / fields
+    def set_params(self, p: pnp_params):
+        check(lib().pnp_set_params(self.h, C.byref(p)))
+
+    def get_params(self) -> pnp_params:
+        p = pnp_params()
+        check(lib().pnp_get_params(self.h, C.byref(p)))
+        return p
+
+    def set_bc(self, face: int, field: int, kind: int, value: float):
+        check(lib().pnp_set_bc(self.h, face, field, kind, value))
+
+    def set_bcs(self, bcs):
+        for f in range(bcs.types.shape[0]):
+            for k in range(3):
+                self.set_bc(f, k, int(bcs.types[f, k]), float(bcs.values[f, k]))
+
+    def set_field(self, which: int, x, where: int | None = None):
+        if where is None:
+            where = PNP_HOST if isinstance(x, np.ndarray) else PNP_DEVICE
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+        check(lib().pnp_set_field(self.h, which, _ptr(x), where))
+
+    def get_field(self, which: int, out=None, where: int | None = None):
+        ncomp = self.dim if which >= PNP_FIELD_ADVECTION else 3
+        if out is None:
+            out = np.zeros((self.n_nodes, ncomp))
+        if where is None:
+            where = PNP_HOST if isinstance(out, np.ndarray) else PNP_DEVICE
+        check(lib().pnp_get_field(self.h, which, _ptr(out), where))
+        return out
+
+    def make_consistent(self):
+        check(lib().pnp_make_consistent(self.h))
+
+    # operators (device pointers: torch CUDA tensors)
+    def residual(self, U, F):
+        check(lib().pnp_residual(self.h, _ptr(U), _ptr(F)))
+        return F
+
+    def jv(self, U, V, JV, precision: int = PNP_F64):
+        check(lib().pnp_jv(self.h, _ptr(U), _ptr(V), _ptr(JV), precision))
+        return JV
+
+    def block_diag(self, U, D):
+        check(lib().pnp_block_diag(self.h, _ptr(U), _ptr(D)))
+        return D
+
+    def gmres(self, U, b, x, rtol: float, precision: int = PNP_F64, raise_on_error=True):
+        st = pnp_solve_stats()
+        rc = lib().pnp_gmres(self.h, _ptr(U), _ptr(b), _ptr(x), rtol, precision, C.byref(st))
+        if raise_on_error:
+            check(rc)
+        return st
+
+    def newton_solve(self, raise_on_error=True) -> pnp_solve_stats:
+        st = pnp_solve_stats()
+        rc = lib().pnp_newton_solve(self.h, C.byref(st))
+        if raise_on_error:
+            check(rc)
+        return st
+
+    def time_step(self, raise_on_error=True) -> pnp_solve_stats:
+        st = pnp_solve_stats()
+        rc = lib().pnp_time_step(self.h, C.byref(st))
+        if raise_on_error:
+            check(rc)
+        return st
+
+    def reset_history(self):
+        check(lib().pnp_reset_history(self.h))
+
+    def step_count(self) -> int:
+        k = C.c_int64()
+        check(lib().pnp_step_count(self.h, C.byref(k)))
+        return k.value
+
+    def profile_enable(self, on: bool = True):
+        check(lib().pnp_profile_enable(self.h, int(on)))
+
+    def profile_read(self) -> dict:
+        out = {}
+        for k, name in enumerate(PROF_NAMES):
+            ms, cnt, by = C.c_double(), C.c_int64(), C.c_double()
+            check(lib().pnp_profile_read(self.h, k, C.byref(ms), C.byref(cnt), C.byref(by)))
+            out[name] = {"ms": ms.value, "count": cnt.value, "alg_bytes": by.value}
+        return out
+
+
+def kernel_launches() -> int:
+    return int(lib().pnp_kernel_launches())
