@@ -61,7 +61,7 @@ def workload_octants(small: bool):
 def mode_params(pnp, mode):
     if mode == "mixed":
         return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F32, start_mode=pnp.PNP_START_LEARNED,
-                                  newton_rtol=1e-8, gmres_restart=30, gmres_max_it=3000)
+                                  newton_rtol=1e-8, gmres_restart=60, gmres_max_it=3000)
     return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F64, start_mode=pnp.PNP_START_PREVIOUS,
                               newton_rtol=1e-8, gmres_rtol=1e-8, gmres_restart=100, gmres_max_it=4000)
 

@@ -141,7 +141,8 @@ static int check_params(const pnp_params* p) {
 static void free_ctx_memory(pnp_ctx* c) {
   void* ptrs[] = {c->d_conn, c->d_level, c->d_faces, c->d_hnode, c->d_hpar, c->d_hnp, c->U, c->Uk, c->Ukm1,
                   c->adv, c->vel, c->vel_prev, c->hs, c->U32, c->adv32, c->hs32, c->V32, c->JV32, c->F,
-                  c->dU, c->Ut, c->Ft, c->rhs, c->Dinv, c->basis, c->w, c->z, c->r, c->part, c->dsc, c->dflag};
+                  c->dU, c->Ut, c->Ft, c->rhs, c->Dinv, c->D32, c->basis, c->w, c->z, c->r, c->part, c->dsc,
+                  c->dflag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hpin) cudaFreeHost(c->hpin);
@@ -203,6 +204,7 @@ int pnp_ctx_create(const pnp_mesh* m, const pnp_params* p, void* stream, pnp_ctx
   ALLOC(c->Ft, v3);
   ALLOC(c->rhs, v3);
   ALLOC(c->Dinv, sizeof(double) * 9 * N);
+  ALLOC(c->D32, sizeof(float) * 9 * N);
   ALLOC(c->w, v3);
   ALLOC(c->z, v3);
   ALLOC(c->r, v3);
@@ -250,8 +252,8 @@ int ctx_alloc_krylov(pnp_ctx* c, int m) {
   const size_t bb = sizeof(double) * (size_t)(m + 1) * (size_t)c->n3();
   cudaError_t e = cudaMalloc((void**)&c->basis, bb);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, sizeof(double) * (size_t)kRedBlocks * (m + 2));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->dsc, sizeof(double) * (2 * (m + 2) + 16));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hpin, sizeof(double) * (2 * (m + 2) + 16));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->dsc, sizeof(double) * (4 * (m + 2) + 16));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hpin, sizeof(double) * (4 * (m + 2) + 16));
   if (e != cudaSuccess) {
     pnp_set_error("Krylov scratch allocation (%zu bytes) failed: %s", bb, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? PNP_ERR_NOMEM : PNP_ERR_CUDA;

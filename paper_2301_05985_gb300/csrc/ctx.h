@@ -33,6 +33,7 @@ struct pnp_ctx {
   // Newton / Krylov scratch
   double *F = nullptr, *dU = nullptr, *Ut = nullptr, *Ft = nullptr, *rhs = nullptr;
   double* Dinv = nullptr;  // [N][9]
+  float* D32 = nullptr;    // [N][9] FP32 block diagonal (mixed-precision preconditioner)
   double* basis = nullptr; // [(m+1)][3N]
   double *w = nullptr, *z = nullptr, *r = nullptr;
   double* part = nullptr;  // reduction partials [kRedBlocks][m+2]

@@ -34,10 +34,12 @@ void note_launch();
 
 template <typename T>
 cudaError_t launch_element(int dim, bool jv, const ElemArgs<T>& A, cudaStream_t s);
-cudaError_t launch_block_diag(int dim, const ElemArgs<double>& A, double* Dout, cudaStream_t s);
+template <typename T>
+cudaError_t launch_block_diag(int dim, const ElemArgs<T>& A, T* Dout, cudaStream_t s);
 template <typename T>
 cudaError_t launch_row_fixups(const RowArgs& R, const T* in, T* out, int mode, cudaStream_t s);
-cudaError_t launch_diag_rows(const RowArgs& R, double* Dg, cudaStream_t s);
+template <typename T>
+cudaError_t launch_diag_rows(const RowArgs& R, T* Dg, cudaStream_t s);
 
 // ------------------------------------------------------------------ vector kernels
 // All reductions are deterministic: fixed grid, per-block partials, one final block.
@@ -66,9 +68,18 @@ cudaError_t launch_multi_axpy(int64_t n, int k, const double* Vb, int64_t ld, co
 // v = w / nrm[0]
 cudaError_t launch_scale_by_inv(int64_t n, const double* w, const double* nrm, double* v, cudaStream_t s);
 // z_i = Dinv_i v_i per node (3x3 blocks); optionally also a float copy z32 (may be null)
-cudaError_t launch_block_apply(int64_t N, const double* Dinv, const double* v, double* z, float* z32, cudaStream_t s);
-// invert 3x3 blocks in place (Gauss-Jordan with partial pivoting); flag[0] |= 1 on a singular block
-cudaError_t launch_block_invert(int64_t N, double* D, int* flag, cudaStream_t s);
+cudaError_t launch_block_apply(int64_t N, const double* Dinv, const double* v, double scale, double* z, float* z32,
+                               cudaStream_t s);
+// d[i] = V_i . w for i < k, plus d[k] = w . w when with_self (part: [kRedBlocks][k+1])
+cudaError_t launch_multi_dot_ext(int64_t n, int k, bool with_self, const double* Vb, int64_t ld, const double* w,
+                                 double* part, double* d, cudaStream_t s);
+// w -= sum_i d[i] dinv[i] V_i (i < k);  nrm2[0] = w . w afterwards
+cudaError_t launch_multi_axpy_norm(int64_t n, int k, const double* Vb, int64_t ld, const double* d, const double* dinv,
+                                   double* w, double* part, double* nrm2, cudaStream_t s);
+// Dinv = inverse of the 3x3 blocks of D (Gauss-Jordan with partial pivoting, FP64);
+// flag[0] |= 1 on a singular or non-finite block.  D may alias Dinv when T = double.
+template <typename T>
+cudaError_t launch_block_invert(int64_t N, const T* D, double* Dinv, int* flag, cudaStream_t s);
 // hanging interpolation + Dirichlet values on U
 cudaError_t launch_make_consistent(const RowArgs& R, double* U, cudaStream_t s);
 // copy with layout change: [N][dim] <-> [N][3]

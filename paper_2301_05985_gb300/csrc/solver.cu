@@ -100,14 +100,26 @@ int ctx_block_diag(pnp_ctx* c, const double* U, double* D) {
   CK(cudaMemsetAsync(D, 0, sizeof(double) * 9 * c->n_nodes, c->stream));
   {
     ProfScope ps(c, PNP_PROF_BLOCKDIAG, 136.0 * c->n_nodes + c->conn_bytes());
-    CK(launch_block_diag(c->dim, elem_args<double>(c, U, nullptr, c->hs, c->adv, nullptr), D, c->stream));
+    CK(launch_block_diag<double>(c->dim, elem_args<double>(c, U, nullptr, c->hs, c->adv, nullptr), D, c->stream));
   }
-  CK(launch_diag_rows(c->rows(), D, c->stream));
+  CK(launch_diag_rows<double>(c->rows(), D, c->stream));
+  return PNP_OK;
+}
+
+// FP32 block diagonal at the FP32 copy of the state (ctx_prepare_f32 first)
+static int ctx_block_diag32(pnp_ctx* c, float* D) {
+  CK(cudaMemsetAsync(D, 0, sizeof(float) * 9 * c->n_nodes, c->stream));
+  {
+    ProfScope ps(c, PNP_PROF_BLOCKDIAG, 68.0 * c->n_nodes + c->conn_bytes());
+    CK(launch_block_diag<float>(c->dim, elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr), D,
+                                c->stream));
+  }
+  CK(launch_diag_rows<float>(c->rows(), D, c->stream));
   return PNP_OK;
 }
 
 int ctx_norm(pnp_ctx* c, const double* x, double* out) {
-  double* slot = c->dsc + 2 * (c->m_alloc + 2) + 8;
+  double* slot = c->dsc + 4 * (c->m_alloc + 2) + 8;
   CK(launch_norm2(c->n3(), x, c->part, slot, c->stream));
   CK(cudaMemcpyAsync(c->hpin, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -115,10 +127,17 @@ int ctx_norm(pnp_ctx* c, const double* x, double* out) {
   return PNP_OK;
 }
 
-static int build_preconditioner(pnp_ctx* c, const double* U) {
-  RC(ctx_block_diag(c, U, c->Dinv));
+// 3x3 block-Jacobi preconditioner at U, built in the precision of the Jv
+static int build_preconditioner(pnp_ctx* c, const double* U, int prec) {
   CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream));
-  CK(launch_block_invert(c->n_nodes, c->Dinv, c->dflag, c->stream));
+  if (prec == PNP_F32) {
+    RC(ctx_prepare_f32(c, U));
+    RC(ctx_block_diag32(c, c->D32));
+    CK(launch_block_invert<float>(c->n_nodes, c->D32, c->Dinv, c->dflag, c->stream));
+  } else {
+    RC(ctx_block_diag(c, U, c->Dinv));
+    CK(launch_block_invert<double>(c->n_nodes, c->Dinv, c->Dinv, c->dflag, c->stream));
+  }
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -135,19 +154,27 @@ static int apply_op(pnp_ctx* c, const double* U, const double* x, double* w, int
   return PNP_OK;
 }
 
+// Right-preconditioned GMRES(m).  The Krylov vectors are stored unnormalised (v_i = u_i / s_i,
+// s_i kept on the host) so no normalisation pass is needed; each iteration does one
+// classical Gram-Schmidt pass (multi-dot, then multi-axpy fused with the new norm) and a
+// second pass only when the norm dropped below 1/sqrt(2) of its value before the pass
+// (Daniel-Gragg-Kaufman-Stewart criterion).  Dots and the Hessenberg system are FP64.
 int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int prec, int max_it, int* its_out,
               double* rel_out, bool have_precond) {
   const int m = c->prm.gmres_restart;
   RC(ctx_alloc_krylov(c, m));
   const int64_t n = c->n3();
   cudaStream_t s = c->stream;
-  if (!have_precond) RC(build_preconditioner(c, U));
+  if (!have_precond) RC(build_preconditioner(c, U, prec));
   if (prec == PNP_F32) RC(ctx_prepare_f32(c, U));
   double* V = c->basis;
-  double* dh = c->dsc;                  // [m+2] projections of one pass
-  double* dacc = c->dsc + (m + 2);      // [m+2] accumulated column, then the norm
-  double* dnrm = c->dsc + 2 * (m + 2);  // [1]
-  double* hp = c->hpin;
+  double* dd = c->dsc;                    // [m+2] dot products of one pass
+  double* dinv = c->dsc + (m + 2);        // [m+2] 1 / s_i^2
+  double* dnrm = c->dsc + 2 * (m + 2);    // [1]  w . w after a pass
+  double* dcoef = c->dsc + 2 * (m + 2) + 2;  // [m+1] solution-update coefficients (shares the tail)
+  double* hp = c->hpin;                   // [0, m+2): D2H scratch
+  double* hup = c->hpin + (m + 2);        // [m+2]: H2D slots for 1/s_i^2
+  double* hco = c->hpin + 2 * (m + 2) + 2;  // [m+1]: H2D slots for the update coefficients
   *its_out = 0;
   double bn;
   RC(ctx_norm(c, b, &bn));
@@ -158,12 +185,12 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
     return PNP_OK;
   }
   const double tol = rtol * bn;
-  // r = b - J x
+  // u_0 = b - J x
   RC(apply_op(c, U, x, c->w, prec));
-  CK(launch_axpbyz(n, 1.0, b, -1.0, c->w, c->r, s));
+  CK(launch_axpbyz(n, 1.0, b, -1.0, c->w, V, s));
   double beta;
-  RC(ctx_norm(c, c->r, &beta));
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  RC(ctx_norm(c, V, &beta));
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), sv(m + 1), h(m + 1);
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   int total = 0;
   while (true) {
@@ -174,48 +201,65 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       *rel_out = beta / bn;
       PNP_FAIL(PNP_ERR_KRYLOV_MAXIT, "gmres: %d iterations, relative residual %.3e > %.3e", total, beta / bn, rtol);
     }
-    CK(launch_axpbyz(n, 1.0 / beta, c->r, 0.0, c->r, V, s));
+    sv[0] = beta;
+    CK(cudaStreamSynchronize(s));  // the pinned upload slots are free again
+    hup[0] = 1.0 / (beta * beta);
+    CK(cudaMemcpyAsync(dinv, hup, sizeof(double), cudaMemcpyHostToDevice, s));
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k = 0;
     double res = beta;
     bool breakdown = false;
     for (int j = 0; j < m && total < max_it; ++j) {
-      double* vj = V + (size_t)j * n;
-      double* vj1 = V + (size_t)(j + 1) * n;
-      // z = M^-1 v_j ; w = J z
+      const double* uj = V + (size_t)j * n;
+      double* w = V + (size_t)(j + 1) * n;
+      // z = M^-1 (u_j / s_j) ; w = J z
       if (prec == PNP_F64) {
         {
           ProfScope ps(c, PNP_PROF_PRECOND, 120.0 * c->n_nodes);
-          CK(launch_block_apply(c->n_nodes, c->Dinv, vj, c->z, nullptr, s));
+          CK(launch_block_apply(c->n_nodes, c->Dinv, uj, 1.0 / sv[j], c->z, nullptr, s));
         }
-        RC(ctx_jv64(c, U, c->z, c->w));
+        RC(ctx_jv64(c, U, c->z, w));
       } else {
         {
           ProfScope ps(c, PNP_PROF_PRECOND, 108.0 * c->n_nodes);
-          CK(launch_block_apply(c->n_nodes, c->Dinv, vj, nullptr, c->V32, s));
+          CK(launch_block_apply(c->n_nodes, c->Dinv, uj, 1.0 / sv[j], nullptr, c->V32, s));
         }
         RC(ctx_jv32(c, c->V32, c->JV32));
         ProfScope ps(c, PNP_PROF_PRECOND, 36.0 * c->n_nodes);
-        CK(launch_to_f64(n, c->JV32, c->w, s));
+        CK(launch_to_f64(n, c->JV32, w, s));
       }
+      double w0sq, w1sq;
       {
-        // classical Gram-Schmidt, twice
-        ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (double)n * (4.0 * (j + 1) + 9.0));
-        CK(cudaMemsetAsync(dacc, 0, sizeof(double) * (j + 1), s));
-        for (int pass = 0; pass < 2; ++pass) {
-          CK(launch_multi_dot(n, j + 1, V, n, c->w, c->part, dh, s));
-          CK(launch_multi_axpy(n, j + 1, V, n, dh, c->w, dacc, s));
-        }
-        CK(launch_norm2(n, c->w, c->part, dnrm, s));
-        CK(launch_scale_by_inv(n, c->w, dnrm, vj1, s));
+        ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (double)n * (2.0 * (j + 1) + 4.0));
+        CK(launch_multi_dot_ext(n, j + 1, true, V, n, w, c->part, dd, s));
+        CK(launch_multi_axpy_norm(n, j + 1, V, n, dd, dinv, w, c->part, dnrm, s));
+        CK(cudaMemcpyAsync(hp, dd, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hp + (m + 1), dnrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
       }
-      CK(cudaMemcpyAsync(hp, dacc, sizeof(double) * (m + 3), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      const double nrm = hp[m + 2];
-      for (int i = 0; i <= j; ++i) Hij(i, j) = hp[i];
-      Hij(j + 1, j) = nrm;
+      for (int i = 0; i <= j; ++i) h[i] = hp[i] / sv[i];
+      w0sq = hp[j + 1];
+      w1sq = hp[m + 1];
+      if (w1sq < 0.5 * w0sq) {
+        ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (double)n * (2.0 * (j + 1) + 2.0));
+        CK(launch_multi_dot_ext(n, j + 1, false, V, n, w, c->part, dd, s));
+        CK(launch_multi_axpy_norm(n, j + 1, V, n, dd, dinv, w, c->part, dnrm, s));
+        CK(cudaMemcpyAsync(hp, dd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hp + (m + 1), dnrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i <= j; ++i) h[i] += hp[i] / sv[i];
+        w1sq = hp[m + 1];
+      }
+      const double nrm = std::sqrt(w1sq);
       if (!std::isfinite(nrm)) PNP_FAIL(PNP_ERR_NAN, "gmres: Krylov vector norm is not finite");
+      sv[j + 1] = nrm;
+      if (nrm > 0) {
+        hup[j + 1] = 1.0 / w1sq;
+        CK(cudaMemcpyAsync(dinv + j + 1, hup + j + 1, sizeof(double), cudaMemcpyHostToDevice, s));
+      }
+      for (int i = 0; i <= j; ++i) Hij(i, j) = h[i];
+      Hij(j + 1, j) = nrm;
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
         Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
@@ -235,17 +279,17 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       if (nrm <= 1e-300 * bn) breakdown = true;
       if (res <= tol || breakdown) break;
     }
-    // y = H^-1 g ; x += M^-1 (V y)
+    // y = H^-1 g ; x += M^-1 (sum_i y_i u_i / s_i)
     for (int i = k - 1; i >= 0; --i) {
       double t = g[i];
       for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
       y[i] = t / Hij(i, i);
     }
-    for (int i = 0; i < k; ++i) hp[i] = -y[i];
-    CK(cudaMemcpyAsync(dh, hp, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    for (int i = 0; i < k; ++i) hco[i] = -y[i] / sv[i];
+    CK(cudaMemcpyAsync(dcoef, hco, sizeof(double) * k, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(c->w, 0, sizeof(double) * n, s));
-    CK(launch_multi_axpy(n, k, V, n, dh, c->w, nullptr, s));
-    CK(launch_block_apply(c->n_nodes, c->Dinv, c->w, c->z, nullptr, s));
+    CK(launch_multi_axpy(n, k, V, n, dcoef, c->w, nullptr, s));
+    CK(launch_block_apply(c->n_nodes, c->Dinv, c->w, 1.0, c->z, nullptr, s));
     CK(launch_axpby(n, 1.0, c->z, 1.0, x, s));
     if (res <= tol || breakdown) {
       beta = res;
@@ -253,9 +297,12 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
     }
     // restart from the true residual
     RC(apply_op(c, U, x, c->w, prec));
-    CK(launch_axpbyz(n, 1.0, b, -1.0, c->w, c->r, s));
-    RC(ctx_norm(c, c->r, &beta));
+    CK(launch_axpbyz(n, 1.0, b, -1.0, c->w, V, s));
+    RC(ctx_norm(c, V, &beta));
+    if (c->prm.monitor >= 2)
+      fprintf(stderr, "[pnp gmres] its %5d  estimate %.3e  true %.3e (relative)\n", total, res / bn, beta / bn);
   }
+  CK(cudaStreamSynchronize(s));
   *its_out = total;
   *rel_out = beta / bn;
   return PNP_OK;
@@ -289,7 +336,7 @@ int ctx_newton(pnp_ctx* c, pnp_solve_stats* st) {
       pnp_set_error("newton: %d iterations, ||F|| = %.3e > target %.3e", it, f, target);
       break;
     }
-    RC(build_preconditioner(c, c->U));
+    RC(build_preconditioner(c, c->U, p.precision));
     CK(launch_axpby(n, -1.0, c->F, 0.0, c->rhs, s));
     double eta;
     if (p.precision == PNP_F64) {

@@ -97,6 +97,52 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_dot_part(int64_t n, int k
   }
 }
 
+// d_i = V_i . w for i < k and, if kk > k, d_k = w . w ; 16 vectors per sweep over n.
+__global__ void __launch_bounds__(kRedThreads) k_multi_dot_ext(int64_t n, int k, int kk, const double* __restrict__ Vb,
+                                                               int64_t ld, const double* __restrict__ w,
+                                                               double* __restrict__ part) {
+  __shared__ double sh[kRedThreads];
+  for (int i0 = 0; i0 < kk; i0 += 16) {
+    const int cnt = min(16, kk - i0);
+    double acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+      const double wv = w[t];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < cnt) {
+          const int i = i0 + j;
+          acc[j] += (i < k ? Vb[(int64_t)i * ld + t] : wv) * wv;
+        }
+    }
+    for (int j = 0; j < cnt; ++j) {
+      const double s = block_sum(acc[j], sh);
+      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kk + i0 + j] = s;
+    }
+  }
+}
+
+// w -= sum_i (d_i * dinv_i) V_i  and per-block partial sums of the updated w . w
+__global__ void __launch_bounds__(kRedThreads) k_multi_axpy_norm(int64_t n, int k, const double* __restrict__ Vb,
+                                                                 int64_t ld, const double* __restrict__ d,
+                                                                 const double* __restrict__ dinv,
+                                                                 double* __restrict__ w, double* __restrict__ part) {
+  extern __shared__ double cf[];
+  __shared__ double sh[kRedThreads];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = d[i] * dinv[i];
+  __syncthreads();
+  double ss = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    double v = w[t];
+    for (int i = 0; i < k; ++i) v -= cf[i] * Vb[(int64_t)i * ld + t];
+    w[t] = v;
+    ss += v * v;
+  }
+  ss = block_sum(ss, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = ss;
+}
+
 __global__ void __launch_bounds__(256) k_multi_axpy(int64_t n, int k, const double* __restrict__ Vb, int64_t ld,
                                                     const double* __restrict__ h, double* __restrict__ w,
                                                     double* __restrict__ hacc) {
@@ -119,12 +165,12 @@ __global__ void k_scale_by_inv(int64_t n, const double* __restrict__ w, const do
     v[i] = w[i] * a;
 }
 
-__global__ void k_block_apply(int64_t N, const double* __restrict__ Dinv, const double* __restrict__ v,
+__global__ void k_block_apply(int64_t N, const double* __restrict__ Dinv, const double* __restrict__ v, double scale,
                               double* __restrict__ z, float* __restrict__ z32) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double* B = Dinv + 9 * i;
-  const double a = v[3 * i], b = v[3 * i + 1], c = v[3 * i + 2];
+  const double a = scale * v[3 * i], b = scale * v[3 * i + 1], c = scale * v[3 * i + 2];
   const double r0 = B[0] * a + B[1] * b + B[2] * c;
   const double r1 = B[3] * a + B[4] * b + B[5] * c;
   const double r2 = B[6] * a + B[7] * b + B[8] * c;
@@ -140,13 +186,14 @@ __global__ void k_block_apply(int64_t N, const double* __restrict__ Dinv, const 
   }
 }
 
-__global__ void k_block_invert(int64_t N, double* __restrict__ D, int* __restrict__ flag) {
+template <typename T>
+__global__ void k_block_invert(int64_t N, const T* D, double* Dinv, int* __restrict__ flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   double a[3][6];
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) {
-      a[r][c] = D[9 * i + 3 * r + c];
+      a[r][c] = (double)D[9 * i + 3 * r + c];
       a[r][3 + c] = (r == c) ? 1.0 : 0.0;
     }
   for (int col = 0; col < 3; ++col) {
@@ -172,7 +219,7 @@ __global__ void k_block_invert(int64_t N, double* __restrict__ D, int* __restric
       }
   }
   for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) D[9 * i + 3 * r + c] = a[r][3 + c];
+    for (int c = 0; c < 3; ++c) Dinv[9 * i + 3 * r + c] = a[r][3 + c];
 }
 
 __global__ void k_set_dirichlet(int64_t N, const uint8_t* __restrict__ faces, BcTable bc, double* __restrict__ U) {
@@ -260,14 +307,33 @@ cudaError_t launch_scale_by_inv(int64_t n, const double* w, const double* nrm, d
   if (n) { k_scale_by_inv<<<gs_blocks(n, 256), 256, 0, s>>>(n, w, nrm, v); note_launch(); }
   return cudaGetLastError();
 }
-cudaError_t launch_block_apply(int64_t N, const double* Dinv, const double* v, double* z, float* z32, cudaStream_t s) {
-  if (N) { k_block_apply<<<nblk(N, 256), 256, 0, s>>>(N, Dinv, v, z, z32); note_launch(); }
+cudaError_t launch_multi_dot_ext(int64_t n, int k, bool with_self, const double* Vb, int64_t ld, const double* w,
+                                 double* part, double* d, cudaStream_t s) {
+  const int kk = k + (with_self ? 1 : 0);
+  if (kk <= 0) return cudaSuccess;
+  k_multi_dot_ext<<<kRedBlocks, kRedThreads, 0, s>>>(n, k, kk, Vb, ld, w, part); note_launch();
+  k_reduce_parts<<<kk, kRedThreads, 0, s>>>(kRedBlocks, kk, part, d, 0); note_launch();
   return cudaGetLastError();
 }
-cudaError_t launch_block_invert(int64_t N, double* D, int* flag, cudaStream_t s) {
-  if (N) { k_block_invert<<<nblk(N, 128), 128, 0, s>>>(N, D, flag); note_launch(); }
+cudaError_t launch_multi_axpy_norm(int64_t n, int k, const double* Vb, int64_t ld, const double* d, const double* dinv,
+                                   double* w, double* part, double* nrm2, cudaStream_t s) {
+  k_multi_axpy_norm<<<kRedBlocks, kRedThreads, (k > 0 ? k : 1) * sizeof(double), s>>>(n, k, Vb, ld, d, dinv, w, part);
+  note_launch();
+  k_reduce_parts<<<1, kRedThreads, 0, s>>>(kRedBlocks, 1, part, nrm2, 0); note_launch();
   return cudaGetLastError();
 }
+cudaError_t launch_block_apply(int64_t N, const double* Dinv, const double* v, double scale, double* z, float* z32,
+                               cudaStream_t s) {
+  if (N) { k_block_apply<<<nblk(N, 256), 256, 0, s>>>(N, Dinv, v, scale, z, z32); note_launch(); }
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_block_invert(int64_t N, const T* D, double* Dinv, int* flag, cudaStream_t s) {
+  if (N) { k_block_invert<T><<<nblk(N, 128), 128, 0, s>>>(N, D, Dinv, flag); note_launch(); }
+  return cudaGetLastError();
+}
+template cudaError_t launch_block_invert<double>(int64_t, const double*, double*, int*, cudaStream_t);
+template cudaError_t launch_block_invert<float>(int64_t, const float*, double*, int*, cudaStream_t);
 cudaError_t launch_make_consistent(const RowArgs& R, double* U, cudaStream_t s) {
   if (R.n_nodes) { k_set_dirichlet<<<nblk(R.n_nodes, 256), 256, 0, s>>>(R.n_nodes, R.faces, R.bc, U); note_launch(); }
   if (R.n_hanging) { k_interp_hanging<<<nblk(R.n_hanging, 256), 256, 0, s>>>(R.n_hanging, R.hnode, R.hpar, R.hnp, U); note_launch(); }

@@ -1,0 +1,84 @@
+"""Pins of the FP64 network oracle: central differences, special cases, closed forms."""
+import math
+
+import numpy as np
+import pytest
+
+import mlp_oracle as M
+
+
+def test_gelu_closed_forms():
+    z = np.array([-3.0, -1.0, 0.0, 0.5, 2.0])
+    # Phi(z) from the complementary error function of the standard library
+    Phi = np.array([0.5 * math.erfc(-v / math.sqrt(2)) for v in z])
+    np.testing.assert_allclose(M.gelu(z), z * Phi, rtol=1e-14, atol=1e-15)
+    assert M.gelu(np.array([0.0]))[0] == 0.0
+    # derivative against a central difference of the closed form
+    h = 1e-6
+    fd = (M.gelu(z + h) - M.gelu(z - h)) / (2 * h)
+    np.testing.assert_allclose(M.gelu_prime(z), fd, rtol=1e-8, atol=1e-10)
+    # limits: GELU ~ identity for large z, ~ 0 for very negative z
+    assert abs(M.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
+    assert abs(M.gelu(np.array([-10.0]))[0]) < 1e-20
+
+
+def test_backward_matches_central_differences():
+    rng = np.random.default_rng(3)
+    layers = (12, 9, 7, 5, 3)
+    Ws, bs = M.init_params(1, layers)
+    for b in bs:
+        b += rng.normal(0, 0.1, b.shape)
+    X = rng.normal(size=(11, 12))
+    Y = rng.normal(size=(11, 3))
+    gW, gb, _ = M.backward(Ws, bs, X, Y)
+    h = 1e-6
+    for l in range(len(Ws)):
+        for (i, j) in [(0, 0), (layers[l] - 1, layers[l + 1] - 1), (layers[l] // 2, 1)]:
+            Wp = [w.copy() for w in Ws]; Wp[l][i, j] += h
+            Wm = [w.copy() for w in Ws]; Wm[l][i, j] -= h
+            fd = (M.loss(Wp, bs, X, Y) - M.loss(Wm, bs, X, Y)) / (2 * h)
+            assert abs(fd - gW[l][i, j]) < 1e-7 * max(1.0, abs(fd))
+        for j in [0, layers[l + 1] - 1]:
+            bp = [b.copy() for b in bs]; bp[l][j] += h
+            bm = [b.copy() for b in bs]; bm[l][j] -= h
+            fd = (M.loss(Ws, bp, X, Y) - M.loss(Ws, bm, X, Y)) / (2 * h)
+            assert abs(fd - gb[l][j]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_linear_special_case():
+    """With every hidden layer driven far into GELU's linear regime the network is an affine
+    map whose least-squares gradient is known in closed form."""
+    rng = np.random.default_rng(5)
+    layers = (4, 3, 3, 3, 2)
+    Ws = [np.eye(4)[:, :3] * 1.0, np.eye(3), np.eye(3), rng.normal(size=(3, 2))]
+    bs = [np.full(3, 50.0), np.zeros(3), np.zeros(3), np.zeros(2)]
+    # with the +50 shift, GELU(z) = z to double precision, so out = (X[:, :3] + 50) W4
+    X = rng.normal(size=(6, 4)) * 0.1
+    Y = rng.normal(size=(6, 2))
+    out, _, _ = M.forward(Ws, bs, X)
+    Aff = X[:, :3] + 50.0
+    np.testing.assert_allclose(out, Aff @ Ws[3], rtol=1e-13)
+    gW, gb, _ = M.backward(Ws, bs, X, Y)
+    np.testing.assert_allclose(gW[3], Aff.T @ (2 * (out - Y) / out.size), rtol=1e-10)
+
+
+def test_adam_first_step_is_sign_times_lr():
+    """Adam's bias-corrected first step moves every parameter by lr * g / (|g| + eps)."""
+    Ws, bs = M.init_params(2, (5, 4, 4, 4, 3))
+    rng = np.random.default_rng(9)
+    X = rng.normal(size=(8, 5)); Y = rng.normal(size=(8, 3))
+    gW, gb, _ = M.backward(Ws, bs, X, Y)
+    W0 = [w.copy() for w in Ws]
+    M.adam_step(Ws, bs, gW, gb, {}, lr=1e-3)
+    for w0, w1, g in zip(W0, Ws, gW):
+        np.testing.assert_allclose(w0 - w1, 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-6, atol=1e-12)
+
+
+def test_bf16_rounding():
+    x = np.array([1.0, 1.0 + 2**-8, 1.0 + 3 * 2**-9, -2.5, 3.0e-5])
+    r = M.bf16_round(x)
+    assert r[0] == 1.0
+    assert r[1] == 1.0          # tie rounds to even (1 + 2^-8 is halfway between 1 and 1 + 2^-7)
+    assert r[2] == 1.0 + 2**-7  # above the halfway point
+    assert r[3] == -2.5
+    assert abs(r[4] - 3.0e-5) <= 3.0e-5 * 2**-8
