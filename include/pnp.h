@@ -149,6 +149,10 @@ int pnp_mesh_hanging(const pnp_mesh* m, uint8_t* flags);
 /* Element anchors host int32 [n_elem][dim] and levels host uint8 [n_elem] in the
  * library's (Morton) element order. */
 int pnp_mesh_elements(const pnp_mesh* m, int32_t* anchors, uint8_t* levels);
+/* Statistics of the Morton patches the element kernels use (host int64 [7]): patches,
+ * most nodes in a patch, most colours, nodes shared between patches, partial rows,
+ * total patch slots, and the number of violated layout invariants (0 when valid). */
+int pnp_mesh_patch_stats(const pnp_mesh* m, int64_t* stats);
 
 /* ---------------------------------------------------------------- context -------- */
 /* Create a context on the current CUDA device: uploads the mesh (the mesh may be
@@ -202,6 +206,74 @@ int pnp_time_step(pnp_ctx* c, pnp_solve_stats* st);
 int pnp_step_count(const pnp_ctx* c, int64_t* k);
 /* Start a new trajectory: U_PREV and U_PREV2 <- U, step count <- 0. */
 int pnp_reset_history(pnp_ctx* c);
+
+/* ---------------------------------------------------------------- learned start -- */
+/* The library's addition to the paper (which has no learned component): a per-node
+ * network proposes the Newton start of pnp_time_step (start_mode PNP_START_LEARNED);
+ * plain Newton judges it -- the start with the smaller ||F|| of {learned, extrapolated
+ * 2 U^k - U^{k-1}} is used.
+ *
+ * Input (216 features per non-hanging node): the fields c+, c-, phi and the last-axis
+ * velocity component at t^k and t^{k-1}, sampled at the 3x3x3 lattice around the node
+ * with spacing equal to the finest element that has the node as a corner (points
+ * clamped to the domain; Q1 interpolation where a point is not a node); feature index
+ * ((step*4 + field)*27 + point), point index x fastest over offsets {-1,0,1}^3.
+ * Each (step, field) group is standardised with the training data's per-field mean and
+ * standard deviation.  Network: 216 -> 128 -> 128 -> 128 -> 3, GELU x Phi(x) after the
+ * hidden layers, BF16 weights and activations, FP32 accumulation on the tensor cores.
+ * Output: the standardised correction U^{k+1} - (2 U^k - U^{k-1}) per field.
+ * Parameters (FP32 master copy) are packed as W1[216][128], b1[128], W2[128][128], b2,
+ * W3[128][128], b3, W4[128][3], b4[3]: PNP_MLP_PARAMS floats.  3D meshes only. */
+#define PNP_MLP_PARAMS 61187
+
+typedef struct pnp_train_cfg {
+  int32_t steps;       /* Adam steps */
+  int32_t batch;       /* samples (node, time) per step, <= 65536 */
+  double lr;           /* Adam learning rate (1e-3) */
+  double beta1, beta2, adam_eps; /* 0.9, 0.999, 1e-8 */
+  uint64_t seed;       /* sampling seed */
+} pnp_train_cfg;
+
+typedef struct pnp_train_stats {
+  double loss_first;   /* mean-squared error (standardised units) of the first batch */
+  double loss_last;    /* ... of the last batch */
+  double wall_ms;
+  int64_t samples;     /* (node, time) pairs available */
+  int32_t steps;
+  int32_t pad_;
+} pnp_train_stats;
+
+/* Allocate the network of a context: He-normal weights from seed, zero biases, Adam
+ * state cleared, identity standardisation; builds the stencil tables of the mesh. */
+int pnp_mlp_init(pnp_ctx* c, uint64_t seed);
+/* Host FP32 parameters in the packed order, n = PNP_MLP_PARAMS. */
+int pnp_mlp_set_weights(pnp_ctx* c, const float* params, int64_t n);
+int pnp_mlp_get_weights(pnp_ctx* c, float* params, int64_t n);
+/* Standardisation (host arrays): input mean/std per field (c+, c-, phi, u) [4] each,
+ * output mean/std per field [3] each. */
+int pnp_mlp_set_normalization(pnp_ctx* c, const double* in_mean, const double* in_std, const double* out_mean,
+                              const double* out_std);
+int pnp_mlp_get_normalization(pnp_ctx* c, double* in_mean, double* in_std, double* out_mean, double* out_std);
+/* Append a trajectory produced by the solver: states device FP64 [T][n_nodes][3]
+ * (consecutive time levels, T >= 3), uz device FP64 [T][n_nodes] or NULL (zero).
+ * The data are copied. */
+int pnp_mlp_add_trajectory(pnp_ctx* c, const double* states, int64_t T, const double* uz);
+int pnp_mlp_clear_data(pnp_ctx* c);
+/* Train with Adam on the appended trajectories (standardisation computed from them
+ * first).  Marks the network as trained. */
+int pnp_mlp_train(pnp_ctx* c, const pnp_train_cfg* cfg, pnp_train_stats* st);
+/* Raw (unstandardised) features of every non-hanging node, node order: device FP64
+ * [n_free][216]; nodes: device int32 [n_free] (may be NULL).  n_free is the number of
+ * non-hanging nodes. */
+int pnp_mlp_features(pnp_ctx* c, const double* Uk, const double* Ukm1, const double* uz_k, const double* uz_km1,
+                     double* X, int32_t* nodes);
+/* Network output for B standardised input rows: X device FP32 [B][216] (rounded to
+ * BF16 inside), Y device FP32 [B][3]. */
+int pnp_mlp_forward(pnp_ctx* c, const float* X, int64_t B, float* Y);
+/* Mean-squared-error loss and its gradient with respect to the packed parameters for
+ * B rows: X device FP32 [B][216], Yt device FP32 [B][3], grad device FP32
+ * [PNP_MLP_PARAMS]; *loss on the host.  B <= 65536. */
+int pnp_mlp_loss_grad(pnp_ctx* c, const float* X, const float* Yt, int64_t B, float* grad, double* loss);
 
 /* ---------------------------------------------------------------- profiling ------ */
 /* Kernel classes timed with CUDA events recorded on the context's stream around each

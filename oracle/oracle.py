@@ -53,6 +53,7 @@ def lib():
         L.ora_qp_eval.argtypes = [vp, vp, C.c_int64, C.c_int, dp, dp, dp, dp, dp]
         L.ora_bc_rows.argtypes = [vp, vp, i32p, dp]
         L.ora_mms.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int64, dp, dp, dp]
+        L.ora_eval_points.argtypes = [vp, dp, C.c_int64, i64p, dp]
         _lib = L
     return _lib
 
@@ -198,6 +199,22 @@ class OracleMesh:
                      _p(v, C.c_double), _p(V, C.c_double), _p(JV, C.c_double))
         return JV
 
+    def eval_points(self, U, pts):
+        """Q1 field U [n_nodes, 3] at integer points pts [k, dim] -> [k, 3]."""
+        U = self._z(U)
+        pts = np.ascontiguousarray(pts, dtype=np.int64)
+        out = np.zeros((pts.shape[0], 3))
+        lib().ora_eval_points(self.h, _p(U, C.c_double), pts.shape[0], _p(pts, C.c_int64), _p(out, C.c_double))
+        return out
+
+    def node_sizes(self, levels):
+        """Edge (integer units) of the finest element having each node as a corner."""
+        s_el = (1 << self.max_level) >> np.asarray(levels, np.int64)
+        hmin = np.full(self.n_nodes, 1 << self.max_level, np.int64)
+        for c in range(self.el_nodes.shape[1]):
+            np.minimum.at(hmin, self.el_nodes[:, c], s_el)
+        return hmin
+
     def qp_eval(self, p: Params, e: int, q: int, U, Uk=None, Ukm1=None, adv=None):
         U = self._z(U); Uk = self._z(Uk); Ukm1 = self._z(Ukm1); v = self._vel3(adv)
         out = np.zeros(3)
@@ -298,6 +315,41 @@ def mms_run(octants, eps: float, dt: float, n_steps: int, steady: bool = False, 
         v_prev, v_cur = v_cur, exact(t_new)[1]
         t = t_new
     return mesh, U_cur, exact(t)[0], t
+
+
+def stencil_offsets(dim: int = 3):
+    """The 27 (9 in 2D) lattice offsets in {-1,0,1}^dim, x fastest."""
+    r = [-1, 0, 1]
+    if dim == 3:
+        return np.array([(x, y, z) for z in r for y in r for x in r], np.int64)
+    return np.array([(x, y) for y in r for x in r], np.int64)
+
+
+def stencil_features(mesh: OracleMesh, levels, Uk, Ukm1, uz_k=None, uz_km1=None):
+    """Raw network inputs of every non-hanging node: the fields (c+, c-, phi, u_z) of the
+    last two time levels at the 3x3x3 lattice around the node with spacing equal to the
+    finest incident element, points clamped to the domain, values of the Q1 fields there.
+    Returns (node ids, features [n, 216]) with feature index ((step*4 + field)*27 + point),
+    step 0 = U^k, step 1 = U^{k-1}.
+    """
+    nodes = np.nonzero(mesh.hanging == 0)[0]
+    hmin = mesh.node_sizes(levels)
+    off = stencil_offsets(mesh.dim)
+    npt = off.shape[0]
+    size = 1 << mesh.max_level
+    pts = mesh.ijk[nodes][:, None, :] + hmin[nodes][:, None, None] * off[None, :, :]
+    pts = np.clip(pts, 0, size).reshape(-1, mesh.dim)
+    feats = np.zeros((nodes.size, 8 * npt))
+    zero = np.zeros(mesh.n_nodes)
+    for step, (U, uz) in enumerate(((Uk, uz_k), (Ukm1, uz_km1))):
+        vals = mesh.eval_points(U, pts).reshape(nodes.size, npt, 3)
+        U4 = np.zeros((mesh.n_nodes, 3))
+        U4[:, 0] = zero if uz is None else uz
+        vz = mesh.eval_points(U4, pts).reshape(nodes.size, npt, 3)[:, :, 0]
+        for f in range(3):
+            feats[:, (step * 4 + f) * npt:(step * 4 + f + 1) * npt] = vals[:, :, f]
+        feats[:, (step * 4 + 3) * npt:(step * 4 + 4) * npt] = vz
+    return nodes, feats
 
 
 def l2_error(mesh: OracleMesh, U, Uex):

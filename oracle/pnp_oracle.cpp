@@ -770,6 +770,44 @@ void ora_qp_eval(void* h, const Params* p, int64_t e, int q, const double* U, co
   out[2] = S.tau;
 }
 
+// Values of the Q1 field U (node-major [nn][3]) at integer points pts [npts][dim]
+// (units of 2^-max_level, inside the closed domain): the point is located in a leaf by
+// trying every level from the root down, then the element's trilinear interpolant (with
+// hanging corners expressed through their constraints) is evaluated.
+void ora_eval_points(void* h, const double* U, int64_t npts, const int64_t* pts, double* out) {
+  const Mesh& m = *static_cast<Mesh*>(h);
+  std::map<std::pair<IPt, int>, int64_t> leaf;
+  for (size_t e = 0; e < m.el_anchor.size(); ++e) leaf[{m.el_anchor[e], m.el_level[e]}] = (int64_t)e;
+  const int64_t size = int64_t(1) << m.L;
+  const int nc = corner_count(m.dim);
+  for (int64_t i = 0; i < npts; ++i) {
+    IPt p = {0, 0, 0};
+    for (int k = 0; k < m.dim; ++k) p[k] = pts[i * m.dim + k];
+    int64_t e = -1;
+    for (int l = 0; l <= m.L && e < 0; ++l) {
+      const int64_t s = int64_t(1) << (m.L - l);
+      IPt a = {0, 0, 0};
+      for (int k = 0; k < m.dim; ++k) a[k] = std::min((p[k] / s) * s, size - s);
+      auto it = leaf.find({a, l});
+      if (it != leaf.end()) e = it->second;
+    }
+    for (int f = 0; f < 3; ++f) out[3 * i + f] = std::nan("");
+    if (e < 0) continue;
+    const int64_t s = int64_t(1) << (m.L - m.el_level[e]);
+    double val[3] = {0, 0, 0};
+    for (int c = 0; c < nc; ++c) {
+      double N = 1.0;
+      for (int k = 0; k < m.dim; ++k) {
+        const double t = (double)(p[k] - m.el_anchor[e][k]) / (double)s;  // in [0, 1]
+        N *= ((c >> k) & 1) ? t : 1.0 - t;
+      }
+      for (auto& pw : m.cons[m.el_nodes[e][c]])
+        for (int f = 0; f < 3; ++f) val[f] += N * pw.second * U[3 * pw.first + f];
+    }
+    for (int f = 0; f < 3; ++f) out[3 * i + f] = val[f];
+  }
+}
+
 // Row kinds [nn][3] (0 = PDE row, 1 = Dirichlet, 2 = hanging) and Dirichlet values.
 void ora_bc_rows(void* h, const Params* p, int32_t* kind, double* g) {
   const Mesh& m = *static_cast<Mesh*>(h);

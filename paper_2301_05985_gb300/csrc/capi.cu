@@ -1,7 +1,9 @@
 // capi.cu -- the extern "C" entry points declared in include/pnp.h: argument checks,
 // handle management, uploads and field copies.  Work runs on the context's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -116,6 +118,20 @@ int pnp_mesh_hanging(const pnp_mesh* m, uint8_t* flags) {
   return PNP_OK;
 }
 
+int pnp_mesh_patch_stats(const pnp_mesh* m, int64_t* stats) {
+  if (!m || !stats) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_patch_stats: null argument");
+  PatchData P;
+  if (int rc = pnp_build_patches(*m, 256, 640, P)) return rc;
+  stats[0] = P.n_patches;
+  stats[1] = P.max_nodes;
+  stats[2] = P.max_colors;
+  stats[3] = (int64_t)P.bnode.size();
+  stats[4] = P.n_partials;
+  stats[5] = (int64_t)P.pnode.size();
+  stats[6] = pnp_check_patches(*m, P);
+  return PNP_OK;
+}
+
 int pnp_mesh_elements(const pnp_mesh* m, int32_t* anchors, uint8_t* levels) {
   if (!m) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_elements: null mesh");
   if (anchors) std::memcpy(anchors, m->el_anchor.data(), m->el_anchor.size() * sizeof(int32_t));
@@ -145,6 +161,10 @@ static void free_ctx_memory(pnp_ctx* c) {
                   c->dflag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (void* p : c->pt_alloc) cudaFree(p);
+  c->pt_alloc.clear();
+  if (c->part64) cudaFree(c->part64);
+  if (c->part32) cudaFree(c->part32);
   if (c->hpin) cudaFreeHost(c->hpin);
 }
 
@@ -232,6 +252,53 @@ int pnp_ctx_create(const pnp_mesh* m, const pnp_params* p, void* stream, pnp_ctx
     return fail(PNP_ERR_CUDA);
   }
   if (int rc = ctx_alloc_krylov(c, p->gmres_restart)) return fail(rc);
+  try {
+    c->host_mesh = *m;
+  } catch (const std::bad_alloc&) {
+    pnp_set_error("pnp_ctx_create: out of host memory");
+    return fail(PNP_ERR_NOMEM);
+  }
+  {
+    const char* ep = getenv("PNP_ELEMENT_PATH");  // "atomic": scatter with global atomics instead
+    c->use_patches = !(ep && std::strcmp(ep, "atomic") == 0);
+  }
+  if (c->use_patches) {
+    PatchData P;
+    if (int rc = pnp_build_patches(*m, 256, 640, P)) return fail(rc);
+    DevPatches& d = c->pt;
+    d.n_patches = P.n_patches;
+    d.n_bnodes = (int64_t)P.bnode.size();
+    d.n_partials = P.n_partials;
+    d.max_nodes = P.max_nodes;
+    auto upload = [&](const void* src, size_t bytes) -> void* {
+      void* ptr = nullptr;
+      if (e != cudaSuccess) return nullptr;
+      e = cudaMalloc(&ptr, bytes > 0 ? bytes : 16);
+      if (e != cudaSuccess) return nullptr;
+      c->pt_alloc.push_back(ptr);
+      if (bytes) e = cudaMemcpyAsync(ptr, src, bytes, cudaMemcpyHostToDevice, s);
+      return ptr;
+    };
+    d.patch_e0 = (const int32_t*)upload(P.patch_e0.data(), 4 * P.patch_e0.size());
+    d.patch_n0 = (const int32_t*)upload(P.patch_n0.data(), 4 * P.patch_n0.size());
+    d.patch_h0 = (const int32_t*)upload(P.patch_h0.data(), 4 * P.patch_h0.size());
+    d.patch_ncol = (const uint8_t*)upload(P.patch_ncol.data(), P.patch_ncol.size());
+    d.pnode = (const int32_t*)upload(P.pnode.data(), 4 * P.pnode.size());
+    d.pbslot = (const int32_t*)upload(P.pbslot.data(), 4 * P.pbslot.size());
+    d.el_slot = (const uint16_t*)upload(P.el_slot.data(), 2 * P.el_slot.size());
+    d.el_color = (const uint8_t*)upload(P.el_color.data(), P.el_color.size());
+    d.hc_np = (const uint8_t*)upload(P.hc_np.data(), P.hc_np.size());
+    d.hc_par = (const uint16_t*)upload(P.hc_par.data(), 2 * P.hc_par.size());
+    d.bnode = (const int32_t*)upload(P.bnode.data(), 4 * P.bnode.size());
+    d.bptr = (const int32_t*)upload(P.bptr.data(), 4 * P.bptr.size());
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->part64, sizeof(double) * 3 * std::max<int64_t>(1, P.n_partials));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->part32, sizeof(float) * 3 * std::max<int64_t>(1, P.n_partials));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      pnp_set_error("pnp_ctx_create: patch upload failed: %s", cudaGetErrorString(e));
+      return fail(e == cudaErrorMemoryAllocation ? PNP_ERR_NOMEM : PNP_ERR_CUDA);
+    }
+  }
   *out = c;
   return PNP_OK;
 }

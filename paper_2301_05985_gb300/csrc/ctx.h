@@ -22,6 +22,13 @@ struct pnp_ctx {
   int32_t* d_hpar = nullptr;
   uint8_t* d_hnp = nullptr;
 
+  // Morton patches for the shared-memory element kernels (device), their partial buffers
+  bool use_patches = true;
+  DevPatches pt;
+  std::vector<void*> pt_alloc;
+  double* part64 = nullptr;
+  float* part32 = nullptr;
+
   // fields, FP64, [N][3]
   double *U = nullptr, *Uk = nullptr, *Ukm1 = nullptr;
   double *adv = nullptr, *vel = nullptr, *vel_prev = nullptr;
@@ -46,8 +53,9 @@ struct pnp_ctx {
   // statistics of the last solve (for the time stepper)
   int jv_count = 0, res_count = 0;
 
-  // learned start (optional)
+  // learned start (optional) and the host copy of the mesh it needs for point location
   struct Mlp* mlp = nullptr;
+  pnp_mesh host_mesh;
 
   // profiling: event pairs per kernel class, resolved on read
   bool prof_on = false;

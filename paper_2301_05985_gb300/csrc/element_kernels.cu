@@ -74,15 +74,14 @@ __device__ __forceinline__ void scatter(const ElemArgs<T>& A, const int32_t (&co
   }
 }
 
+// Element vector (3 fields x 2^D corners) of the residual (JV = false) or of J V (JV =
+// true) from nodal values u (U), va (advection), hs (history), du (direction), all
+// [field][corner]; the inputs are overwritten by their modal coefficients.
 template <typename T, int D, bool JV>
-__global__ void __launch_bounds__(128) k_element(ElemArgs<T> A) {
+__device__ __forceinline__ void element_compute(T (&u)[3][1 << D], T (&va)[3][1 << D], T (&hs)[2][1 << D],
+                                                T (&du)[3][1 << D], int lev, const PhysParams& Pp,
+                                                T (&acc)[3][1 << D]) {
   constexpr int NC = 1 << D;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= A.n_elem) return;
-  int32_t conn[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) conn[c] = __ldg(A.conn + e * NC + c);
-  const int lev = A.level[e];
   const T h = T(ldexp(1.0, -lev));
   const T inv_h = T(ldexp(1.0, lev));
   const T Gs = T(2.0 / kGauss) * inv_h;     // 2 / (h g)
@@ -90,27 +89,19 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs<T> A) {
   T w = T(1);
 #pragma unroll
   for (int k = 0; k < D; ++k) w *= T(0.5) * h;
-  const T kappa = T(A.P.kappa);
-  const T tau0 = T(A.P.tau_t) + T(A.P.C_I * D) * G2 * G2;
-  const T e2 = T(A.P.eps2x2);
-
-  T u[3][NC], va[3][NC], hs[2][NC];
-  gather<T, 3, NC>(A, conn, A.U, 3, u);
-  gather<T, 3, NC>(A, conn, A.adv, 3, va);
-  gather<T, 2, NC>(A, conn, A.hs, 2, hs);
+  const T kappa = T(Pp.kappa);
+  const T tau0 = T(Pp.tau_t) + T(Pp.C_I * D) * G2 * G2;
+  const T e2 = T(Pp.eps2x2);
 #pragma unroll
   for (int f = 0; f < 3; ++f) to_modal<T, D>(u[f]);
 #pragma unroll
   for (int f = 0; f < D; ++f) to_modal<T, D>(va[f]);
 #pragma unroll
   for (int f = 0; f < 2; ++f) to_modal<T, D>(hs[f]);
-  T du[3][NC];
   if constexpr (JV) {
-    gather<T, 3, NC>(A, conn, A.V, 3, du);
 #pragma unroll
     for (int f = 0; f < 3; ++f) to_modal<T, D>(du[f]);
   }
-  T acc[3][NC];
 #pragma unroll
   for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -199,7 +190,170 @@ __global__ void __launch_bounds__(128) k_element(ElemArgs<T> A) {
   });
 #pragma unroll
   for (int f = 0; f < 3; ++f) from_modal<T, D>(acc[f], w);
+}
+
+template <typename T, int D, bool JV>
+__global__ void __launch_bounds__(128) k_element(ElemArgs<T> A) {
+  constexpr int NC = 1 << D;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= A.n_elem) return;
+  int32_t conn[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) conn[c] = __ldg(A.conn + e * NC + c);
+  T u[3][NC], va[3][NC], hs[2][NC], du[3][NC], acc[3][NC];
+  gather<T, 3, NC>(A, conn, A.U, 3, u);
+  gather<T, 3, NC>(A, conn, A.adv, 3, va);
+  gather<T, 2, NC>(A, conn, A.hs, 2, hs);
+  if constexpr (JV) gather<T, 3, NC>(A, conn, A.V, 3, du);
+  element_compute<T, D, JV>(u, va, hs, du, A.level[e], A.P, acc);
   scatter<T, NC>(A, conn, acc);
+}
+
+// ------------------------------------------------------------------ patch kernels
+// One CTA per Morton patch of up to kPatchElems elements: the patch's target nodes are
+// staged in shared memory (one coalesced-by-slot pass over the node data), each thread
+// computes one element from shared memory, contributions are added colour by colour into
+// shared-memory accumulators (elements of one colour share no node: no atomics, fixed
+// order), then owned rows are written with the Dirichlet rows applied and shared rows go
+// to a partial buffer summed by k_patch_finalize in patch order.  Deterministic.
+constexpr int kPatchElems = 256;
+
+template <typename T>
+__device__ __forceinline__ T dirichlet_row(const BcTable& bc, uint8_t fm, int f, bool jv, T acc, T u, T v) {
+  const unsigned msk = fm & bc.dir_faces[f] & 0x3F;
+  if (!msk) return acc;
+  return jv ? v : T(double(u) - bc.val[31 - __clz(msk)][f]);
+}
+
+template <typename T, int D, bool JV>
+__global__ void __launch_bounds__(kPatchElems) k_patch(PatchArgs<T> A) {
+  constexpr int NC = 1 << D;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int PN = A.pt.max_nodes;
+  T* sU = reinterpret_cast<T*>(smem_raw);
+  T* sA = sU + 3 * PN;
+  T* sH = sA + 3 * PN;
+  T* acc = sH + 2 * PN;
+  T* sV = acc + 3 * PN;  // JV only
+  const int p = blockIdx.x;
+  const int n0 = A.pt.patch_n0[p], nn = A.pt.patch_n0[p + 1] - n0;
+  const int e0 = A.pt.patch_e0[p], ne = A.pt.patch_e0[p + 1] - e0;
+  const int h0 = A.pt.patch_h0[p];
+  for (int s = threadIdx.x; s < nn; s += blockDim.x) {
+    const int64_t id = A.pt.pnode[n0 + s];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      sU[f * PN + s] = A.U[3 * id + f];
+      sA[f * PN + s] = A.adv[3 * id + f];
+      acc[f * PN + s] = T(0);
+      if constexpr (JV) sV[f * PN + s] = A.V[3 * id + f];
+    }
+    sH[s] = A.hs[2 * id];
+    sH[PN + s] = A.hs[2 * id + 1];
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  int color = -1;
+  uint16_t slot[NC];
+  T r[3][NC];
+  if (t < ne) {
+    const int64_t e = e0 + t;
+    color = A.pt.el_color[e];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) slot[c] = A.pt.el_slot[e * NC + c];
+    T u[3][NC], va[3][NC], hs[2][NC], du[3][NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const uint16_t sl = slot[c];
+      if (!(sl & 0x8000)) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          u[f][c] = sU[f * PN + sl];
+          va[f][c] = sA[f * PN + sl];
+          if constexpr (JV) du[f][c] = sV[f * PN + sl];
+        }
+        hs[0][c] = sH[sl];
+        hs[1][c] = sH[PN + sl];
+      } else {
+        const int hc = h0 + (sl & 0x7FFF);
+        const int np = A.pt.hc_np[hc];
+        const T wgt = np == 2 ? T(0.5) : T(0.25);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          u[f][c] = T(0);
+          va[f][c] = T(0);
+          du[f][c] = T(0);
+        }
+        hs[0][c] = T(0);
+        hs[1][c] = T(0);
+        for (int q = 0; q < np; ++q) {
+          const int ps = A.pt.hc_par[4 * hc + q];
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            u[f][c] += wgt * sU[f * PN + ps];
+            va[f][c] += wgt * sA[f * PN + ps];
+            if constexpr (JV) du[f][c] += wgt * sV[f * PN + ps];
+          }
+          hs[0][c] += wgt * sH[ps];
+          hs[1][c] += wgt * sH[PN + ps];
+        }
+      }
+    }
+    element_compute<T, D, JV>(u, va, hs, du, A.level[e], A.P, r);
+  }
+  const int ncol = A.pt.patch_ncol[p];
+  for (int col = 0; col < ncol; ++col) {
+    if (color == col) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const uint16_t sl = slot[c];
+        if (!(sl & 0x8000)) {
+#pragma unroll
+          for (int f = 0; f < 3; ++f) acc[f * PN + sl] += r[f][c];
+        } else {
+          const int hc = h0 + (sl & 0x7FFF);
+          const int np = A.pt.hc_np[hc];
+          const T wgt = np == 2 ? T(0.5) : T(0.25);
+          for (int q = 0; q < np; ++q) {
+            const int ps = A.pt.hc_par[4 * hc + q];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) acc[f * PN + ps] += wgt * r[f][c];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int s = threadIdx.x; s < nn; s += blockDim.x) {
+    const int64_t id = A.pt.pnode[n0 + s];
+    const int32_t q = A.pt.pbslot[n0 + s];
+    if (q < 0) {
+      const uint8_t fm = A.faces[id];
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+        A.out[3 * id + f] = dirichlet_row<T>(A.bc, fm, f, JV, acc[f * PN + s], sU[f * PN + s],
+                                             JV ? sV[f * PN + s] : T(0));
+    } else {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) A.partial[3 * (int64_t)q + f] = acc[f * PN + s];
+    }
+  }
+}
+
+// shared nodes: sum their partials in patch order, then apply the Dirichlet rows
+template <typename T>
+__global__ void k_patch_finalize(PatchArgs<T> A, bool jv) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= A.pt.n_bnodes) return;
+  const int64_t id = A.pt.bnode[b];
+  T v[3] = {T(0), T(0), T(0)};
+  for (int32_t q = A.pt.bptr[b]; q < A.pt.bptr[b + 1]; ++q)
+#pragma unroll
+    for (int f = 0; f < 3; ++f) v[f] += A.partial[3 * (int64_t)q + f];
+  const uint8_t fm = A.faces[id];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+    A.out[3 * id + f] = dirichlet_row<T>(A.bc, fm, f, jv, v[f], A.U[3 * id + f], jv ? A.V[3 * id + f] : T(0));
 }
 
 // ------------------------------------------------------------------ block diagonal
@@ -457,6 +611,22 @@ cudaError_t launch_element(int dim, bool jv, const ElemArgs<T>& A, cudaStream_t 
 }
 template cudaError_t launch_element<double>(int, bool, const ElemArgs<double>&, cudaStream_t);
 template cudaError_t launch_element<float>(int, bool, const ElemArgs<float>&, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_patch(int dim, bool jv, const PatchArgs<T>& A, cudaStream_t s) {
+  if (A.pt.n_patches == 0) return cudaSuccess;
+  const size_t smem = (size_t)(jv ? 14 : 11) * A.pt.max_nodes * sizeof(T);
+  void (*kern)(PatchArgs<T>);
+  if (dim == 2) kern = jv ? k_patch<T, 2, true> : k_patch<T, 2, false>;
+  else kern = jv ? k_patch<T, 3, true> : k_patch<T, 3, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)A.pt.n_patches, kPatchElems, smem, s>>>(A); note_launch();
+  if (A.pt.n_bnodes) { k_patch_finalize<T><<<nblk(A.pt.n_bnodes, 256), 256, 0, s>>>(A, jv); note_launch(); }
+  return cudaGetLastError();
+}
+template cudaError_t launch_patch<double>(int, bool, const PatchArgs<double>&, cudaStream_t);
+template cudaError_t launch_patch<float>(int, bool, const PatchArgs<float>&, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_block_diag(int dim, const ElemArgs<T>& A, T* Dout, cudaStream_t s) {

@@ -1,6 +1,7 @@
 // kernels.h -- launch interfaces of the library's CUDA kernels.
 #pragma once
 
+#include "patches.h"
 #include "pnp_internal.h"
 
 // Arguments of the fused element kernels (residual / Jv / block diagonal).
@@ -31,6 +32,24 @@ struct RowArgs {
 
 // Counts every kernel the library launches (read by pnp_kernel_launches).
 void note_launch();
+
+// Arguments of the shared-memory patch kernels (residual / Jv over Morton patches).
+template <typename T>
+struct PatchArgs {
+  DevPatches pt;
+  const uint8_t* level;    // [E]
+  const uint8_t* faces;    // [N]
+  BcTable bc;
+  const T* U;              // [N][3]
+  const T* V;              // [N][3] (Jv)
+  const T* hs;             // [N][2]
+  const T* adv;            // [N][3]
+  T* out;                  // [N][3]: every non-hanging row written (no zeroing needed)
+  T* partial;              // [n_partials][3]
+  PhysParams P;
+};
+template <typename T>
+cudaError_t launch_patch(int dim, bool jv, const PatchArgs<T>& A, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_element(int dim, bool jv, const ElemArgs<T>& A, cudaStream_t s);

@@ -78,6 +78,8 @@ void radix_sort_pairs(std::vector<uint64_t>& key, std::vector<uint32_t>& val) {
 
 }  // namespace
 
+uint64_t pnp_morton(int dim, const int64_t* p) { return morton(dim, p); }
+
 int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels) {
   if (dim != 2 && dim != 3) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_create: dim must be 2 or 3 (got %d)", dim);
   if (L < 0 || L > 16) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_create: max_level must be in 0..16 (got %d)", L);

@@ -37,6 +37,8 @@ struct pnp_mesh {
 };
 
 int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels);
+// Morton (Z-order) key of an integer point (x in bit 0 of each group, then y, then z).
+uint64_t pnp_morton(int dim, const int64_t* p);
 
 // ------------------------------------------------------------------ device views
 struct DevMesh {

@@ -56,24 +56,67 @@ int ctx_prepare_history(pnp_ctx* c) {
   return PNP_OK;
 }
 
+template <typename T>
+static PatchArgs<T> patch_args(const pnp_ctx* c, const T* U, const T* V, const T* hs, const T* adv, T* out,
+                               T* partial) {
+  PatchArgs<T> A;
+  A.pt = c->pt;
+  A.level = c->d_level;
+  A.faces = c->d_faces;
+  A.bc = c->bc_table();
+  A.U = U;
+  A.V = V;
+  A.hs = hs;
+  A.adv = adv;
+  A.out = out;
+  A.partial = partial;
+  A.P = c->phys();
+  return A;
+}
+
+// hanging rows only (the patch kernels write every other row, Dirichlet rows included)
+template <typename T>
+static int hanging_rows(pnp_ctx* c, const T* in, T* out) {
+  RowArgs R = c->rows();
+  R.n_nodes = 0;
+  return ctx_check(c, launch_row_fixups<T>(R, in, out, 0, c->stream), "hanging rows");
+}
+
 int ctx_residual(pnp_ctx* c, const double* U, double* F) {
-  CK(cudaMemsetAsync(F, 0, sizeof(double) * c->n3(), c->stream));
-  {
-    ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes());
-    CK(launch_element<double>(c->dim, false, elem_args<double>(c, U, nullptr, c->hs, c->adv, F), c->stream));
+  if (c->use_patches) {
+    {
+      ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes());
+      CK(launch_patch<double>(c->dim, false, patch_args<double>(c, U, nullptr, c->hs, c->adv, F, c->part64),
+                              c->stream));
+    }
+    RC(hanging_rows<double>(c, U, F));
+  } else {
+    CK(cudaMemsetAsync(F, 0, sizeof(double) * c->n3(), c->stream));
+    {
+      ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes());
+      CK(launch_element<double>(c->dim, false, elem_args<double>(c, U, nullptr, c->hs, c->adv, F), c->stream));
+    }
+    CK(launch_row_fixups<double>(c->rows(), U, F, 0, c->stream));
   }
-  CK(launch_row_fixups<double>(c->rows(), U, F, 0, c->stream));
   c->res_count++;
   return PNP_OK;
 }
 
 int ctx_jv64(pnp_ctx* c, const double* U, const double* V, double* JV) {
-  CK(cudaMemsetAsync(JV, 0, sizeof(double) * c->n3(), c->stream));
-  {
-    ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes());
-    CK(launch_element<double>(c->dim, true, elem_args<double>(c, U, V, c->hs, c->adv, JV), c->stream));
+  if (c->use_patches) {
+    {
+      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes());
+      CK(launch_patch<double>(c->dim, true, patch_args<double>(c, U, V, c->hs, c->adv, JV, c->part64), c->stream));
+    }
+    RC(hanging_rows<double>(c, V, JV));
+  } else {
+    CK(cudaMemsetAsync(JV, 0, sizeof(double) * c->n3(), c->stream));
+    {
+      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes());
+      CK(launch_element<double>(c->dim, true, elem_args<double>(c, U, V, c->hs, c->adv, JV), c->stream));
+    }
+    CK(launch_row_fixups<double>(c->rows(), V, JV, 1, c->stream));
   }
-  CK(launch_row_fixups<double>(c->rows(), V, JV, 1, c->stream));
   c->jv_count++;
   return PNP_OK;
 }
@@ -86,12 +129,21 @@ int ctx_prepare_f32(pnp_ctx* c, const double* U) {
 }
 
 int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32) {
-  CK(cudaMemsetAsync(JV32, 0, sizeof(float) * c->n3(), c->stream));
-  {
-    ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes());
-    CK(launch_element<float>(c->dim, true, elem_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32), c->stream));
+  if (c->use_patches) {
+    {
+      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes());
+      CK(launch_patch<float>(c->dim, true, patch_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32, c->part32),
+                             c->stream));
+    }
+    RC(hanging_rows<float>(c, V32, JV32));
+  } else {
+    CK(cudaMemsetAsync(JV32, 0, sizeof(float) * c->n3(), c->stream));
+    {
+      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes());
+      CK(launch_element<float>(c->dim, true, elem_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32), c->stream));
+    }
+    CK(launch_row_fixups<float>(c->rows(), V32, JV32, 1, c->stream));
   }
-  CK(launch_row_fixups<float>(c->rows(), V32, JV32, 1, c->stream));
   c->jv_count++;
   return PNP_OK;
 }

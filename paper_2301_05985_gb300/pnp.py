@@ -63,6 +63,21 @@ class pnp_solve_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pnp_train_cfg(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("adam_eps", C.c_double), ("seed", C.c_uint64)]
+
+
+class pnp_train_stats(C.Structure):
+    _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double), ("wall_ms", C.c_double),
+                ("samples", C.c_int64), ("steps", C.c_int32), ("pad_", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+PNP_MLP_PARAMS = 61187
+
 _lib = None
 _vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
 _P = C.POINTER
@@ -78,6 +93,7 @@ SIGNATURES = {
     "pnp_mesh_node_coords": (C.c_int, [_vp, _vp]),
     "pnp_mesh_hanging": (C.c_int, [_vp, _vp]),
     "pnp_mesh_elements": (C.c_int, [_vp, _vp, _vp]),
+    "pnp_mesh_patch_stats": (C.c_int, [_vp, _vp]),
     "pnp_ctx_create": (C.c_int, [_vp, _P(pnp_params), _vp, _P(_vp)]),
     "pnp_ctx_destroy": (None, [_vp]),
     "pnp_set_params": (C.c_int, [_vp, _P(pnp_params)]),
@@ -97,6 +113,17 @@ SIGNATURES = {
     "pnp_profile_enable": (C.c_int, [_vp, C.c_int]),
     "pnp_profile_read": (C.c_int, [_vp, C.c_int, _P(_d), _P(_i64), _P(_d)]),
     "pnp_kernel_launches": (_i64, []),
+    "pnp_mlp_init": (C.c_int, [_vp, C.c_uint64]),
+    "pnp_mlp_set_weights": (C.c_int, [_vp, _vp, _i64]),
+    "pnp_mlp_get_weights": (C.c_int, [_vp, _vp, _i64]),
+    "pnp_mlp_set_normalization": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "pnp_mlp_get_normalization": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "pnp_mlp_add_trajectory": (C.c_int, [_vp, _vp, _i64, _vp]),
+    "pnp_mlp_clear_data": (C.c_int, [_vp]),
+    "pnp_mlp_train": (C.c_int, [_vp, _P(pnp_train_cfg), _P(pnp_train_stats)]),
+    "pnp_mlp_features": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pnp_mlp_forward": (C.c_int, [_vp, _vp, _i64, _vp]),
+    "pnp_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _P(_d)]),
 }
 
 PNP_PROF_RESIDUAL, PNP_PROF_JV64, PNP_PROF_JV32, PNP_PROF_BLOCKDIAG = 0, 1, 2, 3
@@ -177,6 +204,12 @@ class Mesh:
         hf = np.zeros(self.n_nodes, np.uint8)
         check(lib().pnp_mesh_hanging(h, hf.ctypes.data))
         self.hanging = hf.astype(bool)
+
+    def patch_stats(self) -> dict:
+        s = np.zeros(7, np.int64)
+        check(lib().pnp_mesh_patch_stats(self.h, s.ctypes.data))
+        keys = ["patches", "max_nodes", "max_colors", "shared_nodes", "partials", "slots", "violations"]
+        return dict(zip(keys, s.tolist()))
 
     def elements(self):
         a = np.zeros((self.n_elem, self.dim), np.int32)
@@ -310,6 +343,55 @@ class Context:
             check(lib().pnp_profile_read(self.h, k, C.byref(ms), C.byref(cnt), C.byref(by)))
             out[name] = {"ms": ms.value, "count": cnt.value, "alg_bytes": by.value}
         return out
+
+
+    # ---------------------------------------------------------------- learned start
+    def mlp_init(self, seed: int = 0):
+        check(lib().pnp_mlp_init(self.h, seed))
+
+    def mlp_set_weights(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        check(lib().pnp_mlp_set_weights(self.h, p.ctypes.data, p.size))
+
+    def mlp_get_weights(self) -> np.ndarray:
+        p = np.zeros(PNP_MLP_PARAMS, np.float32)
+        check(lib().pnp_mlp_get_weights(self.h, p.ctypes.data, p.size))
+        return p
+
+    def mlp_set_normalization(self, in_mean, in_std, out_mean, out_std):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (in_mean, in_std, out_mean, out_std)]
+        check(lib().pnp_mlp_set_normalization(self.h, *[a.ctypes.data for a in arrs]))
+
+    def mlp_get_normalization(self):
+        arrs = [np.zeros(4), np.zeros(4), np.zeros(3), np.zeros(3)]
+        check(lib().pnp_mlp_get_normalization(self.h, *[a.ctypes.data for a in arrs]))
+        return arrs
+
+    def mlp_add_trajectory(self, states, uz=None):
+        """states: device FP64 tensor [T, n_nodes, 3]; uz: device [T, n_nodes] or None."""
+        check(lib().pnp_mlp_add_trajectory(self.h, _ptr(states), int(states.shape[0]), _ptr(uz)))
+
+    def mlp_clear_data(self):
+        check(lib().pnp_mlp_clear_data(self.h))
+
+    def mlp_train(self, steps=2000, batch=4096, lr=1e-3, seed=0, beta1=0.9, beta2=0.999, adam_eps=1e-8):
+        cfg = pnp_train_cfg(steps, batch, lr, beta1, beta2, adam_eps, seed)
+        st = pnp_train_stats()
+        check(lib().pnp_mlp_train(self.h, C.byref(cfg), C.byref(st)))
+        return st
+
+    def mlp_features(self, Uk, Ukm1, uzk=None, uzkm1=None, X=None, nodes=None):
+        check(lib().pnp_mlp_features(self.h, _ptr(Uk), _ptr(Ukm1), _ptr(uzk), _ptr(uzkm1), _ptr(X), _ptr(nodes)))
+        return X, nodes
+
+    def mlp_forward(self, X, Y):
+        check(lib().pnp_mlp_forward(self.h, _ptr(X), int(X.shape[0]), _ptr(Y)))
+        return Y
+
+    def mlp_loss_grad(self, X, Yt, grad):
+        loss = C.c_double()
+        check(lib().pnp_mlp_loss_grad(self.h, _ptr(X), _ptr(Yt), int(X.shape[0]), _ptr(grad), C.byref(loss)))
+        return loss.value
 
 
 def kernel_launches() -> int:

@@ -58,8 +58,11 @@ def test_struct_layouts_match_header(pnp, tmp_path):
     """Field offsets of the ctypes mirrors equal those the C compiler gives the header."""
     p = pnp.default_params()
     assert p.C_I == 6.0 and p.gmres_restart == 30 and p.newton_rtol == 1e-8
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pnp.h"', 'int main(void){']
-    for cname, py in (("pnp_params", pnp.pnp_params), ("pnp_solve_stats", pnp.pnp_solve_stats)):
+    structs = (("pnp_params", pnp.pnp_params), ("pnp_solve_stats", pnp.pnp_solve_stats),
+               ("pnp_train_cfg", pnp.pnp_train_cfg), ("pnp_train_stats", pnp.pnp_train_stats))
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pnp.h"', 'int main(void){',
+             'printf("PNP_MLP_PARAMS size %d\\n", PNP_MLP_PARAMS);']
+    for cname, py in structs:
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:
             lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
@@ -74,7 +77,8 @@ def test_struct_layouts_match_header(pnp, tmp_path):
         if ln:
             s, f, v = ln.split()
             want[(s, f)] = int(v)
-    for cname, py in (("pnp_params", pnp.pnp_params), ("pnp_solve_stats", pnp.pnp_solve_stats)):
+    assert want[("PNP_MLP_PARAMS", "size")] == pnp.PNP_MLP_PARAMS
+    for cname, py in structs:
         assert C.sizeof(py) == want[(cname, "size")]
         for f, _ in py._fields_:
             assert getattr(py, f).offset == want[(cname, f)], (cname, f)
@@ -155,6 +159,18 @@ def test_mesh_builder_rejections(pnp):
     with pytest.raises(pnp.PnpError) as e:
         pnp.Mesh(W.Octants(4, 2, oc.anchors, oc.levels))
     assert e.value.code == pnp.PNP_ERR_ARG
+
+
+@pytest.mark.parametrize("dim,base,top,frac,seed", [(3, 1, 4, 0.3, 12), (3, 2, 4, 0.5, 5), (2, 2, 5, 0.3, 11),
+                                                     (3, 3, 3, 0.0, 0)])
+def test_patch_layout_invariants(pnp, dim, base, top, frac, seed):
+    """Morton patches of the shared-memory kernels: every element slot maps to its target
+    node, elements of one colour share no target, every non-hanging node is covered and
+    hanging nodes are not, and the partial-row count matches the shared coverage."""
+    oc = W.random_balanced_octants(dim, base, top, frac, seed)
+    s = pnp.Mesh(oc).patch_stats()
+    assert s["violations"] == 0, s
+    assert s["max_nodes"] <= 640 and s["max_colors"] <= 64
 
 
 def test_membrane_band_mesh_counts(pnp):

@@ -104,6 +104,24 @@ def test_residual_ignores_stored_hanging_values():
     assert np.allclose(F2[P.mesh.hanging] - F1[P.mesh.hanging], 5.0, atol=1e-12)
 
 
+@pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[CASES[1][0], CASES[3][0]])
+def test_patch_kernels_are_deterministic_and_match_atomic_path(case, monkeypatch):
+    """The shared-memory patch kernels (default) sum in a fixed order: two evaluations are
+    bitwise equal; they agree with the global-atomics kernels to rounding."""
+    P, U, V = _setup(case)
+    outs = [(P.gpu_residual(U), P.gpu_jv(U, V, 0), P.gpu_jv(U, V, 1)) for _ in range(2)]
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    monkeypatch.setenv("PNP_ELEMENT_PATH", "atomic")
+    name, oc, kw, bcs = case
+    Q = Pair(oc, kw, bcs)
+    Q.set_state(P.Uk, P.Ukm1, P.vel)
+    F, JV, JV32 = outs[0]
+    assert rel_err(Q.gpu_residual(U), F) <= 1e-14
+    assert rel_err(Q.gpu_jv(U, V, 0), JV) <= 1e-14
+    assert np.all(field_max_err(Q.gpu_jv(U, V, 1), JV32) <= 1e-5)
+
+
 def test_gmres_solves_oracle_system():
     import scipy.sparse.linalg as spla
     P, U, V = _setup(CASES[1], seed=9)

@@ -74,6 +74,39 @@ def test_adam_first_step_is_sign_times_lr():
         np.testing.assert_allclose(w0 - w1, 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-6, atol=1e-12)
 
 
+@pytest.mark.parametrize("dim,seed", [(3, 2), (3, 7), (2, 4)])
+def test_stencil_features_reproduce_linear_fields(dim, seed):
+    """Point evaluation of the Q1 fields is exact for globally linear fields (on meshes with
+    hanging nodes), the stencil spacing is the finest incident element, and points outside
+    the domain are clamped to it."""
+    import oracle as O
+    from paper_2301_05985_gb300 import workloads as W
+    oc = W.random_balanced_octants(dim, 1, 3 if dim == 3 else 4, 0.35, seed)
+    m = O.OracleMesh(oc)
+    a = np.array([[0.3, -1.2, 0.7], [1.1, 0.4, -0.9], [-0.5, 2.0, 0.25]])[:, :dim]
+    U = 0.1 + m.x @ a.T
+    uz = 0.2 - m.x[:, dim - 1]
+    bc = W.all_natural_bcs(dim)
+    p = O.Params(eps=0.1, steady=True, bc_type=bc.types, bc_val=bc.values)
+    U = m.make_consistent(U, p)
+    nodes, F = O.stencil_features(m, oc.levels, U, 2 * U, uz, -uz)
+    npt = 3**dim
+    hmin = m.node_sizes(oc.levels)
+    size = 1 << m.max_level
+    pts = np.clip(m.ijk[nodes][:, None, :] + hmin[nodes][:, None, None] * O.stencil_offsets(dim)[None], 0, size) / size
+    for f in range(3):
+        ref = 0.1 + pts @ a[f]
+        np.testing.assert_allclose(F[:, f * npt:(f + 1) * npt], ref, atol=1e-14)
+        np.testing.assert_allclose(F[:, (4 + f) * npt:(5 + f) * npt], 2 * ref, atol=1e-14)
+    np.testing.assert_allclose(F[:, 3 * npt:4 * npt], 0.2 - pts[:, :, dim - 1], atol=1e-14)
+    np.testing.assert_allclose(F[:, 7 * npt:8 * npt], -(0.2 - pts[:, :, dim - 1]), atol=1e-14)
+    # the centre point is the node itself
+    np.testing.assert_allclose(F[:, npt // 2], U[nodes, 0], atol=1e-15)
+    # stencil spacing is the finest incident element: a node shared by a finest-level element
+    finest = (1 << m.max_level) >> int(oc.levels.max())
+    assert hmin.min() == finest
+
+
 def test_bf16_rounding():
     x = np.array([1.0, 1.0 + 2**-8, 1.0 + 3 * 2**-9, -2.5, 3.0e-5])
     r = M.bf16_round(x)
