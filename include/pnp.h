@@ -185,6 +185,10 @@ int pnp_jv(pnp_ctx* c, const double* U, const void* V, void* JV, int precision);
 /* 3x3 diagonal blocks of J(U): D device FP64 [n][3][3] (row-major per node), exact
  * for the assembled operator including hanging-node coupling. */
 int pnp_block_diag(pnp_ctx* c, const double* U, double* D);
+/* ||x||_2 of a device FP64 vector of n entries, the reduction Newton and GMRES use
+ * (fixed grid, fixed summation order: bitwise reproducible); result on the host.
+ * x may be NULL when n == 0.  Uses the context's scratch and stream. */
+int pnp_norm2(pnp_ctx* c, const double* x, int64_t n, double* result);
 
 /* ---------------------------------------------------------------- solvers -------- */
 /* Solve J(U) x = b by right-preconditioned GMRES(m) (3x3 block-Jacobi preconditioner,

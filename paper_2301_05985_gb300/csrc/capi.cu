@@ -462,6 +462,21 @@ int pnp_block_diag(pnp_ctx* c, const double* U, double* D) {
   return PNP_OK;
 }
 
+int pnp_norm2(pnp_ctx* c, const double* x, int64_t n, double* result) {
+  CTX_GUARD(c);
+  if (!result || n < 0 || (!x && n > 0)) PNP_FAIL(PNP_ERR_ARG, "pnp_norm2: bad arguments");
+  if (n == 0) {
+    *result = 0.0;
+    return PNP_OK;
+  }
+  double* slot = c->dsc + 4 * (c->m_alloc + 2) + 9;
+  CK(launch_norm2(n, x, c->part, slot, c->stream));
+  CK(cudaMemcpyAsync(c->hpin + 1, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *result = c->hpin[1];
+  return PNP_OK;
+}
+
 int pnp_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int precision,
               pnp_solve_stats* st) {
   CTX_GUARD(c);

@@ -105,6 +105,7 @@ SIGNATURES = {
     "pnp_residual": (C.c_int, [_vp, _vp, _vp]),
     "pnp_jv": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int]),
     "pnp_block_diag": (C.c_int, [_vp, _vp, _vp]),
+    "pnp_norm2": (C.c_int, [_vp, _vp, _i64, _P(_d)]),
     "pnp_gmres": (C.c_int, [_vp, _vp, _vp, _vp, _d, C.c_int, _P(pnp_solve_stats)]),
     "pnp_newton_solve": (C.c_int, [_vp, _P(pnp_solve_stats)]),
     "pnp_time_step": (C.c_int, [_vp, _P(pnp_solve_stats)]),
@@ -303,6 +304,11 @@ class Context:
     def block_diag(self, U, D):
         check(lib().pnp_block_diag(self.h, _ptr(U), _ptr(D)))
         return D
+
+    def norm2(self, x) -> float:
+        r = C.c_double()
+        check(lib().pnp_norm2(self.h, _ptr(x), int(x.numel()), C.byref(r)))
+        return r.value
 
     def gmres(self, U, b, x, rtol: float, precision: int = PNP_F64, raise_on_error=True):
         st = pnp_solve_stats()

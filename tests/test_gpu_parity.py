@@ -122,6 +122,17 @@ def test_patch_kernels_are_deterministic_and_match_atomic_path(case, monkeypatch
     assert np.all(field_max_err(Q.gpu_jv(U, V, 1), JV32) <= 1e-5)
 
 
+def test_norm2_is_reproducible_and_accurate():
+    P, U, _ = _setup(CASES[2])
+    torch = P.torch
+    for n in (0, 1, 7, 1000, 3 * P.mesh.n_nodes, 2_000_003):
+        x = torch.from_numpy(np.random.default_rng(n).normal(size=n)).cuda()
+        a, b = P.ctx.norm2(x), P.ctx.norm2(x)
+        assert a == b
+        ref = float(np.linalg.norm(x.cpu().numpy()))
+        assert abs(a - ref) <= 1e-14 * max(ref, 1e-300) + (0 if n else 0.0)
+
+
 def test_gmres_solves_oracle_system():
     import scipy.sparse.linalg as spla
     P, U, V = _setup(CASES[1], seed=9)
