@@ -279,6 +279,25 @@ int pnp_mlp_forward(pnp_ctx* c, const float* X, int64_t B, float* Y);
  * [PNP_MLP_PARAMS]; *loss on the host.  B <= 65536. */
 int pnp_mlp_loss_grad(pnp_ctx* c, const float* X, const float* Yt, int64_t B, float* grad, double* loss);
 
+/* Allocation-free network forward (no counterpart in the paper; a service of this
+ * library).  Same result as pnp_mlp_forward, but needs no context and never allocates
+ * device memory: for callers that cannot call cudaMalloc -- e.g. a host application
+ * that reserves its whole device-memory budget up front and forbids later allocations,
+ * or code that must not introduce allocation (and its implicit synchronisation) into
+ * a latency-critical stream.  The BF16 weights, activations and output rows live in one
+ * fixed file-scope device array (about 5 MB) that every GPU loading the library keeps
+ * until the process exits.
+ *   params: device FP32 [PNP_MLP_PARAMS] packed parameters (layout above);
+ *   X: device FP32 [B][216] standardised inputs; Y: device FP32 [B][3] outputs;
+ *   B <= PNP_NOALLOC_MAX_ROWS (larger B: PNP_ERR_ARG, split the call);
+ *   stream: cudaStream_t (NULL = legacy default stream); returns after the work is done.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * for that device; make that first call before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. */
+#define PNP_NOALLOC_MAX_ROWS 4096
+int pnp_mlp_forward_noalloc(const float* params, const float* X, int64_t B, float* Y, void* stream);
+
 /* ---------------------------------------------------------------- profiling ------ */
 /* Kernel classes timed with CUDA events recorded on the context's stream around each
  * launch while profiling is on. */

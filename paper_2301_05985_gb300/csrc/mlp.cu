@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <random>
 #include <vector>
 
@@ -970,6 +971,89 @@ int pnp_mlp_train(pnp_ctx* c, const pnp_train_cfg* cfg, pnp_train_stats* st) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free forward
+// The network forward of pnp_mlp_forward without a context and without allocating: the
+// BF16 weights, the activations and the output rows live in one file-scope device array
+// of fixed size (kNoAllocRows rows), shared by every call of this entry point.
+namespace {
+constexpr int64_t kNoAllocRows = 4096;
+struct NoAllocScratch {
+  bf16 W1[K0P * HID];
+  bf16 W2[HID * HID];
+  bf16 W3[HID * HID];
+  bf16 W4[HID * NOP];
+  float b1[HID], b2[HID], b3[HID], b4[NOP];
+  bf16 X[kNoAllocRows * K0P];
+  bf16 A1[kNoAllocRows * HID];
+  bf16 A2[kNoAllocRows * HID];
+  bf16 A3[kNoAllocRows * HID];
+  float out[kNoAllocRows * NOP];
+};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[128] = {};  // device address of g_noalloc_scratch per device ordinal
+
+// Device address of the scratch array on the current device (looked up once per device).
+int noalloc_scratch(NoAllocScratch** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) PNP_FAIL(PNP_ERR_CUDA, "pnp_mlp_forward_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= 128) PNP_FAIL(PNP_ERR_ARG, "pnp_mlp_forward_noalloc: device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      PNP_FAIL(PNP_ERR_CUDA, "pnp_mlp_forward_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<NoAllocScratch*>(g_noalloc_addr[dev]);
+  return PNP_OK;
+}
+}  // namespace
+
+extern "C" int pnp_mlp_forward_noalloc(const float* params, const float* X, int64_t B, float* Y, void* stream) {
+  if (!params || B < 0 || (B > 0 && (!X || !Y))) PNP_FAIL(PNP_ERR_ARG, "pnp_mlp_forward_noalloc: null pointer");
+  if (B > kNoAllocRows)
+    PNP_FAIL(PNP_ERR_ARG, "pnp_mlp_forward_noalloc: %lld rows exceed the fixed scratch of %lld rows; split the call",
+             (long long)B, (long long)kNoAllocRows);
+  NoAllocScratch* S = nullptr;
+  if (int rc = noalloc_scratch(&S)) return rc;
+  if (B == 0) return PNP_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_refresh<<<nblk((int64_t)K0P * HID, 256), 256, 0, s>>>(params, S->W1, S->W2, S->W3, S->W4, S->b1, S->b2, S->b3,
+                                                          S->b4);
+  note_launch();
+  k_f32_to_bf16_rows<<<nblk(B * K0P, 256), 256, 0, s>>>(B, K0, K0, K0P, X, S->X);
+  note_launch();
+  const int R = (int)B;
+  cudaError_t e = cudaSuccess;
+  GemmArgs g = gargs(R, HID, K0P, S->X, K0P, 1, S->W1, HID, 1);
+  g.bias = S->b1; g.Cb = S->A1; g.ldcb = HID;
+  if (e == cudaSuccess) e = gemm<EPI_FWD_GELU>(g, s);
+  g = gargs(R, HID, HID, S->A1, HID, 1, S->W2, HID, 1);
+  g.bias = S->b2; g.Cb = S->A2; g.ldcb = HID;
+  if (e == cudaSuccess) e = gemm<EPI_FWD_GELU>(g, s);
+  g = gargs(R, HID, HID, S->A2, HID, 1, S->W3, HID, 1);
+  g.bias = S->b3; g.Cb = S->A3; g.ldcb = HID;
+  if (e == cudaSuccess) e = gemm<EPI_FWD_GELU>(g, s);
+  g = gargs(R, NO, HID, S->A3, HID, 1, S->W4, NOP, 1);
+  g.bias = S->b4; g.Cf = S->out; g.ldc = NOP;
+  if (e == cudaSuccess) e = gemm<EPI_F32>(g, s);
+  if (e == cudaSuccess) {
+    k_f32_rows<<<nblk(B * NO, 256), 256, 0, s>>>(B, NO, NOP, NO, S->out, Y);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) PNP_FAIL(PNP_ERR_CUDA, "pnp_mlp_forward_noalloc: %s", cudaGetErrorString(e));
+  return PNP_OK;
+}
 
 // Judged learned start of a time step: U <- the better of the network's start and the
 // extrapolated start 2 U^k - U^{k-1} (smaller ||F||); st->start_used says which.

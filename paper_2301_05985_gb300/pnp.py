@@ -125,7 +125,16 @@ SIGNATURES = {
     "pnp_mlp_features": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pnp_mlp_forward": (C.c_int, [_vp, _vp, _i64, _vp]),
     "pnp_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _P(_d)]),
+    "pnp_mlp_forward_noalloc": (C.c_int, [_vp, _vp, _i64, _vp, _vp]),
 }
+
+PNP_NOALLOC_MAX_ROWS = 4096
+
+
+def mlp_forward_noalloc(params, X, Y, stream: int = 0):
+    """Allocation-free network forward (no context); params/X/Y device FP32 tensors."""
+    check(lib().pnp_mlp_forward_noalloc(_ptr(params), _ptr(X), int(X.shape[0]), _ptr(Y), C.c_void_p(stream)))
+    return Y
 
 PNP_PROF_RESIDUAL, PNP_PROF_JV64, PNP_PROF_JV32, PNP_PROF_BLOCKDIAG = 0, 1, 2, 3
 PNP_PROF_ORTHO, PNP_PROF_PRECOND, PNP_PROF_MLP, PNP_PROF_KINDS = 4, 5, 6, 7
