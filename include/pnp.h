@@ -103,6 +103,9 @@ typedef struct pnp_params {
   int32_t monitor;       /* 1: one line per Newton iteration on stderr */
   int32_t f64_fallback;  /* 1: when an FP32-J V Newton iteration fails to decrease
                             ||F||, redo it with FP64 J V (default 1) */
+  int32_t gmres_cgs2;    /* 0: one classical Gram-Schmidt pass per Krylov vector (PETSc's
+                            default, used by the paper's solver); 1: always a second pass */
+  int32_t pad_;
 } pnp_params;
 
 typedef struct pnp_solve_stats {

@@ -259,8 +259,10 @@ int pnp_ctx_create(const pnp_mesh* m, const pnp_params* p, void* stream, pnp_ctx
     return fail(PNP_ERR_NOMEM);
   }
   {
-    const char* ep = getenv("PNP_ELEMENT_PATH");  // "atomic": scatter with global atomics instead
-    c->use_patches = !(ep && std::strcmp(ep, "atomic") == 0);
+    // "patch": deterministic shared-memory patch kernels; default: per-element kernels
+    // scattering with global atomics (faster on this hardware at present)
+    const char* ep = getenv("PNP_ELEMENT_PATH");
+    c->use_patches = ep && std::strcmp(ep, "patch") == 0;
   }
   if (c->use_patches) {
     PatchData P;
@@ -318,7 +320,8 @@ int ctx_alloc_krylov(pnp_ctx* c, int m) {
   c->m_alloc = 0;
   const size_t bb = sizeof(double) * (size_t)(m + 1) * (size_t)c->n3();
   cudaError_t e = cudaMalloc((void**)&c->basis, bb);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, sizeof(double) * (size_t)kRedBlocks * (m + 2));
+  const size_t part_rows = std::max<size_t>((size_t)kRedBlocks, (size_t)multi_dot_blocks(c->n3()));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, sizeof(double) * part_rows * (m + 2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->dsc, sizeof(double) * (4 * (m + 2) + 16));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hpin, sizeof(double) * (4 * (m + 2) + 16));
   if (e != cudaSuccess) {

@@ -107,19 +107,22 @@ __device__ __forceinline__ void element_compute(T (&u)[3][1 << D], T (&va)[3][1 
 #pragma unroll
     for (int m = 0; m < NC; ++m) acc[f][m] = T(0);
 
-  static_for<0, NC>([&](auto qc) {
-    constexpr int Q = decltype(qc)::value;
+#pragma unroll 1
+  for (int q = 0; q < NC; ++q) {
+    QpSign<T, D> sgn;
+    qp_sign<T, D>(q, sgn);
     T cv[2], gc[2][3], gp[3], v[3] = {T(0), T(0), T(0)}, hq[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      qp_value_grad<T, D, Q>(u[s], Gs, cv[s], gc[s]);
-      hq[s] = qp_value<T, D, Q>(hs[s]);
+      cv[s] = qpr_value<T, D>(u[s], sgn);
+      qpr_grad<T, D>(u[s], sgn, Gs, gc[s]);
+      hq[s] = qpr_value<T, D>(hs[s], sgn);
     }
-    qp_grad<T, D, Q>(u[2], Gs, gp);
+    qpr_grad<T, D>(u[2], sgn, Gs, gp);
     T vv = T(0);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      v[k] = qp_value<T, D, Q>(va[k]);
+      v[k] = qpr_value<T, D>(va[k], sgn);
       vv += v[k] * v[k];
     }
     const T tau = rsq(tau0 + G2 * vv);
@@ -148,18 +151,21 @@ __device__ __forceinline__ void element_compute(T (&u)[3][1 << D], T (&va)[3][1 
         T Phi[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) Phi[k] = gc[s][k] + zc * gp[k] + tR * P[s][k];
-        qp_test_acc<T, D, Q>(acc[s], S, Phi, Gs);
+        qpr_test_acc<T, D>(acc[s], S, Phi, Gs, sgn);
       }
       const T S = -(cv[0] - cv[1]) + tau * (R[0] - R[1]);
       T Phi[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) Phi[k] = e2 * gp[k];
-      qp_test_acc<T, D, Q>(acc[2], S, Phi, Gs);
+      qpr_test_acc<T, D>(acc[2], S, Phi, Gs, sgn);
     } else {
       T dcv[2], dgc[2][3], dgp[3];
 #pragma unroll
-      for (int s = 0; s < 2; ++s) qp_value_grad<T, D, Q>(du[s], Gs, dcv[s], dgc[s]);
-      qp_grad<T, D, Q>(du[2], Gs, dgp);
+      for (int s = 0; s < 2; ++s) {
+        dcv[s] = qpr_value<T, D>(du[s], sgn);
+        qpr_grad<T, D>(du[s], sgn, Gs, dgc[s]);
+      }
+      qpr_grad<T, D>(du[2], sgn, Gs, dgp);
       T dR[2];
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
@@ -179,15 +185,15 @@ __device__ __forceinline__ void element_compute(T (&u)[3][1 << D], T (&va)[3][1 
         T Phi[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) Phi[k] = dgc[s][k] + zdc * gp[k] + zc_tR * dgp[k] + tdR * P[s][k];
-        qp_test_acc<T, D, Q>(acc[s], S, Phi, Gs);
+        qpr_test_acc<T, D>(acc[s], S, Phi, Gs, sgn);
       }
       const T S = -(dcv[0] - dcv[1]) + tau * (dR[0] - dR[1]);
       T Phi[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) Phi[k] = e2 * dgp[k];
-      qp_test_acc<T, D, Q>(acc[2], S, Phi, Gs);
+      qpr_test_acc<T, D>(acc[2], S, Phi, Gs, sgn);
     }
-  });
+  }
 #pragma unroll
   for (int f = 0; f < 3; ++f) from_modal<T, D>(acc[f], w);
 }

@@ -125,4 +125,66 @@ __device__ __forceinline__ void from_modal(T (&A)[1 << D], T w) {
   bwd_butterfly<T, D>(A);
 }
 
+// ---- runtime Gauss-point variants (one loop body for all points: small code) ----
+// s[m] = sigma^m(q), sg[k] = sigma_k(q) for the Gauss point with bit pattern q.
+template <typename T, int D>
+struct QpSign {
+  T s[1 << D];
+  T sg[3];
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void qp_sign(int q, QpSign<T, D>& S) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) S.sg[k] = ((q >> k) & 1) ? T(1) : T(-1);
+#pragma unroll
+  for (int k = D; k < 3; ++k) S.sg[k] = T(0);
+  S.s[0] = T(1);
+#pragma unroll
+  for (int m = 1; m < (1 << D); ++m) {
+    const int k = (m & 4) ? 2 : ((m & 2) ? 1 : 0);
+    S.s[m] = S.s[m & ~(1 << k)] * S.sg[k];
+  }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T qpr_value(const T (&b)[1 << D], const QpSign<T, D>& S) {
+  T v = T(0);
+#pragma unroll
+  for (int m = 0; m < (1 << D); ++m) v = fma(S.s[m], b[m], v);
+  return v;
+}
+
+// gradient: d/dx_k = Gs * sum_{m contains k} sigma^{m without k} b_m
+template <typename T, int D>
+__device__ __forceinline__ void qpr_grad(const T (&b)[1 << D], const QpSign<T, D>& S, T Gs, T (&g)[3]) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    T a = T(0);
+#pragma unroll
+    for (int m = 0; m < (1 << D); ++m)
+      if ((m >> k) & 1) a = fma(S.s[m ^ (1 << k)], b[m], a);
+    g[k] = Gs * a;
+  }
+#pragma unroll
+  for (int k = D; k < 3; ++k) g[k] = T(0);
+}
+
+// A_m += sigma^m (S + sum_{k in m} Gs sigma_k Phi_k)
+template <typename T, int D>
+__device__ __forceinline__ void qpr_test_acc(T (&A)[1 << D], T Sv, const T (&Phi)[3], T Gs, const QpSign<T, D>& S) {
+  T p[3];
+#pragma unroll
+  for (int k = 0; k < D; ++k) p[k] = (Gs * S.sg[k]) * Phi[k];
+  T term[1 << D];
+  term[0] = Sv;
+#pragma unroll
+  for (int m = 1; m < (1 << D); ++m) {
+    const int k = (m & 4) ? 2 : ((m & 2) ? 1 : 0);
+    term[m] = term[m & ~(1 << k)] + p[k];
+  }
+#pragma unroll
+  for (int m = 0; m < (1 << D); ++m) A[m] = fma(S.s[m], term[m], A[m]);
+}
+
 }  // namespace pnpk

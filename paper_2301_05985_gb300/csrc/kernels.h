@@ -89,7 +89,9 @@ cudaError_t launch_scale_by_inv(int64_t n, const double* w, const double* nrm, d
 // z_i = Dinv_i v_i per node (3x3 blocks); optionally also a float copy z32 (may be null)
 cudaError_t launch_block_apply(int64_t N, const double* Dinv, const double* v, double scale, double* z, float* z32,
                                cudaStream_t s);
-// d[i] = V_i . w for i < k, plus d[k] = w . w when with_self (part: [kRedBlocks][k+1])
+// blocks (= partial rows) of the multi-dot for vectors of n entries
+int multi_dot_blocks(int64_t n);
+// d[i] = V_i . w for i < k, plus d[k] = w . w when with_self (part: [multi_dot_blocks(n)][k+1])
 cudaError_t launch_multi_dot_ext(int64_t n, int k, bool with_self, const double* Vb, int64_t ld, const double* w,
                                  double* part, double* d, cudaStream_t s);
 // w -= sum_i d[i] dinv[i] V_i (i < k);  nrm2[0] = w . w afterwards

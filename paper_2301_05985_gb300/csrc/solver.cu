@@ -223,10 +223,12 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   double* dd = c->dsc;                    // [m+2] dot products of one pass
   double* dinv = c->dsc + (m + 2);        // [m+2] 1 / s_i^2
   double* dnrm = c->dsc + 2 * (m + 2);    // [1]  w . w after a pass
-  double* dcoef = c->dsc + 2 * (m + 2) + 2;  // [m+1] solution-update coefficients (shares the tail)
-  double* hp = c->hpin;                   // [0, m+2): D2H scratch
-  double* hup = c->hpin + (m + 2);        // [m+2]: H2D slots for 1/s_i^2
+  double* dcoef = c->dsc + 2 * (m + 2) + 2;  // [m+1] solution-update coefficients
+  double* dd2 = c->dsc + 3 * (m + 2) + 2;    // [m+2] projections of the second pass
+  double* hp = c->hpin;                     // [0, m+2): D2H scratch
+  double* hup = c->hpin + (m + 2);          // [m+2]: H2D slots for 1/s_i^2
   double* hco = c->hpin + 2 * (m + 2) + 2;  // [m+1]: H2D slots for the update coefficients
+  double* hp2 = c->hpin + 3 * (m + 2) + 2;  // [m+2]: D2H of the second pass
   *its_out = 0;
   double bn;
   RC(ctx_norm(c, b, &bn));
@@ -281,28 +283,27 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
         ProfScope ps(c, PNP_PROF_PRECOND, 36.0 * c->n_nodes);
         CK(launch_to_f64(n, c->JV32, w, s));
       }
-      double w0sq, w1sq;
+      double w1sq;
       {
-        ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (double)n * (2.0 * (j + 1) + 4.0));
-        CK(launch_multi_dot_ext(n, j + 1, true, V, n, w, c->part, dd, s));
-        CK(launch_multi_axpy_norm(n, j + 1, V, n, dd, dinv, w, c->part, dnrm, s));
-        CK(cudaMemcpyAsync(hp, dd, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(hp + (m + 1), dnrm, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-      }
-      for (int i = 0; i <= j; ++i) h[i] = hp[i] / sv[i];
-      w0sq = hp[j + 1];
-      w1sq = hp[m + 1];
-      if (w1sq < 0.5 * w0sq) {
-        ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (double)n * (2.0 * (j + 1) + 2.0));
+        // classical Gram-Schmidt applied twice (CGS2), one host round trip per iteration;
+        // the projections of both passes go to separate device slots
+        const bool two = c->prm.gmres_cgs2 != 0;
+        ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (double)n * ((two ? 4.0 : 2.0) * (j + 1) + (two ? 6.0 : 3.0)));
         CK(launch_multi_dot_ext(n, j + 1, false, V, n, w, c->part, dd, s));
         CK(launch_multi_axpy_norm(n, j + 1, V, n, dd, dinv, w, c->part, dnrm, s));
+        if (two) {
+          CK(launch_multi_dot_ext(n, j + 1, false, V, n, w, c->part, dd2, s));
+          CK(launch_multi_axpy_norm(n, j + 1, V, n, dd2, dinv, w, c->part, dnrm, s));
+          CK(cudaMemcpyAsync(hp2, dd2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+        }
         CK(cudaMemcpyAsync(hp, dd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(hp + (m + 1), dnrm, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        for (int i = 0; i <= j; ++i) h[i] += hp[i] / sv[i];
-        w1sq = hp[m + 1];
+        if (!two)
+          for (int i = 0; i <= j; ++i) hp2[i] = 0.0;
       }
+      for (int i = 0; i <= j; ++i) h[i] = (hp[i] + hp2[i]) / sv[i];
+      w1sq = hp[m + 1];
       const double nrm = std::sqrt(w1sq);
       if (!std::isfinite(nrm)) PNP_FAIL(PNP_ERR_NAN, "gmres: Krylov vector norm is not finite");
       sv[j + 1] = nrm;

@@ -1,6 +1,7 @@
 // vector_kernels.cu -- streaming kernels of the Newton-Krylov loop (history, conversions,
 // deterministic FP64 reductions, Gram-Schmidt multi-dot / multi-axpy, 3x3 block Jacobi).
 // All of these are HBM-bound: one coalesced pass over their operands.
+#include <algorithm>
 #include <atomic>
 
 #include "kernels.h"
@@ -123,6 +124,60 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_dot_ext(int64_t n, int k,
   }
 }
 
+// d_i = V_i . w (i < k; and w . w as entry k when kk > k).  Each block owns a contiguous
+// chunk of kMdRows x 256 rows: w's rows stay in registers while the block sweeps the basis
+// one vector at a time (kMdRows independent loads per thread per vector, warp-shuffle
+// reduction, fixed order).  Per-block partials part[block][kk].
+constexpr int kMdRows = 8;
+__global__ void __launch_bounds__(256) k_multi_dot2(int64_t n, int k, int kk, const double* __restrict__ Vb,
+                                                    int64_t ld, const double* __restrict__ w,
+                                                    double* __restrict__ part) {
+  __shared__ double sh[64][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * (256 * kMdRows) + threadIdx.x;
+  double wv[kMdRows];
+#pragma unroll
+  for (int r = 0; r < kMdRows; ++r) {
+    const int64_t t = base + r * 256;
+    wv[r] = t < n ? w[t] : 0.0;
+  }
+  for (int i0 = 0; i0 < kk; i0 += 64) {
+    const int cnt = min(64, kk - i0);
+    // four basis vectors per pass: 4 x kMdRows independent loads, four interleaved shuffle trees
+    for (int j0 = 0; j0 < cnt; j0 += 4) {
+      double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + j0 + q;
+        if (j0 + q < cnt) {
+          const double* vi = i < k ? Vb + (int64_t)i * ld : w;
+#pragma unroll
+          for (int r = 0; r < kMdRows; ++r) {
+            const int64_t t = base + r * 256;
+            if (t < n) s[q] = fma(__ldg(vi + t), wv[r], s[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j0 + q < cnt) sh[j0 + q][wid] = s[q];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += sh[j][q];
+      part[(int64_t)blockIdx.x * kk + i0 + j] = s;
+    }
+    __syncthreads();
+  }
+}
+
 // w -= sum_i (d_i * dinv_i) V_i  and per-block partial sums of the updated w . w
 __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_norm(int64_t n, int k, const double* __restrict__ Vb,
                                                                  int64_t ld, const double* __restrict__ d,
@@ -134,8 +189,17 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_norm(int64_t n, int 
   __syncthreads();
   double ss = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    double v = w[t];
-    for (int i = 0; i < k; ++i) v -= cf[i] * Vb[(int64_t)i * ld + t];
+    // independent partial sums so the loads of several basis vectors are in flight at once
+    double v0 = w[t], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int i = 0;
+    for (; i + 4 <= k; i += 4) {
+      v0 -= cf[i] * Vb[(int64_t)i * ld + t];
+      v1 -= cf[i + 1] * Vb[(int64_t)(i + 1) * ld + t];
+      v2 -= cf[i + 2] * Vb[(int64_t)(i + 2) * ld + t];
+      v3 -= cf[i + 3] * Vb[(int64_t)(i + 3) * ld + t];
+    }
+    for (; i < k; ++i) v0 -= cf[i] * Vb[(int64_t)i * ld + t];
+    const double v = (v0 + v1) + (v2 + v3);
     w[t] = v;
     ss += v * v;
   }
@@ -307,12 +371,15 @@ cudaError_t launch_scale_by_inv(int64_t n, const double* w, const double* nrm, d
   if (n) { k_scale_by_inv<<<gs_blocks(n, 256), 256, 0, s>>>(n, w, nrm, v); note_launch(); }
   return cudaGetLastError();
 }
+int multi_dot_blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + 256 * kMdRows - 1) / (256 * kMdRows)); }
+
 cudaError_t launch_multi_dot_ext(int64_t n, int k, bool with_self, const double* Vb, int64_t ld, const double* w,
                                  double* part, double* d, cudaStream_t s) {
   const int kk = k + (with_self ? 1 : 0);
   if (kk <= 0) return cudaSuccess;
-  k_multi_dot_ext<<<kRedBlocks, kRedThreads, 0, s>>>(n, k, kk, Vb, ld, w, part); note_launch();
-  k_reduce_parts<<<kk, kRedThreads, 0, s>>>(kRedBlocks, kk, part, d, 0); note_launch();
+  const int nb = multi_dot_blocks(n);
+  k_multi_dot2<<<nb, 256, 0, s>>>(n, k, kk, Vb, ld, w, part); note_launch();
+  k_reduce_parts<<<kk, kRedThreads, 0, s>>>(nb, kk, part, d, 0); note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_multi_axpy_norm(int64_t n, int k, const double* Vb, int64_t ld, const double* d, const double* dinv,

@@ -46,6 +46,7 @@ class pnp_params(C.Structure):
         ("precision", C.c_int32), ("start_mode", C.c_int32),
         ("ew_eta_max", C.c_double), ("ew_eta_min", C.c_double),
         ("monitor", C.c_int32), ("f64_fallback", C.c_int32),
+        ("gmres_cgs2", C.c_int32), ("pad_", C.c_int32),
     ]
 
 

@@ -106,13 +106,17 @@ def test_residual_ignores_stored_hanging_values():
 
 @pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[CASES[1][0], CASES[3][0]])
 def test_patch_kernels_are_deterministic_and_match_atomic_path(case, monkeypatch):
-    """The shared-memory patch kernels (default) sum in a fixed order: two evaluations are
-    bitwise equal; they agree with the global-atomics kernels to rounding."""
+    """The shared-memory patch kernels sum in a fixed order: two evaluations are bitwise
+    equal; they agree with the default global-atomics kernels to rounding and with the
+    oracle at the FP64 bar."""
+    monkeypatch.setenv("PNP_ELEMENT_PATH", "patch")
     P, U, V = _setup(case)
     outs = [(P.gpu_residual(U), P.gpu_jv(U, V, 0), P.gpu_jv(U, V, 1)) for _ in range(2)]
     for a, b in zip(outs[0], outs[1]):
         assert np.array_equal(a, b)
-    monkeypatch.setenv("PNP_ELEMENT_PATH", "atomic")
+    assert rel_err(outs[0][0], P.oracle_residual(U)) <= TOL64
+    assert rel_err(outs[0][1], P.oracle_jv(U, V)) <= TOL64
+    monkeypatch.delenv("PNP_ELEMENT_PATH")
     name, oc, kw, bcs = case
     Q = Pair(oc, kw, bcs)
     Q.set_state(P.Uk, P.Ukm1, P.vel)
