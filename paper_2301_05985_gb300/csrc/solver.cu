@@ -344,14 +344,13 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
     CK(launch_multi_axpy(n, k, V, n, dcoef, c->w, nullptr, s));
     CK(launch_block_apply(c->n_nodes, c->Dinv, c->w, 1.0, c->z, nullptr, s));
     CK(launch_axpby(n, 1.0, c->z, 1.0, x, s));
-    if (res <= tol || breakdown) {
-      beta = res;
-      break;
-    }
-    // restart from the true residual
+    // true residual (restart vector); when the Arnoldi estimate claims convergence it is
+    // accepted only if the true residual agrees (the estimate drifts when the Krylov
+    // basis loses orthogonality)
     RC(apply_op(c, U, x, c->w, prec));
     CK(launch_axpbyz(n, 1.0, b, -1.0, c->w, V, s));
     RC(ctx_norm(c, V, &beta));
+    if ((res <= tol || breakdown) && beta <= 2.0 * tol) break;
     if (c->prm.monitor >= 2)
       fprintf(stderr, "[pnp gmres] its %5d  estimate %.3e  true %.3e (relative)\n", total, res / bn, beta / bn);
   }

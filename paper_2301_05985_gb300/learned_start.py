@@ -26,7 +26,26 @@ def setup(pnp, W, torch, V, level=5, eps=0.01, dt=1e-3, seed=0, mode="plain"):
     ctx.set_field(pnp.PNP_FIELD_U, U0)
     ctx.make_consistent()
     ctx.reset_history()
+    develop_double_layer(pnp, ctx, dt)
     return mesh, ctx
+
+
+def develop_double_layer(pnp, ctx, dt, dt0=1e-6, factor=4.0):
+    """Start from a developed double layer (as the paper does for its electroconvection
+    runs): BDF1 steps with the step size growing geometrically from dt0 to dt, then the
+    history is reset so the recorded trajectory starts there with the target dt."""
+    p = ctx.get_params()
+    ramp = pnp.default_params(**{k: getattr(p, k) for k, _ in p._fields_})
+    ramp.bdf_order, ramp.newton_max_it, ramp.start_mode = 1, 100, pnp.PNP_START_PREVIOUS
+    h = dt0
+    while h < dt:
+        ramp.dt = h
+        ctx.set_params(ramp)
+        ctx.time_step()
+        ctx.reset_history()
+        h *= factor
+    ctx.set_params(p)
+    ctx.reset_history()
 
 
 def record(pnp, torch, ctx, n_steps):
