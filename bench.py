@@ -7,16 +7,20 @@ at z = 0 (phi = 0, c+ = 2, c- zero flux), reservoir at z = 1 (phi = V, c+- = 1),
 zero-flux side walls; c+- = 1 + seeded uniform noise of amplitude 1e-3, phi linear.
 The velocity is zero (no Navier-Stokes block in this library).
 
-One step = one pnp_time_step: BDF2 (BDF1 first), Newton to ||F|| <= 1e-8 ||F0||,
-GMRES(30) with 3x3 block-Jacobi on the exact Jacobian action.  Modes:
+One step = one pnp_time_step: BDF2 (BDF1 first), Newton to ||F|| <= 1e-8 ||F(U^k)||,
+GMRES with 3x3 block-Jacobi on the exact Jacobian action.  Modes:
   mixed : FP32 J V inside an inexact Newton (Eisenstat-Walker), FP64 residual, dots,
-          orthogonalisation; learned start if a trained network is supplied, else
-          the extrapolated start 2 U^k - U^{k-1}.
-  plain : FP64 J V, GMRES rtol 1e-8 per Newton step, previous-step start (the paper's).
+          orthogonalisation; learned start (network trained, before the timed region,
+          on the first steps of this run's own trajectory), judged against the
+          extrapolated start 2 U^k - U^{k-1}.
+  plain : FP64 J V, GMRES(100) rtol 1e-8 per Newton step, previous-step start (the
+          paper's); timed for comparison from the same state as the first mixed step.
 
 value = unknowns advanced per second = 3 N x steps / time (GDoF/s), timed with CUDA
-events on the library's stream.  The dominant kernel's roofline comes from the
-library's own event timing of each launch class during the timed region.
+events on the library's stream.  Kernel rooflines come from the library's own event
+timing of each launch class during the timed region, against the roofline that bounds
+the class: FP64 or FP32 ALU (peaks derived from 152 SMs x 2 FP64 / 128 FP32 FMA per
+clock x 2.07 GHz), HBM or BF16 tensor (measured peaks).
 """
 from __future__ import annotations
 
@@ -37,6 +41,12 @@ for _p in (ROOT, os.path.join(ROOT, "oracle")):
 
 METRIC = "PNP Jv GDoF/s (% HBM peak); s per PNP–NS step at rel-resid 1e-8, plain vs mixed+learned"
 EPS, VOLT, DT = 1e-3, 20.0, 1e-3
+# ALU peaks: 152 SMs x (2 FP64 | 128 FP32) FMA per clock x 2 flop x 2.07 GHz
+FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# roofline that bounds each kernel class (arithmetic intensity against the balance points)
+BOUNDS = {"residual64": "fp64", "jv64": "fp64", "jv32": "fp32", "blockdiag": "hbm", "ortho_dot": "fp64",
+          "ortho_update": "fp64", "precond": "hbm", "mlp": "bf16"}
 
 
 def parse():
@@ -50,6 +60,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-mode comparison step")
+    ap.add_argument("--no-learned", action="store_true", help="mixed mode without training the learned start")
+    ap.add_argument("--record-steps", type=int, default=8, help="trajectory steps recorded for training")
+    ap.add_argument("--train-steps", type=int, default=400, help="Adam steps of the learned start")
     return ap.parse_args()
 
 
@@ -61,9 +74,10 @@ def workload_octants(small: bool):
 def mode_params(pnp, mode):
     if mode == "mixed":
         return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F32, start_mode=pnp.PNP_START_LEARNED,
-                                  newton_rtol=1e-8, gmres_restart=60, gmres_max_it=3000)
+                                  newton_rtol=1e-8, gmres_restart=60, gmres_max_it=3000, dt_retries=2)
     return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F64, start_mode=pnp.PNP_START_PREVIOUS,
-                              newton_rtol=1e-8, gmres_rtol=1e-8, gmres_restart=100, gmres_max_it=4000)
+                              newton_rtol=1e-8, gmres_rtol=1e-8, gmres_restart=100, gmres_max_it=4000,
+                              dt_retries=2)
 
 
 def measured_peaks():
@@ -180,20 +194,92 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def roofline(prof, peaks, jv_traffic):
-    best = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    name, d = best
-    if d["count"] == 0 or d["ms"] <= 0:
-        return None, None
-    gbs = d["alg_bytes"] / (d["ms"] * 1e-3) / 1e9
-    peak = peaks.get("hbm_gbs", 6800.0)
-    traffic = jv_traffic.get(name)
-    rl = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
-          "traffic": traffic, "kernel": name, "launches": d["count"],
-          "avg_launch_ms": d["ms"] / d["count"],
-          "alg_bytes_per_launch": d["alg_bytes"] / d["count"],
-          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if not peaks.get("fallback") else "fallback"}
-    return rl, name
+def load_traffic(small: bool):
+    """Per-class DRAM traffic from the committed ncu summary, for kernels whose source
+    is unchanged since the capture."""
+    import hashlib
+    try:
+        tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except Exception:
+        return {}
+    if tj.get("workload") != ("small" if small else "full"):
+        return {}
+    out = {}
+    for name, e in tj.get("classes", {}).items():
+        try:
+            same = all(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
+                       for f, h in e["sources"].items())
+        except OSError:
+            same = False
+        if same:
+            out[name] = e
+    return out
+
+
+def kernel_table(prof, peaks, total_ms):
+    """Per class: time share, algorithmic GB/s and TFLOP/s, and the fraction of the
+    roofline that bounds it."""
+    rows = {}
+    for name, d in prof.items():
+        if d["count"] == 0 or d["ms"] <= 0:
+            continue
+        t = d["ms"] * 1e-3
+        gbs = d["alg_bytes"] / t / 1e9
+        tfl = d["alg_flops"] / t / 1e12
+        kind = BOUNDS[name]
+        if kind == "hbm":
+            bound, unit, ach, peak = "hbm", "GB/s", gbs, peaks["hbm_gbs"]
+            src = "measured" if not peaks.get("fallback") else "fallback"
+        elif kind == "bf16":
+            bound, unit, ach, peak = "tensor", "TFLOP/s", tfl, peaks.get("bf16_tflops_sustained", 1700.0)
+            src = "measured sustained" if not peaks.get("fallback") else "fallback"
+        else:
+            bound, unit, ach = "alu", "TFLOP/s", tfl
+            peak = FP64_TFLOPS if kind == "fp64" else FP32_TFLOPS
+            src = f"derived {kind.upper()}: 152 SMs x {2 if kind == 'fp64' else 128} FMA/clk x 2 x 2.07 GHz"
+        rows[name] = {"bound": bound, "achieved": round(ach, 4), "peak": round(peak, 3), "unit": unit,
+                      "frac": round(ach / peak, 4), "peak_source": src, "launches": d["count"],
+                      "avg_launch_ms": d["ms"] / d["count"], "share": round(d["ms"] / total_ms, 4),
+                      "alg_bytes_per_launch": d["alg_bytes"] / d["count"],
+                      "alg_flops_per_launch": d["alg_flops"] / d["count"],
+                      "alg_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
+    return rows
+
+
+def roofline(table, traffic):
+    """The dominant class's roofline object (largest device time)."""
+    if not table:
+        return None
+    name = max(table, key=lambda k: table[k]["avg_launch_ms"] * table[k]["launches"])
+    rl = dict(table[name])
+    rl["kernel"] = name
+    e = traffic.get(name)
+    rl["traffic"] = None
+    if e:
+        if "dram_bytes_per_launch" in e:
+            rl["traffic"] = e["dram_bytes_per_launch"]
+        elif "dram_per_requested" in e:  # launches of varying size: DRAM bytes per requested byte
+            rl["traffic"] = e["dram_per_requested"] * rl["alg_bytes_per_launch"]
+            rl["traffic_note"] = "ncu DRAM bytes per L2-requested byte x this run's algorithmic bytes per launch"
+    return rl
+
+
+def train_learned_start(pnp, torch, ctx, n_record, train_steps):
+    """Record the first steps of this run (extrapolated start) and train the network."""
+    from paper_2301_05985_gb300 import learned_start as LS
+    p = ctx.get_params()
+    mode = p.start_mode
+    p.start_mode = pnp.PNP_START_EXTRAPOLATE
+    ctx.set_params(p)
+    t0 = time.perf_counter()
+    S, its = LS.record(pnp, torch, ctx, n_record)
+    ctx.mlp_init(seed=0)
+    ctx.mlp_add_trajectory(S)
+    st = ctx.mlp_train(steps=train_steps, batch=4096, lr=1e-3, seed=1)
+    p.start_mode = mode
+    ctx.set_params(p)
+    return {"recorded_steps": len(its), "train_steps": train_steps, "loss_first": st.loss_first,
+            "loss_last": st.loss_last, "train_s": st.wall_ms * 1e-3, "setup_s": time.perf_counter() - t0}
 
 
 def main():
@@ -219,9 +305,17 @@ def main():
     N = mesh.n_nodes
     stream = torch.cuda.current_stream()
 
+    learned = None
+    if args.mode == "mixed" and not args.no_learned:
+        learned = train_learned_start(pnp, torch, ctx, args.record_steps, args.train_steps)
     stats = []
     for _ in range(args.warmup):
         ctx.time_step()
+    torch.cuda.synchronize()
+    # the state the timed region starts from (for the plain-mode comparison)
+    hist = [torch.empty((N, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+    ctx.get_field(pnp.PNP_FIELD_U_PREV, hist[0], pnp.PNP_DEVICE)
+    ctx.get_field(pnp.PNP_FIELD_U_PREV2, hist[1], pnp.PNP_DEVICE)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -265,38 +359,37 @@ def main():
                "h2d_bytes_per_step": 2 * 24 * N, "d2h_bytes_per_step": 24 * N,
                "ms_per_step": 1e3 * t_e2e / args.steps}
 
-    # plain-mode comparison (one step from the same state; not part of the timed value)
+    # plain-mode comparison: one step from the state the timed mixed steps started from
     plain = None
-    if not args.no_plain and rank == 0:
+    if not args.no_plain and rank == 0 and args.mode == "mixed":
         mesh_p, ctx_p = setup_ctx(pnp, W, torch, oc, "plain")
-        for _ in range(2):
-            ctx_p.time_step()
+        p = ctx_p.get_params()
+        p.bdf_order = 1
+        ctx_p.set_params(p)
+        ctx_p.time_step()  # one cheap BDF1 step so that the next one is BDF2 (history loaded below)
+        p.bdf_order = 2
+        ctx_p.set_params(p)
+        ctx_p.set_field(pnp.PNP_FIELD_U_PREV, hist[0], pnp.PNP_DEVICE)
+        ctx_p.set_field(pnp.PNP_FIELD_U_PREV2, hist[1], pnp.PNP_DEVICE)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st = ctx_p.time_step().as_dict()
         torch.cuda.synchronize()
         plain = {"s_per_step": time.perf_counter() - t0, "newton_its": st["newton_its"],
-                 "krylov_its": st["krylov_its"], "after_steps": 2}
+                 "krylov_its": st["krylov_its"], "substeps": st["substeps"],
+                 "state": "same state as the first timed mixed step",
+                 "mixed_first_step": {"s": stats[0]["wall_ms"] * 1e-3, "newton_its": stats[0]["newton_its"],
+                                      "krylov_its": stats[0]["krylov_its"]}}
         ctx_p.close()
 
     peaks = measured_peaks()
-    traffic = {}
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp):
-        try:
-            tj = json.load(open(tp))
-            import hashlib
-            src = open(os.path.join(ROOT, "paper_2301_05985_gb300", "csrc", "element_kernels.cu"), "rb").read()
-            if tj.get("element_kernels_sha256") == hashlib.sha256(src).hexdigest() and \
-                    tj.get("workload") == ("small" if args.small else "full"):
-                traffic = tj.get("traffic_per_launch", {})
-        except Exception:
-            traffic = {}
-    rl, dom = roofline(prof, peaks, traffic)
+    table = kernel_table(prof, peaks, ms)
+    rl = roofline(table, load_traffic(args.small))
     jv_name = "jv32" if args.mode == "mixed" else "jv64"
     jv = prof[jv_name]
-    jv_gdofs = 3.0 * N * jv["count"] / (jv["ms"] * 1e-3) / 1e9 if jv["ms"] > 0 else None
-    jv_gbs = jv["alg_bytes"] / (jv["ms"] * 1e-3) / 1e9 if jv["ms"] > 0 else None
+    jv_row = dict(table.get(jv_name, {}))
+    if jv["ms"] > 0:
+        jv_row.update({"name": jv_name, "gdofs": 3.0 * N * jv["count"] / (jv["ms"] * 1e-3) / 1e9})
 
     if rank != 0:
         return
@@ -313,18 +406,23 @@ def main():
                                 "3D membrane-band octree, base level 5, level 8 for z<0.05 (2:1 graded)"),
                    "n_elem": mesh.n_elem, "n_nodes": N, "n_hanging": mesh.n_hanging, "dofs": 3 * N,
                    "eps": EPS, "V": VOLT, "dt": DT, "mode": args.mode, "velocity": "zero (no NS block)",
-                   "l2": "working set > L2 (3.1M-dof vectors, 31-vector Krylov basis = 780 MB)",
+                   "start": ("learned (judged vs extrapolated)" if learned else
+                             "extrapolated" if args.mode == "mixed" else "previous step"),
+                   "l2": "inputs larger than L2 (3.1M-dof FP64 vectors 25 MB each, Krylov basis up to 1.5 GB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": rl,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
+        "launches_before_timed": int(launches0),
         "clocks": clk.summary(),
         "newton_its_per_step": nt / args.steps, "krylov_its_per_step": kt / args.steps,
+        "split_steps": sum(int(s["substeps"] > 1) for s in stats),
+        "learned_start_used": sum(int(s["start_used"] == pnp.PNP_START_LEARNED) for s in stats),
         "s_per_step": ms * 1e-3 / args.steps,
-        "jv_kernel": {"name": jv_name, "gdofs": jv_gdofs, "alg_gbs": jv_gbs,
-                      "avg_ms": jv["ms"] / jv["count"] if jv["count"] else None},
-        "time_share": {k: round(v["ms"] / ms, 4) for k, v in prof.items()},
+        "jv_kernel": jv_row,
+        "kernels": table,
+        "learned_training": learned,
         "plain_step": plain,
     }
     print(json.dumps(out))

@@ -88,7 +88,10 @@ typedef struct pnp_params {
                                  pnp_newton_solve; pnp_time_step sets them itself */
   int32_t steady;        /* 1: drop the d/dt terms and the 4/dt^2 term of tau_c */
   int32_t bdf_order;     /* pnp_time_step: 1 or 2 (first step is always BDF1) */
-  double newton_rtol;    /* stop when ||F(U^m)||_2 <= newton_rtol ||F(U^0)||_2 */
+  double newton_rtol;    /* stop when ||F(U^m)||_2 <= newton_rtol ||F(U^0)||_2; in
+                            pnp_time_step the reference is ||F(U^k)||_2 of the
+                            previous-step state whatever the start, so that all starts
+                            meet one absolute tolerance */
   double newton_atol;    /* ... or ||F(U^m)||_2 <= newton_atol */
   int32_t newton_max_it;
   int32_t line_search;   /* 1: backtracking (halving, Armijo 1e-4) on ||F||_2 */
@@ -105,7 +108,10 @@ typedef struct pnp_params {
                             ||F||, redo it with FP64 J V (default 1) */
   int32_t gmres_cgs2;    /* 0: one classical Gram-Schmidt pass per Krylov vector (PETSc's
                             default, used by the paper's solver); 1: always a second pass */
-  int32_t pad_;
+  int32_t dt_retries;    /* pnp_time_step: when Newton fails, redo the step as two BDF1
+                            half steps, recursively up to this depth (0: report the
+                            failure; the next full step after a split is BDF1 and starts
+                            from the previous state, because the history spacing changed) */
 } pnp_params;
 
 typedef struct pnp_solve_stats {
@@ -116,12 +122,15 @@ typedef struct pnp_solve_stats {
   int32_t jv_evals;
   int32_t start_used;    /* PNP_START_* actually used (learned start may fall back) */
   int32_t f64_fallbacks; /* Newton iterations redone with FP64 J V */
-  int32_t pad_;
+  int32_t substeps;      /* pnp_time_step: Newton solves that completed the step
+                            (1 unless dt_retries split it) */
   double res0;           /* ||F(U^0)||_2 */
   double res_final;      /* ||F(U^m)||_2 */
   double res_start_extrapolated; /* learned start only: ||F|| of the extrapolated start */
   double res_start_learned;      /* learned start only: ||F|| of the network's start */
   double wall_ms;        /* host wall time of the call */
+  double res_ref;        /* ||F|| the relative Newton tolerance refers to: res0, or in
+                            pnp_time_step ||F(U^k)|| of the previous-step state */
 } pnp_solve_stats;
 
 /* Message for the calling thread's most recent failure ("" if none).  Static storage. */
@@ -309,18 +318,21 @@ enum {
   PNP_PROF_JV64 = 1,       /* FP64 J V element kernel */
   PNP_PROF_JV32 = 2,       /* FP32 J V element kernel */
   PNP_PROF_BLOCKDIAG = 3,  /* block-diagonal element kernel + 3x3 inversion */
-  PNP_PROF_ORTHO = 4,      /* Gram-Schmidt multi-dot / multi-axpy / norms */
+  PNP_PROF_ORTHO = 4,      /* Gram-Schmidt projections: the multi-dot kernel */
   PNP_PROF_PRECOND = 5,    /* block-Jacobi apply (and FP32 conversion) */
   PNP_PROF_MLP = 6,        /* learned-start network kernels */
-  PNP_PROF_KINDS = 7
+  PNP_PROF_ORTHO_UPDATE = 7, /* Gram-Schmidt update: the multi-axpy + norm kernel */
+  PNP_PROF_KINDS = 8
 };
 /* on != 0: clear the accumulated times and start recording; on == 0: stop. */
 int pnp_profile_enable(pnp_ctx* c, int on);
-/* Accumulated device time (ms), number of timed regions and algorithmic HBM bytes
- * (each operand read once and each result written once, as the launches' sizes
- * dictate) of one class since profiling was enabled; synchronises the stream.  Any
- * output pointer may be NULL. */
-int pnp_profile_read(pnp_ctx* c, int kind, double* total_ms, int64_t* count, double* alg_bytes);
+/* Accumulated device time (ms), number of timed regions, algorithmic HBM bytes (each
+ * operand read once and each result written once, as the launches' sizes dictate)
+ * and algorithmic floating-point operations (an FMA counts 2; the operation count of
+ * the formulation the kernel evaluates, 0 where not tracked) of one class since
+ * profiling was enabled; synchronises the stream.  Any output pointer may be NULL. */
+int pnp_profile_read(pnp_ctx* c, int kind, double* total_ms, int64_t* count, double* alg_bytes,
+                     double* alg_flops);
 /* Kernels launched by this process through the library since it was loaded. */
 int64_t pnp_kernel_launches(void);
 

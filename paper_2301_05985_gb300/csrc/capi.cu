@@ -541,13 +541,15 @@ int pnp_profile_enable(pnp_ctx* c, int on) {
       c->prof_ms[k] = 0;
       c->prof_cnt[k] = 0;
       c->prof_bytes[k] = 0;
+      c->prof_flops[k] = 0;
     }
   }
   c->prof_on = on != 0;
   return PNP_OK;
 }
 
-int pnp_profile_read(pnp_ctx* c, int kind, double* total_ms, int64_t* count, double* alg_bytes) {
+int pnp_profile_read(pnp_ctx* c, int kind, double* total_ms, int64_t* count, double* alg_bytes,
+                     double* alg_flops) {
   CTX_GUARD(c);
   if (kind < 0 || kind >= PNP_PROF_KINDS) PNP_FAIL(PNP_ERR_ARG, "pnp_profile_read: bad kind %d", kind);
   CK(cudaStreamSynchronize(c->stream));
@@ -555,6 +557,7 @@ int pnp_profile_read(pnp_ctx* c, int kind, double* total_ms, int64_t* count, dou
   if (total_ms) *total_ms = c->prof_ms[kind];
   if (count) *count = c->prof_cnt[kind];
   if (alg_bytes) *alg_bytes = c->prof_bytes[kind];
+  if (alg_flops) *alg_flops = c->prof_flops[kind];
   return PNP_OK;
 }
 
@@ -564,6 +567,7 @@ int pnp_reset_history(pnp_ctx* c) {
   CK(cudaMemcpyAsync(c->Ukm1, c->U, sizeof(double) * c->n3(), cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->step = 0;
+  c->history_split = false;
   return PNP_OK;
 }
 

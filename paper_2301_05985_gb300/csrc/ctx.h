@@ -13,6 +13,7 @@ struct pnp_ctx {
   double bc_val[6][3] = {};
   cudaError_t latched = cudaSuccess;
   int64_t step = 0;
+  bool history_split = false;  // U^{k-1} is not one full step behind U^k (after a split)
 
   // mesh (device)
   int32_t* d_conn = nullptr;
@@ -64,6 +65,7 @@ struct pnp_ctx {
   double prof_ms[PNP_PROF_KINDS] = {};
   int64_t prof_cnt[PNP_PROF_KINDS] = {};
   double prof_bytes[PNP_PROF_KINDS] = {};
+  double prof_flops[PNP_PROF_KINDS] = {};
   // algorithmic bytes of one element-kernel launch: connectivity + level (+ hanging tables)
   double conn_bytes() const {
     return (double)n_elem * (4.0 * (1 << dim) + 1.0) + (double)n_hanging * 17.0;
@@ -119,9 +121,10 @@ struct ProfScope {
   pnp_ctx* c;
   int kind;
   cudaEvent_t a = nullptr;
-  ProfScope(pnp_ctx* c_, int k, double bytes) : c(c_), kind(k) {
+  ProfScope(pnp_ctx* c_, int k, double bytes, double flops = 0.0) : c(c_), kind(k) {
     if (c->prof_on) {
       c->prof_bytes[kind] += bytes;
+      c->prof_flops[kind] += flops;
       a = c->take_event();
       cudaEventRecord(a, c->stream);
     }
@@ -146,7 +149,7 @@ int ctx_block_diag(pnp_ctx* c, const double* U, double* D);
 int ctx_norm(pnp_ctx* c, const double* x, double* out);
 int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int precision, int max_it,
               int* its, double* relres, bool have_precond);
-int ctx_newton(pnp_ctx* c, pnp_solve_stats* st);
+int ctx_newton(pnp_ctx* c, pnp_solve_stats* st, const double* ref_state = nullptr);
 int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st);
 int ctx_alloc_krylov(pnp_ctx* c, int m);
 void pnp_mlp_release(pnp_ctx* c);

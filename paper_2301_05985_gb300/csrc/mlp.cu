@@ -1063,7 +1063,6 @@ int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st) {
   Mlp* m = c->mlp;
   cudaStream_t s = c->stream;
   const int64_t N = c->n_nodes, n = c->n3();
-  ProfScope ps(c, PNP_PROF_MLP, 0.0);
   // extrapolated start in Ut (consistent)
   CK(launch_axpbyz(n, 2.0, c->Uk, -1.0, c->Ukm1, c->Ut, s));
   CK(launch_make_consistent(c->rows(), c->Ut, s));
@@ -1079,24 +1078,31 @@ int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st) {
     CK(cudaMemcpy2DAsync(uzkm1, sizeof(double), c->vel_prev + d, 3 * sizeof(double), sizeof(double), N,
                          cudaMemcpyDeviceToDevice, s));
   }
-  for (int64_t r0 = 0; r0 < m->n_free; r0 += kMaxRows) {
-    const int64_t rows = std::min<int64_t>(kMaxRows, m->n_free - r0);
-    FeatArgs a = feat_args(m, N);
-    a.rows = rows;
-    a.row_slot = nullptr;
-    a.ptr = m->st_ptr + r0 * NPT;  // rows are consecutive free-node slots
-    a.Uk = c->Uk;
-    a.Ukm1 = c->Ukm1;
-    a.uzk = uzk;
-    a.uzkm1 = uzkm1;
-    a.X = m->X;
-    k_features<<<nblk(rows * NPT, 256), 256, 0, s>>>(a);
-    note_launch();
-    RC(mlp_forward_rows(c, m, rows));
-    k_apply_correction<<<nblk(rows, 256), 256, 0, s>>>(rows, m->free_nodes + r0, m->out, m->out_mu[0], m->out_mu[1],
-                                                       m->out_mu[2], m->out_sd[0], m->out_sd[1], m->out_sd[2], c->Ut,
-                                                       c->U);
-    note_launch();
+  // features, network and correction; algorithmic bytes per free node: U^k, U^{k-1}
+  // and u_z read once (64 B), the extrapolated start read and the start written (48 B);
+  // flops: the four layers
+  {
+    ProfScope ps(c, PNP_PROF_MLP, (64.0 + 48.0) * m->n_free,
+                 2.0 * m->n_free * (double)(K0 * HID + 2 * HID * HID + HID * NO));
+    for (int64_t r0 = 0; r0 < m->n_free; r0 += kMaxRows) {
+      const int64_t rows = std::min<int64_t>(kMaxRows, m->n_free - r0);
+      FeatArgs a = feat_args(m, N);
+      a.rows = rows;
+      a.row_slot = nullptr;
+      a.ptr = m->st_ptr + r0 * NPT;  // rows are consecutive free-node slots
+      a.Uk = c->Uk;
+      a.Ukm1 = c->Ukm1;
+      a.uzk = uzk;
+      a.uzkm1 = uzkm1;
+      a.X = m->X;
+      k_features<<<nblk(rows * NPT, 256), 256, 0, s>>>(a);
+      note_launch();
+      RC(mlp_forward_rows(c, m, rows));
+      k_apply_correction<<<nblk(rows, 256), 256, 0, s>>>(rows, m->free_nodes + r0, m->out, m->out_mu[0], m->out_mu[1],
+                                                         m->out_mu[2], m->out_sd[0], m->out_sd[1], m->out_sd[2], c->Ut,
+                                                         c->U);
+      note_launch();
+    }
   }
   CK(cudaGetLastError());
   CK(launch_make_consistent(c->rows(), c->U, s));

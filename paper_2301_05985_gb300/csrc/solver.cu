@@ -82,10 +82,28 @@ static int hanging_rows(pnp_ctx* c, const T* in, T* out) {
   return ctx_check(c, launch_row_fixups<T>(R, in, out, 0, c->stream), "hanging rows");
 }
 
+// Floating-point operations per element of the element kernels (an FMA counts 2),
+// counted from the modal formulation they evaluate: nodal -> modal transforms of the
+// inputs, per Gauss point the values and gradients, physics and test contraction, and
+// the modal -> nodal transform of the three element-vector fields.
+static double element_flops(int D, bool jv) {
+  const double NC = 1 << D;
+  const double val = 2 * NC, grad = D * (NC + 1);
+  const double to_m = D * NC + NC, from_m = D * NC + 2 * NC;
+  const double acc = 2 * D + (NC - 1) + 2 * NC;
+  // c+- values and gradients, history values, grad phi, advection, |v|^2, tau, P_s, R_s
+  const double common = 2 * val + 2 * grad + 2 * val + grad + D * val + 2 * D + 3 + 2 * (3 * D + 3);
+  const double poisson = 4 + D + acc;
+  if (!jv) return NC * (common + 2 * (6 * D + 4 + acc) + poisson) + 8 * to_m + 3 * from_m;
+  const double dir = 2 * val + 3 * grad;  // direction values and gradients
+  return NC * (common + dir + 2 * (12 * D + 8 + acc) + poisson) + 11 * to_m + 3 * from_m;
+}
+
 int ctx_residual(pnp_ctx* c, const double* U, double* F) {
   if (c->use_patches) {
     {
-      ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes());
+      ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes(),
+                   element_flops(c->dim, false) * c->n_elem);
       CK(launch_patch<double>(c->dim, false, patch_args<double>(c, U, nullptr, c->hs, c->adv, F, c->part64),
                               c->stream));
     }
@@ -93,7 +111,8 @@ int ctx_residual(pnp_ctx* c, const double* U, double* F) {
   } else {
     CK(cudaMemsetAsync(F, 0, sizeof(double) * c->n3(), c->stream));
     {
-      ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes());
+      ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes(),
+                   element_flops(c->dim, false) * c->n_elem);
       CK(launch_element<double>(c->dim, false, elem_args<double>(c, U, nullptr, c->hs, c->adv, F), c->stream));
     }
     CK(launch_row_fixups<double>(c->rows(), U, F, 0, c->stream));
@@ -105,14 +124,14 @@ int ctx_residual(pnp_ctx* c, const double* U, double* F) {
 int ctx_jv64(pnp_ctx* c, const double* U, const double* V, double* JV) {
   if (c->use_patches) {
     {
-      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes());
+      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes(), element_flops(c->dim, true) * c->n_elem);
       CK(launch_patch<double>(c->dim, true, patch_args<double>(c, U, V, c->hs, c->adv, JV, c->part64), c->stream));
     }
     RC(hanging_rows<double>(c, V, JV));
   } else {
     CK(cudaMemsetAsync(JV, 0, sizeof(double) * c->n3(), c->stream));
     {
-      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes());
+      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes(), element_flops(c->dim, true) * c->n_elem);
       CK(launch_element<double>(c->dim, true, elem_args<double>(c, U, V, c->hs, c->adv, JV), c->stream));
     }
     CK(launch_row_fixups<double>(c->rows(), V, JV, 1, c->stream));
@@ -131,7 +150,7 @@ int ctx_prepare_f32(pnp_ctx* c, const double* U) {
 int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32) {
   if (c->use_patches) {
     {
-      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes());
+      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_flops(c->dim, true) * c->n_elem);
       CK(launch_patch<float>(c->dim, true, patch_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32, c->part32),
                              c->stream));
     }
@@ -139,7 +158,7 @@ int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32) {
   } else {
     CK(cudaMemsetAsync(JV32, 0, sizeof(float) * c->n3(), c->stream));
     {
-      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes());
+      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_flops(c->dim, true) * c->n_elem);
       CK(launch_element<float>(c->dim, true, elem_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32), c->stream));
     }
     CK(launch_row_fixups<float>(c->rows(), V32, JV32, 1, c->stream));
@@ -270,13 +289,13 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       // z = M^-1 (u_j / s_j) ; w = J z
       if (prec == PNP_F64) {
         {
-          ProfScope ps(c, PNP_PROF_PRECOND, 120.0 * c->n_nodes);
+          ProfScope ps(c, PNP_PROF_PRECOND, 120.0 * c->n_nodes, 18.0 * c->n_nodes);
           CK(launch_block_apply(c->n_nodes, c->Dinv, uj, 1.0 / sv[j], c->z, nullptr, s));
         }
         RC(ctx_jv64(c, U, c->z, w));
       } else {
         {
-          ProfScope ps(c, PNP_PROF_PRECOND, 108.0 * c->n_nodes);
+          ProfScope ps(c, PNP_PROF_PRECOND, 108.0 * c->n_nodes, 18.0 * c->n_nodes);
           CK(launch_block_apply(c->n_nodes, c->Dinv, uj, 1.0 / sv[j], nullptr, c->V32, s));
         }
         RC(ctx_jv32(c, c->V32, c->JV32));
@@ -285,17 +304,20 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       }
       double w1sq;
       {
-        // classical Gram-Schmidt applied twice (CGS2), one host round trip per iteration;
-        // the projections of both passes go to separate device slots
+        // classical Gram-Schmidt (a second pass when gmres_cgs2), one host round trip
+        // per iteration; the projections of the two passes go to separate device slots
         const bool two = c->prm.gmres_cgs2 != 0;
-        ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (double)n * ((two ? 4.0 : 2.0) * (j + 1) + (two ? 6.0 : 3.0)));
-        CK(launch_multi_dot_ext(n, j + 1, false, V, n, w, c->part, dd, s));
-        CK(launch_multi_axpy_norm(n, j + 1, V, n, dd, dinv, w, c->part, dnrm, s));
-        if (two) {
-          CK(launch_multi_dot_ext(n, j + 1, false, V, n, w, c->part, dd2, s));
-          CK(launch_multi_axpy_norm(n, j + 1, V, n, dd2, dinv, w, c->part, dnrm, s));
-          CK(cudaMemcpyAsync(hp2, dd2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+        const double nj = (double)n * (j + 1);
+        for (int pass = 0; pass < (two ? 2 : 1); ++pass) {
+          double* dp = pass == 0 ? dd : dd2;
+          {
+            ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (nj + n), 2.0 * nj);
+            CK(launch_multi_dot_ext(n, j + 1, false, V, n, w, c->part, dp, s));
+          }
+          ProfScope ps(c, PNP_PROF_ORTHO_UPDATE, 8.0 * (nj + 2.0 * n), 2.0 * (nj + n));
+          CK(launch_multi_axpy_norm(n, j + 1, V, n, dp, dinv, w, c->part, dnrm, s));
         }
+        if (two) CK(cudaMemcpyAsync(hp2, dd2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(hp, dd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(hp + (m + 1), dnrm, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -360,7 +382,7 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   return PNP_OK;
 }
 
-int ctx_newton(pnp_ctx* c, pnp_solve_stats* st) {
+int ctx_newton(pnp_ctx* c, pnp_solve_stats* st, const double* ref_state) {
   const double t0 = now_ms();
   std::memset(st, 0, sizeof(*st));
   const pnp_params& p = c->prm;
@@ -378,7 +400,17 @@ int ctx_newton(pnp_ctx* c, pnp_solve_stats* st) {
     st->status = PNP_ERR_NAN;
     PNP_FAIL(PNP_ERR_NAN, "newton: initial residual is not finite");
   }
-  const double target = std::max(p.newton_rtol * f0, p.newton_atol);
+  // the relative tolerance refers to ||F(ref_state)|| when given (the time step's
+  // previous-step state), else to the start's own residual
+  double f_ref = f0;
+  if (ref_state) {
+    CK(cudaMemcpyAsync(c->Ut, ref_state, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(launch_make_consistent(c->rows(), c->Ut, s));
+    RC(ctx_residual(c, c->Ut, c->Ft));
+    RC(ctx_norm(c, c->Ft, &f_ref));
+  }
+  st->res_ref = f_ref;
+  const double target = std::max(p.newton_rtol * f_ref, p.newton_atol);
   double f = f0, f_prev = f0, eta_prev = p.ew_eta_max;
   int it = 0, kry = 0;
   int rc = PNP_OK;
@@ -470,19 +502,61 @@ int ctx_newton(pnp_ctx* c, pnp_solve_stats* st) {
 
 int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st);  // mlp.cu
 
+// One Newton solve over `dt` (BDF2 or BDF1) from the start already in U, to a tolerance
+// relative to ||F(ref)|| (NULL: to the start's own residual); on success the history
+// shifts (U^{k-1} <- U^k <- U).  A failed solve with split depth left is redone as two
+// BDF1 half steps, each started from (and measured against) the previous state.
+static int advance(pnp_ctx* c, double dt, bool bdf2, int depth, const double* ref, pnp_solve_stats* tot) {
+  const int64_t n = c->n3();
+  cudaStream_t s = c->stream;
+  pnp_params& p = c->prm;
+  p.dt = dt;
+  if (bdf2) {
+    p.beta0 = 1.5; p.beta1 = -2.0; p.beta2 = 0.5;
+  } else {
+    p.beta0 = 1.0; p.beta1 = -1.0; p.beta2 = 0.0;
+  }
+  pnp_solve_stats one;
+  std::memset(&one, 0, sizeof(one));
+  const int rc = ctx_newton(c, &one, ref);
+  if (depth == 0) {
+    tot->res0 = one.res0;
+    tot->res_ref = one.res_ref;
+  }
+  tot->newton_its += one.newton_its;
+  tot->krylov_its += one.krylov_its;
+  tot->f64_fallbacks += one.f64_fallbacks;
+  tot->jv_evals = one.jv_evals;
+  tot->residual_evals = one.residual_evals;
+  tot->res_final = one.res_final;
+  tot->status = rc;
+  if (rc == PNP_OK) {
+    CK(cudaMemcpyAsync(c->Ukm1, c->Uk, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->Uk, c->U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    tot->substeps++;
+    return PNP_OK;
+  }
+  const bool recoverable = rc == PNP_ERR_NEWTON_DIVERGED || rc == PNP_ERR_KRYLOV_MAXIT || rc == PNP_ERR_NAN;
+  if (!recoverable || depth >= p.dt_retries) return rc;
+  if (p.monitor) fprintf(stderr, "[pnp step] Newton failed (status %d) at dt %.3e: two half steps\n", rc, dt);
+  for (int h = 0; h < 2; ++h) {
+    CK(cudaMemcpyAsync(c->U, c->Uk, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    RC(advance(c, 0.5 * dt, false, depth + 1, nullptr, tot));
+  }
+  return PNP_OK;
+}
+
 int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st) {
   const double t0 = now_ms();
   const int64_t n = c->n3();
   cudaStream_t s = c->stream;
   pnp_params& p = c->prm;
-  if (c->step == 0 || p.bdf_order == 1) {
-    p.beta0 = 1.0; p.beta1 = -1.0; p.beta2 = 0.0;
-  } else {
-    p.beta0 = 1.5; p.beta1 = -2.0; p.beta2 = 0.5;
-  }
+  // BDF2 needs U^{k-1} one full step behind U^k
+  const bool bdf2 = !(c->step == 0 || p.bdf_order == 1 || c->history_split);
   // advection at t^{k+1}: v~ = 2 v^k - v^{k-1} (Eq. averaging1)
   CK(launch_axpbyz(n, 2.0, c->vel, -1.0, c->vel_prev, c->adv, s));
   int start = p.start_mode;
+  if (c->history_split) start = PNP_START_PREVIOUS;  // extrapolation assumes equal spacing
   double r_extra = 0, r_learn = 0;
   if (start == PNP_START_LEARNED) {
     pnp_solve_stats tmp;
@@ -498,21 +572,31 @@ int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st) {
       return lrc;
     }
   }
-  if (start == PNP_START_PREVIOUS || (start == PNP_START_EXTRAPOLATE && c->step == 0)) {
+  if (start == PNP_START_EXTRAPOLATE && c->step == 0) start = PNP_START_PREVIOUS;  // no history yet
+  if (start == PNP_START_PREVIOUS) {
     CK(cudaMemcpyAsync(c->U, c->Uk, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   } else if (start == PNP_START_EXTRAPOLATE) {
     CK(launch_axpbyz(n, 2.0, c->Uk, -1.0, c->Ukm1, c->U, s));
   }  // learned: U already holds the judged start
-  const int rc = ctx_newton(c, st);
-  st->start_used = start;
-  st->res_start_extrapolated = r_extra;
-  st->res_start_learned = r_learn;
-  if (rc != PNP_OK) return rc;
-  CK(cudaMemcpyAsync(c->Ukm1, c->Uk, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(c->Uk, c->U, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  const double dt = p.dt;
+  pnp_solve_stats tot;
+  std::memset(&tot, 0, sizeof(tot));
+  // Newton's relative tolerance refers to the residual of the previous-step state U^k
+  // (the paper's start), so that every start is held to the same absolute tolerance
+  const int rc = advance(c, dt, bdf2, 0, start == PNP_START_PREVIOUS ? nullptr : c->Uk, &tot);
+  p.dt = dt;
+  tot.start_used = start;
+  tot.res_start_extrapolated = r_extra;
+  tot.res_start_learned = r_learn;
+  *st = tot;
+  if (rc != PNP_OK) {
+    st->wall_ms = now_ms() - t0;
+    return rc;
+  }
   CK(cudaMemcpyAsync(c->vel_prev, c->vel, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   c->step++;
+  c->history_split = tot.substeps > 1;
   st->wall_ms = now_ms() - t0;
   return PNP_OK;
 }

@@ -3,9 +3,11 @@
 The experiment: the 3D transient double-layer problem (unit cube, uniform level 5,
 32,768 elements, 35,937 nodes, Lambda = 0.01, dt = 1e-3; phi = V on z = 0 and 0 on
 z = 1, c+- = 1 on z = 1, zero flux elsewhere; c+- = 1 + seeded noise 1e-3, phi
-linear at t = 0).  Trajectories are recorded with the plain solver at V = 10, 20, 30,
-the network is trained on them, and the time steps at V = 25 (not seen in training)
-are then solved with the previous-step, extrapolated and learned (judged) starts.
+linear at t = 0, double layer developed by a BDF1 step-size ramp).  Trajectories are
+recorded with the FP32-J V inexact Newton solver at V = 10, 20, 30 (a step whose Newton
+solve fails is split into half steps), the network is trained on them, and the time
+steps at V = 25 (not seen in training) are then solved with the previous-step,
+extrapolated and learned (judged) starts.
 """
 from __future__ import annotations
 
@@ -19,7 +21,8 @@ def setup(pnp, W, torch, V, level=5, eps=0.01, dt=1e-3, seed=0, mode="plain"):
     mesh = pnp.Mesh(oc)
     prec = pnp.PNP_F64 if mode == "plain" else pnp.PNP_F32
     prm = pnp.default_params(eps=eps, dt=dt, newton_rtol=1e-8, gmres_rtol=1e-8, gmres_restart=60,
-                             gmres_max_it=4000, precision=prec, start_mode=pnp.PNP_START_EXTRAPOLATE)
+                             gmres_max_it=4000, precision=prec, start_mode=pnp.PNP_START_EXTRAPOLATE,
+                             dt_retries=3)
     ctx = pnp.Context(mesh, prm, torch.cuda.current_stream().cuda_stream)
     ctx.set_bcs(W.equilibrium_bcs(3, V))
     U0 = W.noisy_state(mesh.ijk, oc.max_level, seed=seed, amp=1e-3, phi_bottom=V, phi_top=0.0)
@@ -49,30 +52,33 @@ def develop_double_layer(pnp, ctx, dt, dt0=1e-6, factor=4.0):
 
 
 def record(pnp, torch, ctx, n_steps):
-    """Time-step the context and return the device tensor [n_steps+1, N, 3] of states."""
+    """Time-step the context and return the device tensor [k+1, N, 3] of states at the
+    full steps, k <= n_steps: recording stops at a step that fails even after splitting."""
     N = ctx.n_nodes
     S = torch.zeros((n_steps + 1, N, 3), dtype=torch.float64, device="cuda")
     ctx.get_field(pnp.PNP_FIELD_U, S[0], pnp.PNP_DEVICE)
     its = []
     for k in range(n_steps):
-        st = ctx.time_step()
+        st = ctx.time_step(raise_on_error=False)
+        if st.status != pnp.PNP_OK:
+            return S[:k + 1], its
         its.append(st.newton_its)
         ctx.get_field(pnp.PNP_FIELD_U, S[k + 1], pnp.PNP_DEVICE)
     return S, its
 
 
 def run(pnp, W, torch, train_V=(10.0, 20.0, 30.0), steps_per_V=667, test_V=25.0, test_steps=50, seeds=(0, 1, 2),
-        train_steps=3000, batch=4096, lr=1e-3, level=5, log=print):
+        train_steps=3000, batch=4096, lr=1e-3, level=5, mode="mixed", log=print):
     """Returns a dict of the experiment's numbers (training loss, per-start statistics)."""
     out = {"train_V": list(train_V), "steps_per_V": steps_per_V, "test_V": test_V, "test_steps": test_steps}
-    mesh, ctx = setup(pnp, W, torch, train_V[0], level=level)
+    mesh, ctx = setup(pnp, W, torch, train_V[0], level=level, mode=mode)
     ctx.mlp_init(seed=0)
     t0 = time.perf_counter()
     for V in train_V:
-        m2, c2 = setup(pnp, W, torch, V, level=level)
+        m2, c2 = setup(pnp, W, torch, V, level=level, mode=mode)
         S, its = record(pnp, torch, c2, steps_per_V)
         ctx.mlp_add_trajectory(S)
-        log(f"trajectory V={V}: {steps_per_V} steps, mean Newton its {np.mean(its):.2f}")
+        log(f"trajectory V={V}: {len(its)} of {steps_per_V} steps, mean Newton its {np.mean(its):.2f}")
         del S
         c2.close()
     out["record_s"] = time.perf_counter() - t0
@@ -82,16 +88,16 @@ def run(pnp, W, torch, train_V=(10.0, 20.0, 30.0), steps_per_V=667, test_V=25.0,
     weights = ctx.mlp_get_weights()
     norm = ctx.mlp_get_normalization()
     results = {}
-    for name, mode in (("previous", pnp.PNP_START_PREVIOUS), ("extrapolated", pnp.PNP_START_EXTRAPOLATE),
+    for name, start in (("previous", pnp.PNP_START_PREVIOUS), ("extrapolated", pnp.PNP_START_EXTRAPOLATE),
                        ("learned", pnp.PNP_START_LEARNED)):
-        its, kry, wall, used_learned, r0 = [], [], [], 0, []
+        its, kry, wall, used_learned, r0, splits = [], [], [], 0, [], 0
         for seed in seeds:
-            m3, c3 = setup(pnp, W, torch, test_V, level=level, seed=100 + seed)
-            if mode == pnp.PNP_START_LEARNED:
+            m3, c3 = setup(pnp, W, torch, test_V, level=level, seed=100 + seed, mode=mode)
+            if start == pnp.PNP_START_LEARNED:
                 c3.mlp_init(seed=0)
                 c3.mlp_set_weights(weights)
                 c3.mlp_set_normalization(*norm)
-            p = c3.get_params(); p.start_mode = mode
+            p = c3.get_params(); p.start_mode = start
             c3.set_params(p)
             for k in range(test_steps):
                 torch.cuda.synchronize()
@@ -105,12 +111,13 @@ def run(pnp, W, torch, train_V=(10.0, 20.0, 30.0), steps_per_V=667, test_V=25.0,
                 kry.append(s.krylov_its)
                 r0.append(s.res0)
                 used_learned += int(s.start_used == pnp.PNP_START_LEARNED)
+                splits += int(s.substeps > 1)
             c3.close()
         results[name] = {"newton_its_mean": float(np.mean(its)), "krylov_its_mean": float(np.mean(kry)),
                          "ms_per_step": 1e3 * float(np.mean(wall)), "res0_mean": float(np.mean(r0)),
-                         "learned_used": used_learned, "steps": len(its)}
+                         "learned_used": used_learned, "split_steps": splits, "steps": len(its)}
         log(f"{name:12s}: Newton {np.mean(its):.3f}  Krylov {np.mean(kry):.1f}  {1e3 * np.mean(wall):.2f} ms/step "
-            f" ||F0|| {np.mean(r0):.3e}  learned used {used_learned}/{len(its)}")
+            f" ||F0|| {np.mean(r0):.3e}  learned used {used_learned}/{len(its)}  split {splits}")
     out["results"] = results
     ctx.close()
     return out, weights, norm

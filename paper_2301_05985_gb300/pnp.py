@@ -46,7 +46,7 @@ class pnp_params(C.Structure):
         ("precision", C.c_int32), ("start_mode", C.c_int32),
         ("ew_eta_max", C.c_double), ("ew_eta_min", C.c_double),
         ("monitor", C.c_int32), ("f64_fallback", C.c_int32),
-        ("gmres_cgs2", C.c_int32), ("pad_", C.c_int32),
+        ("gmres_cgs2", C.c_int32), ("dt_retries", C.c_int32),
     ]
 
 
@@ -54,10 +54,10 @@ class pnp_solve_stats(C.Structure):
     _fields_ = [
         ("status", C.c_int32), ("newton_its", C.c_int32), ("krylov_its", C.c_int32),
         ("residual_evals", C.c_int32), ("jv_evals", C.c_int32), ("start_used", C.c_int32),
-        ("f64_fallbacks", C.c_int32), ("pad_", C.c_int32),
+        ("f64_fallbacks", C.c_int32), ("substeps", C.c_int32),
         ("res0", C.c_double), ("res_final", C.c_double),
         ("res_start_extrapolated", C.c_double), ("res_start_learned", C.c_double),
-        ("wall_ms", C.c_double),
+        ("wall_ms", C.c_double), ("res_ref", C.c_double),
     ]
 
     def as_dict(self):
@@ -113,7 +113,7 @@ SIGNATURES = {
     "pnp_step_count": (C.c_int, [_vp, _P(_i64)]),
     "pnp_reset_history": (C.c_int, [_vp]),
     "pnp_profile_enable": (C.c_int, [_vp, C.c_int]),
-    "pnp_profile_read": (C.c_int, [_vp, C.c_int, _P(_d), _P(_i64), _P(_d)]),
+    "pnp_profile_read": (C.c_int, [_vp, C.c_int, _P(_d), _P(_i64), _P(_d), _P(_d)]),
     "pnp_kernel_launches": (_i64, []),
     "pnp_mlp_init": (C.c_int, [_vp, C.c_uint64]),
     "pnp_mlp_set_weights": (C.c_int, [_vp, _vp, _i64]),
@@ -139,7 +139,7 @@ def mlp_forward_noalloc(params, X, Y, stream: int = 0):
 
 PNP_PROF_RESIDUAL, PNP_PROF_JV64, PNP_PROF_JV32, PNP_PROF_BLOCKDIAG = 0, 1, 2, 3
 PNP_PROF_ORTHO, PNP_PROF_PRECOND, PNP_PROF_MLP, PNP_PROF_KINDS = 4, 5, 6, 7
-PROF_NAMES = ["residual64", "jv64", "jv32", "blockdiag", "ortho", "precond", "mlp"]
+PROF_NAMES = ["residual64", "jv64", "jv32", "blockdiag", "ortho_dot", "precond", "mlp", "ortho_update"]
 
 
 def lib():
@@ -355,9 +355,9 @@ class Context:
     def profile_read(self) -> dict:
         out = {}
         for k, name in enumerate(PROF_NAMES):
-            ms, cnt, by = C.c_double(), C.c_int64(), C.c_double()
-            check(lib().pnp_profile_read(self.h, k, C.byref(ms), C.byref(cnt), C.byref(by)))
-            out[name] = {"ms": ms.value, "count": cnt.value, "alg_bytes": by.value}
+            ms, cnt, by, fl = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
+            check(lib().pnp_profile_read(self.h, k, C.byref(ms), C.byref(cnt), C.byref(by), C.byref(fl)))
+            out[name] = {"ms": ms.value, "count": cnt.value, "alg_bytes": by.value, "alg_flops": fl.value}
         return out
 
 
