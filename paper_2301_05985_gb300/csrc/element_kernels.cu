@@ -10,6 +10,8 @@
 // tau = (4/dt^2 + (2/h)^2 |v|^2 + C_I d (2/h)^4)^(-1/2).  J V is the exact directional
 // derivative (the residual is cubic in U; tau does not depend on U).
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 
 #include "element_kernels.cuh"
 #include "kernels.h"
@@ -602,9 +604,45 @@ inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
+// Element kernel of launch_element: one lane group per element unless
+// PNP_ELEMENT_KERNEL=thread selects one thread per element (modal sum factorisation).
+static bool per_thread_elements() {
+  static const bool v = [] {
+    const char* e = getenv("PNP_ELEMENT_KERNEL");
+    return e && strcmp(e, "thread") == 0;
+  }();
+  return v;
+}
+
+double element_kernel_flops(int D, bool jv) {
+  const double NC = 1 << D;
+  if (per_thread_elements()) {
+    // modal form: nodal -> modal transforms, per Gauss point values / gradients from
+    // the modal coefficients, physics, test contraction, modal -> nodal
+    const double val = 2 * NC, grad = D * (NC + 1);
+    const double to_m = D * NC + NC, from_m = D * NC + 2 * NC;
+    const double acc = 2 * D + (NC - 1) + 2 * NC;
+    const double common = 2 * val + 2 * grad + 2 * val + grad + D * val + 2 * D + 3 + 2 * (3 * D + 3);
+    const double poisson = 4 + D + acc;
+    if (!jv) return NC * (common + 2 * (6 * D + 4 + acc) + poisson) + 8 * to_m + 3 * from_m;
+    return NC * (common + 2 * val + 3 * grad + 2 * (12 * D + 8 + acc) + poisson) + 11 * to_m + 3 * from_m;
+  }
+  // lane form, per lane: axis stages of the value/gradient interpolation (3 flops per
+  // interpolated track, 2 per new derivative), the physics at the lane's Gauss point,
+  // and the transposed stages of the three test fields
+  const double tri = D * (D - 1) / 2.0;
+  const double vg = 3 * tri + 5 * D, g = vg - 3, v = 3 * D, tt = 6 * D + 3 * tri + 1;
+  const double state = 2 * vg + 2 * v + g + D * v + 2 * D + 3 + 30;
+  const double phys = jv ? 2 * vg + g + 101 : 53;
+  return NC * (state + phys + 3 * tt);
+}
+
 template <typename T>
 cudaError_t launch_element(int dim, bool jv, const ElemArgs<T>& A, cudaStream_t s) {
   if (A.n_elem == 0) return cudaSuccess;
+  // default: one lane group per element; PNP_ELEMENT_KERNEL=thread selects one thread
+  // per element (modal sum factorisation in registers)
+  if (!per_thread_elements()) return launch_element_lanes<T>(dim, jv, A, s);
   const int t = 128;
   if (dim == 2) {
     if (jv) { k_element<T, 2, true><<<nblk(A.n_elem, t), t, 0, s>>>(A); note_launch(); }

@@ -1,0 +1,260 @@
+// element_lanes.cu -- the VMS PNP residual and its Jacobian action with one lane group
+// per element: 2^d lanes of a warp share an element, lane c holds corner c and the
+// Gauss point next to it.
+//
+// Physics per Gauss point as in Def. 3 of arXiv 2301.05985 with the fine scales
+// c^f = -tau_c R_c (Sec. 3.1; the same statement as element_kernels.cu).  Interpolation
+// is a tensor product of 1D operators on the two nodes of an axis: at the Gauss point
+// next to node b (xi = -g for b = 0, +g for b = 1, g = 1/sqrt 3)
+//     value:       a u_b + b' u_{1-b},       a = (1 + g)/2, b' = (1 - g)/2
+//     derivative:  (u_1 - u_0) / h           (constant along the axis)
+// applied axis by axis with the partner value fetched by a lane shuffle (lane ^ 2^k).
+// The test side (element vector r_c = w sum_q [N_c(q) S_q + grad N_c(q) . Phi_q], w =
+// (h/2)^d) is the transpose: the value operator is symmetric and the derivative's
+// transpose sends s_b (x_0 + x_1) / h to node b (s_0 = -1, s_1 = +1).
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace {
+
+constexpr double kG = 0.57735026918962576450914878050196;  // 1/sqrt(3)
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T flip(T x, int k) {
+  return __shfl_xor_sync(kFull, x, 1 << k);
+}
+
+// value and gradient at this lane's Gauss point from this lane's nodal value x
+template <typename T, int D>
+__device__ __forceinline__ void interp_vg(T x, T a, T b, const T (&sh)[3], T& val, T (&g)[3]) {
+  T I = x;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const T pI = flip(I, k);
+    T pG[3];
+#pragma unroll
+    for (int j = 0; j < k; ++j) pG[j] = flip(g[j], k);
+#pragma unroll
+    for (int j = 0; j < k; ++j) g[j] = fma(a, g[j], b * pG[j]);
+    g[k] = sh[k] * (I - pI);
+    I = fma(a, I, b * pI);
+  }
+#pragma unroll
+  for (int k = D; k < 3; ++k) g[k] = T(0);
+  val = I;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void interp_g(T x, T a, T b, const T (&sh)[3], T (&g)[3]) {
+  T I = x;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const T pI = flip(I, k);
+    T pG[3];
+#pragma unroll
+    for (int j = 0; j < k; ++j) pG[j] = flip(g[j], k);
+#pragma unroll
+    for (int j = 0; j < k; ++j) g[j] = fma(a, g[j], b * pG[j]);
+    g[k] = sh[k] * (I - pI);
+    if (k + 1 < D) I = fma(a, I, b * pI);
+  }
+#pragma unroll
+  for (int k = D; k < 3; ++k) g[k] = T(0);
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T interp_v(T x, T a, T b) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) x = fma(a, x, b * flip(x, k));
+  return x;
+}
+
+// transpose: this lane's node contribution from the Gauss-point tests S, Phi
+template <typename T, int D>
+__device__ __forceinline__ T test_t(T S, T (&Phi)[3], T a, T b, const T (&sh)[3]) {
+  T A = S;
+#pragma unroll
+  for (int k = D - 1; k >= 0; --k) {
+    const T pA = flip(A, k);
+    const T pH = flip(Phi[k], k);
+    T pP[3];
+#pragma unroll
+    for (int j = 0; j < k; ++j) pP[j] = flip(Phi[j], k);
+    A = fma(a, A, fma(b, pA, sh[k] * (Phi[k] + pH)));
+#pragma unroll
+    for (int j = 0; j < k; ++j) Phi[j] = fma(a, Phi[j], b * pP[j]);
+  }
+  return A;
+}
+
+// nodal values of NF interleaved fields at node id (hanging: the parents' mean)
+template <typename T, int NF>
+__device__ __forceinline__ void load_node(const ElemArgs<T>& A, int32_t id, bool valid, const T* __restrict__ src,
+                                          int stride, T (&dst)[NF]) {
+#pragma unroll
+  for (int f = 0; f < NF; ++f) dst[f] = T(0);
+  if (!valid) return;
+  if (id >= 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dst[f] = __ldg(src + (int64_t)stride * id + f);
+  } else {
+    const int32_t h = -id - 1;
+    const int np = A.hang_np[h];
+    const T wgt = np == 2 ? T(0.5) : T(0.25);
+    for (int p = 0; p < np; ++p) {
+      const int32_t pid = A.hang_par[4 * h + p];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) dst[f] += wgt * __ldg(src + (int64_t)stride * pid + f);
+    }
+  }
+}
+
+template <typename T, int D, bool JV>
+__global__ void __launch_bounds__(256) k_element_lanes(ElemArgs<T> A) {
+  constexpr int NC = 1 << D;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // warps whose first element is past the end leave together (shuffles need the warp)
+  if ((t & ~int64_t(31)) / NC >= A.n_elem) return;
+  const int64_t e = t / NC;
+  const int c = (int)(t & (NC - 1));
+  const bool valid = e < A.n_elem;
+  const int32_t id = valid ? __ldg(A.conn + e * NC + c) : 0;
+  const int lev = valid ? A.level[e] : 0;
+
+  const T h = T(ldexp(1.0, -lev));
+  const T inv_h = T(ldexp(1.0, lev));
+  const T a = T(0.5 * (1.0 + kG)), b = T(0.5 * (1.0 - kG));
+  T sh[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sh[k] = ((c >> k) & 1) ? inv_h : -inv_h;
+  T w = T(1);
+#pragma unroll
+  for (int k = 0; k < D; ++k) w *= T(0.5) * h;
+  const T G2 = T(4.0) * inv_h * inv_h;  // (2/h)^2
+  const T kappa = T(A.P.kappa);
+  const T tau0 = T(A.P.tau_t) + T(A.P.C_I * D) * G2 * G2;
+  const T e2 = T(A.P.eps2x2);
+
+  T un[3], vn[3], hn[2];
+  load_node<T, 3>(A, id, valid, A.U, 3, un);
+  load_node<T, 3>(A, id, valid, A.adv, 3, vn);
+  load_node<T, 2>(A, id, valid, A.hs, 2, hn);
+
+  // state at this lane's Gauss point
+  T cv[2], gc[2][3], gp[3], v[3] = {T(0), T(0), T(0)}, hq[2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    interp_vg<T, D>(un[s], a, b, sh, cv[s], gc[s]);
+    hq[s] = interp_v<T, D>(hn[s], a, b);
+  }
+  interp_g<T, D>(un[2], a, b, sh, gp);
+  T vv = T(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    v[k] = interp_v<T, D>(vn[k], a, b);
+    vv = fma(v[k], v[k], vv);
+  }
+  T tau;
+  if constexpr (sizeof(T) == 4) tau = rsqrtf(tau0 + G2 * vv);
+  else tau = T(1) / sqrt(tau0 + G2 * vv);
+  T R[2], P[2][3];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T z = s == 0 ? T(1) : T(-1);
+    T pg = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      P[s][k] = v[k] - z * gp[k];
+      pg = fma(P[s][k], gc[s][k], pg);
+    }
+    R[s] = fma(kappa, cv[s], hq[s] + pg);
+  }
+
+  T S[3], Phi[3][3];
+  if constexpr (!JV) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const T z = s == 0 ? T(1) : T(-1);
+      T vg = T(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) vg = fma(v[k], gc[s][k], vg);
+      S[s] = fma(kappa, cv[s], hq[s] + vg);
+      const T tR = tau * R[s];
+      const T zc = z * cv[s];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Phi[s][k] = fma(tR, P[s][k], fma(zc, gp[k], gc[s][k]));
+    }
+    S[2] = fma(tau, R[0] - R[1], cv[1] - cv[0]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Phi[2][k] = e2 * gp[k];
+  } else {
+    T dn[3];
+    load_node<T, 3>(A, id, valid, A.V, 3, dn);
+    T dcv[2], dgc[2][3], dgp[3], dR[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) interp_vg<T, D>(dn[s], a, b, sh, dcv[s], dgc[s]);
+    interp_g<T, D>(dn[2], a, b, sh, dgp);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const T z = s == 0 ? T(1) : T(-1);
+      T vg = T(0), pg = T(0), gcd = T(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        vg = fma(v[k], dgc[s][k], vg);
+        pg = fma(P[s][k], dgc[s][k], pg);
+        gcd = fma(gc[s][k], dgp[k], gcd);
+      }
+      dR[s] = fma(kappa, dcv[s], pg - z * gcd);
+      S[s] = fma(kappa, dcv[s], vg);
+      const T tdR = tau * dR[s];
+      const T zdc = z * dcv[s];
+      const T zc_tR = z * (cv[s] - tau * R[s]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Phi[s][k] = fma(tdR, P[s][k], fma(zc_tR, dgp[k], fma(zdc, gp[k], dgc[s][k])));
+    }
+    S[2] = fma(tau, dR[0] - dR[1], dcv[1] - dcv[0]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Phi[2][k] = e2 * dgp[k];
+  }
+
+  T r[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) r[f] = w * test_t<T, D>(S[f], Phi[f], a, b, sh);
+  if (!valid) return;
+  if (id >= 0) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)id + f, r[f]);
+  } else {
+    const int32_t hh = -id - 1;
+    const int np = A.hang_np[hh];
+    const T wgt = np == 2 ? T(0.5) : T(0.25);
+    for (int p = 0; p < np; ++p) {
+      const int32_t pid = A.hang_par[4 * hh + p];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)pid + f, wgt * r[f]);
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_element_lanes(int dim, bool jv, const ElemArgs<T>& A, cudaStream_t s) {
+  if (A.n_elem == 0) return cudaSuccess;
+  const int t = 256;
+  const int64_t threads = A.n_elem << dim;
+  const unsigned blocks = (unsigned)((threads + t - 1) / t);
+  if (dim == 2) {
+    if (jv) k_element_lanes<T, 2, true><<<blocks, t, 0, s>>>(A);
+    else k_element_lanes<T, 2, false><<<blocks, t, 0, s>>>(A);
+  } else {
+    if (jv) k_element_lanes<T, 3, true><<<blocks, t, 0, s>>>(A);
+    else k_element_lanes<T, 3, false><<<blocks, t, 0, s>>>(A);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_element_lanes<double>(int, bool, const ElemArgs<double>&, cudaStream_t);
+template cudaError_t launch_element_lanes<float>(int, bool, const ElemArgs<float>&, cudaStream_t);

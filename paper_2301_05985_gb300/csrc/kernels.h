@@ -53,6 +53,12 @@ cudaError_t launch_patch(int dim, bool jv, const PatchArgs<T>& A, cudaStream_t s
 
 template <typename T>
 cudaError_t launch_element(int dim, bool jv, const ElemArgs<T>& A, cudaStream_t s);
+// the same operator with 2^dim lanes per element (element_lanes.cu)
+template <typename T>
+cudaError_t launch_element_lanes(int dim, bool jv, const ElemArgs<T>& A, cudaStream_t s);
+// floating-point operations per element (an FMA counts 2) of the element kernel that
+// launch_element runs, counted from the formulation it evaluates
+double element_kernel_flops(int dim, bool jv);
 template <typename T>
 cudaError_t launch_block_diag(int dim, const ElemArgs<T>& A, T* Dout, cudaStream_t s);
 template <typename T>

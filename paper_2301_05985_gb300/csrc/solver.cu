@@ -82,28 +82,11 @@ static int hanging_rows(pnp_ctx* c, const T* in, T* out) {
   return ctx_check(c, launch_row_fixups<T>(R, in, out, 0, c->stream), "hanging rows");
 }
 
-// Floating-point operations per element of the element kernels (an FMA counts 2),
-// counted from the modal formulation they evaluate: nodal -> modal transforms of the
-// inputs, per Gauss point the values and gradients, physics and test contraction, and
-// the modal -> nodal transform of the three element-vector fields.
-static double element_flops(int D, bool jv) {
-  const double NC = 1 << D;
-  const double val = 2 * NC, grad = D * (NC + 1);
-  const double to_m = D * NC + NC, from_m = D * NC + 2 * NC;
-  const double acc = 2 * D + (NC - 1) + 2 * NC;
-  // c+- values and gradients, history values, grad phi, advection, |v|^2, tau, P_s, R_s
-  const double common = 2 * val + 2 * grad + 2 * val + grad + D * val + 2 * D + 3 + 2 * (3 * D + 3);
-  const double poisson = 4 + D + acc;
-  if (!jv) return NC * (common + 2 * (6 * D + 4 + acc) + poisson) + 8 * to_m + 3 * from_m;
-  const double dir = 2 * val + 3 * grad;  // direction values and gradients
-  return NC * (common + dir + 2 * (12 * D + 8 + acc) + poisson) + 11 * to_m + 3 * from_m;
-}
-
 int ctx_residual(pnp_ctx* c, const double* U, double* F) {
   if (c->use_patches) {
     {
       ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes(),
-                   element_flops(c->dim, false) * c->n_elem);
+                   element_kernel_flops(c->dim, false) * c->n_elem);
       CK(launch_patch<double>(c->dim, false, patch_args<double>(c, U, nullptr, c->hs, c->adv, F, c->part64),
                               c->stream));
     }
@@ -112,7 +95,7 @@ int ctx_residual(pnp_ctx* c, const double* U, double* F) {
     CK(cudaMemsetAsync(F, 0, sizeof(double) * c->n3(), c->stream));
     {
       ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes(),
-                   element_flops(c->dim, false) * c->n_elem);
+                   element_kernel_flops(c->dim, false) * c->n_elem);
       CK(launch_element<double>(c->dim, false, elem_args<double>(c, U, nullptr, c->hs, c->adv, F), c->stream));
     }
     CK(launch_row_fixups<double>(c->rows(), U, F, 0, c->stream));
@@ -124,14 +107,14 @@ int ctx_residual(pnp_ctx* c, const double* U, double* F) {
 int ctx_jv64(pnp_ctx* c, const double* U, const double* V, double* JV) {
   if (c->use_patches) {
     {
-      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes(), element_flops(c->dim, true) * c->n_elem);
+      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes(), element_kernel_flops(c->dim, true) * c->n_elem);
       CK(launch_patch<double>(c->dim, true, patch_args<double>(c, U, V, c->hs, c->adv, JV, c->part64), c->stream));
     }
     RC(hanging_rows<double>(c, V, JV));
   } else {
     CK(cudaMemsetAsync(JV, 0, sizeof(double) * c->n3(), c->stream));
     {
-      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes(), element_flops(c->dim, true) * c->n_elem);
+      ProfScope ps(c, PNP_PROF_JV64, 112.0 * c->n_nodes + c->conn_bytes(), element_kernel_flops(c->dim, true) * c->n_elem);
       CK(launch_element<double>(c->dim, true, elem_args<double>(c, U, V, c->hs, c->adv, JV), c->stream));
     }
     CK(launch_row_fixups<double>(c->rows(), V, JV, 1, c->stream));
@@ -150,7 +133,7 @@ int ctx_prepare_f32(pnp_ctx* c, const double* U) {
 int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32) {
   if (c->use_patches) {
     {
-      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_flops(c->dim, true) * c->n_elem);
+      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_kernel_flops(c->dim, true) * c->n_elem);
       CK(launch_patch<float>(c->dim, true, patch_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32, c->part32),
                              c->stream));
     }
@@ -158,7 +141,7 @@ int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32) {
   } else {
     CK(cudaMemsetAsync(JV32, 0, sizeof(float) * c->n3(), c->stream));
     {
-      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_flops(c->dim, true) * c->n_elem);
+      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_kernel_flops(c->dim, true) * c->n_elem);
       CK(launch_element<float>(c->dim, true, elem_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32), c->stream));
     }
     CK(launch_row_fixups<float>(c->rows(), V32, JV32, 1, c->stream));

@@ -124,12 +124,27 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_dot_ext(int64_t n, int k,
   }
 }
 
+// Sum over the warp of four per-lane values at once (reduce-scatter: 6 adds per lane
+// instead of 4 x 5); lanes 8q .. 8q+7 end with the total of s[q].  Fixed order.
+__device__ __forceinline__ double warp_sum4(const double (&s)[4], int lane) {
+  const bool hi4 = lane & 16, hi3 = lane & 8;
+  const double a0 = (hi4 ? s[2] : s[0]) + __shfl_xor_sync(0xffffffffu, hi4 ? s[0] : s[2], 16);
+  const double a1 = (hi4 ? s[3] : s[1]) + __shfl_xor_sync(0xffffffffu, hi4 ? s[1] : s[3], 16);
+  double b = (hi3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, hi3 ? a0 : a1, 8);
+  b += __shfl_xor_sync(0xffffffffu, b, 4);
+  b += __shfl_xor_sync(0xffffffffu, b, 2);
+  b += __shfl_xor_sync(0xffffffffu, b, 1);
+  return b;
+}
+
 // d_i = V_i . w (i < k; and w . w as entry k when kk > k).  Each block owns a contiguous
 // chunk of kMdRows x 256 rows: w's rows stay in registers while the block sweeps the basis
-// one vector at a time (kMdRows independent loads per thread per vector, warp-shuffle
-// reduction, fixed order).  Per-block partials part[block][kk].
-constexpr int kMdRows = 8;
-__global__ void __launch_bounds__(256) k_multi_dot2(int64_t n, int k, int kk, const double* __restrict__ Vb,
+// four vectors at a time (4 x kMdRows independent loads per thread, one reduce-scatter
+// over the warp, fixed order).  The FP64 pipe bounds the kernel on GB300, so the rows per
+// thread are many enough that the reduction adds stay small next to the FMAs.  Per-block
+// partials part[block][kk].
+constexpr int kMdRows = 16;
+__global__ void __launch_bounds__(256, 4) k_multi_dot2(int64_t n, int k, int kk, const double* __restrict__ Vb,
                                                     int64_t ld, const double* __restrict__ w,
                                                     double* __restrict__ part) {
   __shared__ double sh[64][8];
@@ -158,14 +173,9 @@ __global__ void __launch_bounds__(256) k_multi_dot2(int64_t n, int k, int kk, co
           }
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
-      if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (j0 + q < cnt) sh[j0 + q][wid] = s[q];
+      const double tot = warp_sum4(s, lane);
+      const int q = (lane >> 3) & 3;
+      if ((lane & 7) == 0 && j0 + q < cnt) sh[j0 + q][wid] = tot;
     }
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
@@ -189,17 +199,15 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy_norm(int64_t n, int 
   __syncthreads();
   double ss = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    // independent partial sums so the loads of several basis vectors are in flight at once
-    double v0 = w[t], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    // two independent chains (the loads are independent anyway); one add to join them
+    double v0 = w[t], v1 = 0.0;
     int i = 0;
-    for (; i + 4 <= k; i += 4) {
+    for (; i + 2 <= k; i += 2) {
       v0 -= cf[i] * Vb[(int64_t)i * ld + t];
       v1 -= cf[i + 1] * Vb[(int64_t)(i + 1) * ld + t];
-      v2 -= cf[i + 2] * Vb[(int64_t)(i + 2) * ld + t];
-      v3 -= cf[i + 3] * Vb[(int64_t)(i + 3) * ld + t];
     }
-    for (; i < k; ++i) v0 -= cf[i] * Vb[(int64_t)i * ld + t];
-    const double v = (v0 + v1) + (v2 + v3);
+    if (i < k) v0 -= cf[i] * Vb[(int64_t)i * ld + t];
+    const double v = v0 + v1;
     w[t] = v;
     ss += v * v;
   }
