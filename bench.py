@@ -194,6 +194,22 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (replicas: every rank times the same work)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, ms):
+    """Whole-job GDoF/s: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def load_traffic(small: bool):
     """Per-class DRAM traffic from the committed ncu summary, for kernels whose source
     is unchanged since the capture."""
@@ -333,12 +349,8 @@ def main():
     prof = ctx.profile_read()
     ctx.profile_enable(False)
     launches = pnp.kernel_launches() - launches0
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = 3.0 * N * args.steps * world / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = replica_throughput(3.0 * N * args.steps, world, ms)
 
     # end to end through the C ABI with the state held in pinned host memory
     e2e = None

@@ -628,10 +628,10 @@ double element_kernel_flops(int D, bool jv) {
     return NC * (common + 2 * val + 3 * grad + 2 * (12 * D + 8 + acc) + poisson) + 11 * to_m + 3 * from_m;
   }
   // lane form, per lane: axis stages of the value/gradient interpolation (3 flops per
-  // interpolated track, 2 per new derivative), the physics at the lane's Gauss point,
-  // and the transposed stages of the three test fields
+  // interpolated track, 4 per value + new derivative from one difference), the physics
+  // at the lane's Gauss point, and the transposed stages of the three test fields
   const double tri = D * (D - 1) / 2.0;
-  const double vg = 3 * tri + 5 * D, g = vg - 3, v = 3 * D, tt = 6 * D + 3 * tri + 1;
+  const double vg = 3 * tri + 4 * D, g = vg - 2, v = 3 * D, tt = 6 * D + 3 * tri + 1;
   const double state = 2 * vg + 2 * v + g + D * v + 2 * D + 3 + 30;
   const double phys = jv ? 2 * vg + g + 101 : 53;
   return NC * (state + phys + 3 * tt);

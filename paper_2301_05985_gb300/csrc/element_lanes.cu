@@ -6,9 +6,12 @@
 // c^f = -tau_c R_c (Sec. 3.1; the same statement as element_kernels.cu).  Interpolation
 // is a tensor product of 1D operators on the two nodes of an axis: at the Gauss point
 // next to node b (xi = -g for b = 0, +g for b = 1, g = 1/sqrt 3)
-//     value:       a u_b + b' u_{1-b},       a = (1 + g)/2, b' = (1 - g)/2
+//     value:       a u_b + b' u_{1-b} = u_b - b' (u_b - u_{1-b}),   a = (1 + g)/2, b' = (1 - g)/2
 //     derivative:  (u_1 - u_0) / h           (constant along the axis)
-// applied axis by axis with the partner value fetched by a lane shuffle (lane ^ 2^k).
+// applied axis by axis with the partner value fetched by a lane shuffle (lane ^ 2^k);
+// value and derivative share the difference u_b - u_{1-b}.  The FP32 kernels execute no
+// FP64 instruction (GB300 runs FP64 at 1/64 of the FP32 rate): powers of two come from
+// the exponent bits and the parameters arrive converted.
 // The test side (element vector r_c = w sum_q [N_c(q) S_q + grad N_c(q) . Phi_q], w =
 // (h/2)^d) is the transpose: the value operator is symmetric and the derivative's
 // transpose sends s_b (x_0 + x_1) / h to node b (s_0 = -1, s_1 = +1).
@@ -27,8 +30,9 @@ __device__ __forceinline__ T flip(T x, int k) {
 }
 
 // value and gradient at this lane's Gauss point from this lane's nodal value x
+// (nb = -b': the value operator is x - b' (x - partner))
 template <typename T, int D>
-__device__ __forceinline__ void interp_vg(T x, T a, T b, const T (&sh)[3], T& val, T (&g)[3]) {
+__device__ __forceinline__ void interp_vg(T x, T nb, const T (&sh)[3], T& val, T (&g)[3]) {
   T I = x;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -37,9 +41,10 @@ __device__ __forceinline__ void interp_vg(T x, T a, T b, const T (&sh)[3], T& va
 #pragma unroll
     for (int j = 0; j < k; ++j) pG[j] = flip(g[j], k);
 #pragma unroll
-    for (int j = 0; j < k; ++j) g[j] = fma(a, g[j], b * pG[j]);
-    g[k] = sh[k] * (I - pI);
-    I = fma(a, I, b * pI);
+    for (int j = 0; j < k; ++j) g[j] = fma(nb, g[j] - pG[j], g[j]);
+    const T d = I - pI;
+    g[k] = sh[k] * d;
+    I = fma(nb, d, I);
   }
 #pragma unroll
   for (int k = D; k < 3; ++k) g[k] = T(0);
@@ -47,7 +52,7 @@ __device__ __forceinline__ void interp_vg(T x, T a, T b, const T (&sh)[3], T& va
 }
 
 template <typename T, int D>
-__device__ __forceinline__ void interp_g(T x, T a, T b, const T (&sh)[3], T (&g)[3]) {
+__device__ __forceinline__ void interp_g(T x, T nb, const T (&sh)[3], T (&g)[3]) {
   T I = x;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -56,24 +61,25 @@ __device__ __forceinline__ void interp_g(T x, T a, T b, const T (&sh)[3], T (&g)
 #pragma unroll
     for (int j = 0; j < k; ++j) pG[j] = flip(g[j], k);
 #pragma unroll
-    for (int j = 0; j < k; ++j) g[j] = fma(a, g[j], b * pG[j]);
-    g[k] = sh[k] * (I - pI);
-    if (k + 1 < D) I = fma(a, I, b * pI);
+    for (int j = 0; j < k; ++j) g[j] = fma(nb, g[j] - pG[j], g[j]);
+    const T d = I - pI;
+    g[k] = sh[k] * d;
+    if (k + 1 < D) I = fma(nb, d, I);
   }
 #pragma unroll
   for (int k = D; k < 3; ++k) g[k] = T(0);
 }
 
 template <typename T, int D>
-__device__ __forceinline__ T interp_v(T x, T a, T b) {
+__device__ __forceinline__ T interp_v(T x, T nb) {
 #pragma unroll
-  for (int k = 0; k < D; ++k) x = fma(a, x, b * flip(x, k));
+  for (int k = 0; k < D; ++k) x = fma(nb, x - flip(x, k), x);
   return x;
 }
 
 // transpose: this lane's node contribution from the Gauss-point tests S, Phi
 template <typename T, int D>
-__device__ __forceinline__ T test_t(T S, T (&Phi)[3], T a, T b, const T (&sh)[3]) {
+__device__ __forceinline__ T test_t(T S, T (&Phi)[3], T nb, const T (&sh)[3]) {
   T A = S;
 #pragma unroll
   for (int k = D - 1; k >= 0; --k) {
@@ -82,12 +88,27 @@ __device__ __forceinline__ T test_t(T S, T (&Phi)[3], T a, T b, const T (&sh)[3]
     T pP[3];
 #pragma unroll
     for (int j = 0; j < k; ++j) pP[j] = flip(Phi[j], k);
-    A = fma(a, A, fma(b, pA, sh[k] * (Phi[k] + pH)));
+    A = fma(nb, A - pA, fma(sh[k], Phi[k] + pH, A));
 #pragma unroll
-    for (int j = 0; j < k; ++j) Phi[j] = fma(a, Phi[j], b * pP[j]);
+    for (int j = 0; j < k; ++j) Phi[j] = fma(nb, Phi[j] - pP[j], Phi[j]);
   }
   return A;
 }
+
+// 2^e exactly, from the exponent bits (|e| well inside the exponent range)
+__device__ __forceinline__ float pow2i(int e, float) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ double pow2i(int e, double) {
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// physical parameters in the kernel's arithmetic type
+template <typename T>
+struct LaneParams {
+  T kappa;   // beta0 / dt
+  T tau_t;   // 4 / dt^2
+  T cid;     // C_I d
+  T e2;      // 2 Lambda^2
+};
 
 // nodal values of NF interleaved fields at node id (hanging: the parents' mean)
 template <typename T, int NF>
@@ -112,7 +133,7 @@ __device__ __forceinline__ void load_node(const ElemArgs<T>& A, int32_t id, bool
 }
 
 template <typename T, int D, bool JV>
-__global__ void __launch_bounds__(256) k_element_lanes(ElemArgs<T> A) {
+__global__ void __launch_bounds__(256) k_element_lanes(ElemArgs<T> A, LaneParams<T> K) {
   constexpr int NC = 1 << D;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // warps whose first element is past the end leave together (shuffles need the warp)
@@ -123,19 +144,16 @@ __global__ void __launch_bounds__(256) k_element_lanes(ElemArgs<T> A) {
   const int32_t id = valid ? __ldg(A.conn + e * NC + c) : 0;
   const int lev = valid ? A.level[e] : 0;
 
-  const T h = T(ldexp(1.0, -lev));
-  const T inv_h = T(ldexp(1.0, lev));
-  const T a = T(0.5 * (1.0 + kG)), b = T(0.5 * (1.0 - kG));
+  const T inv_h = pow2i(lev, T(0));
+  const T w = pow2i(-D * (lev + 1), T(0));  // (h/2)^D
+  const T nb = T(-0.5 * (1.0 - kG));
   T sh[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) sh[k] = ((c >> k) & 1) ? inv_h : -inv_h;
-  T w = T(1);
-#pragma unroll
-  for (int k = 0; k < D; ++k) w *= T(0.5) * h;
-  const T G2 = T(4.0) * inv_h * inv_h;  // (2/h)^2
-  const T kappa = T(A.P.kappa);
-  const T tau0 = T(A.P.tau_t) + T(A.P.C_I * D) * G2 * G2;
-  const T e2 = T(A.P.eps2x2);
+  const T G2 = pow2i(2 * lev + 2, T(0));  // (2/h)^2
+  const T kappa = K.kappa;
+  const T tau0 = fma(K.cid * G2, G2, K.tau_t);
+  const T e2 = K.e2;
 
   T un[3], vn[3], hn[2];
   load_node<T, 3>(A, id, valid, A.U, 3, un);
@@ -146,14 +164,14 @@ __global__ void __launch_bounds__(256) k_element_lanes(ElemArgs<T> A) {
   T cv[2], gc[2][3], gp[3], v[3] = {T(0), T(0), T(0)}, hq[2];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
-    interp_vg<T, D>(un[s], a, b, sh, cv[s], gc[s]);
-    hq[s] = interp_v<T, D>(hn[s], a, b);
+    interp_vg<T, D>(un[s], nb, sh, cv[s], gc[s]);
+    hq[s] = interp_v<T, D>(hn[s], nb);
   }
-  interp_g<T, D>(un[2], a, b, sh, gp);
+  interp_g<T, D>(un[2], nb, sh, gp);
   T vv = T(0);
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    v[k] = interp_v<T, D>(vn[k], a, b);
+    v[k] = interp_v<T, D>(vn[k], nb);
     vv = fma(v[k], v[k], vv);
   }
   T tau;
@@ -194,8 +212,8 @@ __global__ void __launch_bounds__(256) k_element_lanes(ElemArgs<T> A) {
     load_node<T, 3>(A, id, valid, A.V, 3, dn);
     T dcv[2], dgc[2][3], dgp[3], dR[2];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) interp_vg<T, D>(dn[s], a, b, sh, dcv[s], dgc[s]);
-    interp_g<T, D>(dn[2], a, b, sh, dgp);
+    for (int s = 0; s < 2; ++s) interp_vg<T, D>(dn[s], nb, sh, dcv[s], dgc[s]);
+    interp_g<T, D>(dn[2], nb, sh, dgp);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const T z = s == 0 ? T(1) : T(-1);
@@ -221,7 +239,7 @@ __global__ void __launch_bounds__(256) k_element_lanes(ElemArgs<T> A) {
 
   T r[3];
 #pragma unroll
-  for (int f = 0; f < 3; ++f) r[f] = w * test_t<T, D>(S[f], Phi[f], a, b, sh);
+  for (int f = 0; f < 3; ++f) r[f] = w * test_t<T, D>(S[f], Phi[f], nb, sh);
   if (!valid) return;
   if (id >= 0) {
 #pragma unroll
@@ -246,12 +264,13 @@ cudaError_t launch_element_lanes(int dim, bool jv, const ElemArgs<T>& A, cudaStr
   const int t = 256;
   const int64_t threads = A.n_elem << dim;
   const unsigned blocks = (unsigned)((threads + t - 1) / t);
+  const LaneParams<T> K{T(A.P.kappa), T(A.P.tau_t), T(A.P.C_I * dim), T(A.P.eps2x2)};
   if (dim == 2) {
-    if (jv) k_element_lanes<T, 2, true><<<blocks, t, 0, s>>>(A);
-    else k_element_lanes<T, 2, false><<<blocks, t, 0, s>>>(A);
+    if (jv) k_element_lanes<T, 2, true><<<blocks, t, 0, s>>>(A, K);
+    else k_element_lanes<T, 2, false><<<blocks, t, 0, s>>>(A, K);
   } else {
-    if (jv) k_element_lanes<T, 3, true><<<blocks, t, 0, s>>>(A);
-    else k_element_lanes<T, 3, false><<<blocks, t, 0, s>>>(A);
+    if (jv) k_element_lanes<T, 3, true><<<blocks, t, 0, s>>>(A, K);
+    else k_element_lanes<T, 3, false><<<blocks, t, 0, s>>>(A, K);
   }
   note_launch();
   return cudaGetLastError();

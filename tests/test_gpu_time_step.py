@@ -78,3 +78,51 @@ def test_failed_step_without_retries_reports_newton_failure():
     st = P.ctx.time_step(raise_on_error=False)
     assert st.status == P.pnp.PNP_ERR_NEWTON_DIVERGED and st.newton_its == 3
     assert P.ctx.step_count() == 0
+
+
+def _small_pair(**extra):
+    oc = W.uniform_octants(2, 4)
+    bcs = W.equilibrium_bcs(2, 1.0)
+    kw = dict(eps=0.05, dt=1e-2, newton_rtol=1e-10, gmres_rtol=1e-10, gmres_restart=30, gmres_max_it=2000)
+    kw.update(extra)
+    P = Pair(oc, kw, bcs)
+    U0 = W.noisy_state(P.mesh.ijk, oc.max_level, seed=1, amp=1e-2, phi_bottom=1.0, phi_top=0.0)
+    P.ctx.set_field(P.pnp.PNP_FIELD_U, U0)
+    P.ctx.make_consistent()
+    P.ctx.reset_history()
+    return P, U0
+
+
+def test_non_finite_state_is_reported_and_the_context_stays_usable():
+    """Failure detection on the host side of a solve: a NaN in the state makes the
+    Newton solve return PNP_ERR_NAN (no device fault, no abort); a valid state then
+    solves normally on the same context."""
+    P, U0 = _small_pair()
+    bad = U0.copy()
+    bad[5, 0] = np.nan
+    P.ctx.set_field(P.pnp.PNP_FIELD_U, bad)
+    st = P.ctx.newton_solve(raise_on_error=False)
+    assert st.status == P.pnp.PNP_ERR_NAN
+    P.ctx.set_field(P.pnp.PNP_FIELD_U, U0)
+    P.ctx.make_consistent()
+    P.ctx.reset_history()
+    st = P.ctx.time_step(raise_on_error=False)
+    assert st.status == 0 and st.res_final <= 1e-10 * st.res_ref
+
+
+def test_krylov_iteration_limit_is_reported():
+    """A GMRES limit of 3 iterations at rtol 1e-12 returns PNP_ERR_KRYLOV_MAXIT with the
+    iterations taken; the context stays usable."""
+    P, U0 = _small_pair(gmres_max_it=3)
+    torch = P.torch
+    n = P.mesh.n_nodes
+    U = torch.from_numpy(P.ctx.get_field(P.pnp.PNP_FIELD_U)).cuda()
+    F = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    P.ctx.residual(U, F)
+    x = torch.zeros_like(F)
+    st = P.ctx.gmres(U, -F, x, 1e-12, raise_on_error=False)
+    assert st.status == P.pnp.PNP_ERR_KRYLOV_MAXIT and st.krylov_its == 3
+    p = P.ctx.get_params(); p.gmres_max_it = 2000; P.ctx.set_params(p)
+    x.zero_()
+    st = P.ctx.gmres(U, -F, x, 1e-10)
+    assert st.status == 0
