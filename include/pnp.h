@@ -204,7 +204,8 @@ int pnp_norm2(pnp_ctx* c, const double* x, int64_t n, double* result);
 
 /* ---------------------------------------------------------------- solvers -------- */
 /* Solve J(U) x = b by right-preconditioned GMRES(m) (3x3 block-Jacobi preconditioner,
- * classical Gram-Schmidt with reorthogonalisation, FP64 basis and dot products).
+ * classical Gram-Schmidt, a second pass when gmres_cgs2, FP64 basis and dot products;
+ * convergence accepted after a true-residual check).
  * U, b, x: device FP64 [n][3]; x is the initial guess on entry.  rtol relative to
  * ||b||; precision selects the J V arithmetic. */
 int pnp_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol,
@@ -214,8 +215,12 @@ int pnp_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
 int pnp_newton_solve(pnp_ctx* c, pnp_solve_stats* st);
 /* One BDF time step (Def. 1): BDF1 on the first step, then bdf_order; advection
  * v~ = 2 v^k - v^{k-1} (Eq. averaging1) from the VELOCITY fields; Newton start per
- * start_mode; on success U_PREV2 <- U_PREV <- U^{k+1} = U and VELOCITY_PREV <-
- * VELOCITY.  The BDF coefficients used are left in the context's parameters. */
+ * start_mode, Newton tolerance relative to ||F(U^k)|| (see newton_rtol); on success
+ * U_PREV2 <- U_PREV <- U^{k+1} = U and VELOCITY_PREV <- VELOCITY.  With dt_retries > 0
+ * a step whose Newton solve fails is redone as two BDF1 half steps (recursively);
+ * st->substeps counts the solves that completed it.  On failure the context keeps the
+ * last completed (sub)step as U_PREV.  The BDF coefficients and dt used last are left
+ * in the context's parameters except dt, which is restored. */
 int pnp_time_step(pnp_ctx* c, pnp_solve_stats* st);
 /* Number of steps taken so far by pnp_time_step (0 after pnp_ctx_create or
  * pnp_reset_history). */
