@@ -46,7 +46,7 @@ FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # roofline that bounds each kernel class (arithmetic intensity against the balance points)
 BOUNDS = {"residual64": "fp64", "jv64": "fp64", "jv32": "fp32", "blockdiag": "hbm", "ortho_dot": "fp64",
-          "ortho_update": "fp64", "precond": "hbm", "mlp": "bf16"}
+          "ortho_update": "fp64", "precond": "hbm", "mlp": "bf16", "inner_ortho": "hbm"}
 
 
 def parse():
@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-mode comparison step")
     ap.add_argument("--no-learned", action="store_true", help="mixed mode without training the learned start")
+    ap.add_argument("--inner", type=int, default=None, help="inner FP32 GMRES steps of the flexible outer GMRES (mixed)")
+    ap.add_argument("--restart", type=int, default=None, help="outer GMRES restart length (mixed)")
     ap.add_argument("--record-steps", type=int, default=8, help="trajectory steps recorded for training")
     ap.add_argument("--train-steps", type=int, default=400, help="Adam steps of the learned start")
     return ap.parse_args()
@@ -71,10 +73,16 @@ def workload_octants(small: bool):
     return W.membrane_band_octants(4, 7, 0.05) if small else W.membrane_band_octants(5, 8, 0.05)
 
 
-def mode_params(pnp, mode):
+INNER, RESTART = 0, 60  # mixed mode: inner FP32 GMRES steps, outer restart
+
+
+def mode_params(pnp, mode, inner=None, restart=None):
     if mode == "mixed":
+        inner = INNER if inner is None else inner
+        restart = RESTART if restart is None else restart
         return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F32, start_mode=pnp.PNP_START_LEARNED,
-                                  newton_rtol=1e-8, gmres_restart=60, gmres_max_it=3000, dt_retries=2)
+                                  newton_rtol=1e-8, gmres_restart=restart, gmres_max_it=3000, dt_retries=2,
+                                  gmres_inner=inner)
     return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F64, start_mode=pnp.PNP_START_PREVIOUS,
                               newton_rtol=1e-8, gmres_rtol=1e-8, gmres_restart=100, gmres_max_it=4000,
                               dt_retries=2)
@@ -134,9 +142,9 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "samples": len(self.rows), "reasons": reasons}
 
 
-def setup_ctx(pnp, W, torch, oc, mode):
+def setup_ctx(pnp, W, torch, oc, mode, inner=None, restart=None):
     mesh = pnp.Mesh(oc)
-    ctx = pnp.Context(mesh, mode_params(pnp, mode), torch.cuda.current_stream().cuda_stream)
+    ctx = pnp.Context(mesh, mode_params(pnp, mode, inner, restart), torch.cuda.current_stream().cuda_stream)
     ctx.set_bcs(W.membrane_bcs(3, VOLT, 2.0))
     U0 = W.noisy_state(mesh.ijk, oc.max_level, seed=0, amp=1e-3, phi_bottom=0.0, phi_top=VOLT)
     ctx.set_field(pnp.PNP_FIELD_U, U0)
@@ -192,6 +200,15 @@ def run_reference(args):
            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": v},
            "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def ctx_krylov_desc(p, mode):
+    if mode == "plain":
+        return f"GMRES({p.gmres_restart}) + block Jacobi, FP64 J V, rtol {p.gmres_rtol:g}"
+    if p.gmres_inner > 0:
+        return (f"flexible GMRES({p.gmres_restart}) in FP64, preconditioned by {p.gmres_inner} steps of FP32 "
+                f"GMRES on J M^-1 (M block Jacobi); Eisenstat-Walker forcing")
+    return f"GMRES({p.gmres_restart}) + block Jacobi, FP32 J V, FP64 dots; Eisenstat-Walker forcing"
 
 
 def max_over_ranks(ms, dist, device):
@@ -317,7 +334,7 @@ def main():
         dist.init_process_group("nccl")
     pnp.lib()
     oc = workload_octants(args.small)
-    mesh, ctx = setup_ctx(pnp, W, torch, oc, args.mode)
+    mesh, ctx = setup_ctx(pnp, W, torch, oc, args.mode, args.inner, args.restart)
     N = mesh.n_nodes
     stream = torch.cuda.current_stream()
 
@@ -418,6 +435,7 @@ def main():
                                 "3D membrane-band octree, base level 5, level 8 for z<0.05 (2:1 graded)"),
                    "n_elem": mesh.n_elem, "n_nodes": N, "n_hanging": mesh.n_hanging, "dofs": 3 * N,
                    "eps": EPS, "V": VOLT, "dt": DT, "mode": args.mode, "velocity": "zero (no NS block)",
+                   "krylov": ctx_krylov_desc(ctx.get_params(), args.mode),
                    "start": ("learned (judged vs extrapolated)" if learned else
                              "extrapolated" if args.mode == "mixed" else "previous step"),
                    "l2": "inputs larger than L2 (3.1M-dof FP64 vectors 25 MB each, Krylov basis up to 1.5 GB)",

@@ -112,6 +112,11 @@ typedef struct pnp_params {
                             half steps, recursively up to this depth (0: report the
                             failure; the next full step after a split is BDF1 and starts
                             from the previous state, because the history spacing changed) */
+  int32_t gmres_inner;   /* PNP_F32 Krylov solves: 0 = right-preconditioned GMRES(m) with
+                            the block diagonal; d in 1..32 = flexible GMRES(m) whose
+                            preconditioner is d steps of FP32 GMRES on J M^-1 (M the
+                            block diagonal), with FP64 outer dots and orthogonalisation */
+  int32_t pad2_;
 } pnp_params;
 
 typedef struct pnp_solve_stats {
@@ -127,7 +132,7 @@ typedef struct pnp_solve_stats {
   double res0;           /* ||F(U^0)||_2 */
   double res_final;      /* ||F(U^m)||_2 */
   double res_start_extrapolated; /* learned start only: ||F|| of the extrapolated start */
-  double res_start_learned;      /* learned start only: ||F|| of the network's start */
+  double res_start_learned;      /* learned start only: ||F|| of the best network-based start */
   double wall_ms;        /* host wall time of the call */
   double res_ref;        /* ||F|| the relative Newton tolerance refers to: res0, or in
                             pnp_time_step ||F(U^k)|| of the previous-step state */
@@ -231,8 +236,9 @@ int pnp_reset_history(pnp_ctx* c);
 /* ---------------------------------------------------------------- learned start -- */
 /* The library's addition to the paper (which has no learned component): a per-node
  * network proposes the Newton start of pnp_time_step (start_mode PNP_START_LEARNED);
- * plain Newton judges it -- the start with the smaller ||F|| of {learned, extrapolated
- * 2 U^k - U^{k-1}} is used.
+ * plain Newton judges it -- the start with the smallest ||F|| of {learned U_l,
+ * extrapolated U_e = 2 U^k - U^{k-1}, blend U_e + a (U_l - U_e)} is used, with a in
+ * [0, 2] the minimiser of ||F_e + a (F_l - F_e)|| (one extra residual).
  *
  * Input (216 features per non-hanging node): the fields c+, c-, phi and the last-axis
  * velocity component at t^k and t^{k-1}, sampled at the 3x3x3 lattice around the node
@@ -327,7 +333,8 @@ enum {
   PNP_PROF_PRECOND = 5,    /* block-Jacobi apply (and FP32 conversion) */
   PNP_PROF_MLP = 6,        /* learned-start network kernels */
   PNP_PROF_ORTHO_UPDATE = 7, /* Gram-Schmidt update: the multi-axpy + norm kernel */
-  PNP_PROF_KINDS = 8
+  PNP_PROF_INNER = 8,      /* FP32 Gram-Schmidt of the inner GMRES (flexible mode) */
+  PNP_PROF_KINDS = 9
 };
 /* on != 0: clear the accumulated times and start recording; on == 0: stop. */
 int pnp_profile_enable(pnp_ctx* c, int on);

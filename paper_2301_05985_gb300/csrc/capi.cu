@@ -69,6 +69,7 @@ void pnp_params_default(pnp_params* p) {
   p->ew_eta_min = 1e-4;
   p->monitor = 0;
   p->f64_fallback = 1;
+  p->gmres_inner = 0;
 }
 
 // ------------------------------------------------------------------ mesh
@@ -151,6 +152,9 @@ static int check_params(const pnp_params* p) {
   if (p->precision != PNP_F64 && p->precision != PNP_F32) PNP_FAIL(PNP_ERR_ARG, "params: bad precision");
   if (p->start_mode < 0 || p->start_mode > 2) PNP_FAIL(PNP_ERR_ARG, "params: bad start_mode");
   if (p->bdf_order != 1 && p->bdf_order != 2) PNP_FAIL(PNP_ERR_ARG, "params: bdf_order must be 1 or 2");
+  if (p->gmres_inner < 0 || p->gmres_inner > inner_max_depth())
+    PNP_FAIL(PNP_ERR_ARG, "params: gmres_inner in 0..%d", inner_max_depth());
+  if (p->dt_retries < 0 || p->dt_retries > 16) PNP_FAIL(PNP_ERR_ARG, "params: dt_retries in 0..16");
   return PNP_OK;
 }
 
@@ -158,7 +162,7 @@ static void free_ctx_memory(pnp_ctx* c) {
   void* ptrs[] = {c->d_conn, c->d_level, c->d_faces, c->d_hnode, c->d_hpar, c->d_hnp, c->U, c->Uk, c->Ukm1,
                   c->adv, c->vel, c->vel_prev, c->hs, c->U32, c->adv32, c->hs32, c->V32, c->JV32, c->F,
                   c->dU, c->Ut, c->Ft, c->rhs, c->Dinv, c->D32, c->basis, c->w, c->z, c->r, c->part, c->dsc,
-                  c->dflag};
+                  c->dflag, c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->pt_alloc) cudaFree(p);
@@ -330,6 +334,33 @@ int ctx_alloc_krylov(pnp_ctx* c, int m) {
   }
   c->basis_bytes = (int64_t)bb;
   c->m_alloc = m;
+  return PNP_OK;
+}
+
+// Buffers of the flexible outer GMRES(m) with an inner FP32 GMRES(d).
+int ctx_alloc_inner(pnp_ctx* c, int m, int d) {
+  if (m <= c->inner_m && d <= c->inner_d) return PNP_OK;
+  m = std::max(m, c->inner_m);
+  d = std::max(d, c->inner_d);
+  if (int rc = ctx_alloc_krylov(c, std::max(c->m_alloc, d))) return rc;  // partials for d projections
+  void* old[] = {c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  c->Zb = c->Qin = c->Dinv32 = c->iinv = nullptr;
+  c->isc = nullptr;
+  c->inner_m = c->inner_d = 0;
+  const size_t n = (size_t)c->n3();
+  cudaError_t e = cudaMalloc((void**)&c->Zb, sizeof(float) * (size_t)m * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->Qin, sizeof(float) * (size_t)(d + 1) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->Dinv32, sizeof(float) * 9 * (size_t)c->n_nodes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->isc, sizeof(double) * ((size_t)(d + 1) * d + 5 * (size_t)(d + 2)));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->iinv, sizeof(float) * (size_t)(d + 2));
+  if (e != cudaSuccess) {
+    pnp_set_error("inner Krylov scratch allocation failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PNP_ERR_NOMEM : PNP_ERR_CUDA;
+  }
+  c->inner_m = m;
+  c->inner_d = d;
   return PNP_OK;
 }
 

@@ -49,6 +49,13 @@ struct pnp_ctx {
   double* hpin = nullptr;  // pinned host mirror of dsc
   int* dflag = nullptr;
   int m_alloc = 0;
+  // flexible outer GMRES with an inner FP32 GMRES(d) preconditioner
+  float* Zb = nullptr;      // [m][3N] preconditioned Krylov vectors
+  float* Qin = nullptr;     // [(d+1)][3N] inner basis (unnormalised)
+  float* Dinv32 = nullptr;  // [N][9] FP32 copy of the inverted block diagonal
+  double* isc = nullptr;    // inner Hessenberg [(d+1) x d] and scalars
+  float* iinv = nullptr;    // [d+2] inverse norms of the inner basis vectors
+  int inner_m = 0, inner_d = 0;
   int64_t basis_bytes = 0;
 
   // statistics of the last solve (for the time stepper)
@@ -147,9 +154,11 @@ int ctx_prepare_f32(pnp_ctx* c, const double* U);
 int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32);
 int ctx_block_diag(pnp_ctx* c, const double* U, double* D);
 int ctx_norm(pnp_ctx* c, const double* x, double* out);
+int ctx_dot(pnp_ctx* c, const double* x, const double* y, double* out);
 int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int precision, int max_it,
               int* its, double* relres, bool have_precond);
 int ctx_newton(pnp_ctx* c, pnp_solve_stats* st, const double* ref_state = nullptr);
+int ctx_alloc_inner(pnp_ctx* c, int m, int d);
 int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st);
 int ctx_alloc_krylov(pnp_ctx* c, int m);
 void pnp_mlp_release(pnp_ctx* c);

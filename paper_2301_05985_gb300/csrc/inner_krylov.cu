@@ -1,0 +1,293 @@
+// inner_krylov.cu -- FP32 kernels of the inner GMRES(d) that preconditions the flexible
+// outer GMRES in mixed precision.  The inner solve is a fixed number of Arnoldi steps on
+// J M^-1 (M: the 3x3 block diagonal) whose small Hessenberg bookkeeping also stays on the
+// device, so it needs no host round trip; the outer Krylov method keeps FP64 dots,
+// orthogonalisation and basis (Sec. 4.1's Newton-Krylov, with the bulk work in FP32).
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace {
+
+inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+__device__ __forceinline__ float warp_sum4f(const float (&s)[4], int lane) {
+  const bool hi4 = lane & 16, hi3 = lane & 8;
+  const float a0 = (hi4 ? s[2] : s[0]) + __shfl_xor_sync(0xffffffffu, hi4 ? s[0] : s[2], 16);
+  const float a1 = (hi4 ? s[3] : s[1]) + __shfl_xor_sync(0xffffffffu, hi4 ? s[1] : s[3], 16);
+  float b = (hi3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, hi3 ? a0 : a1, 8);
+  b += __shfl_xor_sync(0xffffffffu, b, 4);
+  b += __shfl_xor_sync(0xffffffffu, b, 2);
+  b += __shfl_xor_sync(0xffffffffu, b, 1);
+  return b;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// d_i = U_i . w (i < k) for FP32 vectors: 16 rows per thread in registers, four basis
+// vectors per warp reduce-scatter; per-block partials part[block][k] (FP64 from FP32 sums).
+constexpr int kRows = 16;
+__global__ void __launch_bounds__(256) k_multi_dot_f32(int64_t n, int k, const float* __restrict__ Ub, int64_t ld,
+                                                       const float* __restrict__ w, double* __restrict__ part) {
+  __shared__ float sh[64][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * (256 * kRows) + threadIdx.x;
+  float wv[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    const int64_t t = base + r * 256;
+    wv[r] = t < n ? w[t] : 0.0f;
+  }
+  for (int i0 = 0; i0 < k; i0 += 64) {
+    const int cnt = min(64, k - i0);
+    for (int j0 = 0; j0 < cnt; j0 += 4) {
+      float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (j0 + q < cnt) {
+          const float* ui = Ub + (int64_t)(i0 + j0 + q) * ld;
+#pragma unroll
+          for (int r = 0; r < kRows; ++r) {
+            const int64_t t = base + r * 256;
+            if (t < n) s[q] = fmaf(__ldg(ui + t), wv[r], s[q]);
+          }
+        }
+      }
+      const float tot = warp_sum4f(s, lane);
+      const int q = (lane >> 3) & 3;
+      if ((lane & 7) == 0 && j0 + q < cnt) sh[j0 + q][wid] = tot;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += (double)sh[j][q];
+      part[(int64_t)blockIdx.x * k + i0 + j] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// w -= sum_i (d_i dinv_i) U_i (i < k) in FP32, then per-block partials of w . w
+__global__ void __launch_bounds__(256) k_multi_axpy_norm_f32(int64_t n, int k, const float* __restrict__ Ub,
+                                                             int64_t ld, const double* __restrict__ d,
+                                                             const double* __restrict__ dinv, float* __restrict__ w,
+                                                             double* __restrict__ part) {
+  extern __shared__ float cf[];
+  __shared__ double sh[256];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = (float)(d[i] * dinv[i]);
+  __syncthreads();
+  float ss = 0.0f;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    float v0 = w[t], v1 = 0.0f;
+    int i = 0;
+    for (; i + 2 <= k; i += 2) {
+      v0 = fmaf(-cf[i], Ub[(int64_t)i * ld + t], v0);
+      v1 = fmaf(-cf[i + 1], Ub[(int64_t)(i + 1) * ld + t], v1);
+    }
+    if (i < k) v0 = fmaf(-cf[i], Ub[(int64_t)i * ld + t], v0);
+    const float v = v0 + v1;
+    if (k > 0) w[t] = v;
+    ss = fmaf(v, v, ss);
+  }
+  const double tot = block_sum_d((double)ss, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// y_i = Dinv_i (inv_s[0] u_i) per node, FP32 3x3 blocks
+__global__ void k_block_apply32(int64_t N, const float* __restrict__ Dinv, const float* __restrict__ u,
+                                const float* __restrict__ inv_s, float* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float sc = inv_s ? inv_s[0] : 1.0f;
+  const float* B = Dinv + 9 * i;
+  const float a = sc * u[3 * i], b = sc * u[3 * i + 1], c = sc * u[3 * i + 2];
+  y[3 * i] = fmaf(B[0], a, fmaf(B[1], b, B[2] * c));
+  y[3 * i + 1] = fmaf(B[3], a, fmaf(B[4], b, B[5] * c));
+  y[3 * i + 2] = fmaf(B[6], a, fmaf(B[7], b, B[8] * c));
+}
+
+// Arnoldi bookkeeping of the inner process (one thread).  Basis vectors u_i are kept
+// unnormalised with norms s_i: q_i = u_i / s_i.
+__global__ void k_inner_start(const double* __restrict__ nrm2, double* sv, double* dinv, float* inv_s) {
+  const double s = sqrt(nrm2[0]);
+  sv[0] = s;
+  dinv[0] = s > 0 ? 1.0 / (s * s) : 0.0;
+  inv_s[0] = s > 0 ? (float)(1.0 / s) : 0.0f;
+}
+
+__global__ void k_inner_col(int j, int ldh, const double* __restrict__ d, const double* __restrict__ nrm2,
+                            double* H, double* sv, double* dinv, float* inv_s) {
+  for (int i = 0; i <= j; ++i) H[i * ldh + j] = sv[i] > 0 ? d[i] / sv[i] : 0.0;
+  const double s = sqrt(nrm2[0]);
+  H[(j + 1) * ldh + j] = s;
+  sv[j + 1] = s;
+  dinv[j + 1] = s > 0 ? 1.0 / (s * s) : 0.0;
+  inv_s[j + 1] = s > 0 ? (float)(1.0 / s) : 0.0f;
+}
+
+// min || s_0 e_1 - H y || over the leading columns before any breakdown (Givens, FP64);
+// coef_i = y_i / s_i, so that sum_i y_i q_i = sum_i coef_i u_i.
+constexpr int kMaxInner = 32;
+__global__ void k_inner_lsq(int d, int ldh, const double* __restrict__ Hin, const double* __restrict__ sv,
+                            double* __restrict__ coef) {
+  double H[kMaxInner + 1][kMaxInner], g[kMaxInner + 1], cs[kMaxInner], sn[kMaxInner];
+  for (int i = 0; i < d; ++i) coef[i] = 0.0;
+  if (!(sv[0] > 0)) return;
+  int k = 0;
+  for (int j = 0; j < d; ++j) {
+    if (!(Hin[j * ldh + j] != 0.0 || Hin[(j + 1) * ldh + j] != 0.0)) break;
+    k = j + 1;
+    if (!(sv[j + 1] > 0)) break;  // breakdown: the Krylov space is invariant
+  }
+  for (int i = 0; i <= k; ++i)
+    for (int j = 0; j < k; ++j) H[i][j] = Hin[i * ldh + j];
+  for (int i = 0; i <= k; ++i) g[i] = 0.0;
+  g[0] = sv[0];
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
+      H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j];
+      H[i][j] = t;
+    }
+    const double rr = hypot(H[j][j], H[j + 1][j]);
+    if (rr == 0.0) { k = j; break; }
+    cs[j] = H[j][j] / rr;
+    sn[j] = H[j + 1][j] / rr;
+    H[j][j] = rr;
+    H[j + 1][j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int l = i + 1; l < k; ++l) t -= H[i][l] * coef[l];
+    coef[i] = t / H[i][i];
+  }
+  for (int i = 0; i < k; ++i) coef[i] /= sv[i];
+}
+
+// out = sum_i coef_i U_i (FP32 vectors, coefficients on the device)
+__global__ void k_combine_f32(int64_t n, int k, const float* __restrict__ Ub, int64_t ld,
+                              const double* __restrict__ coef, float* __restrict__ out) {
+  extern __shared__ float cf[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = (float)coef[i];
+  __syncthreads();
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    float v0 = 0.0f, v1 = 0.0f;
+    int i = 0;
+    for (; i + 2 <= k; i += 2) {
+      v0 = fmaf(cf[i], Ub[(int64_t)i * ld + t], v0);
+      v1 = fmaf(cf[i + 1], Ub[(int64_t)(i + 1) * ld + t], v1);
+    }
+    if (i < k) v0 = fmaf(cf[i], Ub[(int64_t)i * ld + t], v0);
+    out[t] = v0 + v1;
+  }
+}
+
+// x += sum_i coef_i Z_i: FP32 vectors combined in FP32, added to an FP64 vector
+__global__ void k_combine_f32_add_f64(int64_t n, int k, const float* __restrict__ Zb, int64_t ld,
+                                      const double* __restrict__ coef, double* __restrict__ x) {
+  extern __shared__ float cf[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = (float)coef[i];
+  __syncthreads();
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    float v0 = 0.0f, v1 = 0.0f;
+    int i = 0;
+    for (; i + 2 <= k; i += 2) {
+      v0 = fmaf(cf[i], Zb[(int64_t)i * ld + t], v0);
+      v1 = fmaf(cf[i + 1], Zb[(int64_t)(i + 1) * ld + t], v1);
+    }
+    if (i < k) v0 = fmaf(cf[i], Zb[(int64_t)i * ld + t], v0);
+    x[t] += (double)(v0 + v1);
+  }
+}
+
+// y = scale * (double) x
+__global__ void k_to_f64_scaled(int64_t n, const float* __restrict__ x, double scale, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = scale * (double)x[i];
+}
+
+}  // namespace
+
+int inner_dot_blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + 256 * kRows - 1) / (256 * kRows)); }
+int inner_max_depth() { return kMaxInner; }
+
+cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, const float* w, double* part, double* d,
+                                 cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  const int nb = inner_dot_blocks(n);
+  k_multi_dot_f32<<<nb, 256, 0, s>>>(n, k, Ub, ld, w, part);
+  note_launch();
+  launch_reduce_parts(nb, k, part, d, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* d,
+                                       const double* dinv, float* w, double* part, double* nrm2, cudaStream_t s) {
+  k_multi_axpy_norm_f32<<<kRedBlocks, 256, (k > 0 ? k : 1) * sizeof(float), s>>>(n, k, Ub, ld, d, dinv, w, part);
+  note_launch();
+  launch_reduce_parts(kRedBlocks, 1, part, nrm2, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_apply32(int64_t N, const float* Dinv32, const float* u, const float* inv_s, float* y,
+                                 cudaStream_t s) {
+  if (N) {
+    k_block_apply32<<<nblk(N, 256), 256, 0, s>>>(N, Dinv32, u, inv_s, y);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inner_start(const double* nrm2, double* sv, double* dinv, float* inv_s, cudaStream_t s) {
+  k_inner_start<<<1, 1, 0, s>>>(nrm2, sv, dinv, inv_s);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inner_col(int j, int ldh, const double* d, const double* nrm2, double* H, double* sv, double* dinv,
+                             float* inv_s, cudaStream_t s) {
+  k_inner_col<<<1, 1, 0, s>>>(j, ldh, d, nrm2, H, sv, dinv, inv_s);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inner_lsq(int d, int ldh, const double* H, const double* sv, double* coef, cudaStream_t s) {
+  k_inner_lsq<<<1, 1, 0, s>>>(d, ldh, H, sv, coef);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* coef, float* out,
+                               cudaStream_t s) {
+  k_combine_f32<<<kRedBlocks, 256, (k > 0 ? k : 1) * sizeof(float), s>>>(n, k, Ub, ld, coef, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_f32_add_f64(int64_t n, int k, const float* Zb, int64_t ld, const double* coef, double* x,
+                                       cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_combine_f32_add_f64<<<kRedBlocks, 256, k * sizeof(float), s>>>(n, k, Zb, ld, coef, x);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f64_scaled(int64_t n, const float* x, double scale, double* y, cudaStream_t s) {
+  k_to_f64_scaled<<<kRedBlocks, 256, 0, s>>>(n, x, scale, y);
+  note_launch();
+  return cudaGetLastError();
+}

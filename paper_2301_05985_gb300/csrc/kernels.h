@@ -109,6 +109,32 @@ template <typename T>
 cudaError_t launch_block_invert(int64_t N, const T* D, double* Dinv, int* flag, cudaStream_t s);
 // hanging interpolation + Dirichlet values on U
 cudaError_t launch_make_consistent(const RowArgs& R, double* U, cudaStream_t s);
+// out[j] = sum_b part[b*k + j] for j < k (one block per output, fixed order)
+cudaError_t launch_reduce_parts(int nparts, int k, const double* part, double* out, cudaStream_t s);
+
+// ---------------------------------------------- inner FP32 GMRES (inner_krylov.cu)
+int inner_dot_blocks(int64_t n);
+int inner_max_depth();
+// d_i = U_i . w (FP32 vectors, i < k); part: [inner_dot_blocks(n)][k]
+cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, const float* w, double* part, double* d,
+                                 cudaStream_t s);
+// w -= sum_i d_i dinv_i U_i (i < k, FP32); nrm2[0] = w . w afterwards (part: [kRedBlocks])
+cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* d,
+                                       const double* dinv, float* w, double* part, double* nrm2, cudaStream_t s);
+// y = Dinv32 (inv_s[0] u) per node (inv_s may be null: scale 1)
+cudaError_t launch_block_apply32(int64_t N, const float* Dinv32, const float* u, const float* inv_s, float* y,
+                                 cudaStream_t s);
+cudaError_t launch_inner_start(const double* nrm2, double* sv, double* dinv, float* inv_s, cudaStream_t s);
+cudaError_t launch_inner_col(int j, int ldh, const double* d, const double* nrm2, double* H, double* sv, double* dinv,
+                             float* inv_s, cudaStream_t s);
+cudaError_t launch_inner_lsq(int d, int ldh, const double* H, const double* sv, double* coef, cudaStream_t s);
+// out = sum_i coef_i U_i (FP32); x += sum_i coef_i Z_i (FP32 vectors into FP64)
+cudaError_t launch_combine_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* coef, float* out,
+                               cudaStream_t s);
+cudaError_t launch_combine_f32_add_f64(int64_t n, int k, const float* Zb, int64_t ld, const double* coef, double* x,
+                                       cudaStream_t s);
+// y = scale * x
+cudaError_t launch_to_f64_scaled(int64_t n, const float* x, double scale, double* y, cudaStream_t s);
 // copy with layout change: [N][dim] <-> [N][3]
 cudaError_t launch_vel_pack(int64_t N, int dim, const double* src, double* dst3, cudaStream_t s);
 cudaError_t launch_vel_unpack(int64_t N, int dim, const double* src3, double* dst, cudaStream_t s);

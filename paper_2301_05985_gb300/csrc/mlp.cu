@@ -1055,8 +1055,9 @@ extern "C" int pnp_mlp_forward_noalloc(const float* params, const float* X, int6
   return PNP_OK;
 }
 
-// Judged learned start of a time step: U <- the better of the network's start and the
-// extrapolated start 2 U^k - U^{k-1} (smaller ||F||); st->start_used says which.
+// Judged learned start of a time step: U <- the best (smallest ||F||) of the network's
+// start, the extrapolated start 2 U^k - U^{k-1} and the residual-minimising blend of the
+// two; st->start_used says whether a network-based start won.
 int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st) {
   if (!c->mlp || !c->mlp->trained) PNP_FAIL(PNP_ERR_STATE, "learned start: no trained network in this context");
   if (c->step == 0) PNP_FAIL(PNP_ERR_STATE, "learned start: needs two previous time levels");
@@ -1113,12 +1114,34 @@ int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st) {
   RC(ctx_norm(c, c->F, &fl));
   RC(ctx_residual(c, c->Ut, c->Ft));
   RC(ctx_norm(c, c->Ft, &fe));
-  st->res_start_learned = fl;
+  // residual-minimising blend U_b = U_e + a (U_l - U_e): over this short segment F is
+  // close to linear, so ||F_e + a (F_l - F_e)|| is least near a* = <F_e, D> / ||D||^2
+  // with D = F_e - F_l; a* is checked with one more residual
+  double fb = INFINITY;
+  if (std::isfinite(fl)) {
+    double* D = c->w;
+    CK(launch_axpbyz(n, 1.0, c->Ft, -1.0, c->F, D, s));
+    double dn, ed;
+    RC(ctx_norm(c, D, &dn));
+    RC(ctx_dot(c, c->Ft, D, &ed));
+    const double a = dn > 0 ? std::min(std::max(ed / (dn * dn), 0.0), 2.0) : 0.0;
+    if (a > 0.02 && std::fabs(a - 1.0) > 0.02) {
+      CK(launch_axpbyz(n, 1.0 - a, c->Ut, a, c->U, c->dU, s));
+      RC(ctx_residual(c, c->dU, c->F));
+      RC(ctx_norm(c, c->F, &fb));
+    }
+  }
   st->res_start_extrapolated = fe;
-  if (std::isfinite(fl) && fl < fe) {
+  if (std::isfinite(fb) && fb < fe && fb < fl) {
     st->start_used = PNP_START_LEARNED;
+    st->res_start_learned = fb;
+    CK(cudaMemcpyAsync(c->U, c->dU, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else if (std::isfinite(fl) && fl < fe) {
+    st->start_used = PNP_START_LEARNED;
+    st->res_start_learned = fl;
   } else {
     st->start_used = PNP_START_EXTRAPOLATE;
+    st->res_start_learned = std::isfinite(fb) ? std::min(fl, fb) : fl;
     CK(cudaMemcpyAsync(c->U, c->Ut, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   }
   CK(cudaStreamSynchronize(s));

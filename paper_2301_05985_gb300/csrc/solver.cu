@@ -1,6 +1,7 @@
-// solver.cu -- residual / Jv drivers, GMRES(m) with classical Gram-Schmidt and
-// reorthogonalisation, Newton's method (Sec. 4.1 of arXiv 2301.05985) with optional
-// Eisenstat-Walker forcing for the FP32-Jv inexact mode, and the BDF time step (Def. 1).
+// solver.cu -- residual / Jv drivers, GMRES(m) with classical Gram-Schmidt (flexible
+// GMRES with an inner FP32 GMRES in mixed precision), Newton's method (Sec. 4.1 of
+// arXiv 2301.05985) with Eisenstat-Walker forcing for the FP32-Jv inexact mode, and the
+// BDF time step (Def. 1) with optional step splitting.
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -181,6 +182,15 @@ int ctx_norm(pnp_ctx* c, const double* x, double* out) {
   return PNP_OK;
 }
 
+int ctx_dot(pnp_ctx* c, const double* x, const double* y, double* out) {
+  double* slot = c->dsc + 4 * (c->m_alloc + 2) + 10;
+  CK(launch_dot(c->n3(), x, y, c->part, slot, c->stream));
+  CK(cudaMemcpyAsync(c->hpin, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = c->hpin[0];
+  return PNP_OK;
+}
+
 // 3x3 block-Jacobi preconditioner at U, built in the precision of the Jv
 static int build_preconditioner(pnp_ctx* c, const double* U, int prec) {
   CK(cudaMemsetAsync(c->dflag, 0, sizeof(int), c->stream));
@@ -188,6 +198,10 @@ static int build_preconditioner(pnp_ctx* c, const double* U, int prec) {
     RC(ctx_prepare_f32(c, U));
     RC(ctx_block_diag32(c, c->D32));
     CK(launch_block_invert<float>(c->n_nodes, c->D32, c->Dinv, c->dflag, c->stream));
+    if (c->prm.gmres_inner > 0) {
+      RC(ctx_alloc_inner(c, c->prm.gmres_restart, c->prm.gmres_inner));
+      CK(launch_to_f32(9 * c->n_nodes, c->Dinv, c->Dinv32, c->stream));
+    }
   } else {
     RC(ctx_block_diag(c, U, c->Dinv));
     CK(launch_block_invert<double>(c->n_nodes, c->Dinv, c->Dinv, c->dflag, c->stream));
@@ -208,11 +222,55 @@ static int apply_op(pnp_ctx* c, const double* U, const double* x, double* w, int
   return PNP_OK;
 }
 
-// Right-preconditioned GMRES(m).  The Krylov vectors are stored unnormalised (v_i = u_i / s_i,
-// s_i kept on the host) so no normalisation pass is needed; each iteration does one
-// classical Gram-Schmidt pass (multi-dot, then multi-axpy fused with the new norm) and a
-// second pass only when the norm dropped below 1/sqrt(2) of its value before the pass
-// (Daniel-Gragg-Kaufman-Stewart criterion).  Dots and the Hessenberg system are FP64.
+// z = P(u): d steps of right-preconditioned FP32 GMRES on (J M^-1) t = u from t = 0, then
+// z = M^-1 t (M: the block diagonal).  A fixed number of steps with the Hessenberg
+// bookkeeping on the device: no host round trip.  P is homogeneous, P(a u) = a P(u).
+static int inner_gmres32(pnp_ctx* c, const double* u, float* z32) {
+  const int d = c->prm.gmres_inner;
+  const int64_t n = c->n3(), N = c->n_nodes;
+  cudaStream_t s = c->stream;
+  float* Q = c->Qin;
+  double* H = c->isc;                        // [(d+1) x d], leading dimension d
+  double* sv = H + (size_t)(d + 1) * d;      // [d+1] norms s_i of the basis vectors
+  double* dinv = sv + (d + 2);               // [d+1] 1 / s_i^2
+  double* dd = dinv + (d + 2);               // [d+1] projections
+  double* nrm2 = dd + (d + 2);               // [1]
+  double* coef = nrm2 + 2;                   // [d] combination coefficients
+  float* inv_s = c->iinv;
+  CK(launch_to_f32(n, u, Q, s));
+  {
+    ProfScope ps(c, PNP_PROF_INNER, 4.0 * n, 2.0 * n);
+    CK(launch_multi_axpy_norm_f32(n, 0, Q, n, dd, dinv, Q, c->part, nrm2, s));
+  }
+  CK(launch_inner_start(nrm2, sv, dinv, inv_s, s));
+  for (int j = 0; j < d; ++j) {
+    float* w = Q + (size_t)(j + 1) * n;
+    {
+      ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
+      CK(launch_block_apply32(N, c->Dinv32, Q + (size_t)j * n, inv_s + j, c->V32, s));
+    }
+    RC(ctx_jv32(c, c->V32, w));
+    {
+      const double nj = (double)n * (j + 1);
+      ProfScope ps(c, PNP_PROF_INNER, 4.0 * (nj + n) + 4.0 * (nj + 2.0 * n), 4.0 * nj + 2.0 * n);
+      CK(launch_multi_dot_f32(n, j + 1, Q, n, w, c->part, dd, s));
+      CK(launch_multi_axpy_norm_f32(n, j + 1, Q, n, dd, dinv, w, c->part, nrm2, s));
+    }
+    CK(launch_inner_col(j, d, dd, nrm2, H, sv, dinv, inv_s, s));
+  }
+  CK(launch_inner_lsq(d, d, H, sv, coef, s));
+  CK(launch_combine_f32(n, d, Q, n, coef, c->JV32, s));
+  ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
+  CK(launch_block_apply32(N, c->Dinv32, c->JV32, nullptr, z32, s));
+  return PNP_OK;
+}
+
+// Right-preconditioned GMRES(m), or flexible GMRES(m) when an inner FP32 GMRES(d) is the
+// preconditioner (PNP_F32 with gmres_inner > 0).  The Krylov vectors are stored
+// unnormalised (v_i = u_i / s_i, s_i kept on the host) so no normalisation pass is
+// needed; each iteration does one classical Gram-Schmidt pass (multi-dot, then
+// multi-axpy fused with the new norm), two with gmres_cgs2.  Dots, basis and the
+// Hessenberg system are FP64.
 int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int prec, int max_it, int* its_out,
               double* rel_out, bool have_precond) {
   const int m = c->prm.gmres_restart;
@@ -221,6 +279,8 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   cudaStream_t s = c->stream;
   if (!have_precond) RC(build_preconditioner(c, U, prec));
   if (prec == PNP_F32) RC(ctx_prepare_f32(c, U));
+  const bool flex = prec == PNP_F32 && c->prm.gmres_inner > 0;
+  if (flex) RC(ctx_alloc_inner(c, m, c->prm.gmres_inner));
   double* V = c->basis;
   double* dd = c->dsc;                    // [m+2] dot products of one pass
   double* dinv = c->dsc + (m + 2);        // [m+2] 1 / s_i^2
@@ -269,8 +329,14 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
     for (int j = 0; j < m && total < max_it; ++j) {
       const double* uj = V + (size_t)j * n;
       double* w = V + (size_t)(j + 1) * n;
-      // z = M^-1 (u_j / s_j) ; w = J z
-      if (prec == PNP_F64) {
+      // z = M^-1 (u_j / s_j) ; w = J z   (flexible: z_j = P(u_j) / s_j kept in Zb)
+      if (flex) {
+        float* zj = c->Zb + (size_t)j * n;
+        RC(inner_gmres32(c, uj, zj));
+        RC(ctx_jv32(c, zj, c->JV32));
+        ProfScope ps(c, PNP_PROF_PRECOND, 20.0 * (double)n);
+        CK(launch_to_f64_scaled(n, c->JV32, 1.0 / sv[j], w, s));
+      } else if (prec == PNP_F64) {
         {
           ProfScope ps(c, PNP_PROF_PRECOND, 120.0 * c->n_nodes, 18.0 * c->n_nodes);
           CK(launch_block_apply(c->n_nodes, c->Dinv, uj, 1.0 / sv[j], c->z, nullptr, s));
@@ -343,12 +409,19 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
       y[i] = t / Hij(i, i);
     }
-    for (int i = 0; i < k; ++i) hco[i] = -y[i] / sv[i];
-    CK(cudaMemcpyAsync(dcoef, hco, sizeof(double) * k, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(c->w, 0, sizeof(double) * n, s));
-    CK(launch_multi_axpy(n, k, V, n, dcoef, c->w, nullptr, s));
-    CK(launch_block_apply(c->n_nodes, c->Dinv, c->w, 1.0, c->z, nullptr, s));
-    CK(launch_axpby(n, 1.0, c->z, 1.0, x, s));
+    if (flex) {
+      // x += sum_i y_i z_i with z_i = P(u_i) / s_i
+      for (int i = 0; i < k; ++i) hco[i] = y[i] / sv[i];
+      CK(cudaMemcpyAsync(dcoef, hco, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+      CK(launch_combine_f32_add_f64(n, k, c->Zb, n, dcoef, x, s));
+    } else {
+      for (int i = 0; i < k; ++i) hco[i] = -y[i] / sv[i];
+      CK(cudaMemcpyAsync(dcoef, hco, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(c->w, 0, sizeof(double) * n, s));
+      CK(launch_multi_axpy(n, k, V, n, dcoef, c->w, nullptr, s));
+      CK(launch_block_apply(c->n_nodes, c->Dinv, c->w, 1.0, c->z, nullptr, s));
+      CK(launch_axpby(n, 1.0, c->z, 1.0, x, s));
+    }
     // true residual (restart vector); when the Arnoldi estimate claims convergence it is
     // accepted only if the true residual agrees (the estimate drifts when the Krylov
     // basis loses orthogonality)

@@ -379,6 +379,13 @@ cudaError_t launch_scale_by_inv(int64_t n, const double* w, const double* nrm, d
   if (n) { k_scale_by_inv<<<gs_blocks(n, 256), 256, 0, s>>>(n, w, nrm, v); note_launch(); }
   return cudaGetLastError();
 }
+cudaError_t launch_reduce_parts(int nparts, int k, const double* part, double* out, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_reduce_parts<<<k, kRedThreads, 0, s>>>(nparts, k, part, out, 0);
+  note_launch();
+  return cudaGetLastError();
+}
+
 int multi_dot_blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + 256 * kMdRows - 1) / (256 * kMdRows)); }
 
 cudaError_t launch_multi_dot_ext(int64_t n, int k, bool with_self, const double* Vb, int64_t ld, const double* w,

@@ -90,7 +90,7 @@ def run(pnp, W, torch, train_V=(10.0, 20.0, 30.0), steps_per_V=667, test_V=25.0,
     results = {}
     for name, start in (("previous", pnp.PNP_START_PREVIOUS), ("extrapolated", pnp.PNP_START_EXTRAPOLATE),
                        ("learned", pnp.PNP_START_LEARNED)):
-        its, kry, wall, used_learned, r0, splits = [], [], [], 0, [], 0
+        its, kry, wall, used_learned, r0, splits, ratio = [], [], [], 0, [], 0, []
         for seed in seeds:
             m3, c3 = setup(pnp, W, torch, test_V, level=level, seed=100 + seed, mode=mode)
             if start == pnp.PNP_START_LEARNED:
@@ -112,12 +112,16 @@ def run(pnp, W, torch, train_V=(10.0, 20.0, 30.0), steps_per_V=667, test_V=25.0,
                 r0.append(s.res0)
                 used_learned += int(s.start_used == pnp.PNP_START_LEARNED)
                 splits += int(s.substeps > 1)
+                if s.res_start_extrapolated > 0:
+                    ratio.append(s.res_start_learned / s.res_start_extrapolated)
             c3.close()
         results[name] = {"newton_its_mean": float(np.mean(its)), "krylov_its_mean": float(np.mean(kry)),
                          "ms_per_step": 1e3 * float(np.mean(wall)), "res0_mean": float(np.mean(r0)),
-                         "learned_used": used_learned, "split_steps": splits, "steps": len(its)}
+                         "learned_used": used_learned, "split_steps": splits, "steps": len(its),
+                         "network_over_extrapolated": float(np.mean(ratio)) if ratio else None}
         log(f"{name:12s}: Newton {np.mean(its):.3f}  Krylov {np.mean(kry):.1f}  {1e3 * np.mean(wall):.2f} ms/step "
-            f" ||F0|| {np.mean(r0):.3e}  learned used {used_learned}/{len(its)}  split {splits}")
+            f" ||F0|| {np.mean(r0):.3e}  learned used {used_learned}/{len(its)}  split {splits}"
+            + (f"  ||F(net)||/||F(extrap)|| {np.mean(ratio):.3f}" if ratio else ""))
     out["results"] = results
     ctx.close()
     return out, weights, norm

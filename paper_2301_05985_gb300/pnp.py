@@ -47,6 +47,7 @@ class pnp_params(C.Structure):
         ("ew_eta_max", C.c_double), ("ew_eta_min", C.c_double),
         ("monitor", C.c_int32), ("f64_fallback", C.c_int32),
         ("gmres_cgs2", C.c_int32), ("dt_retries", C.c_int32),
+        ("gmres_inner", C.c_int32), ("pad2_", C.c_int32),
     ]
 
 
@@ -139,7 +140,7 @@ def mlp_forward_noalloc(params, X, Y, stream: int = 0):
 
 PNP_PROF_RESIDUAL, PNP_PROF_JV64, PNP_PROF_JV32, PNP_PROF_BLOCKDIAG = 0, 1, 2, 3
 PNP_PROF_ORTHO, PNP_PROF_PRECOND, PNP_PROF_MLP, PNP_PROF_KINDS = 4, 5, 6, 7
-PROF_NAMES = ["residual64", "jv64", "jv32", "blockdiag", "ortho_dot", "precond", "mlp", "ortho_update"]
+PROF_NAMES = ["residual64", "jv64", "jv32", "blockdiag", "ortho_dot", "precond", "mlp", "ortho_update", "inner_ortho"]
 
 
 def lib():

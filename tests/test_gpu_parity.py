@@ -152,6 +152,29 @@ def test_gmres_solves_oracle_system():
     assert rel_err(x, x_ref) <= 1e-6
 
 
+@pytest.mark.parametrize("inner", [0, 6])
+def test_fp32_gmres_solves_oracle_system(inner):
+    """FP32 J V inside GMRES: plain right preconditioning (inner = 0) and flexible GMRES
+    with an inner FP32 GMRES(6) preconditioner both solve the oracle's system to the
+    accuracy FP32 J V allows (the residual is measured with the oracle's FP64 Jacobian)."""
+    import scipy.sparse.linalg as spla
+    P, U, V = _setup(CASES[1], seed=9)
+    P.ctx.set_params(P.pnp.default_params(**P.params_kw, gmres_restart=40, gmres_max_it=4000, gmres_inner=inner))
+    J = P.oracle_jacobian(U)
+    b = W.random_direction(P.mesh.ijk, P.oc.max_level, 77)
+    x_ref = spla.spsolve(J.tocsc(), b.reshape(-1)).reshape(-1, 3)
+    x = P.torch.zeros((P.mesh.n_nodes, 3), dtype=P.torch.float64, device="cuda")
+    st = P.ctx.gmres(P.dev(U), P.dev(b), x, 1e-4, P.pnp.PNP_F32)
+    assert st.status == 0 and st.krylov_its > 0
+    x = x.cpu().numpy()
+    # against the oracle's assembled FP64 Jacobian: the FP32 operator's error floor
+    # (about 3e-5 relative on this case) plus the requested 1e-4
+    assert np.linalg.norm(J @ x.reshape(-1) - b.reshape(-1)) <= 3e-4 * np.linalg.norm(b)
+    assert rel_err(x, x_ref) <= 0.05
+    if inner:
+        assert st.jv_evals >= inner * st.krylov_its  # the inner steps ran
+
+
 def test_newton_equilibrium_matches_oracle():
     """2D steady double layer, level 5, Lambda = 0.01, V = 1 (the equilibrium case):
     GPU Newton (FP64, exact-Jacobian GMRES) and the oracle's direct-solve Newton converge
