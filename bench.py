@@ -9,10 +9,11 @@ The velocity is zero (no Navier-Stokes block in this library).
 
 One step = one pnp_time_step: BDF2 (BDF1 first), Newton to ||F|| <= 1e-8 ||F(U^k)||,
 GMRES with 3x3 block-Jacobi on the exact Jacobian action.  Modes:
-  mixed : FP32 J V inside an inexact Newton (Eisenstat-Walker), FP64 residual, dots,
-          orthogonalisation; learned start (network trained, before the timed region,
-          on the first steps of this run's own trajectory), judged against the
-          extrapolated start 2 U^k - U^{k-1}.
+  mixed : inexact Newton (Eisenstat-Walker) with flexible GMRES(60) in FP64 (dots,
+          orthogonalisation, basis), preconditioned by 24 steps of FP32 GMRES on J M^-1
+          (FP32 J V, M the 3x3 block Jacobi); FP64 residual; learned start (network
+          trained, before the timed region, on the first steps of this run's own
+          trajectory), judged against the extrapolated start 2 U^k - U^{k-1}.
   plain : FP64 J V, GMRES(100) rtol 1e-8 per Newton step, previous-step start (the
           paper's); timed for comparison from the same state as the first mixed step.
 
@@ -73,7 +74,7 @@ def workload_octants(small: bool):
     return W.membrane_band_octants(4, 7, 0.05) if small else W.membrane_band_octants(5, 8, 0.05)
 
 
-INNER, RESTART = 0, 60  # mixed mode: inner FP32 GMRES steps, outer restart
+INNER, RESTART = 24, 60  # mixed mode: inner FP32 GMRES steps, outer restart
 
 
 def mode_params(pnp, mode, inner=None, restart=None):

@@ -54,7 +54,8 @@ enum pnp_status {
   PNP_ERR_MESH = 2,              /* octants overlap, leave gaps or are misaligned */
   PNP_ERR_MESH_UNBALANCED = 3,   /* neighbours (face, edge or corner) differ by > 1 level */
   PNP_ERR_NAN = 4,               /* a norm became NaN or Inf */
-  PNP_ERR_KRYLOV_MAXIT = 5,      /* GMRES hit its iteration limit */
+  PNP_ERR_KRYLOV_MAXIT = 5,      /* GMRES hit its iteration limit, or a restart cycle cut the
+                                    true residual by less than 5% (stagnation) */
   PNP_ERR_NEWTON_DIVERGED = 6,   /* Newton hit its iteration limit or line search failed */
   PNP_ERR_CUDA = 7,              /* a CUDA call failed; the context is latched */
   PNP_ERR_DEVICE_FLAG = 8,       /* a kernel's own check failed (bad index / input) */
@@ -113,7 +114,7 @@ typedef struct pnp_params {
                             failure; the next full step after a split is BDF1 and starts
                             from the previous state, because the history spacing changed) */
   int32_t gmres_inner;   /* PNP_F32 Krylov solves: 0 = right-preconditioned GMRES(m) with
-                            the block diagonal; d in 1..32 = flexible GMRES(m) whose
+                            the block diagonal; d in 1..64 = flexible GMRES(m) whose
                             preconditioner is d steps of FP32 GMRES on J M^-1 (M the
                             block diagonal), with FP64 outer dots and orthogonalisation */
   int32_t pad2_;

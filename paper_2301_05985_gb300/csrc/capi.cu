@@ -162,7 +162,7 @@ static void free_ctx_memory(pnp_ctx* c) {
   void* ptrs[] = {c->d_conn, c->d_level, c->d_faces, c->d_hnode, c->d_hpar, c->d_hnp, c->U, c->Uk, c->Ukm1,
                   c->adv, c->vel, c->vel_prev, c->hs, c->U32, c->adv32, c->hs32, c->V32, c->JV32, c->F,
                   c->dU, c->Ut, c->Ft, c->rhs, c->Dinv, c->D32, c->basis, c->w, c->z, c->r, c->part, c->dsc,
-                  c->dflag, c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv};
+                  c->dflag, c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv, c->rec32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->pt_alloc) cudaFree(p);
@@ -220,6 +220,7 @@ int pnp_ctx_create(const pnp_mesh* m, const pnp_params* p, void* stream, pnp_ctx
   ALLOC(c->U32, sizeof(float) * 3 * N);
   ALLOC(c->adv32, sizeof(float) * 3 * N);
   ALLOC(c->hs32, sizeof(float) * 2 * N);
+  ALLOC(c->rec32, sizeof(float4) * 2 * N);
   ALLOC(c->V32, sizeof(float) * 3 * N);
   ALLOC(c->JV32, sizeof(float) * 3 * N);
   ALLOC(c->F, v3);

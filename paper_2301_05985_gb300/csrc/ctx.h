@@ -56,6 +56,7 @@ struct pnp_ctx {
   double* isc = nullptr;    // inner Hessenberg [(d+1) x d] and scalars
   float* iinv = nullptr;    // [d+2] inverse norms of the inner basis vectors
   int inner_m = 0, inner_d = 0;
+  float4* rec32 = nullptr;  // [N][2] FP32 node records of the state for the FP32 J V
   int64_t basis_bytes = 0;
 
   // statistics of the last solve (for the time stepper)

@@ -132,8 +132,35 @@ __device__ __forceinline__ void load_node(const ElemArgs<T>& A, int32_t id, bool
   }
 }
 
+// the FP32 state of node id from its 32-byte record (two 16-byte loads; hanging: the
+// parents' mean)
+template <typename T>
+__device__ __forceinline__ void load_record(const ElemArgs<T>& A, int32_t id, bool valid, float (&un)[3],
+                                            float (&hn)[2], float (&vn)[3]) {
+  float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+  if (valid) {
+    if (id >= 0) {
+      r0 = __ldg(A.rec + 2 * (int64_t)id);
+      r1 = __ldg(A.rec + 2 * (int64_t)id + 1);
+    } else {
+      const int32_t h = -id - 1;
+      const int np = A.hang_np[h];
+      const float wgt = np == 2 ? 0.5f : 0.25f;
+      for (int p = 0; p < np; ++p) {
+        const int64_t pid = A.hang_par[4 * h + p];
+        const float4 a = __ldg(A.rec + 2 * pid), b = __ldg(A.rec + 2 * pid + 1);
+        r0.x += wgt * a.x; r0.y += wgt * a.y; r0.z += wgt * a.z; r0.w += wgt * a.w;
+        r1.x += wgt * b.x; r1.y += wgt * b.y; r1.z += wgt * b.z; r1.w += wgt * b.w;
+      }
+    }
+  }
+  un[0] = r0.x; un[1] = r0.y; un[2] = r0.z;
+  hn[0] = r0.w; hn[1] = r1.x;
+  vn[0] = r1.y; vn[1] = r1.z; vn[2] = r1.w;
+}
+
 template <typename T, int D, bool JV>
-__global__ void __launch_bounds__(256) k_element_lanes(ElemArgs<T> A, LaneParams<T> K) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(ElemArgs<T> A, LaneParams<T> K) {
   constexpr int NC = 1 << D;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // warps whose first element is past the end leave together (shuffles need the warp)
@@ -156,9 +183,19 @@ __global__ void __launch_bounds__(256) k_element_lanes(ElemArgs<T> A, LaneParams
   const T e2 = K.e2;
 
   T un[3], vn[3], hn[2];
-  load_node<T, 3>(A, id, valid, A.U, 3, un);
-  load_node<T, 3>(A, id, valid, A.adv, 3, vn);
-  load_node<T, 2>(A, id, valid, A.hs, 2, hn);
+  if constexpr (sizeof(T) == 4) {
+    if (A.rec) {
+      load_record(A, id, valid, un, hn, vn);
+    } else {
+      load_node<T, 3>(A, id, valid, A.U, 3, un);
+      load_node<T, 3>(A, id, valid, A.adv, 3, vn);
+      load_node<T, 2>(A, id, valid, A.hs, 2, hn);
+    }
+  } else {
+    load_node<T, 3>(A, id, valid, A.U, 3, un);
+    load_node<T, 3>(A, id, valid, A.adv, 3, vn);
+    load_node<T, 2>(A, id, valid, A.hs, 2, hn);
+  }
 
   // state at this lane's Gauss point
   T cv[2], gc[2][3], gp[3], v[3] = {T(0), T(0), T(0)}, hq[2];

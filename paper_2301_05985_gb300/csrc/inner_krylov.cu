@@ -35,45 +35,48 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
   return r;
 }
 
-// d_i = U_i . w (i < k) for FP32 vectors: 16 rows per thread in registers, four basis
-// vectors per warp reduce-scatter; per-block partials part[block][k] (FP64 from FP32 sums).
-constexpr int kRows = 16;
-__global__ void __launch_bounds__(256) k_multi_dot_f32(int64_t n, int k, const float* __restrict__ Ub, int64_t ld,
-                                                       const float* __restrict__ w, double* __restrict__ part) {
-  __shared__ float sh[64][8];
+// d_i = U_i . w (i < k) for FP32 vectors.  Persistent grid (kDotBlocks = 4 per SM): each
+// block strides over chunks of 256 x kRows rows; for every group of four basis vectors a
+// thread accumulates its rows of all chunks (w re-read from L2 per group), then one warp
+// reduce-scatter and a fixed-order block sum give the block's partials part[block][k].
+constexpr int kRows = 4;
+constexpr int kDotBlocks = 4 * 152;
+__global__ void __launch_bounds__(256, 4) k_multi_dot_f32(int64_t n, int k, const float* __restrict__ Ub, int64_t ld,
+                                                          const float* __restrict__ w, double* __restrict__ part) {
+  __shared__ float sh[4][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t base = (int64_t)blockIdx.x * (256 * kRows) + threadIdx.x;
-  float wv[kRows];
+  const int64_t chunk = 256 * kRows;
+  for (int j0 = 0; j0 < k; j0 += 4) {
+    const int cnt = min(4, k - j0);
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < n; c0 += (int64_t)gridDim.x * chunk) {
+      float wv[kRows];
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    const int64_t t = base + r * 256;
-    wv[r] = t < n ? w[t] : 0.0f;
-  }
-  for (int i0 = 0; i0 < k; i0 += 64) {
-    const int cnt = min(64, k - i0);
-    for (int j0 = 0; j0 < cnt; j0 += 4) {
-      float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int r = 0; r < kRows; ++r) {
+        const int64_t t = c0 + threadIdx.x + r * 256;
+        wv[r] = t < n ? w[t] : 0.0f;
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if (j0 + q < cnt) {
-          const float* ui = Ub + (int64_t)(i0 + j0 + q) * ld;
+        if (q < cnt) {
+          const float* ui = Ub + (int64_t)(j0 + q) * ld;
 #pragma unroll
           for (int r = 0; r < kRows; ++r) {
-            const int64_t t = base + r * 256;
+            const int64_t t = c0 + threadIdx.x + r * 256;
             if (t < n) s[q] = fmaf(__ldg(ui + t), wv[r], s[q]);
           }
         }
       }
-      const float tot = warp_sum4f(s, lane);
-      const int q = (lane >> 3) & 3;
-      if ((lane & 7) == 0 && j0 + q < cnt) sh[j0 + q][wid] = tot;
     }
+    const float tot = warp_sum4f(s, lane);
+    const int q = (lane >> 3) & 3;
+    if ((lane & 7) == 0) sh[q][wid] = tot;
     __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-      double s = 0.0;
+    if (threadIdx.x < cnt) {
+      double t = 0.0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) s += (double)sh[j][q];
-      part[(int64_t)blockIdx.x * k + i0 + j] = s;
+      for (int v = 0; v < 8; ++v) t += (double)sh[threadIdx.x][v];
+      part[(int64_t)blockIdx.x * k + j0 + threadIdx.x] = t;
     }
     __syncthreads();
   }
@@ -139,7 +142,7 @@ __global__ void k_inner_col(int j, int ldh, const double* __restrict__ d, const 
 
 // min || s_0 e_1 - H y || over the leading columns before any breakdown (Givens, FP64);
 // coef_i = y_i / s_i, so that sum_i y_i q_i = sum_i coef_i u_i.
-constexpr int kMaxInner = 32;
+constexpr int kMaxInner = 64;
 __global__ void k_inner_lsq(int d, int ldh, const double* __restrict__ Hin, const double* __restrict__ sv,
                             double* __restrict__ coef) {
   double H[kMaxInner + 1][kMaxInner], g[kMaxInner + 1], cs[kMaxInner], sn[kMaxInner];
@@ -222,7 +225,7 @@ __global__ void k_to_f64_scaled(int64_t n, const float* __restrict__ x, double s
 
 }  // namespace
 
-int inner_dot_blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + 256 * kRows - 1) / (256 * kRows)); }
+int inner_dot_blocks(int64_t) { return kDotBlocks; }
 int inner_max_depth() { return kMaxInner; }
 
 cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, const float* w, double* part, double* d,

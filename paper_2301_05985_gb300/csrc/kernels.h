@@ -18,6 +18,9 @@ struct ElemArgs {
   const T* adv;            // [N][3] advection velocity
   T* out;                  // [N][3] accumulated (must be zeroed first)
   PhysParams P;
+  // FP32 lane kernel only (may be null): per node {c+, c-, phi, h+, h-, v0, v1, v2}, 32 B
+  // aligned, the same values as U, hs and adv in one sector
+  const float4* rec = nullptr;
 };
 
 // Arguments of the Dirichlet / hanging row kernels.
@@ -76,6 +79,9 @@ cudaError_t launch_history(int64_t N, const double* Uk, const double* Ukm1, doub
                            double* hs, cudaStream_t s);
 // y[i] = (float) x[i]
 cudaError_t launch_to_f32(int64_t n, const double* x, float* y, cudaStream_t s);
+// rec[i] = {U[i][0..2], hs[i][0..1], adv[i][0..2]} in FP32 (two float4 per node)
+cudaError_t launch_node_records(int64_t N, const double* U, const double* hs, const double* adv, float4* rec,
+                                cudaStream_t s);
 cudaError_t launch_to_f64(int64_t n, const float* x, double* y, cudaStream_t s);
 // y = a x + b y
 cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t s);

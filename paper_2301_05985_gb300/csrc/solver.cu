@@ -128,6 +128,7 @@ int ctx_prepare_f32(pnp_ctx* c, const double* U) {
   CK(launch_to_f32(c->n3(), U, c->U32, c->stream));
   CK(launch_to_f32(2 * c->n_nodes, c->hs, c->hs32, c->stream));
   CK(launch_to_f32(c->n3(), c->adv, c->adv32, c->stream));
+  CK(launch_node_records(c->n_nodes, U, c->hs, c->adv, c->rec32, c->stream));
   return PNP_OK;
 }
 
@@ -143,7 +144,9 @@ int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32) {
     CK(cudaMemsetAsync(JV32, 0, sizeof(float) * c->n3(), c->stream));
     {
       ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_kernel_flops(c->dim, true) * c->n_elem);
-      CK(launch_element<float>(c->dim, true, elem_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32), c->stream));
+      ElemArgs<float> A = elem_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32);
+      A.rec = c->rec32;
+      CK(launch_element<float>(c->dim, true, A, c->stream));
     }
     CK(launch_row_fixups<float>(c->rows(), V32, JV32, 1, c->stream));
   }
@@ -309,6 +312,7 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), sv(m + 1), h(m + 1);
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   int total = 0;
+  double beta_cycle = beta;  // true residual at the start of the current cycle
   while (true) {
     if (!std::isfinite(beta)) PNP_FAIL(PNP_ERR_NAN, "gmres: residual norm is not finite");
     if (beta <= tol) break;
@@ -431,6 +435,16 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
     if ((res <= tol || breakdown) && beta <= 2.0 * tol) break;
     if (c->prm.monitor >= 2)
       fprintf(stderr, "[pnp gmres] its %5d  estimate %.3e  true %.3e (relative)\n", total, res / bn, beta / bn);
+    // a whole cycle that cut the true residual by less than 5%: the operator's rounding
+    // floor (FP32 J V) or a stalled flexible preconditioner; stop with the iterate
+    if (std::isfinite(beta) && beta > 0.95 * beta_cycle) {
+      CK(cudaStreamSynchronize(s));
+      *its_out = total;
+      *rel_out = beta / bn;
+      PNP_FAIL(PNP_ERR_KRYLOV_MAXIT, "gmres: stagnated after %d iterations at relative residual %.3e > %.3e", total,
+               beta / bn, rtol);
+    }
+    beta_cycle = beta;
   }
   CK(cudaStreamSynchronize(s));
   *its_out = total;

@@ -379,6 +379,23 @@ cudaError_t launch_scale_by_inv(int64_t n, const double* w, const double* nrm, d
   if (n) { k_scale_by_inv<<<gs_blocks(n, 256), 256, 0, s>>>(n, w, nrm, v); note_launch(); }
   return cudaGetLastError();
 }
+__global__ void k_node_records(int64_t N, const double* __restrict__ U, const double* __restrict__ hs,
+                               const double* __restrict__ adv, float4* __restrict__ rec) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  rec[2 * i] = make_float4((float)U[3 * i], (float)U[3 * i + 1], (float)U[3 * i + 2], (float)hs[2 * i]);
+  rec[2 * i + 1] = make_float4((float)hs[2 * i + 1], (float)adv[3 * i], (float)adv[3 * i + 1], (float)adv[3 * i + 2]);
+}
+
+cudaError_t launch_node_records(int64_t N, const double* U, const double* hs, const double* adv, float4* rec,
+                                cudaStream_t s) {
+  if (N) {
+    k_node_records<<<nblk(N, 256), 256, 0, s>>>(N, U, hs, adv, rec);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_parts(int nparts, int k, const double* part, double* out, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   k_reduce_parts<<<k, kRedThreads, 0, s>>>(nparts, k, part, out, 0);
