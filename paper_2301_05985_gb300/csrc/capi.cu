@@ -354,7 +354,7 @@ int ctx_alloc_inner(pnp_ctx* c, int m, int d) {
   cudaError_t e = cudaMalloc((void**)&c->Zb, sizeof(float) * (size_t)m * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->Qin, sizeof(float) * (size_t)(d + 1) * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->Dinv32, sizeof(float) * 9 * (size_t)c->n_nodes);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->isc, sizeof(double) * ((size_t)(d + 1) * d + 5 * (size_t)(d + 2)));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->isc, sizeof(double) * (inner_scalar_doubles(d) + 5 * (size_t)(d + 2)));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->iinv, sizeof(float) * (size_t)(d + 2));
   if (e != cudaSuccess) {
     pnp_set_error("inner Krylov scratch allocation failed: %s", cudaGetErrorString(e));

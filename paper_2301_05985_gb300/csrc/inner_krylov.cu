@@ -121,62 +121,88 @@ __global__ void k_block_apply32(int64_t N, const float* __restrict__ Dinv, const
   y[3 * i + 2] = fmaf(B[6], a, fmaf(B[7], b, B[8] * c));
 }
 
-// Arnoldi bookkeeping of the inner process (one thread).  Basis vectors u_i are kept
-// unnormalised with norms s_i: q_i = u_i / s_i.
-__global__ void k_inner_start(const double* __restrict__ nrm2, double* sv, double* dinv, float* inv_s) {
-  const double s = sqrt(nrm2[0]);
-  sv[0] = s;
-  dinv[0] = s > 0 ? 1.0 / (s * s) : 0.0;
-  inv_s[0] = s > 0 ? (float)(1.0 / s) : 0.0f;
+// Arnoldi bookkeeping of the inner process.  Basis vectors u_i are kept unnormalised
+// with norms s_i (q_i = u_i / s_i); the Hessenberg columns are reduced by Givens rotations
+// as they arrive, so the least-squares solve at the end is a back-substitution.
+// Scalar layout: R [(d+1) x d] row-major, cs[d], sn[d], g[d+1], kv[1] (the number of
+// columns before the first breakdown, as a double).
+struct InnerScalars {
+  double *R, *cs, *sn, *g, *kv;
+};
+__device__ __forceinline__ InnerScalars inner_scalars(double* base, int d) {
+  InnerScalars S;
+  S.R = base;
+  S.cs = S.R + (size_t)(d + 1) * d;
+  S.sn = S.cs + d;
+  S.g = S.sn + d;
+  S.kv = S.g + (d + 1);
+  return S;
 }
 
-__global__ void k_inner_col(int j, int ldh, const double* __restrict__ d, const double* __restrict__ nrm2,
-                            double* H, double* sv, double* dinv, float* inv_s) {
-  for (int i = 0; i <= j; ++i) H[i * ldh + j] = sv[i] > 0 ? d[i] / sv[i] : 0.0;
-  const double s = sqrt(nrm2[0]);
-  H[(j + 1) * ldh + j] = s;
-  sv[j + 1] = s;
-  dinv[j + 1] = s > 0 ? 1.0 / (s * s) : 0.0;
-  inv_s[j + 1] = s > 0 ? (float)(1.0 / s) : 0.0f;
+__global__ void k_inner_start(int d, const double* __restrict__ nrm2, double* sv, double* dinv, float* inv_s,
+                              double* sc) {
+  const InnerScalars S = inner_scalars(sc, d);
+  for (int i = threadIdx.x; i <= d; i += blockDim.x) S.g[i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double s = sqrt(nrm2[0]);
+    sv[0] = s;
+    dinv[0] = s > 0 ? 1.0 / (s * s) : 0.0;
+    inv_s[0] = s > 0 ? (float)(1.0 / s) : 0.0f;
+    S.g[0] = s;
+    S.kv[0] = 0.0;
+  }
 }
 
-// min || s_0 e_1 - H y || over the leading columns before any breakdown (Givens, FP64);
-// coef_i = y_i / s_i, so that sum_i y_i q_i = sum_i coef_i u_i.
+// column j: h_i = d_i / s_i (i <= j), h_{j+1} = ||u_{j+1}||; apply the earlier rotations,
+// make rotation j, update g.  One block of kMaxInner threads.
 constexpr int kMaxInner = 64;
-__global__ void k_inner_lsq(int d, int ldh, const double* __restrict__ Hin, const double* __restrict__ sv,
-                            double* __restrict__ coef) {
-  double H[kMaxInner + 1][kMaxInner], g[kMaxInner + 1], cs[kMaxInner], sn[kMaxInner];
+__global__ void __launch_bounds__(kMaxInner) k_inner_col(int j, int d, const double* __restrict__ dd,
+                                                         const double* __restrict__ nrm2, double* sv, double* dinv,
+                                                         float* inv_s, double* sc) {
+  __shared__ double h[kMaxInner + 1];
+  const InnerScalars S = inner_scalars(sc, d);
+  const int i = threadIdx.x;
+  if (i <= j) h[i] = sv[i] > 0 ? dd[i] / sv[i] : 0.0;
+  if (i == 0) {
+    const double s = sqrt(nrm2[0]);
+    h[j + 1] = s;
+    sv[j + 1] = s;
+    dinv[j + 1] = s > 0 ? 1.0 / (s * s) : 0.0;
+    inv_s[j + 1] = s > 0 ? (float)(1.0 / s) : 0.0f;
+  }
+  __syncthreads();
+  if (i != 0) return;
+  for (int l = 0; l < j; ++l) {
+    const double t = S.cs[l] * h[l] + S.sn[l] * h[l + 1];
+    h[l + 1] = -S.sn[l] * h[l] + S.cs[l] * h[l + 1];
+    h[l] = t;
+  }
+  const double rr = hypot(h[j], h[j + 1]);
+  if (rr > 0) {
+    S.cs[j] = h[j] / rr;
+    S.sn[j] = h[j + 1] / rr;
+    h[j] = rr;
+    S.g[j + 1] = -S.sn[j] * S.g[j];
+    S.g[j] = S.cs[j] * S.g[j];
+    if (S.kv[0] == (double)j) S.kv[0] = j + 1;
+  } else {
+    S.cs[j] = 1.0;
+    S.sn[j] = 0.0;
+  }
+  for (int l = 0; l <= j; ++l) S.R[l * d + j] = h[l];
+}
+
+// y = R^-1 g over the columns before the first breakdown; coef_i = y_i / s_i, so that
+// sum_i y_i q_i = sum_i coef_i u_i.  One thread.
+__global__ void k_inner_lsq(int d, const double* __restrict__ sv, double* sc, double* __restrict__ coef) {
+  const InnerScalars S = inner_scalars(sc, d);
+  const int k = (int)S.kv[0];
   for (int i = 0; i < d; ++i) coef[i] = 0.0;
-  if (!(sv[0] > 0)) return;
-  int k = 0;
-  for (int j = 0; j < d; ++j) {
-    if (!(Hin[j * ldh + j] != 0.0 || Hin[(j + 1) * ldh + j] != 0.0)) break;
-    k = j + 1;
-    if (!(sv[j + 1] > 0)) break;  // breakdown: the Krylov space is invariant
-  }
-  for (int i = 0; i <= k; ++i)
-    for (int j = 0; j < k; ++j) H[i][j] = Hin[i * ldh + j];
-  for (int i = 0; i <= k; ++i) g[i] = 0.0;
-  g[0] = sv[0];
-  for (int j = 0; j < k; ++j) {
-    for (int i = 0; i < j; ++i) {
-      const double t = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
-      H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j];
-      H[i][j] = t;
-    }
-    const double rr = hypot(H[j][j], H[j + 1][j]);
-    if (rr == 0.0) { k = j; break; }
-    cs[j] = H[j][j] / rr;
-    sn[j] = H[j + 1][j] / rr;
-    H[j][j] = rr;
-    H[j + 1][j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-  }
   for (int i = k - 1; i >= 0; --i) {
-    double t = g[i];
-    for (int l = i + 1; l < k; ++l) t -= H[i][l] * coef[l];
-    coef[i] = t / H[i][i];
+    double t = S.g[i];
+    for (int l = i + 1; l < k; ++l) t -= S.R[i * d + l] * coef[l];
+    coef[i] = t / S.R[i * d + i];
   }
   for (int i = 0; i < k; ++i) coef[i] /= sv[i];
 }
@@ -255,21 +281,22 @@ cudaError_t launch_block_apply32(int64_t N, const float* Dinv32, const float* u,
   return cudaGetLastError();
 }
 
-cudaError_t launch_inner_start(const double* nrm2, double* sv, double* dinv, float* inv_s, cudaStream_t s) {
-  k_inner_start<<<1, 1, 0, s>>>(nrm2, sv, dinv, inv_s);
+cudaError_t launch_inner_start(int d, const double* nrm2, double* sv, double* dinv, float* inv_s, double* sc,
+                               cudaStream_t s) {
+  k_inner_start<<<1, 64, 0, s>>>(d, nrm2, sv, dinv, inv_s, sc);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_inner_col(int j, int ldh, const double* d, const double* nrm2, double* H, double* sv, double* dinv,
-                             float* inv_s, cudaStream_t s) {
-  k_inner_col<<<1, 1, 0, s>>>(j, ldh, d, nrm2, H, sv, dinv, inv_s);
+cudaError_t launch_inner_col(int j, int d, const double* dd, const double* nrm2, double* sv, double* dinv, float* inv_s,
+                             double* sc, cudaStream_t s) {
+  k_inner_col<<<1, kMaxInner, 0, s>>>(j, d, dd, nrm2, sv, dinv, inv_s, sc);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_inner_lsq(int d, int ldh, const double* H, const double* sv, double* coef, cudaStream_t s) {
-  k_inner_lsq<<<1, 1, 0, s>>>(d, ldh, H, sv, coef);
+cudaError_t launch_inner_lsq(int d, const double* sv, double* sc, double* coef, cudaStream_t s) {
+  k_inner_lsq<<<1, 1, 0, s>>>(d, sv, sc, coef);
   note_launch();
   return cudaGetLastError();
 }

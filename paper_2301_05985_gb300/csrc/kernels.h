@@ -130,10 +130,14 @@ cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_
 // y = Dinv32 (inv_s[0] u) per node (inv_s may be null: scale 1)
 cudaError_t launch_block_apply32(int64_t N, const float* Dinv32, const float* u, const float* inv_s, float* y,
                                  cudaStream_t s);
-cudaError_t launch_inner_start(const double* nrm2, double* sv, double* dinv, float* inv_s, cudaStream_t s);
-cudaError_t launch_inner_col(int j, int ldh, const double* d, const double* nrm2, double* H, double* sv, double* dinv,
-                             float* inv_s, cudaStream_t s);
-cudaError_t launch_inner_lsq(int d, int ldh, const double* H, const double* sv, double* coef, cudaStream_t s);
+// inner Arnoldi bookkeeping; sc holds the rotated Hessenberg, the rotations, g and the
+// number of columns before a breakdown: inner_scalar_doubles(d) doubles
+inline size_t inner_scalar_doubles(int d) { return (size_t)(d + 1) * d + 2 * (size_t)d + (size_t)(d + 1) + 1; }
+cudaError_t launch_inner_start(int d, const double* nrm2, double* sv, double* dinv, float* inv_s, double* sc,
+                               cudaStream_t s);
+cudaError_t launch_inner_col(int j, int d, const double* dd, const double* nrm2, double* sv, double* dinv, float* inv_s,
+                             double* sc, cudaStream_t s);
+cudaError_t launch_inner_lsq(int d, const double* sv, double* sc, double* coef, cudaStream_t s);
 // out = sum_i coef_i U_i (FP32); x += sum_i coef_i Z_i (FP32 vectors into FP64)
 cudaError_t launch_combine_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* coef, float* out,
                                cudaStream_t s);

@@ -233,19 +233,19 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32) {
   const int64_t n = c->n3(), N = c->n_nodes;
   cudaStream_t s = c->stream;
   float* Q = c->Qin;
-  double* H = c->isc;                        // [(d+1) x d], leading dimension d
-  double* sv = H + (size_t)(d + 1) * d;      // [d+1] norms s_i of the basis vectors
-  double* dinv = sv + (d + 2);               // [d+1] 1 / s_i^2
-  double* dd = dinv + (d + 2);               // [d+1] projections
-  double* nrm2 = dd + (d + 2);               // [1]
-  double* coef = nrm2 + 2;                   // [d] combination coefficients
+  double* sc = c->isc;                           // rotated Hessenberg, rotations, g, count
+  double* sv = sc + inner_scalar_doubles(d);     // [d+1] norms s_i of the basis vectors
+  double* dinv = sv + (d + 2);                   // [d+1] 1 / s_i^2
+  double* dd = dinv + (d + 2);                   // [d+1] projections
+  double* nrm2 = dd + (d + 2);                   // [1]
+  double* coef = nrm2 + 2;                       // [d] combination coefficients
   float* inv_s = c->iinv;
   CK(launch_to_f32(n, u, Q, s));
   {
     ProfScope ps(c, PNP_PROF_INNER, 4.0 * n, 2.0 * n);
     CK(launch_multi_axpy_norm_f32(n, 0, Q, n, dd, dinv, Q, c->part, nrm2, s));
   }
-  CK(launch_inner_start(nrm2, sv, dinv, inv_s, s));
+  CK(launch_inner_start(d, nrm2, sv, dinv, inv_s, sc, s));
   for (int j = 0; j < d; ++j) {
     float* w = Q + (size_t)(j + 1) * n;
     {
@@ -259,9 +259,9 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32) {
       CK(launch_multi_dot_f32(n, j + 1, Q, n, w, c->part, dd, s));
       CK(launch_multi_axpy_norm_f32(n, j + 1, Q, n, dd, dinv, w, c->part, nrm2, s));
     }
-    CK(launch_inner_col(j, d, dd, nrm2, H, sv, dinv, inv_s, s));
+    CK(launch_inner_col(j, d, dd, nrm2, sv, dinv, inv_s, sc, s));
   }
-  CK(launch_inner_lsq(d, d, H, sv, coef, s));
+  CK(launch_inner_lsq(d, sv, sc, coef, s));
   CK(launch_combine_f32(n, d, Q, n, coef, c->JV32, s));
   ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
   CK(launch_block_apply32(N, c->Dinv32, c->JV32, nullptr, z32, s));
