@@ -325,7 +325,8 @@ int ctx_alloc_krylov(pnp_ctx* c, int m) {
   c->m_alloc = 0;
   const size_t bb = sizeof(double) * (size_t)(m + 1) * (size_t)c->n3();
   cudaError_t e = cudaMalloc((void**)&c->basis, bb);
-  const size_t part_rows = std::max<size_t>((size_t)kRedBlocks, (size_t)multi_dot_blocks(c->n3()));
+  const size_t part_rows =
+      std::max<size_t>(std::max<size_t>((size_t)kRedBlocks, (size_t)kInnerBlocks), (size_t)multi_dot_blocks(c->n3()));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, sizeof(double) * part_rows * (m + 2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->dsc, sizeof(double) * (4 * (m + 2) + 16));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->hpin, sizeof(double) * (4 * (m + 2) + 16));

@@ -35,13 +35,12 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
   return r;
 }
 
-// d_i = U_i . w (i < k) for FP32 vectors.  Persistent grid (kDotBlocks = 4 per SM): each
+// d_i = U_i . w (i < k) for FP32 vectors.  Persistent grid (kInnerBlocks, 8 per SM): each
 // block strides over chunks of 256 x kRows rows; for every group of four basis vectors a
 // thread accumulates its rows of all chunks (w re-read from L2 per group), then one warp
 // reduce-scatter and a fixed-order block sum give the block's partials part[block][k].
 constexpr int kRows = 4;
-constexpr int kDotBlocks = 4 * 152;
-__global__ void __launch_bounds__(256, 4) k_multi_dot_f32(int64_t n, int k, const float* __restrict__ Ub, int64_t ld,
+__global__ void __launch_bounds__(256, 8) k_multi_dot_f32(int64_t n, int k, const float* __restrict__ Ub, int64_t ld,
                                                           const float* __restrict__ w, double* __restrict__ part) {
   __shared__ float sh[4][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -82,8 +81,10 @@ __global__ void __launch_bounds__(256, 4) k_multi_dot_f32(int64_t n, int k, cons
   }
 }
 
-// w -= sum_i (d_i dinv_i) U_i (i < k) in FP32, then per-block partials of w . w
-__global__ void __launch_bounds__(256) k_multi_axpy_norm_f32(int64_t n, int k, const float* __restrict__ Ub,
+// w -= sum_i (d_i dinv_i) U_i (i < k) in FP32, then per-block partials of w . w.
+// Persistent grid of 6 blocks per SM (40 registers).
+constexpr int kUpdBlocks = 6 * 152;
+__global__ void __launch_bounds__(256, 6) k_multi_axpy_norm_f32(int64_t n, int k, const float* __restrict__ Ub,
                                                              int64_t ld, const double* __restrict__ d,
                                                              const double* __restrict__ dinv, float* __restrict__ w,
                                                              double* __restrict__ part) {
@@ -92,17 +93,23 @@ __global__ void __launch_bounds__(256) k_multi_axpy_norm_f32(int64_t n, int k, c
   for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = (float)(d[i] * dinv[i]);
   __syncthreads();
   float ss = 0.0f;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    float v0 = w[t], v1 = 0.0f;
-    int i = 0;
-    for (; i + 2 <= k; i += 2) {
-      v0 = fmaf(-cf[i], Ub[(int64_t)i * ld + t], v0);
-      v1 = fmaf(-cf[i + 1], Ub[(int64_t)(i + 1) * ld + t], v1);
+  // two rows per thread per pass (a grid stride apart): twice the independent loads in flight
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += 2 * stride) {
+    const int64_t t2 = t + stride;
+    const bool two = t2 < n;
+    float a = w[t], b = two ? w[t2] : 0.0f;
+    for (int i = 0; i < k; ++i) {
+      const float* ui = Ub + (int64_t)i * ld;
+      a = fmaf(-cf[i], ui[t], a);
+      if (two) b = fmaf(-cf[i], ui[t2], b);
     }
-    if (i < k) v0 = fmaf(-cf[i], Ub[(int64_t)i * ld + t], v0);
-    const float v = v0 + v1;
-    if (k > 0) w[t] = v;
-    ss = fmaf(v, v, ss);
+    if (k > 0) {
+      w[t] = a;
+      if (two) w[t2] = b;
+    }
+    ss = fmaf(a, a, ss);
+    ss = fmaf(b, b, ss);
   }
   const double tot = block_sum_d((double)ss, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
@@ -251,7 +258,7 @@ __global__ void k_to_f64_scaled(int64_t n, const float* __restrict__ x, double s
 
 }  // namespace
 
-int inner_dot_blocks(int64_t) { return kDotBlocks; }
+int inner_dot_blocks(int64_t) { return kInnerBlocks; }
 int inner_max_depth() { return kMaxInner; }
 
 cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, const float* w, double* part, double* d,
@@ -266,9 +273,9 @@ cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, 
 
 cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* d,
                                        const double* dinv, float* w, double* part, double* nrm2, cudaStream_t s) {
-  k_multi_axpy_norm_f32<<<kRedBlocks, 256, (k > 0 ? k : 1) * sizeof(float), s>>>(n, k, Ub, ld, d, dinv, w, part);
+  k_multi_axpy_norm_f32<<<kUpdBlocks, 256, (k > 0 ? k : 1) * sizeof(float), s>>>(n, k, Ub, ld, d, dinv, w, part);
   note_launch();
-  launch_reduce_parts(kRedBlocks, 1, part, nrm2, s);
+  launch_reduce_parts(kUpdBlocks, 1, part, nrm2, s);
   return cudaGetLastError();
 }
 

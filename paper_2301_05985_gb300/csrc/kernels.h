@@ -72,6 +72,9 @@ cudaError_t launch_diag_rows(const RowArgs& R, T* Dg, cudaStream_t s);
 // ------------------------------------------------------------------ vector kernels
 // All reductions are deterministic: fixed grid, per-block partials, one final block.
 constexpr int kRedBlocks = 608;  // 4 x 152 SMs
+// persistent grid of the inner FP32 Gram-Schmidt kernels: 8 blocks of 256 per SM, enough
+// loads in flight for a streaming kernel with few registers
+constexpr int kInnerBlocks = 8 * 152;
 constexpr int kRedThreads = 256;
 
 // history h_s = (b1 c^k + b2 c^{k-1}) / dt, [N][2]
@@ -124,7 +127,7 @@ int inner_max_depth();
 // d_i = U_i . w (FP32 vectors, i < k); part: [inner_dot_blocks(n)][k]
 cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, const float* w, double* part, double* d,
                                  cudaStream_t s);
-// w -= sum_i d_i dinv_i U_i (i < k, FP32); nrm2[0] = w . w afterwards (part: [kRedBlocks])
+// w -= sum_i d_i dinv_i U_i (i < k, FP32); nrm2[0] = w . w afterwards (part: at most [kInnerBlocks])
 cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* d,
                                        const double* dinv, float* w, double* part, double* nrm2, cudaStream_t s);
 // y = Dinv32 (inv_s[0] u) per node (inv_s may be null: scale 1)
