@@ -57,6 +57,8 @@ struct pnp_ctx {
   float* iinv = nullptr;    // [d+2] inverse norms of the inner basis vectors
   int inner_m = 0, inner_d = 0;
   float4* rec32 = nullptr;  // [N][2] FP32 node records of the state for the FP32 J V
+  float4* V4 = nullptr;     // [N] padded FP32 direction of the inner solve's J V
+  float4* JV4 = nullptr;    // [N] padded FP32 J V accumulator
   int64_t basis_bytes = 0;
 
   // statistics of the last solve (for the time stepper)

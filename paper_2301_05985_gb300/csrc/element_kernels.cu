@@ -614,6 +614,8 @@ static bool per_thread_elements() {
   return v;
 }
 
+bool element_kernel_is_lanes() { return !per_thread_elements(); }
+
 double element_kernel_flops(int D, bool jv) {
   const double NC = 1 << D;
   if (per_thread_elements()) {

@@ -159,6 +159,40 @@ __device__ __forceinline__ void load_record(const ElemArgs<T>& A, int32_t id, bo
   vn[0] = r1.y; vn[1] = r1.z; vn[2] = r1.w;
 }
 
+// the padded FP32 direction at node id (hanging: the parents' mean)
+template <typename T>
+__device__ __forceinline__ void load_dir4(const ElemArgs<T>& A, int32_t id, bool valid, float (&dn)[3]) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) {
+    if (id >= 0) {
+      v = __ldg(A.V4 + id);
+    } else {
+      const int32_t h = -id - 1;
+      const int np = A.hang_np[h];
+      const float wgt = np == 2 ? 0.5f : 0.25f;
+      for (int p = 0; p < np; ++p) {
+        const float4 a = __ldg(A.V4 + A.hang_par[4 * h + p]);
+        v.x += wgt * a.x; v.y += wgt * a.y; v.z += wgt * a.z;
+      }
+    }
+  }
+  dn[0] = v.x; dn[1] = v.y; dn[2] = v.z;
+}
+
+// one vector atomic per target node (hanging: weighted to its parents)
+template <typename T>
+__device__ __forceinline__ void scatter4(const ElemArgs<T>& A, int32_t id, const float (&r)[3]) {
+  if (id >= 0) {
+    atomicAdd(A.out4 + id, make_float4(r[0], r[1], r[2], 0.f));
+  } else {
+    const int32_t h = -id - 1;
+    const int np = A.hang_np[h];
+    const float wgt = np == 2 ? 0.5f : 0.25f;
+    for (int p = 0; p < np; ++p)
+      atomicAdd(A.out4 + A.hang_par[4 * h + p], make_float4(wgt * r[0], wgt * r[1], wgt * r[2], 0.f));
+  }
+}
+
 template <typename T, int D, bool JV>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(ElemArgs<T> A, LaneParams<T> K) {
   constexpr int NC = 1 << D;
@@ -246,7 +280,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
     for (int k = 0; k < 3; ++k) Phi[2][k] = e2 * gp[k];
   } else {
     T dn[3];
-    load_node<T, 3>(A, id, valid, A.V, 3, dn);
+    if constexpr (sizeof(T) == 4) {
+      if (A.V4) load_dir4(A, id, valid, dn);
+      else load_node<T, 3>(A, id, valid, A.V, 3, dn);
+    } else {
+      load_node<T, 3>(A, id, valid, A.V, 3, dn);
+    }
     T dcv[2], dgc[2][3], dgp[3], dR[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) interp_vg<T, D>(dn[s], nb, sh, dcv[s], dgc[s]);
@@ -278,6 +317,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
 #pragma unroll
   for (int f = 0; f < 3; ++f) r[f] = w * test_t<T, D>(S[f], Phi[f], nb, sh);
   if (!valid) return;
+  if constexpr (sizeof(T) == 4) {
+    if (A.out4) {
+      scatter4(A, id, r);
+      return;
+    }
+  }
   if (id >= 0) {
 #pragma unroll
     for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)id + f, r[f]);

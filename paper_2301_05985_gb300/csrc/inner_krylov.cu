@@ -128,6 +128,56 @@ __global__ void k_block_apply32(int64_t N, const float* __restrict__ Dinv, const
   y[3 * i + 2] = fmaf(B[6], a, fmaf(B[7], b, B[8] * c));
 }
 
+__global__ void k_block_apply32_pad(int64_t N, const float* __restrict__ Dinv, const float* __restrict__ u,
+                                    const float* __restrict__ inv_s, float4* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float sc = inv_s ? inv_s[0] : 1.0f;
+  const float* B = Dinv + 9 * i;
+  const float a = sc * u[3 * i], b = sc * u[3 * i + 1], c = sc * u[3 * i + 2];
+  y[i] = make_float4(fmaf(B[0], a, fmaf(B[1], b, B[2] * c)), fmaf(B[3], a, fmaf(B[4], b, B[5] * c)),
+                     fmaf(B[6], a, fmaf(B[7], b, B[8] * c)), 0.0f);
+}
+
+// out <- acc with the Dirichlet rows of J V (= V); hanging rows are left to k_hanging_rows4
+__global__ void k_pack_jv4(int64_t N, const uint8_t* __restrict__ faces, BcTable bc, const float4* __restrict__ V4,
+                           const float4* __restrict__ acc, float* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint8_t fm = faces[i];
+  if (fm & 0x80) return;
+  const float4 a = acc[i];
+  float r[3] = {a.x, a.y, a.z};
+  if (fm & 0x3F) {
+    const float4 v = V4[i];
+    const float vv[3] = {v.x, v.y, v.z};
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+      if (fm & bc.dir_faces[f] & 0x3F) r[f] = vv[f];
+  }
+  out[3 * i] = r[0];
+  out[3 * i + 1] = r[1];
+  out[3 * i + 2] = r[2];
+}
+
+// constraint rows of hanging nodes: out_h = V_h - sum_p w_p V_p, V padded
+__global__ void k_hanging_rows4(int64_t H, const int32_t* __restrict__ hnode, const int32_t* __restrict__ hpar,
+                                const uint8_t* __restrict__ hnp, const float4* __restrict__ V4, float* __restrict__ out) {
+  const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  const int np = hnp[h];
+  const float wgt = np == 2 ? 0.5f : 0.25f;
+  const int64_t id = hnode[h];
+  float4 s = V4[id];
+  for (int p = 0; p < np; ++p) {
+    const float4 a = V4[hpar[4 * h + p]];
+    s.x -= wgt * a.x; s.y -= wgt * a.y; s.z -= wgt * a.z;
+  }
+  out[3 * id] = s.x;
+  out[3 * id + 1] = s.y;
+  out[3 * id + 2] = s.z;
+}
+
 // Arnoldi bookkeeping of the inner process.  Basis vectors u_i are kept unnormalised
 // with norms s_i (q_i = u_i / s_i); the Hessenberg columns are reduced by Givens rotations
 // as they arrive, so the least-squares solve at the end is a back-substitution.
@@ -283,6 +333,27 @@ cudaError_t launch_block_apply32(int64_t N, const float* Dinv32, const float* u,
                                  cudaStream_t s) {
   if (N) {
     k_block_apply32<<<nblk(N, 256), 256, 0, s>>>(N, Dinv32, u, inv_s, y);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_apply32_pad(int64_t N, const float* Dinv32, const float* u, const float* inv_s, float4* y4,
+                                     cudaStream_t s) {
+  if (N) {
+    k_block_apply32_pad<<<nblk(N, 256), 256, 0, s>>>(N, Dinv32, u, inv_s, y4);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, const float4* acc4, float* out, cudaStream_t s) {
+  if (R.n_nodes) {
+    k_pack_jv4<<<nblk(R.n_nodes, 256), 256, 0, s>>>(R.n_nodes, R.faces, R.bc, V4, acc4, out);
+    note_launch();
+  }
+  if (R.n_hanging) {
+    k_hanging_rows4<<<nblk(R.n_hanging, 256), 256, 0, s>>>(R.n_hanging, R.hnode, R.hpar, R.hnp, V4, out);
     note_launch();
   }
   return cudaGetLastError();

@@ -21,6 +21,10 @@ struct ElemArgs {
   // FP32 lane kernel only (may be null): per node {c+, c-, phi, h+, h-, v0, v1, v2}, 32 B
   // aligned, the same values as U, hs and adv in one sector
   const float4* rec = nullptr;
+  // FP32 J V only (may be null): direction and accumulated output padded to [N] float4,
+  // read with one 16-byte load and added with one vector atomic per node
+  const float4* V4 = nullptr;
+  float4* out4 = nullptr;
 };
 
 // Arguments of the Dirichlet / hanging row kernels.
@@ -62,6 +66,8 @@ cudaError_t launch_element_lanes(int dim, bool jv, const ElemArgs<T>& A, cudaStr
 // floating-point operations per element (an FMA counts 2) of the element kernel that
 // launch_element runs, counted from the formulation it evaluates
 double element_kernel_flops(int dim, bool jv);
+// true when launch_element runs the lane-group kernel (not PNP_ELEMENT_KERNEL=thread)
+bool element_kernel_is_lanes();
 template <typename T>
 cudaError_t launch_block_diag(int dim, const ElemArgs<T>& A, T* Dout, cudaStream_t s);
 template <typename T>
@@ -130,9 +136,14 @@ cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, 
 // w -= sum_i d_i dinv_i U_i (i < k, FP32); nrm2[0] = w . w afterwards (part: at most [kInnerBlocks])
 cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* d,
                                        const double* dinv, float* w, double* part, double* nrm2, cudaStream_t s);
-// y = Dinv32 (inv_s[0] u) per node (inv_s may be null: scale 1)
+// y = Dinv32 (inv_s[0] u) per node (inv_s may be null: scale 1); y4: the same, padded
 cudaError_t launch_block_apply32(int64_t N, const float* Dinv32, const float* u, const float* inv_s, float* y,
                                  cudaStream_t s);
+cudaError_t launch_block_apply32_pad(int64_t N, const float* Dinv32, const float* u, const float* inv_s, float4* y4,
+                                     cudaStream_t s);
+// out [N][3] <- acc4 with the Dirichlet rows set to V4 and the hanging rows to
+// V4_h - sum_p w_p V4_p (the J V row fix-ups of the padded FP32 path)
+cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, const float4* acc4, float* out, cudaStream_t s);
 // inner Arnoldi bookkeeping; sc holds the rotated Hessenberg, the rotations, g and the
 // number of columns before a breakdown: inner_scalar_doubles(d) doubles
 inline size_t inner_scalar_doubles(int d) { return (size_t)(d + 1) * d + 2 * (size_t)d + (size_t)(d + 1) + 1; }

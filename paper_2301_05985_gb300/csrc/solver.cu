@@ -225,6 +225,24 @@ static int apply_op(pnp_ctx* c, const double* U, const double* x, double* w, int
   return PNP_OK;
 }
 
+// FP32 J V of the inner solve: the direction padded to 16 bytes per node (one load), the
+// output accumulated with one vector atomic per node, then packed to [N][3] with the
+// Dirichlet and hanging rows of J V.  Lane-group kernel only.
+static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out) {
+  CK(cudaMemsetAsync(c->JV4, 0, sizeof(float4) * c->n_nodes, c->stream));
+  {
+    ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_kernel_flops(c->dim, true) * c->n_elem);
+    ElemArgs<float> A = elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr);
+    A.rec = c->rec32;
+    A.V4 = V4;
+    A.out4 = c->JV4;
+    CK(launch_element_lanes<float>(c->dim, true, A, c->stream));
+  }
+  CK(launch_pack_jv4(c->rows(), V4, c->JV4, out, c->stream));
+  c->jv_count++;
+  return PNP_OK;
+}
+
 // z = P(u): d steps of right-preconditioned FP32 GMRES on (J M^-1) t = u from t = 0, then
 // z = M^-1 t (M: the block diagonal).  A fixed number of steps with the Hessenberg
 // bookkeeping on the device: no host round trip.  P is homogeneous, P(a u) = a P(u).
@@ -246,13 +264,22 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32) {
     CK(launch_multi_axpy_norm_f32(n, 0, Q, n, dd, dinv, Q, c->part, nrm2, s));
   }
   CK(launch_inner_start(d, nrm2, sv, dinv, inv_s, sc, s));
+  const bool pad = !c->use_patches && element_kernel_is_lanes();
   for (int j = 0; j < d; ++j) {
     float* w = Q + (size_t)(j + 1) * n;
-    {
-      ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
-      CK(launch_block_apply32(N, c->Dinv32, Q + (size_t)j * n, inv_s + j, c->V32, s));
+    if (pad) {
+      {
+        ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
+        CK(launch_block_apply32_pad(N, c->Dinv32, Q + (size_t)j * n, inv_s + j, c->V4, s));
+      }
+      RC(ctx_jv32_pad(c, c->V4, w));
+    } else {
+      {
+        ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
+        CK(launch_block_apply32(N, c->Dinv32, Q + (size_t)j * n, inv_s + j, c->V32, s));
+      }
+      RC(ctx_jv32(c, c->V32, w));
     }
-    RC(ctx_jv32(c, c->V32, w));
     {
       const double nj = (double)n * (j + 1);
       ProfScope ps(c, PNP_PROF_INNER, 4.0 * (nj + n) + 4.0 * (nj + 2.0 * n), 4.0 * nj + 2.0 * n);
