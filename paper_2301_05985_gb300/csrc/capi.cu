@@ -162,7 +162,7 @@ static void free_ctx_memory(pnp_ctx* c) {
   void* ptrs[] = {c->d_conn, c->d_level, c->d_faces, c->d_hnode, c->d_hpar, c->d_hnp, c->U, c->Uk, c->Ukm1,
                   c->adv, c->vel, c->vel_prev, c->hs, c->U32, c->adv32, c->hs32, c->V32, c->JV32, c->F,
                   c->dU, c->Ut, c->Ft, c->rhs, c->Dinv, c->D32, c->basis, c->w, c->z, c->r, c->part, c->dsc,
-                  c->dflag, c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv, c->rec32, c->V4, c->JV4};
+                  c->dflag, c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv, c->rec32, c->V4, c->JV4, c->qp32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->pt_alloc) cudaFree(p);
@@ -345,12 +345,12 @@ int ctx_alloc_inner(pnp_ctx* c, int m, int d) {
   m = std::max(m, c->inner_m);
   d = std::max(d, c->inner_d);
   if (int rc = ctx_alloc_krylov(c, std::max(c->m_alloc, d))) return rc;  // partials for d projections
-  void* old[] = {c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv, c->V4, c->JV4};
+  void* old[] = {c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv, c->V4, c->JV4, c->qp32};
   for (void* q : old)
     if (q) cudaFree(q);
   c->Zb = c->Qin = c->Dinv32 = c->iinv = nullptr;
   c->isc = nullptr;
-  c->V4 = c->JV4 = nullptr;
+  c->V4 = c->JV4 = c->qp32 = nullptr;
   c->inner_m = c->inner_d = 0;
   const size_t n = (size_t)c->n3();
   cudaError_t e = cudaMalloc((void**)&c->Zb, sizeof(float) * (size_t)m * n);
@@ -360,6 +360,7 @@ int ctx_alloc_inner(pnp_ctx* c, int m, int d) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->iinv, sizeof(float) * (size_t)(d + 2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->V4, sizeof(float4) * (size_t)c->n_nodes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->JV4, sizeof(float4) * (size_t)c->n_nodes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->qp32, sizeof(float4) * 4 * ((size_t)c->n_elem << c->dim));
   if (e != cudaSuccess) {
     pnp_set_error("inner Krylov scratch allocation failed: %s", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? PNP_ERR_NOMEM : PNP_ERR_CUDA;

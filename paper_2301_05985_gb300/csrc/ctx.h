@@ -59,6 +59,7 @@ struct pnp_ctx {
   float4* rec32 = nullptr;  // [N][2] FP32 node records of the state for the FP32 J V
   float4* V4 = nullptr;     // [N] padded FP32 direction of the inner solve's J V
   float4* JV4 = nullptr;    // [N] padded FP32 J V accumulator
+  float4* qp32 = nullptr;   // [4][2^dim E] stored Gauss-point linearisation of the FP32 J V
   int64_t basis_bytes = 0;
 
   // statistics of the last solve (for the time stepper)

@@ -159,6 +159,41 @@ __device__ __forceinline__ void load_record(const ElemArgs<T>& A, int32_t id, bo
   vn[0] = r1.y; vn[1] = r1.z; vn[2] = r1.w;
 }
 
+// U-dependent quantities at this lane's Gauss point: values and gradients of c+-, grad
+// phi, the advection v, the history h, tau_c, R_s and P_s = v - z_s grad phi
+template <typename T, int D>
+__device__ __forceinline__ void lane_state(const T (&un)[3], const T (&vn)[3], const T (&hn)[2], T nb,
+                                           const T (&sh)[3], T kappa, T tau0, T G2, T (&cv)[2], T (&gc)[2][3],
+                                           T (&gp)[3], T (&v)[3], T (&hq)[2], T& tau, T (&R)[2], T (&P)[2][3]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    interp_vg<T, D>(un[s], nb, sh, cv[s], gc[s]);
+    hq[s] = interp_v<T, D>(hn[s], nb);
+  }
+  interp_g<T, D>(un[2], nb, sh, gp);
+  T vv = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v[k] = T(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    v[k] = interp_v<T, D>(vn[k], nb);
+    vv = fma(v[k], v[k], vv);
+  }
+  if constexpr (sizeof(T) == 4) tau = rsqrtf(tau0 + G2 * vv);
+  else tau = T(1) / sqrt(tau0 + G2 * vv);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T z = s == 0 ? T(1) : T(-1);
+    T pg = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      P[s][k] = v[k] - z * gp[k];
+      pg = fma(P[s][k], gc[s][k], pg);
+    }
+    R[s] = fma(kappa, cv[s], hq[s] + pg);
+  }
+}
+
 // the padded FP32 direction at node id (hanging: the parents' mean)
 template <typename T>
 __device__ __forceinline__ void load_dir4(const ElemArgs<T>& A, int32_t id, bool valid, float (&dn)[3]) {
@@ -232,34 +267,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
   }
 
   // state at this lane's Gauss point
-  T cv[2], gc[2][3], gp[3], v[3] = {T(0), T(0), T(0)}, hq[2];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    interp_vg<T, D>(un[s], nb, sh, cv[s], gc[s]);
-    hq[s] = interp_v<T, D>(hn[s], nb);
-  }
-  interp_g<T, D>(un[2], nb, sh, gp);
-  T vv = T(0);
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    v[k] = interp_v<T, D>(vn[k], nb);
-    vv = fma(v[k], v[k], vv);
-  }
-  T tau;
-  if constexpr (sizeof(T) == 4) tau = rsqrtf(tau0 + G2 * vv);
-  else tau = T(1) / sqrt(tau0 + G2 * vv);
-  T R[2], P[2][3];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const T z = s == 0 ? T(1) : T(-1);
-    T pg = T(0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      P[s][k] = v[k] - z * gp[k];
-      pg = fma(P[s][k], gc[s][k], pg);
-    }
-    R[s] = fma(kappa, cv[s], hq[s] + pg);
-  }
+  T cv[2], gc[2][3], gp[3], v[3], hq[2], tau, R[2], P[2][3];
+  lane_state<T, D>(un, vn, hn, nb, sh, kappa, tau0, G2, cv, gc, gp, v, hq, tau, R, P);
 
   T S[3], Phi[3][3];
   if constexpr (!JV) {
@@ -338,6 +347,124 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
   }
 }
 
+// ---- FP32 J V from a stored linearisation ---------------------------------------
+// Inside one Krylov solve the state (U, h, v) is fixed, so the Gauss-point quantities J V
+// needs from it are computed once per solve and stored per lane, four float4 in
+// lane-major order (qp[j * L + t], L = 2^d E): (v0 v1 v2 gp0) (gp1 gp2 gc+0 gc+1)
+// (gc+2 gc-0 gc-1 gc-2) (tau, z+(c+ - tau R+), z-(c- - tau R-), 0).  Each J V then reads
+// 64 B per lane, coalesced, instead of gathering and interpolating the state.
+constexpr int kLaneThreads = 256;
+
+template <int D>
+__global__ void __launch_bounds__(kLaneThreads, 5) k_lane_state(ElemArgs<float> A, LaneParams<float> K, float4* qp) {
+  constexpr int NC = 1 << D;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((t & ~int64_t(31)) / NC >= A.n_elem) return;
+  const int64_t e = t / NC;
+  const int c = (int)(t & (NC - 1));
+  const bool valid = e < A.n_elem;
+  const int32_t id = valid ? __ldg(A.conn + e * NC + c) : 0;
+  const int lev = valid ? A.level[e] : 0;
+  const float inv_h = pow2i(lev, 0.0f);
+  const float nb = float(-0.5 * (1.0 - kG));
+  float sh[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sh[k] = ((c >> k) & 1) ? inv_h : -inv_h;
+  const float G2 = pow2i(2 * lev + 2, 0.0f);
+  const float tau0 = fmaf(K.cid * G2, G2, K.tau_t);
+  float un[3], vn[3], hn[2];
+  load_record(A, id, valid, un, hn, vn);
+  float cv[2], gc[2][3], gp[3], v[3], hq[2], tau, R[2], P[2][3];
+  lane_state<float, D>(un, vn, hn, nb, sh, K.kappa, tau0, G2, cv, gc, gp, v, hq, tau, R, P);
+  if (!valid) return;
+  const int64_t L = A.n_elem * NC;
+  const float zc0 = cv[0] - tau * R[0], zc1 = -(cv[1] - tau * R[1]);
+  qp[t] = make_float4(v[0], v[1], v[2], gp[0]);
+  qp[L + t] = make_float4(gp[1], gp[2], gc[0][0], gc[0][1]);
+  qp[2 * L + t] = make_float4(gc[0][2], gc[1][0], gc[1][1], gc[1][2]);
+  qp[3 * L + t] = make_float4(tau, zc0, zc1, 0.0f);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<float> A, LaneParams<float> K,
+                                                                 const float4* __restrict__ qp) {
+  constexpr int NC = 1 << D;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((t & ~int64_t(31)) / NC >= A.n_elem) return;
+  const int64_t e = t / NC;
+  const int c = (int)(t & (NC - 1));
+  const bool valid = e < A.n_elem;
+  const int32_t id = valid ? __ldg(A.conn + e * NC + c) : 0;
+  const int lev = valid ? A.level[e] : 0;
+  const float inv_h = pow2i(lev, 0.0f);
+  const float w = pow2i(-D * (lev + 1), 0.0f);
+  const float nb = float(-0.5 * (1.0 - kG));
+  float sh[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sh[k] = ((c >> k) & 1) ? inv_h : -inv_h;
+  const float kappa = K.kappa, e2 = K.e2;
+  const int64_t L = A.n_elem * NC;
+  float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0;
+  if (valid) {
+    q0 = __ldg(qp + t);
+    q1 = __ldg(qp + L + t);
+    q2 = __ldg(qp + 2 * L + t);
+    q3 = __ldg(qp + 3 * L + t);
+  }
+  const float v[3] = {q0.x, q0.y, q0.z}, gp[3] = {q0.w, q1.x, q1.y};
+  const float gc[2][3] = {{q1.z, q1.w, q2.x}, {q2.y, q2.z, q2.w}};
+  const float tau = q3.x, zc_tR[2] = {q3.y, q3.z};
+  float dn[3];
+  if (A.V4) load_dir4(A, id, valid, dn);
+  else load_node<float, 3>(A, id, valid, A.V, 3, dn);
+  float dcv[2], dgc[2][3], dgp[3], dR[2], S[3], Phi[3][3];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) interp_vg<float, D>(dn[s], nb, sh, dcv[s], dgc[s]);
+  interp_g<float, D>(dn[2], nb, sh, dgp);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const float z = s == 0 ? 1.0f : -1.0f;
+    float P[3], vg = 0.0f, pg = 0.0f, gcd = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      P[k] = v[k] - z * gp[k];
+      vg = fmaf(v[k], dgc[s][k], vg);
+      pg = fmaf(P[k], dgc[s][k], pg);
+      gcd = fmaf(gc[s][k], dgp[k], gcd);
+    }
+    dR[s] = fmaf(kappa, dcv[s], pg - z * gcd);
+    S[s] = fmaf(kappa, dcv[s], vg);
+    const float tdR = tau * dR[s];
+    const float zdc = z * dcv[s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Phi[s][k] = fmaf(tdR, P[k], fmaf(zc_tR[s], dgp[k], fmaf(zdc, gp[k], dgc[s][k])));
+  }
+  S[2] = fmaf(tau, dR[0] - dR[1], dcv[1] - dcv[0]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Phi[2][k] = e2 * dgp[k];
+  float r[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) r[f] = w * test_t<float, D>(S[f], Phi[f], nb, sh);
+  if (!valid) return;
+  if (A.out4) {
+    scatter4(A, id, r);
+    return;
+  }
+  if (id >= 0) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)id + f, r[f]);
+  } else {
+    const int32_t hh = -id - 1;
+    const int np = A.hang_np[hh];
+    const float wgt = np == 2 ? 0.5f : 0.25f;
+    for (int p = 0; p < np; ++p) {
+      const int32_t pid = A.hang_par[4 * hh + p];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)pid + f, wgt * r[f]);
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -359,3 +486,32 @@ cudaError_t launch_element_lanes(int dim, bool jv, const ElemArgs<T>& A, cudaStr
 }
 template cudaError_t launch_element_lanes<double>(int, bool, const ElemArgs<double>&, cudaStream_t);
 template cudaError_t launch_element_lanes<float>(int, bool, const ElemArgs<float>&, cudaStream_t);
+
+// the stored linearisation of the FP32 J V (qp: 4 * 2^dim * n_elem float4; A.rec set)
+cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, cudaStream_t s) {
+  if (A.n_elem == 0) return cudaSuccess;
+  const LaneParams<float> K{float(A.P.kappa), float(A.P.tau_t), float(A.P.C_I * dim), float(A.P.eps2x2)};
+  const unsigned blocks = (unsigned)(((A.n_elem << dim) + kLaneThreads - 1) / kLaneThreads);
+  if (dim == 2) k_lane_state<2><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+  else k_lane_state<3><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, cudaStream_t s) {
+  if (A.n_elem == 0) return cudaSuccess;
+  const LaneParams<float> K{float(A.P.kappa), float(A.P.tau_t), float(A.P.C_I * dim), float(A.P.eps2x2)};
+  const unsigned blocks = (unsigned)(((A.n_elem << dim) + kLaneThreads - 1) / kLaneThreads);
+  if (dim == 2) k_jv_from_state<2><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+  else k_jv_from_state<3><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// per lane of the stored-linearisation J V: direction values and gradients, the J V
+// physics (incl. P_s), three transposes; the state part is read, not computed
+double jv_from_state_flops(int D) {
+  const double tri = D * (D - 1) / 2.0;
+  const double vg = 3 * tri + 4 * D, g = vg - 2, tt = 6 * D + 3 * tri + 1;
+  return (double)(1 << D) * (2 * vg + g + 101 + 12 + 3 * tt);
+}

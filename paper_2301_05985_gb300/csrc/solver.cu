@@ -228,15 +228,25 @@ static int apply_op(pnp_ctx* c, const double* U, const double* x, double* w, int
 // FP32 J V of the inner solve: the direction padded to 16 bytes per node (one load), the
 // output accumulated with one vector atomic per node, then packed to [N][3] with the
 // Dirichlet and hanging rows of J V.  Lane-group kernel only.
-static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out) {
+// With from_state, the state's Gauss-point quantities come from the linearisation stored
+// by launch_lane_state for the current Krylov solve.
+static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_state) {
   CK(cudaMemsetAsync(c->JV4, 0, sizeof(float4) * c->n_nodes, c->stream));
   {
-    ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_kernel_flops(c->dim, true) * c->n_elem);
     ElemArgs<float> A = elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr);
     A.rec = c->rec32;
     A.V4 = V4;
     A.out4 = c->JV4;
-    CK(launch_element_lanes<float>(c->dim, true, A, c->stream));
+    if (from_state) {
+      // direction in, result out (12 B per node each), the stored state (64 B per lane)
+      ProfScope ps(c, PNP_PROF_JV32, 24.0 * c->n_nodes + 64.0 * (double)(c->n_elem << c->dim) + c->conn_bytes(),
+                   jv_from_state_flops(c->dim) * c->n_elem);
+      CK(launch_jv_from_state(c->dim, A, c->qp32, c->stream));
+    } else {
+      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(),
+                   element_kernel_flops(c->dim, true) * c->n_elem);
+      CK(launch_element_lanes<float>(c->dim, true, A, c->stream));
+    }
   }
   CK(launch_pack_jv4(c->rows(), V4, c->JV4, out, c->stream));
   c->jv_count++;
@@ -246,7 +256,7 @@ static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out) {
 // z = P(u): d steps of right-preconditioned FP32 GMRES on (J M^-1) t = u from t = 0, then
 // z = M^-1 t (M: the block diagonal).  A fixed number of steps with the Hessenberg
 // bookkeeping on the device: no host round trip.  P is homogeneous, P(a u) = a P(u).
-static int inner_gmres32(pnp_ctx* c, const double* u, float* z32) {
+static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_state) {
   const int d = c->prm.gmres_inner;
   const int64_t n = c->n3(), N = c->n_nodes;
   cudaStream_t s = c->stream;
@@ -272,7 +282,7 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32) {
         ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
         CK(launch_block_apply32_pad(N, c->Dinv32, Q + (size_t)j * n, inv_s + j, c->V4, s));
       }
-      RC(ctx_jv32_pad(c, c->V4, w));
+      RC(ctx_jv32_pad(c, c->V4, w, from_state));
     } else {
       {
         ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
@@ -311,6 +321,14 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   if (prec == PNP_F32) RC(ctx_prepare_f32(c, U));
   const bool flex = prec == PNP_F32 && c->prm.gmres_inner > 0;
   if (flex) RC(ctx_alloc_inner(c, m, c->prm.gmres_inner));
+  // the inner J V reads the state's Gauss-point quantities stored once for this solve
+  const bool from_state = flex && !c->use_patches && element_kernel_is_lanes();
+  if (from_state) {
+    ElemArgs<float> A = elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr);
+    A.rec = c->rec32;
+    ProfScope ps(c, PNP_PROF_PRECOND, 32.0 * c->n_nodes + 64.0 * (double)(c->n_elem << c->dim) + c->conn_bytes());
+    CK(launch_lane_state(c->dim, A, c->qp32, s));
+  }
   double* V = c->basis;
   double* dd = c->dsc;                    // [m+2] dot products of one pass
   double* dinv = c->dsc + (m + 2);        // [m+2] 1 / s_i^2
@@ -363,7 +381,7 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       // z = M^-1 (u_j / s_j) ; w = J z   (flexible: z_j = P(u_j) / s_j kept in Zb)
       if (flex) {
         float* zj = c->Zb + (size_t)j * n;
-        RC(inner_gmres32(c, uj, zj));
+        RC(inner_gmres32(c, uj, zj, from_state));
         RC(ctx_jv32(c, zj, c->JV32));
         ProfScope ps(c, PNP_PROF_PRECOND, 20.0 * (double)n);
         CK(launch_to_f64_scaled(n, c->JV32, 1.0 / sv[j], w, s));
