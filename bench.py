@@ -180,6 +180,14 @@ def cpu_baseline_oracle(n_steps: int = 1):
                       f"solves, {t:.1f} s"}
 
 
+def workload_config(small: bool):
+    """The workload both arms name (the reference arm times the oracle on a bounded sample
+    of it, described in its cpu_baseline)."""
+    return {"workload": ("membrane-band octree L4-7 miniature" if small else
+                         "3D membrane-band octree, base level 5, level 8 for z<0.05 (2:1 graded)"),
+            "eps": EPS, "V": VOLT, "dt": DT, "velocity": "zero (no NS block)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -197,8 +205,7 @@ def run_reference(args):
     out = {"metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": "membrane-band octree level 3-5 miniature (oracle sample)", "eps": EPS,
-                      "V": VOLT, "dt": DT},
+           "config": workload_config(args.small),
            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": v},
            "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -439,10 +446,9 @@ def main():
         "metric": METRIC, "value": round(value, 6), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": ("membrane-band octree L4-7 miniature" if args.small else
-                                "3D membrane-band octree, base level 5, level 8 for z<0.05 (2:1 graded)"),
+        "config": {**workload_config(args.small),
                    "n_elem": mesh.n_elem, "n_nodes": N, "n_hanging": mesh.n_hanging, "dofs": 3 * N,
-                   "eps": EPS, "V": VOLT, "dt": DT, "mode": args.mode, "velocity": "zero (no NS block)",
+                   "mode": args.mode,
                    "krylov": ctx_krylov_desc(ctx.get_params(), args.mode),
                    "start": ("learned (judged vs extrapolated)" if learned else
                              "extrapolated" if args.mode == "mixed" else "previous step"),
