@@ -200,6 +200,18 @@ int pnp_residual(pnp_ctx* c, const double* U, double* F);
  * precision PNP_F64: V, JV are FP64 [n][3]; PNP_F32: V, JV are FP32 [n][3] and the
  * element arithmetic runs in FP32 (U is rounded to FP32 once per call). */
 int pnp_jv(pnp_ctx* c, const double* U, const void* V, void* JV, int precision);
+/* FP32 J V through a stored linearisation, for many directions at one state (the
+ * inner Krylov solve of the flexible GMRES uses the same kernels).  pnp_linearize
+ * evaluates at U (device FP64 [n][3]), with the context's history, advection, parameters
+ * and boundary conditions at this call, the state's quantities at every element's
+ * Gauss points that J V needs (Def. 3 linearised: v, grad phi, grad c+-, tau_c and
+ * z (c - tau_c R) per Gauss point, FP32, 64 B each, held by the context).
+ * pnp_jv_linearized then returns JV = J V for FP32 device vectors V, JV [n][3], equal to
+ * pnp_jv(..., PNP_F32) at that U up to FP32 summation order.  A later solver call
+ * (pnp_gmres, pnp_newton_solve, pnp_time_step) replaces the stored linearisation;
+ * pnp_jv_linearized then returns PNP_ERR_STATE until pnp_linearize is called again. */
+int pnp_linearize(pnp_ctx* c, const double* U);
+int pnp_jv_linearized(pnp_ctx* c, const float* V, float* JV);
 /* 3x3 diagonal blocks of J(U): D device FP64 [n][3][3] (row-major per node), exact
  * for the assembled operator including hanging-node coupling. */
 int pnp_block_diag(pnp_ctx* c, const double* U, double* D);

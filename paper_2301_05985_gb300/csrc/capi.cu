@@ -493,6 +493,27 @@ int pnp_jv(pnp_ctx* c, const double* U, const void* V, void* JV, int precision) 
   return PNP_OK;
 }
 
+int pnp_linearize(pnp_ctx* c, const double* U) {
+  CTX_GUARD(c);
+  if (!U) PNP_FAIL(PNP_ERR_ARG, "pnp_linearize: null pointer");
+  if (int rc = ctx_alloc_inner(c, c->prm.gmres_restart, std::max(1, c->prm.gmres_inner))) return rc;
+  if (int rc = ctx_prepare_history(c)) return rc;
+  if (int rc = ctx_prepare_f32(c, U)) return rc;
+  if (int rc = ctx_linearize32(c)) return rc;
+  c->lin_user = true;
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_jv_linearized(pnp_ctx* c, const float* V, float* JV) {
+  CTX_GUARD(c);
+  if (!V || !JV) PNP_FAIL(PNP_ERR_ARG, "pnp_jv_linearized: null pointer");
+  if (!c->lin_user) PNP_FAIL(PNP_ERR_STATE, "pnp_jv_linearized: no stored linearisation (call pnp_linearize)");
+  if (int rc = ctx_jv32_linearized(c, V, JV)) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
 int pnp_block_diag(pnp_ctx* c, const double* U, double* D) {
   CTX_GUARD(c);
   if (!U || !D) PNP_FAIL(PNP_ERR_ARG, "pnp_block_diag: null pointer");

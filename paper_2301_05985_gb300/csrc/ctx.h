@@ -60,6 +60,7 @@ struct pnp_ctx {
   float4* V4 = nullptr;     // [N] padded FP32 direction of the inner solve's J V
   float4* JV4 = nullptr;    // [N] padded FP32 J V accumulator
   float4* qp32 = nullptr;   // [4][2^dim E] stored Gauss-point linearisation of the FP32 J V
+  bool lin_user = false;    // qp32 holds the linearisation of the last pnp_linearize
   int64_t basis_bytes = 0;
 
   // statistics of the last solve (for the time stepper)
@@ -163,6 +164,8 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
               int* its, double* relres, bool have_precond);
 int ctx_newton(pnp_ctx* c, pnp_solve_stats* st, const double* ref_state = nullptr);
 int ctx_alloc_inner(pnp_ctx* c, int m, int d);
+int ctx_linearize32(pnp_ctx* c);
+int ctx_jv32_linearized(pnp_ctx* c, const float* V, float* JV);
 int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st);
 int ctx_alloc_krylov(pnp_ctx* c, int m);
 void pnp_mlp_release(pnp_ctx* c);

@@ -139,6 +139,11 @@ __global__ void k_block_apply32_pad(int64_t N, const float* __restrict__ Dinv, c
                      fmaf(B[6], a, fmaf(B[7], b, B[8] * c)), 0.0f);
 }
 
+__global__ void k_pad4(int64_t N, const float* __restrict__ x, float4* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) y[i] = make_float4(x[3 * i], x[3 * i + 1], x[3 * i + 2], 0.0f);
+}
+
 // out <- acc with the Dirichlet rows of J V (= V); hanging rows are left to k_hanging_rows4
 __global__ void k_pack_jv4(int64_t N, const uint8_t* __restrict__ faces, BcTable bc, const float4* __restrict__ V4,
                            const float4* __restrict__ acc, float* __restrict__ out) {
@@ -342,6 +347,14 @@ cudaError_t launch_block_apply32_pad(int64_t N, const float* Dinv32, const float
                                      cudaStream_t s) {
   if (N) {
     k_block_apply32_pad<<<nblk(N, 256), 256, 0, s>>>(N, Dinv32, u, inv_s, y4);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad4(int64_t N, const float* x, float4* y4, cudaStream_t s) {
+  if (N) {
+    k_pad4<<<nblk(N, 256), 256, 0, s>>>(N, x, y4);
     note_launch();
   }
   return cudaGetLastError();

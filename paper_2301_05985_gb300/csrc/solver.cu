@@ -253,6 +253,22 @@ static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_stat
   return PNP_OK;
 }
 
+// Gauss-point linearisation of the FP32 J V at the prepared FP32 state (ctx_prepare_f32)
+int ctx_linearize32(pnp_ctx* c) {
+  ElemArgs<float> A = elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr);
+  A.rec = c->rec32;
+  ProfScope ps(c, PNP_PROF_PRECOND, 32.0 * c->n_nodes + 64.0 * (double)(c->n_elem << c->dim) + c->conn_bytes());
+  CK(launch_lane_state(c->dim, A, c->qp32, c->stream));
+  c->lin_user = false;
+  return PNP_OK;
+}
+
+// JV = J V (FP32 [n][3]) from the stored linearisation
+int ctx_jv32_linearized(pnp_ctx* c, const float* V, float* JV) {
+  CK(launch_pad4(c->n_nodes, V, c->V4, c->stream));
+  return ctx_jv32_pad(c, c->V4, JV, true);
+}
+
 // z = P(u): d steps of right-preconditioned FP32 GMRES on (J M^-1) t = u from t = 0, then
 // z = M^-1 t (M: the block diagonal).  A fixed number of steps with the Hessenberg
 // bookkeeping on the device: no host round trip.  P is homogeneous, P(a u) = a P(u).
@@ -323,12 +339,7 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   if (flex) RC(ctx_alloc_inner(c, m, c->prm.gmres_inner));
   // the inner J V reads the state's Gauss-point quantities stored once for this solve
   const bool from_state = flex && !c->use_patches && element_kernel_is_lanes();
-  if (from_state) {
-    ElemArgs<float> A = elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr);
-    A.rec = c->rec32;
-    ProfScope ps(c, PNP_PROF_PRECOND, 32.0 * c->n_nodes + 64.0 * (double)(c->n_elem << c->dim) + c->conn_bytes());
-    CK(launch_lane_state(c->dim, A, c->qp32, s));
-  }
+  if (from_state) RC(ctx_linearize32(c));
   double* V = c->basis;
   double* dd = c->dsc;                    // [m+2] dot products of one pass
   double* dinv = c->dsc + (m + 2);        // [m+2] 1 / s_i^2

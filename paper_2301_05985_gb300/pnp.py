@@ -106,6 +106,8 @@ SIGNATURES = {
     "pnp_make_consistent": (C.c_int, [_vp]),
     "pnp_residual": (C.c_int, [_vp, _vp, _vp]),
     "pnp_jv": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int]),
+    "pnp_linearize": (C.c_int, [_vp, _vp]),
+    "pnp_jv_linearized": (C.c_int, [_vp, _vp, _vp]),
     "pnp_block_diag": (C.c_int, [_vp, _vp, _vp]),
     "pnp_norm2": (C.c_int, [_vp, _vp, _i64, _P(_d)]),
     "pnp_gmres": (C.c_int, [_vp, _vp, _vp, _vp, _d, C.c_int, _P(pnp_solve_stats)]),
@@ -310,6 +312,13 @@ class Context:
 
     def jv(self, U, V, JV, precision: int = PNP_F64):
         check(lib().pnp_jv(self.h, _ptr(U), _ptr(V), _ptr(JV), precision))
+        return JV
+
+    def linearize(self, U):
+        check(lib().pnp_linearize(self.h, _ptr(U)))
+
+    def jv_linearized(self, V, JV):
+        check(lib().pnp_jv_linearized(self.h, _ptr(V), _ptr(JV)))
         return JV
 
     def block_diag(self, U, D):
