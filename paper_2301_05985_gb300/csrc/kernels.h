@@ -105,14 +105,9 @@ cudaError_t launch_axpbyz(int64_t n, double a, const double* x, double b, const 
 // partial sums of x.y into part[kRedBlocks], then result[0] = sum (device)
 cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* part, double* result, cudaStream_t s);
 cudaError_t launch_norm2(int64_t n, const double* x, double* part, double* result, cudaStream_t s);
-// h[i] = sum_n Vb[i*ld + n] w[n], i < k  (part: [kRedBlocks][k] scratch)
-cudaError_t launch_multi_dot(int64_t n, int k, const double* Vb, int64_t ld, const double* w, double* part, double* h,
-                             cudaStream_t s);
 // w -= sum_i h[i] Vb[i*ld + .], i < k ; optionally hacc[i] += h[i]
 cudaError_t launch_multi_axpy(int64_t n, int k, const double* Vb, int64_t ld, const double* h, double* w,
                               double* hacc, cudaStream_t s);
-// v = w / nrm[0]
-cudaError_t launch_scale_by_inv(int64_t n, const double* w, const double* nrm, double* v, cudaStream_t s);
 // z_i = Dinv_i v_i per node (3x3 blocks); optionally also a float copy z32 (may be null)
 cudaError_t launch_block_apply(int64_t N, const double* Dinv, const double* v, double scale, double* z, float* z32,
                                cudaStream_t s);

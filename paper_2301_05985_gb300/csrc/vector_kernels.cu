@@ -77,53 +77,6 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_parts(int nparts, int k,
   if (threadIdx.x == 0) out[j] = take_sqrt ? sqrt(s) : s;
 }
 
-// Gram-Schmidt projections h_i = V_i . w for i < k, 8 basis vectors per sweep.
-__global__ void __launch_bounds__(kRedThreads) k_multi_dot_part(int64_t n, int k, const double* __restrict__ Vb,
-                                                                int64_t ld, const double* __restrict__ w,
-                                                                double* __restrict__ part) {
-  __shared__ double sh[kRedThreads];
-  for (int i0 = 0; i0 < k; i0 += 8) {
-    const int cnt = min(8, k - i0);
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-      const double wv = w[t];
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (j < cnt) acc[j] += Vb[(int64_t)(i0 + j) * ld + t] * wv;
-    }
-    for (int j = 0; j < cnt; ++j) {
-      const double s = block_sum(acc[j], sh);
-      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * k + i0 + j] = s;
-    }
-  }
-}
-
-// d_i = V_i . w for i < k and, if kk > k, d_k = w . w ; 16 vectors per sweep over n.
-__global__ void __launch_bounds__(kRedThreads) k_multi_dot_ext(int64_t n, int k, int kk, const double* __restrict__ Vb,
-                                                               int64_t ld, const double* __restrict__ w,
-                                                               double* __restrict__ part) {
-  __shared__ double sh[kRedThreads];
-  for (int i0 = 0; i0 < kk; i0 += 16) {
-    const int cnt = min(16, kk - i0);
-    double acc[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-      const double wv = w[t];
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (j < cnt) {
-          const int i = i0 + j;
-          acc[j] += (i < k ? Vb[(int64_t)i * ld + t] : wv) * wv;
-        }
-    }
-    for (int j = 0; j < cnt; ++j) {
-      const double s = block_sum(acc[j], sh);
-      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kk + i0 + j] = s;
-    }
-  }
-}
-
 // Sum over the warp of four per-lane values at once (reduce-scatter: 6 adds per lane
 // instead of 4 x 5); lanes 8q .. 8q+7 end with the total of s[q].  Fixed order.
 __device__ __forceinline__ double warp_sum4(const double (&s)[4], int lane) {
@@ -228,13 +181,6 @@ __global__ void __launch_bounds__(256) k_multi_axpy(int64_t n, int k, const doub
     for (int i = 0; i < k; ++i) v -= hs[i] * Vb[(int64_t)i * ld + t];
     w[t] = v;
   }
-}
-
-__global__ void k_scale_by_inv(int64_t n, const double* __restrict__ w, const double* __restrict__ nrm,
-                               double* __restrict__ v) {
-  const double a = 1.0 / nrm[0];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = w[i] * a;
 }
 
 __global__ void k_block_apply(int64_t N, const double* __restrict__ Dinv, const double* __restrict__ v, double scale,
@@ -362,21 +308,10 @@ cudaError_t launch_norm2(int64_t n, const double* x, double* part, double* resul
   k_reduce_parts<<<1, kRedThreads, 0, s>>>(kRedBlocks, 1, part, result, 1); note_launch();
   return cudaGetLastError();
 }
-cudaError_t launch_multi_dot(int64_t n, int k, const double* Vb, int64_t ld, const double* w, double* part, double* h,
-                             cudaStream_t s) {
-  if (k <= 0) return cudaSuccess;
-  k_multi_dot_part<<<kRedBlocks, kRedThreads, 0, s>>>(n, k, Vb, ld, w, part); note_launch();
-  k_reduce_parts<<<k, kRedThreads, 0, s>>>(kRedBlocks, k, part, h, 0); note_launch();
-  return cudaGetLastError();
-}
 cudaError_t launch_multi_axpy(int64_t n, int k, const double* Vb, int64_t ld, const double* h, double* w,
                               double* hacc, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   k_multi_axpy<<<gs_blocks(n, 256), 256, k * sizeof(double), s>>>(n, k, Vb, ld, h, w, hacc); note_launch();
-  return cudaGetLastError();
-}
-cudaError_t launch_scale_by_inv(int64_t n, const double* w, const double* nrm, double* v, cudaStream_t s) {
-  if (n) { k_scale_by_inv<<<gs_blocks(n, 256), 256, 0, s>>>(n, w, nrm, v); note_launch(); }
   return cudaGetLastError();
 }
 __global__ void k_node_records(int64_t N, const double* __restrict__ U, const double* __restrict__ hs,
