@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <random>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.h"
@@ -59,11 +60,16 @@ struct FeatArgs {
   const int32_t* idx;
   const double* wt;
   double mu[4], isd[4];       // standardisation of inputs
+  float mu_f[4], isd_f[4];    // the same in FP32
   double* raw;                // [rows][216] FP64 (raw mode) or null
   bf16* X;                    // [rows][224] standardised BF16 (or null)
 };
 
+// RAW: FP64 features (the parity path); otherwise FP32 accumulation and standardisation,
+// rounded to BF16 (GB300 runs FP64 at 1/64 of the FP32 rate, and BF16 keeps 8 bits)
+template <bool RAW>
 __global__ void k_features(FeatArgs a) {
+  using A = typename std::conditional<RAW, double, float>::type;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= a.rows * NPT) return;
   const int64_t r = t / NPT;
@@ -82,22 +88,26 @@ __global__ void k_features(FeatArgs a) {
     z0 = a.uzk;
     z1 = a.uzkm1;
   }
-  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  A v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   const int32_t b = a.ptr[slot * NPT + p], e = a.ptr[slot * NPT + p + 1];
   for (int32_t q = b; q < e; ++q) {
     const int64_t id = a.idx[q];
-    const double w = a.wt[q];
+    const A w = (A)a.wt[q];
     for (int f = 0; f < 3; ++f) {
-      v[f] += w * U0[3 * id + f];
-      v[4 + f] += w * U1[3 * id + f];
+      v[f] += w * (A)U0[3 * id + f];
+      v[4 + f] += w * (A)U1[3 * id + f];
     }
-    if (z0) v[3] += w * z0[id];
-    if (z1) v[7] += w * z1[id];
+    if (z0) v[3] += w * (A)z0[id];
+    if (z1) v[7] += w * (A)z1[id];
   }
   for (int g = 0; g < 8; ++g) {
     const int col = g * NPT + p;
-    if (a.raw) a.raw[r * K0 + col] = v[g];
-    if (a.X) a.X[r * K0P + col] = __float2bfloat16((float)((v[g] - a.mu[g & 3]) * a.isd[g & 3]));
+    if (RAW) {
+      a.raw[r * K0 + col] = (double)v[g];
+      if (a.X) a.X[r * K0P + col] = __float2bfloat16((float)((v[g] - a.mu[g & 3]) * a.isd[g & 3]));
+    } else if (a.X) {
+      a.X[r * K0P + col] = __float2bfloat16((v[g] - a.mu_f[g & 3]) * a.isd_f[g & 3]);
+    }
   }
   if (a.X && p < K0P - K0) a.X[r * K0P + K0 + p] = __float2bfloat16(0.f);
 }
@@ -537,6 +547,8 @@ FeatArgs feat_args(const Mlp* m, int64_t N) {
   for (int f = 0; f < 4; ++f) {
     a.mu[f] = m->in_mu[f];
     a.isd[f] = 1.0 / m->in_sd[f];
+    a.mu_f[f] = (float)a.mu[f];
+    a.isd_f[f] = (float)a.isd[f];
   }
   return a;
 }
@@ -816,7 +828,8 @@ int pnp_mlp_features(pnp_ctx* c, const double* Uk, const double* Ukm1, const dou
   a.uzkm1 = uz_km1;
   a.raw = X;
   if (a.rows) {
-    k_features<<<nblk(a.rows * NPT, 256), 256, 0, c->stream>>>(a);
+    if (a.raw) k_features<true><<<nblk(a.rows * NPT, 256), 256, 0, c->stream>>>(a);
+    else k_features<false><<<nblk(a.rows * NPT, 256), 256, 0, c->stream>>>(a);
     note_launch();
   }
   CK(cudaGetLastError());
@@ -933,7 +946,7 @@ int pnp_mlp_train(pnp_ctx* c, const pnp_train_cfg* cfg, pnp_train_stats* st) {
     a.base = m->states;
     a.ubase = m->uz;
     a.X = m->X;
-    k_features<<<nblk(B * NPT, 256), 256, 0, s>>>(a);
+    k_features<false><<<nblk(B * NPT, 256), 256, 0, s>>>(a);
     note_launch();
     k_targets<<<nblk(B, 256), 256, 0, s>>>(B, N, m->d_rows, m->d_state, m->free_nodes, m->states, m->out_mu[0],
                                             m->out_mu[1], m->out_mu[2], m->out_sd[0], m->out_sd[1], m->out_sd[2],
@@ -1096,7 +1109,7 @@ int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st) {
       a.uzk = uzk;
       a.uzkm1 = uzkm1;
       a.X = m->X;
-      k_features<<<nblk(rows * NPT, 256), 256, 0, s>>>(a);
+      k_features<false><<<nblk(rows * NPT, 256), 256, 0, s>>>(a);
       note_launch();
       RC(mlp_forward_rows(c, m, rows));
       k_apply_correction<<<nblk(rows, 256), 256, 0, s>>>(rows, m->free_nodes + r0, m->out, m->out_mu[0], m->out_mu[1],
