@@ -354,7 +354,9 @@ int ctx_alloc_inner(pnp_ctx* c, int m, int d) {
   c->inner_m = c->inner_d = 0;
   const size_t n = (size_t)c->n3();
   cudaError_t e = cudaMalloc((void**)&c->Zb, sizeof(float) * (size_t)m * n);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->Qin, sizeof(float) * (size_t)(d + 1) * n);
+  c->ldq = (int64_t)((n + 3) & ~(size_t)3);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->Qin, sizeof(float) * (size_t)(d + 1) * (size_t)c->ldq);
+  if (e == cudaSuccess) e = cudaMemset(c->Qin, 0, sizeof(float) * (size_t)(d + 1) * (size_t)c->ldq);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->Dinv32, sizeof(float) * 9 * (size_t)c->n_nodes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->isc, sizeof(double) * (inner_scalar_doubles(d) + 5 * (size_t)(d + 2)));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->iinv, sizeof(float) * (size_t)(d + 2));

@@ -51,7 +51,8 @@ struct pnp_ctx {
   int m_alloc = 0;
   // flexible outer GMRES with an inner FP32 GMRES(d) preconditioner
   float* Zb = nullptr;      // [m][3N] preconditioned Krylov vectors
-  float* Qin = nullptr;     // [(d+1)][3N] inner basis (unnormalised)
+  float* Qin = nullptr;     // [(d+1)][ldq] inner basis (unnormalised), rows padded with zeros
+  int64_t ldq = 0;          // row length of Qin: 3N rounded up to a multiple of 4
   float* Dinv32 = nullptr;  // [N][9] FP32 copy of the inverted block diagonal
   double* isc = nullptr;    // inner Hessenberg [(d+1) x d] and scalars
   float* iinv = nullptr;    // [d+2] inverse norms of the inner basis vectors

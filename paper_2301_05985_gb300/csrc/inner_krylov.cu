@@ -35,34 +35,42 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
   return r;
 }
 
-// d_i = U_i . w (i < k) for FP32 vectors.  Persistent grid (kInnerBlocks, 8 per SM): each
-// block strides over chunks of 256 x kRows rows; for every group of four basis vectors a
-// thread accumulates its rows of all chunks (w re-read from L2 per group), then one warp
-// reduce-scatter and a fixed-order block sum give the block's partials part[block][k].
-constexpr int kRows = 4;
-__global__ void __launch_bounds__(256, 8) k_multi_dot_f32(int64_t n, int k, const float* __restrict__ Ub, int64_t ld,
-                                                          const float* __restrict__ w, double* __restrict__ part) {
+// The inner basis has rows padded to a multiple of four floats (zeros beyond the
+// vector's length), so both Gram-Schmidt kernels move float4: four entries per load.
+
+// d_i = U_i . w (i < k) for FP32 vectors of n4 float4.  Persistent grid (kInnerBlocks, 8
+// per SM): each block strides over chunks of 256 x kRows float4; for every group of four
+// basis vectors a thread accumulates its rows of all chunks (w re-read from L2 per
+// group), then one warp reduce-scatter and a fixed-order block sum give the block's
+// partials part[block][k].
+constexpr int kRows = 2;
+__device__ __forceinline__ float dot4(float4 a, float4 b, float s) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, s))));
+}
+__global__ void __launch_bounds__(256, 8) k_multi_dot_f32(int64_t n4, int k, const float4* __restrict__ Ub,
+                                                          int64_t ld4, const float4* __restrict__ w,
+                                                          double* __restrict__ part) {
   __shared__ float sh[4][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t chunk = 256 * kRows;
   for (int j0 = 0; j0 < k; j0 += 4) {
     const int cnt = min(4, k - j0);
     float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < n; c0 += (int64_t)gridDim.x * chunk) {
-      float wv[kRows];
+    for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < n4; c0 += (int64_t)gridDim.x * chunk) {
+      float4 wv[kRows];
 #pragma unroll
       for (int r = 0; r < kRows; ++r) {
         const int64_t t = c0 + threadIdx.x + r * 256;
-        wv[r] = t < n ? w[t] : 0.0f;
+        wv[r] = t < n4 ? w[t] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (q < cnt) {
-          const float* ui = Ub + (int64_t)(j0 + q) * ld;
+          const float4* ui = Ub + (int64_t)(j0 + q) * ld4;
 #pragma unroll
           for (int r = 0; r < kRows; ++r) {
             const int64_t t = c0 + threadIdx.x + r * 256;
-            if (t < n) s[q] = fmaf(__ldg(ui + t), wv[r], s[q]);
+            if (t < n4) s[q] = dot4(__ldg(ui + t), wv[r], s[q]);
           }
         }
       }
@@ -81,35 +89,30 @@ __global__ void __launch_bounds__(256, 8) k_multi_dot_f32(int64_t n, int k, cons
   }
 }
 
-// w -= sum_i (d_i dinv_i) U_i (i < k) in FP32, then per-block partials of w . w.
-// Persistent grid of 6 blocks per SM (40 registers).
+// w -= sum_i (d_i dinv_i) U_i (i < k) in FP32 on n4 float4, then per-block partials of
+// w . w.  Persistent grid of 6 blocks per SM.
 constexpr int kUpdBlocks = 6 * 152;
-__global__ void __launch_bounds__(256, 6) k_multi_axpy_norm_f32(int64_t n, int k, const float* __restrict__ Ub,
-                                                             int64_t ld, const double* __restrict__ d,
-                                                             const double* __restrict__ dinv, float* __restrict__ w,
+__global__ void __launch_bounds__(256, 6) k_multi_axpy_norm_f32(int64_t n4, int k, const float4* __restrict__ Ub,
+                                                             int64_t ld4, const double* __restrict__ d,
+                                                             const double* __restrict__ dinv, float4* __restrict__ w,
                                                              double* __restrict__ part) {
   extern __shared__ float cf[];
   __shared__ double sh[256];
   for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = (float)(d[i] * dinv[i]);
   __syncthreads();
   float ss = 0.0f;
-  // two rows per thread per pass (a grid stride apart): twice the independent loads in flight
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += 2 * stride) {
-    const int64_t t2 = t + stride;
-    const bool two = t2 < n;
-    float a = w[t], b = two ? w[t2] : 0.0f;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
+    float4 a = w[t];
     for (int i = 0; i < k; ++i) {
-      const float* ui = Ub + (int64_t)i * ld;
-      a = fmaf(-cf[i], ui[t], a);
-      if (two) b = fmaf(-cf[i], ui[t2], b);
+      const float4 u = Ub[(int64_t)i * ld4 + t];
+      const float c = -cf[i];
+      a.x = fmaf(c, u.x, a.x);
+      a.y = fmaf(c, u.y, a.y);
+      a.z = fmaf(c, u.z, a.z);
+      a.w = fmaf(c, u.w, a.w);
     }
-    if (k > 0) {
-      w[t] = a;
-      if (two) w[t2] = b;
-    }
-    ss = fmaf(a, a, ss);
-    ss = fmaf(b, b, ss);
+    if (k > 0) w[t] = a;
+    ss = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, ss))));
   }
   const double tot = block_sum_d((double)ss, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
@@ -319,8 +322,9 @@ int inner_max_depth() { return kMaxInner; }
 cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, const float* w, double* part, double* d,
                                  cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
+  if ((n | ld) & 3) return cudaErrorInvalidValue;  // rows padded to float4
   const int nb = inner_dot_blocks(n);
-  k_multi_dot_f32<<<nb, 256, 0, s>>>(n, k, Ub, ld, w, part);
+  k_multi_dot_f32<<<nb, 256, 0, s>>>(n / 4, k, (const float4*)Ub, ld / 4, (const float4*)w, part);
   note_launch();
   launch_reduce_parts(nb, k, part, d, s);
   return cudaGetLastError();
@@ -328,7 +332,9 @@ cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, 
 
 cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* d,
                                        const double* dinv, float* w, double* part, double* nrm2, cudaStream_t s) {
-  k_multi_axpy_norm_f32<<<kUpdBlocks, 256, (k > 0 ? k : 1) * sizeof(float), s>>>(n, k, Ub, ld, d, dinv, w, part);
+  if ((n | ld) & 3) return cudaErrorInvalidValue;  // rows padded to float4
+  k_multi_axpy_norm_f32<<<kUpdBlocks, 256, (k > 0 ? k : 1) * sizeof(float), s>>>(n / 4, k, (const float4*)Ub, ld / 4,
+                                                                                 d, dinv, (float4*)w, part);
   note_launch();
   launch_reduce_parts(kUpdBlocks, 1, part, nrm2, s);
   return cudaGetLastError();

@@ -131,10 +131,12 @@ cudaError_t launch_reduce_parts(int nparts, int k, const double* part, double* o
 // ---------------------------------------------- inner FP32 GMRES (inner_krylov.cu)
 int inner_dot_blocks(int64_t n);
 int inner_max_depth();
-// d_i = U_i . w (FP32 vectors, i < k); part: [inner_dot_blocks(n)][k]
+// d_i = U_i . w (FP32 vectors, i < k); part: [inner_dot_blocks(n)][k].  n and ld are
+// multiples of 4 and the vectors 16-byte aligned (rows padded with zeros)
 cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, const float* w, double* part, double* d,
                                  cudaStream_t s);
-// w -= sum_i d_i dinv_i U_i (i < k, FP32); nrm2[0] = w . w afterwards (part: at most [kInnerBlocks])
+// w -= sum_i d_i dinv_i U_i (i < k, FP32); nrm2[0] = w . w afterwards (part: at most
+// [kInnerBlocks]); n, ld multiples of 4 as above
 cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* d,
                                        const double* dinv, float* w, double* part, double* nrm2, cudaStream_t s);
 // y = Dinv32 (inv_s[0] u) per node (inv_s may be null: scale 1); y4: the same, padded

@@ -274,9 +274,9 @@ int ctx_jv32_linearized(pnp_ctx* c, const float* V, float* JV) {
 // bookkeeping on the device: no host round trip.  P is homogeneous, P(a u) = a P(u).
 static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_state) {
   const int d = c->prm.gmres_inner;
-  const int64_t n = c->n3(), N = c->n_nodes;
+  const int64_t n = c->n3(), N = c->n_nodes, ldq = c->ldq;
   cudaStream_t s = c->stream;
-  float* Q = c->Qin;
+  float* Q = c->Qin;  // rows of ldq floats, the entries past n stay zero
   double* sc = c->isc;                           // rotated Hessenberg, rotations, g, count
   double* sv = sc + inner_scalar_doubles(d);     // [d+1] norms s_i of the basis vectors
   double* dinv = sv + (d + 2);                   // [d+1] 1 / s_i^2
@@ -287,35 +287,35 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_stat
   CK(launch_to_f32(n, u, Q, s));
   {
     ProfScope ps(c, PNP_PROF_INNER, 4.0 * n, 2.0 * n);
-    CK(launch_multi_axpy_norm_f32(n, 0, Q, n, dd, dinv, Q, c->part, nrm2, s));
+    CK(launch_multi_axpy_norm_f32(ldq, 0, Q, ldq, dd, dinv, Q, c->part, nrm2, s));
   }
   CK(launch_inner_start(d, nrm2, sv, dinv, inv_s, sc, s));
   const bool pad = !c->use_patches && element_kernel_is_lanes();
   for (int j = 0; j < d; ++j) {
-    float* w = Q + (size_t)(j + 1) * n;
+    float* w = Q + (size_t)(j + 1) * ldq;
     if (pad) {
       {
         ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
-        CK(launch_block_apply32_pad(N, c->Dinv32, Q + (size_t)j * n, inv_s + j, c->V4, s));
+        CK(launch_block_apply32_pad(N, c->Dinv32, Q + (size_t)j * ldq, inv_s + j, c->V4, s));
       }
       RC(ctx_jv32_pad(c, c->V4, w, from_state));
     } else {
       {
         ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
-        CK(launch_block_apply32(N, c->Dinv32, Q + (size_t)j * n, inv_s + j, c->V32, s));
+        CK(launch_block_apply32(N, c->Dinv32, Q + (size_t)j * ldq, inv_s + j, c->V32, s));
       }
       RC(ctx_jv32(c, c->V32, w));
     }
     {
       const double nj = (double)n * (j + 1);
       ProfScope ps(c, PNP_PROF_INNER, 4.0 * (nj + n) + 4.0 * (nj + 2.0 * n), 4.0 * nj + 2.0 * n);
-      CK(launch_multi_dot_f32(n, j + 1, Q, n, w, c->part, dd, s));
-      CK(launch_multi_axpy_norm_f32(n, j + 1, Q, n, dd, dinv, w, c->part, nrm2, s));
+      CK(launch_multi_dot_f32(ldq, j + 1, Q, ldq, w, c->part, dd, s));
+      CK(launch_multi_axpy_norm_f32(ldq, j + 1, Q, ldq, dd, dinv, w, c->part, nrm2, s));
     }
     CK(launch_inner_col(j, d, dd, nrm2, sv, dinv, inv_s, sc, s));
   }
   CK(launch_inner_lsq(d, sv, sc, coef, s));
-  CK(launch_combine_f32(n, d, Q, n, coef, c->JV32, s));
+  CK(launch_combine_f32(n, d, Q, ldq, coef, c->JV32, s));
   ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
   CK(launch_block_apply32(N, c->Dinv32, c->JV32, nullptr, z32, s));
   return PNP_OK;
