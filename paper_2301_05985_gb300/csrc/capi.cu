@@ -362,6 +362,7 @@ int ctx_alloc_inner(pnp_ctx* c, int m, int d) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->iinv, sizeof(float) * (size_t)(d + 2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->V4, sizeof(float4) * (size_t)c->n_nodes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->JV4, sizeof(float4) * (size_t)c->n_nodes);
+  if (e == cudaSuccess) e = cudaMemset(c->JV4, 0, sizeof(float4) * (size_t)c->n_nodes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->qp32, sizeof(float4) * 4 * ((size_t)c->n_elem << c->dim));
   if (e != cudaSuccess) {
     pnp_set_error("inner Krylov scratch allocation failed: %s", cudaGetErrorString(e));

@@ -147,14 +147,17 @@ __global__ void k_pad4(int64_t N, const float* __restrict__ x, float4* __restric
   if (i < N) y[i] = make_float4(x[3 * i], x[3 * i + 1], x[3 * i + 2], 0.0f);
 }
 
-// out <- acc with the Dirichlet rows of J V (= V); hanging rows are left to k_hanging_rows4
+// out <- acc with the Dirichlet rows of J V (= V); hanging rows are left to k_hanging_rows4.
+// The accumulator is cleared as it is read (hanging entries never receive any), so the
+// next J V starts from zero without a memset.
 __global__ void k_pack_jv4(int64_t N, const uint8_t* __restrict__ faces, BcTable bc, const float4* __restrict__ V4,
-                           const float4* __restrict__ acc, float* __restrict__ out) {
+                           float4* __restrict__ acc, float* __restrict__ out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint8_t fm = faces[i];
   if (fm & 0x80) return;
   const float4 a = acc[i];
+  acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   float r[3] = {a.x, a.y, a.z};
   if (fm & 0x3F) {
     const float4 v = V4[i];
@@ -204,13 +207,27 @@ __device__ __forceinline__ InnerScalars inner_scalars(double* base, int d) {
   return S;
 }
 
-__global__ void k_inner_start(int d, const double* __restrict__ nrm2, double* sv, double* dinv, float* inv_s,
-                              double* sc) {
+// sum of the norm partials of k_multi_axpy_norm_f32 in a fixed order (one block of 64)
+__device__ __forceinline__ double sum_parts64(const double* __restrict__ part, int nparts, double* sh) {
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += 64) t += part[b];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int o = 32; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+__global__ void __launch_bounds__(64) k_inner_start(int d, const double* __restrict__ part, int nparts, double* sv,
+                                                    double* dinv, float* inv_s, double* sc) {
+  __shared__ double sh[64];
   const InnerScalars S = inner_scalars(sc, d);
   for (int i = threadIdx.x; i <= d; i += blockDim.x) S.g[i] = 0.0;
-  __syncthreads();
+  const double nrm2 = sum_parts64(part, nparts, sh);
   if (threadIdx.x == 0) {
-    const double s = sqrt(nrm2[0]);
+    const double s = sqrt(nrm2);
     sv[0] = s;
     dinv[0] = s > 0 ? 1.0 / (s * s) : 0.0;
     inv_s[0] = s > 0 ? (float)(1.0 / s) : 0.0f;
@@ -223,14 +240,17 @@ __global__ void k_inner_start(int d, const double* __restrict__ nrm2, double* sv
 // make rotation j, update g.  One block of kMaxInner threads.
 constexpr int kMaxInner = 64;
 __global__ void __launch_bounds__(kMaxInner) k_inner_col(int j, int d, const double* __restrict__ dd,
-                                                         const double* __restrict__ nrm2, double* sv, double* dinv,
-                                                         float* inv_s, double* sc) {
+                                                         const double* __restrict__ part, int nparts, double* sv,
+                                                         double* dinv, float* inv_s, double* sc) {
+  static_assert(kMaxInner == 64, "the norm partials are summed by one block of 64");
   __shared__ double h[kMaxInner + 1];
+  __shared__ double sh[64];
   const InnerScalars S = inner_scalars(sc, d);
   const int i = threadIdx.x;
   if (i <= j) h[i] = sv[i] > 0 ? dd[i] / sv[i] : 0.0;
+  const double nrm2 = sum_parts64(part, nparts, sh);
   if (i == 0) {
-    const double s = sqrt(nrm2[0]);
+    const double s = sqrt(nrm2);
     h[j + 1] = s;
     sv[j + 1] = s;
     dinv[j + 1] = s > 0 ? 1.0 / (s * s) : 0.0;
@@ -331,12 +351,11 @@ cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, 
 }
 
 cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* d,
-                                       const double* dinv, float* w, double* part, double* nrm2, cudaStream_t s) {
+                                       const double* dinv, float* w, double* part, cudaStream_t s) {
   if ((n | ld) & 3) return cudaErrorInvalidValue;  // rows padded to float4
   k_multi_axpy_norm_f32<<<kUpdBlocks, 256, (k > 0 ? k : 1) * sizeof(float), s>>>(n / 4, k, (const float4*)Ub, ld / 4,
                                                                                  d, dinv, (float4*)w, part);
   note_launch();
-  launch_reduce_parts(kUpdBlocks, 1, part, nrm2, s);
   return cudaGetLastError();
 }
 
@@ -366,7 +385,7 @@ cudaError_t launch_pad4(int64_t N, const float* x, float4* y4, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, const float4* acc4, float* out, cudaStream_t s) {
+cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, float4* acc4, float* out, cudaStream_t s) {
   if (R.n_nodes) {
     k_pack_jv4<<<nblk(R.n_nodes, 256), 256, 0, s>>>(R.n_nodes, R.faces, R.bc, V4, acc4, out);
     note_launch();
@@ -378,16 +397,16 @@ cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, const float4* ac
   return cudaGetLastError();
 }
 
-cudaError_t launch_inner_start(int d, const double* nrm2, double* sv, double* dinv, float* inv_s, double* sc,
+cudaError_t launch_inner_start(int d, const double* part, double* sv, double* dinv, float* inv_s, double* sc,
                                cudaStream_t s) {
-  k_inner_start<<<1, 64, 0, s>>>(d, nrm2, sv, dinv, inv_s, sc);
+  k_inner_start<<<1, 64, 0, s>>>(d, part, kUpdBlocks, sv, dinv, inv_s, sc);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_inner_col(int j, int d, const double* dd, const double* nrm2, double* sv, double* dinv, float* inv_s,
+cudaError_t launch_inner_col(int j, int d, const double* dd, const double* part, double* sv, double* dinv, float* inv_s,
                              double* sc, cudaStream_t s) {
-  k_inner_col<<<1, kMaxInner, 0, s>>>(j, d, dd, nrm2, sv, dinv, inv_s, sc);
+  k_inner_col<<<1, kMaxInner, 0, s>>>(j, d, dd, part, kUpdBlocks, sv, dinv, inv_s, sc);
   note_launch();
   return cudaGetLastError();
 }

@@ -135,26 +135,26 @@ int inner_max_depth();
 // multiples of 4 and the vectors 16-byte aligned (rows padded with zeros)
 cudaError_t launch_multi_dot_f32(int64_t n, int k, const float* Ub, int64_t ld, const float* w, double* part, double* d,
                                  cudaStream_t s);
-// w -= sum_i d_i dinv_i U_i (i < k, FP32); nrm2[0] = w . w afterwards (part: at most
-// [kInnerBlocks]); n, ld multiples of 4 as above
+// w -= sum_i d_i dinv_i U_i (i < k, FP32) and the per-block partials of w . w in part
+// (summed by launch_inner_start / launch_inner_col); n, ld multiples of 4 as above
 cudaError_t launch_multi_axpy_norm_f32(int64_t n, int k, const float* Ub, int64_t ld, const double* d,
-                                       const double* dinv, float* w, double* part, double* nrm2, cudaStream_t s);
+                                       const double* dinv, float* w, double* part, cudaStream_t s);
 // y = Dinv32 (inv_s[0] u) per node (inv_s may be null: scale 1); y4: the same, padded
 cudaError_t launch_block_apply32(int64_t N, const float* Dinv32, const float* u, const float* inv_s, float* y,
                                  cudaStream_t s);
 cudaError_t launch_block_apply32_pad(int64_t N, const float* Dinv32, const float* u, const float* inv_s, float4* y4,
                                      cudaStream_t s);
 // out [N][3] <- acc4 with the Dirichlet rows set to V4 and the hanging rows to
-// V4_h - sum_p w_p V4_p (the J V row fix-ups of the padded FP32 path)
-cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, const float4* acc4, float* out, cudaStream_t s);
+// V4_h - sum_p w_p V4_p (the J V row fix-ups of the padded FP32 path); acc4 is left zero
+cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, float4* acc4, float* out, cudaStream_t s);
 // y4[i] = (x[3i], x[3i+1], x[3i+2], 0)
 cudaError_t launch_pad4(int64_t N, const float* x, float4* y4, cudaStream_t s);
 // inner Arnoldi bookkeeping; sc holds the rotated Hessenberg, the rotations, g and the
 // number of columns before a breakdown: inner_scalar_doubles(d) doubles
 inline size_t inner_scalar_doubles(int d) { return (size_t)(d + 1) * d + 2 * (size_t)d + (size_t)(d + 1) + 1; }
-cudaError_t launch_inner_start(int d, const double* nrm2, double* sv, double* dinv, float* inv_s, double* sc,
+cudaError_t launch_inner_start(int d, const double* part, double* sv, double* dinv, float* inv_s, double* sc,
                                cudaStream_t s);
-cudaError_t launch_inner_col(int j, int d, const double* dd, const double* nrm2, double* sv, double* dinv, float* inv_s,
+cudaError_t launch_inner_col(int j, int d, const double* dd, const double* part, double* sv, double* dinv, float* inv_s,
                              double* sc, cudaStream_t s);
 cudaError_t launch_inner_lsq(int d, const double* sv, double* sc, double* coef, cudaStream_t s);
 // out = sum_i coef_i U_i (FP32); x += sum_i coef_i Z_i (FP32 vectors into FP64)

@@ -231,7 +231,7 @@ static int apply_op(pnp_ctx* c, const double* U, const double* x, double* w, int
 // With from_state, the state's Gauss-point quantities come from the linearisation stored
 // by launch_lane_state for the current Krylov solve.
 static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_state) {
-  CK(cudaMemsetAsync(c->JV4, 0, sizeof(float4) * c->n_nodes, c->stream));
+  // c->JV4 is zero here: zeroed at allocation and cleared again by every pack
   {
     ElemArgs<float> A = elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr);
     A.rec = c->rec32;
@@ -281,15 +281,14 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_stat
   double* sv = sc + inner_scalar_doubles(d);     // [d+1] norms s_i of the basis vectors
   double* dinv = sv + (d + 2);                   // [d+1] 1 / s_i^2
   double* dd = dinv + (d + 2);                   // [d+1] projections
-  double* nrm2 = dd + (d + 2);                   // [1]
-  double* coef = nrm2 + 2;                       // [d] combination coefficients
+  double* coef = dd + (d + 2);                   // [d] combination coefficients
   float* inv_s = c->iinv;
   CK(launch_to_f32(n, u, Q, s));
   {
     ProfScope ps(c, PNP_PROF_INNER, 4.0 * n, 2.0 * n);
-    CK(launch_multi_axpy_norm_f32(ldq, 0, Q, ldq, dd, dinv, Q, c->part, nrm2, s));
+    CK(launch_multi_axpy_norm_f32(ldq, 0, Q, ldq, dd, dinv, Q, c->part, s));
   }
-  CK(launch_inner_start(d, nrm2, sv, dinv, inv_s, sc, s));
+  CK(launch_inner_start(d, c->part, sv, dinv, inv_s, sc, s));
   const bool pad = !c->use_patches && element_kernel_is_lanes();
   for (int j = 0; j < d; ++j) {
     float* w = Q + (size_t)(j + 1) * ldq;
@@ -310,9 +309,9 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_stat
       const double nj = (double)n * (j + 1);
       ProfScope ps(c, PNP_PROF_INNER, 4.0 * (nj + n) + 4.0 * (nj + 2.0 * n), 4.0 * nj + 2.0 * n);
       CK(launch_multi_dot_f32(ldq, j + 1, Q, ldq, w, c->part, dd, s));
-      CK(launch_multi_axpy_norm_f32(ldq, j + 1, Q, ldq, dd, dinv, w, c->part, nrm2, s));
+      CK(launch_multi_axpy_norm_f32(ldq, j + 1, Q, ldq, dd, dinv, w, c->part, s));
     }
-    CK(launch_inner_col(j, d, dd, nrm2, sv, dinv, inv_s, sc, s));
+    CK(launch_inner_col(j, d, dd, c->part, sv, dinv, inv_s, sc, s));
   }
   CK(launch_inner_lsq(d, sv, sc, coef, s));
   CK(launch_combine_f32(n, d, Q, ldq, coef, c->JV32, s));
