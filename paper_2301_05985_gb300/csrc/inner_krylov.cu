@@ -147,17 +147,14 @@ __global__ void k_pad4(int64_t N, const float* __restrict__ x, float4* __restric
   if (i < N) y[i] = make_float4(x[3 * i], x[3 * i + 1], x[3 * i + 2], 0.0f);
 }
 
-// out <- acc with the Dirichlet rows of J V (= V); hanging rows are left to k_hanging_rows4.
-// The accumulator is cleared as it is read (hanging entries never receive any), so the
-// next J V starts from zero without a memset.
+// out <- acc with the Dirichlet rows of J V (= V); hanging rows are left to k_hanging_rows4
 __global__ void k_pack_jv4(int64_t N, const uint8_t* __restrict__ faces, BcTable bc, const float4* __restrict__ V4,
-                           float4* __restrict__ acc, float* __restrict__ out) {
+                           const float4* __restrict__ acc, float* __restrict__ out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint8_t fm = faces[i];
   if (fm & 0x80) return;
   const float4 a = acc[i];
-  acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   float r[3] = {a.x, a.y, a.z};
   if (fm & 0x3F) {
     const float4 v = V4[i];
@@ -385,7 +382,7 @@ cudaError_t launch_pad4(int64_t N, const float* x, float4* y4, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, float4* acc4, float* out, cudaStream_t s) {
+cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, const float4* acc4, float* out, cudaStream_t s) {
   if (R.n_nodes) {
     k_pack_jv4<<<nblk(R.n_nodes, 256), 256, 0, s>>>(R.n_nodes, R.faces, R.bc, V4, acc4, out);
     note_launch();

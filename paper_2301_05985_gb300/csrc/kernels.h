@@ -145,8 +145,8 @@ cudaError_t launch_block_apply32(int64_t N, const float* Dinv32, const float* u,
 cudaError_t launch_block_apply32_pad(int64_t N, const float* Dinv32, const float* u, const float* inv_s, float4* y4,
                                      cudaStream_t s);
 // out [N][3] <- acc4 with the Dirichlet rows set to V4 and the hanging rows to
-// V4_h - sum_p w_p V4_p (the J V row fix-ups of the padded FP32 path); acc4 is left zero
-cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, float4* acc4, float* out, cudaStream_t s);
+// V4_h - sum_p w_p V4_p (the J V row fix-ups of the padded FP32 path)
+cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, const float4* acc4, float* out, cudaStream_t s);
 // y4[i] = (x[3i], x[3i+1], x[3i+2], 0)
 cudaError_t launch_pad4(int64_t N, const float* x, float4* y4, cudaStream_t s);
 // inner Arnoldi bookkeeping; sc holds the rotated Hessenberg, the rotations, g and the

@@ -231,7 +231,9 @@ static int apply_op(pnp_ctx* c, const double* U, const double* x, double* w, int
 // With from_state, the state's Gauss-point quantities come from the linearisation stored
 // by launch_lane_state for the current Krylov solve.
 static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_state) {
-  // c->JV4 is zero here: zeroed at allocation and cleared again by every pack
+  // a memset: clearing the accumulator inside the pack, right after the vector atomics
+  // that filled it, measured several times slower on GB300
+  CK(cudaMemsetAsync(c->JV4, 0, sizeof(float4) * c->n_nodes, c->stream));
   {
     ElemArgs<float> A = elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr);
     A.rec = c->rec32;
