@@ -58,7 +58,8 @@ enum pnp_status {
                                     true residual by less than 5% (stagnation) */
   PNP_ERR_NEWTON_DIVERGED = 6,   /* Newton hit its iteration limit or line search failed */
   PNP_ERR_CUDA = 7,              /* a CUDA call failed; the context is latched */
-  PNP_ERR_DEVICE_FLAG = 8,       /* a kernel's own check failed (bad index / input) */
+  PNP_ERR_DEVICE_FLAG = 8,       /* a kernel's own check failed (bad index / input), or a
+                                    bounded wait of a kernel on its own copies gave up */
   PNP_ERR_NOMEM = 9,             /* host or device allocation failed */
   PNP_ERR_STATE = 10             /* call not valid in the current state */
 };
@@ -209,7 +210,10 @@ int pnp_jv(pnp_ctx* c, const double* U, const void* V, void* JV, int precision);
  * pnp_jv_linearized then returns JV = J V for FP32 device vectors V, JV [n][3], equal to
  * pnp_jv(..., PNP_F32) at that U up to FP32 summation order.  A later solver call
  * (pnp_gmres, pnp_newton_solve, pnp_time_step) replaces the stored linearisation;
- * pnp_jv_linearized then returns PNP_ERR_STATE until pnp_linearize is called again. */
+ * pnp_jv_linearized then returns PNP_ERR_STATE until pnp_linearize is called again.
+ * The J V kernel streams the stored quantities through shared memory with bulk copies;
+ * if one of its bounded waits on them gives up it raises PNP_ERR_DEVICE_FLAG (here, and
+ * from the solver calls that use it), latched for the context. */
 int pnp_linearize(pnp_ctx* c, const double* U);
 int pnp_jv_linearized(pnp_ctx* c, const float* V, float* JV);
 /* 3x3 diagonal blocks of J(U): D device FP64 [n][3][3] (row-major per node), exact

@@ -243,6 +243,7 @@ int pnp_ctx_create(const pnp_mesh* m, const pnp_params* p, void* stream, pnp_ctx
   auto up = [&](void* dst, const void* src, size_t bytes) {
     if (bytes && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
   };
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->dflag, 0, sizeof(int) * 4, s);
   up(c->d_conn, m->el_conn.data(), sizeof(int32_t) * m->el_conn.size());
   up(c->d_level, m->el_level.data(), m->el_level.size());
   up(c->d_faces, faces.data(), faces.size());
@@ -513,8 +514,7 @@ int pnp_jv_linearized(pnp_ctx* c, const float* V, float* JV) {
   if (!V || !JV) PNP_FAIL(PNP_ERR_ARG, "pnp_jv_linearized: null pointer");
   if (!c->lin_user) PNP_FAIL(PNP_ERR_STATE, "pnp_jv_linearized: no stored linearisation (call pnp_linearize)");
   if (int rc = ctx_jv32_linearized(c, V, JV)) return rc;
-  CK(cudaStreamSynchronize(c->stream));
-  return PNP_OK;
+  return ctx_check_staged_waits(c);
 }
 
 int pnp_block_diag(pnp_ctx* c, const double* U, double* D) {

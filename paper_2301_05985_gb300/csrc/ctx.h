@@ -158,6 +158,8 @@ int ctx_residual(pnp_ctx* c, const double* U, double* F);
 int ctx_jv64(pnp_ctx* c, const double* U, const double* V, double* JV);
 int ctx_prepare_f32(pnp_ctx* c, const double* U);
 int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32);
+// PNP_ERR_DEVICE_FLAG once a wait of the staged J V has given up (the flag is latched)
+int ctx_check_staged_waits(pnp_ctx* c);
 int ctx_block_diag(pnp_ctx* c, const double* U, double* D);
 int ctx_norm(pnp_ctx* c, const double* x, double* out);
 int ctx_dot(pnp_ctx* c, const double* x, const double* y, double* out);

@@ -15,6 +15,7 @@
 // The test side (element vector r_c = w sum_q [N_c(q) S_q + grad N_c(q) . Phi_q], w =
 // (h/2)^d) is the transpose: the value operator is symmetric and the derivative's
 // transpose sends s_b (x_0 + x_1) / h to node b (s_0 = -1, s_1 = +1).
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.h"
@@ -351,8 +352,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
 // Inside one Krylov solve the state (U, h, v) is fixed, so the Gauss-point quantities J V
 // needs from it are computed once per solve and stored per lane, four float4 in
 // lane-major order (qp[j * L + t], L = 2^d E): (v0 v1 v2 gp0) (gp1 gp2 gc+0 gc+1)
-// (gc+2 gc-0 gc-1 gc-2) (tau, z+(c+ - tau R+), z-(c- - tau R-), 0).  Each J V then reads
-// 64 B per lane, coalesced, instead of gathering and interpolating the state.
+// (gc+2 gc-0 gc-1 gc-2) (tau, z+(c+ - tau R+), z-(c- - tau R-), level) with the element's
+// level as integer bits.  Each J V then reads 64 B per lane, coalesced, instead of
+// gathering and interpolating the state.
 constexpr int kLaneThreads = 256;
 
 template <int D>
@@ -382,85 +384,185 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_lane_state(ElemArgs<float> 
   qp[t] = make_float4(v[0], v[1], v[2], gp[0]);
   qp[L + t] = make_float4(gp[1], gp[2], gc[0][0], gc[0][1]);
   qp[2 * L + t] = make_float4(gc[0][2], gc[1][0], gc[1][1], gc[1][2]);
-  qp[3 * L + t] = make_float4(tau, zc0, zc1, 0.0f);
+  qp[3 * L + t] = make_float4(tau, zc0, zc1, __int_as_float(lev));
+}
+
+// The J V kernel streams the stored state through shared memory: a persistent grid
+// walks tiles of kLaneThreads lanes, and per tile one thread issues bulk copies (TMA,
+// cp.async.bulk) of the four state rows and the tile's connectivity into a stage of
+// shared memory, completing on the stage's mbarrier.  kStages tiles are in flight per
+// block, so the state's HBM stream does not wait on the per-lane arithmetic and
+// atomics of the tile before.
+constexpr int kStages = 2;
+constexpr int kWaitPolls = 1 << 22;  // try_wait polls before a wait gives up (about a second)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bounded wait for the phase of the given parity to complete; false when it did not
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (int i = 0; i < kWaitPolls; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 template <int D>
 __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<float> A, LaneParams<float> K,
-                                                                 const float4* __restrict__ qp) {
+                                                                 const float4* __restrict__ qp, int* err) {
   constexpr int NC = 1 << D;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if ((t & ~int64_t(31)) / NC >= A.n_elem) return;
-  const int64_t e = t / NC;
-  const int c = (int)(t & (NC - 1));
-  const bool valid = e < A.n_elem;
-  const int32_t id = valid ? __ldg(A.conn + e * NC + c) : 0;
-  const int lev = valid ? A.level[e] : 0;
-  const float inv_h = pow2i(lev, 0.0f);
-  const float w = pow2i(-D * (lev + 1), 0.0f);
-  const float nb = float(-0.5 * (1.0 - kG));
-  float sh[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) sh[k] = ((c >> k) & 1) ? inv_h : -inv_h;
-  const float kappa = K.kappa, e2 = K.e2;
+  __shared__ __align__(128) float4 sq[kStages][4][kLaneThreads];
+  __shared__ __align__(16) int32_t sconn[kStages][kLaneThreads];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  const int tid = threadIdx.x;
   const int64_t L = A.n_elem * NC;
-  float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0;
-  if (valid) {
-    q0 = __ldg(qp + t);
-    q1 = __ldg(qp + L + t);
-    q2 = __ldg(qp + 2 * L + t);
-    q3 = __ldg(qp + 3 * L + t);
+  const int64_t n_tiles = (L + kLaneThreads - 1) / kLaneThreads;
+  const int64_t G = gridDim.x;
+  // thread 0: copy tile `tl` into stage `st` (sizes are multiples of 16 bytes: L and the
+  // tile start are multiples of 2^d lanes, 4 B of connectivity per lane)
+  auto issue = [&](int64_t tl, int st) {
+    const int64_t t0 = tl * kLaneThreads;
+    const uint32_t n = (uint32_t)(L - t0 < kLaneThreads ? L - t0 : kLaneThreads);
+    mbar_expect_tx(&bar[st], 4u * 16u * n + 4u * n);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bulk_g2s(&sq[st][j][0], qp + j * L + t0, 16u * n, &bar[st]);
+    bulk_g2s(&sconn[st][0], A.conn + t0, 4u * n, &bar[st]);
+  };
+  if (tid == 0) {
+#pragma unroll
+    for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  const float v[3] = {q0.x, q0.y, q0.z}, gp[3] = {q0.w, q1.x, q1.y};
-  const float gc[2][3] = {{q1.z, q1.w, q2.x}, {q2.y, q2.z, q2.w}};
-  const float tau = q3.x, zc_tR[2] = {q3.y, q3.z};
-  float dn[3];
-  if (A.V4) load_dir4(A, id, valid, dn);
-  else load_node<float, 3>(A, id, valid, A.V, 3, dn);
-  float dcv[2], dgc[2][3], dgp[3], dR[2], S[3], Phi[3][3];
+  __syncthreads();
+  uint32_t pending = 0;  // thread 0: stages with a copy in flight
+  if (tid == 0) {
 #pragma unroll
-  for (int s = 0; s < 2; ++s) interp_vg<float, D>(dn[s], nb, sh, dcv[s], dgc[s]);
-  interp_g<float, D>(dn[2], nb, sh, dgp);
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const float z = s == 0 ? 1.0f : -1.0f;
-    float P[3], vg = 0.0f, pg = 0.0f, gcd = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      P[k] = v[k] - z * gp[k];
-      vg = fmaf(v[k], dgc[s][k], vg);
-      pg = fmaf(P[k], dgc[s][k], pg);
-      gcd = fmaf(gc[s][k], dgp[k], gcd);
+    for (int st = 0; st < kStages; ++st)
+      if (blockIdx.x + st * G < n_tiles) {
+        issue(blockIdx.x + st * G, st);
+        pending |= 1u << st;
+      }
+  }
+
+  const float nb = float(-0.5 * (1.0 - kG));
+  const float kappa = K.kappa, e2 = K.e2;
+  for (int k = 0;; ++k) {
+    const int64_t tl = blockIdx.x + (int64_t)k * G;
+    if (tl >= n_tiles) break;
+    const int st = k % kStages;
+    const uint32_t parity = (uint32_t)(k / kStages) & 1u;
+    const bool ok = mbar_wait(&bar[st], parity);
+    if (__syncthreads_or(!ok)) {
+      // a copy did not complete: flag it, let the copies still in flight land, return
+      if (tid == 0) {
+        atomicOr(err, 1);
+        for (int j = 0; j < kStages; ++j) {
+          const int kk = k + ((j - st + kStages) % kStages);
+          if (pending >> j & 1u) mbar_wait(&bar[j], (uint32_t)(kk / kStages) & 1u);
+        }
+      }
+      return;
     }
-    dR[s] = fmaf(kappa, dcv[s], pg - z * gcd);
-    S[s] = fmaf(kappa, dcv[s], vg);
-    const float tdR = tau * dR[s];
-    const float zdc = z * dcv[s];
+    const int64_t t = tl * kLaneThreads + tid;
+    const bool valid = t < L;
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0;
+    int32_t id = 0;
+    if (valid) {
+      q0 = sq[st][0][tid];
+      q1 = sq[st][1][tid];
+      q2 = sq[st][2][tid];
+      q3 = sq[st][3][tid];
+      id = sconn[st][tid];
+    }
+    __syncthreads();  // stage st is read: refill it with the tile kStages ahead
+    if (tid == 0) {
+      pending &= ~(1u << st);
+      if (tl + kStages * G < n_tiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(tl + kStages * G, st);
+        pending |= 1u << st;
+      }
+    }
+
+    const int c = (int)(t & (NC - 1));
+    const int lev = __float_as_int(q3.w);  // 0 for lanes past the end
+    const float inv_h = pow2i(lev, 0.0f);
+    const float w = pow2i(-D * (lev + 1), 0.0f);
+    float sh[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) Phi[s][k] = fmaf(tdR, P[k], fmaf(zc_tR[s], dgp[k], fmaf(zdc, gp[k], dgc[s][k])));
-  }
-  S[2] = fmaf(tau, dR[0] - dR[1], dcv[1] - dcv[0]);
+    for (int kk = 0; kk < 3; ++kk) sh[kk] = ((c >> kk) & 1) ? inv_h : -inv_h;
+    const float v[3] = {q0.x, q0.y, q0.z}, gp[3] = {q0.w, q1.x, q1.y};
+    const float gc[2][3] = {{q1.z, q1.w, q2.x}, {q2.y, q2.z, q2.w}};
+    const float tau = q3.x, zc_tR[2] = {q3.y, q3.z};
+    float dn[3];
+    if (A.V4) load_dir4(A, id, valid, dn);
+    else load_node<float, 3>(A, id, valid, A.V, 3, dn);
+    float dcv[2], dgc[2][3], dgp[3], dR[2], S[3], Phi[3][3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) Phi[2][k] = e2 * dgp[k];
-  float r[3];
+    for (int s = 0; s < 2; ++s) interp_vg<float, D>(dn[s], nb, sh, dcv[s], dgc[s]);
+    interp_g<float, D>(dn[2], nb, sh, dgp);
 #pragma unroll
-  for (int f = 0; f < 3; ++f) r[f] = w * test_t<float, D>(S[f], Phi[f], nb, sh);
-  if (!valid) return;
-  if (A.out4) {
-    scatter4(A, id, r);
-    return;
-  }
-  if (id >= 0) {
+    for (int s = 0; s < 2; ++s) {
+      const float z = s == 0 ? 1.0f : -1.0f;
+      float P[3], vg = 0.0f, pg = 0.0f, gcd = 0.0f;
 #pragma unroll
-    for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)id + f, r[f]);
-  } else {
-    const int32_t hh = -id - 1;
-    const int np = A.hang_np[hh];
-    const float wgt = np == 2 ? 0.5f : 0.25f;
-    for (int p = 0; p < np; ++p) {
-      const int32_t pid = A.hang_par[4 * hh + p];
+      for (int kk = 0; kk < 3; ++kk) {
+        P[kk] = v[kk] - z * gp[kk];
+        vg = fmaf(v[kk], dgc[s][kk], vg);
+        pg = fmaf(P[kk], dgc[s][kk], pg);
+        gcd = fmaf(gc[s][kk], dgp[kk], gcd);
+      }
+      dR[s] = fmaf(kappa, dcv[s], pg - z * gcd);
+      S[s] = fmaf(kappa, dcv[s], vg);
+      const float tdR = tau * dR[s];
+      const float zdc = z * dcv[s];
 #pragma unroll
-      for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)pid + f, wgt * r[f]);
+      for (int kk = 0; kk < 3; ++kk)
+        Phi[s][kk] = fmaf(tdR, P[kk], fmaf(zc_tR[s], dgp[kk], fmaf(zdc, gp[kk], dgc[s][kk])));
+    }
+    S[2] = fmaf(tau, dR[0] - dR[1], dcv[1] - dcv[0]);
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) Phi[2][kk] = e2 * dgp[kk];
+    float r[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) r[f] = w * test_t<float, D>(S[f], Phi[f], nb, sh);
+    if (!valid) continue;
+    if (A.out4) {
+      scatter4(A, id, r);
+      continue;
+    }
+    if (id >= 0) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)id + f, r[f]);
+    } else {
+      const int32_t hh = -id - 1;
+      const int np = A.hang_np[hh];
+      const float wgt = np == 2 ? 0.5f : 0.25f;
+      for (int p = 0; p < np; ++p) {
+        const int32_t pid = A.hang_par[4 * hh + p];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)pid + f, wgt * r[f]);
+      }
     }
   }
 }
@@ -498,12 +600,28 @@ cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, cudaStream_t s) {
+cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int* err, cudaStream_t s) {
   if (A.n_elem == 0) return cudaSuccess;
   const LaneParams<float> K{float(A.P.kappa), float(A.P.tau_t), float(A.P.C_I * dim), float(A.P.eps2x2)};
-  const unsigned blocks = (unsigned)(((A.n_elem << dim) + kLaneThreads - 1) / kLaneThreads);
-  if (dim == 2) k_jv_from_state<2><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
-  else k_jv_from_state<3><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+  // persistent grid: the resident blocks of every SM, no more than there are tiles
+  static int per_sm[2] = {0, 0}, n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_jv_from_state<2>, kLaneThreads, 0);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_jv_from_state<3>, kLaneThreads, 0);
+    if (e != cudaSuccess) {
+      n_sm = 0;
+      return e;
+    }
+  }
+  const int64_t tiles = ((A.n_elem << dim) + kLaneThreads - 1) / kLaneThreads;
+  const unsigned blocks = (unsigned)std::min<int64_t>(tiles, (int64_t)n_sm * std::max(1, per_sm[dim - 2]));
+  if (dim == 2) k_jv_from_state<2><<<blocks, kLaneThreads, 0, s>>>(A, K, qp, err);
+  else k_jv_from_state<3><<<blocks, kLaneThreads, 0, s>>>(A, K, qp, err);
   note_launch();
   return cudaGetLastError();
 }

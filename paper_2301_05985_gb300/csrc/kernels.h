@@ -70,9 +70,10 @@ double element_kernel_flops(int dim, bool jv);
 bool element_kernel_is_lanes();
 // FP32 J V from a stored linearisation (element_lanes.cu): launch_lane_state computes, per
 // element lane, the state's Gauss-point quantities J V needs (qp: 4 * 2^dim * n_elem float4,
-// A.rec set); launch_jv_from_state applies J V with them (A.V or A.V4, A.out or A.out4)
+// A.rec set); launch_jv_from_state applies J V with them (A.V or A.V4, A.out or A.out4;
+// qp and A.conn 16-byte aligned).  err[0] |= 1 when a staged copy's wait gave up.
 cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, cudaStream_t s);
-cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, cudaStream_t s);
+cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int* err, cudaStream_t s);
 double jv_from_state_flops(int dim);
 template <typename T>
 cudaError_t launch_block_diag(int dim, const ElemArgs<T>& A, T* Dout, cudaStream_t s);

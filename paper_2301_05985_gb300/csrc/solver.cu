@@ -225,6 +225,15 @@ static int apply_op(pnp_ctx* c, const double* U, const double* x, double* w, int
   return PNP_OK;
 }
 
+// PNP_ERR_DEVICE_FLAG when a wait of the staged J V gave up (its copies never landed)
+int ctx_check_staged_waits(pnp_ctx* c) {
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (flag) PNP_FAIL(PNP_ERR_DEVICE_FLAG, "J V: a staged copy of the stored linearisation did not complete");
+  return PNP_OK;
+}
+
 // FP32 J V of the inner solve: the direction padded to 16 bytes per node (one load), the
 // output accumulated with one vector atomic per node, then packed to [N][3] with the
 // Dirichlet and hanging rows of J V.  Lane-group kernel only.
@@ -243,7 +252,7 @@ static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_stat
       // direction in, result out (12 B per node each), the stored state (64 B per lane)
       ProfScope ps(c, PNP_PROF_JV32, 24.0 * c->n_nodes + 64.0 * (double)(c->n_elem << c->dim) + c->conn_bytes(),
                    jv_from_state_flops(c->dim) * c->n_elem);
-      CK(launch_jv_from_state(c->dim, A, c->qp32, c->stream));
+      CK(launch_jv_from_state(c->dim, A, c->qp32, c->dflag + 1, c->stream));
     } else {
       ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(),
                    element_kernel_flops(c->dim, true) * c->n_elem);
@@ -496,6 +505,7 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
     // floor (FP32 J V) or a stalled flexible preconditioner; stop with the iterate
     if (std::isfinite(beta) && beta > 0.95 * beta_cycle) {
       CK(cudaStreamSynchronize(s));
+      if (from_state) RC(ctx_check_staged_waits(c));
       *its_out = total;
       *rel_out = beta / bn;
       PNP_FAIL(PNP_ERR_KRYLOV_MAXIT, "gmres: stagnated after %d iterations at relative residual %.3e > %.3e", total,
@@ -506,6 +516,7 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   CK(cudaStreamSynchronize(s));
   *its_out = total;
   *rel_out = beta / bn;
+  if (from_state) RC(ctx_check_staged_waits(c));
   return PNP_OK;
 }
 
