@@ -147,43 +147,43 @@ __global__ void k_pad4(int64_t N, const float* __restrict__ x, float4* __restric
   if (i < N) y[i] = make_float4(x[3 * i], x[3 * i + 1], x[3 * i + 2], 0.0f);
 }
 
-// out <- acc with the Dirichlet rows of J V (= V); hanging rows are left to k_hanging_rows4
-__global__ void k_pack_jv4(int64_t N, const uint8_t* __restrict__ faces, BcTable bc, const float4* __restrict__ V4,
+// out <- acc with the Dirichlet rows of J V (= V) for threads i < N; threads N + h write
+// the constraint row of hanging node h: out_h = V_h - sum_p w_p V_p (V padded)
+__global__ void k_pack_jv4(int64_t N, int64_t H, const uint8_t* __restrict__ faces, BcTable bc,
+                           const int32_t* __restrict__ hnode, const int32_t* __restrict__ hpar,
+                           const uint8_t* __restrict__ hnp, const float4* __restrict__ V4,
                            const float4* __restrict__ acc, float* __restrict__ out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const uint8_t fm = faces[i];
-  if (fm & 0x80) return;
-  const float4 a = acc[i];
-  float r[3] = {a.x, a.y, a.z};
-  if (fm & 0x3F) {
-    const float4 v = V4[i];
-    const float vv[3] = {v.x, v.y, v.z};
+  if (i < N) {
+    const uint8_t fm = faces[i];
+    if (fm & 0x80) return;
+    const float4 a = acc[i];
+    float r[3] = {a.x, a.y, a.z};
+    if (fm & 0x3F) {
+      const float4 v = V4[i];
+      const float vv[3] = {v.x, v.y, v.z};
 #pragma unroll
-    for (int f = 0; f < 3; ++f)
-      if (fm & bc.dir_faces[f] & 0x3F) r[f] = vv[f];
+      for (int f = 0; f < 3; ++f)
+        if (fm & bc.dir_faces[f] & 0x3F) r[f] = vv[f];
+    }
+    out[3 * i] = r[0];
+    out[3 * i + 1] = r[1];
+    out[3 * i + 2] = r[2];
+    return;
   }
-  out[3 * i] = r[0];
-  out[3 * i + 1] = r[1];
-  out[3 * i + 2] = r[2];
-}
-
-// constraint rows of hanging nodes: out_h = V_h - sum_p w_p V_p, V padded
-__global__ void k_hanging_rows4(int64_t H, const int32_t* __restrict__ hnode, const int32_t* __restrict__ hpar,
-                                const uint8_t* __restrict__ hnp, const float4* __restrict__ V4, float* __restrict__ out) {
-  const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t h = i - N;
   if (h >= H) return;
   const int np = hnp[h];
   const float wgt = np == 2 ? 0.5f : 0.25f;
   const int64_t id = hnode[h];
-  float4 s = V4[id];
+  float4 sv = V4[id];
   for (int p = 0; p < np; ++p) {
     const float4 a = V4[hpar[4 * h + p]];
-    s.x -= wgt * a.x; s.y -= wgt * a.y; s.z -= wgt * a.z;
+    sv.x -= wgt * a.x; sv.y -= wgt * a.y; sv.z -= wgt * a.z;
   }
-  out[3 * id] = s.x;
-  out[3 * id + 1] = s.y;
-  out[3 * id + 2] = s.z;
+  out[3 * id] = sv.x;
+  out[3 * id + 1] = sv.y;
+  out[3 * id + 2] = sv.z;
 }
 
 // Arnoldi bookkeeping of the inner process.  Basis vectors u_i are kept unnormalised
@@ -383,12 +383,9 @@ cudaError_t launch_pad4(int64_t N, const float* x, float4* y4, cudaStream_t s) {
 }
 
 cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, const float4* acc4, float* out, cudaStream_t s) {
-  if (R.n_nodes) {
-    k_pack_jv4<<<nblk(R.n_nodes, 256), 256, 0, s>>>(R.n_nodes, R.faces, R.bc, V4, acc4, out);
-    note_launch();
-  }
-  if (R.n_hanging) {
-    k_hanging_rows4<<<nblk(R.n_hanging, 256), 256, 0, s>>>(R.n_hanging, R.hnode, R.hpar, R.hnp, V4, out);
+  if (R.n_nodes + R.n_hanging) {
+    k_pack_jv4<<<nblk(R.n_nodes + R.n_hanging, 256), 256, 0, s>>>(R.n_nodes, R.n_hanging, R.faces, R.bc, R.hnode,
+                                                                  R.hpar, R.hnp, V4, acc4, out);
     note_launch();
   }
   return cudaGetLastError();
