@@ -387,12 +387,12 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_lane_state(ElemArgs<float> 
   qp[3 * L + t] = make_float4(tau, zc0, zc1, __int_as_float(lev));
 }
 
-// The J V kernel streams the stored state through shared memory, warp by warp: a
-// persistent grid whose warps each walk their own tiles of 32 lanes (2^(5-d) elements);
-// per tile, lane 0 issues bulk copies (TMA, cp.async.bulk) of the four state rows and the
-// tile's connectivity into one of the warp's stages, completing on that stage's
-// mbarrier.  kStages tiles are in flight per warp, so the state's HBM stream does not
-// wait on the arithmetic and atomics of the tiles before, and no warp waits for another.
+// The J V kernel streams the stored state through shared memory: a persistent grid
+// walks tiles of kLaneThreads lanes, and per tile one thread issues bulk copies (TMA,
+// cp.async.bulk) of the four state rows and the tile's connectivity into a stage of
+// shared memory, completing on the stage's mbarrier.  kStages tiles are in flight per
+// block, so the state's HBM stream does not wait on the per-lane arithmetic and
+// atomics of the tile before.
 constexpr int kStages = 2;
 constexpr int kWaitPolls = 1 << 22;  // try_wait polls before a wait gives up (about a second)
 
@@ -431,75 +431,75 @@ template <int D>
 __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<float> A, LaneParams<float> K,
                                                                  const float4* __restrict__ qp, int* err) {
   constexpr int NC = 1 << D;
-  constexpr int kWarps = kLaneThreads / 32;
-  __shared__ __align__(128) float4 sq[kWarps][kStages][4][32];
-  __shared__ __align__(16) int32_t sconn[kWarps][kStages][32];
-  __shared__ __align__(8) uint64_t bar[kWarps][kStages];
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  __shared__ __align__(128) float4 sq[kStages][4][kLaneThreads];
+  __shared__ __align__(16) int32_t sconn[kStages][kLaneThreads];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  const int tid = threadIdx.x;
   const int64_t L = A.n_elem * NC;
-  const int64_t n_tiles = (L + 31) / 32;
-  const int64_t GW = (int64_t)gridDim.x * kWarps;
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + wp;
-  // lane 0: copy tile `tl` into stage `st` of this warp (sizes are multiples of 16 bytes:
-  // L and the tile start are multiples of 2^d >= 4 lanes, 4 B of connectivity per lane)
+  const int64_t n_tiles = (L + kLaneThreads - 1) / kLaneThreads;
+  const int64_t G = gridDim.x;
+  // thread 0: copy tile `tl` into stage `st` (sizes are multiples of 16 bytes: L and the
+  // tile start are multiples of 2^d lanes, 4 B of connectivity per lane)
   auto issue = [&](int64_t tl, int st) {
-    const int64_t t0 = tl * 32;
-    const uint32_t n = (uint32_t)(L - t0 < 32 ? L - t0 : 32);
-    mbar_expect_tx(&bar[wp][st], 4u * 16u * n + 4u * n);
+    const int64_t t0 = tl * kLaneThreads;
+    const uint32_t n = (uint32_t)(L - t0 < kLaneThreads ? L - t0 : kLaneThreads);
+    mbar_expect_tx(&bar[st], 4u * 16u * n + 4u * n);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bulk_g2s(&sq[wp][st][j][0], qp + j * L + t0, 16u * n, &bar[wp][st]);
-    bulk_g2s(&sconn[wp][st][0], A.conn + t0, 4u * n, &bar[wp][st]);
+    for (int j = 0; j < 4; ++j) bulk_g2s(&sq[st][j][0], qp + j * L + t0, 16u * n, &bar[st]);
+    bulk_g2s(&sconn[st][0], A.conn + t0, 4u * n, &bar[st]);
   };
-  uint32_t pending = 0;  // lane 0: stages with a copy in flight
-  if (lane == 0) {
+  if (tid == 0) {
 #pragma unroll
-    for (int st = 0; st < kStages; ++st) mbar_init(&bar[wp][st], 1);
+    for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t pending = 0;  // thread 0: stages with a copy in flight
+  if (tid == 0) {
 #pragma unroll
     for (int st = 0; st < kStages; ++st)
-      if (gw + st * GW < n_tiles) {
-        issue(gw + st * GW, st);
+      if (blockIdx.x + st * G < n_tiles) {
+        issue(blockIdx.x + st * G, st);
         pending |= 1u << st;
       }
   }
-  __syncwarp();
 
   const float nb = float(-0.5 * (1.0 - kG));
   const float kappa = K.kappa, e2 = K.e2;
   for (int k = 0;; ++k) {
-    const int64_t tl = gw + (int64_t)k * GW;
+    const int64_t tl = blockIdx.x + (int64_t)k * G;
     if (tl >= n_tiles) break;
     const int st = k % kStages;
     const uint32_t parity = (uint32_t)(k / kStages) & 1u;
-    const bool ok = mbar_wait(&bar[wp][st], parity);
-    if (__any_sync(kFull, !ok)) {
+    const bool ok = mbar_wait(&bar[st], parity);
+    if (__syncthreads_or(!ok)) {
       // a copy did not complete: flag it, let the copies still in flight land, return
-      if (lane == 0) {
+      if (tid == 0) {
         atomicOr(err, 1);
         for (int j = 0; j < kStages; ++j) {
           const int kk = k + ((j - st + kStages) % kStages);
-          if (pending >> j & 1u) mbar_wait(&bar[wp][j], (uint32_t)(kk / kStages) & 1u);
+          if (pending >> j & 1u) mbar_wait(&bar[j], (uint32_t)(kk / kStages) & 1u);
         }
       }
       return;
     }
-    const int64_t t = tl * 32 + lane;
+    const int64_t t = tl * kLaneThreads + tid;
     const bool valid = t < L;
     float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0;
     int32_t id = 0;
     if (valid) {
-      q0 = sq[wp][st][0][lane];
-      q1 = sq[wp][st][1][lane];
-      q2 = sq[wp][st][2][lane];
-      q3 = sq[wp][st][3][lane];
-      id = sconn[wp][st][lane];
+      q0 = sq[st][0][tid];
+      q1 = sq[st][1][tid];
+      q2 = sq[st][2][tid];
+      q3 = sq[st][3][tid];
+      id = sconn[st][tid];
     }
-    __syncwarp();  // stage st is read: refill it with the tile kStages ahead
-    if (lane == 0) {
+    __syncthreads();  // stage st is read: refill it with the tile kStages ahead
+    if (tid == 0) {
       pending &= ~(1u << st);
-      if (tl + kStages * GW < n_tiles) {
+      if (tl + kStages * G < n_tiles) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(tl + kStages * GW, st);
+        issue(tl + kStages * G, st);
         pending |= 1u << st;
       }
     }
@@ -618,9 +618,8 @@ cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4
       return e;
     }
   }
-  const int64_t warp_tiles = ((A.n_elem << dim) + 31) / 32;
-  const int64_t need = (warp_tiles + kLaneThreads / 32 - 1) / (kLaneThreads / 32);
-  const unsigned blocks = (unsigned)std::min<int64_t>(need, (int64_t)n_sm * std::max(1, per_sm[dim - 2]));
+  const int64_t tiles = ((A.n_elem << dim) + kLaneThreads - 1) / kLaneThreads;
+  const unsigned blocks = (unsigned)std::min<int64_t>(tiles, (int64_t)n_sm * std::max(1, per_sm[dim - 2]));
   if (dim == 2) k_jv_from_state<2><<<blocks, kLaneThreads, 0, s>>>(A, K, qp, err);
   else k_jv_from_state<3><<<blocks, kLaneThreads, 0, s>>>(A, K, qp, err);
   note_launch();
