@@ -217,8 +217,12 @@ int pnp_jv(pnp_ctx* c, const double* U, const void* V, void* JV, int precision);
 int pnp_linearize(pnp_ctx* c, const double* U);
 int pnp_jv_linearized(pnp_ctx* c, const float* V, float* JV);
 /* 3x3 diagonal blocks of J(U): D device FP64 [n][3][3] (row-major per node), exact
- * for the assembled operator including hanging-node coupling. */
+ * for the assembled operator including hanging-node coupling.  Dirichlet rows are
+ * identity rows, hanging rows identity blocks. */
 int pnp_block_diag(pnp_ctx* c, const double* U, double* D);
+/* The same blocks in FP32 arithmetic at U rounded to FP32 (D device FP32 [n][3][3]):
+ * the blocks the mixed-precision solver inverts for its block-Jacobi preconditioner. */
+int pnp_block_diag_f32(pnp_ctx* c, const double* U, float* D);
 /* ||x||_2 of a device FP64 vector of n entries, the reduction Newton and GMRES use
  * (fixed grid, fixed summation order: bitwise reproducible); result on the host.
  * x may be NULL when n == 0.  Uses the context's scratch and stream. */

@@ -526,6 +526,16 @@ int pnp_block_diag(pnp_ctx* c, const double* U, double* D) {
   return PNP_OK;
 }
 
+int pnp_block_diag_f32(pnp_ctx* c, const double* U, float* D) {
+  CTX_GUARD(c);
+  if (!U || !D) PNP_FAIL(PNP_ERR_ARG, "pnp_block_diag_f32: null pointer");
+  if (int rc = ctx_prepare_history(c)) return rc;
+  if (int rc = ctx_prepare_f32(c, U)) return rc;
+  if (int rc = ctx_block_diag32(c, D)) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
 int pnp_norm2(pnp_ctx* c, const double* x, int64_t n, double* result) {
   CTX_GUARD(c);
   if (!result || n < 0 || (!x && n > 0)) PNP_FAIL(PNP_ERR_ARG, "pnp_norm2: bad arguments");

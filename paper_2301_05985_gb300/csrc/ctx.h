@@ -161,6 +161,8 @@ int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32);
 // PNP_ERR_DEVICE_FLAG once a wait of the staged J V has given up (the flag is latched)
 int ctx_check_staged_waits(pnp_ctx* c);
 int ctx_block_diag(pnp_ctx* c, const double* U, double* D);
+// FP32 blocks at the prepared FP32 state (ctx_prepare_f32 first)
+int ctx_block_diag32(pnp_ctx* c, float* D);
 int ctx_norm(pnp_ctx* c, const double* x, double* out);
 int ctx_dot(pnp_ctx* c, const double* x, const double* y, double* out);
 int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int precision, int max_it,

@@ -567,6 +567,229 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
   }
 }
 
+
+// ---- block diagonal of the Jacobian (block-Jacobi preconditioner) ----------------
+// D_n = sum over elements, Gauss points and local pairs (i, j) whose constraint targets
+// both reach node n of t_i(n) t_j(n) B_ij, B_ij the 3x3 block (test N_i, trial N_j) of
+// the linearised element operator and t the constraint weight (1 for a regular node, 1/2
+// or 1/4 for a hanging node's parents).  Regular corners only pair with themselves; the
+// pairs i != j arise only through hanging corners.  Lane c of an element group holds
+// Gauss point c.  A block has seven nonzero entries, stored in this order:
+// (+,+) (+,phi) (-,-) (-,phi) (phi,+) (phi,-) (phi,phi).
+constexpr int kBlk = 7;
+__device__ __forceinline__ int blk_slot(int k) {  // position in the row-major 3x3 block
+  return k == 0 ? 0 : k == 1 ? 2 : k == 2 ? 4 : k == 3 ? 5 : k == 4 ? 6 : k == 5 ? 7 : 8;
+}
+
+// value and gradient of corner i's shape function at this lane's Gauss point (corner c)
+template <typename T, int D>
+__device__ __forceinline__ void shape_at(int i, int c, T inv_h, T& N, T (&dN)[3]) {
+  const T fs = T(0.5 * (1.0 + kG)), fo = T(0.5 * (1.0 - kG));
+  T f[3];
+#pragma unroll
+  for (int k = 0; k < D; ++k) f[k] = (((i ^ c) >> k) & 1) ? fo : fs;
+  N = T(1);
+#pragma unroll
+  for (int k = 0; k < D; ++k) N *= f[k];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T a = T(0);
+    if (k < D) {
+      a = ((i >> k) & 1) ? inv_h : -inv_h;
+#pragma unroll
+      for (int l = 0; l < D; ++l)
+        if (l != k) a *= f[l];
+    }
+    dN[k] = a;
+  }
+}
+
+// the seven entries of B_ij at this Gauss point (without the quadrature weight):
+// derivatives of the species rows S_s, Phi_s and the Poisson row with respect to the
+// trial field N_j, tested with N_i (Def. 3 linearised, as in the J V)
+template <typename T>
+__device__ __forceinline__ void pair_block(T Ni, const T (&dNi)[3], T Nj, const T (&dNj)[3], T kappa, T e2, T tau,
+                                           const T (&cv)[2], const T (&gc)[2][3], const T (&gp)[3], const T (&v)[3],
+                                           const T (&R)[2], const T (&P)[2][3], T (&B)[kBlk]) {
+  T gij = T(0), gip = T(0), vgj = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gij = fma(dNi[k], dNj[k], gij);
+    gip = fma(dNi[k], gp[k], gip);
+    vgj = fma(v[k], dNj[k], vgj);
+  }
+  T pp = T(0);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T z = s == 0 ? T(1) : T(-1);
+    T pgj = T(0), giP = T(0), gcj = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      pgj = fma(P[s][k], dNj[k], pgj);
+      giP = fma(dNi[k], P[s][k], giP);
+      gcj = fma(gc[s][k], dNj[k], gcj);
+    }
+    const T dRdc = fma(kappa, Nj, pgj);  // d R_s / d c_s
+    const T dRdp = -z * gcj;             // d R_s / d phi
+    B[2 * s] = Ni * fma(kappa, Nj, vgj) + gij + z * Nj * gip + tau * dRdc * giP;
+    B[2 * s + 1] = z * cv[s] * gij + tau * dRdp * giP - tau * R[s] * z * gij;
+    B[4 + s] = z * Ni * (tau * dRdc - Nj);
+    pp = fma(z * tau, dRdp, pp);
+  }
+  B[6] = fma(e2, gij, Ni * pp);
+}
+
+// constraint targets of a corner: itself, or a hanging node's parents with their weights
+template <typename T>
+__device__ __forceinline__ int corner_targets(const int32_t* __restrict__ hpar, const uint8_t* __restrict__ hnp,
+                                              int32_t id, int32_t (&tg)[4], T& wt) {
+  if (id >= 0) {
+    tg[0] = id;
+    tg[1] = tg[2] = tg[3] = -1;
+    wt = T(1);
+    return 1;
+  }
+  const int32_t h = -id - 1;
+  const int np = hnp[h];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) tg[p] = p < np ? hpar[4 * h + p] : -1;
+  wt = np == 2 ? T(0.5) : T(0.25);
+  return np;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_block_diag_lanes(ElemArgs<T> A, LaneParams<T> K, T* __restrict__ Dout) {
+  constexpr int NC = 1 << D;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((t & ~int64_t(31)) / NC >= A.n_elem) return;
+  const int64_t e = t / NC;
+  const int c = (int)(t & (NC - 1));
+  const int lane = threadIdx.x & 31, gb = lane & ~(NC - 1);
+  const bool valid = e < A.n_elem;
+  const int32_t id = valid ? __ldg(A.conn + e * NC + c) : 0;
+  const int lev = valid ? A.level[e] : 0;
+  const T inv_h = pow2i(lev, T(0));
+  const T w = pow2i(-D * (lev + 1), T(0));
+  const T nb = T(-0.5 * (1.0 - kG));
+  T sh[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sh[k] = ((c >> k) & 1) ? inv_h : -inv_h;
+  const T G2 = pow2i(2 * lev + 2, T(0));
+  const T tau0 = fma(K.cid * G2, G2, K.tau_t);
+  T un[3], vn[3], hn[2];
+  bool have = false;
+  if constexpr (sizeof(T) == 4) {
+    if (A.rec) {
+      load_record(A, id, valid, un, hn, vn);
+      have = true;
+    }
+  }
+  if (!have) {
+    load_node<T, 3>(A, id, valid, A.U, 3, un);
+    load_node<T, 3>(A, id, valid, A.adv, 3, vn);
+    load_node<T, 2>(A, id, valid, A.hs, 2, hn);
+  }
+  T cv[2], gc[2][3], gp[3], v[3], hq[2], tau, R[2], P[2][3];
+  lane_state<T, D>(un, vn, hn, nb, sh, K.kappa, tau0, G2, cv, gc, gp, v, hq, tau, R, P);
+
+  // diagonal pairs: B_ii at this Gauss point for every corner i, then a reduce-scatter
+  // over the group leaves lane c with sum_q B_cc
+  T a[NC][kBlk];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    T Ni, dNi[3];
+    shape_at<T, D>(i, c, inv_h, Ni, dNi);
+    pair_block<T>(Ni, dNi, Ni, dNi, K.kappa, K.e2, tau, cv, gc, gp, v, R, P, a[i]);
+  }
+  T b[(NC + 1) / 2][kBlk];
+  {
+    const bool hi = c & 1;
+#pragma unroll
+    for (int m = 0; m < NC / 2; ++m)
+#pragma unroll
+      for (int x = 0; x < kBlk; ++x) {
+        const T keep = hi ? a[2 * m + 1][x] : a[2 * m][x];
+        const T send = hi ? a[2 * m][x] : a[2 * m + 1][x];
+        b[m][x] = keep + flip(send, 0);
+      }
+  }
+  T r[kBlk];
+  if constexpr (D == 2) {
+    const bool hi = (c >> 1) & 1;
+#pragma unroll
+    for (int x = 0; x < kBlk; ++x) {
+      const T keep = hi ? b[1][x] : b[0][x];
+      const T send = hi ? b[0][x] : b[1][x];
+      r[x] = keep + flip(send, 1);
+    }
+  } else {
+    T b2[2][kBlk];
+    const bool hi1 = (c >> 1) & 1, hi2 = (c >> 2) & 1;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int x = 0; x < kBlk; ++x) {
+        const T keep = hi1 ? b[2 * m + 1][x] : b[2 * m][x];
+        const T send = hi1 ? b[2 * m][x] : b[2 * m + 1][x];
+        b2[m][x] = keep + flip(send, 1);
+      }
+#pragma unroll
+    for (int x = 0; x < kBlk; ++x) {
+      const T keep = hi2 ? b2[1][x] : b2[0][x];
+      const T send = hi2 ? b2[0][x] : b2[1][x];
+      r[x] = keep + flip(send, 2);
+    }
+  }
+  int32_t tg[4] = {-1, -1, -1, -1};
+  T wt = T(0);
+  const int nt = valid ? corner_targets<T>(A.hang_par, A.hang_np, id, tg, wt) : 0;
+  for (int p = 0; p < nt; ++p) {
+    const T ww = w * wt * wt;
+#pragma unroll
+    for (int x = 0; x < kBlk; ++x) atomicAdd(Dout + 9 * (int64_t)tg[p] + blk_slot(x), ww * r[x]);
+  }
+
+  // pairs i != j through hanging corners: lane gb + i owns the pair's scatter
+  if (!__any_sync(kFull, valid && id < 0)) return;
+#pragma unroll 1
+  for (int i = 0; i < NC; ++i) {
+#pragma unroll 1
+    for (int j = 0; j < NC; ++j) {
+      if (i == j) continue;
+      const int32_t id_i = __shfl_sync(kFull, id, gb + i), id_j = __shfl_sync(kFull, id, gb + j);
+      // targets of j at lane gb + i (the owner), compared with its own
+      int32_t tj[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) tj[p] = __shfl_sync(kFull, tg[p], gb + j);
+      const T wj = __shfl_sync(kFull, wt, gb + j);
+      bool share = false;
+      if (c == i && valid && (id_i < 0 || id_j < 0))
+        for (int p = 0; p < nt; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) share |= tg[p] == tj[q];
+      const bool need = __shfl_sync(kFull, share, gb + i);
+      if (!__any_sync(kFull, need)) continue;
+      T Ni, dNi[3], Nj, dNj[3], B[kBlk];
+      shape_at<T, D>(i, c, inv_h, Ni, dNi);
+      shape_at<T, D>(j, c, inv_h, Nj, dNj);
+      pair_block<T>(Ni, dNi, Nj, dNj, K.kappa, K.e2, tau, cv, gc, gp, v, R, P, B);
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int x = 0; x < kBlk; ++x) B[x] += flip(B[x], k);
+      if (c == i && share)
+        for (int p = 0; p < nt; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (tg[p] == tj[q]) {
+              const T ww = w * wt * wj;
+#pragma unroll
+              for (int x = 0; x < kBlk; ++x) atomicAdd(Dout + 9 * (int64_t)tg[p] + blk_slot(x), ww * B[x]);
+            }
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -632,4 +855,30 @@ double jv_from_state_flops(int D) {
   const double tri = D * (D - 1) / 2.0;
   const double vg = 3 * tri + 4 * D, g = vg - 2, tt = 6 * D + 3 * tri + 1;
   return (double)(1 << D) * (2 * vg + g + 101 + 12 + 3 * tt);
+}
+
+template <typename T>
+cudaError_t launch_block_diag_lanes(int dim, const ElemArgs<T>& A, T* Dout, cudaStream_t s) {
+  if (A.n_elem == 0) return cudaSuccess;
+  const int t = 256;
+  const unsigned blocks = (unsigned)(((A.n_elem << dim) + t - 1) / t);
+  const LaneParams<T> K{T(A.P.kappa), T(A.P.tau_t), T(A.P.C_I * dim), T(A.P.eps2x2)};
+  if (dim == 2) k_block_diag_lanes<T, 2><<<blocks, t, 0, s>>>(A, K, Dout);
+  else k_block_diag_lanes<T, 3><<<blocks, t, 0, s>>>(A, K, Dout);
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_block_diag_lanes<double>(int, const ElemArgs<double>&, double*, cudaStream_t);
+template cudaError_t launch_block_diag_lanes<float>(int, const ElemArgs<float>&, float*, cudaStream_t);
+
+// per element of the block-diagonal kernel, hanging pairs not counted: per lane the
+// state at its Gauss point (as in the residual), per corner the shape function (8) and
+// the seven block entries (114), the reduce-scatter (7 adds per stage and entry over
+// 2^d - 1 entries in all) and the scaling
+double block_diag_flops(int D) {
+  const double NC = 1 << D;
+  const double tri = D * (D - 1) / 2.0;
+  const double vg = 3 * tri + 4 * D, g = vg - 2, v = 3 * D;
+  const double state = 2 * vg + 2 * v + g + D * v + 2 * D + 3 + 30;
+  return NC * (state + NC * (8 + 114) + 7 * (NC - 1) + 7);
 }

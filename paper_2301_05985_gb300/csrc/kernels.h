@@ -75,8 +75,11 @@ bool element_kernel_is_lanes();
 cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, cudaStream_t s);
 cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int* err, cudaStream_t s);
 double jv_from_state_flops(int dim);
+// Dout [N][9] += the 3x3 diagonal blocks of the Jacobian (lane-group kernel; Dout zeroed
+// first, Dirichlet and hanging rows left to launch_diag_rows)
 template <typename T>
-cudaError_t launch_block_diag(int dim, const ElemArgs<T>& A, T* Dout, cudaStream_t s);
+cudaError_t launch_block_diag_lanes(int dim, const ElemArgs<T>& A, T* Dout, cudaStream_t s);
+double block_diag_flops(int dim);
 template <typename T>
 cudaError_t launch_row_fixups(const RowArgs& R, const T* in, T* out, int mode, cudaStream_t s);
 template <typename T>

@@ -157,20 +157,22 @@ int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32) {
 int ctx_block_diag(pnp_ctx* c, const double* U, double* D) {
   CK(cudaMemsetAsync(D, 0, sizeof(double) * 9 * c->n_nodes, c->stream));
   {
-    ProfScope ps(c, PNP_PROF_BLOCKDIAG, 136.0 * c->n_nodes + c->conn_bytes());
-    CK(launch_block_diag<double>(c->dim, elem_args<double>(c, U, nullptr, c->hs, c->adv, nullptr), D, c->stream));
+    ProfScope ps(c, PNP_PROF_BLOCKDIAG, 136.0 * c->n_nodes + c->conn_bytes(), block_diag_flops(c->dim) * c->n_elem);
+    CK(launch_block_diag_lanes<double>(c->dim, elem_args<double>(c, U, nullptr, c->hs, c->adv, nullptr), D,
+                                       c->stream));
   }
   CK(launch_diag_rows<double>(c->rows(), D, c->stream));
   return PNP_OK;
 }
 
 // FP32 block diagonal at the FP32 copy of the state (ctx_prepare_f32 first)
-static int ctx_block_diag32(pnp_ctx* c, float* D) {
+int ctx_block_diag32(pnp_ctx* c, float* D) {
   CK(cudaMemsetAsync(D, 0, sizeof(float) * 9 * c->n_nodes, c->stream));
   {
-    ProfScope ps(c, PNP_PROF_BLOCKDIAG, 68.0 * c->n_nodes + c->conn_bytes());
-    CK(launch_block_diag<float>(c->dim, elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr), D,
-                                c->stream));
+    ProfScope ps(c, PNP_PROF_BLOCKDIAG, 68.0 * c->n_nodes + c->conn_bytes(), block_diag_flops(c->dim) * c->n_elem);
+    ElemArgs<float> A = elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr);
+    A.rec = c->rec32;
+    CK(launch_block_diag_lanes<float>(c->dim, A, D, c->stream));
   }
   CK(launch_diag_rows<float>(c->rows(), D, c->stream));
   return PNP_OK;

@@ -109,6 +109,7 @@ SIGNATURES = {
     "pnp_linearize": (C.c_int, [_vp, _vp]),
     "pnp_jv_linearized": (C.c_int, [_vp, _vp, _vp]),
     "pnp_block_diag": (C.c_int, [_vp, _vp, _vp]),
+    "pnp_block_diag_f32": (C.c_int, [_vp, _vp, _vp]),
     "pnp_norm2": (C.c_int, [_vp, _vp, _i64, _P(_d)]),
     "pnp_gmres": (C.c_int, [_vp, _vp, _vp, _vp, _d, C.c_int, _P(pnp_solve_stats)]),
     "pnp_newton_solve": (C.c_int, [_vp, _P(pnp_solve_stats)]),
@@ -322,7 +323,9 @@ class Context:
         return JV
 
     def block_diag(self, U, D):
-        check(lib().pnp_block_diag(self.h, _ptr(U), _ptr(D)))
+        """D [n][9]: FP64 blocks, or FP32 blocks (FP32 arithmetic) when D is float32."""
+        fn = lib().pnp_block_diag_f32 if str(D.dtype) == "torch.float32" else lib().pnp_block_diag
+        check(fn(self.h, _ptr(U), _ptr(D)))
         return D
 
     def norm2(self, x) -> float:

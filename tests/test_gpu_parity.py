@@ -79,6 +79,14 @@ def test_block_diagonal_matches_oracle_jacobian(case):
     D = D.cpu().numpy().reshape(n, 3, 3)
     scale = np.abs(ref).max()
     assert np.abs(D - ref).max() <= TOL64 * scale
+    # FP32 arithmetic (the mixed-precision preconditioner's blocks), entry by entry
+    # against each entry's own scale over the mesh
+    D32 = P.torch.zeros((n, 9), dtype=P.torch.float32, device="cuda")
+    P.ctx.block_diag(P.dev(U), D32)
+    D32 = D32.cpu().numpy().astype(np.float64).reshape(n, 3, 3)
+    ent = np.abs(ref).max(axis=0)
+    ent[ent == 0] = 1.0
+    assert np.all(np.abs(D32 - ref).max(axis=0) <= TOL32 * ent), np.abs(D32 - ref).max(axis=0) / ent
 
 
 def test_jv_is_exact_derivative_of_gpu_residual():
