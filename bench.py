@@ -47,7 +47,7 @@ FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # arithmetic of each kernel class; for ALU classes the binding roofline is chosen per run
 # from the algorithmic flops and bytes (kernel_table)
-BOUNDS = {"residual64": "fp64", "jv64": "fp64", "jv32": "fp32", "blockdiag": "hbm", "ortho_dot": "fp64",
+BOUNDS = {"residual64": "fp64", "jv64": "fp64", "jv32": "fp32", "blockdiag": "fp32", "ortho_dot": "fp64",
           "ortho_update": "fp64", "precond": "hbm", "mlp": "bf16", "inner_ortho": "hbm"}
 
 

@@ -364,189 +364,6 @@ __global__ void k_patch_finalize(PatchArgs<T> A, bool jv) {
     A.out[3 * id + f] = dirichlet_row<T>(A.bc, fm, f, jv, v[f], A.U[3 * id + f], jv ? A.V[3 * id + f] : T(0));
 }
 
-// ------------------------------------------------------------------ block diagonal
-// 3x3 block (test corner I, trial corner J) of the element Jacobian at Gauss point Q,
-// accumulated into B.  With I, J, Q compile-time constants the shape-function values
-// fold to constants times 1/h.
-template <typename T, int D, int Q>
-__device__ __forceinline__ void jac_block(int I, int J, T inv_h, T kappa, T e2, T tau, const T (&cv)[2],
-                                          const T (&gc)[2][3], const T (&gp)[3], const T (&v)[3], const T (&R)[2],
-                                          const T (&P)[2][3], T w, T (&B)[9]) {
-  T Ni = T(1), Nj = T(1), dNi[3] = {T(0), T(0), T(0)}, dNj[3] = {T(0), T(0), T(0)};
-  T fi[3], fj[3];
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const double sg = ((Q >> k) & 1) ? kGauss : -kGauss;
-    const double si = ((I >> k) & 1) ? 1.0 : -1.0, sj = ((J >> k) & 1) ? 1.0 : -1.0;
-    fi[k] = T(0.5 * (1.0 + si * sg));
-    fj[k] = T(0.5 * (1.0 + sj * sg));
-    Ni *= fi[k];
-    Nj *= fj[k];
-  }
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    T a = ((I >> k) & 1) ? inv_h : -inv_h, b = ((J >> k) & 1) ? inv_h : -inv_h;  // (2/h)(s/2)
-#pragma unroll
-    for (int l = 0; l < D; ++l)
-      if (l != k) {
-        a *= fi[l];
-        b *= fj[l];
-      }
-    dNi[k] = a;
-    dNj[k] = b;
-  }
-  T gij = T(0), gip = T(0), vgj = T(0);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    gij += dNi[k] * dNj[k];
-    gip += dNi[k] * gp[k];
-    vgj += v[k] * dNj[k];
-  }
-  T pp_sum = T(0);
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const T z = s == 0 ? T(1) : T(-1);
-    T pgj = T(0), giP = T(0), gcj = T(0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      pgj += P[s][k] * dNj[k];
-      giP += dNi[k] * P[s][k];
-      gcj += gc[s][k] * dNj[k];
-    }
-    const T dRdc = kappa * Nj + pgj;
-    const T dRdp = -z * gcj;
-    B[3 * s + s] += w * (Ni * (kappa * Nj + vgj) + gij + z * Nj * gip + tau * dRdc * giP);
-    B[3 * s + 2] += w * (z * cv[s] * gij + tau * dRdp * giP - tau * R[s] * z * gij);
-    B[6 + s] += w * (-Ni * z * Nj + Ni * z * tau * dRdc);
-    pp_sum += z * tau * dRdp;
-  }
-  B[8] += w * (e2 * gij + Ni * pp_sum);
-}
-
-template <typename T, int D>
-__global__ void __launch_bounds__(128) k_block_diag(ElemArgs<T> A, T* __restrict__ Dout) {
-  constexpr int NC = 1 << D;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= A.n_elem) return;
-  int32_t conn[NC];
-  bool any_h = false;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    conn[c] = __ldg(A.conn + e * NC + c);
-    any_h |= conn[c] < 0;
-  }
-  const int lev = A.level[e];
-  const T h = T(ldexp(1.0, -lev)), inv_h = T(ldexp(1.0, lev));
-  const T Gs = T(2.0 / kGauss) * inv_h, G2 = T(4) * inv_h * inv_h;
-  T w = T(1);
-#pragma unroll
-  for (int k = 0; k < D; ++k) w *= T(0.5) * h;
-  const T kappa = T(A.P.kappa), tau0 = T(A.P.tau_t) + T(A.P.C_I * D) * G2 * G2, e2 = T(A.P.eps2x2);
-  T u[3][NC], va[3][NC], hs[2][NC];
-  gather<T, 3, NC>(A, conn, A.U, 3, u);
-  gather<T, 3, NC>(A, conn, A.adv, 3, va);
-  gather<T, 2, NC>(A, conn, A.hs, 2, hs);
-#pragma unroll
-  for (int f = 0; f < 3; ++f) to_modal<T, D>(u[f]);
-#pragma unroll
-  for (int f = 0; f < D; ++f) to_modal<T, D>(va[f]);
-#pragma unroll
-  for (int f = 0; f < 2; ++f) to_modal<T, D>(hs[f]);
-
-  T Dacc[NC][9];
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Dacc[c][k] = T(0);
-
-  static_for<0, NC>([&](auto qc) {
-    constexpr int Q = decltype(qc)::value;
-    T cv[2], gc[2][3], gp[3], v[3] = {T(0), T(0), T(0)}, hq[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      qp_value_grad<T, D, Q>(u[s], Gs, cv[s], gc[s]);
-      hq[s] = qp_value<T, D, Q>(hs[s]);
-    }
-    qp_grad<T, D, Q>(u[2], Gs, gp);
-    T vv = T(0);
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      v[k] = qp_value<T, D, Q>(va[k]);
-      vv += v[k] * v[k];
-    }
-    const T tau = rsq(tau0 + G2 * vv);
-    T R[2], P[2][3];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const T z = s == 0 ? T(1) : T(-1);
-      T pg = T(0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        P[s][k] = v[k] - z * gp[k];
-        pg += P[s][k] * gc[s][k];
-      }
-      R[s] = kappa * cv[s] + hq[s] + pg;
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) jac_block<T, D, Q>(c, c, inv_h, kappa, e2, tau, cv, gc, gp, v, R, P, w, Dacc[c]);
-    if (any_h) {
-      // cross pairs (i != j) that reach a common node through the hanging constraints
-      for (int i = 0; i < NC; ++i)
-        for (int j = 0; j < NC; ++j) {
-          if (i == j || (conn[i] >= 0 && conn[j] >= 0)) continue;
-          int32_t ti[4], tj[4];
-          T wi[4], wj[4];
-          int ni, nj;
-          auto targets = [&](int32_t id, int32_t (&t)[4], T (&wt)[4], int& nt) {
-            if (id >= 0) {
-              t[0] = id;
-              wt[0] = T(1);
-              nt = 1;
-            } else {
-              const int32_t hidx = -id - 1;
-              nt = A.hang_np[hidx];
-              for (int p = 0; p < nt; ++p) {
-                t[p] = A.hang_par[4 * hidx + p];
-                wt[p] = nt == 2 ? T(0.5) : T(0.25);
-              }
-            }
-          };
-          targets(conn[i], ti, wi, ni);
-          targets(conn[j], tj, wj, nj);
-          T B[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-          bool computed = false;
-          for (int a = 0; a < ni; ++a)
-            for (int b = 0; b < nj; ++b)
-              if (ti[a] == tj[b]) {
-                if (!computed) {
-                  jac_block<T, D, Q>(i, j, inv_h, kappa, e2, tau, cv, gc, gp, v, R, P, w, B);
-                  computed = true;
-                }
-                const T ww = wi[a] * wj[b];
-                for (int k = 0; k < 9; ++k) atomicAdd(Dout + 9 * (int64_t)ti[a] + k, ww * B[k]);
-              }
-        }
-    }
-  });
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int32_t id = conn[c];
-    if (id >= 0) {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) atomicAdd(Dout + 9 * (int64_t)id + k, Dacc[c][k]);
-    } else {
-      const int32_t hidx = -id - 1;
-      const int np = A.hang_np[hidx];
-      const T ww = np == 2 ? T(0.25) : T(0.0625);
-      for (int p = 0; p < np; ++p) {
-        const int32_t pid = A.hang_par[4 * hidx + p];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) atomicAdd(Dout + 9 * (int64_t)pid + k, ww * Dacc[c][k]);
-      }
-    }
-  }
-}
-
 // ------------------------------------------------------------------ row fix-ups
 // mode 0: F = U - g on Dirichlet rows;  mode 1: out = V on Dirichlet rows.
 template <typename T>
@@ -673,17 +490,6 @@ cudaError_t launch_patch(int dim, bool jv, const PatchArgs<T>& A, cudaStream_t s
 }
 template cudaError_t launch_patch<double>(int, bool, const PatchArgs<double>&, cudaStream_t);
 template cudaError_t launch_patch<float>(int, bool, const PatchArgs<float>&, cudaStream_t);
-
-template <typename T>
-cudaError_t launch_block_diag(int dim, const ElemArgs<T>& A, T* Dout, cudaStream_t s) {
-  if (A.n_elem == 0) return cudaSuccess;
-  const int t = 128;
-  if (dim == 2) { k_block_diag<T, 2><<<nblk(A.n_elem, t), t, 0, s>>>(A, Dout); note_launch(); }
-  else { k_block_diag<T, 3><<<nblk(A.n_elem, t), t, 0, s>>>(A, Dout); note_launch(); }
-  return cudaGetLastError();
-}
-template cudaError_t launch_block_diag<double>(int, const ElemArgs<double>&, double*, cudaStream_t);
-template cudaError_t launch_block_diag<float>(int, const ElemArgs<float>&, float*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_row_fixups(const RowArgs& R, const T* in, T* out, int mode, cudaStream_t s) {
