@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "mlp_tc.h"
 
 #define CK(call)                                 \
   do {                                           \
@@ -587,6 +588,35 @@ int mlp_forward_rows(pnp_ctx* c, Mlp* m, int64_t rows) {
   return PNP_OK;
 }
 
+// inference of `rows` standardised rows in m->X on the tensor cores (tcgen05, all layers
+// in one kernel, no saved activations); output in m->out [rows][8]
+int mlp_infer_rows(pnp_ctx* c, Mlp* m, int64_t rows) {
+  MlpTcArgs a;
+  a.rows = rows;
+  a.X = m->X;
+  a.W1 = m->W1;
+  a.W2 = m->W2;
+  a.W3 = m->W3;
+  a.W4 = m->W4;
+  a.b1 = m->b1;
+  a.b2 = m->b2;
+  a.b3 = m->b3;
+  a.b4 = m->b4;
+  a.out = m->out;
+  a.err = c->dflag + 2;
+  CK(launch_mlp_infer_tc(a, c->stream));
+  return PNP_OK;
+}
+
+// PNP_ERR_DEVICE_FLAG once a wait of the tensor-core inference has given up (latched)
+int mlp_check_infer(pnp_ctx* c) {
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->dflag + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (flag) PNP_FAIL(PNP_ERR_DEVICE_FLAG, "network inference: the tensor core did not signal completion");
+  return PNP_OK;
+}
+
 // loss and packed gradient for `rows` rows (X, Y in the workspace); loss on the host
 int mlp_backward_rows(pnp_ctx* c, Mlp* m, int64_t rows, double* loss) {
   cudaStream_t s = c->stream;
@@ -846,13 +876,12 @@ int pnp_mlp_forward(pnp_ctx* c, const float* X, int64_t B, float* Y) {
     const int64_t rows = std::min<int64_t>(kMaxRows, B - r0);
     k_f32_to_bf16_rows<<<nblk(rows * K0P, 256), 256, 0, c->stream>>>(rows, K0, K0, K0P, X + r0 * K0, m->X);
     note_launch();
-    RC(mlp_forward_rows(c, m, rows));
+    RC(mlp_infer_rows(c, m, rows));
     k_f32_rows<<<nblk(rows * NO, 256), 256, 0, c->stream>>>(rows, NO, NOP, NO, m->out, Y + r0 * NO);
     note_launch();
   }
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->stream));
-  return PNP_OK;
+  return mlp_check_infer(c);
 }
 
 int pnp_mlp_loss_grad(pnp_ctx* c, const float* X, const float* Yt, int64_t B, float* grad, double* loss) {
@@ -1111,7 +1140,7 @@ int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st) {
       a.X = m->X;
       k_features<false><<<nblk(rows * NPT, 256), 256, 0, s>>>(a);
       note_launch();
-      RC(mlp_forward_rows(c, m, rows));
+      RC(mlp_infer_rows(c, m, rows));
       k_apply_correction<<<nblk(rows, 256), 256, 0, s>>>(rows, m->free_nodes + r0, m->out, m->out_mu[0], m->out_mu[1],
                                                          m->out_mu[2], m->out_sd[0], m->out_sd[1], m->out_sd[2], c->Ut,
                                                          c->U);
@@ -1119,6 +1148,7 @@ int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st) {
     }
   }
   CK(cudaGetLastError());
+  RC(mlp_check_infer(c));
   CK(launch_make_consistent(c->rows(), c->U, s));
   // judge with the residual
   RC(ctx_prepare_history(c));
