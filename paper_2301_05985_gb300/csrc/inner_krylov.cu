@@ -206,8 +206,17 @@ __device__ __forceinline__ InnerScalars inner_scalars(double* base, int d) {
 
 // sum of the norm partials of k_multi_axpy_norm_f32 in a fixed order (one block of 64)
 __device__ __forceinline__ double sum_parts64(const double* __restrict__ part, int nparts, double* sh) {
-  double t = 0.0;
-  for (int b = threadIdx.x; b < nparts; b += 64) t += part[b];
+  // four independent running sums per thread keep four loads in flight (fixed order)
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+  int b = threadIdx.x;
+  for (; b + 192 < nparts; b += 256) {
+    t0 += part[b];
+    t1 += part[b + 64];
+    t2 += part[b + 128];
+    t3 += part[b + 192];
+  }
+  for (; b < nparts; b += 64) t0 += part[b];
+  const double t = (t0 + t1) + (t2 + t3);
   sh[threadIdx.x] = t;
   __syncthreads();
   for (int o = 32; o > 0; o >>= 1) {
@@ -242,9 +251,14 @@ __global__ void __launch_bounds__(kMaxInner) k_inner_col(int j, int d, const dou
   static_assert(kMaxInner == 64, "the norm partials are summed by one block of 64");
   __shared__ double h[kMaxInner + 1];
   __shared__ double sh[64];
+  __shared__ double cs[kMaxInner], sn[kMaxInner];
   const InnerScalars S = inner_scalars(sc, d);
   const int i = threadIdx.x;
   if (i <= j) h[i] = sv[i] > 0 ? dd[i] / sv[i] : 0.0;
+  if (i < j) {
+    cs[i] = S.cs[i];
+    sn[i] = S.sn[i];
+  }
   const double nrm2 = sum_parts64(part, nparts, sh);
   if (i == 0) {
     const double s = sqrt(nrm2);
@@ -256,8 +270,8 @@ __global__ void __launch_bounds__(kMaxInner) k_inner_col(int j, int d, const dou
   __syncthreads();
   if (i != 0) return;
   for (int l = 0; l < j; ++l) {
-    const double t = S.cs[l] * h[l] + S.sn[l] * h[l + 1];
-    h[l + 1] = -S.sn[l] * h[l] + S.cs[l] * h[l + 1];
+    const double t = cs[l] * h[l] + sn[l] * h[l + 1];
+    h[l + 1] = -sn[l] * h[l] + cs[l] * h[l + 1];
     h[l] = t;
   }
   const double rr = hypot(h[j], h[j + 1]);
@@ -276,17 +290,25 @@ __global__ void __launch_bounds__(kMaxInner) k_inner_col(int j, int d, const dou
 }
 
 // y = R^-1 g over the columns before the first breakdown; coef_i = y_i / s_i, so that
-// sum_i y_i q_i = sum_i coef_i u_i.  One thread.
-__global__ void k_inner_lsq(int d, const double* __restrict__ sv, double* sc, double* __restrict__ coef) {
+// sum_i y_i q_i = sum_i coef_i u_i.  The block stages R, g and s in shared memory, then
+// one thread back-substitutes.
+__global__ void __launch_bounds__(kMaxInner) k_inner_lsq(int d, const double* __restrict__ sv, double* sc,
+                                                         double* __restrict__ coef) {
+  __shared__ double R[kMaxInner * kMaxInner], g[kMaxInner], y[kMaxInner];
   const InnerScalars S = inner_scalars(sc, d);
   const int k = (int)S.kv[0];
-  for (int i = 0; i < d; ++i) coef[i] = 0.0;
-  for (int i = k - 1; i >= 0; --i) {
-    double t = S.g[i];
-    for (int l = i + 1; l < k; ++l) t -= S.R[i * d + l] * coef[l];
-    coef[i] = t / S.R[i * d + i];
+  for (int t = threadIdx.x; t < k * d; t += blockDim.x) R[t] = S.R[t];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) g[t] = S.g[t];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int l = i + 1; l < k; ++l) t -= R[i * d + l] * y[l];
+      y[i] = t / R[i * d + i];
+    }
   }
-  for (int i = 0; i < k; ++i) coef[i] /= sv[i];
+  __syncthreads();
+  for (int t = threadIdx.x; t < d; t += blockDim.x) coef[t] = t < k ? y[t] / sv[t] : 0.0;
 }
 
 // out = sum_i coef_i U_i (FP32 vectors, coefficients on the device)
@@ -406,7 +428,7 @@ cudaError_t launch_inner_col(int j, int d, const double* dd, const double* part,
 }
 
 cudaError_t launch_inner_lsq(int d, const double* sv, double* sc, double* coef, cudaStream_t s) {
-  k_inner_lsq<<<1, 1, 0, s>>>(d, sv, sc, coef);
+  k_inner_lsq<<<1, kMaxInner, 0, s>>>(d, sv, sc, coef);
   note_launch();
   return cudaGetLastError();
 }

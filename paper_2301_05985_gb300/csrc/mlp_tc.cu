@@ -7,7 +7,8 @@
 // shared memory (K-major, no swizzle: 8x8 core matrices of 128 contiguous bytes); per
 // tile the input rows are loaded once, and per layer one thread issues K/16 MMAs of
 // 128 x N x 16 (tcgen05.mma kind::f16, BF16 x BF16 -> FP32) and commits them to an
-// mbarrier that the epilogue warps wait on (bounded).
+// mbarrier that the epilogue warps wait on (bounded).  Sixteen warps: warp w reads TMEM
+// lanes 32 (w mod 4) .. + 31 (the rows it may access) and a quarter of the columns.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -25,7 +26,7 @@ constexpr int kHid = 128;
 constexpr int kN4 = 16;      // output layer padded to the smallest N of an M = 128 MMA
 constexpr int kNo = 3;       // outputs written
 constexpr int kLdOut = 8;    // row stride of the output
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kTmemCols = 128;
 constexpr int kWaitPolls = 1 << 22;
 
@@ -143,12 +144,12 @@ __device__ void stage_weight(uint8_t* dst, const bf16* __restrict__ W, int K, in
   }
 }
 
-// bias + GELU of 64 accumulator columns of this thread's row, written as BF16 into the
+// bias + GELU of 32 accumulator columns of this thread's row, written as BF16 into the
 // next layer's operand (K = 128)
 __device__ __forceinline__ void epilogue_gelu(uint32_t tmem_row, int col0, int row, const float* __restrict__ bias,
                                               uint8_t* dst) {
 #pragma unroll 1
-  for (int c = col0; c < col0 + 64; c += 16) {
+  for (int c = col0; c < col0 + 32; c += 16) {
     float v[16];
     tmem_ld16(tmem_row + (uint32_t)c, v);
     uint32_t p[8];
@@ -190,8 +191,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_infer_tc(MlpTcArgs a) {
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  // this warp's TMEM lanes (rows) and accumulator column half
-  const int quarter = warp & 3, half = warp >> 2;
+  // this warp's TMEM lanes (rows) and accumulator column quarter
+  const int quarter = warp & 3, part = warp >> 2;
   const int row = quarter * 32 + lane;
   const uint32_t tmem_row = tmem + ((uint32_t)(quarter * 32) << 16);
   const uint32_t sA = smem_u32(sm + oA), sH = smem_u32(sm + oH);
@@ -236,8 +237,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_infer_tc(MlpTcArgs a) {
       if (layer < 3) {
         const float* bias = layer == 0 ? a.b1 : layer == 1 ? a.b2 : a.b3;
         uint8_t* dst = sm + ((layer == 1) ? oA : oH);
-        epilogue_gelu(tmem_row, half * 64, row, bias, dst);
-      } else if (half == 0) {
+        epilogue_gelu(tmem_row, part * 32, row, bias, dst);
+      } else if (part == 0) {
         float v[4];
         tmem_ld4(tmem_row, v);
         if (r0 + row < a.rows) {
