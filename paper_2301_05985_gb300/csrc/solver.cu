@@ -646,16 +646,21 @@ int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st);  // mlp.cu
 // relative to ||F(ref)|| (NULL: to the start's own residual); on success the history
 // shifts (U^{k-1} <- U^k <- U).  A failed solve with split depth left is redone as two
 // BDF1 half steps, each started from (and measured against) the previous state.
-static int advance(pnp_ctx* c, double dt, bool bdf2, int depth, const double* ref, pnp_solve_stats* tot) {
-  const int64_t n = c->n3();
-  cudaStream_t s = c->stream;
-  pnp_params& p = c->prm;
-  p.dt = dt;
+// BDF2 (3/2, -2, 1/2) or BDF1 (1, -1, 0) coefficients of the time derivative (Def. 1)
+static void set_bdf(pnp_params& p, bool bdf2) {
   if (bdf2) {
     p.beta0 = 1.5; p.beta1 = -2.0; p.beta2 = 0.5;
   } else {
     p.beta0 = 1.0; p.beta1 = -1.0; p.beta2 = 0.0;
   }
+}
+
+static int advance(pnp_ctx* c, double dt, bool bdf2, int depth, const double* ref, pnp_solve_stats* tot) {
+  const int64_t n = c->n3();
+  cudaStream_t s = c->stream;
+  pnp_params& p = c->prm;
+  p.dt = dt;
+  set_bdf(p, bdf2);
   pnp_solve_stats one;
   std::memset(&one, 0, sizeof(one));
   const int rc = ctx_newton(c, &one, ref);
@@ -699,6 +704,8 @@ int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st) {
   if (c->history_split) start = PNP_START_PREVIOUS;  // extrapolation assumes equal spacing
   double r_extra = 0, r_learn = 0;
   if (start == PNP_START_LEARNED) {
+    // the judge's residuals use this step's BDF formula
+    set_bdf(p, bdf2);
     pnp_solve_stats tmp;
     std::memset(&tmp, 0, sizeof(tmp));
     const int lrc = pnp_learned_start(c, &tmp);
