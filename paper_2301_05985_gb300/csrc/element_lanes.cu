@@ -392,8 +392,10 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_lane_state(ElemArgs<float> 
 // cp.async.bulk) of the four state rows and the tile's connectivity into a stage of
 // shared memory, completing on the stage's mbarrier.  kStages tiles are in flight per
 // block, so the state's HBM stream does not wait on the per-lane arithmetic and
-// atomics of the tile before.
+// atomics of the tile before.  Two stages with five blocks per SM measured fastest: three
+// (four blocks per SM) and four (three) were 6% and 16% slower per launch.
 constexpr int kStages = 2;
+constexpr size_t jv_stage_bytes(int S) { return (size_t)S * (4 * kLaneThreads * 16 + kLaneThreads * 4 + 8); }
 constexpr int kWaitPolls = 1 << 22;  // try_wait polls before a wait gives up (about a second)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -427,13 +429,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-template <int D>
+template <int D, int S>
 __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<float> A, LaneParams<float> K,
                                                                  const float4* __restrict__ qp, int* err) {
   constexpr int NC = 1 << D;
-  __shared__ __align__(128) float4 sq[kStages][4][kLaneThreads];
-  __shared__ __align__(16) int32_t sconn[kStages][kLaneThreads];
-  __shared__ __align__(8) uint64_t bar[kStages];
+  extern __shared__ __align__(128) uint8_t jv_smem[];
+  // S stages of {four state rows, connectivity} and S mbarriers (jv_stage_bytes(S))
+  auto sq = reinterpret_cast<float4(*)[4][kLaneThreads]>(jv_smem);
+  auto sconn = reinterpret_cast<int32_t(*)[kLaneThreads]>(jv_smem + S * 4 * kLaneThreads * sizeof(float4));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(jv_smem + S * (4 * kLaneThreads * sizeof(float4) + kLaneThreads * 4));
   const int tid = threadIdx.x;
   const int64_t L = A.n_elem * NC;
   const int64_t n_tiles = (L + kLaneThreads - 1) / kLaneThreads;
@@ -450,14 +454,14 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
   };
   if (tid == 0) {
 #pragma unroll
-    for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+    for (int st = 0; st < S; ++st) mbar_init(&bar[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   uint32_t pending = 0;  // thread 0: stages with a copy in flight
   if (tid == 0) {
 #pragma unroll
-    for (int st = 0; st < kStages; ++st)
+    for (int st = 0; st < S; ++st)
       if (blockIdx.x + st * G < n_tiles) {
         issue(blockIdx.x + st * G, st);
         pending |= 1u << st;
@@ -469,16 +473,16 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
   for (int k = 0;; ++k) {
     const int64_t tl = blockIdx.x + (int64_t)k * G;
     if (tl >= n_tiles) break;
-    const int st = k % kStages;
-    const uint32_t parity = (uint32_t)(k / kStages) & 1u;
+    const int st = k % S;
+    const uint32_t parity = (uint32_t)(k / S) & 1u;
     const bool ok = mbar_wait(&bar[st], parity);
     if (__syncthreads_or(!ok)) {
       // a copy did not complete: flag it, let the copies still in flight land, return
       if (tid == 0) {
         atomicOr(err, 1);
-        for (int j = 0; j < kStages; ++j) {
-          const int kk = k + ((j - st + kStages) % kStages);
-          if (pending >> j & 1u) mbar_wait(&bar[j], (uint32_t)(kk / kStages) & 1u);
+        for (int j = 0; j < S; ++j) {
+          const int kk = k + ((j - st + S) % S);
+          if (pending >> j & 1u) mbar_wait(&bar[j], (uint32_t)(kk / S) & 1u);
         }
       }
       return;
@@ -494,12 +498,12 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
       q3 = sq[st][3][tid];
       id = sconn[st][tid];
     }
-    __syncthreads();  // stage st is read: refill it with the tile kStages ahead
+    __syncthreads();  // stage st is read: refill it with the tile S ahead
     if (tid == 0) {
       pending &= ~(1u << st);
-      if (tl + kStages * G < n_tiles) {
+      if (tl + S * G < n_tiles) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(tl + kStages * G, st);
+        issue(tl + S * G, st);
         pending |= 1u << st;
       }
     }
@@ -823,19 +827,24 @@ cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int* err, cudaStream_t s) {
-  if (A.n_elem == 0) return cudaSuccess;
-  const LaneParams<float> K{float(A.P.kappa), float(A.P.tau_t), float(A.P.C_I * dim), float(A.P.eps2x2)};
+template <int S>
+static cudaError_t launch_jv_stages(int dim, const ElemArgs<float>& A, const LaneParams<float>& K, const float4* qp,
+                                    int* err, cudaStream_t s) {
   // persistent grid: the resident blocks of every SM, no more than there are tiles
   static int per_sm[2] = {0, 0}, n_sm = 0;
+  const size_t smem = jv_stage_bytes(S);
   if (n_sm == 0) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_jv_from_state<2>, kLaneThreads, 0);
+      e = cudaFuncSetAttribute(k_jv_from_state<2, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_jv_from_state<3>, kLaneThreads, 0);
+      e = cudaFuncSetAttribute(k_jv_from_state<3, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_jv_from_state<2, S>, kLaneThreads, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_jv_from_state<3, S>, kLaneThreads, smem);
     if (e != cudaSuccess) {
       n_sm = 0;
       return e;
@@ -843,8 +852,16 @@ cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4
   }
   const int64_t tiles = ((A.n_elem << dim) + kLaneThreads - 1) / kLaneThreads;
   const unsigned blocks = (unsigned)std::min<int64_t>(tiles, (int64_t)n_sm * std::max(1, per_sm[dim - 2]));
-  if (dim == 2) k_jv_from_state<2><<<blocks, kLaneThreads, 0, s>>>(A, K, qp, err);
-  else k_jv_from_state<3><<<blocks, kLaneThreads, 0, s>>>(A, K, qp, err);
+  if (dim == 2) k_jv_from_state<2, S><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err);
+  else k_jv_from_state<3, S><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err);
+  return cudaSuccess;
+}
+
+cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int* err, cudaStream_t s) {
+  if (A.n_elem == 0) return cudaSuccess;
+  const LaneParams<float> K{float(A.P.kappa), float(A.P.tau_t), float(A.P.C_I * dim), float(A.P.eps2x2)};
+  const cudaError_t e = launch_jv_stages<kStages>(dim, A, K, qp, err, s);
+  if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();
 }

@@ -405,7 +405,9 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       if (flex) {
         float* zj = c->Zb + (size_t)j * n;
         RC(inner_gmres32(c, uj, zj, from_state));
-        RC(ctx_jv32(c, zj, c->JV32));
+        // the outer J V applies the same linearisation as the inner one
+        if (from_state) RC(ctx_jv32_linearized(c, zj, c->JV32));
+        else RC(ctx_jv32(c, zj, c->JV32));
         ProfScope ps(c, PNP_PROF_PRECOND, 20.0 * (double)n);
         CK(launch_to_f64_scaled(n, c->JV32, 1.0 / sv[j], w, s));
       } else if (prec == PNP_F64) {
