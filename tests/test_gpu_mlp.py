@@ -109,6 +109,37 @@ def test_forward_and_gradients_match_oracle():
         assert np.linalg.norm(gbg[l] - gb[l]) / np.linalg.norm(gb[l]) < 2e-2, l
 
 
+def test_inference_spans_many_tiles_per_cta():
+    """The tensor-core inference is persistent over 128-row tiles: 38,989 rows are 305
+    tiles, two or three per CTA on a 152-SM GPU, the last one ragged (77 rows).  Against
+    the oracle with BF16-rounded weights, inputs and hidden activations (what the kernel
+    feeds its next layer), and against the unrounded oracle as in the small case."""
+    oc = W.uniform_octants(3, 2)
+    pnp, torch, mesh, ctx = _ctx(oc)
+    rng = np.random.default_rng(11)
+    Ws, bs = MO.init_params(3)
+    bs = [b + rng.normal(0, 0.05, b.shape) for b in bs]
+    p = pack(Ws, bs)
+    ctx.mlp_set_weights(p)
+    B = 2 * 152 * 128 + 77
+    X = rng.normal(size=(B, 216)).astype(np.float32)
+    out = torch.zeros((B, 3), dtype=torch.float32, device="cuda")
+    ctx.mlp_forward(torch.from_numpy(X).cuda(), out)
+    out = out.cpu().numpy().astype(np.float64)
+    Wr, br = unpack(p)
+    Wr = [MO.bf16_round(w) for w in Wr]
+    a = MO.bf16_round(X)
+    for l in range(4):
+        z = a @ Wr[l] + br[l]
+        a = MO.bf16_round(MO.gelu(z)) if l < 3 else z
+    assert np.all(np.isfinite(out))
+    scale = np.abs(a).max()
+    assert np.abs(out - a).max() <= 1e-2 * scale, np.abs(out - a).max() / scale
+    assert np.linalg.norm(out - a) / np.linalg.norm(a) < 2e-3
+    ref, _, _ = MO.forward(Wr, br, MO.bf16_round(X))
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-2
+
+
 def test_weights_round_trip_and_normalization():
     oc = W.uniform_octants(3, 2)
     pnp, torch, mesh, ctx = _ctx(oc)
