@@ -258,6 +258,13 @@ def load_traffic(small: bool):
     return out
 
 
+def residual_kind():
+    """The residual runs in double-float arithmetic on the FP32 pipe unless
+    PNP_RESIDUAL_ARITH=f64 (or the one-thread-per-element kernel) selects FP64."""
+    f64 = os.environ.get("PNP_RESIDUAL_ARITH") == "f64" or os.environ.get("PNP_ELEMENT_KERNEL") == "thread"
+    return "fp64" if f64 else "fp32"
+
+
 def kernel_table(prof, peaks, total_ms):
     """Per class: time share, algorithmic GB/s and TFLOP/s, and the fraction of the
     roofline that bounds it."""
@@ -268,7 +275,7 @@ def kernel_table(prof, peaks, total_ms):
         t = d["ms"] * 1e-3
         gbs = d["alg_bytes"] / t / 1e9
         tfl = d["alg_flops"] / t / 1e12
-        kind = BOUNDS[name]
+        kind = residual_kind() if name == "residual64" else BOUNDS[name]
         if kind == "hbm":
             bound, unit, ach, peak = "hbm", "GB/s", gbs, peaks["hbm_gbs"]
             src = "measured" if not peaks.get("fallback") else "fallback"

@@ -433,6 +433,14 @@ static bool per_thread_elements() {
 
 bool element_kernel_is_lanes() { return !per_thread_elements(); }
 
+bool residual_double_float() {
+  static const bool v = [] {
+    const char* e = getenv("PNP_RESIDUAL_ARITH");
+    return !(e && strcmp(e, "f64") == 0);
+  }();
+  return v && !per_thread_elements();
+}
+
 double element_kernel_flops(int D, bool jv) {
   const double NC = 1 << D;
   if (per_thread_elements()) {

@@ -17,7 +17,9 @@
 // transpose sends s_b (x_0 + x_1) / h to node b (s_0 = -1, s_1 = +1).
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
+#include "df32.cuh"
 #include "kernels.h"
 
 namespace {
@@ -28,6 +30,9 @@ constexpr unsigned kFull = 0xffffffffu;
 template <typename T>
 __device__ __forceinline__ T flip(T x, int k) {
   return __shfl_xor_sync(kFull, x, 1 << k);
+}
+__device__ __forceinline__ df flip(df x, int k) {
+  return df(__shfl_xor_sync(kFull, x.hi, 1 << k), __shfl_xor_sync(kFull, x.lo, 1 << k));
 }
 
 // value and gradient at this lane's Gauss point from this lane's nodal value x
@@ -101,6 +106,23 @@ __device__ __forceinline__ float pow2i(int e, float) { return __int_as_float((12
 __device__ __forceinline__ double pow2i(int e, double) {
   return __longlong_as_double((long long)(1023 + e) << 52);
 }
+__device__ __forceinline__ df pow2i(int e, df) { return df(pow2i(e, 0.0f), 0.0f); }
+
+// loaded value in the arithmetic type, and back to the storage type
+template <typename C, typename T>
+__device__ __forceinline__ C to_compute(T x) { return C(x); }
+template <>
+__device__ __forceinline__ df to_compute<df, double>(double x) { return df_split(x); }
+template <typename T>
+__device__ __forceinline__ T to_storage(T x) { return x; }
+template <typename T>
+__device__ __forceinline__ T to_storage(df x) { return df_to_double(x); }
+
+// blocks per SM the lane kernel's register cap is set for
+template <typename T, typename C>
+constexpr int lane_min_blocks() {
+  return sizeof(T) == 4 ? 5 : (std::is_same<C, df>::value ? 2 : 3);
+}
 
 // physical parameters in the kernel's arithmetic type
 template <typename T>
@@ -129,6 +151,28 @@ __device__ __forceinline__ void load_node(const ElemArgs<T>& A, int32_t id, bool
       const int32_t pid = A.hang_par[4 * h + p];
 #pragma unroll
       for (int f = 0; f < NF; ++f) dst[f] += wgt * __ldg(src + (int64_t)stride * pid + f);
+    }
+  }
+}
+
+// the same in arithmetic type C from storage type T
+template <typename T, typename C, int NF>
+__device__ __forceinline__ void load_node_c(const ElemArgs<T>& A, int32_t id, bool valid, const T* __restrict__ src,
+                                            int stride, C (&dst)[NF]) {
+#pragma unroll
+  for (int f = 0; f < NF; ++f) dst[f] = C(0);
+  if (!valid) return;
+  if (id >= 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dst[f] = to_compute<C>(__ldg(src + (int64_t)stride * id + f));
+  } else {
+    const int32_t h = -id - 1;
+    const int np = A.hang_np[h];
+    const C wgt = np == 2 ? C(0.5) : C(0.25);
+    for (int p = 0; p < np; ++p) {
+      const int32_t pid = A.hang_par[4 * h + p];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) dst[f] += wgt * to_compute<C>(__ldg(src + (int64_t)stride * pid + f));
     }
   }
 }
@@ -180,8 +224,7 @@ __device__ __forceinline__ void lane_state(const T (&un)[3], const T (&vn)[3], c
     v[k] = interp_v<T, D>(vn[k], nb);
     vv = fma(v[k], v[k], vv);
   }
-  if constexpr (sizeof(T) == 4) tau = rsqrtf(tau0 + G2 * vv);
-  else tau = T(1) / sqrt(tau0 + G2 * vv);
+  tau = inv_sqrt(tau0 + G2 * vv);
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const T z = s == 0 ? T(1) : T(-1);
@@ -229,8 +272,9 @@ __device__ __forceinline__ void scatter4(const ElemArgs<T>& A, int32_t id, const
   }
 }
 
-template <typename T, int D, bool JV>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(ElemArgs<T> A, LaneParams<T> K) {
+// T: storage type of the vectors; C: arithmetic type (T, or double-float for FP64 data)
+template <typename T, typename C, int D, bool JV>
+__global__ void __launch_bounds__(256, lane_min_blocks<T, C>()) k_element_lanes(ElemArgs<T> A, LaneParams<C> K) {
   constexpr int NC = 1 << D;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // warps whose first element is past the end leave together (shuffles need the warp)
@@ -241,47 +285,47 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
   const int32_t id = valid ? __ldg(A.conn + e * NC + c) : 0;
   const int lev = valid ? A.level[e] : 0;
 
-  const T inv_h = pow2i(lev, T(0));
-  const T w = pow2i(-D * (lev + 1), T(0));  // (h/2)^D
-  const T nb = T(-0.5 * (1.0 - kG));
-  T sh[3];
+  const C inv_h = pow2i(lev, C(0));
+  const C w = pow2i(-D * (lev + 1), C(0));  // (h/2)^D
+  const C nb = C(-0.5 * (1.0 - kG));
+  C sh[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) sh[k] = ((c >> k) & 1) ? inv_h : -inv_h;
-  const T G2 = pow2i(2 * lev + 2, T(0));  // (2/h)^2
-  const T kappa = K.kappa;
-  const T tau0 = fma(K.cid * G2, G2, K.tau_t);
-  const T e2 = K.e2;
+  const C G2 = pow2i(2 * lev + 2, C(0));  // (2/h)^2
+  const C kappa = K.kappa;
+  const C tau0 = fma(K.cid * G2, G2, K.tau_t);
+  const C e2 = K.e2;
 
-  T un[3], vn[3], hn[2];
+  C un[3], vn[3], hn[2];
   if constexpr (sizeof(T) == 4) {
     if (A.rec) {
       load_record(A, id, valid, un, hn, vn);
     } else {
-      load_node<T, 3>(A, id, valid, A.U, 3, un);
-      load_node<T, 3>(A, id, valid, A.adv, 3, vn);
-      load_node<T, 2>(A, id, valid, A.hs, 2, hn);
+      load_node_c<T, C, 3>(A, id, valid, A.U, 3, un);
+      load_node_c<T, C, 3>(A, id, valid, A.adv, 3, vn);
+      load_node_c<T, C, 2>(A, id, valid, A.hs, 2, hn);
     }
   } else {
-    load_node<T, 3>(A, id, valid, A.U, 3, un);
-    load_node<T, 3>(A, id, valid, A.adv, 3, vn);
-    load_node<T, 2>(A, id, valid, A.hs, 2, hn);
+    load_node_c<T, C, 3>(A, id, valid, A.U, 3, un);
+    load_node_c<T, C, 3>(A, id, valid, A.adv, 3, vn);
+    load_node_c<T, C, 2>(A, id, valid, A.hs, 2, hn);
   }
 
   // state at this lane's Gauss point
-  T cv[2], gc[2][3], gp[3], v[3], hq[2], tau, R[2], P[2][3];
-  lane_state<T, D>(un, vn, hn, nb, sh, kappa, tau0, G2, cv, gc, gp, v, hq, tau, R, P);
+  C cv[2], gc[2][3], gp[3], v[3], hq[2], tau, R[2], P[2][3];
+  lane_state<C, D>(un, vn, hn, nb, sh, kappa, tau0, G2, cv, gc, gp, v, hq, tau, R, P);
 
-  T S[3], Phi[3][3];
+  C S[3], Phi[3][3];
   if constexpr (!JV) {
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const T z = s == 0 ? T(1) : T(-1);
-      T vg = T(0);
+      const C z = s == 0 ? C(1) : C(-1);
+      C vg = C(0);
 #pragma unroll
       for (int k = 0; k < 3; ++k) vg = fma(v[k], gc[s][k], vg);
       S[s] = fma(kappa, cv[s], hq[s] + vg);
-      const T tR = tau * R[s];
-      const T zc = z * cv[s];
+      const C tR = tau * R[s];
+      const C zc = z * cv[s];
 #pragma unroll
       for (int k = 0; k < 3; ++k) Phi[s][k] = fma(tR, P[s][k], fma(zc, gp[k], gc[s][k]));
     }
@@ -289,21 +333,21 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
 #pragma unroll
     for (int k = 0; k < 3; ++k) Phi[2][k] = e2 * gp[k];
   } else {
-    T dn[3];
+    C dn[3];
     if constexpr (sizeof(T) == 4) {
       if (A.V4) load_dir4(A, id, valid, dn);
-      else load_node<T, 3>(A, id, valid, A.V, 3, dn);
+      else load_node_c<T, C, 3>(A, id, valid, A.V, 3, dn);
     } else {
-      load_node<T, 3>(A, id, valid, A.V, 3, dn);
+      load_node_c<T, C, 3>(A, id, valid, A.V, 3, dn);
     }
-    T dcv[2], dgc[2][3], dgp[3], dR[2];
+    C dcv[2], dgc[2][3], dgp[3], dR[2];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) interp_vg<T, D>(dn[s], nb, sh, dcv[s], dgc[s]);
-    interp_g<T, D>(dn[2], nb, sh, dgp);
+    for (int s = 0; s < 2; ++s) interp_vg<C, D>(dn[s], nb, sh, dcv[s], dgc[s]);
+    interp_g<C, D>(dn[2], nb, sh, dgp);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const T z = s == 0 ? T(1) : T(-1);
-      T vg = T(0), pg = T(0), gcd = T(0);
+      const C z = s == 0 ? C(1) : C(-1);
+      C vg = C(0), pg = C(0), gcd = C(0);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         vg = fma(v[k], dgc[s][k], vg);
@@ -312,9 +356,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
       }
       dR[s] = fma(kappa, dcv[s], pg - z * gcd);
       S[s] = fma(kappa, dcv[s], vg);
-      const T tdR = tau * dR[s];
-      const T zdc = z * dcv[s];
-      const T zc_tR = z * (cv[s] - tau * R[s]);
+      const C tdR = tau * dR[s];
+      const C zdc = z * dcv[s];
+      const C zc_tR = z * (cv[s] - tau * R[s]);
 #pragma unroll
       for (int k = 0; k < 3; ++k) Phi[s][k] = fma(tdR, P[s][k], fma(zc_tR, dgp[k], fma(zdc, gp[k], dgc[s][k])));
     }
@@ -323,9 +367,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
     for (int k = 0; k < 3; ++k) Phi[2][k] = e2 * dgp[k];
   }
 
-  T r[3];
+  C r[3];
 #pragma unroll
-  for (int f = 0; f < 3; ++f) r[f] = w * test_t<T, D>(S[f], Phi[f], nb, sh);
+  for (int f = 0; f < 3; ++f) r[f] = w * test_t<C, D>(S[f], Phi[f], nb, sh);
   if (!valid) return;
   if constexpr (sizeof(T) == 4) {
     if (A.out4) {
@@ -333,9 +377,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
       return;
     }
   }
+  T ro[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) ro[f] = to_storage<T>(r[f]);
   if (id >= 0) {
 #pragma unroll
-    for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)id + f, r[f]);
+    for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)id + f, ro[f]);
   } else {
     const int32_t hh = -id - 1;
     const int np = A.hang_np[hh];
@@ -343,7 +390,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_element_lanes(E
     for (int p = 0; p < np; ++p) {
       const int32_t pid = A.hang_par[4 * hh + p];
 #pragma unroll
-      for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)pid + f, wgt * r[f]);
+      for (int f = 0; f < 3; ++f) atomicAdd(A.out + 3 * (int64_t)pid + f, wgt * ro[f]);
     }
   }
 }
@@ -429,15 +476,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-template <int D, int S>
+template <int D, int NS>
 __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<float> A, LaneParams<float> K,
                                                                  const float4* __restrict__ qp, int* err) {
   constexpr int NC = 1 << D;
   extern __shared__ __align__(128) uint8_t jv_smem[];
-  // S stages of {four state rows, connectivity} and S mbarriers (jv_stage_bytes(S))
+  // NS stages of {four state rows, connectivity} and NS mbarriers (jv_stage_bytes(NS))
   auto sq = reinterpret_cast<float4(*)[4][kLaneThreads]>(jv_smem);
-  auto sconn = reinterpret_cast<int32_t(*)[kLaneThreads]>(jv_smem + S * 4 * kLaneThreads * sizeof(float4));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(jv_smem + S * (4 * kLaneThreads * sizeof(float4) + kLaneThreads * 4));
+  auto sconn = reinterpret_cast<int32_t(*)[kLaneThreads]>(jv_smem + NS * 4 * kLaneThreads * sizeof(float4));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(jv_smem + NS * (4 * kLaneThreads * sizeof(float4) + kLaneThreads * 4));
   const int tid = threadIdx.x;
   const int64_t L = A.n_elem * NC;
   const int64_t n_tiles = (L + kLaneThreads - 1) / kLaneThreads;
@@ -454,14 +501,14 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
   };
   if (tid == 0) {
 #pragma unroll
-    for (int st = 0; st < S; ++st) mbar_init(&bar[st], 1);
+    for (int st = 0; st < NS; ++st) mbar_init(&bar[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   uint32_t pending = 0;  // thread 0: stages with a copy in flight
   if (tid == 0) {
 #pragma unroll
-    for (int st = 0; st < S; ++st)
+    for (int st = 0; st < NS; ++st)
       if (blockIdx.x + st * G < n_tiles) {
         issue(blockIdx.x + st * G, st);
         pending |= 1u << st;
@@ -473,16 +520,16 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
   for (int k = 0;; ++k) {
     const int64_t tl = blockIdx.x + (int64_t)k * G;
     if (tl >= n_tiles) break;
-    const int st = k % S;
-    const uint32_t parity = (uint32_t)(k / S) & 1u;
+    const int st = k % NS;
+    const uint32_t parity = (uint32_t)(k / NS) & 1u;
     const bool ok = mbar_wait(&bar[st], parity);
     if (__syncthreads_or(!ok)) {
       // a copy did not complete: flag it, let the copies still in flight land, return
       if (tid == 0) {
         atomicOr(err, 1);
-        for (int j = 0; j < S; ++j) {
-          const int kk = k + ((j - st + S) % S);
-          if (pending >> j & 1u) mbar_wait(&bar[j], (uint32_t)(kk / S) & 1u);
+        for (int j = 0; j < NS; ++j) {
+          const int kk = k + ((j - st + NS) % NS);
+          if (pending >> j & 1u) mbar_wait(&bar[j], (uint32_t)(kk / NS) & 1u);
         }
       }
       return;
@@ -498,12 +545,12 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
       q3 = sq[st][3][tid];
       id = sconn[st][tid];
     }
-    __syncthreads();  // stage st is read: refill it with the tile S ahead
+    __syncthreads();  // stage st is read: refill it with the tile NS ahead
     if (tid == 0) {
       pending &= ~(1u << st);
-      if (tl + S * G < n_tiles) {
+      if (tl + NS * G < n_tiles) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(tl + S * G, st);
+        issue(tl + NS * G, st);
         pending |= 1u << st;
       }
     }
@@ -804,17 +851,29 @@ cudaError_t launch_element_lanes(int dim, bool jv, const ElemArgs<T>& A, cudaStr
   const unsigned blocks = (unsigned)((threads + t - 1) / t);
   const LaneParams<T> K{T(A.P.kappa), T(A.P.tau_t), T(A.P.C_I * dim), T(A.P.eps2x2)};
   if (dim == 2) {
-    if (jv) k_element_lanes<T, 2, true><<<blocks, t, 0, s>>>(A, K);
-    else k_element_lanes<T, 2, false><<<blocks, t, 0, s>>>(A, K);
+    if (jv) k_element_lanes<T, T, 2, true><<<blocks, t, 0, s>>>(A, K);
+    else k_element_lanes<T, T, 2, false><<<blocks, t, 0, s>>>(A, K);
   } else {
-    if (jv) k_element_lanes<T, 3, true><<<blocks, t, 0, s>>>(A, K);
-    else k_element_lanes<T, 3, false><<<blocks, t, 0, s>>>(A, K);
+    if (jv) k_element_lanes<T, T, 3, true><<<blocks, t, 0, s>>>(A, K);
+    else k_element_lanes<T, T, 3, false><<<blocks, t, 0, s>>>(A, K);
   }
   note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_element_lanes<double>(int, bool, const ElemArgs<double>&, cudaStream_t);
 template cudaError_t launch_element_lanes<float>(int, bool, const ElemArgs<float>&, cudaStream_t);
+
+// FP64 residual with double-float arithmetic (FP32 pipe), FP64 data in and out
+cudaError_t launch_residual_df(int dim, const ElemArgs<double>& A, cudaStream_t s) {
+  if (A.n_elem == 0) return cudaSuccess;
+  const int t = 256;
+  const unsigned blocks = (unsigned)(((A.n_elem << dim) + t - 1) / t);
+  const LaneParams<df> K{df(A.P.kappa), df(A.P.tau_t), df(A.P.C_I * dim), df(A.P.eps2x2)};
+  if (dim == 2) k_element_lanes<double, df, 2, false><<<blocks, t, 0, s>>>(A, K);
+  else k_element_lanes<double, df, 3, false><<<blocks, t, 0, s>>>(A, K);
+  note_launch();
+  return cudaGetLastError();
+}
 
 // the stored linearisation of the FP32 J V (qp: 4 * 2^dim * n_elem float4; A.rec set)
 cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, cudaStream_t s) {

@@ -66,8 +66,18 @@ cudaError_t launch_element_lanes(int dim, bool jv, const ElemArgs<T>& A, cudaStr
 // floating-point operations per element (an FMA counts 2) of the element kernel that
 // launch_element runs, counted from the formulation it evaluates
 double element_kernel_flops(int dim, bool jv);
+// the FP64 residual of the lane-group kernel evaluated in double-float arithmetic (pairs
+// of floats, about 48 bits, on the FP32 pipe); FP64 inputs and output as launch_element
+cudaError_t launch_residual_df(int dim, const ElemArgs<double>& A, cudaStream_t s);
 // true when launch_element runs the lane-group kernel (not PNP_ELEMENT_KERNEL=thread)
 bool element_kernel_is_lanes();
+// true when the FP64 residual runs in double-float arithmetic (lane-group kernel, unless
+// PNP_RESIDUAL_ARITH=f64 selects FP64 arithmetic)
+bool residual_double_float();
+// FP32 operations per FP64 operation of the double-float arithmetic: a sum costs 20, a
+// product 10, a fused multiply-add (2 FP64 flops) 30, so 15 per flop for the FMA-dominated
+// element formulation
+constexpr double kDfFlopsPerFlop = 15.0;
 // FP32 J V from a stored linearisation (element_lanes.cu): launch_lane_state computes, per
 // element lane, the state's Gauss-point quantities J V needs (qp: 4 * 2^dim * n_elem float4,
 // A.rec set); launch_jv_from_state applies J V with them (A.V or A.V4, A.out or A.out4;

@@ -94,7 +94,12 @@ int ctx_residual(pnp_ctx* c, const double* U, double* F) {
     RC(hanging_rows<double>(c, U, F));
   } else {
     CK(cudaMemsetAsync(F, 0, sizeof(double) * c->n3(), c->stream));
-    {
+    if (residual_double_float()) {
+      // FP32-pipe operations of the double-float formulation
+      ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes(),
+                   kDfFlopsPerFlop * element_kernel_flops(c->dim, false) * c->n_elem);
+      CK(launch_residual_df(c->dim, elem_args<double>(c, U, nullptr, c->hs, c->adv, F), c->stream));
+    } else {
       ProfScope ps(c, PNP_PROF_RESIDUAL, 88.0 * c->n_nodes + c->conn_bytes(),
                    element_kernel_flops(c->dim, false) * c->n_elem);
       CK(launch_element<double>(c->dim, false, elem_args<double>(c, U, nullptr, c->hs, c->adv, F), c->stream));
