@@ -121,7 +121,7 @@ __device__ __forceinline__ T to_storage(df x) { return df_to_double(x); }
 // blocks per SM the lane kernel's register cap is set for
 template <typename T, typename C>
 constexpr int lane_min_blocks() {
-  return sizeof(T) == 4 ? 5 : (std::is_same<C, df>::value ? 2 : 3);
+  return sizeof(T) == 4 ? 5 : (std::is_same<C, df>::value ? 4 : 3);
 }
 
 // physical parameters in the kernel's arithmetic type
