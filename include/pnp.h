@@ -158,6 +158,15 @@ void pnp_params_default(pnp_params* p);
  * owned by the caller and released by pnp_mesh_destroy. */
 int pnp_mesh_create(int dim, int max_level, int64_t n_oct, const int32_t* anchors,
                     const uint8_t* levels, pnp_mesh** out);
+/* The same with periodic sides: bit k of `periodic` (0 <= periodic < 2^dim) identifies the
+ * faces x_k = 0 and x_k = 1 (the periodic side walls of the paper's electroconvection
+ * setup, Sec. 5.2).  A node on an identified face is one node, stored with coordinate 0;
+ * those faces carry no boundary condition; hanging constraints, conformity and the 2:1
+ * balance are taken across the identification (PNP_ERR_MESH_UNBALANCED otherwise).
+ * pnp_mesh_create is the case periodic = 0.  The learned start (pnp_mlp_init) rejects
+ * periodic meshes (PNP_ERR_ARG). */
+int pnp_mesh_create_periodic(int dim, int max_level, int64_t n_oct, const int32_t* anchors,
+                             const uint8_t* levels, int periodic, pnp_mesh** out);
 void pnp_mesh_destroy(pnp_mesh* m);
 int pnp_mesh_info(const pnp_mesh* m, int* dim, int* max_level, int64_t* n_elem,
                   int64_t* n_nodes, int64_t* n_hanging);

@@ -40,7 +40,7 @@ def lib():
         L = C.CDLL(path)
         vp, i64p, dp, i32p = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int32)
         L.ora_mesh_build.restype = vp
-        L.ora_mesh_build.argtypes = [C.c_int, C.c_int, C.c_int64, i32p, C.POINTER(C.c_uint8), i32p]
+        L.ora_mesh_build.argtypes = [C.c_int, C.c_int, C.c_int64, i32p, C.POINTER(C.c_uint8), C.c_int, i32p]
         L.ora_mesh_free.argtypes = [vp]
         L.ora_mesh_sizes.argtypes = [vp, i64p, i64p, i64p]
         L.ora_mesh_nodes.argtypes = [vp, i64p, i32p, i64p]
@@ -114,8 +114,9 @@ class OracleMesh:
         err = C.c_int32(0)
         a = np.ascontiguousarray(octants.anchors, dtype=np.int32)
         lv = np.ascontiguousarray(octants.levels, dtype=np.uint8)
+        self.periodic = int(getattr(octants, "periodic", 0))
         self.h = L.ora_mesh_build(octants.dim, octants.max_level, octants.n, _p(a, C.c_int32),
-                                  _p(lv, C.c_uint8), C.byref(err))
+                                  _p(lv, C.c_uint8), self.periodic, C.byref(err))
         if not self.h:
             raise ValueError(f"oracle mesh build failed (code {err.value})")
         self.dim, self.max_level = octants.dim, octants.max_level

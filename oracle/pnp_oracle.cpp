@@ -18,7 +18,10 @@
 //   * the analytic Jacobian of that residual (Sec. 4.1, Eq. newton_linear_system);
 //   * Q1 elements on a 2:1-balanced octree (Sec. 4.2) with conforming hanging-node
 //     constraints (the paper does not describe them; face-centre = mean of 4 face
-//     corners, edge-midpoint = mean of 2 edge ends).
+//     corners, edge-midpoint = mean of 2 edge ends);
+//   * optional periodic side walls (the electroconvection setup of Sec. 5.2): on a
+//     periodic axis every coordinate is taken modulo the domain length, so the faces
+//     x = 0 and x = 1 are one set of nodes and carry no boundary condition.
 //
 // Everything is written out plainly: std::map on integer coordinates for the mesh,
 // direct evaluation of the tensor-product shape functions at each Gauss point,
@@ -40,6 +43,7 @@ typedef std::array<int64_t, 3> IPt;
 struct Mesh {
   int dim = 0;
   int L = 0;                                   // max level: coordinates in units of 2^-L
+  int periodic = 0;                            // bit k: faces x_k = 0 and x_k = 1 are one
   std::vector<IPt> el_anchor;
   std::vector<int> el_level;
   std::vector<std::vector<int64_t>> el_nodes;  // 2^dim corner node ids (lexicographic corner order)
@@ -132,21 +136,31 @@ void mms_forcing(int dim, const double* x, double t, double eps, int steady, dou
 // ------------------------------------------------------------------ mesh construction
 int corner_count(int dim) { return 1 << dim; }
 
+// On a periodic axis a point is taken modulo the domain length (x = 1 is x = 0).
+void wrap_point(const Mesh& m, IPt& p) {
+  const int64_t size = int64_t(1) << m.L;
+  for (int k = 0; k < m.dim; ++k)
+    if ((m.periodic >> k) & 1) p[k] = ((p[k] % size) + size) % size;
+}
+
 IPt corner_point(const Mesh& m, const IPt& a, int64_t s, int c) {
   IPt p = a;
   for (int k = 0; k < m.dim; ++k)
     if ((c >> k) & 1) p[k] += s;
+  wrap_point(m, p);
   return p;
 }
 
 // Error codes (same meaning as the library's public codes where they overlap).
 enum { ORA_OK = 0, ORA_ERR_ARG = 1, ORA_ERR_UNBALANCED = 3 };
 
-int build_mesh(Mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels) {
+int build_mesh(Mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels, int periodic) {
   if (dim != 2 && dim != 3) return ORA_ERR_ARG;
   if (L < 0 || L > 20 || n <= 0) return ORA_ERR_ARG;
+  if (periodic < 0 || periodic >= (1 << dim)) return ORA_ERR_ARG;
   m.dim = dim;
   m.L = L;
+  m.periodic = periodic;
   const int64_t size = int64_t(1) << L;
   std::map<IPt, int> leaf;  // anchor -> level
   for (int64_t e = 0; e < n; ++e) {
@@ -154,6 +168,7 @@ int build_mesh(Mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const
     for (int k = 0; k < dim; ++k) a[k] = anchors[e * dim + k];
     const int l = levels[e];
     if (l > L) return ORA_ERR_ARG;
+    if (periodic && l == 0) return ORA_ERR_ARG;  // an element would meet itself across the wrap
     const int64_t s = int64_t(1) << (L - l);
     for (int k = 0; k < dim; ++k)
       if (a[k] < 0 || a[k] % s != 0 || a[k] + s > size) return ORA_ERR_ARG;
@@ -191,9 +206,11 @@ int build_mesh(Mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const
       bool inside = true;
       for (int k = 0; k < dim; ++k) {
         r[k] = a[k] + off[k] * s;
+        if ((periodic >> k) & 1) continue;  // wrapped below
         if (r[k] < 0 || r[k] >= size) inside = false;
       }
       if (!inside) continue;
+      wrap_point(m, r);
       for (int lc = l; lc >= 0; --lc) {
         const int64_t sc = int64_t(1) << (L - lc);
         IPt b = {0, 0, 0};
@@ -251,6 +268,7 @@ int build_mesh(Mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const
       if (nmid == 0 || nmid == dim) continue;  // a corner, or the element centre
       IPt p = a;
       for (int k = 0; k < dim; ++k) p[k] = a[k] + t3[k] * (s / 2);
+      wrap_point(m, p);
       auto it = m.node_of.find(p);
       if (it == m.node_of.end()) continue;
       const int64_t h = it->second;
@@ -268,6 +286,7 @@ int build_mesh(Mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const
             pp[k] = a[k] + t3[k] * (s / 2);
           }
         }
+        wrap_point(m, pp);
         auto pit = m.node_of.find(pp);
         if (pit == m.node_of.end()) return ORA_ERR_UNBALANCED;
         par.push_back({pit->second, 1.0 / npar});
@@ -305,6 +324,7 @@ bool dirichlet(const Mesh& m, const Params& p, int64_t i, int f, double* g) {
   bool is = false;
   for (int face = 0; face < 2 * m.dim; ++face) {
     const int ax = face / 2;
+    if ((m.periodic >> ax) & 1) continue;  // identified faces carry no condition
     const int64_t want = (face & 1) ? size : 0;
     if (m.node_xyz[i][ax] != want) continue;
     if (p.bc_type[face][f] != 1) continue;
@@ -688,9 +708,9 @@ void jv(const Mesh& m, const Params& p, const double* U, const double* Uk, const
 extern "C" {
 
 void* ora_mesh_build(int dim, int max_level, int64_t n, const int32_t* anchors, const uint8_t* levels,
-                     int32_t* err) {
+                     int periodic, int32_t* err) {
   Mesh* m = new Mesh();
-  const int rc = build_mesh(*m, dim, max_level, n, anchors, levels);
+  const int rc = build_mesh(*m, dim, max_level, n, anchors, levels, periodic);
   *err = rc;
   if (rc != ORA_OK) {
     delete m;

@@ -75,13 +75,18 @@ void pnp_params_default(pnp_params* p) {
 // ------------------------------------------------------------------ mesh
 int pnp_mesh_create(int dim, int max_level, int64_t n_oct, const int32_t* anchors, const uint8_t* levels,
                     pnp_mesh** out) {
+  return pnp_mesh_create_periodic(dim, max_level, n_oct, anchors, levels, 0, out);
+}
+
+int pnp_mesh_create_periodic(int dim, int max_level, int64_t n_oct, const int32_t* anchors, const uint8_t* levels,
+                             int periodic, pnp_mesh** out) {
   if (!out) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_create: out is null");
   *out = nullptr;
   pnp_mesh* m = new (std::nothrow) pnp_mesh();
   if (!m) PNP_FAIL(PNP_ERR_NOMEM, "pnp_mesh_create: out of host memory");
   int rc;
   try {
-    rc = pnp_build_mesh(*m, dim, max_level, n_oct, anchors, levels);
+    rc = pnp_build_mesh(*m, dim, max_level, n_oct, anchors, levels, periodic);
   } catch (const std::bad_alloc&) {
     pnp_set_error("pnp_mesh_create: out of host memory");
     rc = PNP_ERR_NOMEM;

@@ -6,6 +6,11 @@
 // conforming Q1 constraints of hanging nodes (face centre = mean of 4 face corners,
 // edge midpoint = mean of 2 edge ends; the paper does not describe them).
 //
+// Periodic axes (bit k of `periodic`): the faces x_k = 0 and x_k = 1 are identified, so
+// a corner at x_k = 1 is the node at x_k = 0.  Corners, midpoints and parents are keyed
+// by wrapped coordinates; the neighbourhood count below then covers the wrap too, which
+// makes the conformity and 2:1 checks hold across the identified faces.
+//
 // Validation is done on the node structure: with every octant aligned and the cover
 // complete and non-overlapping (checked on Morton intervals), a mesh is conforming and
 // 2:1 balanced iff at every node the elements touching it fill the node's neighbourhood
@@ -80,8 +85,11 @@ void radix_sort_pairs(std::vector<uint64_t>& key, std::vector<uint32_t>& val) {
 
 uint64_t pnp_morton(int dim, const int64_t* p) { return morton(dim, p); }
 
-int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels) {
+int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels,
+                   int periodic) {
   if (dim != 2 && dim != 3) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_create: dim must be 2 or 3 (got %d)", dim);
+  if (periodic < 0 || periodic >= (1 << dim))
+    PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_create: periodic mask %d has bits beyond dim %d", periodic, dim);
   if (L < 0 || L > 16) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_create: max_level must be in 0..16 (got %d)", L);
   if (n <= 0 || !anchors || !levels) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_create: empty octant list or null pointer");
   const int nc = 1 << dim;
@@ -90,7 +98,13 @@ int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchor
   m = pnp_mesh();
   m.dim = dim;
   m.L = L;
+  m.periodic = periodic;
   m.n_elem = n;
+  // a coordinate on an identified face maps to 0
+  auto wrap = [&](int64_t* p) {
+    for (int k = 0; k < dim; ++k)
+      if (((periodic >> k) & 1) && p[k] == size) p[k] = 0;
+  };
 
   // ---- validate alignment, Morton-sort the octants, check the cover on Morton intervals
   std::vector<uint64_t> ekey(n);
@@ -98,6 +112,8 @@ int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchor
   for (int64_t e = 0; e < n; ++e) {
     const int l = levels[e];
     if (l > L) PNP_FAIL(PNP_ERR_MESH, "octant %lld: level %d > max_level %d", (long long)e, l, L);
+    if (periodic && l == 0)
+      PNP_FAIL(PNP_ERR_MESH, "octant %lld: a periodic axis needs at least two elements across", (long long)e);
     const int64_t s = int64_t(1) << (L - l);
     int64_t a[3] = {0, 0, 0};
     for (int k = 0; k < dim; ++k) {
@@ -137,6 +153,7 @@ int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchor
     for (int c = 0; c < nc; ++c) {
       int64_t p[3] = {0, 0, 0};
       for (int k = 0; k < dim; ++k) p[k] = m.el_anchor[i * dim + k] + (((c >> k) & 1) ? s : 0);
+      wrap(p);
       ckey[i * nc + c] = morton(dim, p);
       cslot[i * nc + c] = (uint32_t)(i * nc + c);
     }
@@ -157,20 +174,25 @@ int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchor
     const int64_t s = int64_t(1) << (L - m.el_level[i]);
     for (int c = 0; c < nc; ++c) {
       const int32_t id = m.el_conn[i * nc + c];
-      for (int k = 0; k < dim; ++k)
-        m.node_ijk[(int64_t)id * dim + k] = (int32_t)(m.el_anchor[i * dim + k] + (((c >> k) & 1) ? s : 0));
+      int64_t p[3] = {0, 0, 0};
+      for (int k = 0; k < dim; ++k) p[k] = m.el_anchor[i * dim + k] + (((c >> k) & 1) ? s : 0);
+      wrap(p);
+      for (int k = 0; k < dim; ++k) m.node_ijk[(int64_t)id * dim + k] = (int32_t)p[k];
     }
   }
   for (int64_t v = 0; v < N; ++v) {
     uint8_t f = 0;
     for (int k = 0; k < dim; ++k) {
+      if ((periodic >> k) & 1) continue;  // identified faces are not boundary
       const int32_t x = m.node_ijk[v * dim + k];
       if (x == 0) f |= (uint8_t)(1u << (2 * k));
       if (x == size) f |= (uint8_t)(1u << (2 * k + 1));
     }
     m.node_faces[v] = f;
   }
-  auto find_node = [&](const int64_t* p) -> int64_t {
+  auto find_node = [&](const int64_t* p0) -> int64_t {
+    int64_t p[3] = {p0[0], p0[1], p0[2]};
+    wrap(p);
     const uint64_t k = morton(dim, p);
     auto it = std::lower_bound(nkey.begin(), nkey.end(), k);
     if (it == nkey.end() || *it != k) return -1;

@@ -692,6 +692,7 @@ int pnp_mlp_init(pnp_ctx* c, uint64_t seed) {
   if (!c) PNP_FAIL(PNP_ERR_ARG, "null context");
   if (c->latched != cudaSuccess) PNP_FAIL(PNP_ERR_CUDA, "context latched");
   if (c->dim != 3) PNP_FAIL(PNP_ERR_STATE, "learned start: 3D meshes only");
+  if (c->host_mesh.periodic) PNP_FAIL(PNP_ERR_ARG, "learned start: periodic meshes are not supported");
   pnp_mlp_release(c);
   Mlp* m = new Mlp();
   c->mlp = m;

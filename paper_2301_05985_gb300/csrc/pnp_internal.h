@@ -24,6 +24,7 @@ void pnp_set_error(const char* fmt, ...);
 struct pnp_mesh {
   int dim = 0;
   int L = 0;
+  int periodic = 0;                 // bit k: axis k is periodic (faces 2k, 2k+1 identified)
   int64_t n_elem = 0, n_nodes = 0, n_hanging = 0;
   std::vector<int32_t> el_anchor;   // [E][dim]
   std::vector<uint8_t> el_level;    // [E]
@@ -36,7 +37,8 @@ struct pnp_mesh {
   std::vector<uint8_t> hang_np;     // [H] number of parents (2 or 4)
 };
 
-int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels);
+int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels,
+                   int periodic);
 // Morton (Z-order) key of an integer point (x in bit 0 of each group, then y, then z).
 uint64_t pnp_morton(int dim, const int64_t* p);
 

@@ -90,6 +90,7 @@ SIGNATURES = {
     "pnp_version": (C.c_char_p, []),
     "pnp_params_default": (None, [_P(pnp_params)]),
     "pnp_mesh_create": (C.c_int, [C.c_int, C.c_int, _i64, _vp, _vp, _P(_vp)]),
+    "pnp_mesh_create_periodic": (C.c_int, [C.c_int, C.c_int, _i64, _vp, _vp, C.c_int, _P(_vp)]),
     "pnp_mesh_destroy": (None, [_vp]),
     "pnp_mesh_info": (C.c_int, [_vp, _P(C.c_int), _P(C.c_int), _P(_i64), _P(_i64), _P(_i64)]),
     "pnp_mesh_node_coords": (C.c_int, [_vp, _vp]),
@@ -200,14 +201,16 @@ def _ptr(x):
 
 
 class Mesh:
-    """Q1 mesh of a 2:1-balanced octree (owns a pnp_mesh handle)."""
+    """Q1 mesh of a 2:1-balanced octree (owns a pnp_mesh handle).  ``octants.periodic``
+    (bit k: axis k periodic, default 0) selects periodic sides."""
 
     def __init__(self, octants):
         a = np.ascontiguousarray(octants.anchors, dtype=np.int32)
         lv = np.ascontiguousarray(octants.levels, dtype=np.uint8)
         h = C.c_void_p()
-        check(lib().pnp_mesh_create(octants.dim, octants.max_level, octants.n, a.ctypes.data, lv.ctypes.data,
-                                    C.byref(h)))
+        self.periodic = int(getattr(octants, "periodic", 0))
+        check(lib().pnp_mesh_create_periodic(octants.dim, octants.max_level, octants.n, a.ctypes.data,
+                                             lv.ctypes.data, self.periodic, C.byref(h)))
         self.h = h
         d, L = C.c_int(), C.c_int()
         ne, nn, nh = C.c_int64(), C.c_int64(), C.c_int64()

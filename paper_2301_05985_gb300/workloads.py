@@ -35,6 +35,7 @@ class Octants:
     max_level: int
     anchors: np.ndarray  # int32 [n, dim]
     levels: np.ndarray   # uint8 [n]
+    periodic: int = 0    # bit k: axis k periodic (faces x_k = 0 and 1 identified)
 
     @property
     def n(self) -> int:
@@ -109,11 +110,18 @@ def membrane_band_octants(base_level: int = 5, fine_level: int = 8, band: float 
     return layered_octants(3, layers)
 
 
-def random_balanced_octants(dim: int, base_level: int, max_level: int, frac: float, seed: int) -> Octants:
+def with_periodic(oc: Octants, periodic: int) -> Octants:
+    """The same octants with periodic axes (bit k: axis k)."""
+    return dataclasses.replace(oc, periodic=int(periodic))
+
+
+def random_balanced_octants(dim: int, base_level: int, max_level: int, frac: float, seed: int,
+                            periodic: int = 0) -> Octants:
     """A seeded random 2:1-balanced octree (face, edge and corner balance).
 
     Start from a uniform base grid, refine a random fraction of leaves level by level,
     then refine any leaf that has a neighbour two or more levels finer until none does.
+    With periodic axes (bit k), neighbours are also looked up across the identified faces.
     Intended for small meshes (tests): pure Python dictionaries.
     """
     rng = np.random.default_rng(seed)
@@ -169,6 +177,7 @@ def random_balanced_octants(dim: int, base_level: int, max_level: int, frac: flo
                         pts.append(list(range(a[k], a[k] + s)))
                 # iterate over the boundary strip at the finest resolution (small meshes only)
                 for pt in np.array(np.meshgrid(*pts, indexing="ij")).reshape(dim, -1).T:
+                    pt = [int(p) % size if (periodic >> k) & 1 else int(p) for k, p in enumerate(pt)]
                     if any(p < 0 or p >= size for p in pt):
                         continue
                     nb = find_leaf(tuple(int(p) for p in pt))
@@ -180,7 +189,7 @@ def random_balanced_octants(dim: int, base_level: int, max_level: int, frac: flo
                         changed = True
     anchors = np.array(sorted(leaves.keys()), dtype=np.int32)
     levels = np.array([leaves[tuple(int(v) for v in a)] for a in anchors], dtype=np.uint8)
-    return Octants(dim, L, anchors, levels)
+    return Octants(dim, L, anchors, levels, int(periodic))
 
 
 # ----------------------------------------------------------------------------- BCs
