@@ -232,6 +232,15 @@ int pnp_block_diag(pnp_ctx* c, const double* U, double* D);
 /* The same blocks in FP32 arithmetic at U rounded to FP32 (D device FP32 [n][3][3]):
  * the blocks the mixed-precision solver inverts for its block-Jacobi preconditioner. */
 int pnp_block_diag_f32(pnp_ctx* c, const double* U, float* D);
+/* Species fluxes through boundary face `face` (0 <= face < 2 dim; axis face/2, the high
+ * side when face is odd): flux[s] = int_face n . (grad c_s + z_s c_s grad phi) dS for
+ * s = +, - (z = +1, -1), n the outward unit normal, U a device FP64 [n][3] state (hanging
+ * entries ignored, taken from their constraints).  Each element side on the face is
+ * integrated with the 2^(d-1)-point Gauss rule; the sum is reduced in a fixed order.
+ * These are the terms of the boundary current of Sec. 5.2, the net species flux
+ * through the top boundary: j_T = -(flux[0] - flux[1]) / L_T, L_T the face's length
+ * (area in 3D; 1 on the unit domain).  A periodic face gives 0.  flux: host double[2]. */
+int pnp_boundary_flux(pnp_ctx* c, const double* U, int face, double* flux);
 /* ||x||_2 of a device FP64 vector of n entries, the reduction Newton and GMRES use
  * (fixed grid, fixed summation order: bitwise reproducible); result on the host.
  * x may be NULL when n == 0.  Uses the context's scratch and stream. */

@@ -54,6 +54,7 @@ def lib():
         L.ora_bc_rows.argtypes = [vp, vp, i32p, dp]
         L.ora_mms.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int64, dp, dp, dp]
         L.ora_eval_points.argtypes = [vp, dp, C.c_int64, i64p, dp]
+        L.ora_boundary_flux.argtypes = [vp, C.c_int, dp, dp]
         _lib = L
     return _lib
 
@@ -180,6 +181,15 @@ class OracleMesh:
         lib().ora_residual(self.h, C.byref(pc), _p(U, C.c_double), _p(Uk, C.c_double), _p(Ukm1, C.c_double),
                            _p(v, C.c_double), _p(F, C.c_double))
         return F
+
+    def boundary_flux(self, U, face: int):
+        """[int_face n.(grad c+ + c+ grad phi), int_face n.(grad c- - c- grad phi)] over
+        boundary face `face` (outward normal): the species terms of the boundary current
+        of Sec. 5.2."""
+        U = self._z(U)
+        out = np.zeros(2)
+        lib().ora_boundary_flux(self.h, int(face), _p(U, C.c_double), _p(out, C.c_double))
+        return out
 
     def jacobian(self, p: Params, U, Uk=None, Ukm1=None, adv=None) -> sp.csr_matrix:
         U = self._z(U); Uk = self._z(Uk); Ukm1 = self._z(Ukm1); v = self._vel3(adv)

@@ -704,8 +704,75 @@ void jv(const Mesh& m, const Params& p, const double* U, const double* Uk, const
 
 }  // namespace
 
+// ------------------------------------------------------------------ boundary flux
+// Integral over boundary face `face` (axis face/2, the high side when face is odd) of
+// n . (grad c_s + z_s c_s grad phi) for s = +, -, n the outward unit normal: the per
+// species terms of the boundary current of Sec. 5.2 (the net species flux through the
+// top boundary).  Each element with a side on that face contributes the tensor Gauss
+// rule with 2^(d-1) points on its side, the Q1 fields through the constraints.
+void boundary_flux(const Mesh& m, int face, const double* U, double out[2]) {
+  const int dim = m.dim;
+  const int ax = face / 2;
+  const bool high = face & 1;
+  const int64_t size = int64_t(1) << m.L;
+  const double g = 1.0 / std::sqrt(3.0);
+  const double nrm = high ? 1.0 : -1.0;
+  out[0] = out[1] = 0.0;
+  if ((m.periodic >> ax) & 1) return;  // an identified face is not a boundary
+  const int nc = corner_count(dim);
+  for (size_t e = 0; e < m.el_anchor.size(); ++e) {
+    const int64_t s = int64_t(1) << (m.L - m.el_level[e]);
+    const int64_t side = m.el_anchor[e][ax] + (high ? s : 0);
+    if (side != (high ? size : 0)) continue;
+    const double h = std::ldexp(1.0, -m.el_level[e]);
+    double u[8][3];
+    gather3(m, (int64_t)e, U, u);
+    // 2^(dim-1) Gauss points of the side, weight (h/2)^(dim-1) each
+    const int nq = 1 << (dim - 1);
+    for (int q = 0; q < nq; ++q) {
+      double xi[3] = {0, 0, 0};
+      int bit = 0;
+      for (int k = 0; k < dim; ++k) {
+        if (k == ax) {
+          xi[k] = high ? 1.0 : -1.0;
+        } else {
+          xi[k] = ((q >> bit) & 1) ? g : -g;
+          ++bit;
+        }
+      }
+      double val[3] = {0, 0, 0}, grad[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      for (int c = 0; c < nc; ++c) {
+        double f1[3], d1[3];
+        for (int k = 0; k < dim; ++k) {
+          const double sk = ((c >> k) & 1) ? 1.0 : -1.0;
+          f1[k] = 0.5 * (1.0 + sk * xi[k]);
+          d1[k] = 0.5 * sk * (2.0 / h);
+        }
+        double N = 1.0;
+        for (int k = 0; k < dim; ++k) N *= f1[k];
+        for (int f = 0; f < 3; ++f) val[f] += N * u[c][f];
+        for (int a = 0; a < dim; ++a) {
+          double d = d1[a];
+          for (int k = 0; k < dim; ++k)
+            if (k != a) d *= f1[k];
+          for (int f = 0; f < 3; ++f) grad[f][a] += d * u[c][f];
+        }
+      }
+      const double w = std::pow(0.5 * h, dim - 1);
+      for (int sp = 0; sp < 2; ++sp) {
+        const double z = sp == 0 ? 1.0 : -1.0;
+        out[sp] += w * nrm * (grad[sp][ax] + z * val[sp] * grad[2][ax]);
+      }
+    }
+  }
+}
+
 // ================================================================== C interface
 extern "C" {
+
+void ora_boundary_flux(void* h, int face, const double* U, double* out) {
+  boundary_flux(*static_cast<Mesh*>(h), face, U, out);
+}
 
 void* ora_mesh_build(int dim, int max_level, int64_t n, const int32_t* anchors, const uint8_t* levels,
                      int periodic, int32_t* err) {

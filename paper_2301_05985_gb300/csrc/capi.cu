@@ -541,6 +541,20 @@ int pnp_block_diag_f32(pnp_ctx* c, const double* U, float* D) {
   return PNP_OK;
 }
 
+int pnp_boundary_flux(pnp_ctx* c, const double* U, int face, double* flux) {
+  CTX_GUARD(c);
+  if (!U || !flux) PNP_FAIL(PNP_ERR_ARG, "pnp_boundary_flux: null pointer");
+  if (face < 0 || face >= 2 * c->dim) PNP_FAIL(PNP_ERR_ARG, "pnp_boundary_flux: face %d out of range", face);
+  double* slot = c->dsc + 4 * (c->m_alloc + 2) + 12;
+  CK(launch_boundary_flux(c->dim, c->n_elem, c->d_conn, c->d_level, c->d_faces, c->d_hnode, c->d_hpar, c->d_hnp, U,
+                          face, c->part, slot, c->stream));
+  CK(cudaMemcpyAsync(c->hpin + 2, slot, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  flux[0] = c->hpin[2];
+  flux[1] = c->hpin[3];
+  return PNP_OK;
+}
+
 int pnp_norm2(pnp_ctx* c, const double* x, int64_t n, double* result) {
   CTX_GUARD(c);
   if (!result || n < 0 || (!x && n > 0)) PNP_FAIL(PNP_ERR_ARG, "pnp_norm2: bad arguments");

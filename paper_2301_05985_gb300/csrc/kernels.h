@@ -178,6 +178,11 @@ cudaError_t launch_combine_f32_add_f64(int64_t n, int k, const float* Zb, int64_
                                        cudaStream_t s);
 // y = scale * x
 cudaError_t launch_to_f64_scaled(int64_t n, const float* x, double scale, double* y, cudaStream_t s);
+// out[s] = int_face n . (grad c_s + z_s c_s grad phi) dS (s = +, -) over boundary face
+// `face` (boundary.cu); part: kRedBlocks x 2 partials; out: 2 device doubles
+cudaError_t launch_boundary_flux(int dim, int64_t n_elem, const int32_t* conn, const uint8_t* level,
+                                 const uint8_t* faces, const int32_t* hnode, const int32_t* hpar, const uint8_t* hnp,
+                                 const double* U, int face, double* part, double* out, cudaStream_t s);
 // copy with layout change: [N][dim] <-> [N][3]
 cudaError_t launch_vel_pack(int64_t N, int dim, const double* src, double* dst3, cudaStream_t s);
 cudaError_t launch_vel_unpack(int64_t N, int dim, const double* src3, double* dst, cudaStream_t s);

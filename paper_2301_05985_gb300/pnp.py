@@ -111,6 +111,7 @@ SIGNATURES = {
     "pnp_jv_linearized": (C.c_int, [_vp, _vp, _vp]),
     "pnp_block_diag": (C.c_int, [_vp, _vp, _vp]),
     "pnp_block_diag_f32": (C.c_int, [_vp, _vp, _vp]),
+    "pnp_boundary_flux": (C.c_int, [_vp, _vp, C.c_int, _vp]),
     "pnp_norm2": (C.c_int, [_vp, _vp, _i64, _P(_d)]),
     "pnp_gmres": (C.c_int, [_vp, _vp, _vp, _vp, _d, C.c_int, _P(pnp_solve_stats)]),
     "pnp_newton_solve": (C.c_int, [_vp, _P(pnp_solve_stats)]),
@@ -330,6 +331,19 @@ class Context:
         fn = lib().pnp_block_diag_f32 if str(D.dtype) == "torch.float32" else lib().pnp_block_diag
         check(fn(self.h, _ptr(U), _ptr(D)))
         return D
+
+    def boundary_flux(self, U, face: int) -> np.ndarray:
+        """[int_face n.(grad c+ + c+ grad phi), int_face n.(grad c- - c- grad phi)] over a
+        boundary face (outward normal n); U a device FP64 [n][3] tensor."""
+        out = np.zeros(2)
+        check(lib().pnp_boundary_flux(self.h, _ptr(U), int(face), out.ctypes.data))
+        return out
+
+    def boundary_current(self, U, face: int) -> float:
+        """Net species flux through a face, j = -(flux_+ - flux_-) / |face| (Sec. 5.2)
+        on the unit domain."""
+        f = self.boundary_flux(U, face)
+        return -(f[0] - f[1])
 
     def norm2(self, x) -> float:
         r = C.c_double()
