@@ -241,6 +241,13 @@ int pnp_block_diag_f32(pnp_ctx* c, const double* U, float* D);
  * through the top boundary: j_T = -(flux[0] - flux[1]) / L_T, L_T the face's length
  * (area in 3D; 1 on the unit domain).  A periodic face gives 0.  flux: host double[2]. */
 int pnp_boundary_flux(pnp_ctx* c, const double* U, int face, double* flux);
+/* Averages of (c+, c-, phi) over the plane x_axis = coord * 2^-max_level (0 <= coord <=
+ * 2^max_level; coord < 2^max_level on a periodic axis) of the unit domain: the integral
+ * of each Q1 field over the plane, each element's cross-section integrated with the
+ * 2^(d-1)-point Gauss rule (exact), U a device FP64 [n][3] state.  Evaluated at every node
+ * level along the wall-normal axis these are the x-averaged profiles of Sec. 5.2.  The
+ * first call uploads the element anchors (4 dim bytes per element).  avg: host double[3]. */
+int pnp_plane_average(pnp_ctx* c, const double* U, int axis, int64_t coord, double* avg);
 /* ||x||_2 of a device FP64 vector of n entries, the reduction Newton and GMRES use
  * (fixed grid, fixed summation order: bitwise reproducible); result on the host.
  * x may be NULL when n == 0.  Uses the context's scratch and stream. */

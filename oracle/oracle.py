@@ -55,6 +55,7 @@ def lib():
         L.ora_mms.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int64, dp, dp, dp]
         L.ora_eval_points.argtypes = [vp, dp, C.c_int64, i64p, dp]
         L.ora_boundary_flux.argtypes = [vp, C.c_int, dp, dp]
+        L.ora_plane_integral.argtypes = [vp, C.c_int, C.c_int64, dp, dp]
         _lib = L
     return _lib
 
@@ -189,6 +190,14 @@ class OracleMesh:
         U = self._z(U)
         out = np.zeros(2)
         lib().ora_boundary_flux(self.h, int(face), _p(U, C.c_double), _p(out, C.c_double))
+        return out
+
+    def plane_integral(self, U, axis: int, coord: int):
+        """Integrals of (c+, c-, phi) over the plane x_axis = coord 2^-max_level (the
+        x-averaged profiles of Sec. 5.2 on the unit domain)."""
+        U = self._z(U)
+        out = np.zeros(3)
+        lib().ora_plane_integral(self.h, int(axis), int(coord), _p(U, C.c_double), _p(out, C.c_double))
         return out
 
     def jacobian(self, p: Params, U, Uk=None, Ukm1=None, adv=None) -> sp.csr_matrix:

@@ -767,8 +767,54 @@ void boundary_flux(const Mesh& m, int face, const double* U, double out[2]) {
   }
 }
 
+// ------------------------------------------------------------------ plane integral
+// Integral of each field over the plane x_ax = coord (integer units): every point of the
+// plane lies in the elements whose closed range [a, a + s] along ax holds coord; an
+// element whose side lies in the plane shares it with its neighbour across, so the
+// element above the plane takes it (below only at the top face).  Cross-section at
+// xi_ax = 2 (coord - a) / s - 1, tensor Gauss rule with 2^(d-1) points.
+void plane_integral(const Mesh& m, int ax, int64_t coord, const double* U, double out[3]) {
+  const int dim = m.dim;
+  const int64_t size = int64_t(1) << m.L;
+  const double g = 1.0 / std::sqrt(3.0);
+  out[0] = out[1] = out[2] = 0.0;
+  const int nc = corner_count(dim);
+  for (size_t e = 0; e < m.el_anchor.size(); ++e) {
+    const int64_t s = int64_t(1) << (m.L - m.el_level[e]);
+    const int64_t a = m.el_anchor[e][ax];
+    if (coord < a || coord > a + s) continue;          // the plane misses the element
+    if (coord == a + s && coord != size) continue;     // the element above takes the side
+    const double h = std::ldexp(1.0, -m.el_level[e]);
+    double u[8][3];
+    gather3(m, (int64_t)e, U, u);
+    const int nq = 1 << (dim - 1);
+    for (int q = 0; q < nq; ++q) {
+      double xi[3] = {0, 0, 0};
+      int bit = 0;
+      for (int k = 0; k < dim; ++k) {
+        if (k == ax) {
+          xi[k] = 2.0 * (double)(coord - a) / (double)s - 1.0;
+        } else {
+          xi[k] = ((q >> bit) & 1) ? g : -g;
+          ++bit;
+        }
+      }
+      const double w = std::pow(0.5 * h, dim - 1);
+      for (int c = 0; c < nc; ++c) {
+        double N = 1.0;
+        for (int k = 0; k < dim; ++k) N *= 0.5 * (1.0 + (((c >> k) & 1) ? 1.0 : -1.0) * xi[k]);
+        for (int f = 0; f < 3; ++f) out[f] += w * N * u[c][f];
+      }
+    }
+  }
+}
+
 // ================================================================== C interface
 extern "C" {
+
+void ora_plane_integral(void* h, int ax, int64_t coord, const double* U, double* out) {
+  plane_integral(*static_cast<Mesh*>(h), ax, coord, U, out);
+}
 
 void ora_boundary_flux(void* h, int face, const double* U, double* out) {
   boundary_flux(*static_cast<Mesh*>(h), face, U, out);

@@ -164,7 +164,7 @@ static int check_params(const pnp_params* p) {
 }
 
 static void free_ctx_memory(pnp_ctx* c) {
-  void* ptrs[] = {c->d_conn, c->d_level, c->d_faces, c->d_hnode, c->d_hpar, c->d_hnp, c->U, c->Uk, c->Ukm1,
+  void* ptrs[] = {c->d_conn, c->d_anchor, c->d_level, c->d_faces, c->d_hnode, c->d_hpar, c->d_hnp, c->U, c->Uk, c->Ukm1,
                   c->adv, c->vel, c->vel_prev, c->hs, c->U32, c->adv32, c->hs32, c->V32, c->JV32, c->F,
                   c->dU, c->Ut, c->Ft, c->rhs, c->Dinv, c->D32, c->basis, c->w, c->z, c->r, c->part, c->dsc,
                   c->dflag, c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv, c->rec32, c->V4, c->JV4, c->qp32};
@@ -552,6 +552,30 @@ int pnp_boundary_flux(pnp_ctx* c, const double* U, int face, double* flux) {
   CK(cudaStreamSynchronize(c->stream));
   flux[0] = c->hpin[2];
   flux[1] = c->hpin[3];
+  return PNP_OK;
+}
+
+int pnp_plane_average(pnp_ctx* c, const double* U, int axis, int64_t coord, double* avg) {
+  CTX_GUARD(c);
+  if (!U || !avg) PNP_FAIL(PNP_ERR_ARG, "pnp_plane_average: null pointer");
+  if (axis < 0 || axis >= c->dim) PNP_FAIL(PNP_ERR_ARG, "pnp_plane_average: axis %d out of range", axis);
+  const int L = c->host_mesh.L;
+  const int64_t size = int64_t(1) << L;
+  const bool per = (c->host_mesh.periodic >> axis) & 1;
+  if (coord < 0 || coord > size || (per && coord == size))
+    PNP_FAIL(PNP_ERR_ARG, "pnp_plane_average: coordinate %lld outside the domain", (long long)coord);
+  if (!c->d_anchor) {
+    const size_t bytes = sizeof(int32_t) * c->host_mesh.el_anchor.size();
+    CK(cudaMalloc((void**)&c->d_anchor, bytes));
+    CK(cudaMemcpyAsync(c->d_anchor, c->host_mesh.el_anchor.data(), bytes, cudaMemcpyHostToDevice, c->stream));
+  }
+  double* slot = c->dsc + 4 * (c->m_alloc + 2) + 12;
+  CK(launch_plane_integral(c->dim, L, c->n_elem, c->d_conn, c->d_level, c->d_anchor, c->d_hnode, c->d_hpar, c->d_hnp,
+                           U, axis, coord, c->part, slot, c->stream));
+  CK(cudaMemcpyAsync(c->hpin + 2, slot, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  // the plane's area is 1 on the unit domain
+  for (int f = 0; f < 3; ++f) avg[f] = c->hpin[2 + f];
   return PNP_OK;
 }
 

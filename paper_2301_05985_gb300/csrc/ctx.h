@@ -17,6 +17,7 @@ struct pnp_ctx {
 
   // mesh (device)
   int32_t* d_conn = nullptr;
+  int32_t* d_anchor = nullptr;  // [E][dim] element anchors, uploaded on first use (plane integrals)
   uint8_t* d_level = nullptr;
   uint8_t* d_faces = nullptr;  // boundary-face bits, bit 7 = hanging
   int32_t* d_hnode = nullptr;

@@ -183,6 +183,11 @@ cudaError_t launch_to_f64_scaled(int64_t n, const float* x, double scale, double
 cudaError_t launch_boundary_flux(int dim, int64_t n_elem, const int32_t* conn, const uint8_t* level,
                                  const uint8_t* faces, const int32_t* hnode, const int32_t* hpar, const uint8_t* hnp,
                                  const double* U, int face, double* part, double* out, cudaStream_t s);
+// out[f] = integral of field f over the plane x_ax = coord 2^-L (boundary.cu); anchor:
+// element anchors [E][dim] on the device; part: kRedBlocks x 3 partials
+cudaError_t launch_plane_integral(int dim, int L, int64_t n_elem, const int32_t* conn, const uint8_t* level,
+                                  const int32_t* anchor, const int32_t* hnode, const int32_t* hpar, const uint8_t* hnp,
+                                  const double* U, int ax, int64_t coord, double* part, double* out, cudaStream_t s);
 // copy with layout change: [N][dim] <-> [N][3]
 cudaError_t launch_vel_pack(int64_t N, int dim, const double* src, double* dst3, cudaStream_t s);
 cudaError_t launch_vel_unpack(int64_t N, int dim, const double* src3, double* dst, cudaStream_t s);

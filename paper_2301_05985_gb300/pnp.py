@@ -112,6 +112,7 @@ SIGNATURES = {
     "pnp_block_diag": (C.c_int, [_vp, _vp, _vp]),
     "pnp_block_diag_f32": (C.c_int, [_vp, _vp, _vp]),
     "pnp_boundary_flux": (C.c_int, [_vp, _vp, C.c_int, _vp]),
+    "pnp_plane_average": (C.c_int, [_vp, _vp, C.c_int, _i64, _vp]),
     "pnp_norm2": (C.c_int, [_vp, _vp, _i64, _P(_d)]),
     "pnp_gmres": (C.c_int, [_vp, _vp, _vp, _vp, _d, C.c_int, _P(pnp_solve_stats)]),
     "pnp_newton_solve": (C.c_int, [_vp, _P(pnp_solve_stats)]),
@@ -344,6 +345,17 @@ class Context:
         on the unit domain."""
         f = self.boundary_flux(U, face)
         return -(f[0] - f[1])
+
+    def plane_average(self, U, axis: int, coord: int) -> np.ndarray:
+        """Averages of (c+, c-, phi) over the plane x_axis = coord 2^-max_level."""
+        out = np.zeros(3)
+        check(lib().pnp_plane_average(self.h, _ptr(U), int(axis), int(coord), out.ctypes.data))
+        return out
+
+    def averaged_profile(self, U, axis: int, coords) -> np.ndarray:
+        """[len(coords)][3] plane averages along `axis` (the x-averaged profiles of
+        Sec. 5.2 when `axis` is the wall-normal axis and `coords` its node levels)."""
+        return np.array([self.plane_average(U, axis, int(z)) for z in coords])
 
     def norm2(self, x) -> float:
         r = C.c_double()

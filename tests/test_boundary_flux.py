@@ -45,3 +45,37 @@ def test_flux_through_an_identified_face_is_zero():
     assert np.array_equal(om.boundary_flux(U, 0), [0.0, 0.0])
     assert np.array_equal(om.boundary_flux(U, 1), [0.0, 0.0])
     assert np.any(om.boundary_flux(U, 3) != 0.0)
+
+
+# ------------------------------------------------------------------ plane averages
+@pytest.mark.parametrize("dim", [2, 3])
+def test_plane_average_of_linear_fields_is_exact(dim):
+    """On every node level of a 2:1 octree (planes through element sides and through the
+    middle of coarse elements), the plane average of a field linear in the normal
+    coordinate is its value there, and of a field linear in a tangential coordinate the
+    value at the middle."""
+    oc = W.random_balanced_octants(dim, 2, 5 if dim == 2 else 4, 0.3, 12)
+    om = O.OracleMesh(oc)
+    L = oc.max_level
+    size = 1 << L
+    z = om.ijk[:, dim - 1].astype(np.float64) / size
+    x = om.ijk[:, 0].astype(np.float64) / size
+    bcs = W.all_natural_bcs(dim)
+    p = O.Params(eps=0.1, dt=0.1, bc_type=bcs.types, bc_val=bcs.values)
+    U = om.make_consistent(np.stack([1.3 + 0.7 * z, 2.0 - 0.5 * x, -1.0 + 3.0 * z], axis=1), p)
+    levels = np.unique(om.ijk[:, dim - 1])
+    assert len(levels) > (1 << 2) + 1  # finer levels than the base grid
+    for zl in levels:
+        zz = zl / size
+        got = om.plane_integral(U, dim - 1, int(zl))
+        assert np.allclose(got, [1.3 + 0.7 * zz, 2.0 - 0.25, -1.0 + 3.0 * zz], rtol=1e-13, atol=1e-13), zl
+
+
+def test_plane_average_over_a_period():
+    """sin(2 pi x) sampled on a uniform periodic grid: its Q1 interpolant averages to 0."""
+    oc = W.with_periodic(W.uniform_octants(2, 4), 1)
+    om = O.OracleMesh(oc)
+    x = om.ijk[:, 0].astype(np.float64) / (1 << 4)
+    U = np.stack([np.sin(2 * np.pi * x), 1.0 + np.cos(2 * np.pi * x), x * 0], axis=1)
+    for yl in range(0, 17, 5):
+        assert np.allclose(om.plane_integral(U, 1, yl), [0.0, 1.0, 0.0], atol=1e-14)

@@ -32,3 +32,22 @@ def test_boundary_flux_matches_oracle(case):
     top = 2 * oc.dim - 1
     f = P.om.boundary_flux(Uo, top)
     assert abs(P.ctx.boundary_current(Ud, top) + (f[0] - f[1])) <= 1e-12 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_plane_average_matches_oracle(case):
+    _, oc, bcs = case
+    P = Pair(oc, dict(eps=0.02, dt=0.01), bcs)
+    U = W.random_state(P.mesh.ijk, oc.max_level, 9)
+    Ud, Uo = P.dev(U), P.to_ora(U)
+    size = 1 << oc.max_level
+    for axis in range(oc.dim):
+        coords = np.unique(P.mesh.ijk[:, axis])
+        if not (oc.periodic >> axis) & 1:
+            assert coords[-1] == size
+        for zl in coords:
+            got = P.ctx.plane_average(Ud, axis, int(zl))
+            ref = P.om.plane_integral(Uo, axis, int(zl))
+            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (axis, zl)
+    prof = P.ctx.averaged_profile(Ud, oc.dim - 1, np.unique(P.mesh.ijk[:, oc.dim - 1]))
+    assert prof.shape[1] == 3 and np.all(np.isfinite(prof))
