@@ -391,6 +391,8 @@ void pnp_ctx_destroy(pnp_ctx* c) {
     cudaEventDestroy(pe.second.second);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->inner_exec) cudaGraphExecDestroy(c->inner_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   free_ctx_memory(c);
   delete c;
 }

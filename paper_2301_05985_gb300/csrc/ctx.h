@@ -63,6 +63,14 @@ struct pnp_ctx {
   float4* JV4 = nullptr;    // [N] padded FP32 J V accumulator
   float4* qp32 = nullptr;   // [4][2^dim E] stored Gauss-point linearisation of the FP32 J V
   bool lin_user = false;    // qp32 holds the linearisation of the last pnp_linearize
+  // the inner FP32 GMRES captured as a CUDA graph (replayed while profiling is off): the
+  // launches depend only on the key below, captured on a stream of the context's own
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t inner_exec = nullptr;
+  std::vector<unsigned char> inner_key;
+  int64_t inner_graph_launches = 0;  // kernels one replay runs
+  bool inner_eager_done = false;     // one eager solve ran (launchers' one-time set-up done)
+  bool inner_graph_off = false;      // a capture was refused: eager from then on
   int64_t basis_bytes = 0;
 
   // statistics of the last solve (for the time stepper)

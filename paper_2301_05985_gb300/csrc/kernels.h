@@ -39,6 +39,9 @@ struct RowArgs {
 
 // Counts every kernel the library launches (read by pnp_kernel_launches).
 void note_launch();
+// adds n launches (a replayed graph's kernels) and reads the counter
+void note_launches(int64_t n);
+int64_t launch_count();
 
 // Arguments of the shared-memory patch kernels (residual / Jv over Morton patches).
 template <typename T>

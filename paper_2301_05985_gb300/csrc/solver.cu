@@ -290,7 +290,11 @@ int ctx_jv32_linearized(pnp_ctx* c, const float* V, float* JV) {
 // z = P(u): d steps of right-preconditioned FP32 GMRES on (J M^-1) t = u from t = 0, then
 // z = M^-1 t (M: the block diagonal).  A fixed number of steps with the Hessenberg
 // bookkeeping on the device: no host round trip.  P is homogeneous, P(a u) = a P(u).
-static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_state) {
+// d steps of the inner solve on the basis row Q_0 already written: normalisation,
+// Arnoldi with the device-side bookkeeping, and t = sum_i y_i q_i into c->JV32.  Every
+// launch depends only on the context's buffers, sizes and parameters (no host round
+// trip), so the sequence can be captured as a graph.
+static int inner_gmres32_body(pnp_ctx* c, bool from_state) {
   const int d = c->prm.gmres_inner;
   const int64_t n = c->n3(), N = c->n_nodes, ldq = c->ldq;
   cudaStream_t s = c->stream;
@@ -301,7 +305,6 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_stat
   double* dd = dinv + (d + 2);                   // [d+1] projections
   double* coef = dd + (d + 2);                   // [d] combination coefficients
   float* inv_s = c->iinv;
-  CK(launch_to_f32(n, u, Q, s));
   {
     ProfScope ps(c, PNP_PROF_INNER, 4.0 * n, 2.0 * n);
     CK(launch_multi_axpy_norm_f32(ldq, 0, Q, ldq, dd, dinv, Q, c->part, s));
@@ -333,6 +336,115 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_stat
   }
   CK(launch_inner_lsq(d, sv, sc, coef, s));
   CK(launch_combine_f32(n, d, Q, ldq, coef, c->JV32, s));
+  return PNP_OK;
+}
+
+// what the captured inner solve depends on: sizes, buffers, parameters, boundary table
+static std::vector<unsigned char> inner_graph_key(const pnp_ctx* c, bool from_state) {
+  struct Key {
+    int d, dim, from_state, pad, use_patches, steady;
+    int64_t n_nodes, n_elem, ldq;
+    const void* bufs[14];
+    double phys[4];
+    double bc_val[6][3];
+    uint8_t dir_faces[4];
+  } k;
+  std::memset(&k, 0, sizeof(k));
+  k.d = c->prm.gmres_inner;
+  k.dim = c->dim;
+  k.from_state = from_state;
+  k.pad = element_kernel_is_lanes();
+  k.use_patches = c->use_patches;
+  k.n_nodes = c->n_nodes;
+  k.n_elem = c->n_elem;
+  k.ldq = c->ldq;
+  const void* b[14] = {c->Qin, c->isc, c->iinv, c->Dinv32, c->V4, c->JV4, c->qp32, c->part, c->JV32,
+                       c->V32, c->U32, c->hs32, c->adv32, c->rec32};
+  std::memcpy(k.bufs, b, sizeof(b));
+  const PhysParams P = c->phys();
+  k.phys[0] = P.eps2x2;
+  k.phys[1] = P.kappa;
+  k.phys[2] = P.tau_t;
+  k.phys[3] = P.C_I;
+  k.steady = P.steady;
+  const BcTable bc = c->bc_table();
+  for (int f = 0; f < 3; ++f) k.dir_faces[f] = bc.dir_faces[f];
+  for (int face = 0; face < 6; ++face)
+    for (int f = 0; f < 3; ++f) k.bc_val[face][f] = bc.val[face][f];
+  std::vector<unsigned char> v(sizeof(k));
+  std::memcpy(v.data(), &k, sizeof(k));
+  return v;
+}
+
+// replays of the captured inner solve while profiling is off (the per-kernel event pairs
+// of the profile need eager launches); PNP_INNER_GRAPH=0 turns the graph off
+static bool inner_graph_enabled(const pnp_ctx* c) {
+  static const bool env_off = [] {
+    const char* e = getenv("PNP_INNER_GRAPH");
+    return e && std::strcmp(e, "0") == 0;
+  }();
+  return !env_off && !c->prof_on && c->inner_eager_done && !c->inner_graph_off;
+}
+
+// true when the graph was captured; on false the caller runs the solve eagerly (a capture
+// that the runtime refuses turns the graph off for the context, with no error latched)
+static bool inner_graph_capture(pnp_ctx* c, bool from_state) {
+  if (c->inner_exec) {
+    cudaGraphExecDestroy(c->inner_exec);
+    c->inner_exec = nullptr;
+  }
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+    c->inner_graph_off = true;
+    return false;
+  }
+  cudaStream_t saved = c->stream;
+  const cudaError_t latched0 = c->latched;
+  c->stream = c->cap_stream;
+  const int64_t l0 = launch_count();
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  int rc = e == cudaSuccess ? inner_gmres32_body(c, from_state) : PNP_OK;
+  cudaGraph_t g = nullptr;
+  if (e == cudaSuccess) {
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  c->stream = saved;
+  if (rc == PNP_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->inner_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  // the capture counted its launches once; replays add them per run
+  c->inner_graph_launches = launch_count() - l0;
+  note_launches(-c->inner_graph_launches);
+  if (rc != PNP_OK || e != cudaSuccess) {
+    cudaGetLastError();
+    if (c->inner_exec) cudaGraphExecDestroy(c->inner_exec);
+    c->inner_exec = nullptr;
+    c->inner_graph_off = true;
+    c->latched = latched0;  // a refused capture is not a device error
+    return false;
+  }
+  c->inner_key = inner_graph_key(c, from_state);
+  return true;
+}
+
+// z = P(u): d steps of right-preconditioned FP32 GMRES on (J M^-1) t = u from t = 0, then
+// z = M^-1 t (M: the block diagonal).  A fixed number of steps with the Hessenberg
+// bookkeeping on the device: no host round trip.  P is homogeneous, P(a u) = a P(u).
+static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_state) {
+  const int64_t n = c->n3(), N = c->n_nodes;
+  cudaStream_t s = c->stream;
+  CK(launch_to_f32(n, u, c->Qin, s));
+  bool replay = inner_graph_enabled(c);
+  if (replay && (!c->inner_exec || c->inner_key != inner_graph_key(c, from_state)))
+    replay = inner_graph_capture(c, from_state);
+  if (replay) {
+    CK(cudaGraphLaunch(c->inner_exec, s));
+    note_launches(c->inner_graph_launches);
+  } else {
+    RC(inner_gmres32_body(c, from_state));
+    c->inner_eager_done = true;
+  }
   ProfScope ps(c, PNP_PROF_PRECOND, 60.0 * N, 18.0 * N);
   CK(launch_block_apply32(N, c->Dinv32, c->JV32, nullptr, z32, s));
   return PNP_OK;
