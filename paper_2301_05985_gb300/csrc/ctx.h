@@ -69,6 +69,7 @@ struct pnp_ctx {
   cudaGraphExec_t inner_exec = nullptr;
   std::vector<unsigned char> inner_key;
   int64_t inner_graph_launches = 0;  // kernels one replay runs
+  int inner_graph_jv = 0;            // J V applications one replay runs
   bool inner_eager_done = false;     // one eager solve ran (launchers' one-time set-up done)
   bool inner_graph_off = false;      // a capture was refused: eager from then on
   int64_t basis_bytes = 0;

@@ -403,6 +403,7 @@ static bool inner_graph_capture(pnp_ctx* c, bool from_state) {
   const cudaError_t latched0 = c->latched;
   c->stream = c->cap_stream;
   const int64_t l0 = launch_count();
+  const int jv0 = c->jv_count;
   cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
   int rc = e == cudaSuccess ? inner_gmres32_body(c, from_state) : PNP_OK;
   cudaGraph_t g = nullptr;
@@ -413,9 +414,11 @@ static bool inner_graph_capture(pnp_ctx* c, bool from_state) {
   c->stream = saved;
   if (rc == PNP_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->inner_exec, g, 0);
   if (g) cudaGraphDestroy(g);
-  // the capture counted its launches once; replays add them per run
+  // the capture counted its launches and J V calls once; replays add them per run
   c->inner_graph_launches = launch_count() - l0;
   note_launches(-c->inner_graph_launches);
+  c->inner_graph_jv = c->jv_count - jv0;
+  c->jv_count = jv0;
   if (rc != PNP_OK || e != cudaSuccess) {
     cudaGetLastError();
     if (c->inner_exec) cudaGraphExecDestroy(c->inner_exec);
@@ -441,6 +444,7 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_stat
   if (replay) {
     CK(cudaGraphLaunch(c->inner_exec, s));
     note_launches(c->inner_graph_launches);
+    c->jv_count += c->inner_graph_jv;
   } else {
     RC(inner_gmres32_body(c, from_state));
     c->inner_eager_done = true;
