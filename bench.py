@@ -375,6 +375,7 @@ def main():
     if dist:
         dist.barrier()
     launches0 = pnp.kernel_launches()
+    captures0 = pnp.graph_captures()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -385,6 +386,7 @@ def main():
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     launches = pnp.kernel_launches() - launches0
+    captures = pnp.graph_captures() - captures0
     # per-class kernel times: K further steps with the library's event pair around every
     # launch (eager launches: the inner solve's graph replays only while profiling is off)
     ctx.profile_enable(True)
@@ -408,6 +410,7 @@ def main():
         ctx.get_field(pnp.PNP_FIELD_U_PREV, hU[0], pnp.PNP_HOST)
         ctx.get_field(pnp.PNP_FIELD_U_PREV2, hU[1], pnp.PNP_HOST)
         torch.cuda.synchronize()
+        c_e2e0 = pnp.graph_captures()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ctx.set_field(pnp.PNP_FIELD_U_PREV, hU[0], pnp.PNP_HOST)
@@ -416,9 +419,10 @@ def main():
             ctx.get_field(pnp.PNP_FIELD_U, hU[2], pnp.PNP_HOST)
             hU = [hU[2], hU[0], hU[1]]
         t_e2e = time.perf_counter() - t0
+        e2e_captures = pnp.graph_captures() - c_e2e0
         e2e = {"value": 3.0 * N * args.steps * world / t_e2e / 1e9, "unit": "GDoF/s",
                "h2d_bytes_per_step": 2 * 24 * N, "d2h_bytes_per_step": 24 * N,
-               "ms_per_step": 1e3 * t_e2e / args.steps}
+               "ms_per_step": 1e3 * t_e2e / args.steps, "graph_captures": e2e_captures}
 
     # plain-mode comparison: one step from the state the timed mixed steps started from
     plain = None
@@ -475,6 +479,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
+        "graph_captures": int(captures),
         "launches_before_timed": int(launches0),
         "clocks": clk.summary(),
         "newton_its_per_step": nt / args.steps, "krylov_its_per_step": kt / args.steps,

@@ -391,8 +391,12 @@ int pnp_profile_enable(pnp_ctx* c, int on);
  * profiling was enabled; synchronises the stream.  Any output pointer may be NULL. */
 int pnp_profile_read(pnp_ctx* c, int kind, double* total_ms, int64_t* count, double* alg_bytes,
                      double* alg_flops);
-/* Kernels launched by this process through the library since it was loaded. */
+/* Kernels launched by this process through the library since it was loaded (a graph
+ * replay counts the kernels it runs). */
 int64_t pnp_kernel_launches(void);
+/* Captures of the inner Krylov solve as a CUDA graph since the library was loaded (one
+ * per change of its sizes, buffers or parameters; replays run while profiling is off). */
+int64_t pnp_graph_captures(void);
 
 #ifdef __cplusplus
 }

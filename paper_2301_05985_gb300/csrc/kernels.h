@@ -42,6 +42,8 @@ void note_launch();
 // adds n launches (a replayed graph's kernels) and reads the counter
 void note_launches(int64_t n);
 int64_t launch_count();
+// counts a capture of the inner solve (read by pnp_graph_captures)
+void note_capture();
 
 // Arguments of the shared-memory patch kernels (residual / Jv over Morton patches).
 template <typename T>

@@ -428,6 +428,7 @@ static bool inner_graph_capture(pnp_ctx* c, bool from_state) {
     return false;
   }
   c->inner_key = inner_graph_key(c, from_state);
+  note_capture();
   return true;
 }
 

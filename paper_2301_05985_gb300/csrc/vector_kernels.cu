@@ -11,6 +11,9 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(); }
 extern "C" int64_t pnp_kernel_launches(void) { return g_launches.load(); }
+static std::atomic<int64_t> g_captures{0};
+void note_capture() { g_captures.fetch_add(1, std::memory_order_relaxed); }
+extern "C" int64_t pnp_graph_captures(void) { return g_captures.load(); }
 
 namespace {
 

@@ -122,6 +122,7 @@ SIGNATURES = {
     "pnp_profile_enable": (C.c_int, [_vp, C.c_int]),
     "pnp_profile_read": (C.c_int, [_vp, C.c_int, _P(_d), _P(_i64), _P(_d), _P(_d)]),
     "pnp_kernel_launches": (_i64, []),
+    "pnp_graph_captures": (_i64, []),
     "pnp_mlp_init": (C.c_int, [_vp, C.c_uint64]),
     "pnp_mlp_set_weights": (C.c_int, [_vp, _vp, _i64]),
     "pnp_mlp_get_weights": (C.c_int, [_vp, _vp, _i64]),
@@ -454,3 +455,7 @@ class Context:
 
 def kernel_launches() -> int:
     return int(lib().pnp_kernel_launches())
+
+
+def graph_captures() -> int:
+    return int(lib().pnp_graph_captures())
