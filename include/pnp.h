@@ -215,7 +215,8 @@ int pnp_jv(pnp_ctx* c, const double* U, const void* V, void* JV, int precision);
  * evaluates at U (device FP64 [n][3]), with the context's history, advection, parameters
  * and boundary conditions at this call, the state's quantities at every element's
  * Gauss points that J V needs (Def. 3 linearised: v, grad phi, grad c+-, tau_c and
- * z (c - tau_c R) per Gauss point, FP32, 64 B each, held by the context).
+ * z (c - tau_c R) per Gauss point, FP32, 64 B each, held by the context; 48 B when the
+ * advection field is zero: v and tau_c are then not stored, tau_c follows from the level).
  * pnp_jv_linearized then returns JV = J V for FP32 device vectors V, JV [n][3], equal to
  * pnp_jv(..., PNP_F32) at that U up to FP32 summation order.  A later solver call
  * (pnp_gmres, pnp_newton_solve, pnp_time_step) replaces the stored linearisation;

@@ -63,6 +63,7 @@ struct pnp_ctx {
   float4* JV4 = nullptr;    // [N] padded FP32 J V accumulator
   float4* qp32 = nullptr;   // [4][2^dim E] stored Gauss-point linearisation of the FP32 J V
   bool lin_user = false;    // qp32 holds the linearisation of the last pnp_linearize
+  int lin_rows = 4;         // float4 rows per lane in qp32 (3 without advection)
   // the inner FP32 GMRES captured as a CUDA graph (replayed while profiling is off): the
   // launches depend only on the key below, captured on a stream of the context's own
   cudaStream_t cap_stream = nullptr;

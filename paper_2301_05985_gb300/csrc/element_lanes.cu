@@ -397,14 +397,17 @@ __global__ void __launch_bounds__(256, lane_min_blocks<T, C>()) k_element_lanes(
 
 // ---- FP32 J V from a stored linearisation ---------------------------------------
 // Inside one Krylov solve the state (U, h, v) is fixed, so the Gauss-point quantities J V
-// needs from it are computed once per solve and stored per lane, four float4 in
-// lane-major order (qp[j * L + t], L = 2^d E): (v0 v1 v2 gp0) (gp1 gp2 gc+0 gc+1)
-// (gc+2 gc-0 gc-1 gc-2) (tau, z+(c+ - tau R+), z-(c- - tau R-), level) with the element's
-// level as integer bits.  Each J V then reads 64 B per lane, coalesced, instead of
-// gathering and interpolating the state.
+// needs from it are computed once per solve and stored per lane, NR float4 in lane-major
+// order (qp[j * L + t], L = 2^d E).  With advection (NR = 4): (v0 v1 v2 gp0)
+// (gp1 gp2 gc+0 gc+1) (gc+2 gc-0 gc-1 gc-2) (tau, z+(c+ - tau R+), z-(c- - tau R-), level).
+// Without (the advection field is zero, NR = 3): (gp0 gp1 gp2 gc+0) (gc+1 gc+2 gc-0 gc-1)
+// (gc-2, z+(c+ - tau R+), z-(c- - tau R-), level), and tau = (4/dt^2 + C_I d (2/h)^4)^(-1/2)
+// is recomputed from the level (the same FP32 value: |v|^2 = 0).  The level is stored as
+// integer bits.  Each J V then reads 16 NR bytes per lane, coalesced, instead of gathering
+// and interpolating the state.
 constexpr int kLaneThreads = 256;
 
-template <int D>
+template <int D, int NR>
 __global__ void __launch_bounds__(kLaneThreads, 5) k_lane_state(ElemArgs<float> A, LaneParams<float> K, float4* qp) {
   constexpr int NC = 1 << D;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -428,10 +431,16 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_lane_state(ElemArgs<float> 
   if (!valid) return;
   const int64_t L = A.n_elem * NC;
   const float zc0 = cv[0] - tau * R[0], zc1 = -(cv[1] - tau * R[1]);
-  qp[t] = make_float4(v[0], v[1], v[2], gp[0]);
-  qp[L + t] = make_float4(gp[1], gp[2], gc[0][0], gc[0][1]);
-  qp[2 * L + t] = make_float4(gc[0][2], gc[1][0], gc[1][1], gc[1][2]);
-  qp[3 * L + t] = make_float4(tau, zc0, zc1, __int_as_float(lev));
+  if constexpr (NR == 4) {
+    qp[t] = make_float4(v[0], v[1], v[2], gp[0]);
+    qp[L + t] = make_float4(gp[1], gp[2], gc[0][0], gc[0][1]);
+    qp[2 * L + t] = make_float4(gc[0][2], gc[1][0], gc[1][1], gc[1][2]);
+    qp[3 * L + t] = make_float4(tau, zc0, zc1, __int_as_float(lev));
+  } else {
+    qp[t] = make_float4(gp[0], gp[1], gp[2], gc[0][0]);
+    qp[L + t] = make_float4(gc[0][1], gc[0][2], gc[1][0], gc[1][1]);
+    qp[2 * L + t] = make_float4(gc[1][2], zc0, zc1, __int_as_float(lev));
+  }
 }
 
 // The J V kernel streams the stored state through shared memory: a persistent grid
@@ -442,7 +451,9 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_lane_state(ElemArgs<float> 
 // atomics of the tile before.  Two stages with five blocks per SM measured fastest: three
 // (four blocks per SM) and four (three) were 6% and 16% slower per launch.
 constexpr int kStages = 2;
-constexpr size_t jv_stage_bytes(int S) { return (size_t)S * (4 * kLaneThreads * 16 + kLaneThreads * 4 + 8); }
+constexpr size_t jv_stage_bytes(int S, int NR) {
+  return (size_t)S * ((size_t)NR * kLaneThreads * 16 + kLaneThreads * 4 + 8);
+}
 constexpr int kWaitPolls = 1 << 22;  // try_wait polls before a wait gives up (about a second)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -476,15 +487,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-template <int D, int NS>
+template <int D, int NS, int NR>
 __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<float> A, LaneParams<float> K,
                                                                  const float4* __restrict__ qp, int* err) {
   constexpr int NC = 1 << D;
   extern __shared__ __align__(128) uint8_t jv_smem[];
-  // NS stages of {four state rows, connectivity} and NS mbarriers (jv_stage_bytes(NS))
-  auto sq = reinterpret_cast<float4(*)[4][kLaneThreads]>(jv_smem);
-  auto sconn = reinterpret_cast<int32_t(*)[kLaneThreads]>(jv_smem + NS * 4 * kLaneThreads * sizeof(float4));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(jv_smem + NS * (4 * kLaneThreads * sizeof(float4) + kLaneThreads * 4));
+  // NS stages of {NR state rows, connectivity} and NS mbarriers (jv_stage_bytes(NS, NR))
+  auto sq = reinterpret_cast<float4(*)[NR][kLaneThreads]>(jv_smem);
+  auto sconn = reinterpret_cast<int32_t(*)[kLaneThreads]>(jv_smem + NS * NR * kLaneThreads * sizeof(float4));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(jv_smem + NS * (NR * kLaneThreads * sizeof(float4) + kLaneThreads * 4));
   const int tid = threadIdx.x;
   const int64_t L = A.n_elem * NC;
   const int64_t n_tiles = (L + kLaneThreads - 1) / kLaneThreads;
@@ -494,9 +505,9 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
   auto issue = [&](int64_t tl, int st) {
     const int64_t t0 = tl * kLaneThreads;
     const uint32_t n = (uint32_t)(L - t0 < kLaneThreads ? L - t0 : kLaneThreads);
-    mbar_expect_tx(&bar[st], 4u * 16u * n + 4u * n);
+    mbar_expect_tx(&bar[st], (uint32_t)NR * 16u * n + 4u * n);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bulk_g2s(&sq[st][j][0], qp + j * L + t0, 16u * n, &bar[st]);
+    for (int j = 0; j < NR; ++j) bulk_g2s(&sq[st][j][0], qp + j * L + t0, 16u * n, &bar[st]);
     bulk_g2s(&sconn[st][0], A.conn + t0, 4u * n, &bar[st]);
   };
   if (tid == 0) {
@@ -542,7 +553,7 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
       q0 = sq[st][0][tid];
       q1 = sq[st][1][tid];
       q2 = sq[st][2][tid];
-      q3 = sq[st][3][tid];
+      if constexpr (NR == 4) q3 = sq[st][NR - 1][tid];
       id = sconn[st][tid];
     }
     __syncthreads();  // stage st is read: refill it with the tile NS ahead
@@ -556,15 +567,31 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
     }
 
     const int c = (int)(t & (NC - 1));
-    const int lev = __float_as_int(q3.w);  // 0 for lanes past the end
+    float v[3], gp[3], gc[2][3], tau, zc_tR[2];
+    int lev;
+    if constexpr (NR == 4) {
+      lev = __float_as_int(q3.w);  // 0 for lanes past the end
+      v[0] = q0.x; v[1] = q0.y; v[2] = q0.z;
+      gp[0] = q0.w; gp[1] = q1.x; gp[2] = q1.y;
+      gc[0][0] = q1.z; gc[0][1] = q1.w; gc[0][2] = q2.x;
+      gc[1][0] = q2.y; gc[1][1] = q2.z; gc[1][2] = q2.w;
+      tau = q3.x;
+      zc_tR[0] = q3.y; zc_tR[1] = q3.z;
+    } else {
+      lev = __float_as_int(q2.w);
+      v[0] = v[1] = v[2] = 0.0f;
+      gp[0] = q0.x; gp[1] = q0.y; gp[2] = q0.z;
+      gc[0][0] = q0.w; gc[0][1] = q1.x; gc[0][2] = q1.y;
+      gc[1][0] = q1.z; gc[1][1] = q1.w; gc[1][2] = q2.x;
+      zc_tR[0] = q2.y; zc_tR[1] = q2.z;
+      const float G2 = pow2i(2 * lev + 2, 0.0f);
+      tau = rsqrtf(fmaf(K.cid * G2, G2, K.tau_t));
+    }
     const float inv_h = pow2i(lev, 0.0f);
     const float w = pow2i(-D * (lev + 1), 0.0f);
     float sh[3];
 #pragma unroll
     for (int kk = 0; kk < 3; ++kk) sh[kk] = ((c >> kk) & 1) ? inv_h : -inv_h;
-    const float v[3] = {q0.x, q0.y, q0.z}, gp[3] = {q0.w, q1.x, q1.y};
-    const float gc[2][3] = {{q1.z, q1.w, q2.x}, {q2.y, q2.z, q2.w}};
-    const float tau = q3.x, zc_tR[2] = {q3.y, q3.z};
     float dn[3];
     if (A.V4) load_dir4(A, id, valid, dn);
     else load_node<float, 3>(A, id, valid, A.V, 3, dn);
@@ -876,34 +903,40 @@ cudaError_t launch_residual_df(int dim, const ElemArgs<double>& A, cudaStream_t 
 }
 
 // the stored linearisation of the FP32 J V (qp: 4 * 2^dim * n_elem float4; A.rec set)
-cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, cudaStream_t s) {
+cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, int rows, cudaStream_t s) {
   if (A.n_elem == 0) return cudaSuccess;
+  if (rows != 3 && rows != 4) return cudaErrorInvalidValue;
   const LaneParams<float> K{float(A.P.kappa), float(A.P.tau_t), float(A.P.C_I * dim), float(A.P.eps2x2)};
   const unsigned blocks = (unsigned)(((A.n_elem << dim) + kLaneThreads - 1) / kLaneThreads);
-  if (dim == 2) k_lane_state<2><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
-  else k_lane_state<3><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+  if (dim == 2) {
+    if (rows == 4) k_lane_state<2, 4><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+    else k_lane_state<2, 3><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+  } else {
+    if (rows == 4) k_lane_state<3, 4><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+    else k_lane_state<3, 3><<<blocks, kLaneThreads, 0, s>>>(A, K, qp);
+  }
   note_launch();
   return cudaGetLastError();
 }
 
-template <int S>
+template <int S, int NR>
 static cudaError_t launch_jv_stages(int dim, const ElemArgs<float>& A, const LaneParams<float>& K, const float4* qp,
                                     int* err, cudaStream_t s) {
   // persistent grid: the resident blocks of every SM, no more than there are tiles
   static int per_sm[2] = {0, 0}, n_sm = 0;
-  const size_t smem = jv_stage_bytes(S);
+  const size_t smem = jv_stage_bytes(S, NR);
   if (n_sm == 0) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_jv_from_state<2, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(k_jv_from_state<2, S, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_jv_from_state<3, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(k_jv_from_state<3, S, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_jv_from_state<2, S>, kLaneThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_jv_from_state<2, S, NR>, kLaneThreads, smem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_jv_from_state<3, S>, kLaneThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_jv_from_state<3, S, NR>, kLaneThreads, smem);
     if (e != cudaSuccess) {
       n_sm = 0;
       return e;
@@ -911,15 +944,18 @@ static cudaError_t launch_jv_stages(int dim, const ElemArgs<float>& A, const Lan
   }
   const int64_t tiles = ((A.n_elem << dim) + kLaneThreads - 1) / kLaneThreads;
   const unsigned blocks = (unsigned)std::min<int64_t>(tiles, (int64_t)n_sm * std::max(1, per_sm[dim - 2]));
-  if (dim == 2) k_jv_from_state<2, S><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err);
-  else k_jv_from_state<3, S><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err);
+  if (dim == 2) k_jv_from_state<2, S, NR><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err);
+  else k_jv_from_state<3, S, NR><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err);
   return cudaSuccess;
 }
 
-cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int* err, cudaStream_t s) {
+cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int rows, int* err,
+                                 cudaStream_t s) {
   if (A.n_elem == 0) return cudaSuccess;
+  if (rows != 3 && rows != 4) return cudaErrorInvalidValue;
   const LaneParams<float> K{float(A.P.kappa), float(A.P.tau_t), float(A.P.C_I * dim), float(A.P.eps2x2)};
-  const cudaError_t e = launch_jv_stages<kStages>(dim, A, K, qp, err, s);
+  const cudaError_t e = rows == 4 ? launch_jv_stages<kStages, 4>(dim, A, K, qp, err, s)
+                                  : launch_jv_stages<kStages, 3>(dim, A, K, qp, err, s);
   if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();

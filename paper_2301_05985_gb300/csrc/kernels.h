@@ -84,11 +84,13 @@ bool residual_double_float();
 // element formulation
 constexpr double kDfFlopsPerFlop = 15.0;
 // FP32 J V from a stored linearisation (element_lanes.cu): launch_lane_state computes, per
-// element lane, the state's Gauss-point quantities J V needs (qp: 4 * 2^dim * n_elem float4,
-// A.rec set); launch_jv_from_state applies J V with them (A.V or A.V4, A.out or A.out4;
-// qp and A.conn 16-byte aligned).  err[0] |= 1 when a staged copy's wait gave up.
-cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, cudaStream_t s);
-cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int* err, cudaStream_t s);
+// element lane, the state's Gauss-point quantities J V needs (qp: rows * 2^dim * n_elem
+// float4, A.rec set; rows = 4, or 3 when the advection field is zero); launch_jv_from_state
+// applies J V with them (A.V or A.V4, A.out or A.out4; qp and A.conn 16-byte aligned).
+// err[0] |= 1 when a staged copy's wait gave up.
+cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, int rows, cudaStream_t s);
+cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int rows, int* err,
+                                 cudaStream_t s);
 double jv_from_state_flops(int dim);
 // Dout [N][9] += the 3x3 diagonal blocks of the Jacobian (lane-group kernel; Dout zeroed
 // first, Dirichlet and hanging rows left to launch_diag_rows)

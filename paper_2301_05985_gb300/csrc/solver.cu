@@ -257,9 +257,10 @@ static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_stat
     A.out4 = c->JV4;
     if (from_state) {
       // direction in, result out (12 B per node each), the stored state (64 B per lane)
-      ProfScope ps(c, PNP_PROF_JV32, 24.0 * c->n_nodes + 64.0 * (double)(c->n_elem << c->dim) + c->conn_bytes(),
+      ProfScope ps(c, PNP_PROF_JV32,
+                   24.0 * c->n_nodes + 16.0 * c->lin_rows * (double)(c->n_elem << c->dim) + c->conn_bytes(),
                    jv_from_state_flops(c->dim) * c->n_elem);
-      CK(launch_jv_from_state(c->dim, A, c->qp32, c->dflag + 1, c->stream));
+      CK(launch_jv_from_state(c->dim, A, c->qp32, c->lin_rows, c->dflag + 1, c->stream));
     } else {
       ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(),
                    element_kernel_flops(c->dim, true) * c->n_elem);
@@ -273,10 +274,15 @@ static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_stat
 
 // Gauss-point linearisation of the FP32 J V at the prepared FP32 state (ctx_prepare_f32)
 int ctx_linearize32(pnp_ctx* c) {
+  // a zero advection field (pure PNP) leaves v out of the stored state: three rows
+  double vn = 0.0;
+  RC(ctx_norm(c, c->adv, &vn));
+  c->lin_rows = vn == 0.0 ? 3 : 4;
   ElemArgs<float> A = elem_args<float>(c, c->U32, nullptr, c->hs32, c->adv32, nullptr);
   A.rec = c->rec32;
-  ProfScope ps(c, PNP_PROF_PRECOND, 32.0 * c->n_nodes + 64.0 * (double)(c->n_elem << c->dim) + c->conn_bytes());
-  CK(launch_lane_state(c->dim, A, c->qp32, c->stream));
+  ProfScope ps(c, PNP_PROF_PRECOND,
+               32.0 * c->n_nodes + 16.0 * c->lin_rows * (double)(c->n_elem << c->dim) + c->conn_bytes());
+  CK(launch_lane_state(c->dim, A, c->qp32, c->lin_rows, c->stream));
   c->lin_user = false;
   return PNP_OK;
 }
@@ -342,7 +348,7 @@ static int inner_gmres32_body(pnp_ctx* c, bool from_state) {
 // what the captured inner solve depends on: sizes, buffers, parameters, boundary table
 static std::vector<unsigned char> inner_graph_key(const pnp_ctx* c, bool from_state) {
   struct Key {
-    int d, dim, from_state, pad, use_patches, steady;
+    int d, dim, from_state, pad, use_patches, steady, lin_rows;
     int64_t n_nodes, n_elem, ldq;
     const void* bufs[14];
     double phys[4];
@@ -355,6 +361,7 @@ static std::vector<unsigned char> inner_graph_key(const pnp_ctx* c, bool from_st
   k.from_state = from_state;
   k.pad = element_kernel_is_lanes();
   k.use_patches = c->use_patches;
+  k.lin_rows = c->lin_rows;
   k.n_nodes = c->n_nodes;
   k.n_elem = c->n_elem;
   k.ldq = c->ldq;
