@@ -245,7 +245,8 @@ int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchor
         }
         par[pc] = m.el_conn[i * nc + corner];
       }
-      std::sort(par, par + npar);
+      for (int x = 1; x < npar; ++x)  // insertion sort of at most four parents
+        for (int y = x; y > 0 && par[y - 1] > par[y]; --y) std::swap(par[y - 1], par[y]);
       units[id] += npar;
       lmin[id] = std::min(lmin[id], l);
       lmax[id] = std::max(lmax[id], l);
