@@ -480,6 +480,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": int(launches),
         "graph_captures": int(captures),
+        "graph_captures_total": int(pnp.graph_captures()),
         "launches_before_timed": int(launches0),
         "clocks": clk.summary(),
         "newton_its_per_step": nt / args.steps, "krylov_its_per_step": kt / args.steps,
