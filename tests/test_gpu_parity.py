@@ -235,3 +235,40 @@ def test_bdf_time_steps_match_oracle():
         Ug = P.ctx.get_field(P.pnp.PNP_FIELD_U)
         assert rel_err(P.to_ora(Ug), Uk) <= 1e-9, k
     assert P.ctx.step_count() == 3
+
+
+def test_inner_solve_graph_replay_matches_eager_launches():
+    """The flexible solve's inner FP32 GMRES runs eagerly the first time and while
+    profiling is on, and as a captured CUDA graph otherwise: both solve the same system
+    to the requested tolerance, a replay counts its kernels and J V applications, and a
+    change of the physical parameters triggers a new capture."""
+    P, U, V = _setup(CASES[1], seed=9)
+    P.ctx.set_params(P.pnp.default_params(**P.params_kw, gmres_restart=40, gmres_max_it=4000, gmres_inner=6))
+    b = P.dev(W.random_direction(P.mesh.ijk, P.oc.max_level, 77))
+    Ud = P.dev(U)
+
+    def solve():
+        x = P.torch.zeros_like(Ud)
+        st = P.ctx.gmres(Ud, b, x, 1e-4, P.pnp.PNP_F32)
+        assert st.status == 0
+        return x.cpu().numpy(), st
+
+    P.ctx.profile_enable(True)
+    x_eager, st_e = solve()  # eager: profiling on
+    P.ctx.profile_enable(False)
+    c0 = P.pnp.graph_captures()
+    x1, st1 = solve()  # first unprofiled solve: capture, then replays
+    c1 = P.pnp.graph_captures()
+    l0 = P.pnp.kernel_launches()
+    x2, st2 = solve()  # replays only
+    assert P.pnp.graph_captures() == c1 and c1 == c0 + 1
+    assert P.pnp.kernel_launches() - l0 > 6 * st2.krylov_its  # replays counted
+    assert st2.jv_evals >= 6 * st2.krylov_its
+    for x in (x1, x2):
+        assert rel_err(x, x_eager) <= 1e-3
+    # new parameters (time step size) change the captured kernels' arguments: re-capture
+    p = P.ctx.get_params()
+    p.dt *= 0.5
+    P.ctx.set_params(p)
+    solve()
+    assert P.pnp.graph_captures() == c1 + 1
