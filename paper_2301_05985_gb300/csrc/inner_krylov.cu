@@ -205,33 +205,34 @@ __device__ __forceinline__ InnerScalars inner_scalars(double* base, int d) {
 }
 
 // sum of the norm partials of k_multi_axpy_norm_f32 in a fixed order (one block of 64)
-__device__ __forceinline__ double sum_parts64(const double* __restrict__ part, int nparts, double* sh) {
-  // four independent running sums per thread keep four loads in flight (fixed order)
+// sum of the norm partials by one block of kBookThreads threads: every thread issues its
+// loads at once (at most four), then a fixed-order tree
+constexpr int kBookThreads = 256;
+__device__ __forceinline__ double sum_parts(const double* __restrict__ part, int nparts, double* sh) {
   double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
   int b = threadIdx.x;
-  for (; b + 192 < nparts; b += 256) {
+  for (; b + 3 * kBookThreads < nparts; b += 4 * kBookThreads) {
     t0 += part[b];
-    t1 += part[b + 64];
-    t2 += part[b + 128];
-    t3 += part[b + 192];
+    t1 += part[b + kBookThreads];
+    t2 += part[b + 2 * kBookThreads];
+    t3 += part[b + 3 * kBookThreads];
   }
-  for (; b < nparts; b += 64) t0 += part[b];
-  const double t = (t0 + t1) + (t2 + t3);
-  sh[threadIdx.x] = t;
+  for (; b < nparts; b += kBookThreads) t0 += part[b];
+  sh[threadIdx.x] = (t0 + t1) + (t2 + t3);
   __syncthreads();
-  for (int o = 32; o > 0; o >>= 1) {
+  for (int o = kBookThreads / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
   return sh[0];
 }
 
-__global__ void __launch_bounds__(64) k_inner_start(int d, const double* __restrict__ part, int nparts, double* sv,
-                                                    double* dinv, float* inv_s, double* sc) {
-  __shared__ double sh[64];
+__global__ void __launch_bounds__(kBookThreads) k_inner_start(int d, const double* __restrict__ part, int nparts,
+                                                              double* sv, double* dinv, float* inv_s, double* sc) {
+  __shared__ double sh[kBookThreads];
   const InnerScalars S = inner_scalars(sc, d);
   for (int i = threadIdx.x; i <= d; i += blockDim.x) S.g[i] = 0.0;
-  const double nrm2 = sum_parts64(part, nparts, sh);
+  const double nrm2 = sum_parts(part, nparts, sh);
   if (threadIdx.x == 0) {
     const double s = sqrt(nrm2);
     sv[0] = s;
@@ -243,14 +244,15 @@ __global__ void __launch_bounds__(64) k_inner_start(int d, const double* __restr
 }
 
 // column j: h_i = d_i / s_i (i <= j), h_{j+1} = ||u_{j+1}||; apply the earlier rotations,
-// make rotation j, update g.  One block of kMaxInner threads.
+// make rotation j, update g.  One block of kBookThreads threads (the first kMaxInner hold
+// the column).
 constexpr int kMaxInner = 64;
-__global__ void __launch_bounds__(kMaxInner) k_inner_col(int j, int d, const double* __restrict__ dd,
-                                                         const double* __restrict__ part, int nparts, double* sv,
-                                                         double* dinv, float* inv_s, double* sc) {
-  static_assert(kMaxInner == 64, "the norm partials are summed by one block of 64");
+static_assert(kBookThreads >= kMaxInner, "one thread per column entry");
+__global__ void __launch_bounds__(kBookThreads) k_inner_col(int j, int d, const double* __restrict__ dd,
+                                                            const double* __restrict__ part, int nparts, double* sv,
+                                                            double* dinv, float* inv_s, double* sc) {
   __shared__ double h[kMaxInner + 1];
-  __shared__ double sh[64];
+  __shared__ double sh[kBookThreads];
   __shared__ double cs[kMaxInner], sn[kMaxInner];
   const InnerScalars S = inner_scalars(sc, d);
   const int i = threadIdx.x;
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(kMaxInner) k_inner_col(int j, int d, const dou
     cs[i] = S.cs[i];
     sn[i] = S.sn[i];
   }
-  const double nrm2 = sum_parts64(part, nparts, sh);
+  const double nrm2 = sum_parts(part, nparts, sh);
   if (i == 0) {
     const double s = sqrt(nrm2);
     h[j + 1] = s;
@@ -415,14 +417,14 @@ cudaError_t launch_pack_jv4(const RowArgs& R, const float4* V4, const float4* ac
 
 cudaError_t launch_inner_start(int d, const double* part, double* sv, double* dinv, float* inv_s, double* sc,
                                cudaStream_t s) {
-  k_inner_start<<<1, 64, 0, s>>>(d, part, kUpdBlocks, sv, dinv, inv_s, sc);
+  k_inner_start<<<1, kBookThreads, 0, s>>>(d, part, kUpdBlocks, sv, dinv, inv_s, sc);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_inner_col(int j, int d, const double* dd, const double* part, double* sv, double* dinv, float* inv_s,
                              double* sc, cudaStream_t s) {
-  k_inner_col<<<1, kMaxInner, 0, s>>>(j, d, dd, part, kUpdBlocks, sv, dinv, inv_s, sc);
+  k_inner_col<<<1, kBookThreads, 0, s>>>(j, d, dd, part, kUpdBlocks, sv, dinv, inv_s, sc);
   note_launch();
   return cudaGetLastError();
 }
