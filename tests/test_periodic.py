@@ -172,3 +172,14 @@ def test_periodic_discrete_conservation(dim, mask):
         field = (beta[0] * U[:, s] + beta[1] * Uk[:, s] + beta[2] * Ukm1[:, s]) / dt
         integral = np.sum(vol * field[m.el_nodes].mean(axis=1))
         assert abs(F[free, s].sum() - integral) < 1e-12 * abs(integral)
+
+
+def test_periodic_mask_is_validated(pnp):
+    oc = W.uniform_octants(2, 2)
+    for mask in (-1, 4, 8):
+        with pytest.raises(pnp.PnpError) as e:
+            pnp.Mesh(W.with_periodic(oc, mask))
+        assert e.value.code == pnp.PNP_ERR_ARG
+    # a periodic axis carries no boundary-face bits: no node of the mesh lies on x = 1
+    m = pnp.Mesh(W.with_periodic(oc, 1))
+    assert m.ijk[:, 0].max() == (1 << 2) - 1 and m.ijk[:, 1].max() == 1 << 2
