@@ -271,17 +271,22 @@ size_t mlp_tc_smem_bytes() { return kSmemUsed + 1024; }
 
 cudaError_t launch_mlp_infer_tc(const MlpTcArgs& a, cudaStream_t s) {
   if (a.rows <= 0) return cudaSuccess;
-  static int n_sm = 0;
-  static bool attr = false;
-  if (!attr) {
+  // the device query and the shared-memory attribute run once, thread-safely
+  struct Cfg {
+    cudaError_t e;
+    int n_sm;
+  };
+  static const Cfg cfg = [] {
+    Cfg r{cudaSuccess, 0};
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_tc_smem_bytes());
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+    r.e = cudaGetDevice(&dev);
+    if (r.e == cudaSuccess) r.e = cudaDeviceGetAttribute(&r.n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (r.e == cudaSuccess)
+      r.e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_tc_smem_bytes());
+    return r;
+  }();
+  if (cfg.e != cudaSuccess) return cfg.e;
+  const int n_sm = cfg.n_sm;
   const int64_t tiles = (a.rows + kRows - 1) / kRows;
   const unsigned blocks = (unsigned)(tiles < n_sm ? tiles : n_sm);
   k_mlp_infer_tc<<<blocks, kThreads, mlp_tc_smem_bytes(), s>>>(a);
