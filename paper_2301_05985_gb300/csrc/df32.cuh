@@ -21,34 +21,34 @@ struct df {
   __host__ __device__ explicit df(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
 };
 
-__device__ __forceinline__ df df_two_sum(float a, float b) {
+__host__ __device__ __forceinline__ df df_two_sum(float a, float b) {
   const float s = a + b;
   const float bb = s - a;
   return df(s, (a - (s - bb)) + (b - bb));
 }
-__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+__host__ __device__ __forceinline__ df df_fast_two_sum(float a, float b) {
   const float s = a + b;
   return df(s, b - (s - a));
 }
-__device__ __forceinline__ df df_two_prod(float a, float b) {
+__host__ __device__ __forceinline__ df df_two_prod(float a, float b) {
   const float p = a * b;
   return df(p, fmaf(a, b, -p));
 }
 
-__device__ __forceinline__ df operator+(df a, df b) {
+__host__ __device__ __forceinline__ df operator+(df a, df b) {
   df s = df_two_sum(a.hi, b.hi);
   const df t = df_two_sum(a.lo, b.lo);
   s = df_fast_two_sum(s.hi, s.lo + t.hi);
   return df_fast_two_sum(s.hi, s.lo + t.lo);
 }
-__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
-__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
-__device__ __forceinline__ df operator*(df a, df b) {
+__host__ __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__host__ __device__ __forceinline__ df operator*(df a, df b) {
   const df p = df_two_prod(a.hi, b.hi);
   return df_fast_two_sum(p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo)));
 }
-__device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
-__device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
+__host__ __device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
+__host__ __device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
 
 // 1 / sqrt(x), x > 0: the float estimate refined by two Newton steps y += y (1 - x y^2) / 2,
 // each evaluated in double-float (the error of the estimate squares per step)
