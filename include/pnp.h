@@ -255,15 +255,24 @@ int pnp_plane_average(pnp_ctx* c, const double* U, int axis, int64_t coord, doub
 int pnp_norm2(pnp_ctx* c, const double* x, int64_t n, double* result);
 
 /* ---------------------------------------------------------------- solvers -------- */
-/* Solve J(U) x = b by right-preconditioned GMRES(m) (3x3 block-Jacobi preconditioner,
+/* The linear solve of each Newton iteration (Sec. 4.1, Eq. newton_linear_system), by the
+ * Krylov method of the paper's PNP solver options (App. A: PETSc FGMRES, relative
+ * tolerance 1e-8), with a 3x3 block-Jacobi preconditioner in place of its GAMG.
+ * Solve J(U) x = b by right-preconditioned GMRES(m) (3x3 block-Jacobi preconditioner,
  * classical Gram-Schmidt, a second pass when gmres_cgs2, FP64 basis and dot products;
  * convergence accepted after a true-residual check).
  * U, b, x: device FP64 [n][3]; x is the initial guess on entry.  rtol relative to
  * ||b||; precision selects the J V arithmetic. */
 int pnp_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol,
               int precision, pnp_solve_stats* st);
-/* Newton solve of F(U) = 0 for PNP_FIELD_U in place, starting from its current
- * value (made consistent first), with the context's parameters. */
+/* Newton solve of F(U) = 0 for PNP_FIELD_U in place (Sec. 4.1: Newton's method on the
+ * fully discrete PNP residual of Def. 3 with the analytic Jacobian, Eq.
+ * newton_linear_system, here applied matrix-free), starting from its current value (made
+ * consistent first), with the context's parameters: stop when ||F|| <= newton_rtol
+ * ||F(U^0)|| or newton_atol; PNP_F64 solves each linear system with pnp_gmres to
+ * gmres_rtol (App. A's 1e-8), PNP_F32 inexactly (Eisenstat-Walker forcing) with FP32 J V;
+ * optional backtracking line search.  Returns PNP_ERR_NEWTON_DIVERGED when newton_max_it
+ * is reached or the line search fails, PNP_ERR_NAN on a non-finite norm. */
 int pnp_newton_solve(pnp_ctx* c, pnp_solve_stats* st);
 /* One BDF time step (Def. 1): BDF1 on the first step, then bdf_order; advection
  * v~ = 2 v^k - v^{k-1} (Eq. averaging1) from the VELOCITY fields; Newton start per
@@ -348,6 +357,20 @@ int pnp_mlp_forward(pnp_ctx* c, const float* X, int64_t B, float* Y);
  * B rows: X device FP32 [B][216], Yt device FP32 [B][3], grad device FP32
  * [PNP_MLP_PARAMS]; *loss on the host.  B <= 65536. */
 int pnp_mlp_loss_grad(pnp_ctx* c, const float* X, const float* Yt, int64_t B, float* grad, double* loss);
+/* One Adam update (Kingma and Ba, "Adam: a method for stochastic optimization", ICLR
+ * 2015, Algorithm 1, with bias correction) of the FP32 master parameters with a given
+ * gradient, the same update pnp_mlp_train applies after each batch:
+ *     t += 1;  m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *     p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+ * in FP32 per parameter, then the BF16 weights are refreshed.  grad: device FP32
+ * [PNP_MLP_PARAMS] in the packed order; cfg: lr, beta1, beta2, adam_eps (steps, batch and
+ * seed are ignored).  The moments and t carry over between calls and pnp_mlp_train
+ * steps; pnp_mlp_init clears them.  Lets a caller run its own training loop with the
+ * library's gradients (pnp_mlp_loss_grad). */
+int pnp_mlp_adam_step(pnp_ctx* c, const float* grad, const pnp_train_cfg* cfg);
+/* Adam state: first and second moments host FP32 [PNP_MLP_PARAMS] each (packed order)
+ * and the step count t.  Any pointer may be NULL. */
+int pnp_mlp_get_adam_state(pnp_ctx* c, float* m, float* v, int64_t* t);
 
 /* Allocation-free network forward (no counterpart in the paper; a service of this
  * library).  Same result as pnp_mlp_forward, but needs no context and never allocates
@@ -361,6 +384,10 @@ int pnp_mlp_loss_grad(pnp_ctx* c, const float* X, const float* Yt, int64_t B, fl
  *   X: device FP32 [B][216] standardised inputs; Y: device FP32 [B][3] outputs;
  *   B <= PNP_NOALLOC_MAX_ROWS (larger B: PNP_ERR_ARG, split the call);
  *   stream: cudaStream_t (NULL = legacy default stream); returns after the work is done.
+ * The array is part of the library's device code: CUDA commits it on a device when it
+ * loads that code there, which under lazy module loading (CUDA's default) can be the
+ * first call of this or another network entry point on that device -- a caller with a
+ * fixed device budget should count these 5 MB in it.  Later calls allocate nothing.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * for that device; make that first call before any stream capture.  All calls share the
  * array, so calls that overlap on the GPU (other streams, other host threads) race and

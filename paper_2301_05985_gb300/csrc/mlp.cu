@@ -679,6 +679,19 @@ void pnp_mlp_release(pnp_ctx* c) {
   }
 }
 
+// One Adam update of the FP32 master parameters with gradient G (device FP32 [P]), the
+// moments and step count carried in the network's state, then the BF16 weight refresh.
+static int mlp_adam(pnp_ctx* c, Mlp* m, const float* G, const pnp_train_cfg* cfg) {
+  m->adam_t++;
+  const float c1 = (float)(1.0 - std::pow(cfg->beta1, (double)m->adam_t));
+  const float c2 = (float)(1.0 - std::pow(cfg->beta2, (double)m->adam_t));
+  k_adam<<<nblk(PNP_MLP_PARAMS, 256), 256, 0, c->stream>>>(PNP_MLP_PARAMS, m->P, G, m->Am, m->Av, (float)cfg->lr,
+                                                          (float)cfg->beta1, (float)cfg->beta2,
+                                                          (float)cfg->adam_eps, c1, c2);
+  note_launch();
+  return mlp_refresh(c, m);
+}
+
 #define MLP_GUARD(c)                                                                   \
   do {                                                                                 \
     if (!(c)) PNP_FAIL(PNP_ERR_ARG, "null context");                                   \
@@ -988,13 +1001,7 @@ int pnp_mlp_train(pnp_ctx* c, const pnp_train_cfg* cfg, pnp_train_stats* st) {
     if ((rc = mlp_backward_rows(c, m, B, want ? &l : nullptr))) break;
     if (it == 0) l_first = l;
     if (it + 1 == cfg->steps) l_last = l;
-    m->adam_t++;
-    const float c1 = (float)(1.0 - std::pow(cfg->beta1, (double)m->adam_t));
-    const float c2 = (float)(1.0 - std::pow(cfg->beta2, (double)m->adam_t));
-    k_adam<<<nblk(PNP_MLP_PARAMS, 256), 256, 0, s>>>(PNP_MLP_PARAMS, m->P, m->G, m->Am, m->Av, (float)cfg->lr,
-                                                    (float)cfg->beta1, (float)cfg->beta2, (float)cfg->adam_eps, c1, c2);
-    note_launch();
-    if ((rc = mlp_refresh(c, m))) break;
+    if ((rc = mlp_adam(c, m, m->G, cfg))) break;
   }
   cudaStreamSynchronize(s);
   cudaFreeHost(pin_s);
@@ -1010,6 +1017,27 @@ int pnp_mlp_train(pnp_ctx* c, const pnp_train_cfg* cfg, pnp_train_stats* st) {
     st->samples = (int64_t)vstates.size() * m->n_free;
     st->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
+  return PNP_OK;
+}
+
+int pnp_mlp_adam_step(pnp_ctx* c, const float* grad, const pnp_train_cfg* cfg) {
+  MLP_GUARD(c);
+  if (!grad || !cfg || !(cfg->lr > 0) || !(cfg->beta1 >= 0 && cfg->beta1 < 1) || !(cfg->beta2 >= 0 && cfg->beta2 < 1) ||
+      !(cfg->adam_eps >= 0))
+    PNP_FAIL(PNP_ERR_ARG, "pnp_mlp_adam_step: bad arguments");
+  RC(mlp_adam(c, c->mlp, grad, cfg));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  c->mlp->trained = true;
+  return PNP_OK;
+}
+
+int pnp_mlp_get_adam_state(pnp_ctx* c, float* m1, float* m2, int64_t* t) {
+  MLP_GUARD(c);
+  if (m1) CK(cudaMemcpyAsync(m1, c->mlp->Am, 4 * (size_t)PNP_MLP_PARAMS, cudaMemcpyDeviceToHost, c->stream));
+  if (m2) CK(cudaMemcpyAsync(m2, c->mlp->Av, 4 * (size_t)PNP_MLP_PARAMS, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (t) *t = c->mlp->adam_t;
   return PNP_OK;
 }
 

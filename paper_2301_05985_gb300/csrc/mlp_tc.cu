@@ -14,6 +14,8 @@
 #include <cstdint>
 
 #include "mlp_tc.h"
+
+#include <mutex>
 #include "kernels.h"
 
 namespace {
@@ -271,22 +273,28 @@ size_t mlp_tc_smem_bytes() { return kSmemUsed + 1024; }
 
 cudaError_t launch_mlp_infer_tc(const MlpTcArgs& a, cudaStream_t s) {
   if (a.rows <= 0) return cudaSuccess;
-  // the device query and the shared-memory attribute run once, thread-safely
-  struct Cfg {
-    cudaError_t e;
-    int n_sm;
-  };
-  static const Cfg cfg = [] {
-    Cfg r{cudaSuccess, 0};
-    int dev = 0;
-    r.e = cudaGetDevice(&dev);
-    if (r.e == cudaSuccess) r.e = cudaDeviceGetAttribute(&r.n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (r.e == cudaSuccess)
-      r.e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_tc_smem_bytes());
-    return r;
-  }();
-  if (cfg.e != cudaSuccess) return cfg.e;
-  const int n_sm = cfg.n_sm;
+  // the SM count and the shared-memory attribute, once per device (the attribute is a
+  // per-device setting); only a successful set-up is cached
+  static std::mutex mu;
+  static int n_sm_of[128] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  int n_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!n_sm_of[dev]) {
+      int n = 0;
+      e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mlp_tc_smem_bytes());
+      if (e != cudaSuccess) return e;
+      n_sm_of[dev] = n;
+    }
+    n_sm = n_sm_of[dev];
+  }
   const int64_t tiles = (a.rows + kRows - 1) / kRows;
   const unsigned blocks = (unsigned)(tiles < n_sm ? tiles : n_sm);
   k_mlp_infer_tc<<<blocks, kThreads, mlp_tc_smem_bytes(), s>>>(a);

@@ -135,6 +135,8 @@ SIGNATURES = {
     "pnp_mlp_forward": (C.c_int, [_vp, _vp, _i64, _vp]),
     "pnp_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _P(_d)]),
     "pnp_mlp_forward_noalloc": (C.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "pnp_mlp_adam_step": (C.c_int, [_vp, _vp, _P(pnp_train_cfg)]),
+    "pnp_mlp_get_adam_state": (C.c_int, [_vp, _vp, _vp, _P(_i64)]),
 }
 
 PNP_NOALLOC_MAX_ROWS = 4096
@@ -438,6 +440,19 @@ class Context:
         st = pnp_train_stats()
         check(lib().pnp_mlp_train(self.h, C.byref(cfg), C.byref(st)))
         return st
+
+    def mlp_adam_step(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, adam_eps=1e-8):
+        """One Adam update of the parameters with a device FP32 gradient [PNP_MLP_PARAMS]."""
+        cfg = pnp_train_cfg(0, 1, lr, beta1, beta2, adam_eps, 0)
+        check(lib().pnp_mlp_adam_step(self.h, _ptr(grad), C.byref(cfg)))
+
+    def mlp_adam_state(self):
+        """(m, v, t): Adam moments (host FP32 [PNP_MLP_PARAMS]) and step count."""
+        m = np.zeros(PNP_MLP_PARAMS, np.float32)
+        v = np.zeros(PNP_MLP_PARAMS, np.float32)
+        t = C.c_int64()
+        check(lib().pnp_mlp_get_adam_state(self.h, m.ctypes.data, v.ctypes.data, C.byref(t)))
+        return m, v, t.value
 
     def mlp_features(self, Uk, Ukm1, uzk=None, uzkm1=None, X=None, nodes=None):
         check(lib().pnp_mlp_features(self.h, _ptr(Uk), _ptr(Ukm1), _ptr(uzk), _ptr(uzkm1), _ptr(X), _ptr(nodes)))

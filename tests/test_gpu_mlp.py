@@ -178,3 +178,94 @@ def test_training_fits_a_solver_trajectory():
     assert st2.status == 0
     assert st2.start_used in (pnp.PNP_START_LEARNED, pnp.PNP_START_EXTRAPOLATE)
     assert st2.res0 <= st2.res_start_extrapolated * (1 + 1e-12)
+
+
+def _adam_oracle(p0, grads, lr, b1, b2, eps):
+    """The oracle's Adam applied to the packed parameters (one tensor) for each gradient."""
+    P = [p0.astype(np.float64).copy()]
+    state = {}
+    out = []
+    for g in grads:
+        MO.adam_step(P, [], [g.astype(np.float64)], [], state, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        out.append((P[0].copy(), state["m"][0].copy(), state["v"][0].copy(), state["t"]))
+    return out
+
+
+def test_adam_update_matches_oracle_over_several_steps():
+    """The library's Adam update (the one pnp_mlp_train applies after every batch) against
+    the oracle's Adam for four consecutive steps fed the same gradients: parameters, both
+    moments and the step count.  The gradients mix magnitudes over six decades and change
+    sign between steps, so the bias correction, the betas and the moments carried from one
+    step to the next all show.  FP32 arithmetic against FP64: moments within 1e-6 of their
+    norm, parameters within FP32 rounding of the parameter plus 1e-5 of the step size."""
+    oc = W.uniform_octants(3, 2)
+    pnp, torch, mesh, ctx = _ctx(oc)
+    rng = np.random.default_rng(21)
+    P = pnp.PNP_MLP_PARAMS
+    p0 = rng.normal(0, 0.1, P).astype(np.float32)
+    ctx.mlp_set_weights(p0)
+    lr, b1, b2, eps = 3e-3, 0.85, 0.995, 1e-7
+    mags = 10.0 ** rng.uniform(-6, 0, P)
+    grads = [(rng.choice([-1.0, 1.0], P) * mags * rng.uniform(0.5, 2.0, P)).astype(np.float32) for _ in range(4)]
+    grads[2] = (-grads[1] * 0.5).astype(np.float32)  # a sign reversal
+    ref = _adam_oracle(p0, grads, lr, b1, b2, eps)
+    m0, v0, t0 = ctx.mlp_adam_state()
+    assert t0 == 0 and not m0.any() and not v0.any()
+    for t, g in enumerate(grads, start=1):
+        ctx.mlp_adam_step(torch.from_numpy(g).cuda(), lr=lr, beta1=b1, beta2=b2, adam_eps=eps)
+        p = ctx.mlp_get_weights().astype(np.float64)
+        m, v, tt = ctx.mlp_adam_state()
+        pr, mr, vr, tr = ref[t - 1]
+        assert tt == tr == t
+        assert np.linalg.norm(m - mr) <= 1e-6 * np.linalg.norm(mr), t
+        assert np.linalg.norm(v - vr) <= 1e-6 * np.linalg.norm(vr), t
+        assert np.abs(m - mr).max() <= 1e-6 * np.abs(mr).max(), t
+        tol = 2.0**-23 * np.abs(pr) * t + 1e-5 * lr * t
+        assert np.all(np.abs(p - pr) <= tol), (t, np.abs(p - pr).max())
+        # each step moved the parameters by about lr at most (a bias correction that
+        # shrinks towards zero with t would break this on the first steps)
+        step = np.abs(p - (ref[t - 2][0] if t > 1 else p0))
+        assert step.max() <= lr * (1.0 + 1e-3) / (1 - b1) + 1e-9
+
+
+def test_training_steps_match_oracle_gradients_and_moments():
+    """Three training steps on a fixed batch through the library's own gradient and Adam
+    calls, against the oracle's FP64 backward pass on the same BF16-rounded weights and
+    inputs and its Adam: the gradient and both Adam moments within the gradient test's
+    2e-2 per tensor (the second moment, quadratic in the gradient, within 4e-2), and the
+    loss within 1e-2 at every step."""
+    oc = W.uniform_octants(3, 2)
+    pnp, torch, mesh, ctx = _ctx(oc)
+    rng = np.random.default_rng(8)
+    Ws, bs = MO.init_params(5)
+    bs = [b + rng.normal(0, 0.05, b.shape) for b in bs]
+    p = pack(Ws, bs)
+    ctx.mlp_set_weights(p)
+    B = 1024
+    X = rng.normal(size=(B, 216)).astype(np.float32)
+    Y = rng.normal(size=(B, 3)).astype(np.float32)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    g = torch.zeros(pnp.PNP_MLP_PARAMS, dtype=torch.float32, device="cuda")
+    lr = 1e-3
+    P = [p.astype(np.float64)]
+    state = {}
+    Xr = MO.bf16_round(X)
+    for t in range(1, 4):
+        loss = ctx.mlp_loss_grad(Xd, Yd, g)
+        ctx.mlp_adam_step(g, lr=lr)
+        # the oracle: gradient at the library's current FP32 master weights rounded to BF16
+        Wr, br = unpack(P[0].astype(np.float32))
+        gW, gb, lref = MO.backward([MO.bf16_round(w) for w in Wr], br, Xr, Y.astype(np.float64))
+        gref = pack(gW, gb).astype(np.float64)
+        MO.adam_step(P, [], [gref], [], state, lr=lr)
+        gg = g.cpu().numpy().astype(np.float64)
+        m, v, tt = ctx.mlp_adam_state()
+        assert tt == t
+        assert abs(loss - lref) <= 1e-2 * lref, t
+        for (off, fi, fo) in SHAPES:
+            for a, b_, tol in [(gg, gref, 2e-2), (m, state["m"][0], 2e-2), (v, state["v"][0], 4e-2)]:
+                sl = slice(off, off + fi * fo)
+                assert np.linalg.norm(a[sl] - b_[sl]) <= tol * np.linalg.norm(b_[sl]), (t, off)
+        # keep the oracle's master weights on the library's (their difference is the
+        # gradient's BF16 error; the next step compares the update it makes from there)
+        P[0] = ctx.mlp_get_weights().astype(np.float64)

@@ -74,6 +74,53 @@ def test_adam_first_step_is_sign_times_lr():
         np.testing.assert_allclose(w0 - w1, 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-6, atol=1e-12)
 
 
+def test_adam_later_steps_closed_forms():
+    """Adam's moments and bias correction beyond the first step.  With the same gradient g
+    at every step, m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2 exactly, so the corrected
+    moments are g and g^2 and every step moves a parameter by lr g / (|g| + eps).  With
+    the gradients g, -g, 3g the moments follow the recurrences written out by hand.  A
+    bias correction frozen at t = 1, moments not carried between steps, or swapped
+    betas fail one of these."""
+    b1, b2, lr, eps = 0.9, 0.999, 1e-2, 1e-8
+    g = np.array([[0.5, -2.0], [1e-3, 4.0]])
+    gb = np.array([-0.25])
+    W = [np.zeros((2, 2))]
+    b = [np.ones(1)]
+    state = {}
+    for t in range(1, 6):
+        M.adam_step(W, b, [g], [gb], state, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        np.testing.assert_allclose(state["m"][0], (1 - b1**t) * g, rtol=1e-14)
+        np.testing.assert_allclose(state["v"][0], (1 - b2**t) * g * g, rtol=1e-13)
+        np.testing.assert_allclose(W[0], -t * lr * g / (np.abs(g) + eps), rtol=1e-12)
+        np.testing.assert_allclose(b[0], 1.0 - t * lr * gb / (np.abs(gb) + eps), rtol=1e-12)
+        assert state["t"] == t
+    # a changing gradient: g1 = g, g2 = -g, g3 = 3 g
+    W = [np.zeros((2, 2))]
+    b = [np.zeros(1)]
+    state = {}
+    seq = [1.0, -1.0, 3.0]
+    m = np.zeros((2, 2)); v = np.zeros((2, 2)); p = np.zeros((2, 2))
+    for t, s in enumerate(seq, start=1):
+        M.adam_step(W, b, [s * g], [s * gb], state, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        # by hand: t = 2 gives m = (1 - b1)(b1 - 1) g, v = (1 - b2)(b2 + 1) g^2
+        m = b1 * m + (1 - b1) * s * g
+        v = b2 * v + (1 - b2) * (s * g) ** 2
+        p = p - lr * (m / (1 - b1**t)) / (np.sqrt(v / (1 - b2**t)) + eps)
+        if t == 2:
+            np.testing.assert_allclose(m, -(1 - b1) ** 2 * g, rtol=1e-14)
+            np.testing.assert_allclose(v, (1 - b2 * b2) * g * g, rtol=1e-13)
+        np.testing.assert_allclose(state["m"][0], m, rtol=1e-14)
+        np.testing.assert_allclose(state["v"][0], v, rtol=1e-13)
+        np.testing.assert_allclose(W[0], p, rtol=1e-12, atol=1e-15)
+    # after g, -g the corrected first moment is -(1 - b1)^2 g / (1 - b1^2) = -(1 - b1)/(1 + b1) g
+    st2 = {}
+    W2, b2_ = [np.zeros((2, 2))], [np.zeros(1)]
+    M.adam_step(W2, b2_, [g], [gb], st2, lr=lr, beta1=b1, beta2=b2, eps=eps)
+    M.adam_step(W2, b2_, [-g], [-gb], st2, lr=lr, beta1=b1, beta2=b2, eps=eps)
+    mh = st2["m"][0] / (1 - b1**2)
+    np.testing.assert_allclose(mh, -(1 - b1) / (1 + b1) * g, rtol=1e-13)
+
+
 @pytest.mark.parametrize("dim,seed", [(3, 2), (3, 7), (2, 4)])
 def test_stencil_features_reproduce_linear_fields(dim, seed):
     """Point evaluation of the Q1 fields is exact for globally linear fields (on meshes with

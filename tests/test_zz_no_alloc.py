@@ -33,9 +33,17 @@ def test_noalloc_forward_matches_context_forward_twice():
         ref = torch.zeros((B, 3), dtype=torch.float32, device="cuda")
         ctx.mlp_forward(X, ref)
         ref = ref.cpu().numpy()
-        for _ in range(2):  # the shared scratch keeps the previous call's contents
-            Y = torch.full((B, 3), float("nan"), dtype=torch.float32, device="cuda")
+        Ys = [torch.full((B, 3), float("nan"), dtype=torch.float32, device="cuda") for _ in range(2)]
+        pnp.mlp_forward_noalloc(dparams, X, Ys[0], stream)  # loads the array if not yet resident
+        torch.cuda.synchronize()
+        Ys[0].fill_(float("nan"))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for Y in Ys:  # the shared scratch keeps the previous call's contents
             pnp.mlp_forward_noalloc(dparams, X, Y, stream)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0  # nothing was allocated on the device
+        for Y in Ys:
             Y = Y.cpu().numpy()
             assert np.all(np.isfinite(Y))
             assert np.linalg.norm(Y - ref) <= TOL * np.linalg.norm(ref)
