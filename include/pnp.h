@@ -167,6 +167,17 @@ int pnp_mesh_create(int dim, int max_level, int64_t n_oct, const int32_t* anchor
  * periodic meshes (PNP_ERR_ARG). */
 int pnp_mesh_create_periodic(int dim, int max_level, int64_t n_oct, const int32_t* anchors,
                              const uint8_t* levels, int periodic, pnp_mesh** out);
+/* The same after refinement (the paper builds its octrees top-down with a refinement
+ * predicate on coordinates and field values, Sec. 4.2, and refines near the membrane and
+ * where the fields vary fastest, Sec. 5.2): every input octant is split until it reaches
+ * target_levels[e] (host uint8 [n_oct], <= max_level; NULL = no targets), then leaves are
+ * split until the octree is 2:1 balanced across faces, edges and corners (across the
+ * identified faces of periodic axes too).  The result is the coarsest balanced octree
+ * refining each octant to at least its target; pnp_mesh_elements returns its leaves.
+ * The input octants must tile the domain without overlap (PNP_ERR_MESH otherwise). */
+int pnp_mesh_create_refined(int dim, int max_level, int64_t n_oct, const int32_t* anchors,
+                            const uint8_t* levels, const uint8_t* target_levels, int periodic,
+                            pnp_mesh** out);
 void pnp_mesh_destroy(pnp_mesh* m);
 int pnp_mesh_info(const pnp_mesh* m, int* dim, int* max_level, int64_t* n_elem,
                   int64_t* n_nodes, int64_t* n_hanging);
@@ -242,6 +253,12 @@ int pnp_block_diag_f32(pnp_ctx* c, const double* U, float* D);
  * through the top boundary: j_T = -(flux[0] - flux[1]) / L_T, L_T the face's length
  * (area in 3D; 1 on the unit domain).  A periodic face gives 0.  flux: host double[2]. */
 int pnp_boundary_flux(pnp_ctx* c, const double* U, int face, double* flux);
+/* Refinement indicator: |grad c+|, |grad c-|, |grad phi| of the Q1 fields of U (device FP64
+ * [n][3], hanging entries taken from their constraints) at the centre of every element,
+ * G device FP64 [n_elem][3] in the library's element order (pnp_mesh_elements).  With
+ * pnp_mesh_create_refined it refines where the fields vary fastest (Sec. 5.2 refines the
+ * electroconvection meshes where the concentration gradients are largest). */
+int pnp_element_gradient(pnp_ctx* c, const double* U, double* G);
 /* Averages of (c+, c-, phi) over the plane x_axis = coord * 2^-max_level (0 <= coord <=
  * 2^max_level; coord < 2^max_level on a periodic axis) of the unit domain: the integral
  * of each Q1 field over the plane, each element's cross-section integrated with the

@@ -50,6 +50,8 @@ def lib():
         L.ora_jacobian.restype = C.c_int64
         L.ora_jacobian.argtypes = [vp, vp, dp, dp, dp, dp, i64p, i64p, dp]
         L.ora_jv.argtypes = [vp, vp, dp, dp, dp, dp, dp, dp]
+        L.ora_residual_elements.argtypes = [vp, vp, dp, dp, dp, dp, C.c_int64, C.c_int64, dp]
+        L.ora_jv_elements.argtypes = [vp, vp, dp, dp, dp, dp, dp, C.c_int64, C.c_int64, dp]
         L.ora_qp_eval.argtypes = [vp, vp, C.c_int64, C.c_int, dp, dp, dp, dp, dp]
         L.ora_bc_rows.argtypes = [vp, vp, i32p, dp]
         L.ora_mms.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int64, dp, dp, dp]
@@ -217,6 +219,24 @@ class OracleMesh:
         pc = p.to_c()
         lib().ora_jv(self.h, C.byref(pc), _p(U, C.c_double), _p(Uk, C.c_double), _p(Ukm1, C.c_double),
                      _p(v, C.c_double), _p(V, C.c_double), _p(JV, C.c_double))
+        return JV
+
+    def residual_elements(self, p: Params, U, Uk, Ukm1, adv, e0: int, e1: int, F):
+        """Add the element contributions of elements e0 <= e < e1 into F [n_nodes, 3]
+        (C-contiguous float64, modified in place; no Dirichlet or constraint rows)."""
+        U = self._z(U); Uk = self._z(Uk); Ukm1 = self._z(Ukm1); v = self._vel3(adv)
+        pc = p.to_c()
+        lib().ora_residual_elements(self.h, C.byref(pc), _p(U, C.c_double), _p(Uk, C.c_double),
+                                    _p(Ukm1, C.c_double), _p(v, C.c_double), int(e0), int(e1), _p(F, C.c_double))
+        return F
+
+    def jv_elements(self, p: Params, U, V, Uk, Ukm1, adv, e0: int, e1: int, JV):
+        """Add the element contributions of elements e0 <= e < e1 into JV [n_nodes, 3]
+        (C-contiguous float64, modified in place; no Dirichlet or constraint rows)."""
+        U = self._z(U); V = self._z(V); Uk = self._z(Uk); Ukm1 = self._z(Ukm1); v = self._vel3(adv)
+        pc = p.to_c()
+        lib().ora_jv_elements(self.h, C.byref(pc), _p(U, C.c_double), _p(Uk, C.c_double), _p(Ukm1, C.c_double),
+                              _p(v, C.c_double), _p(V, C.c_double), int(e0), int(e1), _p(JV, C.c_double))
         return JV
 
     def eval_points(self, U, pts):

@@ -496,12 +496,12 @@ void element_residual(const Mesh& m, const Params& p, int64_t e, const double* U
   }
 }
 
-void residual(const Mesh& m, const Params& p, const double* U, const double* Uk, const double* Ukm1,
-              const double* adv, double* F) {
-  const int64_t nn = (int64_t)m.node_xyz.size();
+// Element contributions of elements e0 <= e < e1, assembled with the transpose of the
+// constraints and added into F (no other rows touched).
+void residual_elements(const Mesh& m, const Params& p, const double* U, const double* Uk, const double* Ukm1,
+                       const double* adv, int64_t e0, int64_t e1, double* F) {
   const int nc = corner_count(m.dim);
-  for (int64_t i = 0; i < 3 * nn; ++i) F[i] = 0.0;
-  for (int64_t e = 0; e < (int64_t)m.el_nodes.size(); ++e) {
+  for (int64_t e = e0; e < e1; ++e) {
     double Fe[8][3];
     element_residual(m, p, e, U, Uk, Ukm1, adv, Fe);
     // assemble with the transpose of the constraints
@@ -509,6 +509,13 @@ void residual(const Mesh& m, const Params& p, const double* U, const double* Uk,
       for (auto& pw : m.cons[m.el_nodes[e][c]])
         for (int f = 0; f < 3; ++f) F[3 * pw.first + f] += pw.second * Fe[c][f];
   }
+}
+
+void residual(const Mesh& m, const Params& p, const double* U, const double* Uk, const double* Ukm1,
+              const double* adv, double* F) {
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  for (int64_t i = 0; i < 3 * nn; ++i) F[i] = 0.0;
+  residual_elements(m, p, U, Uk, Ukm1, adv, 0, (int64_t)m.el_nodes.size(), F);
   for (int64_t i = 0; i < nn; ++i) {
     if (m.hanging[i]) {
       // constraint row: U_h - sum_p w_p U_p
@@ -628,13 +635,12 @@ int64_t jacobian_triplets(const Mesh& m, const Params& p, const double* U, const
 // ------------------------------------------------------------------ matrix-free Jv
 // Directional derivative of the residual written from the linearised Gauss-point
 // expressions (an independent derivation from element_jacobian).
-void jv(const Mesh& m, const Params& p, const double* U, const double* Uk, const double* Ukm1,
-        const double* adv, const double* V, double* JV) {
-  const int64_t nn = (int64_t)m.node_xyz.size();
+// Element contributions of elements e0 <= e < e1 added into JV (no other rows touched).
+void jv_elements(const Mesh& m, const Params& p, const double* U, const double* Uk, const double* Ukm1,
+                 const double* adv, const double* V, int64_t e0, int64_t e1, double* JV) {
   const int dim = m.dim, nc = corner_count(dim);
   const double lam2 = 2.0 * p.eps * p.eps;
-  for (int64_t i = 0; i < 3 * nn; ++i) JV[i] = 0.0;
-  for (int64_t e = 0; e < (int64_t)m.el_nodes.size(); ++e) {
+  for (int64_t e = e0; e < e1; ++e) {
     double Ue[8][3], Uke[8][3], Ukm1e[8][3], Ve[8][3], De[8][3], Fe[8][3];
     gather3(m, e, U, Ue);
     gather3(m, e, Uk, Uke);
@@ -686,6 +692,13 @@ void jv(const Mesh& m, const Params& p, const double* U, const double* Uk, const
       for (auto& pw : m.cons[m.el_nodes[e][c]])
         for (int f = 0; f < 3; ++f) JV[3 * pw.first + f] += pw.second * Fe[c][f];
   }
+}
+
+void jv(const Mesh& m, const Params& p, const double* U, const double* Uk, const double* Ukm1,
+        const double* adv, const double* V, double* JV) {
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  for (int64_t i = 0; i < 3 * nn; ++i) JV[i] = 0.0;
+  jv_elements(m, p, U, Uk, Ukm1, adv, V, 0, (int64_t)m.el_nodes.size(), JV);
   for (int64_t i = 0; i < nn; ++i) {
     if (m.hanging[i]) {
       for (int f = 0; f < 3; ++f) {
@@ -882,6 +895,20 @@ int64_t ora_jacobian(void* h, const Params* p, const double* U, const double* Uk
 void ora_jv(void* h, const Params* p, const double* U, const double* Uk, const double* Ukm1,
             const double* adv, const double* V, double* JV) {
   jv(*static_cast<Mesh*>(h), *p, U, Uk, Ukm1, adv, V, JV);
+}
+
+// The element contributions of elements e0 <= e < e1 (oracle element order), added into
+// F / JV: no zeroing, no Dirichlet or constraint rows.  Summed over a partition of the
+// elements and followed by those rows they give ora_residual / ora_jv (up to summation
+// order); used to time the oracle on a sample of elements and across host threads.
+void ora_residual_elements(void* h, const Params* p, const double* U, const double* Uk, const double* Ukm1,
+                           const double* adv, int64_t e0, int64_t e1, double* F) {
+  residual_elements(*static_cast<Mesh*>(h), *p, U, Uk, Ukm1, adv, e0, e1, F);
+}
+
+void ora_jv_elements(void* h, const Params* p, const double* U, const double* Uk, const double* Ukm1,
+                     const double* adv, const double* V, int64_t e0, int64_t e1, double* JV) {
+  jv_elements(*static_cast<Mesh*>(h), *p, U, Uk, Ukm1, adv, V, e0, e1, JV);
 }
 
 // Strong residuals R_+, R_- and tau_c at one Gauss point of element e (for the

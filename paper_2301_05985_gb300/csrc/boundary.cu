@@ -182,7 +182,58 @@ __global__ void __launch_bounds__(kFluxThreads) k_plane_integral(int64_t E, int 
     for (int f = 0; f < 3; ++f) part[3 * blockIdx.x + f] = sh[f][0];
 }
 
+// |grad u| of each field at the element centre (the refinement indicator of the octree
+// construction): for Q1, du/dx_k there is the mean over the element's 2^(d-1) edges along
+// axis k of (u_high - u_low) / h.  One thread per element; out [E][3].
+template <int D>
+__global__ void k_element_gradient(int64_t E, const int32_t* __restrict__ conn, const uint8_t* __restrict__ level,
+                                   const int32_t* __restrict__ hpar, const uint8_t* __restrict__ hnp,
+                                   const double* __restrict__ U, double* __restrict__ out) {
+  constexpr int NC = 1 << D;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double u[NC][3];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int32_t id = conn[e * NC + c];
+    for (int f = 0; f < 3; ++f) u[c][f] = 0.0;
+    if (id >= 0) {
+      for (int f = 0; f < 3; ++f) u[c][f] = U[3 * (int64_t)id + f];
+    } else {
+      const int32_t h = -id - 1;
+      const int np = hnp[h];
+      const double w = np == 2 ? 0.5 : 0.25;
+      for (int p = 0; p < np; ++p)
+        for (int f = 0; f < 3; ++f) u[c][f] += w * U[3 * (int64_t)hpar[4 * h + p] + f];
+    }
+  }
+  const double inv = ldexp(1.0, level[e]) / (double)(NC / 2);  // 1 / (h * edges per axis)
+  for (int f = 0; f < 3; ++f) {
+    double g2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      double d = 0.0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) d += ((c >> k) & 1) ? u[c][f] : -u[c][f];
+      d *= inv;
+      g2 += d * d;
+    }
+    out[3 * e + f] = sqrt(g2);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_element_gradient(int dim, int64_t n_elem, const int32_t* conn, const uint8_t* level,
+                                    const int32_t* hpar, const uint8_t* hnp, const double* U, double* out,
+                                    cudaStream_t s) {
+  if (n_elem == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n_elem + 255) / 256);
+  if (dim == 2) k_element_gradient<2><<<blocks, 256, 0, s>>>(n_elem, conn, level, hpar, hnp, U, out);
+  else k_element_gradient<3><<<blocks, 256, 0, s>>>(n_elem, conn, level, hpar, hnp, U, out);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_plane_integral(int dim, int L, int64_t n_elem, const int32_t* conn, const uint8_t* level,
                                   const int32_t* anchor, const int32_t* hnode, const int32_t* hpar, const uint8_t* hnp,

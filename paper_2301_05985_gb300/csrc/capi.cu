@@ -99,6 +99,23 @@ int pnp_mesh_create_periodic(int dim, int max_level, int64_t n_oct, const int32_
   return PNP_OK;
 }
 
+int pnp_mesh_create_refined(int dim, int max_level, int64_t n_oct, const int32_t* anchors, const uint8_t* levels,
+                            const uint8_t* target_levels, int periodic, pnp_mesh** out) {
+  if (!out) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_create_refined: out is null");
+  *out = nullptr;
+  std::vector<int32_t> a;
+  std::vector<uint8_t> l;
+  int rc;
+  try {
+    rc = pnp_refine_balance(dim, max_level, periodic, n_oct, anchors, levels, target_levels, a, l);
+  } catch (const std::bad_alloc&) {
+    pnp_set_error("pnp_mesh_create_refined: out of host memory");
+    rc = PNP_ERR_NOMEM;
+  }
+  if (rc != PNP_OK) return rc;
+  return pnp_mesh_create_periodic(dim, max_level, (int64_t)l.size(), a.data(), l.data(), periodic, out);
+}
+
 void pnp_mesh_destroy(pnp_mesh* m) { delete m; }
 
 int pnp_mesh_info(const pnp_mesh* m, int* dim, int* max_level, int64_t* n_elem, int64_t* n_nodes,
@@ -554,6 +571,14 @@ int pnp_boundary_flux(pnp_ctx* c, const double* U, int face, double* flux) {
   CK(cudaStreamSynchronize(c->stream));
   flux[0] = c->hpin[2];
   flux[1] = c->hpin[3];
+  return PNP_OK;
+}
+
+int pnp_element_gradient(pnp_ctx* c, const double* U, double* G) {
+  CTX_GUARD(c);
+  if (!U || (!G && c->n_elem)) PNP_FAIL(PNP_ERR_ARG, "pnp_element_gradient: null pointer");
+  CK(launch_element_gradient(c->dim, c->n_elem, c->d_conn, c->d_level, c->d_hpar, c->d_hnp, U, G, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return PNP_OK;
 }
 

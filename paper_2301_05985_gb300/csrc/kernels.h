@@ -92,6 +92,11 @@ cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, int
 cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int rows, int* err,
                                  cudaStream_t s);
 double jv_from_state_flops(int dim);
+// FP32 J V on hexahedra with two lanes per element (jv_pair.cu): the state from the node
+// records (A.rec), the direction A.V4 (with A.out4) or A.V (with A.out); `advection`
+// false when the advection field is zero (tau_c then depends on the level only)
+cudaError_t launch_jv_pair(const ElemArgs<float>& A, bool advection, cudaStream_t s);
+double jv_pair_flops(bool advection);
 // Dout [N][9] += the 3x3 diagonal blocks of the Jacobian (lane-group kernel; Dout zeroed
 // first, Dirichlet and hanging rows left to launch_diag_rows)
 template <typename T>
@@ -187,6 +192,9 @@ cudaError_t launch_combine_f32_add_f64(int64_t n, int k, const float* Zb, int64_
 cudaError_t launch_to_f64_scaled(int64_t n, const float* x, double scale, double* y, cudaStream_t s);
 // out[s] = int_face n . (grad c_s + z_s c_s grad phi) dS (s = +, -) over boundary face
 // `face` (boundary.cu); part: kRedBlocks x 2 partials; out: 2 device doubles
+cudaError_t launch_element_gradient(int dim, int64_t n_elem, const int32_t* conn, const uint8_t* level,
+                                    const int32_t* hpar, const uint8_t* hnp, const double* U, double* out,
+                                    cudaStream_t s);
 cudaError_t launch_boundary_flux(int dim, int64_t n_elem, const int32_t* conn, const uint8_t* level,
                                  const uint8_t* faces, const int32_t* hnode, const int32_t* hpar, const uint8_t* hnp,
                                  const double* U, int face, double* part, double* out, cudaStream_t s);

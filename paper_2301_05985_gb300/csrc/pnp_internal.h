@@ -39,6 +39,11 @@ struct pnp_mesh {
 
 int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchors, const uint8_t* levels,
                    int periodic);
+// Refine each octant to at least target[e] (NULL: no targets), then split leaves until the
+// octree is 2:1 balanced across faces, edges and corners (periodic axes wrap); the
+// coarsest such octree, as unordered leaves.
+int pnp_refine_balance(int dim, int L, int periodic, int64_t n, const int32_t* anchors, const uint8_t* levels,
+                       const uint8_t* target, std::vector<int32_t>& out_anchor, std::vector<uint8_t>& out_level);
 // Morton (Z-order) key of an integer point (x in bit 0 of each group, then y, then z).
 uint64_t pnp_morton(int dim, const int64_t* p);
 

@@ -91,7 +91,9 @@ SIGNATURES = {
     "pnp_params_default": (None, [_P(pnp_params)]),
     "pnp_mesh_create": (C.c_int, [C.c_int, C.c_int, _i64, _vp, _vp, _P(_vp)]),
     "pnp_mesh_create_periodic": (C.c_int, [C.c_int, C.c_int, _i64, _vp, _vp, C.c_int, _P(_vp)]),
+    "pnp_mesh_create_refined": (C.c_int, [C.c_int, C.c_int, _i64, _vp, _vp, _vp, C.c_int, _P(_vp)]),
     "pnp_mesh_destroy": (None, [_vp]),
+    "pnp_element_gradient": (C.c_int, [_vp, _vp, _vp]),
     "pnp_mesh_info": (C.c_int, [_vp, _P(C.c_int), _P(C.c_int), _P(_i64), _P(_i64), _P(_i64)]),
     "pnp_mesh_node_coords": (C.c_int, [_vp, _vp]),
     "pnp_mesh_hanging": (C.c_int, [_vp, _vp]),
@@ -207,15 +209,24 @@ def _ptr(x):
 
 class Mesh:
     """Q1 mesh of a 2:1-balanced octree (owns a pnp_mesh handle).  ``octants.periodic``
-    (bit k: axis k periodic, default 0) selects periodic sides."""
+    (bit k: axis k periodic, default 0) selects periodic sides.  With ``target_levels``
+    (uint8 per octant) the octants are first refined to those levels and 2:1 balanced
+    (pnp_mesh_create_refined); ``elements()`` then returns the resulting leaves."""
 
-    def __init__(self, octants):
+    def __init__(self, octants, target_levels=None):
         a = np.ascontiguousarray(octants.anchors, dtype=np.int32)
         lv = np.ascontiguousarray(octants.levels, dtype=np.uint8)
         h = C.c_void_p()
         self.periodic = int(getattr(octants, "periodic", 0))
-        check(lib().pnp_mesh_create_periodic(octants.dim, octants.max_level, octants.n, a.ctypes.data,
-                                             lv.ctypes.data, self.periodic, C.byref(h)))
+        if target_levels is None:
+            check(lib().pnp_mesh_create_periodic(octants.dim, octants.max_level, octants.n, a.ctypes.data,
+                                                 lv.ctypes.data, self.periodic, C.byref(h)))
+        else:
+            t = np.ascontiguousarray(target_levels, dtype=np.uint8)
+            if t.shape != (octants.n,):
+                raise ValueError("target_levels needs one level per octant")
+            check(lib().pnp_mesh_create_refined(octants.dim, octants.max_level, octants.n, a.ctypes.data,
+                                                lv.ctypes.data, t.ctypes.data, self.periodic, C.byref(h)))
         self.h = h
         d, L = C.c_int(), C.c_int()
         ne, nn, nh = C.c_int64(), C.c_int64(), C.c_int64()
@@ -348,6 +359,11 @@ class Context:
         on the unit domain."""
         f = self.boundary_flux(U, face)
         return -(f[0] - f[1])
+
+    def element_gradient(self, U, G):
+        """G [n_elem][3] (device FP64): |grad c+|, |grad c-|, |grad phi| at element centres."""
+        check(lib().pnp_element_gradient(self.h, _ptr(U), _ptr(G)))
+        return G
 
     def plane_average(self, U, axis: int, coord: int) -> np.ndarray:
         """Averages of (c+, c-, phi) over the plane x_axis = coord 2^-max_level."""

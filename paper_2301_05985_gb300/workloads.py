@@ -115,6 +115,81 @@ def with_periodic(oc: Octants, periodic: int) -> Octants:
     return dataclasses.replace(oc, periodic=int(periodic))
 
 
+def _children(a, l, dim, L):
+    s = 1 << (L - l - 1)
+    for c in range(1 << dim):
+        yield tuple(a[k] + (s if (c >> k) & 1 else 0) for k in range(dim)), l + 1
+
+
+def balance_leaves(leaves: dict, dim: int, L: int, periodic: int = 0) -> dict:
+    """Split leaves ({anchor tuple: level}, modified in place) until no leaf has a face,
+    edge or corner neighbour two or more levels finer.  Neighbours are found by sampling
+    the points just outside each face, edge and corner at the finest spacing (small
+    meshes only: pure Python)."""
+    size = 1 << L
+    dirs = [d for d in np.ndindex(*([3] * dim)) if any(v != 1 for v in d)]
+
+    def find_leaf(pt):
+        # leaf containing integer point pt (inside the domain); search coarse-to-fine
+        for l in range(0, L + 1):
+            s = 1 << (L - l)
+            a = tuple((p // s) * s for p in pt)
+            if leaves.get(a) == l:
+                return a, l
+        return None
+
+    changed = True
+    while changed:
+        changed = False
+        for a, l in list(leaves.items()):
+            if leaves.get(a) != l:
+                continue
+            s = 1 << (L - l)
+            for d in dirs:
+                pts = []
+                for k in range(dim):
+                    dk = d[k] - 1
+                    if dk < 0:
+                        pts.append([a[k] - 1])
+                    elif dk > 0:
+                        pts.append([a[k] + s])
+                    else:
+                        pts.append(list(range(a[k], a[k] + s)))
+                for pt in np.array(np.meshgrid(*pts, indexing="ij")).reshape(dim, -1).T:
+                    pt = [int(p) % size if (periodic >> k) & 1 else int(p) for k, p in enumerate(pt)]
+                    if any(p < 0 or p >= size for p in pt):
+                        continue
+                    nb = find_leaf(tuple(int(p) for p in pt))
+                    if nb is not None and nb[1] < l - 1:
+                        na, nl = nb
+                        del leaves[na]
+                        for ca, cl in _children(na, nl, dim, L):
+                            leaves[ca] = cl
+                        changed = True
+    return leaves
+
+
+def refine_and_balance(oc: Octants, target) -> Octants:
+    """Each octant split down to ``target`` (its level at least), then 2:1 balanced with
+    ``balance_leaves`` (small meshes only: pure Python)."""
+    L, dim = oc.max_level, oc.dim
+    leaves: dict[tuple, int] = {}
+
+    def put(a, l, t):
+        if l >= t:
+            leaves[a] = l
+            return
+        for ca, cl in _children(a, l, dim, L):
+            put(ca, cl, t)
+
+    for a, l, t in zip(oc.anchors, oc.levels, target):
+        put(tuple(int(v) for v in a), int(l), int(t))
+    balance_leaves(leaves, dim, L, oc.periodic)
+    anchors = np.array(sorted(leaves.keys()), dtype=np.int32)
+    levels = np.array([leaves[tuple(int(v) for v in a)] for a in anchors], dtype=np.uint8)
+    return Octants(dim, L, anchors, levels, int(oc.periodic))
+
+
 def random_balanced_octants(dim: int, base_level: int, max_level: int, frac: float, seed: int,
                             periodic: int = 0) -> Octants:
     """A seeded random 2:1-balanced octree (face, edge and corner balance).
@@ -145,48 +220,7 @@ def random_balanced_octants(dim: int, base_level: int, max_level: int, frac: flo
                 for ca, cl in children(a, lev):
                     leaves[ca] = cl
 
-    size = 1 << L
-    dirs = [d for d in np.ndindex(*([3] * dim)) if any(v != 1 for v in d)]
-
-    def find_leaf(pt):
-        # leaf containing integer point pt (inside the domain); search coarse-to-fine
-        for l in range(0, L + 1):
-            s = 1 << (L - l)
-            a = tuple((p // s) * s for p in pt)
-            if leaves.get(a) == l:
-                return a, l
-        return None
-
-    changed = True
-    while changed:
-        changed = False
-        for a, l in list(leaves.items()):
-            if leaves.get(a) != l:
-                continue
-            s = 1 << (L - l)
-            # sample points just outside each face/edge/corner, at the finest spacing
-            for d in dirs:
-                pts = []
-                for k in range(dim):
-                    dk = d[k] - 1
-                    if dk < 0:
-                        pts.append([a[k] - 1])
-                    elif dk > 0:
-                        pts.append([a[k] + s])
-                    else:
-                        pts.append(list(range(a[k], a[k] + s)))
-                # iterate over the boundary strip at the finest resolution (small meshes only)
-                for pt in np.array(np.meshgrid(*pts, indexing="ij")).reshape(dim, -1).T:
-                    pt = [int(p) % size if (periodic >> k) & 1 else int(p) for k, p in enumerate(pt)]
-                    if any(p < 0 or p >= size for p in pt):
-                        continue
-                    nb = find_leaf(tuple(int(p) for p in pt))
-                    if nb is not None and nb[1] < l - 1:
-                        na, nl = nb
-                        del leaves[na]
-                        for ca, cl in children(na, nl):
-                            leaves[ca] = cl
-                        changed = True
+    balance_leaves(leaves, dim, L, periodic)
     anchors = np.array(sorted(leaves.keys()), dtype=np.int32)
     levels = np.array([leaves[tuple(int(v) for v in a)] for a in anchors], dtype=np.uint8)
     return Octants(dim, L, anchors, levels, int(periodic))

@@ -460,3 +460,38 @@ def test_golden_boundary_table():
             assert bc.types[f, k] == W.DIRICHLET and bc.values[f, k] == float(val.replace("V", "20"))
         else:
             assert bc.types[f, k] == W.NATURAL
+
+
+def test_element_range_sums_reproduce_the_serial_oracle():
+    """The element-range entry points (used to time the oracle across host threads on a
+    sample of elements) add up, over a partition of the elements and run concurrently from
+    several threads, to the serial residual and J V on every PDE row."""
+    import threading
+    oc = W.random_balanced_octants(3, 1, 4, 0.3, 17)
+    m = O.OracleMesh(oc)
+    bcs = W.membrane_bcs(3, 5.0, 2.0)
+    p = O.Params(eps=0.05, dt=0.01, beta=(1.5, -2.0, 0.5), bc_type=bcs.types, bc_val=bcs.values)
+    L = oc.max_level
+    U, Uk, Ukm1 = (W.random_state(m.ijk, L, s) for s in (1, 2, 3))
+    V = W.random_direction(m.ijk, L, 4)
+    vel = W.random_velocity(m.ijk, L, 5, 0.5)
+    F = m.residual(p, U, Uk, Ukm1, vel)
+    JV = m.jv(p, U, V, Uk, Ukm1, vel)
+    cuts = np.linspace(0, m.n_elem, 5).astype(int)
+    parts = [(np.zeros((m.n_nodes, 3)), np.zeros((m.n_nodes, 3))) for _ in range(4)]
+
+    def run(i):
+        m.residual_elements(p, U, Uk, Ukm1, vel, cuts[i], cuts[i + 1], parts[i][0])
+        m.jv_elements(p, U, V, Uk, Ukm1, vel, cuts[i], cuts[i + 1], parts[i][1])
+
+    th = [threading.Thread(target=run, args=(i,)) for i in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    kind, _ = m.bc_rows(p)
+    pde = (kind == 0) & (m.hanging[:, None] == 0)
+    Fs = sum(a for a, _ in parts)
+    Js = sum(b for _, b in parts)
+    assert np.abs(Fs[pde] - F[pde]).max() <= 1e-13 * np.abs(F[pde]).max()
+    assert np.abs(Js[pde] - JV[pde]).max() <= 1e-13 * np.abs(JV[pde]).max()
