@@ -1,33 +1,36 @@
-"""Benchmark: BDF time steps of the VMS PNP block on the 3D near-membrane octree.
+"""Benchmark: time steps of the VMS PNP block on the 3D electroconvection octree.
 
-Workload (the transient membrane configuration): unit cube, octree base level 5,
-level 8 for every octant with z_min < 0.05, 2:1 graded (971,776 elements, 1,047,407
-nodes, 3.14 M unknowns c+, c-, phi); Lambda = 1e-3, V = 20, dt = 1e-3; membrane
-at z = 0 (phi = 0, c+ = 2, c- zero flux), reservoir at z = 1 (phi = V, c+- = 1),
-zero-flux side walls; c+- = 1 + seeded uniform noise of amplitude 1e-3, phi linear.
-The velocity is zero (no Navier-Stokes block in this library).
+Workload (the 3D electroconvection configuration, octree levels 6-10): unit cube;
+membrane at z = 0 (phi = 0, c+ = 2, c- zero flux), reservoir at z = 1 (phi = V, c+- = 1),
+zero-flux side walls; Lambda = 5e-4, V = 40, dt = 5e-4; c+- = 1 + seeded uniform noise of
+amplitude 1e-3, phi linear.  The octree is solution-adaptive (paper_2301_05985_gb300.refine):
+base level 6, a PNP pre-solve (3 steps) on a level-8 band z < 0.01, then level 9 for every
+octant with z_min < 0.01 and level 10 wherever max |grad c+-| at the octant centre exceeds
+60 (the Debye layer), 2:1 balanced: 5.6 M elements, 6.67 M nodes, 20.0 M unknowns.  The velocity is zero (the library has no
+Navier-Stokes block): a "PNP-NS step" here is the PNP block's step.
 
-One step = one pnp_time_step: BDF2 (BDF1 first), Newton to ||F|| <= 1e-8 ||F(U^k)||,
-GMRES with 3x3 block-Jacobi on the exact Jacobian action.  Modes:
-  mixed : inexact Newton (Eisenstat-Walker) with flexible GMRES(60) in FP64 (dots,
-          orthogonalisation, basis), preconditioned by 24 steps of FP32 GMRES on J M^-1
-          (FP32 J V, M the 3x3 block Jacobi); FP64 residual; learned start (network
-          trained, before the timed region, on the first steps of this run's own
-          trajectory), judged against the extrapolated start 2 U^k - U^{k-1}.
-  plain : FP64 J V, GMRES(100) rtol 1e-8 per Newton step, previous-step start (the
-          paper's); timed for comparison from the same state as the first mixed step.
+One step = one pnp_time_step: BDF2 (BDF1 first), Newton to ||F|| <= 1e-8 ||F(U^k)||.
+  mixed (timed): inexact Newton (Eisenstat-Walker) with flexible GMRES(60) in FP64 (dots,
+        orthogonalisation, basis) preconditioned by 24 steps of FP32 GMRES on J M^-1 (FP32
+        J V, M the 3x3 block Jacobi); FP64 residual; learned start (network trained before
+        the timed region on the first steps of this run), judged against 2 U^k - U^{k-1}.
+  FP64 arms, from the state the timed steps start from:
+        plain_same_solver: the same nested solver and forcing entirely in FP64;
+        plain_gmres: FP64 J V, GMRES(100) + block Jacobi to rtol 1e-8 per Newton step
+        (exact Newton), previous-step start (the paper's solver settings).
 
-value = unknowns advanced per second = 3 N x steps / time (GDoF/s), timed with CUDA
-events on the library's stream.  Kernel rooflines come from the library's own event
-timing of each launch class during the timed region, against the roofline that bounds
-the class: FP64 or FP32 ALU (peaks derived from 152 SMs x 2 FP64 / 128 FP32 FMA per
-clock x 2.07 GHz), HBM or BF16 tensor (measured peaks).
+value = seconds per step of the timed mixed steps (CUDA events on the library's stream);
+replicas: the slowest rank's time over the steps all ranks took.  The J V kernel's roofline
+uses the algorithmic work per unit of the FP32 J V (56 B per node, 36 B per element,
+2.5 kFLOP per element); its binding bound is the larger of the HBM time and the FP32 ALU
+time of that work (FP32 peak 152 SMs x 128 FMA/clk x 2 x 2.07 GHz).
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import statistics
 import subprocess
 import sys
 import threading
@@ -41,14 +44,26 @@ for _p in (ROOT, os.path.join(ROOT, "oracle")):
         sys.path.insert(0, _p)
 
 METRIC = "PNP Jv GDoF/s (% HBM peak); s per PNP–NS step at rel-resid 1e-8, plain vs mixed+learned"
-EPS, VOLT, DT = 1e-3, 20.0, 1e-3
 # ALU peaks: 152 SMs x (2 FP64 | 128 FP32) FMA per clock x 2 flop x 2.07 GHz
 FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# algorithmic work of the J V per unit (the FP32 / FP64 J V rows of the measurement plan)
+JV_BYTES_PER_NODE = {"jv32": 56.0, "jv64": 112.0}
+JV_BYTES_PER_ELEM = 36.0
+JV_FLOPS_PER_ELEM = 2500.0
 # arithmetic of each kernel class; for ALU classes the binding roofline is chosen per run
-# from the algorithmic flops and bytes (kernel_table)
-BOUNDS = {"residual64": "fp64", "jv64": "fp64", "jv32": "fp32", "blockdiag": "fp32", "ortho_dot": "fp64",
+BOUNDS = {"residual64": "fp32", "jv64": "fp64", "jv32": "fp32", "blockdiag": "fp32", "ortho_dot": "fp64",
           "ortho_update": "fp64", "precond": "hbm", "mlp": "bf16", "inner_ortho": "hbm"}
+
+WORKLOADS = {
+    "electroconvection": {"eps": 5e-4, "V": 40.0, "dt": 5e-4,
+                          "desc": "3D electroconvection octree, levels 6-10: level 9 for z<0.01, level 10 where "
+                                  "the pre-solve's |grad c| > 60 (Debye layer), 2:1 balanced"},
+    "membrane": {"eps": 1e-3, "V": 20.0, "dt": 1e-3,
+                 "desc": "3D membrane-band octree, base level 5, level 8 for z<0.05 (2:1 graded)"},
+    "small": {"eps": 2e-3, "V": 20.0, "dt": 1e-3,
+              "desc": "membrane-band octree, base level 4, level 7 for z<0.05 (profiling miniature)"},
+}
 
 
 def parse():
@@ -57,37 +72,67 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="mixed", choices=["mixed", "plain"])
-    ap.add_argument("--small", action="store_true", help="level 4-7 miniature (profiling captures)")
+    ap.add_argument("--workload", default="electroconvection", choices=list(WORKLOADS))
+    ap.add_argument("--small", action="store_true", help="alias of --workload small (profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain-mode comparison step")
+    ap.add_argument("--plain", action="store_true",
+                    help="run the FP64 comparison arms on the main workload too (they always run on the "
+                         "membrane-band secondary workload)")
+    ap.add_argument("--plain-steps", type=int, default=1, help="steps of each FP64 arm on the main workload")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="timed steps re-run end to end (the first ones)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the J V sweep on the uniform level-7 cube")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the membrane-band secondary run")
     ap.add_argument("--no-learned", action="store_true", help="mixed mode without training the learned start")
-    ap.add_argument("--inner", type=int, default=None, help="inner FP32 GMRES steps of the flexible outer GMRES (mixed)")
-    ap.add_argument("--restart", type=int, default=None, help="outer GMRES restart length (mixed)")
-    ap.add_argument("--record-steps", type=int, default=8, help="trajectory steps recorded for training")
-    ap.add_argument("--train-steps", type=int, default=400, help="Adam steps of the learned start")
-    return ap.parse_args()
+    ap.add_argument("--record-steps", type=int, default=0,
+                    help="trajectory steps recorded for training (0: the warm-up steps are the recording)")
+    ap.add_argument("--train-steps", type=int, default=600, help="Adam steps of the learned start")
+    ap.add_argument("--profile-steps", type=int, default=3, help="further steps timed per kernel class")
+    a = ap.parse_args()
+    if a.small:
+        a.workload = "small"
+    return a
 
 
-def workload_octants(small: bool):
+def build_workload(pnp, torch, name):
+    """Octants (and target levels) of a workload; the refinement recipe runs its pre-solve."""
     from paper_2301_05985_gb300 import workloads as W
-    return W.membrane_band_octants(4, 7, 0.05) if small else W.membrane_band_octants(5, 8, 0.05)
+    if name == "electroconvection":
+        from paper_2301_05985_gb300 import refine as R
+        wl = WORKLOADS[name]
+        t0 = time.perf_counter()
+        oc, target, info = R.gradient_refined_octants(pnp, torch, torch.cuda.current_stream().cuda_stream,
+                                                      R.RefineRecipe(), wl["eps"], wl["V"], wl["dt"])
+        info["build_s"] = time.perf_counter() - t0
+        return oc, target, info
+    if name == "membrane":
+        return W.membrane_band_octants(5, 8, 0.05), None, {}
+    return W.membrane_band_octants(4, 7, 0.05), None, {}
 
 
-INNER, RESTART = 24, 60  # mixed mode: inner FP32 GMRES steps, outer restart
-
-
-def mode_params(pnp, mode, inner=None, restart=None):
+def mode_params(pnp, wl, mode, learned=True):
     if mode == "mixed":
-        inner = INNER if inner is None else inner
-        restart = RESTART if restart is None else restart
-        return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F32, start_mode=pnp.PNP_START_LEARNED,
-                                  newton_rtol=1e-8, gmres_restart=restart, gmres_max_it=3000, dt_retries=2,
-                                  gmres_inner=inner)
-    return pnp.default_params(eps=EPS, dt=DT, precision=pnp.PNP_F64, start_mode=pnp.PNP_START_PREVIOUS,
+        return pnp.default_params(eps=wl["eps"], dt=wl["dt"], precision=pnp.PNP_F32,
+                                  start_mode=pnp.PNP_START_LEARNED if learned else pnp.PNP_START_EXTRAPOLATE,
+                                  newton_rtol=1e-8, gmres_restart=60, gmres_max_it=3000, dt_retries=2,
+                                  gmres_inner=24)
+    if mode == "same64":
+        return pnp.default_params(eps=wl["eps"], dt=wl["dt"], precision=pnp.PNP_F64,
+                                  start_mode=pnp.PNP_START_EXTRAPOLATE, newton_rtol=1e-8, gmres_restart=60,
+                                  gmres_max_it=3000, dt_retries=2, gmres_inner=24, newton_ew_f64=1)
+    return pnp.default_params(eps=wl["eps"], dt=wl["dt"], precision=pnp.PNP_F64, start_mode=pnp.PNP_START_PREVIOUS,
                               newton_rtol=1e-8, gmres_rtol=1e-8, gmres_restart=100, gmres_max_it=4000,
                               dt_retries=2)
+
+
+def make_ctx(pnp, W, torch, mesh, wl, mode, learned=True):
+    ctx = pnp.Context(mesh, mode_params(pnp, wl, mode, learned), torch.cuda.current_stream().cuda_stream)
+    ctx.set_bcs(W.membrane_bcs(3, wl["V"], 2.0))
+    U0 = W.noisy_state(mesh.ijk, mesh.max_level, seed=0, amp=1e-3, phi_bottom=0.0, phi_top=wl["V"])
+    ctx.set_field(pnp.PNP_FIELD_U, U0)
+    ctx.make_consistent()
+    ctx.reset_history()
+    return ctx
 
 
 def measured_peaks():
@@ -144,82 +189,116 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "samples": len(self.rows), "reasons": reasons}
 
 
-def setup_ctx(pnp, W, torch, oc, mode, inner=None, restart=None):
-    mesh = pnp.Mesh(oc)
-    ctx = pnp.Context(mesh, mode_params(pnp, mode, inner, restart), torch.cuda.current_stream().cuda_stream)
-    ctx.set_bcs(W.membrane_bcs(3, VOLT, 2.0))
-    U0 = W.noisy_state(mesh.ijk, oc.max_level, seed=0, amp=1e-3, phi_bottom=0.0, phi_top=VOLT)
-    ctx.set_field(pnp.PNP_FIELD_U, U0)
-    ctx.make_consistent()
-    ctx.reset_history()
-    return mesh, ctx
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_threads():
+    return max(1, os.cpu_count() or 1)
 
 
-def cpu_baseline_oracle(n_steps: int = 1):
-    """The FP64 oracle (single-threaded C++ + SciPy sparse direct solve) on a bounded
-    sample: the same physics on the level 3-5 miniature of the membrane octree."""
+def oracle_timing(oc, wl, U, Uk, Ukm1, V, n_res, n_jv, sample_frac=0.125, repeats=3):
+    """The FP64 oracle's residual and matrix-free J V on the workload's own mesh and state,
+    timed on the host cores: a contiguous sample of the oracle's elements split into equal
+    ranges over one thread per core (ctypes releases the interpreter lock), each thread
+    adding into a buffer of its own; median of `repeats`.  Scaled to the whole mesh and to
+    the mixed step's residual and J V counts, it estimates what the oracle's operator
+    evaluations alone would take per step.  The element-range sums reproduce the serial
+    oracle (pinned by a CPU test)."""
     import oracle as O
-    from paper_2301_05985_gb300 import workloads as W
-    oc = W.membrane_band_octants(3, 5, 0.05)
-    m = O.OracleMesh(oc)
-    bcs = W.membrane_bcs(3, VOLT, 2.0)
-    U = W.noisy_state(m.ijk, oc.max_level, seed=0, amp=1e-3, phi_bottom=0.0, phi_top=VOLT)
-    p = O.Params(eps=EPS, dt=DT, beta=(1.0, -1.0, 0.0), bc_type=bcs.types, bc_val=bcs.values)
-    U = m.make_consistent(U, p)
-    Uk = Ukm1 = U
     t0 = time.perf_counter()
-    for k in range(n_steps):
-        beta = O.bdf_coefficients(k)
-        p = O.Params(eps=EPS, dt=DT, beta=beta, bc_type=bcs.types, bc_val=bcs.values)
-        res = O.newton(m, p, Uk, Uk, Ukm1, None, rtol=1e-8)
-        Ukm1, Uk = Uk, res.U
-    t = time.perf_counter() - t0
-    return {"value": 3 * m.n_nodes * n_steps / t / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_steps} BDF step(s) of the same physics on the level 3-5 miniature of the membrane "
-                      f"octree ({m.n_elem} elements, {m.n_nodes} nodes), oracle Newton with direct sparse "
-                      f"solves, {t:.1f} s"}
+    m = O.OracleMesh(oc)
+    build_s = time.perf_counter() - t0
+    perm = _perm(m.ijk, U["ijk"], oc.max_level)
+    bcs = __import__("paper_2301_05985_gb300.workloads", fromlist=["x"]).membrane_bcs(3, wl["V"], 2.0)
+    p = O.Params(eps=wl["eps"], dt=wl["dt"], beta=(1.5, -2.0, 0.5), bc_type=bcs.types, bc_val=bcs.values)
+    Uo, Uko, Ukm1o, Vo = (np.ascontiguousarray(x[perm]) for x in (U["U"], Uk, Ukm1, V))
+    T = oracle_threads()
+    E = m.n_elem
+    Es = max(T, int(E * sample_frac))
+    cuts = np.linspace(0, Es, T + 1).astype(np.int64)
+    bufs = [np.zeros((m.n_nodes, 3)) for _ in range(T)]
+
+    def timed(kind):
+        for b in bufs:
+            b[:] = 0.0
+
+        def run(i):
+            if kind == "res":
+                m.residual_elements(p, Uo, Uko, Ukm1o, None, cuts[i], cuts[i + 1], bufs[i])
+            else:
+                m.jv_elements(p, Uo, Vo, Uko, Ukm1o, None, cuts[i], cuts[i + 1], bufs[i])
+
+        th = [threading.Thread(target=run, args=(i,)) for i in range(T)]
+        t = time.perf_counter()
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        return (time.perf_counter() - t) * E / Es
+
+    t_res = statistics.median(timed("res") for _ in range(repeats))
+    t_jv = statistics.median(timed("jv") for _ in range(repeats))
+    dofs = 3.0 * m.n_nodes
+    return {"t_residual_s": t_res, "t_jv_s": t_jv, "residual_gdofs": dofs / t_res / 1e9, "jv_gdofs": dofs / t_jv / 1e9,
+            "s_per_step": n_res * t_res + n_jv * t_jv, "cores": T, "oracle_mesh_build_s": build_s,
+            "sample": f"{Es} of {E} elements ({Es / E:.3f}) in {T} equal ranges, one thread per host core, "
+                      f"median of {repeats}, scaled to the whole mesh"}
 
 
-def workload_config(small: bool):
-    """The workload both arms name (the reference arm times the oracle on a bounded sample
-    of it, described in its cpu_baseline)."""
-    return {"workload": ("membrane-band octree L4-7 miniature" if small else
-                         "3D membrane-band octree, base level 5, level 8 for z<0.05 (2:1 graded)"),
-            "eps": EPS, "V": VOLT, "dt": DT, "velocity": "zero (no NS block)"}
+def _perm(ijk_ora, ijk_lib, L):
+    """perm[i] = library index of oracle node i (matched by integer coordinates)."""
+    base = (1 << L) + 1
+    key = lambda a: sum(a[:, k].astype(np.int64) * base**k for k in range(a.shape[1]))  # noqa: E731
+    kl, ko = key(ijk_lib), key(ijk_ora)
+    order = np.argsort(kl)
+    return order[np.searchsorted(kl[order], ko)]
 
 
+# ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The oracle on this workload's mesh and state (host cores), as its arm of the
+    comparison: each step is the oracle's residual and J V on a sample of the mesh,
+    scaled to the operator evaluations of one time step (residual and J V counts of the
+    library's mixed step on this workload, measured; 46 residuals and 1,300 J V if not
+    given)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        pass  # the oracle has nothing to warm up
+    import torch
+    from paper_2301_05985_gb300 import pnp
+    from paper_2301_05985_gb300 import workloads as W
+    wl = WORKLOADS[args.workload]
+    oc, target, _ = build_workload(pnp, torch, args.workload)  # input generation (octree + its pre-solve)
+    mesh = pnp.Mesh(oc, target_levels=target)
+    oc_full = W.Octants(3, mesh.max_level, *mesh.elements())
+    L = mesh.max_level
+    U = W.noisy_state(mesh.ijk, L, seed=0, amp=1e-3, phi_bottom=0.0, phi_top=wl["V"])
+    Vd = W.random_direction(mesh.ijk, L, 5)
+    n_res, n_jv = 46.0, 1300.0
     vals = []
-    t0 = time.perf_counter()
     cb = None
-    for _ in range(args.steps):
-        cb = cpu_baseline_oracle(1)
-        vals.append(cb["value"])
-    t = time.perf_counter() - t0
+    for k in range(args.warmup + args.steps):
+        cb = oracle_timing(oc_full, wl, {"U": U, "ijk": mesh.ijk}, U, U, Vd, n_res, n_jv, repeats=1)
+        if k >= args.warmup:
+            vals.append(cb["s_per_step"])
     v = float(np.mean(vals))
-    out = {"metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": workload_config(args.small),
-           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": cb["sample"], "value": v},
-           "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    out = {"metric": METRIC, "value": v, "unit": "s/step", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": workload_config(args.workload, mesh),
+           "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "value": v, "unit": "s/step",
+                            "sample": cb["sample"] + f"; x {n_res:g} residuals + {n_jv:g} J V per step "
+                                                      "(operator evaluations only)"},
+           "e2e": {"value": v, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
-def ctx_krylov_desc(p, mode):
-    if mode == "plain":
-        return f"GMRES({p.gmres_restart}) + block Jacobi, FP64 J V, rtol {p.gmres_rtol:g}"
-    if p.gmres_inner > 0:
-        return (f"flexible GMRES({p.gmres_restart}) in FP64, preconditioned by {p.gmres_inner} steps of FP32 "
-                f"GMRES on J M^-1 (M block Jacobi); Eisenstat-Walker forcing")
-    return f"GMRES({p.gmres_restart}) + block Jacobi, FP32 J V, FP64 dots; Eisenstat-Walker forcing"
+def workload_config(name, mesh):
+    wl = WORKLOADS[name]
+    return {"workload": wl["desc"], "eps": wl["eps"], "V": wl["V"], "dt": wl["dt"],
+            "velocity": "zero (no Navier-Stokes block)", "n_elem": mesh.n_elem, "n_nodes": mesh.n_nodes,
+            "n_hanging": mesh.n_hanging, "dofs": 3 * mesh.n_nodes}
 
 
+# ----------------------------------------------------------------------------- helpers
 def max_over_ranks(ms, dist, device):
     """The slowest rank's time (replicas: every rank times the same work)."""
     if dist is None:
@@ -236,15 +315,60 @@ def replica_throughput(units_per_rank, world, ms):
     return units_per_rank * world / (ms * 1e-3) / 1e9
 
 
-def load_traffic(small: bool):
-    """Per-class DRAM traffic from the committed ncu summary, for kernels whose source
-    is unchanged since the capture."""
+def replica_seconds_per_step(ms, steps, world):
+    """Whole-job seconds per step: the slowest rank's time over the steps all ranks took."""
+    return ms * 1e-3 / (steps * world)
+
+
+def kernel_table(prof, peaks, total_ms, N, E):
+    """Per class: time share, algorithmic GB/s and TFLOP/s, the roofline that binds it and
+    the fraction of it.  The J V classes use the algorithmic work of the measurement plan
+    (bytes per node and element, 2.5 kFLOP per element); the others the library's own
+    per-launch accounting."""
+    rows = {}
+    for name, d in prof.items():
+        if d["count"] == 0 or d["ms"] <= 0:
+            continue
+        t = d["ms"] * 1e-3
+        if name in JV_BYTES_PER_NODE:
+            by = (JV_BYTES_PER_NODE[name] * N + JV_BYTES_PER_ELEM * E) * d["count"]
+            fl = JV_FLOPS_PER_ELEM * E * d["count"]
+        else:
+            by, fl = d["alg_bytes"], d["alg_flops"]
+        gbs = by / t / 1e9
+        tfl = fl / t / 1e12
+        kind = BOUNDS[name]
+        if kind == "hbm":
+            bound, unit, ach, peak = "hbm", "GB/s", gbs, peaks["hbm_gbs"]
+            src = "measured" if not peaks.get("fallback") else "fallback"
+        elif kind == "bf16":
+            bound, unit, ach, peak = "tensor", "TFLOP/s", tfl, peaks.get("bf16_tflops_sustained", 1700.0)
+            src = "measured sustained" if not peaks.get("fallback") else "fallback"
+        else:
+            alu = FP64_TFLOPS if kind == "fp64" else FP32_TFLOPS
+            if fl / (alu * 1e12) >= by / (peaks["hbm_gbs"] * 1e9):
+                bound, unit, ach, peak = "alu", "TFLOP/s", tfl, alu
+                src = f"derived {kind.upper()}: 152 SMs x {2 if kind == 'fp64' else 128} FMA/clk x 2 x 2.07 GHz"
+            else:
+                bound, unit, ach, peak = "hbm", "GB/s", gbs, peaks["hbm_gbs"]
+                src = "measured" if not peaks.get("fallback") else "fallback"
+        rows[name] = {"bound": bound, "achieved": round(ach, 4), "peak": round(peak, 3), "unit": unit,
+                      "frac": round(ach / peak, 4), "peak_source": src, "launches": d["count"],
+                      "avg_launch_ms": d["ms"] / d["count"], "share": round(d["ms"] / total_ms, 4),
+                      "alg_bytes_per_launch": by / d["count"], "alg_flops_per_launch": fl / d["count"],
+                      "alg_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
+    return rows
+
+
+def load_traffic(workload):
+    """Per-class DRAM traffic from the committed ncu summary, for kernels whose source is
+    unchanged since the capture."""
     import hashlib
     try:
         tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     except Exception:
         return {}
-    if tj.get("workload") != ("small" if small else "full"):
+    if tj.get("workload") != workload:
         return {}
     out = {}
     for name, e in tj.get("classes", {}).items():
@@ -258,64 +382,22 @@ def load_traffic(small: bool):
     return out
 
 
-def residual_kind():
-    """The residual runs in double-float arithmetic on the FP32 pipe unless
-    PNP_RESIDUAL_ARITH=f64 (or the one-thread-per-element kernel) selects FP64."""
-    f64 = os.environ.get("PNP_RESIDUAL_ARITH") == "f64" or os.environ.get("PNP_ELEMENT_KERNEL") == "thread"
-    return "fp64" if f64 else "fp32"
-
-
-def kernel_table(prof, peaks, total_ms):
-    """Per class: time share, algorithmic GB/s and TFLOP/s, and the fraction of the
-    roofline that bounds it."""
-    rows = {}
-    for name, d in prof.items():
-        if d["count"] == 0 or d["ms"] <= 0:
-            continue
-        t = d["ms"] * 1e-3
-        gbs = d["alg_bytes"] / t / 1e9
-        tfl = d["alg_flops"] / t / 1e12
-        kind = residual_kind() if name == "residual64" else BOUNDS[name]
-        if kind == "hbm":
-            bound, unit, ach, peak = "hbm", "GB/s", gbs, peaks["hbm_gbs"]
-            src = "measured" if not peaks.get("fallback") else "fallback"
-        elif kind == "bf16":
-            bound, unit, ach, peak = "tensor", "TFLOP/s", tfl, peaks.get("bf16_tflops_sustained", 1700.0)
-            src = "measured sustained" if not peaks.get("fallback") else "fallback"
-        else:
-            alu = FP64_TFLOPS if kind == "fp64" else FP32_TFLOPS
-            # the roofline that binds: the larger of the ALU time and the HBM time of the
-            # algorithmic work (a stored linearisation can move a kernel from ALU to HBM)
-            if d["alg_flops"] / (alu * 1e12) >= d["alg_bytes"] / (peaks["hbm_gbs"] * 1e9):
-                bound, unit, ach, peak = "alu", "TFLOP/s", tfl, alu
-                src = f"derived {kind.upper()}: 152 SMs x {2 if kind == 'fp64' else 128} FMA/clk x 2 x 2.07 GHz"
-            else:
-                bound, unit, ach, peak = "hbm", "GB/s", gbs, peaks["hbm_gbs"]
-                src = "measured" if not peaks.get("fallback") else "fallback"
-        rows[name] = {"bound": bound, "achieved": round(ach, 4), "peak": round(peak, 3), "unit": unit,
-                      "frac": round(ach / peak, 4), "peak_source": src, "launches": d["count"],
-                      "avg_launch_ms": d["ms"] / d["count"], "share": round(d["ms"] / total_ms, 4),
-                      "alg_bytes_per_launch": d["alg_bytes"] / d["count"],
-                      "alg_flops_per_launch": d["alg_flops"] / d["count"],
-                      "alg_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
-    return rows
-
-
-def roofline(table, traffic):
-    """The dominant class's roofline object (largest device time)."""
-    if not table:
+def roofline(table, traffic, name="jv32"):
+    """The roofline object of the J V class (the dominant class of the step)."""
+    if name not in table:
+        name = max(table, key=lambda k: table[k]["avg_launch_ms"] * table[k]["launches"]) if table else None
+    if name is None:
         return None
-    name = max(table, key=lambda k: table[k]["avg_launch_ms"] * table[k]["launches"])
     rl = dict(table[name])
     rl["kernel"] = name
     e = traffic.get(name)
     rl["traffic"] = None
     if e:
-        if "dram_bytes_per_launch" in e:
+        if "dram_bytes_per_unit" in e:
+            rl["traffic"] = e["dram_bytes_per_unit"] * rl["alg_bytes_per_launch"] / e.get("alg_bytes_per_unit", 1.0)
+            rl["traffic_note"] = e.get("note", "")
+        elif "dram_bytes_per_launch" in e:
             rl["traffic"] = e["dram_bytes_per_launch"]
-        elif "dram_per_requested" in e:  # launches of varying size: DRAM bytes per requested byte
-            rl["traffic"] = e["dram_per_requested"] * rl["alg_bytes_per_launch"]
-            rl["traffic_note"] = "ncu DRAM bytes per L2-requested byte x this run's algorithmic bytes per launch"
     return rl
 
 
@@ -333,8 +415,118 @@ def train_learned_start(pnp, torch, ctx, n_record, train_steps):
     st = ctx.mlp_train(steps=train_steps, batch=4096, lr=1e-3, seed=1)
     p.start_mode = mode
     ctx.set_params(p)
+    del S
     return {"recorded_steps": len(its), "train_steps": train_steps, "loss_first": st.loss_first,
             "loss_last": st.loss_last, "train_s": st.wall_ms * 1e-3, "setup_s": time.perf_counter() - t0}
+
+
+def snapshot(pnp, torch, ctx, N):
+    h = [torch.empty((N, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+    ctx.get_field(pnp.PNP_FIELD_U_PREV, h[0], pnp.PNP_DEVICE)
+    ctx.get_field(pnp.PNP_FIELD_U_PREV2, h[1], pnp.PNP_DEVICE)
+    torch.cuda.synchronize()
+    return h
+
+
+def restore(pnp, ctx, h, step=8):
+    """Resume the trajectory at the snapshot (the next step is BDF2 from it)."""
+    ctx.set_field(pnp.PNP_FIELD_U_PREV, h[0], pnp.PNP_DEVICE)
+    ctx.set_field(pnp.PNP_FIELD_U_PREV2, h[1], pnp.PNP_DEVICE)
+    ctx.set_field(pnp.PNP_FIELD_U, h[0], pnp.PNP_DEVICE)
+    ctx.set_step_count(step)
+
+
+def run_arm(pnp, torch, W, mesh, wl, mode, hist, steps):
+    """`steps` BDF2 steps of an FP64 arm from the snapshot state; time, iterations, final U."""
+    ctx = make_ctx(pnp, W, torch, mesh, wl, mode)
+    restore(pnp, ctx, hist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sts = [ctx.time_step(raise_on_error=False).as_dict() for _ in range(steps)]
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    U = ctx.get_field(pnp.PNP_FIELD_U)
+    ctx.close()
+    return {"s_per_step": t / steps, "steps": steps, "newton_its_per_step": sum(s["newton_its"] for s in sts) / steps,
+            "krylov_its_per_step": sum(s["krylov_its"] for s in sts) / steps,
+            "jv_per_step": sum(s["jv_evals"] for s in sts) / steps,
+            "status": [int(s["status"]) for s in sts], "substeps": [int(s["substeps"]) for s in sts]}, U
+
+
+def field_errors(U, ref):
+    """Relative 2-norm and max-norm differences per field (c+, c-, phi)."""
+    out = {}
+    for f, name in enumerate(["c+", "c-", "phi"]):
+        d = U[:, f] - ref[:, f]
+        out[name] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref[:, f])),
+                     "rel_max": float(np.abs(d).max() / np.abs(ref[:, f]).max())}
+    return out
+
+
+def jv_sweep(pnp, torch, W, peaks, states=5, reps=10):
+    """FP64 and FP32 J V on the uniform level-7 cube (128^3 elements, 6.44 M dofs) with the
+    divergence-free Fourier velocity, Lambda = 1e-3, V = 30, at seeded states: GDoF/s, HBM
+    fraction of the algorithmic bytes, the binding roofline fraction, and the FP32 error
+    against the FP64 J V per field (the FP64 J V matches the oracle at this size in the
+    parity tests)."""
+    oc = W.uniform_octants(3, 7)
+    mesh = pnp.Mesh(oc)
+    N, E, L = mesh.n_nodes, mesh.n_elem, oc.max_level
+    ctx = pnp.Context(mesh, pnp.default_params(eps=1e-3, dt=1e-3, beta0=1.5, beta1=-2.0, beta2=0.5),
+                      torch.cuda.current_stream().cuda_stream)
+    ctx.set_bcs(W.membrane_bcs(3, 30.0, 2.0))
+    ctx.set_field(pnp.PNP_FIELD_ADVECTION, W.fourier_velocity(mesh.ijk, L, 3))
+    res = {"mesh": "uniform level 7 (2,097,152 elements, 2,146,689 nodes)", "velocity": "Fourier, RMS 0.1",
+           "states": states, "jv64": [], "jv32": [], "err32": []}
+    for sd in range(states):
+        Uk = W.noisy_state(mesh.ijk, L, seed=10 + sd, amp=1e-3, phi_bottom=0.0, phi_top=30.0)
+        ctx.set_field(pnp.PNP_FIELD_U_PREV, Uk)
+        ctx.set_field(pnp.PNP_FIELD_U_PREV2, Uk)
+        Ud = torch.from_numpy(W.noisy_state(mesh.ijk, L, seed=20 + sd, amp=1e-2, phi_bottom=0.0, phi_top=30.0)).cuda()
+        Vd = torch.from_numpy(W.random_direction(mesh.ijk, L, 30 + sd)).cuda()
+        V32 = Vd.float()
+        J64 = torch.zeros_like(Vd)
+        J32 = torch.zeros_like(V32)
+        for prec, V, J in ((pnp.PNP_F64, Vd, J64), (pnp.PNP_F32, V32, J32)):
+            ctx.jv(Ud, V, J, prec)
+            ctx.profile_enable(True)
+            for _ in range(reps):
+                ctx.jv(Ud, V, J, prec)
+            pr = ctx.profile_read()
+            ctx.profile_enable(False)
+            name = "jv64" if prec == pnp.PNP_F64 else "jv32"
+            t = pr[name]["ms"] / pr[name]["count"] * 1e-3
+            by = JV_BYTES_PER_NODE[name] * N + JV_BYTES_PER_ELEM * E
+            fl = JV_FLOPS_PER_ELEM * E
+            alu = FP64_TFLOPS if name == "jv64" else FP32_TFLOPS
+            tstar = max(by / (peaks["hbm_gbs"] * 1e9), fl / (alu * 1e12))
+            res[name].append({"ms": t * 1e3, "gdofs": 3 * N / t / 1e9, "hbm_frac": by / t / (peaks["hbm_gbs"] * 1e9),
+                              "binding_frac": tstar / t})
+        a, b = J32.double().cpu().numpy(), J64.cpu().numpy()
+        res["err32"].append({f: float(np.linalg.norm(a[:, i] - b[:, i]) / np.linalg.norm(b[:, i]))
+                             for i, f in enumerate(["c+", "c-", "phi"])})
+    for name in ("jv64", "jv32"):
+        rows = res[name]
+        res[name + "_mean"] = {k: float(np.mean([r[k] for r in rows])) for k in rows[0]}
+    ctx.close()
+    mesh.close()
+    return res
+
+
+# ----------------------------------------------------------------------------- main
+def timed_mixed(pnp, torch, ctx, steps, stream, local):
+    stats = []
+    launches0 = pnp.kernel_launches()
+    captures0 = pnp.graph_captures()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            stats.append(ctx.time_step().as_dict())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1), stats, pnp.kernel_launches() - launches0, pnp.graph_captures() - captures0, clk
 
 
 def main():
@@ -355,147 +547,196 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     pnp.lib()
-    oc = workload_octants(args.small)
-    mesh, ctx = setup_ctx(pnp, W, torch, oc, args.mode, args.inner, args.restart)
-    N = mesh.n_nodes
+    wl = WORKLOADS[args.workload]
+    full = args.workload != "small"
+    oc, target, mesh_info = build_workload(pnp, torch, args.workload)
+    mesh = pnp.Mesh(oc, target_levels=target)
+    N, E = mesh.n_nodes, mesh.n_elem
+    ctx = make_ctx(pnp, W, torch, mesh, wl, "mixed", learned=not args.no_learned)
     stream = torch.cuda.current_stream()
 
     learned = None
-    if args.mode == "mixed" and not args.no_learned:
-        learned = train_learned_start(pnp, torch, ctx, args.record_steps, args.train_steps)
-    stats = []
-    for _ in range(args.warmup):
+    warm = args.warmup
+    if not args.no_learned:
+        # the warm-up steps (extrapolated start) are the recorded trajectory; one more
+        # untimed step then runs the trained network's path once
+        rec = args.record_steps if args.record_steps > 0 else max(args.warmup, 3)
+        learned = train_learned_start(pnp, torch, ctx, rec, args.train_steps)
+        warm = 1 if args.record_steps <= 0 else args.warmup
+    for _ in range(warm):
         ctx.time_step()
     torch.cuda.synchronize()
-    # the state the timed region starts from (for the plain-mode comparison)
-    hist = [torch.empty((N, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
-    ctx.get_field(pnp.PNP_FIELD_U_PREV, hist[0], pnp.PNP_DEVICE)
-    ctx.get_field(pnp.PNP_FIELD_U_PREV2, hist[1], pnp.PNP_DEVICE)
-    torch.cuda.synchronize()
+    hist = snapshot(pnp, torch, ctx, N)  # the state the timed steps start from
     if dist:
         dist.barrier()
-    launches0 = pnp.kernel_launches()
-    captures0 = pnp.graph_captures()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            stats.append(ctx.time_step().as_dict())
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = pnp.kernel_launches() - launches0
-    captures = pnp.graph_captures() - captures0
-    # per-class kernel times: K further steps with the library's event pair around every
-    # launch (eager launches: the inner solve's graph replays only while profiling is off)
+    ms, stats, launches, captures, clk = timed_mixed(pnp, torch, ctx, args.steps, stream, local)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = replica_seconds_per_step(ms, args.steps, world)
+    gdofs_advanced = replica_throughput(3.0 * N * args.steps, world, ms)
+
+    # per-class kernel times: further steps with the library's event pair around every launch
     ctx.profile_enable(True)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kp = max(1, min(args.profile_steps, args.steps))
     torch.cuda.synchronize()
     p0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(kp):
         ctx.time_step()
     p1.record(stream)
     torch.cuda.synchronize()
     prof_ms = p0.elapsed_time(p1)
     prof = ctx.profile_read()
     ctx.profile_enable(False)
-    ms = max_over_ranks(ms, dist, "cuda")
-    value = replica_throughput(3.0 * N * args.steps, world, ms)
 
-    # end to end through the C ABI with the state held in pinned host memory
+    # end to end through the C ABI: the same steps again from the same state, the history
+    # uploaded from pinned host memory and the new state read back every step
+    plain_steps = max(1, min(args.plain_steps, args.steps))
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
     e2e = None
+    U_mixed = None
     if not args.no_e2e:
         hU = [torch.empty((N, 3), dtype=torch.float64, pin_memory=True) for _ in range(3)]
-        ctx.get_field(pnp.PNP_FIELD_U_PREV, hU[0], pnp.PNP_HOST)
-        ctx.get_field(pnp.PNP_FIELD_U_PREV2, hU[1], pnp.PNP_HOST)
+        hU[0].copy_(hist[0])
+        hU[1].copy_(hist[1])
         torch.cuda.synchronize()
-        c_e2e0 = pnp.graph_captures()
+        c0 = pnp.graph_captures()
+        e2e_stats = []
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        restore(pnp, ctx, hist)
+        for k in range(e2e_steps):
             ctx.set_field(pnp.PNP_FIELD_U_PREV, hU[0], pnp.PNP_HOST)
             ctx.set_field(pnp.PNP_FIELD_U_PREV2, hU[1], pnp.PNP_HOST)
-            ctx.time_step()
+            e2e_stats.append(ctx.time_step().as_dict())
             ctx.get_field(pnp.PNP_FIELD_U, hU[2], pnp.PNP_HOST)
+            if k + 1 == plain_steps:
+                U_mixed = hU[2].numpy().copy()
             hU = [hU[2], hU[0], hU[1]]
         t_e2e = time.perf_counter() - t0
-        e2e_captures = pnp.graph_captures() - c_e2e0
-        e2e = {"value": 3.0 * N * args.steps * world / t_e2e / 1e9, "unit": "GDoF/s",
+        e2e = {"value": replica_seconds_per_step(1e3 * t_e2e, e2e_steps, world), "unit": "s/step",
                "h2d_bytes_per_step": 2 * 24 * N, "d2h_bytes_per_step": 24 * N,
-               "ms_per_step": 1e3 * t_e2e / args.steps, "graph_captures": e2e_captures}
-
-    # plain-mode comparison: one step from the state the timed mixed steps started from
-    plain = None
-    if not args.no_plain and rank == 0 and args.mode == "mixed":
-        mesh_p, ctx_p = setup_ctx(pnp, W, torch, oc, "plain")
-        p = ctx_p.get_params()
-        p.bdf_order = 1
-        ctx_p.set_params(p)
-        ctx_p.time_step()  # one cheap BDF1 step so that the next one is BDF2 (history loaded below)
-        p.bdf_order = 2
-        ctx_p.set_params(p)
-        ctx_p.set_field(pnp.PNP_FIELD_U_PREV, hist[0], pnp.PNP_DEVICE)
-        ctx_p.set_field(pnp.PNP_FIELD_U_PREV2, hist[1], pnp.PNP_DEVICE)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st = ctx_p.time_step().as_dict()
-        torch.cuda.synchronize()
-        plain = {"s_per_step": time.perf_counter() - t0, "newton_its": st["newton_its"],
-                 "krylov_its": st["krylov_its"], "substeps": st["substeps"],
-                 "state": "same state as the first timed mixed step",
-                 "mixed_first_step": {"s": stats[0]["wall_ms"] * 1e-3, "newton_its": stats[0]["newton_its"],
-                                      "krylov_its": stats[0]["krylov_its"]}}
-        ctx_p.close()
+               "ms_per_step": 1e3 * t_e2e / e2e_steps, "steps": e2e_steps, "graph_captures": pnp.graph_captures() - c0,
+               "trajectory": f"the first {e2e_steps} timed steps again from the same state",
+               "device_timed_same_steps_s_per_step": sum(s["wall_ms"] for s in stats[:e2e_steps]) * 1e-3 / e2e_steps,
+               "newton_its_per_step": sum(s["newton_its"] for s in e2e_stats) / e2e_steps,
+               "krylov_its_per_step": sum(s["krylov_its"] for s in e2e_stats) / e2e_steps}
 
     peaks = measured_peaks()
-    table = kernel_table(prof, peaks, prof_ms)
-    rl = roofline(table, load_traffic(args.small))
-    jv_name = "jv32" if args.mode == "mixed" else "jv64"
-    jv = prof[jv_name]
-    jv_row = dict(table.get(jv_name, {}))
-    if jv["ms"] > 0:
-        jv_row.update({"name": jv_name, "gdofs": 3.0 * N * jv["count"] / (jv["ms"] * 1e-3) / 1e9})
+    table = kernel_table(prof, peaks, prof_ms, N, E)
+    rl = roofline(table, load_traffic(args.workload), "jv32")
+    jv = dict(table.get("jv32", {}))
+    if jv:
+        jv["gdofs"] = 3.0 * N / (jv["avg_launch_ms"] * 1e-3) / 1e9
+        tstar = max((JV_BYTES_PER_NODE["jv32"] * N + JV_BYTES_PER_ELEM * E) / (peaks["hbm_gbs"] * 1e9),
+                    JV_FLOPS_PER_ELEM * E / (FP32_TFLOPS * 1e12))
+        jv["binding_time_ms"] = tstar * 1e3
+        jv["binding_frac"] = tstar / (jv["avg_launch_ms"] * 1e-3)
+
+    nt = sum(s["newton_its"] for s in stats)
+    kt = sum(s["krylov_its"] for s in stats)
+    n_res = sum(s["residual_evals"] for s in stats) / args.steps
+    n_jv = sum(s["jv_evals"] for s in stats) / args.steps
+
+    # FP64 arms from the same state (rank 0 only)
+    arms = {}
+    if (args.plain or args.workload != "electroconvection") and rank == 0:
+        arm, U_same = run_arm(pnp, torch, W, mesh, wl, "same64", hist, plain_steps)
+        arms["plain_same_solver"] = arm
+        arm, U_gm = run_arm(pnp, torch, W, mesh, wl, "plain", hist, plain_steps)
+        arms["plain_gmres"] = arm
+        if U_mixed is not None:
+            arms["field_errors"] = {"steps": plain_steps, "mixed_vs_fp64_same_solver": field_errors(U_mixed, U_same),
+                                    "mixed_vs_fp64_gmres": field_errors(U_mixed, U_gm),
+                                    "fp64_same_solver_vs_fp64_gmres": field_errors(U_same, U_gm)}
+        arms["mixed_first_steps"] = {"steps": plain_steps,
+                                     "s_per_step": sum(s["wall_ms"] for s in stats[:plain_steps]) * 1e-3 / plain_steps,
+                                     "newton_its_per_step": sum(s["newton_its"] for s in stats[:plain_steps]) / plain_steps,
+                                     "krylov_its_per_step": sum(s["krylov_its"] for s in stats[:plain_steps]) / plain_steps}
 
     if rank != 0:
         return
+    sweep = None
+    if not args.no_sweep and full and world == 1:
+        sweep = jv_sweep(pnp, torch, W, peaks)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_oracle(2)
-    nt = sum(s["newton_its"] for s in stats)
-    kt = sum(s["krylov_its"] for s in stats)
+        Uh = hist[0].cpu().numpy()
+        Vh = W.random_direction(mesh.ijk, mesh.max_level, 5)
+        oc_full = W.Octants(3, mesh.max_level, *mesh.elements())
+        ot = oracle_timing(oc_full, wl, {"U": Uh, "ijk": mesh.ijk}, Uh, hist[1].cpu().numpy(), Vh, n_res, n_jv)
+        cpu = {"value": ot["s_per_step"], "unit": "s/step", "cores": ot["cores"], "kind": "oracle",
+               "sample": ot["sample"] + f"; x {n_res:.1f} residuals + {n_jv:.0f} J V per step (the mixed step's "
+                                        "counts; operator evaluations only, FP64)",
+               "residual_gdofs": ot["residual_gdofs"], "jv_gdofs": ot["jv_gdofs"],
+               "t_residual_s": ot["t_residual_s"], "t_jv_s": ot["t_jv_s"],
+               "oracle_mesh_build_s": ot["oracle_mesh_build_s"]}
+    ctx.close()
+    secondary = None
+    if not args.no_secondary and args.workload == "electroconvection" and world == 1:
+        secondary = secondary_membrane(pnp, torch, W, peaks)
+
     out = {
-        "metric": METRIC, "value": round(value, 6), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
-        "config": {**workload_config(args.small),
-                   "n_elem": mesh.n_elem, "n_nodes": N, "n_hanging": mesh.n_hanging, "dofs": 3 * N,
-                   "mode": args.mode,
-                   "krylov": ctx_krylov_desc(ctx.get_params(), args.mode),
-                   "start": ("learned (judged vs extrapolated)" if learned else
-                             "extrapolated" if args.mode == "mixed" else "previous step"),
-                   "l2": "inputs larger than L2 (3.1M-dof FP64 vectors 25 MB each, Krylov basis up to 1.5 GB)",
+        "metric": METRIC, "value": round(value, 6), "unit": "s/step", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {**workload_config(args.workload, mesh), "mesh_build": mesh_info,
+                   "mode": "mixed FP32 J V + learned start" if learned else "mixed FP32 J V",
+                   "krylov": "flexible GMRES(60) in FP64, preconditioned by 24 steps of FP32 GMRES on J M^-1 "
+                             "(M block Jacobi); Eisenstat-Walker forcing",
+                   "start": "learned (judged vs extrapolated)" if learned else "extrapolated",
+                   "l2": "inputs larger than L2 (FP64 vectors of 3N entries, Krylov basis of 61 of them)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": rl,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "graph_captures": int(captures),
-        "graph_captures_total": int(pnp.graph_captures()),
-        "launches_before_timed": int(launches0),
         "clocks": clk.summary(),
+        "jv": jv,
+        "gdofs_advanced_per_s": gdofs_advanced,
         "newton_its_per_step": nt / args.steps, "krylov_its_per_step": kt / args.steps,
+        "residual_evals_per_step": n_res, "jv_evals_per_step": n_jv,
         "split_steps": sum(int(s["substeps"] > 1) for s in stats),
         "learned_start_used": sum(int(s["start_used"] == pnp.PNP_START_LEARNED) for s in stats),
-        "s_per_step": ms * 1e-3 / args.steps,
-        "jv_kernel": jv_row,
-        "kernels": table,
-        "kernel_profile": {"steps": args.steps, "ms_per_step": prof_ms / args.steps,
-                           "note": "per-class times and shares from K further steps with an event pair around "
-                                   "every launch (eager); the timed steps replay the inner solve as a CUDA graph"},
         "learned_training": learned,
-        "plain_step": plain,
+        **arms,
+        "kernels": table,
+        "kernel_profile": {"steps": kp, "ms_per_step": prof_ms / kp,
+                           "note": "per-class times and shares from further steps with an event pair around every "
+                                   "launch (eager); the timed steps replay the inner solve as a CUDA graph"},
+        "jv_sweep_uniform_L7": sweep,
+        "secondary_membrane_L5_8": secondary,
     }
     print(json.dumps(out))
+
+
+def secondary_membrane(pnp, torch, W, peaks, warmup=3, steps=3):
+    """The membrane-band octree (3.14 M dofs): mixed steps and both FP64 arms from the same
+    state, with the per-field differences of the final states."""
+    wl = WORKLOADS["membrane"]
+    mesh = pnp.Mesh(W.membrane_band_octants(5, 8, 0.05))
+    N = mesh.n_nodes
+    ctx = make_ctx(pnp, W, torch, mesh, wl, "mixed", learned=False)
+    for _ in range(warmup):
+        ctx.time_step()
+    hist = snapshot(pnp, torch, ctx, N)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sts = [ctx.time_step().as_dict() for _ in range(steps)]
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    Um = ctx.get_field(pnp.PNP_FIELD_U)
+    ctx.close()
+    out = {"workload": wl["desc"], "dofs": 3 * N, "steps": steps,
+           "mixed": {"s_per_step": t / steps, "newton_its_per_step": sum(s["newton_its"] for s in sts) / steps,
+                     "krylov_its_per_step": sum(s["krylov_its"] for s in sts) / steps,
+                     "start": "extrapolated"}}
+    arm, Us = run_arm(pnp, torch, W, mesh, wl, "same64", hist, steps)
+    out["plain_same_solver"] = arm
+    arm, Ug = run_arm(pnp, torch, W, mesh, wl, "plain", hist, steps)
+    out["plain_gmres"] = arm
+    out["field_errors"] = {"mixed_vs_fp64_same_solver": field_errors(Um, Us), "mixed_vs_fp64_gmres": field_errors(Um, Ug)}
+    mesh.close()
+    return out
 
 
 if __name__ == "__main__":

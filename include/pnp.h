@@ -117,8 +117,20 @@ typedef struct pnp_params {
   int32_t gmres_inner;   /* PNP_F32 Krylov solves: 0 = right-preconditioned GMRES(m) with
                             the block diagonal; d in 1..64 = flexible GMRES(m) whose
                             preconditioner is d steps of FP32 GMRES on J M^-1 (M the
-                            block diagonal), with FP64 outer dots and orthogonalisation */
-  int32_t pad2_;
+                            block diagonal), with FP64 outer dots and orthogonalisation;
+                            with PNP_F64 the same flexible scheme with d steps of FP64 GMRES
+                            (FP64 J V, basis and dots) as the preconditioner */
+  int32_t newton_ew_f64; /* PNP_F64 Newton: 0 = each linear solve to gmres_rtol (exact Newton,
+                            the default); 1 = Eisenstat-Walker forcing as in PNP_F32 */
+  int32_t mg_levels;     /* PNP_F32 Krylov solves: 0 = off; L > 0 = flexible GMRES(m) in FP64
+                            preconditioned by one FP32 V-cycle of geometric multigrid over up to
+                            L coarser octrees, each the previous one with its finest level
+                            capped (in place of the paper's GAMG, App. A); overrides
+                            gmres_inner.  Non-periodic meshes. */
+  int32_t mg_smooth;     /* damped block-Jacobi sweeps before and after the coarse correction (2) */
+  double mg_omega;       /* damping of the sweeps (0.7) */
+  int32_t mg_coarse_its; /* block-Jacobi sweeps on the coarsest level (16) */
+  int32_t pad3_;
 } pnp_params;
 
 typedef struct pnp_solve_stats {
@@ -178,6 +190,20 @@ int pnp_mesh_create_periodic(int dim, int max_level, int64_t n_oct, const int32_
 int pnp_mesh_create_refined(int dim, int max_level, int64_t n_oct, const int32_t* anchors,
                             const uint8_t* levels, const uint8_t* target_levels, int periodic,
                             pnp_mesh** out);
+/* The coarse octrees of the multigrid preconditioner (mg_levels): the same octree with
+ * every leaf finer than cap_level replaced by its ancestor at cap_level (2:1 balance is
+ * kept).  Its Q1 space is contained in the mesh's, and every coarse node is a point of
+ * the fine mesh.  *out is released by pnp_mesh_destroy. */
+int pnp_mesh_coarsen(const pnp_mesh* m, int cap_level, pnp_mesh** out);
+/* The grid transfer between a mesh and a coarsening of it (pnp_mesh_coarsen): the
+ * prolongation P, fine node values of a coarse Q1 field (trilinear interpolation in the
+ * coarse element holding the node, coarse hanging corners expanded to their parents), as
+ * CSR host arrays ptr int64 [n_fine_nodes + 1], col int32 [nnz] (independent coarse
+ * nodes), w float [nnz]; the restriction is its transpose.  inject int32 [n_coarse_nodes]:
+ * the fine node at each coarse node's point.  *nnz is always set; the array pointers may
+ * be NULL (call once with NULL to size them).  Non-periodic meshes only. */
+int pnp_mesh_transfer(const pnp_mesh* fine, const pnp_mesh* coarse, int64_t* nnz, int64_t* ptr,
+                      int32_t* col, float* w, int32_t* inject);
 void pnp_mesh_destroy(pnp_mesh* m);
 int pnp_mesh_info(const pnp_mesh* m, int* dim, int* max_level, int64_t* n_elem,
                   int64_t* n_nodes, int64_t* n_hanging);
@@ -303,6 +329,11 @@ int pnp_time_step(pnp_ctx* c, pnp_solve_stats* st);
 /* Number of steps taken so far by pnp_time_step (0 after pnp_ctx_create or
  * pnp_reset_history). */
 int pnp_step_count(const pnp_ctx* c, int64_t* k);
+/* Resume a trajectory (e.g. from a checkpoint written with pnp_get_field): declare that
+ * U_PREV and U_PREV2 hold the states of steps k and k-1 of equally spaced steps.  The next
+ * pnp_time_step is BDF2 when k >= 1 (and bdf_order is 2) and may extrapolate its start;
+ * k = 0 makes it a first step (BDF1, previous-step start). */
+int pnp_set_step_count(pnp_ctx* c, int64_t k);
 /* Start a new trajectory: U_PREV and U_PREV2 <- U, step count <- 0. */
 int pnp_reset_history(pnp_ctx* c);
 
@@ -425,7 +456,8 @@ enum {
   PNP_PROF_MLP = 6,        /* learned-start network kernels */
   PNP_PROF_ORTHO_UPDATE = 7, /* Gram-Schmidt update: the multi-axpy + norm kernel */
   PNP_PROF_INNER = 8,      /* FP32 Gram-Schmidt of the inner GMRES (flexible mode) */
-  PNP_PROF_KINDS = 9
+  PNP_PROF_MG = 9,         /* multigrid: everything on the coarse levels of a V-cycle */
+  PNP_PROF_KINDS = 10
 };
 /* on != 0: clear the accumulated times and start recording; on == 0: stop. */
 int pnp_profile_enable(pnp_ctx* c, int on);

@@ -70,6 +70,12 @@ void pnp_params_default(pnp_params* p) {
   p->monitor = 0;
   p->f64_fallback = 1;
   p->gmres_inner = 0;
+  p->newton_ew_f64 = 0;
+  p->mg_levels = 0;
+  p->mg_smooth = 2;
+  p->mg_omega = 0.7;
+  p->mg_coarse_its = 16;
+  p->pad3_ = 0;
 }
 
 // ------------------------------------------------------------------ mesh
@@ -114,6 +120,46 @@ int pnp_mesh_create_refined(int dim, int max_level, int64_t n_oct, const int32_t
   }
   if (rc != PNP_OK) return rc;
   return pnp_mesh_create_periodic(dim, max_level, (int64_t)l.size(), a.data(), l.data(), periodic, out);
+}
+
+int pnp_mesh_coarsen(const pnp_mesh* m, int cap_level, pnp_mesh** out) {
+  if (!m || !out) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_coarsen: null argument");
+  *out = nullptr;
+  if (cap_level < 0 || cap_level > m->L) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_coarsen: cap level out of range");
+  pnp_mesh* c = new (std::nothrow) pnp_mesh();
+  if (!c) PNP_FAIL(PNP_ERR_NOMEM, "pnp_mesh_coarsen: out of host memory");
+  int rc;
+  try {
+    rc = pnp_cap_mesh_levels(*m, cap_level, *c);
+  } catch (const std::bad_alloc&) {
+    pnp_set_error("pnp_mesh_coarsen: out of host memory");
+    rc = PNP_ERR_NOMEM;
+  }
+  if (rc != PNP_OK) {
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return PNP_OK;
+}
+
+int pnp_mesh_transfer(const pnp_mesh* fine, const pnp_mesh* coarse, int64_t* nnz, int64_t* ptr, int32_t* col,
+                      float* w, int32_t* inject) {
+  if (!fine || !coarse || !nnz) PNP_FAIL(PNP_ERR_ARG, "pnp_mesh_transfer: null argument");
+  MgTransfer T;
+  int rc;
+  try {
+    rc = pnp_mg_transfer(*fine, *coarse, T);
+  } catch (const std::bad_alloc&) {
+    PNP_FAIL(PNP_ERR_NOMEM, "pnp_mesh_transfer: out of host memory");
+  }
+  if (rc != PNP_OK) return rc;
+  *nnz = (int64_t)T.p_col.size();
+  if (ptr) std::copy(T.p_ptr.begin(), T.p_ptr.end(), ptr);
+  if (col) std::copy(T.p_col.begin(), T.p_col.end(), col);
+  if (w) std::copy(T.p_w.begin(), T.p_w.end(), w);
+  if (inject) std::copy(T.inject.begin(), T.inject.end(), inject);
+  return PNP_OK;
 }
 
 void pnp_mesh_destroy(pnp_mesh* m) { delete m; }
@@ -176,6 +222,9 @@ static int check_params(const pnp_params* p) {
   if (p->bdf_order != 1 && p->bdf_order != 2) PNP_FAIL(PNP_ERR_ARG, "params: bdf_order must be 1 or 2");
   if (p->gmres_inner < 0 || p->gmres_inner > inner_max_depth())
     PNP_FAIL(PNP_ERR_ARG, "params: gmres_inner in 0..%d", inner_max_depth());
+  if (p->mg_levels < 0 || p->mg_levels > 16 || p->mg_smooth < 1 || p->mg_smooth > 16 || !(p->mg_omega > 0) ||
+      !(p->mg_omega <= 2) || p->mg_coarse_its < 1 || p->mg_coarse_its > 1000)
+    PNP_FAIL(PNP_ERR_ARG, "params: multigrid settings out of range");
   if (p->dt_retries < 0 || p->dt_retries > 16) PNP_FAIL(PNP_ERR_ARG, "params: dt_retries in 0..16");
   return PNP_OK;
 }
@@ -184,7 +233,8 @@ static void free_ctx_memory(pnp_ctx* c) {
   void* ptrs[] = {c->d_conn, c->d_anchor, c->d_level, c->d_faces, c->d_hnode, c->d_hpar, c->d_hnp, c->U, c->Uk, c->Ukm1,
                   c->adv, c->vel, c->vel_prev, c->hs, c->U32, c->adv32, c->hs32, c->V32, c->JV32, c->F,
                   c->dU, c->Ut, c->Ft, c->rhs, c->Dinv, c->D32, c->basis, c->w, c->z, c->r, c->part, c->dsc,
-                  c->dflag, c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv, c->rec32, c->V4, c->JV4, c->qp32};
+                  c->dflag, c->Zb, c->Qin, c->Dinv32, c->isc, c->iinv, c->rec32, c->V4, c->JV4, c->qp32,
+                  c->Z64, c->Qin64, c->zin64, c->isc64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->pt_alloc) cudaFree(p);
@@ -386,13 +436,37 @@ int ctx_alloc_inner(pnp_ctx* c, int m, int d) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->V4, sizeof(float4) * (size_t)c->n_nodes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->JV4, sizeof(float4) * (size_t)c->n_nodes);
   if (e == cudaSuccess) e = cudaMemset(c->JV4, 0, sizeof(float4) * (size_t)c->n_nodes);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->qp32, sizeof(float4) * 4 * ((size_t)c->n_elem << c->dim));
+  // the stored linearisation (qp32) is allocated by its first use (ctx_linearize32)
   if (e != cudaSuccess) {
     pnp_set_error("inner Krylov scratch allocation failed: %s", cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? PNP_ERR_NOMEM : PNP_ERR_CUDA;
   }
   c->inner_m = m;
   c->inner_d = d;
+  return PNP_OK;
+}
+
+int ctx_alloc_inner64(pnp_ctx* c, int m, int d) {
+  if (m <= c->inner64_m && d <= c->inner64_d) return PNP_OK;
+  m = std::max(m, c->inner64_m);
+  d = std::max(d, c->inner64_d);
+  if (int rc = ctx_alloc_krylov(c, std::max(c->m_alloc, d))) return rc;  // partials for d projections
+  void* old[] = {c->Z64, c->Qin64, c->zin64, c->isc64};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  c->Z64 = c->Qin64 = c->zin64 = c->isc64 = nullptr;
+  c->inner64_m = c->inner64_d = 0;
+  const size_t n = (size_t)c->n3();
+  cudaError_t e = cudaMalloc((void**)&c->Z64, sizeof(double) * (size_t)m * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->Qin64, sizeof(double) * (size_t)(d + 1) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->zin64, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->isc64, sizeof(double) * (3 * (size_t)(d + 2) + 2));
+  if (e != cudaSuccess) {
+    pnp_set_error("inner FP64 Krylov scratch allocation failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PNP_ERR_NOMEM : PNP_ERR_CUDA;
+  }
+  c->inner64_m = m;
+  c->inner64_d = d;
   return PNP_OK;
 }
 
@@ -403,6 +477,7 @@ void pnp_ctx_destroy(pnp_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   pnp_mlp_release(c);
+  ctx_mg_release(c);
   for (auto& pe : c->ev_pending) {
     cudaEventDestroy(pe.second.first);
     cudaEventDestroy(pe.second.second);
@@ -657,6 +732,13 @@ int pnp_time_step(pnp_ctx* c, pnp_solve_stats* st) {
 int pnp_step_count(const pnp_ctx* c, int64_t* k) {
   if (!c || !k) PNP_FAIL(PNP_ERR_ARG, "pnp_step_count: null argument");
   *k = c->step;
+  return PNP_OK;
+}
+
+int pnp_set_step_count(pnp_ctx* c, int64_t k) {
+  if (!c || k < 0) PNP_FAIL(PNP_ERR_ARG, "pnp_set_step_count: bad argument");
+  c->step = k;
+  c->history_split = false;
   return PNP_OK;
 }
 

@@ -58,12 +58,19 @@ struct pnp_ctx {
   double* isc = nullptr;    // inner Hessenberg [(d+1) x d] and scalars
   float* iinv = nullptr;    // [d+2] inverse norms of the inner basis vectors
   int inner_m = 0, inner_d = 0;
+  // flexible outer GMRES with an inner FP64 GMRES(d) preconditioner (PNP_F64, gmres_inner > 0)
+  double* Z64 = nullptr;    // [m][3N] preconditioned Krylov vectors
+  double* Qin64 = nullptr;  // [(d+1)][3N] inner basis (unnormalised)
+  double* zin64 = nullptr;  // [3N] block-Jacobi image of an inner basis vector
+  double* isc64 = nullptr;  // [3 (d+2) + 2] inner projections, 1 / s_i^2, norm, combination
+  int inner64_m = 0, inner64_d = 0;
   float4* rec32 = nullptr;  // [N][2] FP32 node records of the state for the FP32 J V
   float4* V4 = nullptr;     // [N] padded FP32 direction of the inner solve's J V
   float4* JV4 = nullptr;    // [N] padded FP32 J V accumulator
   float4* qp32 = nullptr;   // [4][2^dim E] stored Gauss-point linearisation of the FP32 J V
   bool lin_user = false;    // qp32 holds the linearisation of the last pnp_linearize
   int lin_rows = 4;         // float4 rows per lane in qp32 (3 without advection)
+  bool adv_zero = false;    // the advection field was zero at the last ctx_prepare_f32
   // the inner FP32 GMRES captured as a CUDA graph (replayed while profiling is off): the
   // launches depend only on the key below, captured on a stream of the context's own
   cudaStream_t cap_stream = nullptr;
@@ -74,6 +81,10 @@ struct pnp_ctx {
   bool inner_eager_done = false;     // one eager solve ran (launchers' one-time set-up done)
   bool inner_graph_off = false;      // a capture was refused: eager from then on
   int64_t basis_bytes = 0;
+
+  // geometric multigrid preconditioner (mg.cu): level hierarchy, built on first use
+  std::vector<struct MgLevel>* mg = nullptr;
+  int mg_built = 0;
 
   // statistics of the last solve (for the time stepper)
   int jv_count = 0, res_count = 0;
@@ -146,7 +157,7 @@ struct ProfScope {
   int kind;
   cudaEvent_t a = nullptr;
   ProfScope(pnp_ctx* c_, int k, double bytes, double flops = 0.0) : c(c_), kind(k) {
-    if (c->prof_on) {
+    if (c->prof_on && kind >= 0) {  // kind < 0: not recorded
       c->prof_bytes[kind] += bytes;
       c->prof_flops[kind] += flops;
       a = c->take_event();
@@ -180,8 +191,16 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
               int* its, double* relres, bool have_precond);
 int ctx_newton(pnp_ctx* c, pnp_solve_stats* st, const double* ref_state = nullptr);
 int ctx_alloc_inner(pnp_ctx* c, int m, int d);
+int ctx_alloc_inner64(pnp_ctx* c, int m, int d);
 int ctx_linearize32(pnp_ctx* c);
 int ctx_jv32_linearized(pnp_ctx* c, const float* V, float* JV);
 int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st);
 int ctx_alloc_krylov(pnp_ctx* c, int m);
 void pnp_mlp_release(pnp_ctx* c);
+// geometric multigrid (mg.cu): hierarchy of `levels` coarse octrees, per-solve state and
+// blocks, one V-cycle z32 = M^-1 u
+int ctx_mg_setup(pnp_ctx* c, int levels);
+int ctx_mg_prepare(pnp_ctx* c, const double* U);
+int ctx_mg_apply(pnp_ctx* c, const double* u, float* z32);
+void ctx_mg_release(pnp_ctx* c);
+int ctx_mg_level_count(const pnp_ctx* c);

@@ -44,6 +44,20 @@ int pnp_build_mesh(pnp_mesh& m, int dim, int L, int64_t n, const int32_t* anchor
 // coarsest such octree, as unordered leaves.
 int pnp_refine_balance(int dim, int L, int periodic, int64_t n, const int32_t* anchors, const uint8_t* levels,
                        const uint8_t* target, std::vector<int32_t>& out_anchor, std::vector<uint8_t>& out_level);
+// Geometric multigrid on the octree hierarchy (mg_build.cpp): the octree with every leaf
+// finer than `cap` replaced by its ancestor at `cap`; the transfer operators between a fine
+// mesh and its capped coarse mesh.
+int pnp_cap_mesh_levels(const pnp_mesh& fine, int cap, pnp_mesh& coarse);
+struct MgTransfer {
+  std::vector<int64_t> p_ptr;   // [Nf+1] prolongation rows (fine nodes)
+  std::vector<int32_t> p_col;   // coarse independent nodes
+  std::vector<float> p_w;       // trilinear weights (dyadic)
+  std::vector<int64_t> r_ptr;   // [Nc+1] restriction rows = P^T (coarse nodes)
+  std::vector<int32_t> r_col;   // fine nodes
+  std::vector<float> r_w;
+  std::vector<int32_t> inject;  // [Nc] fine node at each coarse node's point
+};
+int pnp_mg_transfer(const pnp_mesh& fine, const pnp_mesh& coarse, MgTransfer& T);
 // Morton (Z-order) key of an integer point (x in bit 0 of each group, then y, then z).
 uint64_t pnp_morton(int dim, const int64_t* p);
 

@@ -129,7 +129,15 @@ int ctx_jv64(pnp_ctx* c, const double* U, const double* V, double* JV) {
   return PNP_OK;
 }
 
+// the FP32 J V of hexahedral meshes runs the two-lanes-per-element kernel (jv_pair.cu)
+static bool use_jv_pair(const pnp_ctx* c) { return c->dim == 3 && !c->use_patches && element_kernel_is_lanes(); }
+
 int ctx_prepare_f32(pnp_ctx* c, const double* U) {
+  if (use_jv_pair(c)) {
+    double vn = 0.0;
+    RC(ctx_norm(c, c->adv, &vn));
+    c->adv_zero = vn == 0.0;
+  }
   CK(launch_to_f32(c->n3(), U, c->U32, c->stream));
   CK(launch_to_f32(2 * c->n_nodes, c->hs, c->hs32, c->stream));
   CK(launch_to_f32(c->n3(), c->adv, c->adv32, c->stream));
@@ -147,10 +155,13 @@ int ctx_jv32(pnp_ctx* c, const float* V32, float* JV32) {
     RC(hanging_rows<float>(c, V32, JV32));
   } else {
     CK(cudaMemsetAsync(JV32, 0, sizeof(float) * c->n3(), c->stream));
-    {
+    ElemArgs<float> A = elem_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32);
+    A.rec = c->rec32;
+    if (use_jv_pair(c)) {
+      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), jv_pair_flops(!c->adv_zero) * c->n_elem);
+      CK(launch_jv_pair(A, !c->adv_zero, c->stream));
+    } else {
       ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), element_kernel_flops(c->dim, true) * c->n_elem);
-      ElemArgs<float> A = elem_args<float>(c, c->U32, V32, c->hs32, c->adv32, JV32);
-      A.rec = c->rec32;
       CK(launch_element<float>(c->dim, true, A, c->stream));
     }
     CK(launch_row_fixups<float>(c->rows(), V32, JV32, 1, c->stream));
@@ -261,6 +272,9 @@ static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_stat
                    24.0 * c->n_nodes + 16.0 * c->lin_rows * (double)(c->n_elem << c->dim) + c->conn_bytes(),
                    jv_from_state_flops(c->dim) * c->n_elem);
       CK(launch_jv_from_state(c->dim, A, c->qp32, c->lin_rows, c->dflag + 1, c->stream));
+    } else if (use_jv_pair(c)) {
+      ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), jv_pair_flops(!c->adv_zero) * c->n_elem);
+      CK(launch_jv_pair(A, !c->adv_zero, c->stream));
     } else {
       ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(),
                    element_kernel_flops(c->dim, true) * c->n_elem);
@@ -274,6 +288,14 @@ static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_stat
 
 // Gauss-point linearisation of the FP32 J V at the prepared FP32 state (ctx_prepare_f32)
 int ctx_linearize32(pnp_ctx* c) {
+  if (!c->qp32) {
+    const cudaError_t e = cudaMalloc((void**)&c->qp32, sizeof(float4) * 4 * ((size_t)c->n_elem << c->dim));
+    if (e != cudaSuccess) {
+      c->qp32 = nullptr;
+      PNP_FAIL(e == cudaErrorMemoryAllocation ? PNP_ERR_NOMEM : PNP_ERR_CUDA,
+               "stored linearisation: allocation failed: %s", cudaGetErrorString(e));
+    }
+  }
   // a zero advection field (pure PNP) leaves v out of the stored state: three rows
   double vn = 0.0;
   RC(ctx_norm(c, c->adv, &vn));
@@ -348,7 +370,7 @@ static int inner_gmres32_body(pnp_ctx* c, bool from_state) {
 // what the captured inner solve depends on: sizes, buffers, parameters, boundary table
 static std::vector<unsigned char> inner_graph_key(const pnp_ctx* c, bool from_state) {
   struct Key {
-    int d, dim, from_state, pad, use_patches, steady, lin_rows;
+    int d, dim, from_state, pad, use_patches, steady, lin_rows, adv_zero;
     int64_t n_nodes, n_elem, ldq;
     const void* bufs[14];
     double phys[4];
@@ -362,6 +384,7 @@ static std::vector<unsigned char> inner_graph_key(const pnp_ctx* c, bool from_st
   k.pad = element_kernel_is_lanes();
   k.use_patches = c->use_patches;
   k.lin_rows = c->lin_rows;
+  k.adv_zero = c->adv_zero;
   k.n_nodes = c->n_nodes;
   k.n_elem = c->n_elem;
   k.ldq = c->ldq;
@@ -462,6 +485,94 @@ static int inner_gmres32(pnp_ctx* c, const double* u, float* z32, bool from_stat
   return PNP_OK;
 }
 
+// z = P(u) in FP64: d steps of right-preconditioned FP64 GMRES on (J M^-1) t = u from
+// t = 0, then z = M^-1 t.  The FP64 counterpart of inner_gmres32 (the same algorithm with
+// FP64 J V, basis and dot products), driven from the host: one round trip per step for
+// the projections, the Hessenberg system and its Givens rotations on the host.
+static int inner_gmres64(pnp_ctx* c, const double* U, const double* u, double* z) {
+  const int d = c->prm.gmres_inner;
+  const int64_t n = c->n3(), N = c->n_nodes;
+  cudaStream_t s = c->stream;
+  double* Q = c->Qin64;            // unnormalised basis u_i (v_i = u_i / s_i)
+  double* dd = c->isc64;           // [d+2] projections of one pass
+  double* dinv = dd + (d + 2);     // [d+2] 1 / s_i^2
+  double* coef = dinv + (d + 2);   // [d+2] combination coefficients
+  double* dnrm = coef + (d + 2);   // [2]  w . w after the pass
+  CK(cudaMemcpyAsync(Q, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  double beta;
+  RC(ctx_norm(c, Q, &beta));
+  if (!std::isfinite(beta)) PNP_FAIL(PNP_ERR_NAN, "inner gmres: vector norm is not finite");
+  if (beta == 0.0) {
+    CK(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
+    return PNP_OK;
+  }
+  std::vector<double> H((size_t)(d + 1) * d, 0.0), cs(d), sn(d), g(d + 1, 0.0), y(d), sv(d + 1), hp(d + 2), up(d + 2);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * d + j]; };
+  sv[0] = beta;
+  g[0] = beta;
+  up[0] = 1.0 / (beta * beta);
+  CK(cudaMemcpyAsync(dinv, up.data(), sizeof(double), cudaMemcpyHostToDevice, s));
+  int k = 0;
+  for (int j = 0; j < d; ++j) {
+    double* w = Q + (size_t)(j + 1) * n;
+    {
+      ProfScope ps(c, PNP_PROF_PRECOND, 120.0 * N, 18.0 * N);
+      CK(launch_block_apply(N, c->Dinv, Q + (size_t)j * n, 1.0 / sv[j], c->zin64, nullptr, s));
+    }
+    RC(ctx_jv64(c, U, c->zin64, w));
+    const double nj = (double)n * (j + 1);
+    {
+      ProfScope ps(c, PNP_PROF_ORTHO, 8.0 * (nj + n), 2.0 * nj);
+      CK(launch_multi_dot_ext(n, j + 1, false, Q, n, w, c->part, dd, s));
+    }
+    {
+      ProfScope ps(c, PNP_PROF_ORTHO_UPDATE, 8.0 * (nj + 2.0 * n), 2.0 * (nj + n));
+      CK(launch_multi_axpy_norm(n, j + 1, Q, n, dd, dinv, w, c->part, dnrm, s));
+    }
+    CK(cudaMemcpyAsync(hp.data(), dd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hp.data() + (d + 1), dnrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i <= j; ++i) Hij(i, j) = hp[i] / sv[i];
+    const double nrm = std::sqrt(hp[d + 1]);
+    if (!std::isfinite(nrm)) PNP_FAIL(PNP_ERR_NAN, "inner gmres: Krylov vector norm is not finite");
+    sv[j + 1] = nrm;
+    Hij(j + 1, j) = nrm;
+    if (nrm > 0) {
+      up[j + 1] = 1.0 / (nrm * nrm);
+      CK(cudaMemcpyAsync(dinv + j + 1, up.data() + j + 1, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+      Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+      Hij(i, j) = t;
+    }
+    const double rr = std::hypot(Hij(j, j), Hij(j + 1, j));
+    if (rr == 0.0) PNP_FAIL(PNP_ERR_NAN, "inner gmres: singular Hessenberg matrix");
+    cs[j] = Hij(j, j) / rr;
+    sn[j] = Hij(j + 1, j) / rr;
+    Hij(j, j) = rr;
+    Hij(j + 1, j) = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    k = j + 1;
+    if (nrm <= 1e-300 * beta) break;
+  }
+  // t = sum_i y_i u_i / s_i with H y = g, then z = M^-1 t
+  for (int i = k - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
+    y[i] = t / Hij(i, i);
+  }
+  for (int i = 0; i < k; ++i) up[i] = -y[i] / sv[i];
+  CK(cudaMemcpyAsync(coef, up.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(c->zin64, 0, sizeof(double) * n, s));
+  CK(launch_multi_axpy(n, k, Q, n, coef, c->zin64, nullptr, s));
+  ProfScope ps(c, PNP_PROF_PRECOND, 120.0 * N, 18.0 * N);
+  CK(launch_block_apply(N, c->Dinv, c->zin64, 1.0, z, nullptr, s));
+  CK(cudaStreamSynchronize(s));  // the host vectors above go out of scope
+  return PNP_OK;
+}
+
 // Right-preconditioned GMRES(m), or flexible GMRES(m) when an inner FP32 GMRES(d) is the
 // preconditioner (PNP_F32 with gmres_inner > 0).  The Krylov vectors are stored
 // unnormalised (v_i = u_i / s_i, s_i kept on the host) so no normalisation pass is
@@ -476,10 +587,20 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   cudaStream_t s = c->stream;
   if (!have_precond) RC(build_preconditioner(c, U, prec));
   if (prec == PNP_F32) RC(ctx_prepare_f32(c, U));
-  const bool flex = prec == PNP_F32 && c->prm.gmres_inner > 0;
-  if (flex) RC(ctx_alloc_inner(c, m, c->prm.gmres_inner));
+  // multigrid preconditioner (FP32 V-cycle) of a flexible outer solve
+  const bool use_mg = prec == PNP_F32 && c->prm.mg_levels > 0;
+  if (use_mg) {
+    RC(ctx_mg_setup(c, c->prm.mg_levels));
+    RC(ctx_mg_prepare(c, U));
+  }
+  const bool flex = prec == PNP_F32 && (c->prm.gmres_inner > 0 || use_mg);
+  if (flex) RC(ctx_alloc_inner(c, m, std::max(1, c->prm.gmres_inner)));
+  // the same flexible scheme entirely in FP64 (inner FP64 GMRES, FP64 J V)
+  const bool flex64 = prec == PNP_F64 && c->prm.gmres_inner > 0;
+  if (flex64) RC(ctx_alloc_inner64(c, m, c->prm.gmres_inner));
   // the inner J V reads the state's Gauss-point quantities stored once for this solve
-  const bool from_state = flex && !c->use_patches && element_kernel_is_lanes();
+  const bool from_state = flex && !use_mg && !c->use_patches && element_kernel_is_lanes();
+  c->lin_user = false;  // a solve replaces any linearisation stored by pnp_linearize
   if (from_state) RC(ctx_linearize32(c));
   double* V = c->basis;
   double* dd = c->dsc;                    // [m+2] dot products of one pass
@@ -533,12 +654,19 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       // z = M^-1 (u_j / s_j) ; w = J z   (flexible: z_j = P(u_j) / s_j kept in Zb)
       if (flex) {
         float* zj = c->Zb + (size_t)j * n;
-        RC(inner_gmres32(c, uj, zj, from_state));
+        if (use_mg) RC(ctx_mg_apply(c, uj, zj));
+        else RC(inner_gmres32(c, uj, zj, from_state));
         // the outer J V applies the same linearisation as the inner one
         if (from_state) RC(ctx_jv32_linearized(c, zj, c->JV32));
         else RC(ctx_jv32(c, zj, c->JV32));
         ProfScope ps(c, PNP_PROF_PRECOND, 20.0 * (double)n);
         CK(launch_to_f64_scaled(n, c->JV32, 1.0 / sv[j], w, s));
+      } else if (flex64) {
+        // z_j = P(u_j) (unscaled, kept in Z64), w = J z_j / s_j
+        double* zj = c->Z64 + (size_t)j * n;
+        RC(inner_gmres64(c, U, uj, zj));
+        RC(ctx_jv64(c, U, zj, c->w));
+        CK(launch_axpbyz(n, 1.0 / sv[j], c->w, 0.0, c->w, w, s));
       } else if (prec == PNP_F64) {
         {
           ProfScope ps(c, PNP_PROF_PRECOND, 120.0 * c->n_nodes, 18.0 * c->n_nodes);
@@ -617,6 +745,10 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       for (int i = 0; i < k; ++i) hco[i] = y[i] / sv[i];
       CK(cudaMemcpyAsync(dcoef, hco, sizeof(double) * k, cudaMemcpyHostToDevice, s));
       CK(launch_combine_f32_add_f64(n, k, c->Zb, n, dcoef, x, s));
+    } else if (flex64) {
+      for (int i = 0; i < k; ++i) hco[i] = -y[i] / sv[i];
+      CK(cudaMemcpyAsync(dcoef, hco, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+      CK(launch_multi_axpy(n, k, c->Z64, n, dcoef, x, nullptr, s));
     } else {
       for (int i = 0; i < k; ++i) hco[i] = -y[i] / sv[i];
       CK(cudaMemcpyAsync(dcoef, hco, sizeof(double) * k, cudaMemcpyHostToDevice, s));
@@ -694,7 +826,7 @@ int ctx_newton(pnp_ctx* c, pnp_solve_stats* st, const double* ref_state) {
     RC(build_preconditioner(c, c->U, p.precision));
     CK(launch_axpby(n, -1.0, c->F, 0.0, c->rhs, s));
     double eta;
-    if (p.precision == PNP_F64) {
+    if (p.precision == PNP_F64 && !p.newton_ew_f64) {
       eta = p.gmres_rtol;
     } else {
       // Eisenstat-Walker, choice 2 (gamma = 0.9, alpha = 2) with safeguards

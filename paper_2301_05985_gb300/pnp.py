@@ -47,7 +47,9 @@ class pnp_params(C.Structure):
         ("ew_eta_max", C.c_double), ("ew_eta_min", C.c_double),
         ("monitor", C.c_int32), ("f64_fallback", C.c_int32),
         ("gmres_cgs2", C.c_int32), ("dt_retries", C.c_int32),
-        ("gmres_inner", C.c_int32), ("pad2_", C.c_int32),
+        ("gmres_inner", C.c_int32), ("newton_ew_f64", C.c_int32),
+        ("mg_levels", C.c_int32), ("mg_smooth", C.c_int32), ("mg_omega", C.c_double),
+        ("mg_coarse_its", C.c_int32), ("pad3_", C.c_int32),
     ]
 
 
@@ -93,6 +95,8 @@ SIGNATURES = {
     "pnp_mesh_create_periodic": (C.c_int, [C.c_int, C.c_int, _i64, _vp, _vp, C.c_int, _P(_vp)]),
     "pnp_mesh_create_refined": (C.c_int, [C.c_int, C.c_int, _i64, _vp, _vp, _vp, C.c_int, _P(_vp)]),
     "pnp_mesh_destroy": (None, [_vp]),
+    "pnp_mesh_coarsen": (C.c_int, [_vp, C.c_int, _P(_vp)]),
+    "pnp_mesh_transfer": (C.c_int, [_vp, _vp, _P(_i64), _vp, _vp, _vp, _vp]),
     "pnp_element_gradient": (C.c_int, [_vp, _vp, _vp]),
     "pnp_mesh_info": (C.c_int, [_vp, _P(C.c_int), _P(C.c_int), _P(_i64), _P(_i64), _P(_i64)]),
     "pnp_mesh_node_coords": (C.c_int, [_vp, _vp]),
@@ -120,6 +124,7 @@ SIGNATURES = {
     "pnp_newton_solve": (C.c_int, [_vp, _P(pnp_solve_stats)]),
     "pnp_time_step": (C.c_int, [_vp, _P(pnp_solve_stats)]),
     "pnp_step_count": (C.c_int, [_vp, _P(_i64)]),
+    "pnp_set_step_count": (C.c_int, [_vp, _i64]),
     "pnp_reset_history": (C.c_int, [_vp]),
     "pnp_profile_enable": (C.c_int, [_vp, C.c_int]),
     "pnp_profile_read": (C.c_int, [_vp, C.c_int, _P(_d), _P(_i64), _P(_d), _P(_d)]),
@@ -150,8 +155,10 @@ def mlp_forward_noalloc(params, X, Y, stream: int = 0):
     return Y
 
 PNP_PROF_RESIDUAL, PNP_PROF_JV64, PNP_PROF_JV32, PNP_PROF_BLOCKDIAG = 0, 1, 2, 3
-PNP_PROF_ORTHO, PNP_PROF_PRECOND, PNP_PROF_MLP, PNP_PROF_KINDS = 4, 5, 6, 7
-PROF_NAMES = ["residual64", "jv64", "jv32", "blockdiag", "ortho_dot", "precond", "mlp", "ortho_update", "inner_ortho"]
+PNP_PROF_ORTHO, PNP_PROF_PRECOND, PNP_PROF_MLP = 4, 5, 6
+PNP_PROF_ORTHO_UPDATE, PNP_PROF_INNER, PNP_PROF_MG, PNP_PROF_KINDS = 7, 8, 9, 10
+PROF_NAMES = ["residual64", "jv64", "jv32", "blockdiag", "ortho_dot", "precond", "mlp", "ortho_update", "inner_ortho",
+              "mg_coarse"]
 
 
 def lib():
@@ -213,7 +220,10 @@ class Mesh:
     (uint8 per octant) the octants are first refined to those levels and 2:1 balanced
     (pnp_mesh_create_refined); ``elements()`` then returns the resulting leaves."""
 
-    def __init__(self, octants, target_levels=None):
+    def __init__(self, octants=None, target_levels=None, _handle=None):
+        if _handle is not None:
+            self._wrap(_handle)
+            return
         a = np.ascontiguousarray(octants.anchors, dtype=np.int32)
         lv = np.ascontiguousarray(octants.levels, dtype=np.uint8)
         h = C.c_void_p()
@@ -227,6 +237,10 @@ class Mesh:
                 raise ValueError("target_levels needs one level per octant")
             check(lib().pnp_mesh_create_refined(octants.dim, octants.max_level, octants.n, a.ctypes.data,
                                                 lv.ctypes.data, t.ctypes.data, self.periodic, C.byref(h)))
+        self._wrap(h)
+
+    def _wrap(self, h):
+        self.periodic = getattr(self, "periodic", 0)
         self.h = h
         d, L = C.c_int(), C.c_int()
         ne, nn, nh = C.c_int64(), C.c_int64(), C.c_int64()
@@ -238,6 +252,24 @@ class Mesh:
         hf = np.zeros(self.n_nodes, np.uint8)
         check(lib().pnp_mesh_hanging(h, hf.ctypes.data))
         self.hanging = hf.astype(bool)
+
+    def coarsen(self, cap_level: int) -> "Mesh":
+        """The octree with every leaf finer than cap_level replaced by its ancestor there."""
+        h = C.c_void_p()
+        check(lib().pnp_mesh_coarsen(self.h, int(cap_level), C.byref(h)))
+        return Mesh(_handle=h)
+
+    def transfer(self, coarse: "Mesh"):
+        """Prolongation CSR (ptr, col, w) from `coarse` to this mesh and the injection map."""
+        nnz = C.c_int64()
+        check(lib().pnp_mesh_transfer(self.h, coarse.h, C.byref(nnz), None, None, None, None))
+        ptr = np.zeros(self.n_nodes + 1, np.int64)
+        col = np.zeros(nnz.value, np.int32)
+        w = np.zeros(nnz.value, np.float32)
+        inj = np.zeros(coarse.n_nodes, np.int32)
+        check(lib().pnp_mesh_transfer(self.h, coarse.h, C.byref(nnz), ptr.ctypes.data, col.ctypes.data,
+                                      w.ctypes.data, inj.ctypes.data))
+        return ptr, col, w, inj
 
     def patch_stats(self) -> dict:
         s = np.zeros(7, np.int64)
@@ -404,6 +436,9 @@ class Context:
 
     def reset_history(self):
         check(lib().pnp_reset_history(self.h))
+
+    def set_step_count(self, k: int):
+        check(lib().pnp_set_step_count(self.h, int(k)))
 
     def step_count(self) -> int:
         k = C.c_int64()

@@ -29,7 +29,7 @@ class RefineRecipe:
     base: int = 6
     band_level: int = 9
     fine: int = 10
-    band: float = 0.02
+    band: float = 0.01
     theta: float = 60.0
     presolve_steps: int = 3
 

@@ -183,6 +183,98 @@ def test_fp32_gmres_solves_oracle_system(inner):
         assert st.jv_evals >= inner * st.krylov_its  # the inner steps ran
 
 
+def test_fp64_flexible_gmres_solves_oracle_system():
+    """Flexible GMRES with an inner FP64 GMRES(6) preconditioner (PNP_F64 with gmres_inner):
+    the FP64 counterpart of the mixed-precision nested solver reaches the oracle's direct
+    solution to FP64 accuracy."""
+    import scipy.sparse.linalg as spla
+    P, U, V = _setup(CASES[1], seed=9)
+    P.ctx.set_params(P.pnp.default_params(**P.params_kw, gmres_restart=40, gmres_max_it=4000, gmres_inner=6))
+    J = P.oracle_jacobian(U)
+    b = W.random_direction(P.mesh.ijk, P.oc.max_level, 77)
+    x_ref = spla.spsolve(J.tocsc(), b.reshape(-1)).reshape(-1, 3)
+    x = P.torch.zeros((P.mesh.n_nodes, 3), dtype=P.torch.float64, device="cuda")
+    st = P.ctx.gmres(P.dev(U), P.dev(b), x, 1e-11, P.pnp.PNP_F64)
+    assert st.status == 0 and st.krylov_its > 0
+    assert st.jv_evals >= 6 * st.krylov_its  # the inner steps ran
+    x = x.cpu().numpy()
+    assert np.linalg.norm(J @ x.reshape(-1) - b.reshape(-1)) <= 1e-10 * np.linalg.norm(b)
+    assert rel_err(x, x_ref) <= 1e-8
+
+
+def test_fp64_nested_inexact_newton_time_steps_match_oracle():
+    """Three BDF steps with FP64 J V, the nested FP64 solver and Eisenstat-Walker forcing
+    (the FP64 arm of the mixed-precision comparison) reach the oracle's steps."""
+    oc = W.random_balanced_octants(3, 1, 4, 0.3, 21)
+    bcs = W.membrane_bcs(3, 4.0, 2.0)
+    kw = dict(eps=0.05, dt=0.01, newton_rtol=1e-11, gmres_restart=30, gmres_max_it=20000, start_mode=1,
+              gmres_inner=8, newton_ew_f64=1, ew_eta_min=1e-6)
+    P = Pair(oc, kw, bcs)
+    L = oc.max_level
+    U0 = W.noisy_state(P.mesh.ijk, L, seed=3, amp=1e-2, phi_bottom=0.0, phi_top=4.0)
+    P.ctx.set_field(P.pnp.PNP_FIELD_U, U0)
+    P.ctx.make_consistent()
+    U0c = P.ctx.get_field(P.pnp.PNP_FIELD_U)
+    P.ctx.reset_history()
+    Uk, Ukm1 = P.to_ora(U0c), P.to_ora(U0c)
+    for k in range(3):
+        st = P.ctx.time_step()
+        assert st.status == 0
+        beta = O.bdf_coefficients(k)
+        op = O.Params(eps=0.05, dt=0.01, beta=beta, bc_type=bcs.types, bc_val=bcs.values)
+        start = Uk if k == 0 else 2 * Uk - Ukm1
+        res = O.newton(P.om, op, start, Uk, Ukm1, None, rtol=1e-13)
+        Ukm1, Uk = Uk, res.U
+        Ug = P.ctx.get_field(P.pnp.PNP_FIELD_U)
+        assert rel_err(P.to_ora(Ug), Uk) <= 1e-9, k
+
+
+@pytest.mark.parametrize("ci", [1, 3])
+def test_multigrid_preconditioned_gmres_solves_oracle_system(ci):
+    """Flexible GMRES preconditioned by the geometric-multigrid V-cycle (FP32, coarse
+    octrees by capping levels, injected state, block-Jacobi smoothing) solves the oracle's
+    system to the accuracy FP32 J V allows, on a 2D and a 3D octree with hanging nodes."""
+    import scipy.sparse.linalg as spla
+    P, U, V = _setup(CASES[ci], seed=9)
+    P.ctx.set_params(P.pnp.default_params(**P.params_kw, gmres_restart=40, gmres_max_it=4000, mg_levels=2))
+    J = P.oracle_jacobian(U)
+    b = W.random_direction(P.mesh.ijk, P.oc.max_level, 77)
+    x_ref = spla.spsolve(J.tocsc(), b.reshape(-1)).reshape(-1, 3)
+    x = P.torch.zeros((P.mesh.n_nodes, 3), dtype=P.torch.float64, device="cuda")
+    st = P.ctx.gmres(P.dev(U), P.dev(b), x, 1e-4, P.pnp.PNP_F32)
+    assert st.status == 0 and st.krylov_its > 0
+    x = x.cpu().numpy()
+    assert np.linalg.norm(J @ x.reshape(-1) - b.reshape(-1)) <= 3e-4 * np.linalg.norm(b)
+    assert rel_err(x, x_ref) <= 0.05
+
+
+def test_multigrid_time_steps_match_oracle():
+    """Three BDF steps with the multigrid-preconditioned mixed solver reach the oracle's
+    steps (the preconditioner changes the path, not the converged state)."""
+    oc = W.random_balanced_octants(3, 1, 4, 0.3, 21)
+    bcs = W.membrane_bcs(3, 4.0, 2.0)
+    kw = dict(eps=0.05, dt=0.01, newton_rtol=1e-11, gmres_restart=40, gmres_max_it=20000, start_mode=1,
+              precision=1, mg_levels=3, ew_eta_min=1e-6)
+    P = Pair(oc, kw, bcs)
+    L = oc.max_level
+    U0 = W.noisy_state(P.mesh.ijk, L, seed=3, amp=1e-2, phi_bottom=0.0, phi_top=4.0)
+    P.ctx.set_field(P.pnp.PNP_FIELD_U, U0)
+    P.ctx.make_consistent()
+    U0c = P.ctx.get_field(P.pnp.PNP_FIELD_U)
+    P.ctx.reset_history()
+    Uk, Ukm1 = P.to_ora(U0c), P.to_ora(U0c)
+    for k in range(3):
+        st = P.ctx.time_step()
+        assert st.status == 0
+        beta = O.bdf_coefficients(k)
+        op = O.Params(eps=0.05, dt=0.01, beta=beta, bc_type=bcs.types, bc_val=bcs.values)
+        start = Uk if k == 0 else 2 * Uk - Ukm1
+        res = O.newton(P.om, op, start, Uk, Ukm1, None, rtol=1e-13)
+        Ukm1, Uk = Uk, res.U
+        Ug = P.ctx.get_field(P.pnp.PNP_FIELD_U)
+        assert rel_err(P.to_ora(Ug), Uk) <= 1e-9, k
+
+
 def test_newton_equilibrium_matches_oracle():
     """2D steady double layer, level 5, Lambda = 0.01, V = 1 (the equilibrium case):
     GPU Newton (FP64, exact-Jacobian GMRES) and the oracle's direct-solve Newton converge
