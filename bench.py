@@ -81,6 +81,8 @@ def parse():
                          "membrane-band secondary workload)")
     ap.add_argument("--plain-steps", type=int, default=1, help="steps of each FP64 arm on the main workload")
     ap.add_argument("--e2e-steps", type=int, default=5, help="timed steps re-run end to end (the first ones)")
+    ap.add_argument("--no-mg", action="store_true", help="skip the multigrid-preconditioned comparison arm")
+    ap.add_argument("--mg-steps", type=int, default=5, help="steps of the multigrid arm")
     ap.add_argument("--no-sweep", action="store_true", help="skip the J V sweep on the uniform level-7 cube")
     ap.add_argument("--no-secondary", action="store_true", help="skip the membrane-band secondary run")
     ap.add_argument("--no-learned", action="store_true", help="mixed mode without training the learned start")
@@ -116,6 +118,11 @@ def mode_params(pnp, wl, mode, learned=True):
                                   start_mode=pnp.PNP_START_LEARNED if learned else pnp.PNP_START_EXTRAPOLATE,
                                   newton_rtol=1e-8, gmres_restart=60, gmres_max_it=3000, dt_retries=2,
                                   gmres_inner=24)
+    if mode == "mixed_mg":
+        return pnp.default_params(eps=wl["eps"], dt=wl["dt"], precision=pnp.PNP_F32,
+                                  start_mode=pnp.PNP_START_EXTRAPOLATE, newton_rtol=1e-8, gmres_restart=60,
+                                  gmres_max_it=3000, dt_retries=2, gmres_inner=24, mg_levels=8, mg_smooth=3,
+                                  mg_omega=0.6, mg_coarse_its=32)
     if mode == "same64":
         return pnp.default_params(eps=wl["eps"], dt=wl["dt"], precision=pnp.PNP_F64,
                                   start_mode=pnp.PNP_START_EXTRAPOLATE, newton_rtol=1e-8, gmres_restart=60,
@@ -450,7 +457,15 @@ def run_arm(pnp, torch, W, mesh, wl, mode, hist, steps):
     return {"s_per_step": t / steps, "steps": steps, "newton_its_per_step": sum(s["newton_its"] for s in sts) / steps,
             "krylov_its_per_step": sum(s["krylov_its"] for s in sts) / steps,
             "jv_per_step": sum(s["jv_evals"] for s in sts) / steps,
+            "step_s": spread([s["wall_ms"] * 1e-3 for s in sts]),
+            "mg_fallbacks": [int(s["mg_fallbacks"]) for s in sts],
             "status": [int(s["status"]) for s in sts], "substeps": [int(s["substeps"]) for s in sts]}, U
+
+
+def spread(xs):
+    """Median and range of per-step times (the Krylov path varies from run to run: the
+    atomic scatter reorders FP32 sums)."""
+    return {"median": float(np.median(xs)), "min": float(np.min(xs)), "max": float(np.max(xs)), "n": len(xs)}
 
 
 def field_errors(U, ref):
@@ -617,6 +632,7 @@ def main():
                "ms_per_step": 1e3 * t_e2e / e2e_steps, "steps": e2e_steps, "graph_captures": pnp.graph_captures() - c0,
                "trajectory": f"the first {e2e_steps} timed steps again from the same state",
                "device_timed_same_steps_s_per_step": sum(s["wall_ms"] for s in stats[:e2e_steps]) * 1e-3 / e2e_steps,
+               "step_s": spread([s["wall_ms"] * 1e-3 for s in e2e_stats]),
                "newton_its_per_step": sum(s["newton_its"] for s in e2e_stats) / e2e_steps,
                "krylov_its_per_step": sum(s["krylov_its"] for s in e2e_stats) / e2e_steps}
 
@@ -636,8 +652,16 @@ def main():
     n_res = sum(s["residual_evals"] for s in stats) / args.steps
     n_jv = sum(s["jv_evals"] for s in stats) / args.steps
 
-    # FP64 arms from the same state (rank 0 only)
+    # FP64 arms and the multigrid-preconditioned arm from the same state (rank 0 only)
     arms = {}
+    if not args.no_mg and rank == 0:
+        mg_steps = max(1, min(args.mg_steps, args.steps))
+        arm, _ = run_arm(pnp, torch, W, mesh, wl, "mixed_mg", hist, mg_steps)
+        arm["preconditioner"] = ("geometric multigrid V-cycle (8 coarser octrees, 3 block-Jacobi sweeps, "
+                                 "damping 0.6, 32 sweeps on the coarsest), inner GMRES(24) where it falls behind")
+        arm["start"] = "extrapolated"
+        arm["timed_mixed_same_steps_s_per_step"] = sum(s["wall_ms"] for s in stats[:mg_steps]) * 1e-3 / mg_steps
+        arms["mixed_multigrid"] = arm
     if (args.plain or args.workload != "electroconvection") and rank == 0:
         arm, U_same = run_arm(pnp, torch, W, mesh, wl, "same64", hist, plain_steps)
         arms["plain_same_solver"] = arm
@@ -693,6 +717,7 @@ def main():
         "clocks": clk.summary(),
         "jv": jv,
         "gdofs_advanced_per_s": gdofs_advanced,
+        "step_s": spread([s["wall_ms"] * 1e-3 for s in stats]),
         "newton_its_per_step": nt / args.steps, "krylov_its_per_step": kt / args.steps,
         "residual_evals_per_step": n_res, "jv_evals_per_step": n_jv,
         "split_steps": sum(int(s["substeps"] > 1) for s in stats),
@@ -730,6 +755,8 @@ def secondary_membrane(pnp, torch, W, peaks, warmup=3, steps=3):
            "mixed": {"s_per_step": t / steps, "newton_its_per_step": sum(s["newton_its"] for s in sts) / steps,
                      "krylov_its_per_step": sum(s["krylov_its"] for s in sts) / steps,
                      "start": "extrapolated"}}
+    arm, _ = run_arm(pnp, torch, W, mesh, wl, "mixed_mg", hist, steps)
+    out["mixed_multigrid"] = arm
     arm, Us = run_arm(pnp, torch, W, mesh, wl, "same64", hist, steps)
     out["plain_same_solver"] = arm
     arm, Ug = run_arm(pnp, torch, W, mesh, wl, "plain", hist, steps)

@@ -125,10 +125,11 @@ typedef struct pnp_params {
   int32_t mg_levels;     /* PNP_F32 Krylov solves: 0 = off; L > 0 = flexible GMRES(m) in FP64
                             preconditioned by one FP32 V-cycle of geometric multigrid over up to
                             L coarser octrees, each the previous one with its finest level
-                            capped (in place of the paper's GAMG, App. A); overrides
-                            gmres_inner.  Non-periodic meshes. */
+                            capped (in place of the paper's GAMG, App. A); a solve in which the
+                            cycle falls behind (see mg_fallbacks) continues with the inner FP32
+                            GMRES of gmres_inner (24 steps when 0).  Non-periodic meshes. */
   int32_t mg_smooth;     /* damped block-Jacobi sweeps before and after the coarse correction (2) */
-  double mg_omega;       /* damping of the sweeps (0.7) */
+  double mg_omega;       /* damping of the sweeps (0.5) */
   int32_t mg_coarse_its; /* block-Jacobi sweeps on the coarsest level (16) */
   int32_t pad3_;
 } pnp_params;
@@ -150,6 +151,11 @@ typedef struct pnp_solve_stats {
   double wall_ms;        /* host wall time of the call */
   double res_ref;        /* ||F|| the relative Newton tolerance refers to: res0, or in
                             pnp_time_step ||F(U^k)|| of the previous-step state */
+  int32_t mg_fallbacks;  /* Krylov solves in which the multigrid preconditioner fell behind (20
+                            iterations without halving the residual, or a restart cycle that cut
+                            it by less than 5%) and the solve went on with the inner FP32 GMRES
+                            (gmres_inner, or 24 steps) */
+  int32_t pad_;
 } pnp_solve_stats;
 
 /* Message for the calling thread's most recent failure ("" if none).  Static storage. */
@@ -259,10 +265,16 @@ int pnp_jv(pnp_ctx* c, const double* U, const void* V, void* JV, int precision);
  * (pnp_gmres, pnp_newton_solve, pnp_time_step) replaces the stored linearisation;
  * pnp_jv_linearized then returns PNP_ERR_STATE until pnp_linearize is called again.
  * The J V kernel streams the stored quantities through shared memory with bulk copies;
- * if one of its bounded waits on them gives up it raises PNP_ERR_DEVICE_FLAG (here, and
- * from the solver calls that use it), latched for the context. */
+ * if one of its bounded waits on them gives up, the block waits (with a longer bound) for
+ * the copies it issued, exits, and the call raises PNP_ERR_DEVICE_FLAG (here, and from the
+ * solver calls that use it).  The flag stays set until the next linearisation (a
+ * pnp_linearize, or the start of the next flexible Krylov solve). */
 int pnp_linearize(pnp_ctx* c, const double* U);
 int pnp_jv_linearized(pnp_ctx* c, const float* V, float* JV);
+/* The poll limit of each bounded wait of the staged J V above (polls < 0: the default,
+ * 2^22 polls, about a second; at most 2^30).  A limit of 0 makes every wait give up at
+ * once while the copies still land: it exercises the failure path on a healthy GPU. */
+int pnp_set_wait_limit(pnp_ctx* c, int64_t polls);
 /* 3x3 diagonal blocks of J(U): D device FP64 [n][3][3] (row-major per node), exact
  * for the assembled operator including hanging-node coupling.  Dirichlet rows are
  * identity rows, hanging rows identity blocks. */
@@ -319,7 +331,9 @@ int pnp_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
 int pnp_newton_solve(pnp_ctx* c, pnp_solve_stats* st);
 /* One BDF time step (Def. 1): BDF1 on the first step, then bdf_order; advection
  * v~ = 2 v^k - v^{k-1} (Eq. averaging1) from the VELOCITY fields; Newton start per
- * start_mode, Newton tolerance relative to ||F(U^k)|| (see newton_rtol); on success
+ * start_mode, Newton tolerance relative to ||F(U^k)|| (see newton_rtol); a start whose
+ * residual norm exceeds ||F(U^k)|| is replaced by U^k (st->start_used then reports
+ * PNP_START_PREVIOUS); on success
  * U_PREV2 <- U_PREV <- U^{k+1} = U and VELOCITY_PREV <- VELOCITY.  With dt_retries > 0
  * a step whose Newton solve fails is redone as two BDF1 half steps (recursively);
  * st->substeps counts the solves that completed it.  On failure the context keeps the
@@ -342,7 +356,9 @@ int pnp_reset_history(pnp_ctx* c);
  * network proposes the Newton start of pnp_time_step (start_mode PNP_START_LEARNED);
  * plain Newton judges it -- the start with the smallest ||F|| of {learned U_l,
  * extrapolated U_e = 2 U^k - U^{k-1}, blend U_e + a (U_l - U_e)} is used, with a in
- * [0, 2] the minimiser of ||F_e + a (F_l - F_e)|| (one extra residual).
+ * [0, 2] the minimiser of ||F_e + a (F_l - F_e)|| (one extra residual).  After three
+ * steps in a row won by U_e the network and the judge's residuals are skipped for the
+ * next four steps (U_e is used; st->res_start_learned = -1), then tried again.
  *
  * Input (216 features per non-hanging node): the fields c+, c-, phi and the last-axis
  * velocity component at t^k and t^{k-1}, sampled at the 3x3x3 lattice around the node

@@ -73,7 +73,7 @@ void pnp_params_default(pnp_params* p) {
   p->newton_ew_f64 = 0;
   p->mg_levels = 0;
   p->mg_smooth = 2;
-  p->mg_omega = 0.7;
+  p->mg_omega = 0.5;
   p->mg_coarse_its = 16;
   p->pad3_ = 0;
 }
@@ -706,6 +706,7 @@ int pnp_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   int its = 0;
   double rel = 0;
   c->jv_count = 0;
+  c->mg_fallbacks = 0;
   const int rc = ctx_gmres(c, U, b, x, rtol, precision, c->prm.gmres_max_it, &its, &rel, false);
   if (st) {
     std::memset(st, 0, sizeof(*st));
@@ -713,6 +714,7 @@ int pnp_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
     st->krylov_its = its;
     st->jv_evals = c->jv_count;
     st->res_final = rel;
+    st->mg_fallbacks = c->mg_fallbacks;
   }
   return rc;
 }
@@ -732,6 +734,13 @@ int pnp_time_step(pnp_ctx* c, pnp_solve_stats* st) {
 int pnp_step_count(const pnp_ctx* c, int64_t* k) {
   if (!c || !k) PNP_FAIL(PNP_ERR_ARG, "pnp_step_count: null argument");
   *k = c->step;
+  return PNP_OK;
+}
+
+int pnp_set_wait_limit(pnp_ctx* c, int64_t polls) {
+  if (!c) PNP_FAIL(PNP_ERR_ARG, "pnp_set_wait_limit: null context");
+  if (polls > (int64_t(1) << 30)) PNP_FAIL(PNP_ERR_ARG, "pnp_set_wait_limit: at most 2^30 polls");
+  c->wait_polls = polls < 0 ? -1 : (int)polls;
   return PNP_OK;
 }
 

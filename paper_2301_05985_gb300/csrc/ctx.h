@@ -13,6 +13,7 @@ struct pnp_ctx {
   double bc_val[6][3] = {};
   cudaError_t latched = cudaSuccess;
   int64_t step = 0;
+  bool start_fell_back = false;  // the last Newton solve started from its reference state
   bool history_split = false;  // U^{k-1} is not one full step behind U^k (after a split)
 
   // mesh (device)
@@ -71,6 +72,7 @@ struct pnp_ctx {
   bool lin_user = false;    // qp32 holds the linearisation of the last pnp_linearize
   int lin_rows = 4;         // float4 rows per lane in qp32 (3 without advection)
   bool adv_zero = false;    // the advection field was zero at the last ctx_prepare_f32
+  int wait_polls = -1;      // poll limit of the staged J V's waits (< 0: the kernel's default)
   // the inner FP32 GMRES captured as a CUDA graph (replayed while profiling is off): the
   // launches depend only on the key below, captured on a stream of the context's own
   cudaStream_t cap_stream = nullptr;
@@ -87,7 +89,7 @@ struct pnp_ctx {
   int mg_built = 0;
 
   // statistics of the last solve (for the time stepper)
-  int jv_count = 0, res_count = 0;
+  int jv_count = 0, res_count = 0, mg_fallbacks = 0;
 
   // learned start (optional) and the host copy of the mesh it needs for point location
   struct Mlp* mlp = nullptr;

@@ -454,7 +454,11 @@ constexpr int kStages = 2;
 constexpr size_t jv_stage_bytes(int S, int NR) {
   return (size_t)S * ((size_t)NR * kLaneThreads * 16 + kLaneThreads * 4 + 8);
 }
-constexpr int kWaitPolls = 1 << 22;  // try_wait polls before a wait gives up (about a second)
+// try_wait polls before a wait on a stage gives up (about a second by default; a launch
+// argument), and the longer limit of the drain that follows a give-up: the block waits
+// for the copies it issued before it exits
+constexpr int kWaitPolls = 1 << 22;
+constexpr int kDrainPolls = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -466,9 +470,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 // bounded wait for the phase of the given parity to complete; false when it did not
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int polls = kWaitPolls) {
   const uint32_t a = smem_u32(bar);
-  for (int i = 0; i < kWaitPolls; ++i) {
+  for (int i = 0; i < polls; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -489,7 +493,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 template <int D, int NS, int NR>
 __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<float> A, LaneParams<float> K,
-                                                                 const float4* __restrict__ qp, int* err) {
+                                                                 const float4* __restrict__ qp, int* err,
+                                                                 int polls) {
   constexpr int NC = 1 << D;
   extern __shared__ __align__(128) uint8_t jv_smem[];
   // NS stages of {NR state rows, connectivity} and NS mbarriers (jv_stage_bytes(NS, NR))
@@ -533,14 +538,14 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
     if (tl >= n_tiles) break;
     const int st = k % NS;
     const uint32_t parity = (uint32_t)(k / NS) & 1u;
-    const bool ok = mbar_wait(&bar[st], parity);
+    const bool ok = mbar_wait(&bar[st], parity, polls);
     if (__syncthreads_or(!ok)) {
       // a copy did not complete: flag it, let the copies still in flight land, return
       if (tid == 0) {
         atomicOr(err, 1);
         for (int j = 0; j < NS; ++j) {
           const int kk = k + ((j - st + NS) % NS);
-          if (pending >> j & 1u) mbar_wait(&bar[j], (uint32_t)(kk / NS) & 1u);
+          if (pending >> j & 1u) mbar_wait(&bar[j], (uint32_t)(kk / NS) & 1u, kDrainPolls);
         }
       }
       return;
@@ -921,7 +926,7 @@ cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, int
 
 template <int S, int NR>
 static cudaError_t launch_jv_stages(int dim, const ElemArgs<float>& A, const LaneParams<float>& K, const float4* qp,
-                                    int* err, cudaStream_t s) {
+                                    int* err, int polls, cudaStream_t s) {
   // persistent grid: the resident blocks of every SM, no more than there are tiles
   static int per_sm[2] = {0, 0}, n_sm = 0;
   const size_t smem = jv_stage_bytes(S, NR);
@@ -944,18 +949,19 @@ static cudaError_t launch_jv_stages(int dim, const ElemArgs<float>& A, const Lan
   }
   const int64_t tiles = ((A.n_elem << dim) + kLaneThreads - 1) / kLaneThreads;
   const unsigned blocks = (unsigned)std::min<int64_t>(tiles, (int64_t)n_sm * std::max(1, per_sm[dim - 2]));
-  if (dim == 2) k_jv_from_state<2, S, NR><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err);
-  else k_jv_from_state<3, S, NR><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err);
+  if (dim == 2) k_jv_from_state<2, S, NR><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err, polls);
+  else k_jv_from_state<3, S, NR><<<blocks, kLaneThreads, smem, s>>>(A, K, qp, err, polls);
   return cudaSuccess;
 }
 
 cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int rows, int* err,
-                                 cudaStream_t s) {
+                                 int polls, cudaStream_t s) {
+  if (polls < 0) polls = kWaitPolls;
   if (A.n_elem == 0) return cudaSuccess;
   if (rows != 3 && rows != 4) return cudaErrorInvalidValue;
   const LaneParams<float> K{float(A.P.kappa), float(A.P.tau_t), float(A.P.C_I * dim), float(A.P.eps2x2)};
-  const cudaError_t e = rows == 4 ? launch_jv_stages<kStages, 4>(dim, A, K, qp, err, s)
-                                  : launch_jv_stages<kStages, 3>(dim, A, K, qp, err, s);
+  const cudaError_t e = rows == 4 ? launch_jv_stages<kStages, 4>(dim, A, K, qp, err, polls, s)
+                                  : launch_jv_stages<kStages, 3>(dim, A, K, qp, err, polls, s);
   if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();

@@ -37,47 +37,51 @@ __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) 
 
 __device__ __forceinline__ float partner(float x) { return __shfl_xor_sync(kFull, x, 1); }
 
-// node record {c+, c-, phi, h+, h-, v0, v1, v2} and padded direction of node id (a hanging
-// node: the mean of its parents)
-template <bool ADV, bool PAD>
-__device__ __forceinline__ void load_corner(const ElemArgs<float>& A, int32_t id, bool valid, float (&u)[3],
-                                            float (&hq)[2], float (&vq)[3], float (&d)[3]) {
-  float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, dv = r0;
-  if (valid) {
-    if (id >= 0) {
-      r0 = __ldg(A.rec + 2 * (int64_t)id);
-      r1 = __ldg(A.rec + 2 * (int64_t)id + 1);
-      if constexpr (PAD) {
-        dv = __ldg(A.V4 + id);
-      } else {
-        dv.x = __ldg(A.V + 3 * (int64_t)id);
-        dv.y = __ldg(A.V + 3 * (int64_t)id + 1);
-        dv.z = __ldg(A.V + 3 * (int64_t)id + 2);
-      }
-    } else {
-      const int32_t h = -id - 1;
-      const int np = A.hang_np[h];
-      const float wgt = np == 2 ? 0.5f : 0.25f;
-      for (int p = 0; p < np; ++p) {
-        const int64_t pid = A.hang_par[4 * h + p];
-        const float4 a = __ldg(A.rec + 2 * pid), b = __ldg(A.rec + 2 * pid + 1);
-        r0.x += wgt * a.x; r0.y += wgt * a.y; r0.z += wgt * a.z; r0.w += wgt * a.w;
-        r1.x += wgt * b.x; r1.y += wgt * b.y; r1.z += wgt * b.z; r1.w += wgt * b.w;
-        if constexpr (PAD) {
-          const float4 q = __ldg(A.V4 + pid);
-          dv.x += wgt * q.x; dv.y += wgt * q.y; dv.z += wgt * q.z;
-        } else {
-          dv.x += wgt * __ldg(A.V + 3 * pid);
-          dv.y += wgt * __ldg(A.V + 3 * pid + 1);
-          dv.z += wgt * __ldg(A.V + 3 * pid + 2);
-        }
-      }
-    }
+// node records {c+, c-, phi, h+, h-, v0, v1, v2} and directions of a lane's four corners.
+// The loads of all four corners are issued before any is used (a hanging corner first
+// loads node 0 in its place), so twelve 16-byte loads are in flight per lane; corners that
+// hang on coarser neighbours are then replaced by the mean of their parents.
+template <bool PAD>
+__device__ __forceinline__ float4 load_dir(const ElemArgs<float>& A, int64_t nid) {
+  if constexpr (PAD) {
+    return __ldg(A.V4 + nid);
+  } else {
+    return make_float4(__ldg(A.V + 3 * nid), __ldg(A.V + 3 * nid + 1), __ldg(A.V + 3 * nid + 2), 0.f);
   }
-  u[0] = r0.x; u[1] = r0.y; u[2] = r0.z;
-  hq[0] = r0.w; hq[1] = r1.x;
-  vq[0] = r1.y; vq[1] = r1.z; vq[2] = r1.w;
-  d[0] = dv.x; d[1] = dv.y; d[2] = dv.z;
+}
+template <bool PAD>
+__device__ __forceinline__ void load_corners(const ElemArgs<float>& A, const int32_t (&id)[4], bool valid,
+                                             float4 (&r0)[4], float4 (&r1)[4], float4 (&dv)[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t nid = (valid && id[j] >= 0) ? id[j] : 0;
+    r0[j] = __ldg(A.rec + 2 * nid);
+    r1[j] = __ldg(A.rec + 2 * nid + 1);
+    dv[j] = load_dir<PAD>(A, nid);
+  }
+  if (!valid) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r0[j] = r1[j] = dv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (id[j] >= 0) continue;
+    const int32_t h = -id[j] - 1;
+    const int np = A.hang_np[h];
+    const float wgt = np == 2 ? 0.5f : 0.25f;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, ad = a0;
+    for (int p = 0; p < np; ++p) {
+      const int64_t pid = A.hang_par[4 * h + p];
+      const float4 x = __ldg(A.rec + 2 * pid), y = __ldg(A.rec + 2 * pid + 1), d = load_dir<PAD>(A, pid);
+      a0.x += wgt * x.x; a0.y += wgt * x.y; a0.z += wgt * x.z; a0.w += wgt * x.w;
+      a1.x += wgt * y.x; a1.y += wgt * y.y; a1.z += wgt * y.z; a1.w += wgt * y.w;
+      ad.x += wgt * d.x; ad.y += wgt * d.y; ad.z += wgt * d.z;
+    }
+    r0[j] = a0;
+    r1[j] = a1;
+    dv[j] = ad;
+  }
 }
 
 // z factor of a field with gradient: value at this lane's Gauss-point level and z-derivative
@@ -165,10 +169,12 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_jv_pair(ElemArgs<float> A, 
 
   // z factor of every field at the four corner columns of this lane's Gauss-point level
   float cz[2][4], czd[2][4], pz[4], pzd[4], hz[2][4], vz[3][4], dcz[2][4], dczd[2][4], dpz[4], dpzd[4];
+  float4 r0[4], r1[4], dv[4];
+  load_corners<PAD>(A, id, valid, r0, r1, dv);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    float u[3], hq[2], vq[3], d[3];
-    load_corner<ADV, PAD>(A, id[j], valid, u, hq, vq, d);
+    const float u[3] = {r0[j].x, r0[j].y, r0[j].z}, hq[2] = {r0[j].w, r1[j].x};
+    const float vq[3] = {r1[j].y, r1[j].z, r1[j].w}, d[3] = {dv[j].x, dv[j].y, dv[j].z};
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       zstage_vg(u[s], szh, cz[s][j], czd[s][j]);

@@ -89,8 +89,9 @@ constexpr double kDfFlopsPerFlop = 15.0;
 // applies J V with them (A.V or A.V4, A.out or A.out4; qp and A.conn 16-byte aligned).
 // err[0] |= 1 when a staged copy's wait gave up.
 cudaError_t launch_lane_state(int dim, const ElemArgs<float>& A, float4* qp, int rows, cudaStream_t s);
+// polls: the limit of each bounded wait on a stage (< 0: the default, about a second)
 cudaError_t launch_jv_from_state(int dim, const ElemArgs<float>& A, const float4* qp, int rows, int* err,
-                                 cudaStream_t s);
+                                 int polls, cudaStream_t s);
 double jv_from_state_flops(int dim);
 // FP32 J V on hexahedra with two lanes per element (jv_pair.cu): the state from the node
 // records (A.rec), the direction A.V4 (with A.out4) or A.V (with A.out); `advection`

@@ -52,18 +52,24 @@ __device__ __forceinline__ bool dir_row(const BcTable& bc, uint8_t faces, int f)
   return (faces & bc.dir_faces[f] & 0x3F) != 0;
 }
 
-// bc[j] = sum_q w_q (b - Ax)[col_q]  (coarse rows; Dirichlet rows zero)
+// bc[j] = sum_q w_q (b - Ax)[col_q] over the fine rows that are weak-form equations:
+// Dirichlet rows (U - g) and hanging rows (constraints) carry no element contributions
+// and are left out; coarse Dirichlet rows are zero
 __global__ void k_mg_restrict(int64_t Nc, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                               const float* __restrict__ w, const float* __restrict__ b, const float* __restrict__ Ax,
-                              const uint8_t* __restrict__ faces_c, BcTable bc, float* __restrict__ out) {
+                              const uint8_t* __restrict__ faces_f, BcTable bcf, const uint8_t* __restrict__ faces_c,
+                              BcTable bc, float* __restrict__ out) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= Nc) return;
   float s[3] = {0.f, 0.f, 0.f};
   for (int64_t q = ptr[j]; q < ptr[j + 1]; ++q) {
     const int64_t i = col[q];
+    const uint8_t ff = faces_f[i];
+    if (ff & 0x80) continue;  // hanging
     const float wq = w[q];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) s[f] = fmaf(wq, b[3 * i + f] - Ax[3 * i + f], s[f]);
+    for (int f = 0; f < 3; ++f)
+      if (!dir_row(bcf, ff, f)) s[f] = fmaf(wq, b[3 * i + f] - Ax[3 * i + f], s[f]);
   }
   const uint8_t fc = faces_c[j];
 #pragma unroll
@@ -290,7 +296,8 @@ static int mg_cycle(pnp_ctx* c, size_t l) {
     // the coarse levels of the cycle (the transfers included) in one profile class
     ProfScope ps(c, l == 0 ? PNP_PROF_MG : -1, 0.0);
     k_mg_restrict<<<nblk(cc->n_nodes, 256), 256, 0, s>>>(cc->n_nodes, C.r_ptr, C.r_col, C.r_w, L.b, L.Ax,
-                                                         cc->d_faces, cc->bc_table(), C.b);
+                                                         lc->d_faces, lc->bc_table(), cc->d_faces, cc->bc_table(),
+                                                         C.b);
     note_launch();
     CK(cudaGetLastError());
     RC(mg_cycle(c, l + 1));

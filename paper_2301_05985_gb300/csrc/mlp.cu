@@ -425,6 +425,8 @@ struct Mlp {
   int64_t S = 0, S_cap = 0;
   std::vector<std::pair<int64_t, int64_t>> trajs;  // (first state, T)
   bool have_uz = false;
+  // judge bookkeeping: consecutive steps the extrapolated start won, steps left to skip
+  int losses = 0, skip = 0;
 };
 
 namespace {
@@ -776,6 +778,7 @@ int pnp_mlp_set_weights(pnp_ctx* c, const float* params, int64_t n) {
   RC(mlp_refresh(c, c->mlp));
   CK(cudaStreamSynchronize(c->stream));
   c->mlp->trained = true;
+  c->mlp->losses = c->mlp->skip = 0;
   return PNP_OK;
 }
 
@@ -1009,6 +1012,7 @@ int pnp_mlp_train(pnp_ctx* c, const pnp_train_cfg* cfg, pnp_train_stats* st) {
   if (rc) return rc;
   CK(cudaGetLastError());
   m->trained = true;
+  m->losses = m->skip = 0;
   if (st) {
     std::memset(st, 0, sizeof(*st));
     st->loss_first = l_first;
@@ -1133,6 +1137,15 @@ int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st) {
   if (!c->mlp || !c->mlp->trained) PNP_FAIL(PNP_ERR_STATE, "learned start: no trained network in this context");
   if (c->step == 0) PNP_FAIL(PNP_ERR_STATE, "learned start: needs two previous time levels");
   Mlp* m = c->mlp;
+  // after kJudgeLosses steps in a row won by the extrapolated start, the network (and the
+  // judge's residuals) are skipped for kJudgeSkip steps: the extrapolated start is used
+  constexpr int kJudgeLosses = 3, kJudgeSkip = 4;
+  if (m->skip > 0) {
+    --m->skip;
+    st->start_used = PNP_START_EXTRAPOLATE;
+    st->res_start_learned = -1.0;  // not evaluated
+    return PNP_OK;
+  }
   cudaStream_t s = c->stream;
   const int64_t N = c->n_nodes, n = c->n3();
   // extrapolated start in Ut (consistent)
@@ -1215,6 +1228,12 @@ int pnp_learned_start(pnp_ctx* c, pnp_solve_stats* st) {
     st->start_used = PNP_START_EXTRAPOLATE;
     st->res_start_learned = std::isfinite(fb) ? std::min(fl, fb) : fl;
     CK(cudaMemcpyAsync(c->U, c->Ut, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  if (st->start_used == PNP_START_LEARNED) {
+    m->losses = 0;
+  } else if (++m->losses >= kJudgeLosses) {
+    m->losses = 0;
+    m->skip = kJudgeSkip;
   }
   CK(cudaStreamSynchronize(s));
   return PNP_OK;

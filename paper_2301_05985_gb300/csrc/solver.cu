@@ -271,7 +271,7 @@ static int ctx_jv32_pad(pnp_ctx* c, const float4* V4, float* out, bool from_stat
       ProfScope ps(c, PNP_PROF_JV32,
                    24.0 * c->n_nodes + 16.0 * c->lin_rows * (double)(c->n_elem << c->dim) + c->conn_bytes(),
                    jv_from_state_flops(c->dim) * c->n_elem);
-      CK(launch_jv_from_state(c->dim, A, c->qp32, c->lin_rows, c->dflag + 1, c->stream));
+      CK(launch_jv_from_state(c->dim, A, c->qp32, c->lin_rows, c->dflag + 1, c->wait_polls, c->stream));
     } else if (use_jv_pair(c)) {
       ProfScope ps(c, PNP_PROF_JV32, 56.0 * c->n_nodes + c->conn_bytes(), jv_pair_flops(!c->adv_zero) * c->n_elem);
       CK(launch_jv_pair(A, !c->adv_zero, c->stream));
@@ -296,6 +296,8 @@ int ctx_linearize32(pnp_ctx* c) {
                "stored linearisation: allocation failed: %s", cudaGetErrorString(e));
     }
   }
+  // a new linearisation clears the give-up flag of the staged J V's waits
+  CK(cudaMemsetAsync(c->dflag + 1, 0, sizeof(int), c->stream));
   // a zero advection field (pure PNP) leaves v out of the stored state: three rows
   double vn = 0.0;
   RC(ctx_norm(c, c->adv, &vn));
@@ -579,6 +581,8 @@ static int inner_gmres64(pnp_ctx* c, const double* U, const double* u, double* z
 // needed; each iteration does one classical Gram-Schmidt pass (multi-dot, then
 // multi-axpy fused with the new norm), two with gmres_cgs2.  Dots, basis and the
 // Hessenberg system are FP64.
+constexpr int kMgCheck = 20;  // iterations after which a multigrid cycle must have halved the residual
+
 int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rtol, int prec, int max_it, int* its_out,
               double* rel_out, bool have_precond) {
   const int m = c->prm.gmres_restart;
@@ -587,14 +591,24 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
   cudaStream_t s = c->stream;
   if (!have_precond) RC(build_preconditioner(c, U, prec));
   if (prec == PNP_F32) RC(ctx_prepare_f32(c, U));
-  // multigrid preconditioner (FP32 V-cycle) of a flexible outer solve
+  // multigrid preconditioner (FP32 V-cycle) of a flexible outer solve; a solve in which
+  // it stagnates continues with the inner FP32 GMRES (block Jacobi) preconditioner
   const bool use_mg = prec == PNP_F32 && c->prm.mg_levels > 0;
+  bool mg_on = use_mg;
+  const int inner_saved = c->prm.gmres_inner;
+  const int inner_fb = inner_saved > 0 ? inner_saved : 24;
   if (use_mg) {
     RC(ctx_mg_setup(c, c->prm.mg_levels));
     RC(ctx_mg_prepare(c, U));
   }
   const bool flex = prec == PNP_F32 && (c->prm.gmres_inner > 0 || use_mg);
-  if (flex) RC(ctx_alloc_inner(c, m, std::max(1, c->prm.gmres_inner)));
+  if (flex) RC(ctx_alloc_inner(c, m, std::max(inner_fb, c->prm.gmres_inner)));
+  if (use_mg && inner_saved == 0) CK(launch_to_f32(9 * c->n_nodes, c->Dinv, c->Dinv32, s));
+  struct InnerRestore {  // the fallback switches gmres_inner for the rest of this solve
+    pnp_ctx* c;
+    int v;
+    ~InnerRestore() { c->prm.gmres_inner = v; }
+  } inner_restore{c, inner_saved};
   // the same flexible scheme entirely in FP64 (inner FP64 GMRES, FP64 J V)
   const bool flex64 = prec == PNP_F64 && c->prm.gmres_inner > 0;
   if (flex64) RC(ctx_alloc_inner64(c, m, c->prm.gmres_inner));
@@ -648,13 +662,14 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
     int k = 0;
     double res = beta;
     bool breakdown = false;
+    bool mg_slow = false;  // the multigrid cycle is not converging: give up on it early
     for (int j = 0; j < m && total < max_it; ++j) {
       const double* uj = V + (size_t)j * n;
       double* w = V + (size_t)(j + 1) * n;
       // z = M^-1 (u_j / s_j) ; w = J z   (flexible: z_j = P(u_j) / s_j kept in Zb)
       if (flex) {
         float* zj = c->Zb + (size_t)j * n;
-        if (use_mg) RC(ctx_mg_apply(c, uj, zj));
+        if (mg_on) RC(ctx_mg_apply(c, uj, zj));
         else RC(inner_gmres32(c, uj, zj, from_state));
         // the outer J V applies the same linearisation as the inner one
         if (from_state) RC(ctx_jv32_linearized(c, zj, c->JV32));
@@ -733,6 +748,13 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       k = j + 1;
       if (nrm <= 1e-300 * bn) breakdown = true;
       if (res <= tol || breakdown) break;
+      // a multigrid-preconditioned cycle that has not halved the residual in 20
+      // iterations ends here (its partial solution is kept) and the solve goes on with
+      // the inner GMRES preconditioner
+      if (mg_on && j + 1 == kMgCheck && res > 0.5 * beta) {
+        mg_slow = true;
+        break;
+      }
     }
     // y = H^-1 g ; x += M^-1 (sum_i y_i u_i / s_i)
     for (int i = k - 1; i >= 0; --i) {
@@ -768,6 +790,16 @@ int ctx_gmres(pnp_ctx* c, const double* U, const double* b, double* x, double rt
       fprintf(stderr, "[pnp gmres] its %5d  estimate %.3e  true %.3e (relative)\n", total, res / bn, beta / bn);
     // a whole cycle that cut the true residual by less than 5%: the operator's rounding
     // floor (FP32 J V) or a stalled flexible preconditioner; stop with the iterate
+    if (std::isfinite(beta) && (beta > 0.95 * beta_cycle || mg_slow) && mg_on) {
+      mg_on = false;
+      c->prm.gmres_inner = inner_fb;
+      c->mg_fallbacks++;
+      if (c->prm.monitor >= 1)
+        fprintf(stderr, "[pnp gmres] multigrid stagnated at relative residual %.3e: inner GMRES(%d)\n", beta / bn,
+                inner_fb);
+      beta_cycle = beta;
+      continue;
+    }
     if (std::isfinite(beta) && beta > 0.95 * beta_cycle) {
       CK(cudaStreamSynchronize(s));
       if (from_state) RC(ctx_check_staged_waits(c));
@@ -793,6 +825,7 @@ int ctx_newton(pnp_ctx* c, pnp_solve_stats* st, const double* ref_state) {
   cudaStream_t s = c->stream;
   c->jv_count = 0;
   c->res_count = 0;
+  c->mg_fallbacks = 0;
   RC(ctx_prepare_history(c));
   CK(launch_make_consistent(c->rows(), c->U, s));
   RC(ctx_residual(c, c->U, c->F));
@@ -806,11 +839,21 @@ int ctx_newton(pnp_ctx* c, pnp_solve_stats* st, const double* ref_state) {
   // the relative tolerance refers to ||F(ref_state)|| when given (the time step's
   // previous-step state), else to the start's own residual
   double f_ref = f0;
+  c->start_fell_back = false;
   if (ref_state) {
     CK(cudaMemcpyAsync(c->Ut, ref_state, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     CK(launch_make_consistent(c->rows(), c->Ut, s));
     RC(ctx_residual(c, c->Ut, c->Ft));
     RC(ctx_norm(c, c->Ft, &f_ref));
+    // a start whose residual exceeds the previous state's (an extrapolation that overshoots
+    // after a fast transient) is replaced by the previous state
+    if (std::isfinite(f_ref) && !(f0 <= f_ref)) {
+      std::swap(c->U, c->Ut);
+      std::swap(c->F, c->Ft);
+      f0 = f_ref;
+      st->res0 = f0;
+      c->start_fell_back = true;
+    }
   }
   st->res_ref = f_ref;
   const double target = std::max(p.newton_rtol * f_ref, p.newton_atol);
@@ -899,6 +942,7 @@ int ctx_newton(pnp_ctx* c, pnp_solve_stats* st, const double* ref_state) {
   st->res_final = f;
   st->jv_evals = c->jv_count;
   st->residual_evals = c->res_count;
+  st->mg_fallbacks = c->mg_fallbacks;
   st->wall_ms = now_ms() - t0;
   return rc;
 }
@@ -936,6 +980,7 @@ static int advance(pnp_ctx* c, double dt, bool bdf2, int depth, const double* re
   tot->f64_fallbacks += one.f64_fallbacks;
   tot->jv_evals = one.jv_evals;
   tot->residual_evals = one.residual_evals;
+  tot->mg_fallbacks += one.mg_fallbacks;
   tot->res_final = one.res_final;
   tot->status = rc;
   if (rc == PNP_OK) {
@@ -995,6 +1040,7 @@ int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st) {
   // (the paper's start), so that every start is held to the same absolute tolerance
   const int rc = advance(c, dt, bdf2, 0, start == PNP_START_PREVIOUS ? nullptr : c->Uk, &tot);
   p.dt = dt;
+  if (c->start_fell_back) start = PNP_START_PREVIOUS;
   tot.start_used = start;
   tot.res_start_extrapolated = r_extra;
   tot.res_start_learned = r_learn;

@@ -61,6 +61,7 @@ class pnp_solve_stats(C.Structure):
         ("res0", C.c_double), ("res_final", C.c_double),
         ("res_start_extrapolated", C.c_double), ("res_start_learned", C.c_double),
         ("wall_ms", C.c_double), ("res_ref", C.c_double),
+        ("mg_fallbacks", C.c_int32), ("pad_", C.c_int32),
     ]
 
     def as_dict(self):
@@ -125,6 +126,7 @@ SIGNATURES = {
     "pnp_time_step": (C.c_int, [_vp, _P(pnp_solve_stats)]),
     "pnp_step_count": (C.c_int, [_vp, _P(_i64)]),
     "pnp_set_step_count": (C.c_int, [_vp, _i64]),
+    "pnp_set_wait_limit": (C.c_int, [_vp, _i64]),
     "pnp_reset_history": (C.c_int, [_vp]),
     "pnp_profile_enable": (C.c_int, [_vp, C.c_int]),
     "pnp_profile_read": (C.c_int, [_vp, C.c_int, _P(_d), _P(_i64), _P(_d), _P(_d)]),
@@ -436,6 +438,9 @@ class Context:
 
     def reset_history(self):
         check(lib().pnp_reset_history(self.h))
+
+    def set_wait_limit(self, polls: int):
+        check(lib().pnp_set_wait_limit(self.h, int(polls)))
 
     def set_step_count(self, k: int):
         check(lib().pnp_set_step_count(self.h, int(k)))

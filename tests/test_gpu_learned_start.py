@@ -16,7 +16,7 @@ from paper_2301_05985_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def test_trained_network_lowers_the_starting_residual_without_costing_newton_iterations():
+def test_trained_network_lowers_the_starting_residual_and_the_newton_iterations():
     pnp = lib()
     torch = torch_cuda()
     from paper_2301_05985_gb300 import learned_start as LS
@@ -28,6 +28,7 @@ def test_trained_network_lowers_the_starting_residual_without_costing_newton_ite
     # often enough to lower the mean starting residual by a quarter or more
     assert lrn["learned_used"] >= 3
     assert lrn["res0_mean"] <= 0.75 * ext["res0_mean"]
-    # Newton is held to the same absolute tolerance (relative to ||F(U^k)||) in both runs
-    assert lrn["newton_its_mean"] <= ext["newton_its_mean"] + 0.15
+    # Newton is held to the same absolute tolerance (relative to ||F(U^k)||) in both runs:
+    # the better start takes no more iterations on average than extrapolation
+    assert lrn["newton_its_mean"] <= ext["newton_its_mean"], (lrn, ext)
     assert len(weights) == pnp.PNP_MLP_PARAMS and np.all(np.isfinite(weights))
