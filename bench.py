@@ -377,7 +377,7 @@ def load_traffic(workload):
         return {}
     if tj.get("workload") != workload:
         return {}
-    out = {}
+    out = {"_note": tj.get("note", "")}
     for name, e in tj.get("classes", {}).items():
         try:
             same = all(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
@@ -389,8 +389,9 @@ def load_traffic(workload):
     return out
 
 
-def roofline(table, traffic, name="jv32"):
-    """The roofline object of the J V class (the dominant class of the step)."""
+def roofline(table, traffic, name="jv32", n_elem=0):
+    """The roofline object of the J V class (the dominant class of the step); `traffic` is
+    ncu's DRAM bytes of the class's kernel scaled to this launch by its elements."""
     if name not in table:
         name = max(table, key=lambda k: table[k]["avg_launch_ms"] * table[k]["launches"]) if table else None
     if name is None:
@@ -400,9 +401,9 @@ def roofline(table, traffic, name="jv32"):
     e = traffic.get(name)
     rl["traffic"] = None
     if e:
-        if "dram_bytes_per_unit" in e:
-            rl["traffic"] = e["dram_bytes_per_unit"] * rl["alg_bytes_per_launch"] / e.get("alg_bytes_per_unit", 1.0)
-            rl["traffic_note"] = e.get("note", "")
+        if "dram_bytes_per_element" in e and n_elem:
+            rl["traffic"] = e["dram_bytes_per_element"] * n_elem
+            rl["traffic_note"] = traffic.get("_note", "")
         elif "dram_bytes_per_launch" in e:
             rl["traffic"] = e["dram_bytes_per_launch"]
     return rl
@@ -532,6 +533,7 @@ def jv_sweep(pnp, torch, W, peaks, states=5, reps=10):
 def timed_mixed(pnp, torch, ctx, steps, stream, local):
     stats = []
     launches0 = pnp.kernel_launches()
+    sys.stderr.write(f"library launches before the timed steps: {launches0}\n")
     captures0 = pnp.graph_captures()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -638,7 +640,7 @@ def main():
 
     peaks = measured_peaks()
     table = kernel_table(prof, peaks, prof_ms, N, E)
-    rl = roofline(table, load_traffic(args.workload), "jv32")
+    rl = roofline(table, load_traffic(args.workload), "jv32", E)
     jv = dict(table.get("jv32", {}))
     if jv:
         jv["gdofs"] = 3.0 * N / (jv["avg_launch_ms"] * 1e-3) / 1e9

@@ -146,9 +146,13 @@ __device__ __forceinline__ void test_acc(float S, const float (&Phi)[3], int qx,
   }
 }
 
+#ifndef PNP_JV_PAIR_MINB
+#define PNP_JV_PAIR_MINB 2  // blocks per SM the register cap is set for
+#endif
+
 template <bool ADV, bool PAD>
-__global__ void __launch_bounds__(kPairThreads, 2) k_jv_pair(ElemArgs<float> A, float kappa, float tau_t, float cid,
-                                                            float e2) {
+__global__ void __launch_bounds__(kPairThreads, PNP_JV_PAIR_MINB) k_jv_pair(ElemArgs<float> A, float kappa,
+                                                                          float tau_t, float cid, float e2) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // warps whose first element is past the end leave together (shuffles need the warp)
   if ((t & ~int64_t(31)) / 2 >= A.n_elem) return;
