@@ -39,14 +39,15 @@ __global__ void k_to_f64(int64_t n, const float* __restrict__ x, double* __restr
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (double)x[i];
 }
+// b = 0 does not read y (it may hold any bit pattern, NaN included: 0 * NaN is NaN)
 __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i] + b * y[i];
+    y[i] = b == 0.0 ? a * x[i] : a * x[i] + b * y[i];
 }
 __global__ void k_axpbyz(int64_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
                          double* __restrict__ z) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    z[i] = a * x[i] + b * y[i];
+    z[i] = b == 0.0 ? a * x[i] : a * x[i] + b * y[i];
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
