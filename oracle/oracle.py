@@ -13,6 +13,9 @@ adds the solution algorithms of the paper written out plainly:
   (beta = 3/2, -2, 1/2) after it; the advection velocity is the extrapolation
   v~ = 2 v^k - v^{k-1} (Eq. averaging1) of a caller-supplied velocity history.
 * The method-of-manufactured-solutions driver of Sec. 5.1.
+* The semi-implicit VMS Navier-Stokes block (Def. 3, Sec. 3.1): a linear system in
+  (v, p) solved by a sparse direct factorisation, and the block iteration of Sec. 4.1
+  (NS from the latest PNP state, then PNP Newton with the new velocity as advection).
 """
 from __future__ import annotations
 
@@ -58,6 +61,11 @@ def lib():
         L.ora_eval_points.argtypes = [vp, dp, C.c_int64, i64p, dp]
         L.ora_boundary_flux.argtypes = [vp, C.c_int, dp, dp]
         L.ora_plane_integral.argtypes = [vp, C.c_int, C.c_int64, dp, dp]
+        L.ora_ns_apply.argtypes = [vp, vp, dp, dp, dp, dp, dp, C.c_int, dp]
+        L.ora_ns_matrix.restype = C.c_int64
+        L.ora_ns_matrix.argtypes = [vp, vp, dp, i64p, i64p, dp]
+        L.ora_ns_bc_rows.argtypes = [vp, vp, i32p, dp]
+        L.ora_ns_mms.argtypes = [vp, C.c_int, C.c_double, C.c_int64, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -108,6 +116,64 @@ class Params:
                     p.bc_type[f][k] = int(self.bc_type[f, k])
                     p.bc_val[f][k] = float(self.bc_val[f, k])
         return p
+
+
+class _NsParams(C.Structure):
+    _fields_ = [
+        ("Sc", C.c_double), ("kappa", C.c_double), ("eps", C.c_double), ("dt", C.c_double),
+        ("beta0", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("C_I", C.c_double),
+        ("t", C.c_double), ("pin_val", C.c_double),
+        ("steady", C.c_int32), ("vms", C.c_int32), ("mms", C.c_int32), ("pin", C.c_int32),
+        ("bc_type", (C.c_int32 * 4) * 6), ("bc_val", (C.c_double * 4) * 6),
+    ]
+
+
+@dataclasses.dataclass
+class NsParams:
+    """Parameters of the linear VMS Navier-Stokes block.
+
+    Sc    : Schmidt number (inertia coefficient 1/Sc; 1/Re = Sc in tau_m)
+    kappa : electrohydrodynamic coupling constant; eps: Lambda (body force kappa/(2 Lambda^2))
+    dt, beta : time step and BDF coefficients;  C_I: constant of tau_m (6)
+    steady: drop d/dt terms;  vms: include the fine-scale terms;  mms: manufactured forcing
+    pin   : fix the pressure of the node at the origin to pin_val
+    bc_type / bc_val : [2*dim, 4] per face, per slot (v_x, v_y, v_z, p): 0 natural, 1 Dirichlet
+    """
+    Sc: float = 1.0
+    kappa: float = 0.5
+    eps: float = 1.0
+    dt: float = 1.0
+    beta: tuple = (1.0, -1.0, 0.0)
+    C_I: float = 6.0
+    t: float = 0.0
+    steady: bool = False
+    vms: bool = True
+    mms: bool = False
+    pin: bool = True
+    pin_val: float = 0.0
+    bc_type: np.ndarray | None = None
+    bc_val: np.ndarray | None = None
+
+    def to_c(self) -> _NsParams:
+        p = _NsParams()
+        p.Sc, p.kappa, p.eps, p.dt = self.Sc, self.kappa, self.eps, self.dt
+        p.beta0, p.beta1, p.beta2 = self.beta
+        p.C_I, p.t, p.pin_val = self.C_I, self.t, self.pin_val
+        p.steady, p.vms, p.mms, p.pin = int(self.steady), int(self.vms), int(self.mms), int(self.pin)
+        if self.bc_type is not None:
+            for f in range(self.bc_type.shape[0]):
+                for k in range(4):
+                    p.bc_type[f][k] = int(self.bc_type[f, k])
+                    p.bc_val[f][k] = float(self.bc_val[f, k])
+        return p
+
+
+def no_slip_bcs(dim: int, walls=None):
+    """Velocity Dirichlet 0 on the faces in `walls` (default: all 2*dim faces); pressure natural."""
+    bt = np.zeros((2 * dim, 4), np.int32)
+    for f in (range(2 * dim) if walls is None else walls):
+        bt[f, :3] = 1
+    return bt, np.zeros((2 * dim, 4))
 
 
 class OracleMesh:
@@ -255,6 +321,43 @@ class OracleMesh:
             np.minimum.at(hmin, self.el_nodes[:, c], s_el)
         return hmin
 
+    # ------------------------------------------------------------------ Navier-Stokes block
+    def _x4(self, X):
+        return np.zeros((self.n_nodes, 4)) if X is None else np.ascontiguousarray(X, dtype=np.float64).reshape(self.n_nodes, 4)
+
+    def ns_apply(self, p: NsParams, X, adv=None, Vk=None, Vkm1=None, U=None, with_data=True):
+        """NS rows [n_nodes, 4] of X: the residual of the linear system (with_data) or the
+        matrix times X."""
+        X = self._x4(X); a = self._vel3(adv); vk = self._vel3(Vk); vkm1 = self._vel3(Vkm1); U = self._z(U)
+        F = np.zeros((self.n_nodes, 4))
+        pc = p.to_c()
+        lib().ora_ns_apply(self.h, C.byref(pc), _p(X, C.c_double), _p(a, C.c_double), _p(vk, C.c_double),
+                           _p(vkm1, C.c_double), _p(U, C.c_double), int(bool(with_data)), _p(F, C.c_double))
+        return F
+
+    def ns_matrix(self, p: NsParams, adv=None) -> sp.csr_matrix:
+        a = self._vel3(adv)
+        pc = p.to_c()
+        L = lib()
+        k = L.ora_ns_matrix(self.h, C.byref(pc), _p(a, C.c_double), None, None, None)
+        I = np.zeros(k, np.int64); J = np.zeros(k, np.int64); X = np.zeros(k)
+        L.ora_ns_matrix(self.h, C.byref(pc), _p(a, C.c_double), _p(I, C.c_int64), _p(J, C.c_int64), _p(X, C.c_double))
+        n = 4 * self.n_nodes
+        return sp.coo_matrix((X, (I, J)), shape=(n, n)).tocsr()
+
+    def ns_bc_rows(self, p: NsParams):
+        kind = np.zeros((self.n_nodes, 4), np.int32)
+        g = np.zeros((self.n_nodes, 4))
+        pc = p.to_c()
+        lib().ora_ns_bc_rows(self.h, C.byref(pc), _p(kind, C.c_int32), _p(g, C.c_double))
+        return kind, g
+
+    def ns_solve(self, p: NsParams, adv=None, Vk=None, Vkm1=None, U=None):
+        """The (v, p) of the linear NS system: A X = -F(0) by a sparse direct solve."""
+        b = -self.ns_apply(p, None, adv, Vk, Vkm1, U, with_data=True).reshape(-1)
+        A = self.ns_matrix(p, adv)
+        return spla.spsolve(A.tocsc(), b).reshape(-1, 4)
+
     def qp_eval(self, p: Params, e: int, q: int, U, Uk=None, Ukm1=None, adv=None):
         U = self._z(U); Uk = self._z(Uk); Ukm1 = self._z(Ukm1); v = self._vel3(adv)
         out = np.zeros(3)
@@ -397,3 +500,43 @@ def l2_error(mesh: OracleMesh, U, Uex):
     h = 1.0 / (1 << mesh.max_level)
     d = U - Uex
     return np.sqrt(h ** mesh.dim * np.sum(d**2, axis=0))
+
+
+def ns_mms_eval(p: NsParams, dim: int, t: float, x: np.ndarray):
+    """Manufactured (u, v, w, p) [n, 4] of Eq. manufac_sol and the momentum forcing [n, 3]."""
+    n = x.shape[0]
+    x3 = np.zeros((n, 3)); x3[:, : x.shape[1]] = x
+    vals = np.zeros((n, 4)); forc = np.zeros((n, 3))
+    pc = p.to_c()
+    lib().ora_ns_mms(C.byref(pc), dim, t, n, _p(x3, C.c_double), _p(vals, C.c_double), _p(forc, C.c_double))
+    return vals, forc
+
+
+@dataclasses.dataclass
+class CoupledResult:
+    X: np.ndarray          # (v, p) at t^{k+1}, [n, 4]
+    U: np.ndarray          # (c+, c-, phi) at t^{k+1}, [n, 3]
+    newton_its: list
+
+
+def coupled_step(mesh: OracleMesh, p: Params, nsp: NsParams, Uk, Ukm1, Vk, Vkm1, n_block: int = 1,
+                 start: str = "previous", rtol: float = 1e-10, line_search: bool = True) -> CoupledResult:
+    """One NS-PNP time step by block iteration (Sec. 4.1): the linear NS block from the
+    latest PNP state (U^k in the first pass), then PNP Newton with the new velocity as
+    advection; repeated n_block times.  p and nsp carry the step's dt and BDF
+    coefficients; the NS advection is v~ = 2 v^k - v^{k-1} (Eq. averaging1).
+    """
+    Uk = mesh._z(Uk); Ukm1 = mesh._z(Ukm1)
+    vk = mesh._vel3(Vk); vkm1 = mesh._vel3(Vkm1)
+    adv = 2.0 * vk - vkm1
+    U = Uk.copy() if start == "previous" else 2.0 * Uk - Ukm1
+    body = Uk
+    its = []
+    X = None
+    for _ in range(n_block):
+        X = mesh.ns_solve(nsp, adv, vk, vkm1, body)
+        res = newton(mesh, p, U, Uk, Ukm1, adv=X[:, :3], rtol=rtol, line_search=line_search)
+        U = res.U
+        body = U
+        its.append(res.iterations)
+    return CoupledResult(X, U, its)

@@ -19,6 +19,9 @@
 //   * Q1 elements on a 2:1-balanced octree (Sec. 4.2) with conforming hanging-node
 //     constraints (the paper does not describe them; face-centre = mean of 4 face
 //     corners, edge-midpoint = mean of 2 edge ends);
+//   * the semi-implicit VMS Navier-Stokes block of Def. 3 (momentum and solenoidality
+//     rows, linear in (v, p)) with its closure v^f = -tau_m R_m, p^f = -tau_sol R_sol of
+//     Sec. 3.1, and the manufactured (u, v, p) of Eq. manufac_sol;
 //   * optional periodic side walls (the electroconvection setup of Sec. 5.2): on a
 //     periodic axis every coordinate is taken modulo the domain length, so the faces
 //     x = 0 and x = 1 are one set of nodes and carry no boundary condition.
@@ -715,6 +718,291 @@ void jv(const Mesh& m, const Params& p, const double* U, const double* Uk, const
   }
 }
 
+// ------------------------------------------------------------------ Navier-Stokes block
+// The semi-implicit VMS momentum and solenoidality rows of Def. 3 (Sec. 3.1), linear in
+// the unknown (v, p) at t^{k+1}:
+//   momentum, test w_i:
+//     (1/Sc)(w_i, (b0 v_i + b1 v_i^k + b2 v_i^{k-1})/dt) + (1/Sc)(w_i, v~_j d_j v_i)
+//     + (1/Sc)(d_j w_i, v~_j tau_m R_m,i) + (w_i, d_i p) + (d_i w_i, tau_sol R_sol)
+//     + (d_j w_i, d_j v_i) + kappa/(2 Lambda^2) (w_i, (sum_s z_s c_s) d_i phi) - (w_i, f_i)
+//   solenoidality, test q:
+//     (q, d_i v_i) + (d_i q, tau_m R_m,i)
+// with the strong residuals
+//     R_m,i = (1/Sc)((b0 v_i + b1 v_i^k + b2 v_i^{k-1})/dt + v~_j d_j v_i) + d_i p
+//             + kappa/(2 Lambda^2)(sum_s z_s c_s) d_i phi - f_i     (lap v = 0 on a Q1 cube)
+//     R_sol = d_i v_i,
+//     tau_m = (4/dt^2 + v~.G.v~ + C_I Sc^2 G:G)^(-1/2),   tau_sol = 1 / (tr(G) tau_m),
+// G = (2/h)^2 I, and 1/Re = Sc (the velocity scale D/L of Sec. 2.2 makes Re = 1/Sc).  The
+// fine-scale velocity is v^f = -tau_m R_m (Sec. 3.1), so the solenoidality row carries
+// +(d_i q, tau_m R_m,i): the printed minus sign in front of that term (next to the
+// misprinted test function) contradicts v^f = -tau_m R_m and would destabilise the
+// pressure.  v~ = 2 v^k - v^{k-1} (Eq. averaging1) is an input.  (c_s, phi) is the PNP
+// state the body force is taken from (the latest block iterate).  f is the forcing of
+// the manufactured solution (zero otherwise).
+//
+// Unknowns: node-major [nn][4] = (v_x, v_y, v_z, p); in 2D slot 2 is inactive (its row
+// is X_2 = 0).  Row kinds: hanging-node constraint rows, Dirichlet rows X - g (per face
+// and component, the last Dirichlet face containing the node wins) and, with `pin`, the
+// pressure row of the node at the origin, X_3 - pin_val.
+struct NsParams {
+  double Sc;     // Schmidt number (inertia coefficient 1/Sc)
+  double kappa;  // electrohydrodynamic coupling constant
+  double eps;    // Lambda: body-force coefficient kappa / (2 Lambda^2)
+  double dt;
+  double beta0, beta1, beta2;
+  double C_I;
+  double t;      // time level of the unknown (manufactured solution only)
+  double pin_val;
+  int32_t steady;  // 1: drop the time-derivative terms and 4/dt^2 in tau_m
+  int32_t vms;     // 0: tau_m = tau_sol = 0
+  int32_t mms;     // 1: manufactured forcing and Dirichlet values
+  int32_t pin;     // 1: pressure of the origin node fixed to pin_val
+  int32_t bc_type[6][4];
+  double bc_val[6][4];
+  double Sc_inv() const { return 1.0 / Sc; }
+};
+
+// Manufactured (u, v, w, p) of Eq. manufac_sol (3D: times cos(pi z), w = 0): value,
+// gradient, Laplacian, time derivative; the momentum forcing that makes them (with the
+// manufactured c+-, phi) an exact solution of the non-dimensional NS equation of Sec. 2.2,
+//   (1/Sc)(dv/dt + v.grad v) + grad p - lap v + kappa/(2 Lambda^2)(c+ - c-) grad phi = f.
+void ns_mms(const NsParams& p, int dim, const double* x, double t, MmsField out[4], double f[3]) {
+  MmsField m[6];
+  mms_fields(dim, x, t, p.steady, m);
+  out[0] = m[3];
+  out[1] = m[4];
+  out[2] = m[5];
+  // p = cos(2t) sin(2 pi x) cos(2 pi y) (3D: cos(pi z)): the same function as u
+  out[3] = m[3];
+  const double body = p.kappa / (2.0 * p.eps * p.eps) * (m[0].val - m[1].val);
+  for (int i = 0; i < 3; ++i) {
+    f[i] = 0.0;
+    if (i >= dim) continue;
+    double adv = 0.0;
+    for (int j = 0; j < dim; ++j) adv += out[j].val * out[i].grad[j];
+    f[i] = p.Sc_inv() * (out[i].dval_dt + adv) + out[3].grad[i] - out[i].lap + body * m[2].grad[i];
+  }
+}
+
+// Dirichlet value of (node, slot), if any.
+bool ns_dirichlet(const Mesh& m, const NsParams& p, int64_t i, int f, double* g) {
+  if (m.hanging[i]) return false;
+  if (m.dim == 2 && f == 2) {
+    *g = 0.0;
+    return true;
+  }
+  const int64_t size = int64_t(1) << m.L;
+  bool is = false;
+  for (int face = 0; face < 2 * m.dim; ++face) {
+    const int ax = face / 2;
+    if ((m.periodic >> ax) & 1) continue;
+    const int64_t want = (face & 1) ? size : 0;
+    if (m.node_xyz[i][ax] != want) continue;
+    if (p.bc_type[face][f] != 1) continue;
+    is = true;
+    if (p.mms) {
+      double x[3] = {0, 0, 0};
+      for (int k = 0; k < m.dim; ++k) x[k] = (double)m.node_xyz[i][k] / (double)size;
+      MmsField mf[4];
+      double fr[3];
+      ns_mms(p, m.dim, x, p.t, mf, fr);
+      *g = mf[f].val;
+    } else {
+      *g = p.bc_val[face][f];
+    }
+  }
+  if (!is && f == 3 && p.pin) {
+    bool origin = true;
+    for (int k = 0; k < m.dim; ++k) origin = origin && m.node_xyz[i][k] == 0;
+    if (origin) {
+      *g = p.pin_val;
+      return true;
+    }
+  }
+  return is;
+}
+
+// Element nodal values of a node-major 4-slot vector through the constraints.
+void gather4(const Mesh& m, int64_t e, const double* X, double out[8][4]) {
+  const int nc = corner_count(m.dim);
+  for (int c = 0; c < nc; ++c) {
+    for (int f = 0; f < 4; ++f) out[c][f] = 0.0;
+    for (auto& pw : m.cons[m.el_nodes[e][c]])
+      for (int f = 0; f < 4; ++f) out[c][f] += pw.second * X[4 * pw.first + f];
+  }
+}
+
+// Element rows of the NS system from element-local nodal values (X through the
+// constraints).  `with_data` = 0 drops every term that does not depend on X (history,
+// body force, forcing): then Fe is the element matrix times Xe.
+void ns_element_core(const Mesh& m, const NsParams& p, int64_t e, const double Xe[8][4], const double Ae[8][3],
+                     const double Vke[8][3], const double Vkm1e[8][3], const double Ue[8][3], int with_data,
+                     double Fe[8][4]) {
+  const int dim = m.dim, nc = corner_count(dim);
+  for (int c = 0; c < nc; ++c)
+    for (int f = 0; f < 4; ++f) Fe[c][f] = 0.0;
+  const double h = std::ldexp(1.0, -m.el_level[e]);
+  const double G = (2.0 / h) * (2.0 / h);
+  const double kap = p.steady ? 0.0 : p.beta0 / p.dt;
+  const double isc = p.Sc_inv();
+  const double fb = p.kappa / (2.0 * p.eps * p.eps);
+  for (int q = 0; q < nc; ++q) {
+    Qp Q;
+    eval_qp(m, e, q, Q);
+    double v[3] = {0, 0, 0}, gv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gp[3] = {0, 0, 0};
+    double va[3] = {0, 0, 0}, hv[3] = {0, 0, 0}, cp = 0, cm = 0, gphi[3] = {0, 0, 0};
+    for (int c = 0; c < nc; ++c) {
+      for (int i = 0; i < dim; ++i) {
+        v[i] += Q.N[c] * Xe[c][i];
+        va[i] += Q.N[c] * Ae[c][i];
+        if (!p.steady) hv[i] += Q.N[c] * (p.beta1 * Vke[c][i] + p.beta2 * Vkm1e[c][i]) / p.dt;
+        for (int j = 0; j < dim; ++j) gv[i][j] += Q.dN[c][j] * Xe[c][i];  // d v_i / d x_j
+        gp[i] += Q.dN[c][i] * Xe[c][3];
+        gphi[i] += Q.dN[c][i] * Ue[c][2];
+      }
+      cp += Q.N[c] * Ue[c][0];
+      cm += Q.N[c] * Ue[c][1];
+    }
+    double f[3] = {0, 0, 0};
+    if (p.mms && with_data) {
+      MmsField mf[4];
+      ns_mms(p, dim, Q.x, p.t, mf, f);
+    }
+    double vv = 0, div = 0;
+    for (int i = 0; i < dim; ++i) {
+      vv += va[i] * va[i];
+      div += gv[i][i];
+    }
+    // tau_m = (4/dt^2 + v~.G.v~ + C_I (1/Re)^2 G:G)^(-1/2), G:G = d (2/h)^4, 1/Re = Sc
+    const double arg = (p.steady ? 0.0 : 4.0 / (p.dt * p.dt)) + G * vv + p.C_I * p.Sc * p.Sc * dim * G * G;
+    const double tau_m = p.vms ? 1.0 / std::sqrt(arg) : 0.0;
+    const double tau_s = p.vms ? 1.0 / (dim * G * tau_m) : 0.0;  // 1 / (tr(G) tau_m)
+    double Rm[3] = {0, 0, 0};
+    for (int i = 0; i < dim; ++i) {
+      double adv_i = 0;
+      for (int j = 0; j < dim; ++j) adv_i += va[j] * gv[i][j];
+      Rm[i] = isc * (kap * v[i] + adv_i) + gp[i];
+      if (with_data) Rm[i] += isc * hv[i] + fb * (cp - cm) * gphi[i] - f[i];
+    }
+    for (int a = 0; a < nc; ++a) {
+      double vgN = 0;  // v~ . grad N_a
+      for (int j = 0; j < dim; ++j) vgN += va[j] * Q.dN[a][j];
+      for (int i = 0; i < dim; ++i) {
+        double visc = 0;
+        for (int j = 0; j < dim; ++j) visc += Q.dN[a][j] * gv[i][j];
+        // the Galerkin terms other than the viscous one are N_a R_m,i (lap v = 0)
+        Fe[a][i] += Q.w * (Q.N[a] * Rm[i] + visc + isc * vgN * tau_m * Rm[i] + Q.dN[a][i] * tau_s * div);
+      }
+      double pspg = 0;
+      for (int i = 0; i < dim; ++i) pspg += Q.dN[a][i] * tau_m * Rm[i];
+      Fe[a][3] += Q.w * (Q.N[a] * div + pspg);
+    }
+  }
+}
+
+void ns_element(const Mesh& m, const NsParams& p, int64_t e, const double* X, const double* adv,
+                const double* Vk, const double* Vkm1, const double* U, int with_data, double Fe[8][4]) {
+  double Xe[8][4], Ae[8][3], Vke[8][3], Vkm1e[8][3], Ue[8][3];
+  gather4(m, e, X, Xe);
+  gather3(m, e, adv, Ae);
+  gather3(m, e, Vk, Vke);
+  gather3(m, e, Vkm1, Vkm1e);
+  gather3(m, e, U, Ue);
+  ns_element_core(m, p, e, Xe, Ae, Vke, Vkm1e, Ue, with_data, Fe);
+}
+
+// Row fix-ups of the NS system: constraint rows of hanging nodes and Dirichlet rows.
+// affine = 1: the rows of the residual (X - g); 0: the rows of the matrix (X).
+void ns_rows(const Mesh& m, const NsParams& p, const double* X, int affine, double* F) {
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  for (int64_t i = 0; i < nn; ++i) {
+    if (m.hanging[i]) {
+      for (int f = 0; f < 4; ++f) {
+        double v = X[4 * i + f];
+        for (auto& pw : m.cons[i]) v -= pw.second * X[4 * pw.first + f];
+        F[4 * i + f] = v;
+      }
+      continue;
+    }
+    for (int f = 0; f < 4; ++f) {
+      double g;
+      if (ns_dirichlet(m, p, i, f, &g)) F[4 * i + f] = X[4 * i + f] - (affine ? g : 0.0);
+    }
+  }
+}
+
+void ns_apply(const Mesh& m, const NsParams& p, const double* X, const double* adv, const double* Vk,
+              const double* Vkm1, const double* U, int with_data, double* F) {
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  const int nc = corner_count(m.dim);
+  for (int64_t i = 0; i < 4 * nn; ++i) F[i] = 0.0;
+  for (int64_t e = 0; e < (int64_t)m.el_nodes.size(); ++e) {
+    double Fe[8][4];
+    ns_element(m, p, e, X, adv, Vk, Vkm1, U, with_data, Fe);
+    for (int c = 0; c < nc; ++c)
+      for (auto& pw : m.cons[m.el_nodes[e][c]])
+        for (int f = 0; f < 4; ++f) F[4 * pw.first + f] += pw.second * Fe[c][f];
+  }
+  ns_rows(m, p, X, with_data, F);
+}
+
+// Triplets of the NS matrix: each element matrix column is the element operator (without
+// data) applied to a unit vector of the element's nodal values; assembled with the
+// constraints, then the Dirichlet / constraint rows.
+int64_t ns_matrix_triplets(const Mesh& m, const NsParams& p, const double* adv, int64_t* I, int64_t* J,
+                           double* Xv) {
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  const int nc = corner_count(m.dim);
+  std::vector<char> kind(4 * nn, 0);
+  for (int64_t i = 0; i < nn; ++i)
+    for (int f = 0; f < 4; ++f) {
+      double g;
+      if (m.hanging[i]) kind[4 * i + f] = 2;
+      else if (ns_dirichlet(m, p, i, f, &g)) kind[4 * i + f] = 1;
+    }
+  int64_t k = 0;
+  auto put = [&](int64_t r, int64_t c, double v) {
+    if (I) { I[k] = r; J[k] = c; Xv[k] = v; }
+    ++k;
+  };
+  for (int64_t e = 0; e < (int64_t)m.el_nodes.size(); ++e) {
+    double Ke[32][32];
+    if (I) {
+      // column (cj, fj): the element rows (no data) of the element-local unit vector
+      double Ae[8][3], Z3[8][3] = {};
+      gather3(m, e, adv, Ae);
+      for (int cj = 0; cj < nc; ++cj)
+        for (int fj = 0; fj < 4; ++fj) {
+          double Xe[8][4] = {}, Fe[8][4];
+          Xe[cj][fj] = 1.0;
+          ns_element_core(m, p, e, Xe, Ae, Z3, Z3, Z3, 0, Fe);
+          for (int ci = 0; ci < nc; ++ci)
+            for (int fi = 0; fi < 4; ++fi) Ke[4 * ci + fi][4 * cj + fj] = Fe[ci][fi];
+        }
+    }
+    for (int ci = 0; ci < nc; ++ci)
+      for (auto& pi : m.cons[m.el_nodes[e][ci]])
+        for (int fi = 0; fi < 4; ++fi) {
+          const int64_t r = 4 * pi.first + fi;
+          if (kind[r] != 0) continue;
+          for (int cj = 0; cj < nc; ++cj)
+            for (auto& pj : m.cons[m.el_nodes[e][cj]])
+              for (int fj = 0; fj < 4; ++fj)
+                put(r, 4 * pj.first + fj, I ? pi.second * pj.second * Ke[4 * ci + fi][4 * cj + fj] : 0.0);
+        }
+  }
+  for (int64_t i = 0; i < nn; ++i)
+    for (int f = 0; f < 4; ++f) {
+      const int64_t r = 4 * i + f;
+      if (kind[r] == 1) put(r, r, 1.0);
+      if (kind[r] == 2) {
+        put(r, r, 1.0);
+        for (auto& pw : m.cons[i]) put(r, 4 * pw.first + f, -pw.second);
+      }
+    }
+  return k;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ boundary flux
@@ -994,4 +1282,43 @@ void ora_mms(int dim, double eps, double t, int steady, int64_t n, const double*
   }
 }
 
+// ------------------------------------------------------------------ Navier-Stokes block
+// F = the NS rows of the unknown X [nn][4] (with_data = 1: the residual of the linear
+// system, affine in X; 0: the matrix times X), given v~ (adv), the velocity history
+// (Vk, Vkm1) and the PNP state U the body force is taken from, all [nn][3].
+void ora_ns_apply(void* h, const NsParams* p, const double* X, const double* adv, const double* Vk,
+                  const double* Vkm1, const double* U, int with_data, double* F) {
+  ns_apply(*static_cast<Mesh*>(h), *p, X, adv, Vk, Vkm1, U, with_data, F);
+}
+
+// Triplets of the NS matrix (duplicates to be summed by the caller); pass null arrays to
+// count them.
+int64_t ora_ns_matrix(void* h, const NsParams* p, const double* adv, int64_t* I, int64_t* J, double* X) {
+  return ns_matrix_triplets(*static_cast<Mesh*>(h), *p, adv, I, J, X);
+}
+
+// Row kinds [nn][4] (0 = PDE row, 1 = Dirichlet or pressure pin, 2 = hanging) and values.
+void ora_ns_bc_rows(void* h, const NsParams* p, int32_t* kind, double* g) {
+  const Mesh& m = *static_cast<Mesh*>(h);
+  for (size_t i = 0; i < m.node_xyz.size(); ++i)
+    for (int f = 0; f < 4; ++f) {
+      double v = 0.0;
+      int k = 0;
+      if (m.hanging[i]) k = 2;
+      else if (ns_dirichlet(m, *p, (int64_t)i, f, &v)) k = 1;
+      kind[4 * i + f] = k;
+      g[4 * i + f] = v;
+    }
+}
+
+// Manufactured (u, v, w, p) [n][4] and momentum forcing [n][3] at points x [n][3].
+void ora_ns_mms(const NsParams* p, int dim, double t, int64_t n, const double* x, double* vals, double* forcing) {
+  for (int64_t i = 0; i < n; ++i) {
+    MmsField mf[4];
+    ns_mms(*p, dim, x + 3 * i, t, mf, forcing + 3 * i);
+    for (int f = 0; f < 4; ++f) vals[4 * i + f] = mf[f].val;
+  }
+}
+
 }  // extern "C"
+
