@@ -74,8 +74,11 @@ enum {
   PNP_FIELD_U_PREV2 = 2,       /* U^{k-1}                              [n][3] */
   PNP_FIELD_ADVECTION = 3,     /* advection velocity v~ of the residual [n][dim] */
   PNP_FIELD_VELOCITY = 4,      /* fluid velocity v^k                    [n][dim] */
-  PNP_FIELD_VELOCITY_PREV = 5  /* fluid velocity v^{k-1}                [n][dim] */
+  PNP_FIELD_VELOCITY_PREV = 5, /* fluid velocity v^{k-1}                [n][dim] */
+  PNP_FIELD_NS = 6             /* Navier-Stokes unknown (v_x, v_y, v_z, p) at the latest
+                                  solve (start of the next one)       [n][4]; 2D: v_z = 0 */
 };
+enum { PNP_NS_VX = 0, PNP_NS_VY = 1, PNP_NS_VZ = 2, PNP_NS_P = 3 };
 enum { PNP_START_PREVIOUS = 0, PNP_START_EXTRAPOLATE = 1, PNP_START_LEARNED = 2 };
 
 typedef struct pnp_mesh pnp_mesh;
@@ -131,7 +134,19 @@ typedef struct pnp_params {
   int32_t mg_smooth;     /* damped block-Jacobi sweeps before and after the coarse correction (2) */
   double mg_omega;       /* damping of the sweeps (0.5) */
   int32_t mg_coarse_its; /* block-Jacobi sweeps on the coarsest level (16) */
-  int32_t pad3_;
+  /* Navier-Stokes block (semi-implicit VMS momentum and solenoidality, Def. 3 and Sec. 3.1) */
+  int32_t ns_blocks;     /* pnp_coupled_step: NS -> PNP block iterations per step (1; Sec. 4.1) */
+  double ns_Sc;          /* Schmidt number Sc: inertia coefficient 1/Sc, 1/Re = Sc in tau_m (1) */
+  double ns_kappa;       /* electrohydrodynamic coupling constant kappa: body force
+                            kappa / (2 Lambda^2) (c+ - c-) grad phi (0.5) */
+  double ns_rtol;        /* NS linear solve: ||F(X)||_2 <= max(ns_rtol ||F(X^0)||_2, ns_atol)
+                            (1e-8 and 1e-10, the tolerances of App. A) */
+  double ns_atol;
+  double ns_inner_rtol;  /* relative residual reduction of the FP32 BiCGStab of each FP64
+                            refinement step (1e-4) */
+  int32_t ns_max_it;     /* total FP32 BiCGStab iterations per NS solve (4000) */
+  int32_t ns_pin;        /* 1: the pressure of the node at the origin is pinned to 0 unless a
+                            pressure Dirichlet face holds it (1) */
 } pnp_params;
 
 typedef struct pnp_solve_stats {
@@ -157,6 +172,19 @@ typedef struct pnp_solve_stats {
                             (gmres_inner, or 24 steps) */
   int32_t pad_;
 } pnp_solve_stats;
+
+/* Statistics of one Navier-Stokes linear solve. */
+typedef struct pnp_ns_stats {
+  int32_t status;        /* pnp_status of the solve */
+  int32_t refinements;   /* FP64 refinement steps (one FP32 BiCGStab each) */
+  int32_t inner_its;     /* total FP32 BiCGStab iterations */
+  int32_t matvecs32;     /* FP32 matrix applications (2 per BiCGStab iteration) */
+  int32_t matvecs64;     /* FP64 residual evaluations */
+  int32_t singular_blocks; /* 1 when a 4x4 diagonal block was singular (replaced by I) */
+  double res0;           /* ||F(X^0)||_2 */
+  double res_final;      /* ||F(X)||_2 */
+  double wall_ms;        /* host wall time of the call */
+} pnp_ns_stats;
 
 /* Message for the calling thread's most recent failure ("" if none).  Static storage. */
 const char* pnp_last_error(void);
@@ -351,6 +379,53 @@ int pnp_set_step_count(pnp_ctx* c, int64_t k);
 /* Start a new trajectory: U_PREV and U_PREV2 <- U, step count <- 0. */
 int pnp_reset_history(pnp_ctx* c);
 
+/* ---------------------------------------------------------------- Navier-Stokes -- */
+/* The semi-implicit VMS Navier-Stokes block (Def. 3 momentum and solenoidality with the
+ * closure v^f = -tau_m R_m, p^f = -tau_sol R_sol of Sec. 3.1), linear in X = (v, p) at
+ * t^{k+1}: with v~ = 2 v^k - v^{k-1} (Eq. averaging1) from VELOCITY / VELOCITY_PREV,
+ *   momentum, test N_a e_i:  N_a R_m,i + grad N_a . grad v_i
+ *                            + (1/Sc) tau_m (v~ . grad N_a) R_m,i + d_i N_a tau_sol div v
+ *   solenoidality, test N_a: N_a div v + tau_m grad N_a . R_m
+ *   R_m,i = (1/Sc)((beta0 v_i + beta1 v_i^k + beta2 v_i^{k-1})/dt + v~ . grad v_i) + d_i p
+ *           + kappa / (2 Lambda^2) (c+ - c-) d_i phi,
+ *   tau_m = (4/dt^2 + (2/h)^2 |v~|^2 + C_I Sc^2 d (2/h)^4)^(-1/2), tau_sol = 1/(d (2/h)^2 tau_m)
+ * (parameters ns_Sc, ns_kappa, eps, dt, beta0..2, C_I, steady).  The solenoidality row
+ * takes +tau_m grad N_a . R_m, the sign v^f = -tau_m R_m gives (the printed form has a
+ * minus and a misprinted test function there).  Unknowns node-major [n][4] = (v_x, v_y,
+ * v_z, p), 2D: slot v_z inactive (its row is X = 0).  Rows: hanging-node constraints,
+ * Dirichlet rows X - g from pnp_ns_set_bc, and with ns_pin the pressure of the node at
+ * the origin fixed to 0.  The PNP state of the body force is PNP_FIELD_U. */
+/* Boundary condition of slot PNP_NS_* on one face: PNP_DIRICHLET (value g; a no-slip wall
+ * is g = 0 on the three velocity slots) or PNP_NATURAL (the boundary terms of the weak
+ * form vanish). */
+int pnp_ns_set_bc(pnp_ctx* c, int face, int slot, int type, double value);
+/* F = the NS rows at X (device FP64 [n][4] each): the residual of the linear system,
+ * A X - b, with b from the history, the body force and the Dirichlet values. */
+int pnp_ns_residual(pnp_ctx* c, const double* X, double* F);
+/* Y = A X: the matrix of the linear system (the residual without its data terms), with
+ * identity rows on Dirichlet / pin rows and the constraint rows of hanging nodes.
+ * precision PNP_F64: double [n][4]; PNP_F32: float [n][4] (16-byte aligned). */
+int pnp_ns_matvec(pnp_ctx* c, const void* X, void* Y, int precision);
+/* The 4x4 nodal diagonal blocks of A (device FP64 [n][16], row-major per node) before the
+ * row substitutions; a hanging corner contributes w_p^2 times its own block to each
+ * parent p (the cross pairs through hanging corners are left out).  The preconditioner
+ * of pnp_ns_solve inverts them (identity rows on constrained rows). */
+int pnp_ns_block_diag(pnp_ctx* c, double* D);
+/* Solve the linear NS system for PNP_FIELD_NS in place, starting from its value: FP64
+ * defect correction around FP32 BiCGStab (App. A solves this block with BiCGStab),
+ * right-preconditioned by the inverted diagonal blocks, until ||F(X)|| <= max(ns_rtol
+ * ||F(X^0)||, ns_atol).  PNP_ERR_KRYLOV_MAXIT after ns_max_it BiCGStab iterations or 40
+ * refinement steps; PNP_ERR_NAN on a non-finite norm.  Uses the context's beta0..2. */
+int pnp_ns_solve(pnp_ctx* c, pnp_ns_stats* st);
+/* One NS-PNP time step by block iteration (Sec. 4.1): ns_blocks times, the NS system
+ * (body force from U^k in the first pass, then from the latest U^{k+1}) and then the PNP
+ * Newton solve of pnp_time_step with the new velocity v^{k+1} as the advection; BDF1 on the
+ * first step, then bdf_order, for both blocks.  On success VELOCITY_PREV <- VELOCITY <-
+ * v^{k+1}, PNP_FIELD_NS holds (v, p)^{k+1} and the PNP history is shifted as in
+ * pnp_time_step.  pst: the last PNP solve (Newton / Krylov counts summed over the block
+ * iterations), nst: the NS solves (iterations summed). */
+int pnp_coupled_step(pnp_ctx* c, pnp_solve_stats* pst, pnp_ns_stats* nst);
+
 /* ---------------------------------------------------------------- learned start -- */
 /* The library's addition to the paper (which has no learned component): a per-node
  * network proposes the Newton start of pnp_time_step (start_mode PNP_START_LEARNED);
@@ -473,7 +548,10 @@ enum {
   PNP_PROF_ORTHO_UPDATE = 7, /* Gram-Schmidt update: the multi-axpy + norm kernel */
   PNP_PROF_INNER = 8,      /* FP32 Gram-Schmidt of the inner GMRES (flexible mode) */
   PNP_PROF_MG = 9,         /* multigrid: everything on the coarse levels of a V-cycle */
-  PNP_PROF_KINDS = 10
+  PNP_PROF_NS = 10,        /* Navier-Stokes FP64 element kernels (residual, blocks) */
+  PNP_PROF_NS32 = 11,      /* Navier-Stokes FP32 matrix action */
+  PNP_PROF_NS_KRYLOV = 12, /* Navier-Stokes BiCGStab vector, dot and block-Jacobi kernels */
+  PNP_PROF_KINDS = 13
 };
 /* on != 0: clear the accumulated times and start recording; on == 0: stop. */
 int pnp_profile_enable(pnp_ctx* c, int on);

@@ -535,7 +535,9 @@ def coupled_step(mesh: OracleMesh, p: Params, nsp: NsParams, Uk, Ukm1, Vk, Vkm1,
     X = None
     for _ in range(n_block):
         X = mesh.ns_solve(nsp, adv, vk, vkm1, body)
-        res = newton(mesh, p, U, Uk, Ukm1, adv=X[:, :3], rtol=rtol, line_search=line_search)
+        # every pass meets rtol ||F(U^k)|| (with this pass's advection), whatever its start
+        f_ref = np.linalg.norm(mesh.residual(p, mesh.make_consistent(Uk, p), Uk, Ukm1, X[:, :3]))
+        res = newton(mesh, p, U, Uk, Ukm1, adv=X[:, :3], rtol=rtol, atol=rtol * f_ref, line_search=line_search)
         U = res.U
         body = U
         its.append(res.iterations)

@@ -71,11 +71,18 @@ void pnp_params_default(pnp_params* p) {
   p->f64_fallback = 1;
   p->gmres_inner = 0;
   p->newton_ew_f64 = 0;
+  p->ns_blocks = 1;
+  p->ns_Sc = 1.0;
+  p->ns_kappa = 0.5;
+  p->ns_rtol = 1e-8;
+  p->ns_atol = 1e-10;
+  p->ns_inner_rtol = 1e-4;
+  p->ns_max_it = 4000;
+  p->ns_pin = 1;
   p->mg_levels = 0;
   p->mg_smooth = 2;
   p->mg_omega = 0.5;
   p->mg_coarse_its = 16;
-  p->pad3_ = 0;
 }
 
 // ------------------------------------------------------------------ mesh
@@ -226,6 +233,10 @@ static int check_params(const pnp_params* p) {
       !(p->mg_omega <= 2) || p->mg_coarse_its < 1 || p->mg_coarse_its > 1000)
     PNP_FAIL(PNP_ERR_ARG, "params: multigrid settings out of range");
   if (p->dt_retries < 0 || p->dt_retries > 16) PNP_FAIL(PNP_ERR_ARG, "params: dt_retries in 0..16");
+  if (p->ns_blocks < 1 || p->ns_blocks > 16 || !(p->ns_Sc > 0) || !std::isfinite(p->ns_Sc) ||
+      !std::isfinite(p->ns_kappa) || !(p->ns_rtol >= 0) || !(p->ns_atol >= 0) || !(p->ns_inner_rtol > 0) ||
+      !(p->ns_inner_rtol < 1) || p->ns_max_it < 1 || (p->ns_pin != 0 && p->ns_pin != 1))
+    PNP_FAIL(PNP_ERR_ARG, "params: Navier-Stokes settings out of range");
   return PNP_OK;
 }
 
@@ -478,6 +489,7 @@ void pnp_ctx_destroy(pnp_ctx* c) {
   else cudaDeviceSynchronize();
   pnp_mlp_release(c);
   ctx_mg_release(c);
+  ctx_ns_release(c);
   for (auto& pe : c->ev_pending) {
     cudaEventDestroy(pe.second.first);
     cudaEventDestroy(pe.second.second);
@@ -514,6 +526,17 @@ int pnp_set_bc(pnp_ctx* c, int face, int field, int type, double value) {
   return PNP_OK;
 }
 
+int pnp_ns_set_bc(pnp_ctx* c, int face, int slot, int type, double value) {
+  CTX_GUARD(c);
+  if (face < 0 || face >= 2 * c->dim) PNP_FAIL(PNP_ERR_ARG, "pnp_ns_set_bc: face %d out of range", face);
+  if (slot < 0 || slot > 3) PNP_FAIL(PNP_ERR_ARG, "pnp_ns_set_bc: slot %d out of range", slot);
+  if (type != PNP_NATURAL && type != PNP_DIRICHLET) PNP_FAIL(PNP_ERR_ARG, "pnp_ns_set_bc: bad type %d", type);
+  if (!std::isfinite(value)) PNP_FAIL(PNP_ERR_ARG, "pnp_ns_set_bc: value not finite");
+  c->ns_bc_type[face][slot] = type;
+  c->ns_bc_val[face][slot] = value;
+  return PNP_OK;
+}
+
 static double* field_ptr(pnp_ctx* c, int which) {
   switch (which) {
     case PNP_FIELD_U: return c->U;
@@ -528,6 +551,14 @@ static double* field_ptr(pnp_ctx* c, int which) {
 
 int pnp_set_field(pnp_ctx* c, int which, const double* src, int where) {
   CTX_GUARD(c);
+  if (which == PNP_FIELD_NS) {
+    if (!src || (where != PNP_DEVICE && where != PNP_HOST)) PNP_FAIL(PNP_ERR_ARG, "pnp_set_field: bad arguments");
+    if (int rc = ctx_ns_alloc(c)) return rc;
+    CK(cudaMemcpyAsync(ctx_ns_field(c), src, sizeof(double) * 4 * c->n_nodes,
+                       where == PNP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PNP_OK;
+  }
   double* dst = field_ptr(c, which);
   if (!dst || !src) PNP_FAIL(PNP_ERR_ARG, "pnp_set_field: bad field %d or null source", which);
   if (where != PNP_DEVICE && where != PNP_HOST) PNP_FAIL(PNP_ERR_ARG, "pnp_set_field: bad where");
@@ -547,6 +578,14 @@ int pnp_set_field(pnp_ctx* c, int which, const double* src, int where) {
 
 int pnp_get_field(pnp_ctx* c, int which, double* dstp, int where) {
   CTX_GUARD(c);
+  if (which == PNP_FIELD_NS) {
+    if (!dstp || (where != PNP_DEVICE && where != PNP_HOST)) PNP_FAIL(PNP_ERR_ARG, "pnp_get_field: bad arguments");
+    if (int rc = ctx_ns_alloc(c)) return rc;
+    CK(cudaMemcpyAsync(dstp, ctx_ns_field(c), sizeof(double) * 4 * c->n_nodes,
+                       where == PNP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PNP_OK;
+  }
   double* src = field_ptr(c, which);
   if (!src || !dstp) PNP_FAIL(PNP_ERR_ARG, "pnp_get_field: bad field %d or null destination", which);
   if (where != PNP_DEVICE && where != PNP_HOST) PNP_FAIL(PNP_ERR_ARG, "pnp_get_field: bad where");
@@ -729,6 +768,54 @@ int pnp_time_step(pnp_ctx* c, pnp_solve_stats* st) {
   CTX_GUARD(c);
   pnp_solve_stats local;
   return ctx_time_step(c, st ? st : &local);
+}
+
+// ------------------------------------------------------------------ Navier-Stokes
+int pnp_ns_residual(pnp_ctx* c, const double* X, double* F) {
+  CTX_GUARD(c);
+  if (!X || !F) PNP_FAIL(PNP_ERR_ARG, "pnp_ns_residual: null pointer");
+  if (int rc = ctx_ns_prepare(c)) return rc;
+  if (int rc = ctx_ns_apply64(c, X, c->U, F, true)) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_ns_matvec(pnp_ctx* c, const void* X, void* Y, int precision) {
+  CTX_GUARD(c);
+  if (!X || !Y) PNP_FAIL(PNP_ERR_ARG, "pnp_ns_matvec: null pointer");
+  if (precision != PNP_F64 && precision != PNP_F32) PNP_FAIL(PNP_ERR_ARG, "pnp_ns_matvec: bad precision");
+  if (precision == PNP_F32 && (((uintptr_t)X | (uintptr_t)Y) & 15))
+    PNP_FAIL(PNP_ERR_ARG, "pnp_ns_matvec: FP32 vectors must be 16-byte aligned");
+  if (int rc = ctx_ns_prepare(c)) return rc;
+  if (precision == PNP_F64) {
+    if (int rc = ctx_ns_apply64(c, (const double*)X, nullptr, (double*)Y, false)) return rc;
+  } else {
+    if (int rc = ctx_ns_apply32(c, (const float4*)X, (float4*)Y)) return rc;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_ns_block_diag(pnp_ctx* c, double* D) {
+  CTX_GUARD(c);
+  if (!D) PNP_FAIL(PNP_ERR_ARG, "pnp_ns_block_diag: null pointer");
+  if (int rc = ctx_ns_prepare(c)) return rc;
+  if (int rc = ctx_ns_block_diag(c, D)) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_ns_solve(pnp_ctx* c, pnp_ns_stats* st) {
+  CTX_GUARD(c);
+  pnp_ns_stats local;
+  return ctx_ns_solve(c, c->U, st ? st : &local);
+}
+
+int pnp_coupled_step(pnp_ctx* c, pnp_solve_stats* pst, pnp_ns_stats* nst) {
+  CTX_GUARD(c);
+  pnp_solve_stats lp;
+  pnp_ns_stats ln;
+  return ctx_coupled_step(c, pst ? pst : &lp, nst ? nst : &ln);
 }
 
 int pnp_step_count(const pnp_ctx* c, int64_t* k) {

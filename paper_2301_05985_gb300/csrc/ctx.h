@@ -88,6 +88,16 @@ struct pnp_ctx {
   std::vector<struct MgLevel>* mg = nullptr;
   int mg_built = 0;
 
+  // Navier-Stokes block (ns.cu): state allocated on first use, boundary conditions per
+  // face and slot (v_x, v_y, v_z, p)
+  struct NsState* ns = nullptr;
+  int ns_bc_type[6][4] = {};
+  double ns_bc_val[6][4] = {};
+  // pnp_coupled_step: the PNP step takes the advection as set (v^{k+1}) and leaves the
+  // velocity history alone; a repeated block iteration starts from the U already set
+  bool coupled = false;
+  bool start_given = false;
+
   // statistics of the last solve (for the time stepper)
   int jv_count = 0, res_count = 0, mg_fallbacks = 0;
 
@@ -206,3 +216,17 @@ int ctx_mg_prepare(pnp_ctx* c, const double* U);
 int ctx_mg_apply(pnp_ctx* c, const double* u, float* z32);
 void ctx_mg_release(pnp_ctx* c);
 int ctx_mg_level_count(const pnp_ctx* c);
+// Navier-Stokes block (ns.cu)
+int ctx_ns_alloc(pnp_ctx* c);
+void ctx_ns_release(pnp_ctx* c);
+double* ctx_ns_field(pnp_ctx* c);
+int ctx_ns_prepare(pnp_ctx* c);
+int ctx_ns_apply64(pnp_ctx* c, const double* X, const double* Ubody, double* F, bool data);
+int ctx_ns_apply32(pnp_ctx* c, const float4* x, float4* y);
+int ctx_ns_block_diag(pnp_ctx* c, double* Dg);
+int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st);
+int ctx_ns_velocity(pnp_ctx* c, double* v3);
+// [2][3N] scratch for the PNP history of repeated block iterations (allocated on first use)
+double* ctx_ns_history_save(pnp_ctx* c);
+int ctx_coupled_step(pnp_ctx* c, pnp_solve_stats* st, pnp_ns_stats* nst);
+double now_ms();

@@ -21,92 +21,9 @@
 
 #include "df32.cuh"
 #include "kernels.h"
+#include "lane_ops.cuh"
 
 namespace {
-
-constexpr double kG = 0.57735026918962576450914878050196;  // 1/sqrt(3)
-constexpr unsigned kFull = 0xffffffffu;
-
-template <typename T>
-__device__ __forceinline__ T flip(T x, int k) {
-  return __shfl_xor_sync(kFull, x, 1 << k);
-}
-__device__ __forceinline__ df flip(df x, int k) {
-  return df(__shfl_xor_sync(kFull, x.hi, 1 << k), __shfl_xor_sync(kFull, x.lo, 1 << k));
-}
-
-// value and gradient at this lane's Gauss point from this lane's nodal value x
-// (nb = -b': the value operator is x - b' (x - partner))
-template <typename T, int D>
-__device__ __forceinline__ void interp_vg(T x, T nb, const T (&sh)[3], T& val, T (&g)[3]) {
-  T I = x;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const T pI = flip(I, k);
-    T pG[3];
-#pragma unroll
-    for (int j = 0; j < k; ++j) pG[j] = flip(g[j], k);
-#pragma unroll
-    for (int j = 0; j < k; ++j) g[j] = fma(nb, g[j] - pG[j], g[j]);
-    const T d = I - pI;
-    g[k] = sh[k] * d;
-    I = fma(nb, d, I);
-  }
-#pragma unroll
-  for (int k = D; k < 3; ++k) g[k] = T(0);
-  val = I;
-}
-
-template <typename T, int D>
-__device__ __forceinline__ void interp_g(T x, T nb, const T (&sh)[3], T (&g)[3]) {
-  T I = x;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const T pI = flip(I, k);
-    T pG[3];
-#pragma unroll
-    for (int j = 0; j < k; ++j) pG[j] = flip(g[j], k);
-#pragma unroll
-    for (int j = 0; j < k; ++j) g[j] = fma(nb, g[j] - pG[j], g[j]);
-    const T d = I - pI;
-    g[k] = sh[k] * d;
-    if (k + 1 < D) I = fma(nb, d, I);
-  }
-#pragma unroll
-  for (int k = D; k < 3; ++k) g[k] = T(0);
-}
-
-template <typename T, int D>
-__device__ __forceinline__ T interp_v(T x, T nb) {
-#pragma unroll
-  for (int k = 0; k < D; ++k) x = fma(nb, x - flip(x, k), x);
-  return x;
-}
-
-// transpose: this lane's node contribution from the Gauss-point tests S, Phi
-template <typename T, int D>
-__device__ __forceinline__ T test_t(T S, T (&Phi)[3], T nb, const T (&sh)[3]) {
-  T A = S;
-#pragma unroll
-  for (int k = D - 1; k >= 0; --k) {
-    const T pA = flip(A, k);
-    const T pH = flip(Phi[k], k);
-    T pP[3];
-#pragma unroll
-    for (int j = 0; j < k; ++j) pP[j] = flip(Phi[j], k);
-    A = fma(nb, A - pA, fma(sh[k], Phi[k] + pH, A));
-#pragma unroll
-    for (int j = 0; j < k; ++j) Phi[j] = fma(nb, Phi[j] - pP[j], Phi[j]);
-  }
-  return A;
-}
-
-// 2^e exactly, from the exponent bits (|e| well inside the exponent range)
-__device__ __forceinline__ float pow2i(int e, float) { return __int_as_float((127 + e) << 23); }
-__device__ __forceinline__ double pow2i(int e, double) {
-  return __longlong_as_double((long long)(1023 + e) << 52);
-}
-__device__ __forceinline__ df pow2i(int e, df) { return df(pow2i(e, 0.0f), 0.0f); }
 
 // loaded value in the arithmetic type, and back to the storage type
 template <typename C, typename T>
@@ -662,29 +579,6 @@ __global__ void __launch_bounds__(kLaneThreads, 5) k_jv_from_state(ElemArgs<floa
 constexpr int kBlk = 7;
 __device__ __forceinline__ int blk_slot(int k) {  // position in the row-major 3x3 block
   return k == 0 ? 0 : k == 1 ? 2 : k == 2 ? 4 : k == 3 ? 5 : k == 4 ? 6 : k == 5 ? 7 : 8;
-}
-
-// value and gradient of corner i's shape function at this lane's Gauss point (corner c)
-template <typename T, int D>
-__device__ __forceinline__ void shape_at(int i, int c, T inv_h, T& N, T (&dN)[3]) {
-  const T fs = T(0.5 * (1.0 + kG)), fo = T(0.5 * (1.0 - kG));
-  T f[3];
-#pragma unroll
-  for (int k = 0; k < D; ++k) f[k] = (((i ^ c) >> k) & 1) ? fo : fs;
-  N = T(1);
-#pragma unroll
-  for (int k = 0; k < D; ++k) N *= f[k];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    T a = T(0);
-    if (k < D) {
-      a = ((i >> k) & 1) ? inv_h : -inv_h;
-#pragma unroll
-      for (int l = 0; l < D; ++l)
-        if (l != k) a *= f[l];
-    }
-    dN[k] = a;
-  }
 }
 
 // the seven entries of B_ij at this Gauss point (without the quadrature weight):

@@ -41,12 +41,12 @@ ElemArgs<T> elem_args(const pnp_ctx* c, const T* U, const T* V, const T* hs, con
   return A;
 }
 
+}  // namespace
+
 double now_ms() {
   using namespace std::chrono;
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
-
-}  // namespace
 
 int ctx_prepare_history(pnp_ctx* c) {
   if (c->prm.steady) {
@@ -1006,10 +1006,12 @@ int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st) {
   pnp_params& p = c->prm;
   // BDF2 needs U^{k-1} one full step behind U^k
   const bool bdf2 = !(c->step == 0 || p.bdf_order == 1 || c->history_split);
-  // advection at t^{k+1}: v~ = 2 v^k - v^{k-1} (Eq. averaging1)
-  CK(launch_axpbyz(n, 2.0, c->vel, -1.0, c->vel_prev, c->adv, s));
+  // advection at t^{k+1}: v~ = 2 v^k - v^{k-1} (Eq. averaging1); in a coupled step the
+  // NS block has set v^{k+1}
+  if (!c->coupled) CK(launch_axpbyz(n, 2.0, c->vel, -1.0, c->vel_prev, c->adv, s));
   int start = p.start_mode;
   if (c->history_split) start = PNP_START_PREVIOUS;  // extrapolation assumes equal spacing
+  if (c->start_given) start = -1;  // a repeated block iteration: U holds the start
   double r_extra = 0, r_learn = 0;
   if (start == PNP_START_LEARNED) {
     // the judge's residuals use this step's BDF formula
@@ -1049,10 +1051,85 @@ int ctx_time_step(pnp_ctx* c, pnp_solve_stats* st) {
     st->wall_ms = now_ms() - t0;
     return rc;
   }
-  CK(cudaMemcpyAsync(c->vel_prev, c->vel, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if (!c->coupled) CK(cudaMemcpyAsync(c->vel_prev, c->vel, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   c->step++;
   c->history_split = tot.substeps > 1;
+  st->wall_ms = now_ms() - t0;
+  return PNP_OK;
+}
+
+// One NS-PNP step by block iteration (Sec. 4.1): the linear NS block first (body force
+// from U^k, then from the latest U^{k+1}), then the PNP Newton solve with v^{k+1} as the
+// advection; a repeated iteration restores the PNP history and restarts Newton from the
+// latest U^{k+1}.
+int ctx_coupled_step(pnp_ctx* c, pnp_solve_stats* st, pnp_ns_stats* nst) {
+  const double t0 = now_ms();
+  std::memset(st, 0, sizeof(*st));
+  std::memset(nst, 0, sizeof(*nst));
+  RC(ctx_ns_alloc(c));
+  pnp_params& p = c->prm;
+  const int64_t n = c->n3();
+  cudaStream_t s = c->stream;
+  const bool bdf2 = !(c->step == 0 || p.bdf_order == 1);
+  const int nb = p.ns_blocks;
+  const int64_t step0 = c->step;
+  const bool split0 = c->history_split;
+  double* save = nb > 1 ? ctx_ns_history_save(c) : nullptr;  // [2][3N]: U^k, U^{k-1}
+  if (nb > 1) {
+    if (!save) PNP_FAIL(PNP_ERR_NOMEM, "coupled step: no memory for the PNP history");
+    CK(cudaMemcpyAsync(save, c->Uk, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(save + n, c->Ukm1, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  for (int b = 0; b < nb; ++b) {
+    if (b > 0) {
+      CK(cudaMemcpyAsync(c->Uk, save, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(c->Ukm1, save + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      c->step = step0;
+      c->history_split = split0;
+    }
+    set_bdf(p, bdf2);
+    pnp_ns_stats one;
+    int rc = ctx_ns_solve(c, b == 0 ? c->Uk : c->U, &one);
+    nst->status = rc;
+    nst->refinements += one.refinements;
+    nst->inner_its += one.inner_its;
+    nst->matvecs32 += one.matvecs32;
+    nst->matvecs64 += one.matvecs64;
+    nst->singular_blocks |= one.singular_blocks;
+    if (b == 0) nst->res0 = one.res0;
+    nst->res_final = one.res_final;
+    nst->wall_ms += one.wall_ms;
+    if (rc != PNP_OK) return rc;
+    RC(ctx_ns_velocity(c, c->adv));
+    pnp_solve_stats ps;
+    c->coupled = true;
+    c->start_given = b > 0;
+    rc = ctx_time_step(c, &ps);
+    c->coupled = false;
+    c->start_given = false;
+    const int start_used = b == 0 ? ps.start_used : st->start_used;
+    const double rse = b == 0 ? ps.res_start_extrapolated : st->res_start_extrapolated;
+    const double rsl = b == 0 ? ps.res_start_learned : st->res_start_learned;
+    const int nits = st->newton_its + ps.newton_its, kits = st->krylov_its + ps.krylov_its;
+    const int revs = st->residual_evals + ps.residual_evals, jvs = st->jv_evals + ps.jv_evals;
+    const int f64 = st->f64_fallbacks + ps.f64_fallbacks, mgf = st->mg_fallbacks + ps.mg_fallbacks;
+    *st = ps;
+    st->start_used = start_used;
+    st->res_start_extrapolated = rse;
+    st->res_start_learned = rsl;
+    st->newton_its = nits;
+    st->krylov_its = kits;
+    st->residual_evals = revs;
+    st->jv_evals = jvs;
+    st->f64_fallbacks = f64;
+    st->mg_fallbacks = mgf;
+    if (rc != PNP_OK) return rc;
+  }
+  // velocity history: v^{k-1} <- v^k <- v^{k+1}
+  CK(cudaMemcpyAsync(c->vel_prev, c->vel, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  RC(ctx_ns_velocity(c, c->vel));
+  CK(cudaStreamSynchronize(s));
   st->wall_ms = now_ms() - t0;
   return PNP_OK;
 }

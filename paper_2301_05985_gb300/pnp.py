@@ -25,6 +25,8 @@ PNP_F64, PNP_F32 = 0, 1
 PNP_DEVICE, PNP_HOST = 0, 1
 PNP_FIELD_U, PNP_FIELD_U_PREV, PNP_FIELD_U_PREV2 = 0, 1, 2
 PNP_FIELD_ADVECTION, PNP_FIELD_VELOCITY, PNP_FIELD_VELOCITY_PREV = 3, 4, 5
+PNP_FIELD_NS = 6
+PNP_NS_VX, PNP_NS_VY, PNP_NS_VZ, PNP_NS_P = 0, 1, 2, 3
 PNP_START_PREVIOUS, PNP_START_EXTRAPOLATE, PNP_START_LEARNED = 0, 1, 2
 
 
@@ -49,8 +51,21 @@ class pnp_params(C.Structure):
         ("gmres_cgs2", C.c_int32), ("dt_retries", C.c_int32),
         ("gmres_inner", C.c_int32), ("newton_ew_f64", C.c_int32),
         ("mg_levels", C.c_int32), ("mg_smooth", C.c_int32), ("mg_omega", C.c_double),
-        ("mg_coarse_its", C.c_int32), ("pad3_", C.c_int32),
+        ("mg_coarse_its", C.c_int32), ("ns_blocks", C.c_int32),
+        ("ns_Sc", C.c_double), ("ns_kappa", C.c_double), ("ns_rtol", C.c_double), ("ns_atol", C.c_double),
+        ("ns_inner_rtol", C.c_double), ("ns_max_it", C.c_int32), ("ns_pin", C.c_int32),
     ]
+
+
+class pnp_ns_stats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("refinements", C.c_int32), ("inner_its", C.c_int32),
+        ("matvecs32", C.c_int32), ("matvecs64", C.c_int32), ("singular_blocks", C.c_int32),
+        ("res0", C.c_double), ("res_final", C.c_double), ("wall_ms", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class pnp_solve_stats(C.Structure):
@@ -124,6 +139,12 @@ SIGNATURES = {
     "pnp_gmres": (C.c_int, [_vp, _vp, _vp, _vp, _d, C.c_int, _P(pnp_solve_stats)]),
     "pnp_newton_solve": (C.c_int, [_vp, _P(pnp_solve_stats)]),
     "pnp_time_step": (C.c_int, [_vp, _P(pnp_solve_stats)]),
+    "pnp_ns_set_bc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _d]),
+    "pnp_ns_residual": (C.c_int, [_vp, _vp, _vp]),
+    "pnp_ns_matvec": (C.c_int, [_vp, _vp, _vp, C.c_int]),
+    "pnp_ns_block_diag": (C.c_int, [_vp, _vp]),
+    "pnp_ns_solve": (C.c_int, [_vp, _P(pnp_ns_stats)]),
+    "pnp_coupled_step": (C.c_int, [_vp, _P(pnp_solve_stats), _P(pnp_ns_stats)]),
     "pnp_step_count": (C.c_int, [_vp, _P(_i64)]),
     "pnp_set_step_count": (C.c_int, [_vp, _i64]),
     "pnp_set_wait_limit": (C.c_int, [_vp, _i64]),
@@ -158,9 +179,10 @@ def mlp_forward_noalloc(params, X, Y, stream: int = 0):
 
 PNP_PROF_RESIDUAL, PNP_PROF_JV64, PNP_PROF_JV32, PNP_PROF_BLOCKDIAG = 0, 1, 2, 3
 PNP_PROF_ORTHO, PNP_PROF_PRECOND, PNP_PROF_MLP = 4, 5, 6
-PNP_PROF_ORTHO_UPDATE, PNP_PROF_INNER, PNP_PROF_MG, PNP_PROF_KINDS = 7, 8, 9, 10
+PNP_PROF_ORTHO_UPDATE, PNP_PROF_INNER, PNP_PROF_MG = 7, 8, 9
+PNP_PROF_NS, PNP_PROF_NS32, PNP_PROF_NS_KRYLOV, PNP_PROF_KINDS = 10, 11, 12, 13
 PROF_NAMES = ["residual64", "jv64", "jv32", "blockdiag", "ortho_dot", "precond", "mlp", "ortho_update", "inner_ortho",
-              "mg_coarse"]
+              "mg_coarse", "ns64", "ns32", "ns_krylov"]
 
 
 def lib():
@@ -348,7 +370,7 @@ class Context:
         check(lib().pnp_set_field(self.h, which, _ptr(x), where))
 
     def get_field(self, which: int, out=None, where: int | None = None):
-        ncomp = self.dim if which >= PNP_FIELD_ADVECTION else 3
+        ncomp = 4 if which == PNP_FIELD_NS else (self.dim if which >= PNP_FIELD_ADVECTION else 3)
         if out is None:
             out = np.zeros((self.n_nodes, ncomp))
         if where is None:
@@ -438,6 +460,43 @@ class Context:
 
     def reset_history(self):
         check(lib().pnp_reset_history(self.h))
+
+    # ---------------------------------------------------------------- Navier-Stokes
+    def ns_set_bc(self, face: int, slot: int, typ: int, value: float = 0.0):
+        check(lib().pnp_ns_set_bc(self.h, face, slot, typ, float(value)))
+
+    def ns_set_bcs(self, types, values):
+        """types / values: [2*dim, 4] per face and slot (v_x, v_y, v_z, p)."""
+        for f in range(len(types)):
+            for k in range(4):
+                self.ns_set_bc(f, k, int(types[f][k]), float(values[f][k]))
+
+    def ns_residual(self, X, F):
+        check(lib().pnp_ns_residual(self.h, _ptr(X), _ptr(F)))
+        return F
+
+    def ns_matvec(self, X, Y, precision: int = PNP_F64):
+        check(lib().pnp_ns_matvec(self.h, _ptr(X), _ptr(Y), precision))
+        return Y
+
+    def ns_block_diag(self, D):
+        check(lib().pnp_ns_block_diag(self.h, _ptr(D)))
+        return D
+
+    def ns_solve(self, raise_on_error=True) -> pnp_ns_stats:
+        st = pnp_ns_stats()
+        rc = lib().pnp_ns_solve(self.h, C.byref(st))
+        if raise_on_error:
+            check(rc)
+        return st
+
+    def coupled_step(self, raise_on_error=True):
+        """One NS-PNP step (block iteration): (PNP stats, NS stats)."""
+        st, nst = pnp_solve_stats(), pnp_ns_stats()
+        rc = lib().pnp_coupled_step(self.h, C.byref(st), C.byref(nst))
+        if raise_on_error:
+            check(rc)
+        return st, nst
 
     def set_wait_limit(self, polls: int):
         check(lib().pnp_set_wait_limit(self.h, int(polls)))

@@ -1,0 +1,227 @@
+"""GPU parity of the Navier-Stokes block (Def. 3 momentum and solenoidality rows with the
+closure of Sec. 3.1) and of the NS-PNP block iteration (Sec. 4.1) against the FP64 oracle:
+residual and matrix action (FP64 and FP32) on octrees with hanging nodes and periodic
+sides, the 4x4 nodal diagonal blocks against the oracle's assembled matrix, the linear
+solve, and coupled time steps (one and two block iterations)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2301_05985_gb300 import workloads as W
+
+from gpu_common import lib, perm_to_oracle, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 5e-5
+
+
+class NsPair:
+    """Library context and oracle mesh of the same octants, NS parameters on both sides."""
+
+    def __init__(self, oc, kw, ns_kw, pnp_bcs=None, wall_faces=None, lid=0.0):
+        self.pnp = lib()
+        self.torch = torch_cuda()
+        self.oc = oc
+        self.dim = oc.dim
+        self.mesh = self.pnp.Mesh(oc)
+        self.om = O.OracleMesh(oc)
+        self.perm = perm_to_oracle(self.mesh.ijk, self.om.ijk, oc.max_level)
+        allkw = dict(kw)
+        allkw.update(ns_kw)
+        self.ctx = self.pnp.Context(self.mesh, self.pnp.default_params(**allkw), 0)
+        self.pnp_bcs = pnp_bcs
+        if pnp_bcs is not None:
+            self.ctx.set_bcs(pnp_bcs)
+        periodic = getattr(oc, "periodic", 0)
+        walls = [f for f in range(2 * self.dim) if not (periodic >> (f // 2)) & 1] if wall_faces is None else wall_faces
+        bt, bv = O.no_slip_bcs(self.dim, walls)
+        if lid and (2 * self.dim - 1) in walls:
+            bv[2 * self.dim - 1, 0] = lid
+        self.bt, self.bv = bt, bv
+        self.ctx.ns_set_bcs(bt, bv)
+        self.kw, self.ns_kw = allkw, ns_kw
+
+    def ns_params(self, beta=None, dt=None):
+        kw = self.kw
+        return O.NsParams(Sc=self.ns_kw.get("ns_Sc", 1.0), kappa=self.ns_kw.get("ns_kappa", 0.5), eps=kw["eps"],
+                          dt=kw.get("dt", 1.0) if dt is None else dt,
+                          beta=(kw.get("beta0", 1.0), kw.get("beta1", -1.0), kw.get("beta2", 0.0)) if beta is None else beta,
+                          C_I=kw.get("C_I", 6.0), steady=bool(kw.get("steady", 0)), pin=bool(self.ns_kw.get("ns_pin", 1)),
+                          bc_type=self.bt, bc_val=self.bv)
+
+    def to_ora(self, x):
+        out = np.zeros_like(x)
+        out[self.perm] = x
+        return out
+
+    def to_lib(self, x):
+        return x[self.perm]
+
+    def dev(self, x):
+        return self.torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+    def set_history(self, Vk, Vkm1, U):
+        d = self.dim
+        self.Vk, self.Vkm1, self.U = Vk, Vkm1, U
+        self.ctx.set_field(self.pnp.PNP_FIELD_VELOCITY, np.ascontiguousarray(Vk[:, :d]))
+        self.ctx.set_field(self.pnp.PNP_FIELD_VELOCITY_PREV, np.ascontiguousarray(Vkm1[:, :d]))
+        self.ctx.set_field(self.pnp.PNP_FIELD_U, U)
+
+    def oracle_apply(self, X, with_data):
+        o = self.to_ora
+        adv = 2.0 * self.Vk - self.Vkm1
+        return self.to_lib(self.om.ns_apply(self.ns_params(), o(X), o(adv), o(self.Vk), o(self.Vkm1), o(self.U),
+                                            with_data=with_data))
+
+
+def _vel(n, dim, rng, amp):
+    v = np.zeros((n, 3))
+    v[:, :dim] = amp * rng.standard_normal((n, dim))
+    return v
+
+
+def _slot_err(x, ref):
+    out = []
+    for f in range(4):
+        s = np.abs(ref[:, f]).max()
+        out.append(np.abs(x[:, f] - ref[:, f]).max() / s if s > 0 else np.abs(x[:, f]).max())
+    return np.array(out)
+
+
+CASES = [
+    ("2d_octree", W.random_balanced_octants(2, 2, 5, 0.3, 11), dict(eps=0.1, dt=0.01, beta0=1.5, beta1=-2.0, beta2=0.5),
+     dict(ns_Sc=1.0, ns_kappa=0.5)),
+    ("3d_octree", W.random_balanced_octants(3, 1, 4, 0.3, 12), dict(eps=0.2, dt=5e-3, beta0=1.0, beta1=-1.0, beta2=0.0),
+     dict(ns_Sc=2.0, ns_kappa=0.3)),
+    ("3d_octree_periodic_x", W.random_balanced_octants(3, 2, 4, 0.3, 12, periodic=1),
+     dict(eps=0.15, dt=1e-2, beta0=1.5, beta1=-2.0, beta2=0.5), dict(ns_Sc=0.5, ns_kappa=0.5)),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_ns_residual_and_matrix_action_match_oracle(case):
+    _, oc, kw, ns_kw = case
+    P = NsPair(oc, kw, ns_kw, lid=0.3)
+    n, d = P.mesh.n_nodes, oc.dim
+    rng = np.random.default_rng(4)
+    P.set_history(_vel(n, d, rng, 0.5), _vel(n, d, rng, 0.5), W.random_state(P.mesh.ijk, oc.max_level, 1))
+    X = rng.standard_normal((n, 4))
+    if d == 2:
+        X[:, 2] = 0.0
+    Xd = P.dev(X)
+    F = P.torch.zeros_like(Xd)
+    P.ctx.ns_residual(Xd, F)
+    ref = P.oracle_apply(X, True)
+    Fh = F.cpu().numpy()
+    assert np.linalg.norm(Fh - ref) / np.linalg.norm(ref) <= TOL64
+    assert np.all(_slot_err(Fh, ref)[[0, 1, 3] if d == 2 else [0, 1, 2, 3]] <= 10 * TOL64)
+    # matrix action, FP64 and FP32
+    Y = P.torch.zeros_like(Xd)
+    P.ctx.ns_matvec(Xd, Y, P.pnp.PNP_F64)
+    refA = P.oracle_apply(X, False)
+    Yh = Y.cpu().numpy()
+    assert np.linalg.norm(Yh - refA) / np.linalg.norm(refA) <= TOL64
+    X32 = P.dev(X.astype(np.float32))
+    Y32 = P.torch.zeros_like(X32)
+    P.ctx.ns_matvec(X32, Y32, P.pnp.PNP_F32)
+    e32 = _slot_err(Y32.cpu().numpy().astype(np.float64), refA)
+    assert np.all(e32[[0, 1, 3] if d == 2 else [0, 1, 2, 3]] <= TOL32), e32
+    # affine structure on the GPU: F(X) - F(0) = A X
+    F0 = P.torch.zeros_like(Xd)
+    P.ctx.ns_residual(P.torch.zeros_like(Xd), F0)
+    diff = (F - F0).cpu().numpy()
+    assert np.linalg.norm(diff - Yh) / np.linalg.norm(Yh) <= 1e-11
+
+
+@pytest.mark.parametrize("dim,level", [(2, 4), (3, 3)])
+def test_ns_diagonal_blocks_match_oracle_matrix(dim, level):
+    oc = W.uniform_octants(dim, level)
+    kw = dict(eps=0.1, dt=0.01, beta0=1.5, beta1=-2.0, beta2=0.5)
+    P = NsPair(oc, kw, dict(ns_Sc=1.5, ns_kappa=0.5))
+    n = P.mesh.n_nodes
+    rng = np.random.default_rng(7)
+    P.set_history(_vel(n, dim, rng, 0.7), _vel(n, dim, rng, 0.7), np.ones((n, 3)))
+    D = P.torch.zeros((n, 16), dtype=P.torch.float64, device="cuda")
+    P.ctx.ns_block_diag(D)
+    D = D.cpu().numpy().reshape(n, 4, 4)
+    adv = 2.0 * P.Vk - P.Vkm1
+    A = P.om.ns_matrix(P.ns_params(), P.to_ora(adv)).tocsr()
+    kind, _ = P.om.ns_bc_rows(P.ns_params())
+    kind = P.to_lib(kind)
+    po = P.perm
+    checked = 0
+    for f in range(4):
+        for g in range(4):
+            if dim == 2 and (f == 2 or g == 2):
+                continue
+            ref = np.asarray(A[4 * po + f, 4 * po + g]).reshape(-1)
+            rows = kind[:, f] == 0
+            np.testing.assert_allclose(D[rows, f, g], ref[rows], rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+            checked += rows.sum()
+    assert checked > 0
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_ns_solve_matches_oracle(case):
+    _, oc, kw, ns_kw = case
+    ns_kw = dict(ns_kw, ns_rtol=1e-13, ns_atol=0.0)
+    P = NsPair(oc, kw, ns_kw, lid=0.3)
+    n, d = P.mesh.n_nodes, oc.dim
+    rng = np.random.default_rng(5)
+    U = W.random_state(P.mesh.ijk, oc.max_level, 2)
+    P.set_history(_vel(n, d, rng, 0.3), _vel(n, d, rng, 0.3), U)
+    st = P.ctx.ns_solve()
+    assert st.status == 0 and st.refinements >= 1 and st.inner_its > 0 and st.singular_blocks == 0
+    X = P.ctx.get_field(P.pnp.PNP_FIELD_NS)
+    o = P.to_ora
+    ref = P.to_lib(P.om.ns_solve(P.ns_params(), o(2.0 * P.Vk - P.Vkm1), o(P.Vk), o(P.Vkm1), o(U)))
+    e = _slot_err(X, ref)
+    assert np.all(e[[0, 1, 3] if d == 2 else [0, 1, 2, 3]] <= 1e-9), e
+    # the residual the solve reports is the one of the returned field
+    F = P.torch.zeros((n, 4), dtype=P.torch.float64, device="cuda")
+    P.ctx.ns_residual(P.dev(X), F)
+    assert abs(np.linalg.norm(F.cpu().numpy()) - st.res_final) <= 1e-6 * st.res0
+
+
+@pytest.mark.parametrize("blocks", [1, 2])
+def test_coupled_steps_match_oracle_block_iteration(blocks):
+    """Two NS-PNP steps (BDF1 then BDF2) on a 2D octree with a membrane double layer and
+    no-slip walls: the body force of the charged layer drives the flow, the flow advects
+    the ions."""
+    oc = W.random_balanced_octants(2, 2, 5, 0.3, 12)
+    V, eps, dt = 5.0, 0.05, 1e-2
+    kw = dict(eps=eps, dt=dt, newton_rtol=1e-12, gmres_rtol=1e-13, gmres_restart=60, gmres_max_it=20000,
+              start_mode=0, newton_max_it=40, precision=0)
+    ns_kw = dict(ns_Sc=1.0, ns_kappa=0.5, ns_rtol=1e-13, ns_atol=0.0, ns_blocks=blocks)
+    bcs = W.membrane_bcs(2, V, 2.0)
+    P = NsPair(oc, kw, ns_kw, pnp_bcs=bcs)
+    n = P.mesh.n_nodes
+    U0 = W.noisy_state(P.mesh.ijk, oc.max_level, seed=3, amp=5e-2, phi_bottom=0.0, phi_top=V)
+    P.ctx.set_field(P.pnp.PNP_FIELD_U, U0)
+    P.ctx.make_consistent()
+    P.ctx.reset_history()
+    U0 = P.ctx.get_field(P.pnp.PNP_FIELD_U)
+    op = O.Params(eps=eps, dt=dt, bc_type=bcs.types, bc_val=bcs.values)
+    o = P.to_ora
+    Uk, Ukm1 = o(U0), o(U0)
+    Vk, Vkm1 = np.zeros((n, 3)), np.zeros((n, 3))
+    for k in range(2):
+        beta = O.bdf_coefficients(k)
+        op.beta = beta
+        nsp = P.ns_params(beta=beta)
+        ref = O.coupled_step(P.om, op, nsp, Uk, Ukm1, Vk, Vkm1, n_block=blocks, rtol=1e-12)
+        st, nst = P.ctx.coupled_step()
+        assert st.status == 0 and nst.status == 0
+        U = P.ctx.get_field(P.pnp.PNP_FIELD_U)
+        X = P.ctx.get_field(P.pnp.PNP_FIELD_NS)
+        eU = np.abs(U - P.to_lib(ref.U)).max(axis=0) / np.abs(ref.U).max(axis=0)
+        eX = _slot_err(X, P.to_lib(ref.X))
+        assert np.all(eU <= 1e-8), (k, eU)
+        assert np.all(eX[[0, 1, 3]] <= 1e-7), (k, eX)
+        assert np.abs(ref.X[:, :2]).max() > 1e-6   # the body force moved the fluid
+        vel = P.ctx.get_field(P.pnp.PNP_FIELD_VELOCITY)
+        np.testing.assert_allclose(vel, X[:, :2], rtol=0, atol=0)
+        Ukm1, Uk = Uk, ref.U
+        Vkm1, Vk = Vk, ref.X[:, :3].copy()
