@@ -143,10 +143,17 @@ typedef struct pnp_params {
                             (1e-8 and 1e-10, the tolerances of App. A) */
   double ns_atol;
   double ns_inner_rtol;  /* relative residual reduction of the FP32 BiCGStab of each FP64
-                            refinement step (1e-4) */
+                            refinement step (1e-3) */
   int32_t ns_max_it;     /* total FP32 BiCGStab iterations per NS solve (4000) */
   int32_t ns_pin;        /* 1: the pressure of the node at the origin is pinned to 0 unless a
                             pressure Dirichlet face holds it (1) */
+  int32_t ns_mg_levels;  /* 0: BiCGStab preconditioned by the inverted 4x4 nodal blocks; L > 0:
+                            by one FP32 V-cycle of geometric multigrid over up to L coarser
+                            octrees (the hierarchy of mg_levels, shared with it: mg_levels wins
+                            when both are set), damped block-Jacobi sweeps (mg_smooth, mg_omega,
+                            mg_coarse_its), rediscretised NS operators at the injected v~.
+                            Non-periodic meshes (0) */
+  int32_t ns_inner_max_it; /* BiCGStab iterations per FP64 refinement step (200) */
 } pnp_params;
 
 typedef struct pnp_solve_stats {
@@ -181,6 +188,10 @@ typedef struct pnp_ns_stats {
   int32_t matvecs32;     /* FP32 matrix applications (2 per BiCGStab iteration) */
   int32_t matvecs64;     /* FP64 residual evaluations */
   int32_t singular_blocks; /* 1 when a 4x4 diagonal block was singular (replaced by I) */
+  int32_t floor_stop;    /* 1 when the solve stopped at the rounding floor of the FP64 residual
+                            (three refinement steps without progress, ||F|| <= 1e-6 ||F(X^0)||)
+                            above the requested tolerance */
+  int32_t pad_;
   double res0;           /* ||F(X^0)||_2 */
   double res_final;      /* ||F(X)||_2 */
   double wall_ms;        /* host wall time of the call */
@@ -412,10 +423,13 @@ int pnp_ns_matvec(pnp_ctx* c, const void* X, void* Y, int precision);
  * of pnp_ns_solve inverts them (identity rows on constrained rows). */
 int pnp_ns_block_diag(pnp_ctx* c, double* D);
 /* Solve the linear NS system for PNP_FIELD_NS in place, starting from its value: FP64
- * defect correction around FP32 BiCGStab (App. A solves this block with BiCGStab),
- * right-preconditioned by the inverted diagonal blocks, until ||F(X)|| <= max(ns_rtol
- * ||F(X^0)||, ns_atol).  PNP_ERR_KRYLOV_MAXIT after ns_max_it BiCGStab iterations or 40
- * refinement steps; PNP_ERR_NAN on a non-finite norm.  Uses the context's beta0..2. */
+ * defect correction around FP32 BiCGStab (App. A solves this block with BiCGStab) of at
+ * most ns_inner_max_it iterations each, right-preconditioned by the inverted diagonal
+ * blocks or (ns_mg_levels) a multigrid V-cycle, until ||F(X)|| <= max(ns_rtol ||F(X^0)||,
+ * ns_atol).  PNP_ERR_KRYLOV_MAXIT after ns_max_it BiCGStab iterations, 60 refinement
+ * steps or three refinement steps in a row without progress above 1e-6 ||F(X^0)|| (at or
+ * below it the solve ends as converged with st->floor_stop = 1); PNP_ERR_NAN on a
+ * non-finite norm.  Uses the context's beta0..2. */
 int pnp_ns_solve(pnp_ctx* c, pnp_ns_stats* st);
 /* One NS-PNP time step by block iteration (Sec. 4.1): ns_blocks times, the NS system
  * (body force from U^k in the first pass, then from the latest U^{k+1}) and then the PNP

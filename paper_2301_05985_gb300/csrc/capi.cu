@@ -76,9 +76,11 @@ void pnp_params_default(pnp_params* p) {
   p->ns_kappa = 0.5;
   p->ns_rtol = 1e-8;
   p->ns_atol = 1e-10;
-  p->ns_inner_rtol = 1e-4;
+  p->ns_inner_rtol = 1e-3;
   p->ns_max_it = 4000;
   p->ns_pin = 1;
+  p->ns_mg_levels = 0;
+  p->ns_inner_max_it = 200;
   p->mg_levels = 0;
   p->mg_smooth = 2;
   p->mg_omega = 0.5;
@@ -235,7 +237,8 @@ static int check_params(const pnp_params* p) {
   if (p->dt_retries < 0 || p->dt_retries > 16) PNP_FAIL(PNP_ERR_ARG, "params: dt_retries in 0..16");
   if (p->ns_blocks < 1 || p->ns_blocks > 16 || !(p->ns_Sc > 0) || !std::isfinite(p->ns_Sc) ||
       !std::isfinite(p->ns_kappa) || !(p->ns_rtol >= 0) || !(p->ns_atol >= 0) || !(p->ns_inner_rtol > 0) ||
-      !(p->ns_inner_rtol < 1) || p->ns_max_it < 1 || (p->ns_pin != 0 && p->ns_pin != 1))
+      !(p->ns_inner_rtol < 1) || p->ns_max_it < 1 || (p->ns_pin != 0 && p->ns_pin != 1) || p->ns_mg_levels < 0 ||
+      p->ns_mg_levels > 16 || p->ns_inner_max_it < 1)
     PNP_FAIL(PNP_ERR_ARG, "params: Navier-Stokes settings out of range");
   return PNP_OK;
 }

@@ -3,6 +3,21 @@
 
 #include "kernels.h"
 
+// One level of the multigrid hierarchy (mg.cu): the level's context and the transfers
+// between the next finer level (rows Nf) and this level (rows Nc), on the device.
+struct MgLevel {
+  pnp_ctx* sub = nullptr;             // the level's context (null for level 0: the owner)
+  // transfer between the next finer level (rows Nf) and this level (rows Nc)
+  int64_t* p_ptr = nullptr;
+  int32_t* p_col = nullptr;
+  float* p_w = nullptr;
+  int64_t* r_ptr = nullptr;
+  int32_t* r_col = nullptr;
+  float* r_w = nullptr;
+  int32_t* inject = nullptr;
+  float *b = nullptr, *x = nullptr, *Ax = nullptr, *Dinv32 = nullptr;
+};
+
 struct pnp_ctx {
   int dim = 0, L = 0;
   int64_t n_elem = 0, n_nodes = 0, n_hanging = 0;

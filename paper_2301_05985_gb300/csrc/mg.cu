@@ -107,19 +107,6 @@ __global__ void k_mg_inject(int64_t Nc, int nf, const int32_t* __restrict__ map,
 
 }  // namespace
 
-struct MgLevel {
-  pnp_ctx* sub = nullptr;             // the level's context (null for level 0: the owner)
-  // transfer between the next finer level (rows Nf) and this level (rows Nc)
-  int64_t* p_ptr = nullptr;
-  int32_t* p_col = nullptr;
-  float* p_w = nullptr;
-  int64_t* r_ptr = nullptr;
-  int32_t* r_col = nullptr;
-  float* r_w = nullptr;
-  int32_t* inject = nullptr;
-  float *b = nullptr, *x = nullptr, *Ax = nullptr, *Dinv32 = nullptr;
-};
-
 static void mg_free_level(MgLevel& L) {
   void* p[] = {L.p_ptr, L.p_col, L.p_w, L.r_ptr, L.r_col, L.r_w, L.inject, L.b, L.x, L.Ax, L.Dinv32};
   for (void* q : p)

@@ -49,7 +49,7 @@ namespace {
 
 constexpr int kNsThreads = 256;
 constexpr int kCheck = 8;          // BiCGStab iterations between host reads of ||r||
-constexpr int kMaxRefine = 40;     // FP64 refinement steps per solve
+constexpr int kMaxRefine = 60;     // FP64 refinement steps per solve
 
 template <typename T>
 struct NsArgs {
@@ -583,6 +583,103 @@ __global__ void k_ns_velocity(int64_t N, const double* __restrict__ X, double* _
   for (int f = 0; f < 3; ++f) v3[3 * i + f] = X[4 * i + f];
 }
 
+// ------------------------------------------------------------------ multigrid pieces
+// Dirichlet / pin / inactive row of slot f at a free node (hanging nodes: faces bit 7)
+__device__ __forceinline__ bool ns_dir(const NsBc& bc, uint8_t fm, int64_t i, int f) {
+  if (f == 2 && bc.dim == 2) return true;
+  const bool d = (fm & bc.dir[f] & 0x3F) != 0;
+  return d || (f == 3 && i == bc.pin);
+}
+
+// x = omega D^-1 b (first sweep) or x += omega D^-1 (b - Ax), 4x4 blocks
+__global__ void k_ns_smooth(int64_t N, const float* __restrict__ Dinv, const float4* __restrict__ b,
+                            const float4* __restrict__ Ax, float4* __restrict__ x, float om, int first) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float4 r = b[i];
+  if (!first) {
+    const float4 a = Ax[i];
+    r = make_float4(r.x - a.x, r.y - a.y, r.z - a.z, r.w - a.w);
+  }
+  const float4* M = reinterpret_cast<const float4*>(Dinv) + 4 * i;
+  const float4 m0 = M[0], m1 = M[1], m2 = M[2], m3 = M[3];
+  const float4 d = make_float4(om * (m0.x * r.x + m0.y * r.y + m0.z * r.z + m0.w * r.w),
+                               om * (m1.x * r.x + m1.y * r.y + m1.z * r.z + m1.w * r.w),
+                               om * (m2.x * r.x + m2.y * r.y + m2.z * r.z + m2.w * r.w),
+                               om * (m3.x * r.x + m3.y * r.y + m3.z * r.z + m3.w * r.w));
+  if (first) {
+    x[i] = d;
+  } else {
+    const float4 o = x[i];
+    x[i] = make_float4(o.x + d.x, o.y + d.y, o.z + d.z, o.w + d.w);
+  }
+}
+
+// out[j] = sum_q w_q (b - Ax)[col_q] over the fine rows that are weak-form equations
+// (Dirichlet, pin, inactive and hanging rows carry no element contributions); coarse
+// constrained rows are zero
+__global__ void k_ns_restrict(int64_t Nc, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                              const float* __restrict__ w, const float4* __restrict__ b, const float4* __restrict__ Ax,
+                              const uint8_t* __restrict__ faces_f, NsBc bcf, const uint8_t* __restrict__ faces_c,
+                              NsBc bcc, float4* __restrict__ out) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= Nc) return;
+  float s[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t q = ptr[j]; q < ptr[j + 1]; ++q) {
+    const int64_t i = col[q];
+    const uint8_t ff = faces_f[i];
+    if (ff & 0x80) continue;
+    const float wq = w[q];
+    const float4 bi = b[i], ai = Ax[i];
+    const float r[4] = {bi.x - ai.x, bi.y - ai.y, bi.z - ai.z, bi.w - ai.w};
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (!ns_dir(bcf, ff, i, f)) s[f] = fmaf(wq, r[f], s[f]);
+  }
+  const uint8_t fc = faces_c[j];
+  float o[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) o[f] = ((fc & 0x80) || ns_dir(bcc, fc, j, f)) ? 0.f : s[f];
+  out[j] = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+// x[i] += sum_q w_q xc[col_q] on the fine rows that are not constrained by a value
+__global__ void k_ns_prolong_add(int64_t Nf, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                 const float* __restrict__ w, const float4* __restrict__ xc,
+                                 const uint8_t* __restrict__ faces_f, NsBc bcf, float4* __restrict__ x) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Nf) return;
+  float s[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+    const float4 a = xc[col[q]];
+    const float wq = w[q];
+    s[0] = fmaf(wq, a.x, s[0]); s[1] = fmaf(wq, a.y, s[1]); s[2] = fmaf(wq, a.z, s[2]); s[3] = fmaf(wq, a.w, s[3]);
+  }
+  const uint8_t ff = faces_f[i];
+  float4 o = x[i];
+  const bool h = (ff & 0x80) != 0;
+  if (h || !ns_dir(bcf, ff, i, 0)) o.x += s[0];
+  if (h || !ns_dir(bcf, ff, i, 1)) o.y += s[1];
+  if (h || !ns_dir(bcf, ff, i, 2)) o.z += s[2];
+  if (h || !ns_dir(bcf, ff, i, 3)) o.w += s[3];
+  x[i] = o;
+}
+
+// coarse v~ (FP64 [Nc][4] and its FP32 copy) at the coarse nodes' points
+__global__ void k_ns_inject_adv(int64_t Nc, const int32_t* __restrict__ map, const double* __restrict__ fine,
+                                double* __restrict__ coarse, float4* __restrict__ coarse32) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= Nc) return;
+  const int64_t i = map[j];
+  double a[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    a[f] = fine[4 * i + f];
+    coarse[4 * j + f] = a[f];
+  }
+  coarse32[j] = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
+}
+
 inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
 inline int gsb(int64_t n) { return (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (n + 255) / 256)); }
 
@@ -597,6 +694,7 @@ struct NsState {
          *x = nullptr;
   double *part = nullptr, *sc = nullptr, *hsc = nullptr;
   double* usave = nullptr;  // [2][3N] PNP history of repeated block iterations
+  float4* mgAx = nullptr;   // [N] operator scratch of the finest multigrid level
   int64_t pin = -1;
   std::vector<void*> alloc;
 };
@@ -825,6 +923,110 @@ int ctx_ns_blocks_row_fix(pnp_ctx* c, double* Dg, float* Dinv) {
   return PNP_OK;
 }
 
+// ------------------------------------------------------------------ multigrid
+static int ns_mg_levels(const pnp_ctx* c) { return c->prm.mg_levels > 0 ? c->prm.mg_levels : c->prm.ns_mg_levels; }
+
+// Per solve: every coarse level's parameters, boundary table, injected v~ and inverted
+// diagonal blocks (level 0 uses the solve's own blocks).
+static int ctx_ns_mg_prepare(pnp_ctx* c) {
+  RC(ctx_mg_setup(c, ns_mg_levels(c)));
+  NsState* S = c->ns;
+  if (!S->mgAx) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, sizeof(float4) * c->n_nodes) != cudaSuccess) {
+      cudaGetLastError();
+      PNP_FAIL(PNP_ERR_NOMEM, "ns multigrid: device allocation failed");
+    }
+    S->mgAx = (float4*)q;
+    S->alloc.push_back(q);
+  }
+  auto& lv = *c->mg;
+  pnp_ctx* fine = c;
+  for (size_t l = 1; l < lv.size(); ++l) {
+    pnp_ctx* sc = lv[l].sub;
+    pnp_params& q = sc->prm;
+    const pnp_params& p = c->prm;
+    q.eps = p.eps;
+    q.dt = p.dt;
+    q.C_I = p.C_I;
+    q.beta0 = p.beta0;
+    q.beta1 = p.beta1;
+    q.beta2 = p.beta2;
+    q.steady = p.steady;
+    q.ns_Sc = p.ns_Sc;
+    q.ns_kappa = p.ns_kappa;
+    q.ns_pin = p.ns_pin;
+    std::memcpy(sc->ns_bc_type, c->ns_bc_type, sizeof(c->ns_bc_type));
+    std::memcpy(sc->ns_bc_val, c->ns_bc_val, sizeof(c->ns_bc_val));
+    RC(ctx_ns_alloc(sc));
+    const int64_t Nc = sc->n_nodes;
+    k_ns_inject_adv<<<nblk(Nc, 256), 256, 0, c->stream>>>(Nc, lv[l].inject, fine->ns->adv, sc->ns->adv,
+                                                          sc->ns->adv32);
+    note_launch();
+    CK(cudaGetLastError());
+    RC(ctx_ns_block_diag(sc, sc->ns->Dg));
+    RC(ctx_ns_blocks_row_fix(sc, sc->ns->Dg, sc->ns->Dinv));
+    fine = sc;
+  }
+  return PNP_OK;
+}
+
+// x = one V-cycle on level l applied to b (level 0: the caller's vectors; coarser levels:
+// their contexts' r and x)
+static int ns_mg_cycle(pnp_ctx* c, size_t l, const float4* b, float4* x) {
+  auto& lv = *c->mg;
+  pnp_ctx* lc = l == 0 ? c : lv[l].sub;
+  NsState* LS = lc->ns;
+  float4* Ax = l == 0 ? c->ns->mgAx : LS->t;
+  const int64_t N = lc->n_nodes;
+  cudaStream_t s = c->stream;
+  const float om = (float)c->prm.mg_omega;
+  const NsBc bc = ns_bc(lc);
+  auto smooth = [&](bool first) -> int {
+    if (!first) RC(ctx_ns_apply32(lc, x, Ax));
+    ProfScope ps(c, l == 0 ? PNP_PROF_NS_KRYLOV : -1, 112.0 * N, 36.0 * N);
+    k_ns_smooth<<<nblk(N, 256), 256, 0, s>>>(N, LS->Dinv, b, Ax, x, om, first ? 1 : 0);
+    note_launch();
+    CK(cudaGetLastError());
+    return PNP_OK;
+  };
+  if (l + 1 == lv.size()) {
+    const int sweeps = std::max(1, c->prm.mg_coarse_its);
+    for (int k = 0; k < sweeps; ++k) RC(smooth(k == 0));
+    return PNP_OK;
+  }
+  const int nu = std::max(1, c->prm.mg_smooth);
+  for (int k = 0; k < nu; ++k) RC(smooth(k == 0));
+  RC(ctx_ns_apply32(lc, x, Ax));
+  pnp_ctx* cc = lv[l + 1].sub;
+  const MgLevel& C = lv[l + 1];
+  {
+    ProfScope ps(c, l == 0 ? PNP_PROF_MG : -1, 0.0);
+    k_ns_restrict<<<nblk(cc->n_nodes, 256), 256, 0, s>>>(cc->n_nodes, C.r_ptr, C.r_col, C.r_w, b, Ax, lc->d_faces, bc,
+                                                         cc->d_faces, ns_bc(cc), cc->ns->r);
+    note_launch();
+    CK(cudaGetLastError());
+    RC(ns_mg_cycle(c, l + 1, cc->ns->r, cc->ns->x));
+    k_ns_prolong_add<<<nblk(N, 256), 256, 0, s>>>(N, C.p_ptr, C.p_col, C.p_w, cc->ns->x, lc->d_faces, bc, x);
+    note_launch();
+    CK(cudaGetLastError());
+  }
+  for (int k = 0; k < nu; ++k) RC(smooth(false));
+  return PNP_OK;
+}
+
+// out = M^-1 in: the inverted blocks, or one V-cycle
+static int ns_precond(pnp_ctx* c, const float4* in, float4* out) {
+  NsState* S = c->ns;
+  const int64_t N = c->n_nodes;
+  if (ns_mg_levels(c) > 0 && c->mg && c->mg->size() > 1) return ns_mg_cycle(c, 0, in, out);
+  ProfScope ps(c, PNP_PROF_NS_KRYLOV, 96.0 * N, 32.0 * N);
+  k_ns_block_apply<<<nblk(N, 256), 256, 0, c->stream>>>(N, S->Dinv, in, out);
+  note_launch();
+  CK(cudaGetLastError());
+  return PNP_OK;
+}
+
 // FP32 BiCGStab on A d = r (r = S->r on entry, d = S->x), right preconditioned by the
 // inverted blocks, to ||r|| <= rtol ||r_0|| or `max_it` iterations; returns the iterations
 static int ns_bicgstab32(pnp_ctx* c, double rtol, int max_it, int* its_out) {
@@ -855,24 +1057,24 @@ static int ns_bicgstab32(pnp_ctx* c, double rtol, int max_it, int* its_out) {
     const int batch = std::min(kCheck, max_it - its);
     for (int b = 0; b < batch; ++b) {
       {
-        // <r^, r>, p = r + beta (p - omega v), p^ = M^-1 p
-        ProfScope ps(c, PNP_PROF_NS_KRYLOV, 192.0 * N, 24.0 * N);
+        // <r^, r>, p = r + beta (p - omega v)
+        ProfScope ps(c, PNP_PROF_NS_KRYLOV, 96.0 * N, 16.0 * N);
         k_dot4_part<<<G, kRedThreads, 0, s>>>(N, S->rh, S->r, nullptr, nullptr, S->part);
         k_bicg_scalar<<<1, kRedThreads, 0, s>>>(0, G, S->part, S->sc);
         k_bicg_p<<<G, 256, 0, s>>>(N, S->r, S->v, S->p, S->sc);
-        k_ns_block_apply<<<nblk(N, 256), 256, 0, s>>>(N, S->Dinv, S->p, S->ph);
-        note_launches(4);
+        note_launches(3);
       }
+      RC(ns_precond(c, S->p, S->ph));  // p^ = M^-1 p
       RC(ctx_ns_apply32(c, S->ph, S->v));
       {
-        // alpha = rho / <r^, v>, s = r - alpha v, s^ = M^-1 s
-        ProfScope ps(c, PNP_PROF_NS_KRYLOV, 176.0 * N, 48.0 * N);
+        // alpha = rho / <r^, v>, s = r - alpha v
+        ProfScope ps(c, PNP_PROF_NS_KRYLOV, 80.0 * N, 16.0 * N);
         k_dot4_part<<<G, kRedThreads, 0, s>>>(N, S->rh, S->v, nullptr, nullptr, S->part);
         k_bicg_scalar<<<1, kRedThreads, 0, s>>>(1, G, S->part, S->sc);
         k_bicg_s<<<G, 256, 0, s>>>(N, S->r, S->v, S->sc);
-        k_ns_block_apply<<<nblk(N, 256), 256, 0, s>>>(N, S->Dinv, S->r, S->sh);
-        note_launches(4);
+        note_launches(3);
       }
+      RC(ns_precond(c, S->r, S->sh));  // s^ = M^-1 s
       RC(ctx_ns_apply32(c, S->sh, S->t));
       {
         // omega = <t, s> / <t, t>, x += alpha p^ + omega s^, r = s - omega t, <r, r>
@@ -907,6 +1109,7 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
   cudaStream_t s = c->stream;
   RC(ctx_ns_block_diag(c, S->Dg));
   RC(ctx_ns_blocks_row_fix(c, S->Dg, S->Dinv));
+  if (ns_mg_levels(c) > 0) RC(ctx_ns_mg_prepare(c));
   RC(ctx_ns_apply64(c, S->X, Ubody, S->F, true));
   st->matvecs64 = 1;
   double f;
@@ -926,7 +1129,7 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
     k_ns_to_f32<<<nblk(N, 256), 256, 0, s>>>(N, S->F, -1.0 / f, S->r);
     note_launch();
     int its = 0;
-    RC(ns_bicgstab32(c, p.ns_inner_rtol, p.ns_max_it - inner_total, &its));
+    RC(ns_bicgstab32(c, p.ns_inner_rtol, std::min(p.ns_inner_max_it, p.ns_max_it - inner_total), &its));
     inner_total += its;
     k_ns_add_f32<<<nblk(N, 256), 256, 0, s>>>(N, S->x, f, S->X);
     note_launch();
@@ -935,10 +1138,15 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
     RC(ctx_norm4(c, S->F, &f));
     if (!std::isfinite(f)) PNP_FAIL(PNP_ERR_NAN, "ns: residual is not finite");
     ++ref;
-    // a refinement step that does not reduce ||F|| (BiCGStab broke down at once) three
-    // times in a row ends the solve
+    // three refinement steps in a row without reducing ||F|| end the solve: at the
+    // rounding floor of the FP64 residual (||F|| <= 1e-6 ||F(X^0)||) as converged
+    // (floor_stop), above it as a failure
     stalls = f < f_prev ? 0 : stalls + 1;
     if (stalls >= 3) {
+      if (f <= 1e-6 * st->res0) {
+        st->floor_stop = 1;
+        break;
+      }
       rc = PNP_ERR_KRYLOV_MAXIT;
       pnp_set_error("ns: no progress in three refinement steps (||F|| = %.3e)", f);
       break;

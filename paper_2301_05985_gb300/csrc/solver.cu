@@ -1097,6 +1097,7 @@ int ctx_coupled_step(pnp_ctx* c, pnp_solve_stats* st, pnp_ns_stats* nst) {
     nst->matvecs32 += one.matvecs32;
     nst->matvecs64 += one.matvecs64;
     nst->singular_blocks |= one.singular_blocks;
+    nst->floor_stop |= one.floor_stop;
     if (b == 0) nst->res0 = one.res0;
     nst->res_final = one.res_final;
     nst->wall_ms += one.wall_ms;
