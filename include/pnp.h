@@ -191,7 +191,8 @@ typedef struct pnp_ns_stats {
   int32_t floor_stop;    /* 1 when the solve stopped at the rounding floor of the FP64 residual
                             (three refinement steps without progress, ||F|| <= 1e-6 ||F(X^0)||)
                             above the requested tolerance */
-  int32_t pad_;
+  int32_t mg_fallbacks;  /* refinement steps whose multigrid-preconditioned correction raised
+                            ||F||: undone, the rest of the solve used the inverted blocks */
   double res0;           /* ||F(X^0)||_2 */
   double res_final;      /* ||F(X)||_2 */
   double wall_ms;        /* host wall time of the call */

@@ -62,6 +62,7 @@ def lib():
         L.ora_boundary_flux.argtypes = [vp, C.c_int, dp, dp]
         L.ora_plane_integral.argtypes = [vp, C.c_int, C.c_int64, dp, dp]
         L.ora_ns_apply.argtypes = [vp, vp, dp, dp, dp, dp, dp, C.c_int, dp]
+        L.ora_ns_apply_elements.argtypes = [vp, vp, dp, dp, dp, dp, dp, C.c_int, C.c_int64, C.c_int64, dp]
         L.ora_ns_matrix.restype = C.c_int64
         L.ora_ns_matrix.argtypes = [vp, vp, dp, i64p, i64p, dp]
         L.ora_ns_bc_rows.argtypes = [vp, vp, i32p, dp]
@@ -333,6 +334,16 @@ class OracleMesh:
         pc = p.to_c()
         lib().ora_ns_apply(self.h, C.byref(pc), _p(X, C.c_double), _p(a, C.c_double), _p(vk, C.c_double),
                            _p(vkm1, C.c_double), _p(U, C.c_double), int(bool(with_data)), _p(F, C.c_double))
+        return F
+
+    def ns_apply_elements(self, p: NsParams, X, adv, Vk, Vkm1, U, with_data, e0: int, e1: int, F):
+        """Add the element contributions of elements e0 <= e < e1 into F [n_nodes, 4]
+        (C-contiguous float64, modified in place; no Dirichlet or constraint rows)."""
+        X = self._x4(X); a = self._vel3(adv); vk = self._vel3(Vk); vkm1 = self._vel3(Vkm1); U = self._z(U)
+        pc = p.to_c()
+        lib().ora_ns_apply_elements(self.h, C.byref(pc), _p(X, C.c_double), _p(a, C.c_double), _p(vk, C.c_double),
+                                    _p(vkm1, C.c_double), _p(U, C.c_double), int(bool(with_data)), int(e0), int(e1),
+                                    _p(F, C.c_double))
         return F
 
     def ns_matrix(self, p: NsParams, adv=None) -> sp.csr_matrix:

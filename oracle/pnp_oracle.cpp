@@ -931,18 +931,25 @@ void ns_rows(const Mesh& m, const NsParams& p, const double* X, int affine, doub
   }
 }
 
-void ns_apply(const Mesh& m, const NsParams& p, const double* X, const double* adv, const double* Vk,
-              const double* Vkm1, const double* U, int with_data, double* F) {
-  const int64_t nn = (int64_t)m.node_xyz.size();
+// Element contributions of elements e0 <= e < e1, assembled with the transpose of the
+// constraints and added into F (no other rows touched).
+void ns_apply_elements(const Mesh& m, const NsParams& p, const double* X, const double* adv, const double* Vk,
+                       const double* Vkm1, const double* U, int with_data, int64_t e0, int64_t e1, double* F) {
   const int nc = corner_count(m.dim);
-  for (int64_t i = 0; i < 4 * nn; ++i) F[i] = 0.0;
-  for (int64_t e = 0; e < (int64_t)m.el_nodes.size(); ++e) {
+  for (int64_t e = e0; e < e1; ++e) {
     double Fe[8][4];
     ns_element(m, p, e, X, adv, Vk, Vkm1, U, with_data, Fe);
     for (int c = 0; c < nc; ++c)
       for (auto& pw : m.cons[m.el_nodes[e][c]])
         for (int f = 0; f < 4; ++f) F[4 * pw.first + f] += pw.second * Fe[c][f];
   }
+}
+
+void ns_apply(const Mesh& m, const NsParams& p, const double* X, const double* adv, const double* Vk,
+              const double* Vkm1, const double* U, int with_data, double* F) {
+  const int64_t nn = (int64_t)m.node_xyz.size();
+  for (int64_t i = 0; i < 4 * nn; ++i) F[i] = 0.0;
+  ns_apply_elements(m, p, X, adv, Vk, Vkm1, U, with_data, 0, (int64_t)m.el_nodes.size(), F);
   ns_rows(m, p, X, with_data, F);
 }
 
@@ -1289,6 +1296,13 @@ void ora_mms(int dim, double eps, double t, int steady, int64_t n, const double*
 void ora_ns_apply(void* h, const NsParams* p, const double* X, const double* adv, const double* Vk,
                   const double* Vkm1, const double* U, int with_data, double* F) {
   ns_apply(*static_cast<Mesh*>(h), *p, X, adv, Vk, Vkm1, U, with_data, F);
+}
+
+// The element contributions of elements e0 <= e < e1 added into F (no zeroing, no
+// Dirichlet or constraint rows); for timing the oracle on a sample across host threads.
+void ora_ns_apply_elements(void* h, const NsParams* p, const double* X, const double* adv, const double* Vk,
+                           const double* Vkm1, const double* U, int with_data, int64_t e0, int64_t e1, double* F) {
+  ns_apply_elements(*static_cast<Mesh*>(h), *p, X, adv, Vk, Vkm1, U, with_data, e0, e1, F);
 }
 
 // Triplets of the NS matrix (duplicates to be summed by the caller); pass null arrays to

@@ -27,6 +27,7 @@
 // the residual norm every kCheck iterations.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -695,6 +696,7 @@ struct NsState {
   double *part = nullptr, *sc = nullptr, *hsc = nullptr;
   double* usave = nullptr;  // [2][3N] PNP history of repeated block iterations
   float4* mgAx = nullptr;   // [N] operator scratch of the finest multigrid level
+  bool mg_off = false;      // this solve fell back from the V-cycle to the inverted blocks
   int64_t pin = -1;
   std::vector<void*> alloc;
 };
@@ -1019,7 +1021,7 @@ static int ns_mg_cycle(pnp_ctx* c, size_t l, const float4* b, float4* x) {
 static int ns_precond(pnp_ctx* c, const float4* in, float4* out) {
   NsState* S = c->ns;
   const int64_t N = c->n_nodes;
-  if (ns_mg_levels(c) > 0 && c->mg && c->mg->size() > 1) return ns_mg_cycle(c, 0, in, out);
+  if (ns_mg_levels(c) > 0 && !S->mg_off && c->mg && c->mg->size() > 1) return ns_mg_cycle(c, 0, in, out);
   ProfScope ps(c, PNP_PROF_NS_KRYLOV, 96.0 * N, 32.0 * N);
   k_ns_block_apply<<<nblk(N, 256), 256, 0, c->stream>>>(N, S->Dinv, in, out);
   note_launch();
@@ -1120,12 +1122,19 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
   int inner_total = 0, ref = 0, stalls = 0;
   int rc = PNP_OK;
   double f_prev = f;
+  // a refinement step that raises ||F|| is undone (X and F kept in the free block buffer)
+  // and, with multigrid, the rest of the solve uses the inverted blocks
+  double* Xs = S->Dg;
+  double* Fs = S->Dg + 4 * N;
+  S->mg_off = false;
   while (f > target) {
     if (ref >= kMaxRefine || inner_total >= p.ns_max_it) {
       rc = PNP_ERR_KRYLOV_MAXIT;
       pnp_set_error("ns: %d refinements, %d BiCGStab iterations, ||F|| = %.3e > %.3e", ref, inner_total, f, target);
       break;
     }
+    CK(cudaMemcpyAsync(Xs, S->X, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(Fs, S->F, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, s));
     k_ns_to_f32<<<nblk(N, 256), 256, 0, s>>>(N, S->F, -1.0 / f, S->r);
     note_launch();
     int its = 0;
@@ -1135,9 +1144,24 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
     note_launch();
     RC(ctx_ns_apply64(c, S->X, Ubody, S->F, true));
     st->matvecs64++;
-    RC(ctx_norm4(c, S->F, &f));
-    if (!std::isfinite(f)) PNP_FAIL(PNP_ERR_NAN, "ns: residual is not finite");
+    double fn;
+    RC(ctx_norm4(c, S->F, &fn));
     ++ref;
+    const bool worse = !(fn <= f);  // non-finite included
+    if (p.monitor)
+      fprintf(stderr, "[pnp ns %2d] ||F|| %.6e -> %.6e  bicgstab its %4d%s%s\n", ref, f, fn, its,
+              (ns_mg_levels(c) > 0 && !S->mg_off) ? "  multigrid" : "", worse ? "  (undone)" : "");
+    if (worse) {
+      CK(cudaMemcpyAsync(S->X, Xs, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(S->F, Fs, sizeof(double) * 4 * N, cudaMemcpyDeviceToDevice, s));
+      if (ns_mg_levels(c) > 0 && !S->mg_off) {
+        S->mg_off = true;
+        st->mg_fallbacks++;
+        continue;
+      }
+    } else {
+      f = fn;
+    }
     // three refinement steps in a row without reducing ||F|| end the solve: at the
     // rounding floor of the FP64 residual (||F|| <= 1e-6 ||F(X^0)||) as converged
     // (floor_stop), above it as a failure

@@ -1098,10 +1098,14 @@ int ctx_coupled_step(pnp_ctx* c, pnp_solve_stats* st, pnp_ns_stats* nst) {
     nst->matvecs64 += one.matvecs64;
     nst->singular_blocks |= one.singular_blocks;
     nst->floor_stop |= one.floor_stop;
+    nst->mg_fallbacks += one.mg_fallbacks;
     if (b == 0) nst->res0 = one.res0;
     nst->res_final = one.res_final;
     nst->wall_ms += one.wall_ms;
-    if (rc != PNP_OK) return rc;
+    if (rc != PNP_OK) {
+      st->status = rc;  // the step failed in its NS block
+      return rc;
+    }
     RC(ctx_ns_velocity(c, c->adv));
     pnp_solve_stats ps;
     c->coupled = true;

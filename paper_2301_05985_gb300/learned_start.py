@@ -51,20 +51,33 @@ def develop_double_layer(pnp, ctx, dt, dt0=1e-6, factor=4.0):
     ctx.reset_history()
 
 
-def record(pnp, torch, ctx, n_steps):
-    """Time-step the context and return the device tensor [k+1, N, 3] of states at the
-    full steps, k <= n_steps: recording stops at a step that fails even after splitting."""
+def record(pnp, torch, ctx, n_steps, coupled=False):
+    """Time-step the context and return (states, Newton iterations, u_z): the device tensor
+    [k+1, N, 3] of states at the full steps, k <= n_steps (recording stops at a step that
+    fails even after splitting), and with coupled NS-PNP steps the last velocity component
+    [k+1, N] at the same steps (None for PNP steps: the fluid is at rest)."""
     N = ctx.n_nodes
     S = torch.zeros((n_steps + 1, N, 3), dtype=torch.float64, device="cuda")
+    UZ = torch.zeros((n_steps + 1, N), dtype=torch.float64, device="cuda") if coupled else None
+    vel = torch.zeros((N, 3), dtype=torch.float64, device="cuda") if coupled else None
     ctx.get_field(pnp.PNP_FIELD_U, S[0], pnp.PNP_DEVICE)
+    if coupled:
+        ctx.get_field(pnp.PNP_FIELD_VELOCITY, vel, pnp.PNP_DEVICE)
+        UZ[0] = vel[:, 2]
     its = []
     for k in range(n_steps):
-        st = ctx.time_step(raise_on_error=False)
+        if coupled:
+            st, _ = ctx.coupled_step(raise_on_error=False)
+        else:
+            st = ctx.time_step(raise_on_error=False)
         if st.status != pnp.PNP_OK:
-            return S[:k + 1], its
+            return S[:k + 1], its, (UZ[:k + 1] if coupled else None)
         its.append(st.newton_its)
         ctx.get_field(pnp.PNP_FIELD_U, S[k + 1], pnp.PNP_DEVICE)
-    return S, its
+        if coupled:
+            ctx.get_field(pnp.PNP_FIELD_VELOCITY, vel, pnp.PNP_DEVICE)
+            UZ[k + 1] = vel[:, 2]
+    return S, its, UZ
 
 
 def run(pnp, W, torch, train_V=(10.0, 20.0, 30.0), steps_per_V=667, test_V=25.0, test_steps=50, seeds=(0, 1, 2),
@@ -76,7 +89,7 @@ def run(pnp, W, torch, train_V=(10.0, 20.0, 30.0), steps_per_V=667, test_V=25.0,
     t0 = time.perf_counter()
     for V in train_V:
         m2, c2 = setup(pnp, W, torch, V, level=level, mode=mode)
-        S, its = record(pnp, torch, c2, steps_per_V)
+        S, its, _ = record(pnp, torch, c2, steps_per_V)
         ctx.mlp_add_trajectory(S)
         log(f"trajectory V={V}: {len(its)} of {steps_per_V} steps, mean Newton its {np.mean(its):.2f}")
         del S

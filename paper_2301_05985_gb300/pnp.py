@@ -62,7 +62,7 @@ class pnp_ns_stats(C.Structure):
     _fields_ = [
         ("status", C.c_int32), ("refinements", C.c_int32), ("inner_its", C.c_int32),
         ("matvecs32", C.c_int32), ("matvecs64", C.c_int32), ("singular_blocks", C.c_int32),
-        ("floor_stop", C.c_int32), ("pad_", C.c_int32),
+        ("floor_stop", C.c_int32), ("mg_fallbacks", C.c_int32),
         ("res0", C.c_double), ("res_final", C.c_double), ("wall_ms", C.c_double),
     ]
 

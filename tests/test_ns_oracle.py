@@ -169,3 +169,24 @@ def test_residual_is_affine_with_the_assembled_matrix():
     A = mesh.ns_matrix(p, adv)
     np.testing.assert_allclose(AX.reshape(-1), A @ X.reshape(-1), rtol=1e-12, atol=1e-12 * np.abs(AX).max())
     np.testing.assert_allclose(F - F0, AX, rtol=1e-11, atol=1e-11 * np.abs(AX).max())
+
+
+def test_element_range_sums_reproduce_the_serial_ns_rows():
+    """The element-range entry point the CPU baseline times across threads adds up, over a
+    partition of the elements, to the serial rows (PDE rows; the others are set apart)."""
+    oc = W.random_balanced_octants(3, 2, 4, 0.3, 5)
+    mesh = O.OracleMesh(oc)
+    rng = np.random.default_rng(1)
+    n = mesh.n_nodes
+    bt, bv = O.no_slip_bcs(3)
+    p = O.NsParams(Sc=1.3, kappa=0.5, eps=0.2, dt=1e-2, beta=(1.5, -2.0, 0.5), bc_type=bt, bc_val=bv)
+    X, a, vk, vkm1 = (rng.standard_normal((n, k)) for k in (4, 3, 3, 3))
+    U = 1.0 + 0.1 * rng.standard_normal((n, 3))
+    kind, _ = mesh.ns_bc_rows(p)
+    for data in (True, False):
+        F = np.zeros((n, 4))
+        cuts = [0, 37, 300, mesh.n_elem]
+        for i in range(3):
+            mesh.ns_apply_elements(p, X, a, vk, vkm1, U, data, cuts[i], cuts[i + 1], F)
+        G = mesh.ns_apply(p, X, a, vk, vkm1, U, with_data=data)
+        np.testing.assert_allclose(F[kind == 0], G[kind == 0], rtol=0, atol=1e-12 * np.abs(G).max())
