@@ -1,23 +1,29 @@
-"""Benchmark: time steps of the VMS PNP block on the 3D electroconvection octree.
+"""Benchmark: NS-PNP time steps on the 3D electroconvection octree.
 
 Workload (the 3D electroconvection configuration, octree levels 6-10): unit cube;
 membrane at z = 0 (phi = 0, c+ = 2, c- zero flux), reservoir at z = 1 (phi = V, c+- = 1),
-zero-flux side walls; Lambda = 5e-4, V = 40, dt = 5e-4; c+- = 1 + seeded uniform noise of
-amplitude 1e-3, phi linear.  The octree is solution-adaptive (paper_2301_05985_gb300.refine):
-base level 6, a PNP pre-solve (3 steps) on a level-8 band z < 0.01, then level 9 for every
-octant with z_min < 0.01 and level 10 wherever max |grad c+-| at the octant centre exceeds
-60 (the Debye layer), 2:1 balanced: 5.6 M elements, 6.67 M nodes, 20.0 M unknowns.  The velocity is zero (the library has no
-Navier-Stokes block): a "PNP-NS step" here is the PNP block's step.
+zero-flux side walls, no-slip walls for the fluid; Lambda = 5e-4, V = 40, dt = 5e-4,
+Sc = 1, kappa = 0.5; c+- = 1 + seeded uniform noise of amplitude 1e-3, phi linear, fluid
+at rest.  The octree is solution-adaptive (paper_2301_05985_gb300.refine): base level 6, a
+PNP pre-solve (3 steps) on a level-8 band z < 0.01, then level 9 for every octant with
+z_min < 0.01 and level 10 wherever max |grad c+-| at the octant centre exceeds 60 (the
+Debye layer), 2:1 balanced: 5.6 M elements, 6.67 M nodes, 20.0 M PNP unknowns and 26.7 M
+NS unknowns.
 
-One step = one pnp_time_step: BDF2 (BDF1 first), Newton to ||F|| <= 1e-8 ||F(U^k)||.
+One step = one pnp_coupled_step (Sec. 4.1, one block iteration): the semi-implicit VMS
+Navier-Stokes block (linear in v, p; FGMRES in FP64 right-preconditioned by an FP32
+multigrid V-cycle on the octree hierarchy, to ||F|| <= 1e-8 ||F(X^0)||) with the body
+force of U^k, then the PNP block's pnp_time_step with v^{k+1} as the advection: BDF2
+(BDF1 first), Newton to ||F|| <= 1e-8 ||F(U^k)||.
   mixed (timed): inexact Newton (Eisenstat-Walker) with flexible GMRES(60) in FP64 (dots,
         orthogonalisation, basis) preconditioned by 24 steps of FP32 GMRES on J M^-1 (FP32
         J V, M the 3x3 block Jacobi); FP64 residual; learned start (network trained before
         the timed region on the first steps of this run), judged against 2 U^k - U^{k-1}.
-  FP64 arms, from the state the timed steps start from:
-        plain_same_solver: the same nested solver and forcing entirely in FP64;
+  FP64 arms, from the state the timed steps start from (the NS block solved the same way):
+        plain_same_solver: the same nested PNP solver and forcing entirely in FP64;
         plain_gmres: FP64 J V, GMRES(100) + block Jacobi to rtol 1e-8 per Newton step
         (exact Newton), previous-step start (the paper's solver settings).
+  --pnp-only times the PNP block's step alone (fluid at rest).
 
 value = seconds per step of the timed mixed steps (CUDA events on the library's stream);
 replicas: the slowest rank's time over the steps all ranks took.  The J V kernel's roofline
@@ -53,7 +59,12 @@ JV_BYTES_PER_ELEM = 36.0
 JV_FLOPS_PER_ELEM = 2500.0
 # arithmetic of each kernel class; for ALU classes the binding roofline is chosen per run
 BOUNDS = {"residual64": "fp32", "jv64": "fp64", "jv32": "fp32", "blockdiag": "fp32", "ortho_dot": "fp64",
-          "ortho_update": "fp64", "precond": "hbm", "mlp": "bf16", "inner_ortho": "hbm"}
+          "ortho_update": "fp64", "precond": "hbm", "mlp": "bf16", "inner_ortho": "hbm", "ns64": "fp64",
+          "ns32": "fp32", "ns_krylov": "hbm", "mg_coarse": "hbm"}
+# the Navier-Stokes block (the configurations give neither Sc nor kappa): Sc = 1, kappa = 0.5,
+# multigrid-preconditioned FP32 BiCGStab under FP64 refinement, App. A's tolerances
+NS_KW = dict(ns_Sc=1.0, ns_kappa=0.5, ns_mg_levels=8, mg_smooth=3, mg_omega=0.6, mg_coarse_its=32,
+             ns_rtol=1e-8, ns_atol=1e-10, ns_blocks=1)
 
 WORKLOADS = {
     "electroconvection": {"eps": 5e-4, "V": 40.0, "dt": 5e-4,
@@ -90,6 +101,8 @@ def parse():
                     help="trajectory steps recorded for training (0: the warm-up steps are the recording)")
     ap.add_argument("--train-steps", type=int, default=600, help="Adam steps of the learned start")
     ap.add_argument("--profile-steps", type=int, default=3, help="further steps timed per kernel class")
+    ap.add_argument("--pnp-only", action="store_true",
+                    help="time the PNP block's step alone (fluid at rest, no Navier-Stokes block)")
     a = ap.parse_args()
     if a.small:
         a.workload = "small"
@@ -113,6 +126,13 @@ def build_workload(pnp, torch, name):
 
 
 def mode_params(pnp, wl, mode, learned=True):
+    p = _mode_params(pnp, wl, mode, learned)
+    for k, v in NS_KW.items():
+        setattr(p, k, v)
+    return p
+
+
+def _mode_params(pnp, wl, mode, learned=True):
     if mode == "mixed":
         return pnp.default_params(eps=wl["eps"], dt=wl["dt"], precision=pnp.PNP_F32,
                                   start_mode=pnp.PNP_START_LEARNED if learned else pnp.PNP_START_EXTRAPOLATE,
@@ -135,11 +155,39 @@ def mode_params(pnp, wl, mode, learned=True):
 def make_ctx(pnp, W, torch, mesh, wl, mode, learned=True):
     ctx = pnp.Context(mesh, mode_params(pnp, wl, mode, learned), torch.cuda.current_stream().cuda_stream)
     ctx.set_bcs(W.membrane_bcs(3, wl["V"], 2.0))
+    bt = np.zeros((6, 4), np.int32)
+    bt[:, :3] = pnp.PNP_DIRICHLET  # no-slip walls
+    ctx.ns_set_bcs(bt, np.zeros((6, 4)))
     U0 = W.noisy_state(mesh.ijk, mesh.max_level, seed=0, amp=1e-3, phi_bottom=0.0, phi_top=wl["V"])
     ctx.set_field(pnp.PNP_FIELD_U, U0)
     ctx.make_consistent()
     ctx.reset_history()
     return ctx
+
+
+def do_step(ctx, coupled, raise_on_error=True):
+    """One step: the coupled NS-PNP step (its NS statistics under "ns") or the PNP step."""
+    if coupled:
+        st, nst = ctx.coupled_step(raise_on_error=raise_on_error)
+        d = st.as_dict()
+        d["ns"] = nst.as_dict()
+        return d
+    return ctx.time_step(raise_on_error=raise_on_error).as_dict()
+
+
+def ns_summary(stats):
+    """Per-step means of the NS solves of coupled steps (None for PNP-only steps)."""
+    ns = [s["ns"] for s in stats if "ns" in s]
+    if not ns:
+        return None
+    k = len(ns)
+    return {"bicgstab_its_per_step": sum(x["inner_its"] for x in ns) / k,
+            "refinements_per_step": sum(x["refinements"] for x in ns) / k,
+            "fp32_matvecs_per_step": sum(x["matvecs32"] for x in ns) / k,
+            "fp64_residuals_per_step": sum(x["matvecs64"] for x in ns) / k,
+            "s_per_step": sum(x["wall_ms"] for x in ns) * 1e-3 / k,
+            "rel_res_max": max(x["res_final"] / x["res0"] if x["res0"] > 0 else 0.0 for x in ns),
+            "floor_stops": sum(int(x["floor_stop"]) for x in ns), "status": [int(x["status"]) for x in ns]}
 
 
 def measured_peaks():
@@ -201,7 +249,7 @@ def oracle_threads():
     return max(1, os.cpu_count() or 1)
 
 
-def oracle_timing(oc, wl, U, Uk, Ukm1, V, n_res, n_jv, sample_frac=0.125, repeats=3):
+def oracle_timing(oc, wl, U, Uk, Ukm1, V, n_res, n_jv, sample_frac=0.125, repeats=3, ns_state=None, n_ns=0.0):
     """The FP64 oracle's residual and matrix-free J V on the workload's own mesh and state,
     timed on the host cores: a contiguous sample of the oracle's elements split into equal
     ranges over one thread per core (ctypes releases the interpreter lock), each thread
@@ -217,11 +265,17 @@ def oracle_timing(oc, wl, U, Uk, Ukm1, V, n_res, n_jv, sample_frac=0.125, repeat
     bcs = __import__("paper_2301_05985_gb300.workloads", fromlist=["x"]).membrane_bcs(3, wl["V"], 2.0)
     p = O.Params(eps=wl["eps"], dt=wl["dt"], beta=(1.5, -2.0, 0.5), bc_type=bcs.types, bc_val=bcs.values)
     Uo, Uko, Ukm1o, Vo = (np.ascontiguousarray(x[perm]) for x in (U["U"], Uk, Ukm1, V))
+    if ns_state is not None:
+        nsp = O.NsParams(Sc=NS_KW["ns_Sc"], kappa=NS_KW["ns_kappa"], eps=wl["eps"], dt=wl["dt"], beta=(1.5, -2.0, 0.5),
+                         bc_type=np.ones((6, 4), np.int32), bc_val=np.zeros((6, 4)))
+        Xo, vko, vkm1o = (np.ascontiguousarray(ns_state[k][perm]) for k in ("X", "vk", "vkm1"))
+        advo = 2.0 * vko - vkm1o
     T = oracle_threads()
     E = m.n_elem
     Es = max(T, int(E * sample_frac))
     cuts = np.linspace(0, Es, T + 1).astype(np.int64)
     bufs = [np.zeros((m.n_nodes, 3)) for _ in range(T)]
+    bufs4 = [np.zeros((m.n_nodes, 4)) for _ in range(T)] if ns_state is not None else None
 
     def timed(kind):
         for b in bufs:
@@ -230,8 +284,10 @@ def oracle_timing(oc, wl, U, Uk, Ukm1, V, n_res, n_jv, sample_frac=0.125, repeat
         def run(i):
             if kind == "res":
                 m.residual_elements(p, Uo, Uko, Ukm1o, None, cuts[i], cuts[i + 1], bufs[i])
-            else:
+            elif kind == "jv":
                 m.jv_elements(p, Uo, Vo, Uko, Ukm1o, None, cuts[i], cuts[i + 1], bufs[i])
+            else:
+                m.ns_apply_elements(nsp, Xo, advo, vko, vkm1o, Uo, False, cuts[i], cuts[i + 1], bufs4[i])
 
         th = [threading.Thread(target=run, args=(i,)) for i in range(T)]
         t = time.perf_counter()
@@ -243,9 +299,11 @@ def oracle_timing(oc, wl, U, Uk, Ukm1, V, n_res, n_jv, sample_frac=0.125, repeat
 
     t_res = statistics.median(timed("res") for _ in range(repeats))
     t_jv = statistics.median(timed("jv") for _ in range(repeats))
+    t_ns = statistics.median(timed("ns") for _ in range(repeats)) if ns_state is not None else 0.0
     dofs = 3.0 * m.n_nodes
-    return {"t_residual_s": t_res, "t_jv_s": t_jv, "residual_gdofs": dofs / t_res / 1e9, "jv_gdofs": dofs / t_jv / 1e9,
-            "s_per_step": n_res * t_res + n_jv * t_jv, "cores": T, "oracle_mesh_build_s": build_s,
+    return {"t_residual_s": t_res, "t_jv_s": t_jv, "t_ns_s": t_ns if ns_state is not None else None,
+            "residual_gdofs": dofs / t_res / 1e9, "jv_gdofs": dofs / t_jv / 1e9,
+            "s_per_step": n_res * t_res + n_jv * t_jv + n_ns * t_ns, "cores": T, "oracle_mesh_build_s": build_s,
             "sample": f"{Es} of {E} elements ({Es / E:.3f}) in {T} equal ranges, one thread per host core, "
                       f"median of {repeats}, scaled to the whole mesh"}
 
@@ -263,9 +321,9 @@ def _perm(ijk_ora, ijk_lib, L):
 def run_reference(args):
     """The oracle on this workload's mesh and state (host cores), as its arm of the
     comparison: each step is the oracle's residual and J V on a sample of the mesh,
-    scaled to the operator evaluations of one time step (residual and J V counts of the
-    library's mixed step on this workload, measured; 46 residuals and 1,300 J V if not
-    given)."""
+    scaled to the operator evaluations of one time step (about the counts of the library's
+    mixed coupled step on this workload: 8 residuals, 2,500 J V and 600 NS operator
+    applications)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -279,30 +337,45 @@ def run_reference(args):
     L = mesh.max_level
     U = W.noisy_state(mesh.ijk, L, seed=0, amp=1e-3, phi_bottom=0.0, phi_top=wl["V"])
     Vd = W.random_direction(mesh.ijk, L, 5)
-    n_res, n_jv = 46.0, 1300.0
+    n_res, n_jv = 8.0, 2500.0
+    coupled = not args.pnp_only
+    n_ns = 600.0 if coupled else 0.0
+    ns_state = {"X": np.zeros((mesh.n_nodes, 4)), "vk": np.zeros((mesh.n_nodes, 3)),
+                "vkm1": np.zeros((mesh.n_nodes, 3))} if coupled else None
     vals = []
     cb = None
     for k in range(args.warmup + args.steps):
-        cb = oracle_timing(oc_full, wl, {"U": U, "ijk": mesh.ijk}, U, U, Vd, n_res, n_jv, repeats=1)
+        cb = oracle_timing(oc_full, wl, {"U": U, "ijk": mesh.ijk}, U, U, Vd, n_res, n_jv, repeats=1,
+                           ns_state=ns_state, n_ns=n_ns)
         if k >= args.warmup:
             vals.append(cb["s_per_step"])
     v = float(np.mean(vals))
     out = {"metric": METRIC, "value": v, "unit": "s/step", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": workload_config(args.workload, mesh),
+           "config": workload_config(args.workload, mesh, coupled),
            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "value": v, "unit": "s/step",
-                            "sample": cb["sample"] + f"; x {n_res:g} residuals + {n_jv:g} J V per step "
-                                                      "(operator evaluations only)"},
+                            "sample": cb["sample"] + f"; x {n_res:g} residuals + {n_jv:g} J V"
+                                      + (f" + {n_ns:g} NS operator applications" if coupled else "")
+                                      + " per step (operator evaluations only)"},
            "e2e": {"value": v, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
-def workload_config(name, mesh):
+def workload_config(name, mesh, coupled=True):
     wl = WORKLOADS[name]
-    return {"workload": wl["desc"], "eps": wl["eps"], "V": wl["V"], "dt": wl["dt"],
-            "velocity": "zero (no Navier-Stokes block)", "n_elem": mesh.n_elem, "n_nodes": mesh.n_nodes,
-            "n_hanging": mesh.n_hanging, "dofs": 3 * mesh.n_nodes}
+    cfg = {"workload": wl["desc"], "eps": wl["eps"], "V": wl["V"], "dt": wl["dt"],
+           "n_elem": mesh.n_elem, "n_nodes": mesh.n_nodes, "n_hanging": mesh.n_hanging, "dofs": 3 * mesh.n_nodes}
+    if coupled:
+        cfg.update({"step": "NS-PNP block iteration (one pass): linear VMS Navier-Stokes, then PNP Newton",
+                    "velocity": "Navier-Stokes block: Sc = 1, kappa = 0.5, no-slip walls, fluid at rest at t = 0",
+                    "ns_dofs": 4 * mesh.n_nodes,
+                    "ns_solver": "FGMRES(30) in FP64 (basis, two-pass Gram-Schmidt, matrix action) right-"
+                                 "preconditioned by an FP32 multigrid V-cycle (8 coarser octrees, 3 block-Jacobi "
+                                 "sweeps, damping 0.6, 32 on the coarsest), to 1e-8 relative / 1e-10 absolute"})
+    else:
+        cfg["velocity"] = "zero (the PNP block alone)"
+    return cfg
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -409,7 +482,7 @@ def roofline(table, traffic, name="jv32", n_elem=0):
     return rl
 
 
-def train_learned_start(pnp, torch, ctx, n_record, train_steps):
+def train_learned_start(pnp, torch, ctx, n_record, train_steps, coupled=True):
     """Record the first steps of this run (extrapolated start) and train the network."""
     from paper_2301_05985_gb300 import learned_start as LS
     p = ctx.get_params()
@@ -417,9 +490,9 @@ def train_learned_start(pnp, torch, ctx, n_record, train_steps):
     p.start_mode = pnp.PNP_START_EXTRAPOLATE
     ctx.set_params(p)
     t0 = time.perf_counter()
-    S, its = LS.record(pnp, torch, ctx, n_record)
+    S, its, uz = LS.record(pnp, torch, ctx, n_record, coupled=coupled)
     ctx.mlp_init(seed=0)
-    ctx.mlp_add_trajectory(S)
+    ctx.mlp_add_trajectory(S, uz)
     st = ctx.mlp_train(steps=train_steps, batch=4096, lr=1e-3, seed=1)
     p.start_mode = mode
     ctx.set_params(p)
@@ -429,9 +502,14 @@ def train_learned_start(pnp, torch, ctx, n_record, train_steps):
 
 
 def snapshot(pnp, torch, ctx, N):
-    h = [torch.empty((N, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+    """U^k, U^{k-1}, v^k, v^{k-1} and (v, p)^k on the device."""
+    h = [torch.empty((N, 3), dtype=torch.float64, device="cuda") for _ in range(4)]
+    h.append(torch.empty((N, 4), dtype=torch.float64, device="cuda"))
     ctx.get_field(pnp.PNP_FIELD_U_PREV, h[0], pnp.PNP_DEVICE)
     ctx.get_field(pnp.PNP_FIELD_U_PREV2, h[1], pnp.PNP_DEVICE)
+    ctx.get_field(pnp.PNP_FIELD_VELOCITY, h[2], pnp.PNP_DEVICE)
+    ctx.get_field(pnp.PNP_FIELD_VELOCITY_PREV, h[3], pnp.PNP_DEVICE)
+    ctx.get_field(pnp.PNP_FIELD_NS, h[4], pnp.PNP_DEVICE)
     torch.cuda.synchronize()
     return h
 
@@ -441,16 +519,19 @@ def restore(pnp, ctx, h, step=8):
     ctx.set_field(pnp.PNP_FIELD_U_PREV, h[0], pnp.PNP_DEVICE)
     ctx.set_field(pnp.PNP_FIELD_U_PREV2, h[1], pnp.PNP_DEVICE)
     ctx.set_field(pnp.PNP_FIELD_U, h[0], pnp.PNP_DEVICE)
+    ctx.set_field(pnp.PNP_FIELD_VELOCITY, h[2], pnp.PNP_DEVICE)
+    ctx.set_field(pnp.PNP_FIELD_VELOCITY_PREV, h[3], pnp.PNP_DEVICE)
+    ctx.set_field(pnp.PNP_FIELD_NS, h[4], pnp.PNP_DEVICE)
     ctx.set_step_count(step)
 
 
-def run_arm(pnp, torch, W, mesh, wl, mode, hist, steps):
-    """`steps` BDF2 steps of an FP64 arm from the snapshot state; time, iterations, final U."""
+def run_arm(pnp, torch, W, mesh, wl, mode, hist, steps, coupled=True):
+    """`steps` BDF2 steps of an arm from the snapshot state; time, iterations, final U."""
     ctx = make_ctx(pnp, W, torch, mesh, wl, mode)
     restore(pnp, ctx, hist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sts = [ctx.time_step(raise_on_error=False).as_dict() for _ in range(steps)]
+    sts = [do_step(ctx, coupled, raise_on_error=False) for _ in range(steps)]
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     U = ctx.get_field(pnp.PNP_FIELD_U)
@@ -460,7 +541,8 @@ def run_arm(pnp, torch, W, mesh, wl, mode, hist, steps):
             "jv_per_step": sum(s["jv_evals"] for s in sts) / steps,
             "step_s": spread([s["wall_ms"] * 1e-3 for s in sts]),
             "mg_fallbacks": [int(s["mg_fallbacks"]) for s in sts],
-            "status": [int(s["status"]) for s in sts], "substeps": [int(s["substeps"]) for s in sts]}, U
+            "status": [int(s["status"]) for s in sts], "substeps": [int(s["substeps"]) for s in sts],
+            "ns": ns_summary(sts)}, U
 
 
 def spread(xs):
@@ -530,7 +612,7 @@ def jv_sweep(pnp, torch, W, peaks, states=5, reps=10):
 
 
 # ----------------------------------------------------------------------------- main
-def timed_mixed(pnp, torch, ctx, steps, stream, local):
+def timed_mixed(pnp, torch, ctx, steps, stream, local, coupled):
     stats = []
     launches0 = pnp.kernel_launches()
     sys.stderr.write(f"library launches before the timed steps: {launches0}\n")
@@ -540,7 +622,7 @@ def timed_mixed(pnp, torch, ctx, steps, stream, local):
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(steps):
-            stats.append(ctx.time_step().as_dict())
+            stats.append(do_step(ctx, coupled))
         e1.record(stream)
         torch.cuda.synchronize()
     return e0.elapsed_time(e1), stats, pnp.kernel_launches() - launches0, pnp.graph_captures() - captures0, clk
@@ -571,6 +653,7 @@ def main():
     N, E = mesh.n_nodes, mesh.n_elem
     ctx = make_ctx(pnp, W, torch, mesh, wl, "mixed", learned=not args.no_learned)
     stream = torch.cuda.current_stream()
+    coupled = not args.pnp_only
 
     learned = None
     warm = args.warmup
@@ -578,15 +661,15 @@ def main():
         # the warm-up steps (extrapolated start) are the recorded trajectory; one more
         # untimed step then runs the trained network's path once
         rec = args.record_steps if args.record_steps > 0 else max(args.warmup, 3)
-        learned = train_learned_start(pnp, torch, ctx, rec, args.train_steps)
+        learned = train_learned_start(pnp, torch, ctx, rec, args.train_steps, coupled)
         warm = 1 if args.record_steps <= 0 else args.warmup
     for _ in range(warm):
-        ctx.time_step()
+        do_step(ctx, coupled)
     torch.cuda.synchronize()
     hist = snapshot(pnp, torch, ctx, N)  # the state the timed steps start from
     if dist:
         dist.barrier()
-    ms, stats, launches, captures, clk = timed_mixed(pnp, torch, ctx, args.steps, stream, local)
+    ms, stats, launches, captures, clk = timed_mixed(pnp, torch, ctx, args.steps, stream, local, coupled)
     ms = max_over_ranks(ms, dist, "cuda")
     value = replica_seconds_per_step(ms, args.steps, world)
     gdofs_advanced = replica_throughput(3.0 * N * args.steps, world, ms)
@@ -598,7 +681,7 @@ def main():
     torch.cuda.synchronize()
     p0.record(stream)
     for _ in range(kp):
-        ctx.time_step()
+        do_step(ctx, coupled)
     p1.record(stream)
     torch.cuda.synchronize()
     prof_ms = p0.elapsed_time(p1)
@@ -612,9 +695,11 @@ def main():
     e2e = None
     U_mixed = None
     if not args.no_e2e:
-        hU = [torch.empty((N, 3), dtype=torch.float64, pin_memory=True) for _ in range(3)]
-        hU[0].copy_(hist[0])
-        hU[1].copy_(hist[1])
+        # pinned host copies of the step's inputs (U^k, U^{k-1}, v^k, v^{k-1}, (v, p)^k) and outputs
+        pin = lambda k: torch.empty((N, k), dtype=torch.float64, pin_memory=True)  # noqa: E731
+        hU, hV, hX = [pin(3) for _ in range(3)], [pin(3) for _ in range(2)], [pin(4) for _ in range(2)]
+        for dst, src in ((hU[0], hist[0]), (hU[1], hist[1]), (hV[0], hist[2]), (hV[1], hist[3]), (hX[0], hist[4])):
+            dst.copy_(src)
         torch.cuda.synchronize()
         c0 = pnp.graph_captures()
         e2e_stats = []
@@ -623,20 +708,32 @@ def main():
         for k in range(e2e_steps):
             ctx.set_field(pnp.PNP_FIELD_U_PREV, hU[0], pnp.PNP_HOST)
             ctx.set_field(pnp.PNP_FIELD_U_PREV2, hU[1], pnp.PNP_HOST)
-            e2e_stats.append(ctx.time_step().as_dict())
+            if coupled:
+                ctx.set_field(pnp.PNP_FIELD_VELOCITY, hV[0], pnp.PNP_HOST)
+                ctx.set_field(pnp.PNP_FIELD_VELOCITY_PREV, hV[1], pnp.PNP_HOST)
+                ctx.set_field(pnp.PNP_FIELD_NS, hX[0], pnp.PNP_HOST)
+            e2e_stats.append(do_step(ctx, coupled))
             ctx.get_field(pnp.PNP_FIELD_U, hU[2], pnp.PNP_HOST)
+            if coupled:
+                ctx.get_field(pnp.PNP_FIELD_NS, hX[1], pnp.PNP_HOST)
+                hV = [hV[1], hV[0]]
+                hV[0].copy_(hX[1][:, :3])  # v^{k+1} is the next step's v^k
+                hX = [hX[1], hX[0]]
             if k + 1 == plain_steps:
                 U_mixed = hU[2].numpy().copy()
             hU = [hU[2], hU[0], hU[1]]
         t_e2e = time.perf_counter() - t0
+        h2d = (2 * 24 + (2 * 24 + 32 if coupled else 0)) * N
+        d2h = (24 + (32 if coupled else 0)) * N
         e2e = {"value": replica_seconds_per_step(1e3 * t_e2e, e2e_steps, world), "unit": "s/step",
-               "h2d_bytes_per_step": 2 * 24 * N, "d2h_bytes_per_step": 24 * N,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": 1e3 * t_e2e / e2e_steps, "steps": e2e_steps, "graph_captures": pnp.graph_captures() - c0,
                "trajectory": f"the first {e2e_steps} timed steps again from the same state",
                "device_timed_same_steps_s_per_step": sum(s["wall_ms"] for s in stats[:e2e_steps]) * 1e-3 / e2e_steps,
                "step_s": spread([s["wall_ms"] * 1e-3 for s in e2e_stats]),
                "newton_its_per_step": sum(s["newton_its"] for s in e2e_stats) / e2e_steps,
-               "krylov_its_per_step": sum(s["krylov_its"] for s in e2e_stats) / e2e_steps}
+               "krylov_its_per_step": sum(s["krylov_its"] for s in e2e_stats) / e2e_steps,
+               "ns": ns_summary(e2e_stats)}
 
     peaks = measured_peaks()
     table = kernel_table(prof, peaks, prof_ms, N, E)
@@ -653,21 +750,23 @@ def main():
     kt = sum(s["krylov_its"] for s in stats)
     n_res = sum(s["residual_evals"] for s in stats) / args.steps
     n_jv = sum(s["jv_evals"] for s in stats) / args.steps
+    nss = ns_summary(stats)
+    n_ns = (nss["fp32_matvecs_per_step"] + nss["fp64_residuals_per_step"]) if nss else 0.0
 
     # FP64 arms and the multigrid-preconditioned arm from the same state (rank 0 only)
     arms = {}
     if not args.no_mg and rank == 0:
         mg_steps = max(1, min(args.mg_steps, args.steps))
-        arm, _ = run_arm(pnp, torch, W, mesh, wl, "mixed_mg", hist, mg_steps)
+        arm, _ = run_arm(pnp, torch, W, mesh, wl, "mixed_mg", hist, mg_steps, coupled)
         arm["preconditioner"] = ("geometric multigrid V-cycle (8 coarser octrees, 3 block-Jacobi sweeps, "
                                  "damping 0.6, 32 sweeps on the coarsest), inner GMRES(24) where it falls behind")
         arm["start"] = "extrapolated"
         arm["timed_mixed_same_steps_s_per_step"] = sum(s["wall_ms"] for s in stats[:mg_steps]) * 1e-3 / mg_steps
         arms["mixed_multigrid"] = arm
     if (args.plain or args.workload != "electroconvection") and rank == 0:
-        arm, U_same = run_arm(pnp, torch, W, mesh, wl, "same64", hist, plain_steps)
+        arm, U_same = run_arm(pnp, torch, W, mesh, wl, "same64", hist, plain_steps, coupled)
         arms["plain_same_solver"] = arm
-        arm, U_gm = run_arm(pnp, torch, W, mesh, wl, "plain", hist, plain_steps)
+        arm, U_gm = run_arm(pnp, torch, W, mesh, wl, "plain", hist, plain_steps, coupled)
         arms["plain_gmres"] = arm
         if U_mixed is not None:
             arms["field_errors"] = {"steps": plain_steps, "mixed_vs_fp64_same_solver": field_errors(U_mixed, U_same),
@@ -688,23 +787,27 @@ def main():
         Uh = hist[0].cpu().numpy()
         Vh = W.random_direction(mesh.ijk, mesh.max_level, 5)
         oc_full = W.Octants(3, mesh.max_level, *mesh.elements())
-        ot = oracle_timing(oc_full, wl, {"U": Uh, "ijk": mesh.ijk}, Uh, hist[1].cpu().numpy(), Vh, n_res, n_jv)
+        ns_state = {"X": hist[4].cpu().numpy(), "vk": hist[2].cpu().numpy(), "vkm1": hist[3].cpu().numpy()} \
+            if coupled else None
+        ot = oracle_timing(oc_full, wl, {"U": Uh, "ijk": mesh.ijk}, Uh, hist[1].cpu().numpy(), Vh, n_res, n_jv,
+                           ns_state=ns_state, n_ns=n_ns)
         cpu = {"value": ot["s_per_step"], "unit": "s/step", "cores": ot["cores"], "kind": "oracle",
-               "sample": ot["sample"] + f"; x {n_res:.1f} residuals + {n_jv:.0f} J V per step (the mixed step's "
-                                        "counts; operator evaluations only, FP64)",
+               "sample": ot["sample"] + f"; x {n_res:.1f} residuals + {n_jv:.0f} J V"
+                         + (f" + {n_ns:.0f} NS operator applications" if coupled else "")
+                         + " per step (the mixed step's counts; operator evaluations only, FP64)",
                "residual_gdofs": ot["residual_gdofs"], "jv_gdofs": ot["jv_gdofs"],
-               "t_residual_s": ot["t_residual_s"], "t_jv_s": ot["t_jv_s"],
+               "t_residual_s": ot["t_residual_s"], "t_jv_s": ot["t_jv_s"], "t_ns_s": ot.get("t_ns_s"),
                "oracle_mesh_build_s": ot["oracle_mesh_build_s"]}
     ctx.close()
     secondary = None
     if not args.no_secondary and args.workload == "electroconvection" and world == 1:
-        secondary = secondary_membrane(pnp, torch, W, peaks)
+        secondary = secondary_membrane(pnp, torch, W, peaks, coupled=coupled)
 
     out = {
         "metric": METRIC, "value": round(value, 6), "unit": "s/step", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {**workload_config(args.workload, mesh), "mesh_build": mesh_info,
+        "config": {**workload_config(args.workload, mesh, coupled), "mesh_build": mesh_info,
                    "mode": "mixed FP32 J V + learned start" if learned else "mixed FP32 J V",
                    "krylov": "flexible GMRES(60) in FP64, preconditioned by 24 steps of FP32 GMRES on J M^-1 "
                              "(M block Jacobi); Eisenstat-Walker forcing",
@@ -722,6 +825,7 @@ def main():
         "step_s": spread([s["wall_ms"] * 1e-3 for s in stats]),
         "newton_its_per_step": nt / args.steps, "krylov_its_per_step": kt / args.steps,
         "residual_evals_per_step": n_res, "jv_evals_per_step": n_jv,
+        "ns": nss,
         "split_steps": sum(int(s["substeps"] > 1) for s in stats),
         "learned_start_used": sum(int(s["start_used"] == pnp.PNP_START_LEARNED) for s in stats),
         "learned_training": learned,
@@ -736,7 +840,7 @@ def main():
     print(json.dumps(out))
 
 
-def secondary_membrane(pnp, torch, W, peaks, warmup=3, steps=3):
+def secondary_membrane(pnp, torch, W, peaks, warmup=3, steps=3, coupled=True):
     """The membrane-band octree (3.14 M dofs): mixed steps and both FP64 arms from the same
     state, with the per-field differences of the final states."""
     wl = WORKLOADS["membrane"]
@@ -744,11 +848,11 @@ def secondary_membrane(pnp, torch, W, peaks, warmup=3, steps=3):
     N = mesh.n_nodes
     ctx = make_ctx(pnp, W, torch, mesh, wl, "mixed", learned=False)
     for _ in range(warmup):
-        ctx.time_step()
+        do_step(ctx, coupled)
     hist = snapshot(pnp, torch, ctx, N)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sts = [ctx.time_step().as_dict() for _ in range(steps)]
+    sts = [do_step(ctx, coupled) for _ in range(steps)]
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     Um = ctx.get_field(pnp.PNP_FIELD_U)
@@ -756,12 +860,12 @@ def secondary_membrane(pnp, torch, W, peaks, warmup=3, steps=3):
     out = {"workload": wl["desc"], "dofs": 3 * N, "steps": steps,
            "mixed": {"s_per_step": t / steps, "newton_its_per_step": sum(s["newton_its"] for s in sts) / steps,
                      "krylov_its_per_step": sum(s["krylov_its"] for s in sts) / steps,
-                     "start": "extrapolated"}}
-    arm, _ = run_arm(pnp, torch, W, mesh, wl, "mixed_mg", hist, steps)
+                     "start": "extrapolated", "ns": ns_summary(sts)}}
+    arm, _ = run_arm(pnp, torch, W, mesh, wl, "mixed_mg", hist, steps, coupled)
     out["mixed_multigrid"] = arm
-    arm, Us = run_arm(pnp, torch, W, mesh, wl, "same64", hist, steps)
+    arm, Us = run_arm(pnp, torch, W, mesh, wl, "same64", hist, steps, coupled)
     out["plain_same_solver"] = arm
-    arm, Ug = run_arm(pnp, torch, W, mesh, wl, "plain", hist, steps)
+    arm, Ug = run_arm(pnp, torch, W, mesh, wl, "plain", hist, steps, coupled)
     out["plain_gmres"] = arm
     out["field_errors"] = {"mixed_vs_fp64_same_solver": field_errors(Um, Us), "mixed_vs_fp64_gmres": field_errors(Um, Ug)}
     mesh.close()

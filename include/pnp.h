@@ -154,6 +154,10 @@ typedef struct pnp_params {
                             mg_coarse_its), rediscretised NS operators at the injected v~.
                             Non-periodic meshes (0) */
   int32_t ns_inner_max_it; /* BiCGStab iterations per FP64 refinement step (200) */
+  int32_t ns_fgmres;     /* 0: FP32 BiCGStab under FP64 defect correction; m in 1..200: FGMRES(m)
+                            in FP64 (basis, dots, matrix action) right-preconditioned in FP32 by
+                            the same V-cycle or blocks, restarted to the tolerance (30) */
+  int32_t pad4_;
 } pnp_params;
 
 typedef struct pnp_solve_stats {
@@ -193,6 +197,9 @@ typedef struct pnp_ns_stats {
                             above the requested tolerance */
   int32_t mg_fallbacks;  /* refinement steps whose multigrid-preconditioned correction raised
                             ||F||: undone, the rest of the solve used the inverted blocks */
+  int32_t krylov_fallbacks; /* 1 when FGMRES stagnated (three restart cycles cutting ||F|| by
+                            less than 5 %) and the solve continued with BiCGStab refinement */
+  int32_t pad_;
   double res0;           /* ||F(X^0)||_2 */
   double res_final;      /* ||F(X)||_2 */
   double wall_ms;        /* host wall time of the call */
@@ -423,14 +430,19 @@ int pnp_ns_matvec(pnp_ctx* c, const void* X, void* Y, int precision);
  * parent p (the cross pairs through hanging corners are left out).  The preconditioner
  * of pnp_ns_solve inverts them (identity rows on constrained rows). */
 int pnp_ns_block_diag(pnp_ctx* c, double* D);
-/* Solve the linear NS system for PNP_FIELD_NS in place, starting from its value: FP64
- * defect correction around FP32 BiCGStab (App. A solves this block with BiCGStab) of at
- * most ns_inner_max_it iterations each, right-preconditioned by the inverted diagonal
- * blocks or (ns_mg_levels) a multigrid V-cycle, until ||F(X)|| <= max(ns_rtol ||F(X^0)||,
- * ns_atol).  PNP_ERR_KRYLOV_MAXIT after ns_max_it BiCGStab iterations, 60 refinement
- * steps or three refinement steps in a row without progress above 1e-6 ||F(X^0)|| (at or
- * below it the solve ends as converged with st->floor_stop = 1); PNP_ERR_NAN on a
- * non-finite norm.  Uses the context's beta0..2. */
+/* Solve the linear NS system for PNP_FIELD_NS in place, starting from its value, until
+ * ||F(X)|| <= max(ns_rtol ||F(X^0)||, ns_atol), right-preconditioned in FP32 by the inverted
+ * diagonal blocks or (ns_mg_levels) a multigrid V-cycle.  ns_fgmres = m > 0 (default):
+ * FGMRES(m) with an FP64 basis, FP64 dots and FP64 matrix action, restarted (three restart
+ * cycles in a row that cut ||F|| by less than 5 % hand the solve, from its iterate, to the
+ * BiCGStab refinement below: st->krylov_fallbacks).  ns_fgmres = 0: FP64 defect
+ * correction around FP32 BiCGStab (App. A solves this block with BiCGStab) of at most
+ * ns_inner_max_it iterations each (a step that raises ||F|| is undone, and with multigrid the
+ * solve continues with the blocks).  PNP_ERR_KRYLOV_MAXIT after ns_max_it Krylov
+ * iterations, 60 refinement steps, or when progress stops above 1e-6 ||F(X^0)|| (at or below
+ * it the solve ends as converged with st->floor_stop = 1); PNP_ERR_NAN on a non-finite
+ * norm.  st->inner_its counts the Krylov iterations, st->refinements the FGMRES restart
+ * cycles or refinement steps.  Uses the context's beta0..2. */
 int pnp_ns_solve(pnp_ctx* c, pnp_ns_stats* st);
 /* One NS-PNP time step by block iteration (Sec. 4.1): ns_blocks times, the NS system
  * (body force from U^k in the first pass, then from the latest U^{k+1}) and then the PNP

@@ -81,6 +81,8 @@ void pnp_params_default(pnp_params* p) {
   p->ns_pin = 1;
   p->ns_mg_levels = 0;
   p->ns_inner_max_it = 200;
+  p->ns_fgmres = 30;
+  p->pad4_ = 0;
   p->mg_levels = 0;
   p->mg_smooth = 2;
   p->mg_omega = 0.5;
@@ -238,7 +240,7 @@ static int check_params(const pnp_params* p) {
   if (p->ns_blocks < 1 || p->ns_blocks > 16 || !(p->ns_Sc > 0) || !std::isfinite(p->ns_Sc) ||
       !std::isfinite(p->ns_kappa) || !(p->ns_rtol >= 0) || !(p->ns_atol >= 0) || !(p->ns_inner_rtol > 0) ||
       !(p->ns_inner_rtol < 1) || p->ns_max_it < 1 || (p->ns_pin != 0 && p->ns_pin != 1) || p->ns_mg_levels < 0 ||
-      p->ns_mg_levels > 16 || p->ns_inner_max_it < 1)
+      p->ns_mg_levels > 16 || p->ns_inner_max_it < 1 || p->ns_fgmres < 0 || p->ns_fgmres > 200)
     PNP_FAIL(PNP_ERR_ARG, "params: Navier-Stokes settings out of range");
   return PNP_OK;
 }

@@ -576,6 +576,25 @@ __global__ void k_ns_history(int64_t N, const double* __restrict__ vk, const dou
   adv32[i] = make_float4((float)a[0], (float)a[1], (float)a[2], 0.f);
 }
 
+// x += sum_i coef_i Z_i: FP32 vectors and FP64 coefficients combined in FP64 (the terms of
+// a flexible GMRES update can be large and cancel)
+__global__ void k_ns_combine(int64_t n, int k, const float* __restrict__ Zb, int64_t ld,
+                             const double* __restrict__ coef, double* __restrict__ x) {
+  extern __shared__ double cfd[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cfd[i] = coef[i];
+  __syncthreads();
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    double v0 = 0.0, v1 = 0.0;
+    int i = 0;
+    for (; i + 2 <= k; i += 2) {
+      v0 = fma(cfd[i], (double)Zb[(int64_t)i * ld + t], v0);
+      v1 = fma(cfd[i + 1], (double)Zb[(int64_t)(i + 1) * ld + t], v1);
+    }
+    if (i < k) v0 = fma(cfd[i], (double)Zb[(int64_t)i * ld + t], v0);
+    x[t] += v0 + v1;
+  }
+}
+
 // v^{k+1} of X [N][4] into a node-major [N][3] velocity
 __global__ void k_ns_velocity(int64_t N, const double* __restrict__ X, double* __restrict__ v3) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -697,6 +716,11 @@ struct NsState {
   double* usave = nullptr;  // [2][3N] PNP history of repeated block iterations
   float4* mgAx = nullptr;   // [N] operator scratch of the finest multigrid level
   bool mg_off = false;      // this solve fell back from the V-cycle to the inverted blocks
+  // FGMRES(m): unnormalised FP64 basis [(m+1)][4N], FP32 preconditioned vectors [m][4N], an
+  // FP64 scratch vector, reduction partials and device scalars
+  double *Q = nullptr, *z64 = nullptr, *fpart = nullptr, *fsc = nullptr, *fsc2 = nullptr;
+  float* Z = nullptr;
+  int fg_m = 0;
   int64_t pin = -1;
   std::vector<void*> alloc;
 };
@@ -726,7 +750,8 @@ int ctx_ns_alloc(pnp_ctx* c) {
             get((void**)&S->rh, f4) && get((void**)&S->p, f4) && get((void**)&S->v, f4) && get((void**)&S->t, f4) &&
             get((void**)&S->ph, f4) && get((void**)&S->sh, f4) && get((void**)&S->x, f4) &&
             get((void**)&S->part, sizeof(double) * 2 * kRedBlocks) && get((void**)&S->sc, sizeof(double) * kScalars);
-  if (ok) ok = cudaMallocHost((void**)&S->hsc, sizeof(double) * kScalars) == cudaSuccess;
+  // pinned host scalars: the BiCGStab scalars, or FGMRES projections (m <= 200)
+  if (ok) ok = cudaMallocHost((void**)&S->hsc, sizeof(double) * 256) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     ctx_ns_release(c);
@@ -1100,6 +1125,155 @@ static int ns_bicgstab32(pnp_ctx* c, double rtol, int max_it, int* its_out) {
   return PNP_OK;
 }
 
+// FGMRES(m) in FP64 on A d = -F(X), right-preconditioned in FP32 (the V-cycle or the
+// inverted blocks), restarted until ||F(X)|| <= target.  The preconditioned vectors are
+// kept (FP32) so the flexible relation A Z = Q H holds in FP64; the basis is unnormalised
+// with its scales on the host (as the PNP solver's outer GMRES).
+static int ns_alloc_fgmres(pnp_ctx* c, int m) {
+  NsState* S = c->ns;
+  if (S->fg_m == m && S->Q) return PNP_OK;
+  const int64_t n = 4 * c->n_nodes;
+  auto get = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+    S->alloc.push_back(*p);
+    return true;
+  };
+  // earlier (smaller) buffers stay in the allocation list until the context is destroyed
+  const bool ok = get((void**)&S->Q, sizeof(double) * (size_t)(m + 1) * n) &&
+                  get((void**)&S->Z, sizeof(float) * (size_t)m * n) && get((void**)&S->z64, sizeof(double) * n) &&
+                  get((void**)&S->fpart, sizeof(double) * (size_t)multi_dot_blocks(n) * (m + 2)) &&
+                  get((void**)&S->fsc, sizeof(double) * (size_t)(3 * (m + 2) + 4)) &&
+                  get((void**)&S->fsc2, sizeof(double) * (size_t)(m + 2));
+  if (!ok) {
+    cudaGetLastError();
+    S->Q = nullptr;
+    PNP_FAIL(PNP_ERR_NOMEM, "ns: no device memory for FGMRES(%d)", m);
+  }
+  S->fg_m = m;
+  return PNP_OK;
+}
+
+static int ns_fgmres(pnp_ctx* c, const double* Ubody, double target, double& f, pnp_ns_stats* st) {
+  NsState* S = c->ns;
+  const pnp_params& p = c->prm;
+  const int m = p.ns_fgmres;
+  RC(ns_alloc_fgmres(c, m));
+  const int64_t N = c->n_nodes, n = 4 * N;
+  cudaStream_t s = c->stream;
+  double* dd = S->fsc;               // [m+2] projections
+  double* dinv = dd + (m + 2);       // [m+2] 1 / s_i^2
+  double* dcoef = dinv + (m + 2);    // [m+2] combination coefficients
+  double* dnrm = dcoef + (m + 2);    // w . w after the pass
+  double* dd2 = S->fsc2;             // [m+2] projections of the second pass
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), sv(m + 1), hp(m + 2);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  int total = 0, cycles = 0;
+  double f_prev = f;
+  int stalls = 0;
+  while (f > target) {
+    if (total >= p.ns_max_it) {
+      pnp_set_error("ns: FGMRES %d iterations, ||F|| = %.3e > %.3e", total, f, target);
+      return PNP_ERR_KRYLOV_MAXIT;
+    }
+    // u_0 = -F, s_0 = ||F||
+    CK(launch_axpbyz(n, -1.0, S->F, 0.0, S->F, S->Q, s));
+    sv[0] = f;
+    hp[0] = 1.0 / (f * f);
+    CK(cudaMemcpyAsync(dinv, hp.data(), sizeof(double), cudaMemcpyHostToDevice, s));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = f;
+    int k = 0;
+    for (int j = 0; j < m && total < p.ns_max_it; ++j) {
+      double* uj = S->Q + (size_t)j * n;
+      double* w = S->Q + (size_t)(j + 1) * n;
+      float4* zj = reinterpret_cast<float4*>(S->Z + (size_t)j * n);
+      // z_j = M^-1 (u_j / s_j) in FP32; w = A z_j in FP64
+      k_ns_to_f32<<<nblk(N, 256), 256, 0, s>>>(N, uj, 1.0 / sv[j], S->r);
+      note_launch();
+      RC(ns_precond(c, S->r, zj));
+      CK(launch_to_f64_scaled(n, reinterpret_cast<const float*>(zj), 1.0, S->z64, s));
+      RC(ctx_ns_apply64(c, S->z64, nullptr, w, false));
+      st->matvecs64++;
+      {
+        // classical Gram-Schmidt, two passes (the pressure and velocity scales differ by
+        // orders of magnitude: one pass loses orthogonality and the Arnoldi estimate with it)
+        const double nj = (double)n * (j + 1);
+        ProfScope ps(c, PNP_PROF_NS_KRYLOV, 16.0 * (2.0 * nj + 3.0 * n), 8.0 * nj);
+        CK(launch_multi_dot_ext(n, j + 1, false, S->Q, n, w, S->fpart, dd, s));
+        CK(launch_multi_axpy_norm(n, j + 1, S->Q, n, dd, dinv, w, S->fpart, dnrm, s));
+        CK(launch_multi_dot_ext(n, j + 1, false, S->Q, n, w, S->fpart, dd2, s));
+        CK(launch_multi_axpy_norm(n, j + 1, S->Q, n, dd2, dinv, w, S->fpart, dnrm, s));
+      }
+      CK(cudaMemcpyAsync(S->hsc, dd, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(S->hsc + (m + 2), dd2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(S->hsc + (m + 1), dnrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i) Hij(i, j) = (S->hsc[i] + S->hsc[m + 2 + i]) / sv[i];
+      const double nrm = std::sqrt(S->hsc[m + 1]);
+      if (!std::isfinite(nrm)) PNP_FAIL(PNP_ERR_NAN, "ns: FGMRES vector norm is not finite");
+      sv[j + 1] = nrm;
+      Hij(j + 1, j) = nrm;
+      if (nrm > 0) {
+        hp[j + 1] = 1.0 / (nrm * nrm);
+        CK(cudaMemcpyAsync(dinv + j + 1, hp.data() + j + 1, sizeof(double), cudaMemcpyHostToDevice, s));
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double rr = std::hypot(Hij(j, j), Hij(j + 1, j));
+      if (rr == 0.0) PNP_FAIL(PNP_ERR_NAN, "ns: singular FGMRES Hessenberg matrix");
+      cs[j] = Hij(j, j) / rr;
+      sn[j] = Hij(j + 1, j) / rr;
+      Hij(j, j) = rr;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      k = j + 1;
+      if (p.monitor)
+        fprintf(stderr, "[pnp ns fgmres %3d] estimated ||F|| %.6e\n", total, std::fabs(g[j + 1]));
+      if (std::fabs(g[j + 1]) <= target || nrm <= 1e-300 * f) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
+      y[i] = t / Hij(i, i);
+    }
+    // X += sum_j y_j z_j
+    CK(cudaStreamSynchronize(s));  // the pinned slots are free
+    for (int i = 0; i < k; ++i) S->hsc[i] = y[i];
+    CK(cudaMemcpyAsync(dcoef, S->hsc, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    k_ns_combine<<<gsb(n), 256, k * sizeof(double), s>>>(n, k, S->Z, n, dcoef, S->X);
+    note_launch();
+    CK(cudaGetLastError());
+    RC(ctx_ns_apply64(c, S->X, Ubody, S->F, true));
+    st->matvecs64++;
+    RC(ctx_norm4(c, S->F, &f));
+    if (!std::isfinite(f)) PNP_FAIL(PNP_ERR_NAN, "ns: residual is not finite");
+    ++cycles;
+    if (p.monitor) fprintf(stderr, "[pnp ns cycle %2d] ||F|| %.6e (%d iterations)\n", cycles, f, total);
+    // restart cycles that cut ||F|| by less than 5% three times in a row: the rounding floor
+    // (<= 1e-6 ||F(X^0)||, converged) or a failure
+    stalls = f < 0.95 * f_prev ? 0 : stalls + 1;
+    if (stalls >= 3) {
+      if (f <= 1e-6 * st->res0) {
+        st->floor_stop = 1;
+        break;
+      }
+      st->inner_its = total;
+      st->refinements = cycles;
+      return -1;  // stagnated: the caller continues with BiCGStab
+    }
+    f_prev = f;
+  }
+  st->inner_its = total;
+  st->refinements = cycles;
+  st->matvecs32 = 0;
+  return PNP_OK;
+}
+
 // Solve the linear NS system for X (start: its current value), body force from Ubody.
 int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
   const double t0 = now_ms();
@@ -1119,7 +1293,23 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
   if (!std::isfinite(f)) PNP_FAIL(PNP_ERR_NAN, "ns: initial residual is not finite");
   st->res0 = f;
   const double target = std::max(p.ns_rtol * f, p.ns_atol);
+  S->mg_off = false;
   int inner_total = 0, ref = 0, stalls = 0;
+  if (p.ns_fgmres > 0) {
+    const int rc = f > target ? ns_fgmres(c, Ubody, target, f, st) : PNP_OK;
+    if (rc >= 0) {
+      st->status = rc;
+      st->res_final = f;
+      st->wall_ms = now_ms() - t0;
+      return rc;
+    }
+    // FGMRES stagnated: BiCGStab refinement from its iterate (restart cycles and refinement
+    // steps add up in st->refinements, Krylov iterations in st->inner_its)
+    st->krylov_fallbacks++;
+    inner_total = st->inner_its;
+    ref = st->refinements;
+    if (p.monitor) fprintf(stderr, "[pnp ns] FGMRES stagnated at ||F|| %.6e: BiCGStab refinement\n", f);
+  }
   int rc = PNP_OK;
   double f_prev = f;
   // a refinement step that raises ||F|| is undone (X and F kept in the free block buffer)
@@ -1182,8 +1372,8 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
   CK(cudaStreamSynchronize(s));
   st->status = rc;
   st->refinements = ref;
+  st->matvecs32 += 2 * (inner_total - st->inner_its);  // BiCGStab: two per iteration
   st->inner_its = inner_total;
-  st->matvecs32 = 2 * inner_total;
   st->res_final = f;
   st->singular_blocks = (flag & 4) ? 1 : 0;
   st->wall_ms = now_ms() - t0;

@@ -1099,6 +1099,7 @@ int ctx_coupled_step(pnp_ctx* c, pnp_solve_stats* st, pnp_ns_stats* nst) {
     nst->singular_blocks |= one.singular_blocks;
     nst->floor_stop |= one.floor_stop;
     nst->mg_fallbacks += one.mg_fallbacks;
+    nst->krylov_fallbacks += one.krylov_fallbacks;
     if (b == 0) nst->res0 = one.res0;
     nst->res_final = one.res_final;
     nst->wall_ms += one.wall_ms;

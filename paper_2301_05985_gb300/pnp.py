@@ -55,6 +55,7 @@ class pnp_params(C.Structure):
         ("ns_Sc", C.c_double), ("ns_kappa", C.c_double), ("ns_rtol", C.c_double), ("ns_atol", C.c_double),
         ("ns_inner_rtol", C.c_double), ("ns_max_it", C.c_int32), ("ns_pin", C.c_int32),
         ("ns_mg_levels", C.c_int32), ("ns_inner_max_it", C.c_int32),
+        ("ns_fgmres", C.c_int32), ("pad4_", C.c_int32),
     ]
 
 
@@ -63,6 +64,7 @@ class pnp_ns_stats(C.Structure):
         ("status", C.c_int32), ("refinements", C.c_int32), ("inner_its", C.c_int32),
         ("matvecs32", C.c_int32), ("matvecs64", C.c_int32), ("singular_blocks", C.c_int32),
         ("floor_stop", C.c_int32), ("mg_fallbacks", C.c_int32),
+        ("krylov_fallbacks", C.c_int32), ("pad_", C.c_int32),
         ("res0", C.c_double), ("res_final", C.c_double), ("wall_ms", C.c_double),
     ]
 
