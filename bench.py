@@ -59,7 +59,7 @@ JV_BYTES_PER_ELEM = 36.0
 JV_FLOPS_PER_ELEM = 2500.0
 # arithmetic of each kernel class; for ALU classes the binding roofline is chosen per run
 BOUNDS = {"residual64": "fp32", "jv64": "fp64", "jv32": "fp32", "blockdiag": "fp32", "ortho_dot": "fp64",
-          "ortho_update": "fp64", "precond": "hbm", "mlp": "bf16", "inner_ortho": "hbm", "ns64": "fp64",
+          "ortho_update": "fp64", "precond": "hbm", "mlp": "bf16", "inner_ortho": "hbm", "ns64": "fp32",
           "ns32": "fp32", "ns_krylov": "hbm", "mg_coarse": "hbm"}
 # the Navier-Stokes block (the configurations give neither Sc nor kappa): Sc = 1, kappa = 0.5,
 # multigrid-preconditioned FP32 BiCGStab under FP64 refinement, App. A's tolerances

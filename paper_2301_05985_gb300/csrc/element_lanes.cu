@@ -25,16 +25,6 @@
 
 namespace {
 
-// loaded value in the arithmetic type, and back to the storage type
-template <typename C, typename T>
-__device__ __forceinline__ C to_compute(T x) { return C(x); }
-template <>
-__device__ __forceinline__ df to_compute<df, double>(double x) { return df_split(x); }
-template <typename T>
-__device__ __forceinline__ T to_storage(T x) { return x; }
-template <typename T>
-__device__ __forceinline__ T to_storage(df x) { return df_to_double(x); }
-
 // blocks per SM the lane kernel's register cap is set for
 template <typename T, typename C>
 constexpr int lane_min_blocks() {

@@ -121,4 +121,14 @@ __device__ __forceinline__ void shape_at(int i, int c, T inv_h, T& N, T (&dN)[3]
   }
 }
 
+// loaded value in the arithmetic type, and back to the storage type
+template <typename C, typename T>
+__device__ __forceinline__ C to_compute(T x) { return C(x); }
+template <>
+__device__ __forceinline__ df to_compute<df, double>(double x) { return df_split(x); }
+template <typename T>
+__device__ __forceinline__ T to_storage(T x) { return x; }
+template <typename T>
+__device__ __forceinline__ T to_storage(df x) { return df_to_double(x); }
+
 }  // namespace

@@ -64,7 +64,7 @@ struct NsArgs {
   const double* hv;    // [N][4] history (beta1 v^k + beta2 v^{k-1}) / dt (data kernel only)
   const double* U;     // [N][3] PNP state (c+, c-, phi) of the body force (data kernel only)
   T* out;              // [N][4] accumulated
-  T isc, kap, tau_t, cid, fb;  // 1/Sc, beta0/dt, 4/dt^2, C_I Sc^2 d, kappa / (2 Lambda^2)
+  double isc, kap, tau_t, cid, fb;  // 1/Sc, beta0/dt, 4/dt^2, C_I Sc^2 d, kappa / (2 Lambda^2)
 };
 
 struct NsBc {
@@ -135,11 +135,18 @@ __device__ __forceinline__ void scatter_rows(const NsArgs<T>& A, int32_t id, con
   }
 }
 
+// physical constants in the kernel's arithmetic type
+template <typename C>
+struct NsK {
+  C isc, kap, tau_t, cid, fb;  // 1/Sc, beta0/dt, 4/dt^2, C_I Sc^2 d, kappa / (2 Lambda^2)
+};
+
 // One lane per (element, corner): the lane's Gauss point is the one next to its corner.
 // DATA adds the history and body-force terms (the residual F = A X - b); without them
-// the kernel applies the matrix.
-template <typename T, int D, bool DATA>
-__global__ void __launch_bounds__(kNsThreads) k_ns_lanes(NsArgs<T> A) {
+// the kernel applies the matrix.  T: storage type of the vectors; C: arithmetic type (T,
+// or double-float for FP64 data: GB300 runs FP64 at 1/64 of the FP32 rate).
+template <typename T, typename C, int D, bool DATA>
+__global__ void __launch_bounds__(kNsThreads) k_ns_lanes(NsArgs<T> A, NsK<C> K) {
   constexpr int NC = 1 << D;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if ((t & ~int64_t(31)) / NC >= A.n_elem) return;  // shuffles need the whole warp
@@ -148,99 +155,104 @@ __global__ void __launch_bounds__(kNsThreads) k_ns_lanes(NsArgs<T> A) {
   const bool valid = e < A.n_elem;
   const int32_t id = valid ? __ldg(A.conn + e * NC + c) : 0;
   const int lev = valid ? A.level[e] : 0;
-  const T inv_h = pow2i(lev, T(0));
-  const T w = pow2i(-D * (lev + 1), T(0));  // (h/2)^D
-  const T nb = T(-0.5 * (1.0 - kG));
-  T sh[3];
+  const C inv_h = pow2i(lev, C(0));
+  const C w = pow2i(-D * (lev + 1), C(0));  // (h/2)^D
+  const C nb = C(-0.5 * (1.0 - kG));
+  C sh[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) sh[k] = ((c >> k) & 1) ? inv_h : -inv_h;
-  const T G2 = pow2i(2 * lev + 2, T(0));  // (2/h)^2
+  const C G2 = pow2i(2 * lev + 2, C(0));        // (2/h)^2
+  const C iG2d = pow2i(-2 * lev - 2, C(0)) * C(1.0 / D);  // 1 / (d (2/h)^2)
 
-  T xn[4], an[4];
-  load4(A.hang_par, A.hang_np, A.X, id, valid, xn);
-  load4(A.hang_par, A.hang_np, A.adv, id, valid, an);
-  T v[3] = {T(0), T(0), T(0)}, gv[3][3], gp[3], va[3] = {T(0), T(0), T(0)};
+  T xs[4], as[4];
+  load4(A.hang_par, A.hang_np, A.X, id, valid, xs);
+  load4(A.hang_par, A.hang_np, A.adv, id, valid, as);
+  C xn[4], an[4];
 #pragma unroll
-  for (int i = 0; i < D; ++i) interp_vg<T, D>(xn[i], nb, sh, v[i], gv[i]);
+  for (int f = 0; f < 4; ++f) {
+    xn[f] = to_compute<C>(xs[f]);
+    an[f] = to_compute<C>(as[f]);
+  }
+  C v[3] = {C(0), C(0), C(0)}, gv[3][3], gp[3], va[3] = {C(0), C(0), C(0)};
 #pragma unroll
-  for (int i = D; i < 3; ++i) gv[i][0] = gv[i][1] = gv[i][2] = T(0);
-  interp_g<T, D>(xn[3], nb, sh, gp);
-  T vv = T(0);
+  for (int i = 0; i < D; ++i) interp_vg<C, D>(xn[i], nb, sh, v[i], gv[i]);
+#pragma unroll
+  for (int i = D; i < 3; ++i) gv[i][0] = gv[i][1] = gv[i][2] = C(0);
+  interp_g<C, D>(xn[3], nb, sh, gp);
+  C vv = C(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    va[i] = interp_v<T, D>(an[i], nb);
+    va[i] = interp_v<C, D>(an[i], nb);
     vv = fma(va[i], va[i], vv);
   }
-  const T tau_m = inv_sqrt(fma(A.cid * G2, G2, fma(G2, vv, A.tau_t)));
-  const T tau_s = T(1) / (T(D) * G2 * tau_m);
-  T div = T(0);
+  const C arg = fma(K.cid * G2, G2, fma(G2, vv, K.tau_t));
+  const C tau_m = inv_sqrt(arg);
+  const C tau_s = (arg * tau_m) * iG2d;  // 1 / (tr(G) tau_m) = sqrt(arg) / (d (2/h)^2)
+  C div = C(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) div += gv[i][i];
-  T Rm[3] = {T(0), T(0), T(0)};
+  C Rm[3] = {C(0), C(0), C(0)};
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    T a = A.kap * v[i];
+    C a = K.kap * v[i];
 #pragma unroll
     for (int j = 0; j < D; ++j) a = fma(va[j], gv[i][j], a);
-    Rm[i] = fma(A.isc, a, gp[i]);
+    Rm[i] = fma(K.isc, a, gp[i]);
   }
   if constexpr (DATA) {
-    double hn[4], un[4] = {0.0, 0.0, 0.0, 0.0};
-    load4(A.hang_par, A.hang_np, A.hv, id, valid, hn);
-    {
-      // (c+ - c-, phi) of the PNP state, node-major [N][3]
-      double u3[3] = {0.0, 0.0, 0.0};
-      if (valid) {
-        if (id >= 0) {
+    // history h_i and the body force kappa/(2 Lambda^2) (c+ - c-) grad phi of the PNP state
+    double hs[4], u3[3] = {0.0, 0.0, 0.0};
+    load4(A.hang_par, A.hang_np, A.hv, id, valid, hs);
+    if (valid) {
+      if (id >= 0) {
 #pragma unroll
-          for (int f = 0; f < 3; ++f) u3[f] = __ldg(A.U + 3 * (int64_t)id + f);
-        } else {
-          const int32_t h = -id - 1;
-          const int np = A.hang_np[h];
-          const double wgt = np == 2 ? 0.5 : 0.25;
-          for (int p = 0; p < np; ++p) {
-            const int64_t pid = A.hang_par[4 * h + p];
+        for (int f = 0; f < 3; ++f) u3[f] = __ldg(A.U + 3 * (int64_t)id + f);
+      } else {
+        const int32_t h = -id - 1;
+        const int np = A.hang_np[h];
+        const double wgt = np == 2 ? 0.5 : 0.25;
+        for (int p = 0; p < np; ++p) {
+          const int64_t pid = A.hang_par[4 * h + p];
 #pragma unroll
-            for (int f = 0; f < 3; ++f) u3[f] += wgt * __ldg(A.U + 3 * pid + f);
-          }
+          for (int f = 0; f < 3; ++f) u3[f] += wgt * __ldg(A.U + 3 * pid + f);
         }
       }
-      un[0] = u3[0] - u3[1];
-      un[1] = u3[2];
     }
-    const double dsh[3] = {double(sh[0]), double(sh[1]), double(sh[2])};
-    const double dnb = -0.5 * (1.0 - kG);
-    const double rho = interp_v<double, D>(un[0], dnb);
-    double gphi[3];
-    interp_g<double, D>(un[1], dnb, dsh, gphi);
+    const C rho = interp_v<C, D>(to_compute<C>(u3[0] - u3[1]), nb);
+    C gphi[3];
+    interp_g<C, D>(to_compute<C>(u3[2]), nb, sh, gphi);
+    const C frho = K.fb * rho;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      const double hq = interp_v<double, D>(hn[i], dnb);
-      Rm[i] += T(double(A.isc) * hq + double(A.fb) * rho * gphi[i]);
+      const C hq = interp_v<C, D>(to_compute<C>(hs[i]), nb);
+      Rm[i] += fma(K.isc, hq, frho * gphi[i]);
     }
   }
-  T r[4];
+  C r[4];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (i < D) {
-      T Phi[3];
-      const T su = A.isc * tau_m * Rm[i];
+      C Phi[3];
+      const C su = K.isc * tau_m * Rm[i];
 #pragma unroll
       for (int j = 0; j < 3; ++j) Phi[j] = fma(su, va[j], gv[i][j]);
       Phi[i] = fma(tau_s, div, Phi[i]);
-      r[i] = w * test_t<T, D>(Rm[i], Phi, nb, sh);
+      r[i] = w * test_t<C, D>(Rm[i], Phi, nb, sh);
     } else {
-      r[i] = T(0);
+      r[i] = C(0);
     }
   }
   {
-    T Phi[3];
+    C Phi[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) Phi[j] = tau_m * Rm[j];
-    r[3] = w * test_t<T, D>(div, Phi, nb, sh);
+    r[3] = w * test_t<C, D>(div, Phi, nb, sh);
   }
   if (!valid) return;
-  scatter_rows(A, id, r);
+  T ro[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) ro[f] = to_storage<T>(r[f]);
+  scatter_rows(A, id, ro);
 }
 
 // Dirichlet / pin rows (mode 0: X - g, the residual; 1: X, the matrix) of free nodes.
@@ -715,6 +727,7 @@ struct NsState {
   double *part = nullptr, *sc = nullptr, *hsc = nullptr;
   double* usave = nullptr;  // [2][3N] PNP history of repeated block iterations
   float4* mgAx = nullptr;   // [N] operator scratch of the finest multigrid level
+  float4* xbest = nullptr;  // [N] BiCGStab's best iterate
   bool mg_off = false;      // this solve fell back from the V-cycle to the inverted blocks
   // FGMRES(m): unnormalised FP64 basis [(m+1)][4N], FP32 preconditioned vectors [m][4N], an
   // FP64 scratch vector, reduction partials and device scalars
@@ -811,12 +824,24 @@ static NsArgs<T> ns_args(const pnp_ctx* c, const T* X, const T* adv, T* out) {
   A.X = X;
   A.adv = adv;
   A.out = out;
-  A.isc = T(1.0 / p.ns_Sc);
-  A.kap = T(p.steady ? 0.0 : p.beta0 / p.dt);
-  A.tau_t = T(p.steady ? 0.0 : 4.0 / (p.dt * p.dt));
-  A.cid = T(p.C_I * p.ns_Sc * p.ns_Sc * c->dim);
-  A.fb = T(p.ns_kappa / (2.0 * p.eps * p.eps));
+  A.isc = 1.0 / p.ns_Sc;
+  A.kap = p.steady ? 0.0 : p.beta0 / p.dt;
+  A.tau_t = p.steady ? 0.0 : 4.0 / (p.dt * p.dt);
+  A.cid = p.C_I * p.ns_Sc * p.ns_Sc * c->dim;
+  A.fb = p.ns_kappa / (2.0 * p.eps * p.eps);
   return A;
+}
+
+template <typename C, typename T>
+static NsK<C> ns_k(const NsArgs<T>& A) {
+  return NsK<C>{C(A.isc), C(A.kap), C(A.tau_t), C(A.cid), C(A.fb)};
+}
+
+// the FP64 rows in double-float arithmetic (default) or FP64 arithmetic
+template <int D, bool DATA>
+static void launch_ns64(const NsArgs<double>& A, int blocks, cudaStream_t s) {
+  if (residual_double_float()) k_ns_lanes<double, df, D, DATA><<<blocks, kNsThreads, 0, s>>>(A, ns_k<df>(A));
+  else k_ns_lanes<double, double, D, DATA><<<blocks, kNsThreads, 0, s>>>(A, ns_k<double>(A));
 }
 
 // element-kernel flops per lane (FP counts of the code above, fma = 2)
@@ -864,16 +889,17 @@ int ctx_ns_apply64(pnp_ctx* c, const double* X, const double* Ubody, double* F, 
   A.U = Ubody;
   const int64_t lanes = c->n_elem << c->dim;
   {
+    // flops: the FP64 formulation's, times 15 FP32 operations per double-float operation
     ProfScope ps(c, PNP_PROF_NS, 72.0 * N + (data ? 56.0 * N : 0.0) + 32.0 * N + c->conn_bytes(),
-                 ns_lane_flops(c->dim, data) * lanes);
+                 ns_lane_flops(c->dim, data) * lanes * (residual_double_float() ? 15.0 : 1.0));
     if (c->n_elem) {
       const int blocks = nblk(lanes, kNsThreads);
       if (c->dim == 2) {
-        if (data) k_ns_lanes<double, 2, true><<<blocks, kNsThreads, 0, s>>>(A);
-        else k_ns_lanes<double, 2, false><<<blocks, kNsThreads, 0, s>>>(A);
+        if (data) launch_ns64<2, true>(A, blocks, s);
+        else launch_ns64<2, false>(A, blocks, s);
       } else {
-        if (data) k_ns_lanes<double, 3, true><<<blocks, kNsThreads, 0, s>>>(A);
-        else k_ns_lanes<double, 3, false><<<blocks, kNsThreads, 0, s>>>(A);
+        if (data) launch_ns64<3, true>(A, blocks, s);
+        else launch_ns64<3, false>(A, blocks, s);
       }
       note_launch();
     }
@@ -903,8 +929,8 @@ int ctx_ns_apply32(pnp_ctx* c, const float4* x, float4* y) {
     ProfScope ps(c, PNP_PROF_NS32, 48.0 * N + c->conn_bytes(), ns_lane_flops(c->dim, false) * lanes);
     if (c->n_elem) {
       const int blocks = nblk(lanes, kNsThreads);
-      if (c->dim == 2) k_ns_lanes<float, 2, false><<<blocks, kNsThreads, 0, s>>>(A);
-      else k_ns_lanes<float, 3, false><<<blocks, kNsThreads, 0, s>>>(A);
+      if (c->dim == 2) k_ns_lanes<float, float, 2, false><<<blocks, kNsThreads, 0, s>>>(A, ns_k<float>(A));
+      else k_ns_lanes<float, float, 3, false><<<blocks, kNsThreads, 0, s>>>(A, ns_k<float>(A));
       note_launch();
     }
   }
@@ -1077,6 +1103,19 @@ static int ns_bicgstab32(pnp_ctx* c, double rtol, int max_it, int* its_out) {
   CK(cudaStreamSynchronize(s));
   const double rr0 = S->hsc[S_RR];
   int its = 0;
+  // the iterate with the smallest recursive residual seen at a check is the result (BiCGStab
+  // can diverge late; the zero start is the first candidate)
+  if (!S->xbest) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, f4) != cudaSuccess) {
+      cudaGetLastError();
+      PNP_FAIL(PNP_ERR_NOMEM, "ns: device allocation failed");
+    }
+    S->xbest = (float4*)q;
+    S->alloc.push_back(q);
+  }
+  double best = rr0;
+  bool x_is_best = true;  // S->x (zero) is the best so far
   *its_out = 0;
   if (!(rr0 > 0.0)) return PNP_OK;
   const double tol2 = rtol * rtol * rr0;
@@ -1118,8 +1157,18 @@ static int ns_bicgstab32(pnp_ctx* c, double rtol, int max_it, int* its_out) {
     CK(cudaMemcpyAsync(S->hsc, S->sc, sizeof(double) * kScalars, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const double rr = S->hsc[S_RR];
-    if (!std::isfinite(rr)) PNP_FAIL(PNP_ERR_NAN, "ns: BiCGStab residual is not finite");
-    if (rr <= tol2 || S->hsc[S_BREAK] != 0.0) break;
+    if (std::isfinite(rr) && rr < best) {
+      best = rr;
+      x_is_best = true;
+      if (rr > tol2) CK(cudaMemcpyAsync(S->xbest, S->x, f4, cudaMemcpyDeviceToDevice, s));
+    } else {
+      x_is_best = false;
+    }
+    if (!std::isfinite(rr) || rr <= tol2 || S->hsc[S_BREAK] != 0.0) break;
+  }
+  if (!x_is_best) {
+    if (best < rr0) CK(cudaMemcpyAsync(S->x, S->xbest, f4, cudaMemcpyDeviceToDevice, s));
+    else CK(cudaMemsetAsync(S->x, 0, f4, s));
   }
   *its_out = its;
   return PNP_OK;
@@ -1141,7 +1190,11 @@ static int ns_alloc_fgmres(pnp_ctx* c, int m) {
   // earlier (smaller) buffers stay in the allocation list until the context is destroyed
   const bool ok = get((void**)&S->Q, sizeof(double) * (size_t)(m + 1) * n) &&
                   get((void**)&S->Z, sizeof(float) * (size_t)m * n) && get((void**)&S->z64, sizeof(double) * n) &&
-                  get((void**)&S->fpart, sizeof(double) * (size_t)multi_dot_blocks(n) * (m + 2)) &&
+                  // partials: the multi-dot's blocks x (m + 2), and the update-and-norm kernel's
+                  // kRedBlocks (whichever is larger)
+                  get((void**)&S->fpart, sizeof(double) *
+                                             std::max<size_t>((size_t)kRedBlocks, (size_t)multi_dot_blocks(n)) *
+                                             (size_t)(m + 2)) &&
                   get((void**)&S->fsc, sizeof(double) * (size_t)(3 * (m + 2) + 4)) &&
                   get((void**)&S->fsc2, sizeof(double) * (size_t)(m + 2));
   if (!ok) {

@@ -6,7 +6,8 @@ tolerances (FP64 1e-12 relative, whole vector and per field; FP32 2e-5 per field
 
 * PNP_ELEMENT_KERNEL=thread: one thread per element with the modal sum factorisation
   (residual and J V, FP64 and FP32) instead of one lane group per element;
-* PNP_RESIDUAL_ARITH=f64: the residual in FP64 arithmetic instead of double-float pairs;
+* PNP_RESIDUAL_ARITH=f64: the residual (and the FP64 rows of the Navier-Stokes block) in
+  FP64 arithmetic instead of double-float pairs;
 * PNP_INNER_GRAPH=0: the inner FP32 Krylov solve launched eagerly instead of replayed as
   a CUDA graph.
 """
@@ -29,12 +30,13 @@ CASES = {
                                "residual_f64 or exact_derivative or hanging_values or newton_equilibrium "
                                "or bdf_time_steps"),
     "PNP_INNER_GRAPH=0": ("test_gpu_parity.py", "fp32_gmres or bdf_time_steps"),
+    "PNP_RESIDUAL_ARITH=f64 (NS)": ("test_gpu_ns.py", "residual_and_matrix or solve_matches"),
 }
 
 
 @pytest.mark.parametrize("setting", list(CASES))
 def test_alternate_path_matches_oracle(setting):
-    var, val = setting.split("=")
+    var, val = setting.split(" ")[0].split("=")
     fname, expr = CASES[setting]
     env = dict(os.environ)
     env[var] = val

@@ -94,3 +94,45 @@ def test_linearized_jv_needs_a_current_linearisation():
     P.ctx.gmres(U, -b, x, 1e-3, P.pnp.PNP_F32, raise_on_error=False)
     with pytest.raises(P.pnp.PnpError):
         P.ctx.jv_linearized(V, JV)
+
+
+def test_full_size_ns_rows_match_oracle():
+    """The Navier-Stokes rows at the membrane-band octree's full size (no-slip walls, the
+    bench's Sc = 1 and kappa = 0.5, a random (v, p), velocity history and PNP state): the
+    double-float residual and matrix action at 1e-12, the FP32 matrix action at 5e-5 per
+    slot, every row against the oracle."""
+    import oracle as O
+    oc = W.membrane_band_octants(5, 8, 0.05)
+    kw = dict(eps=1e-3, dt=1e-3, beta0=1.5, beta1=-2.0, beta2=0.5, ns_Sc=1.0, ns_kappa=0.5)
+    P = Pair(oc, kw, W.membrane_bcs(3, 20.0, 2.0))
+    ijk, L, n = P.mesh.ijk, oc.max_level, P.mesh.n_nodes
+    bt, bv = O.no_slip_bcs(3)
+    P.ctx.ns_set_bcs(bt, bv)
+    vk, vkm1 = W.fourier_velocity(ijk, L, 41, rms=0.5), W.fourier_velocity(ijk, L, 42, rms=0.5)
+    U = W.random_state(ijk, L, 43)
+    P.ctx.set_field(P.pnp.PNP_FIELD_VELOCITY, vk)
+    P.ctx.set_field(P.pnp.PNP_FIELD_VELOCITY_PREV, vkm1)
+    P.ctx.set_field(P.pnp.PNP_FIELD_U, U)
+    X = np.random.default_rng(44).standard_normal((n, 4))
+    nsp = O.NsParams(Sc=1.0, kappa=0.5, eps=1e-3, dt=1e-3, beta=(1.5, -2.0, 0.5), bc_type=bt, bc_val=bv)
+    o = P.to_ora
+    args = (o(X), o(2.0 * vk - vkm1), o(vk), o(vkm1), o(U))
+    torch = P.torch
+    Xd = torch.from_numpy(X).cuda()
+    F = torch.zeros_like(Xd)
+    P.ctx.ns_residual(Xd, F)
+    Fo = P.to_lib(P.om.ns_apply(nsp, *args, with_data=True))
+    assert np.linalg.norm(F.cpu().numpy() - Fo) / np.linalg.norm(Fo) <= TOL64
+    Y = torch.zeros_like(Xd)
+    P.ctx.ns_matvec(Xd, Y, P.pnp.PNP_F64)
+    Ao = P.to_lib(P.om.ns_apply(nsp, *args, with_data=False))
+    Yh = Y.cpu().numpy()
+    assert np.linalg.norm(Yh - Ao) / np.linalg.norm(Ao) <= TOL64
+    for f in range(4):
+        assert np.abs(Yh[:, f] - Ao[:, f]).max() <= 10 * TOL64 * np.abs(Ao[:, f]).max()
+    X32 = Xd.float()
+    Y32 = torch.zeros_like(X32)
+    P.ctx.ns_matvec(X32, Y32, P.pnp.PNP_F32)
+    Y32h = Y32.cpu().numpy().astype(np.float64)
+    for f in range(4):
+        assert np.abs(Y32h[:, f] - Ao[:, f]).max() <= 5e-5 * np.abs(Ao[:, f]).max()
