@@ -440,9 +440,10 @@ def kernel_table(prof, peaks, total_ms, N, E):
     return rows
 
 
-def load_traffic(workload):
+def load_traffic(workload, coupled=True):
     """Per-class DRAM traffic from the committed ncu summary, for kernels whose source is
-    unchanged since the capture."""
+    unchanged since the capture and whose variant the step runs (the coupled step's PNP
+    solve has an advection field: four stored rows per lane; the PNP step alone three)."""
     import hashlib
     try:
         tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
@@ -452,6 +453,8 @@ def load_traffic(workload):
         return {}
     out = {"_note": tj.get("note", "")}
     for name, e in tj.get("classes", {}).items():
+        if e.get("step", "coupled") != ("coupled" if coupled else "pnp_only"):
+            continue
         try:
             same = all(hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest() == h
                        for f, h in e["sources"].items())
@@ -737,7 +740,7 @@ def main():
 
     peaks = measured_peaks()
     table = kernel_table(prof, peaks, prof_ms, N, E)
-    rl = roofline(table, load_traffic(args.workload), "jv32", E)
+    rl = roofline(table, load_traffic(args.workload, coupled), "jv32", E)
     jv = dict(table.get("jv32", {}))
     if jv:
         jv["gdofs"] = 3.0 * N / (jv["avg_launch_ms"] * 1e-3) / 1e9

@@ -193,7 +193,7 @@ typedef struct pnp_ns_stats {
   int32_t matvecs64;     /* FP64 residual evaluations */
   int32_t singular_blocks; /* 1 when a 4x4 diagonal block was singular (replaced by I) */
   int32_t floor_stop;    /* 1 when the solve stopped at the rounding floor of the FP64 residual
-                            (three refinement steps without progress, ||F|| <= 1e-6 ||F(X^0)||)
+                            (three refinement steps without progress, ||F|| <= 1e-9 ||F(X^0)||)
                             above the requested tolerance */
   int32_t mg_fallbacks;  /* refinement steps whose multigrid-preconditioned correction raised
                             ||F||: undone, the rest of the solve used the inverted blocks */
@@ -439,7 +439,7 @@ int pnp_ns_block_diag(pnp_ctx* c, double* D);
  * correction around FP32 BiCGStab (App. A solves this block with BiCGStab) of at most
  * ns_inner_max_it iterations each (a step that raises ||F|| is undone, and with multigrid the
  * solve continues with the blocks).  PNP_ERR_KRYLOV_MAXIT after ns_max_it Krylov
- * iterations, 60 refinement steps, or when progress stops above 1e-6 ||F(X^0)|| (at or below
+ * iterations, 60 refinement steps, or when progress stops above 1e-9 ||F(X^0)|| (at or below
  * it the solve ends as converged with st->floor_stop = 1); PNP_ERR_NAN on a non-finite
  * norm.  st->inner_its counts the Krylov iterations, st->refinements the FGMRES restart
  * cycles or refinement steps.  Uses the context's beta0..2. */

@@ -1308,10 +1308,10 @@ static int ns_fgmres(pnp_ctx* c, const double* Ubody, double target, double& f, 
     ++cycles;
     if (p.monitor) fprintf(stderr, "[pnp ns cycle %2d] ||F|| %.6e (%d iterations)\n", cycles, f, total);
     // restart cycles that cut ||F|| by less than 5% three times in a row: the rounding floor
-    // (<= 1e-6 ||F(X^0)||, converged) or a failure
+    // (<= 1e-9 ||F(X^0)||, converged) or a failure
     stalls = f < 0.95 * f_prev ? 0 : stalls + 1;
     if (stalls >= 3) {
-      if (f <= 1e-6 * st->res0) {
+      if (f <= 1e-9 * st->res0) {
         st->floor_stop = 1;
         break;
       }
@@ -1406,11 +1406,11 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
       f = fn;
     }
     // three refinement steps in a row without reducing ||F|| end the solve: at the
-    // rounding floor of the FP64 residual (||F|| <= 1e-6 ||F(X^0)||) as converged
+    // rounding floor of the FP64 residual (||F|| <= 1e-9 ||F(X^0)||) as converged
     // (floor_stop), above it as a failure
     stalls = f < f_prev ? 0 : stalls + 1;
     if (stalls >= 3) {
-      if (f <= 1e-6 * st->res0) {
+      if (f <= 1e-9 * st->res0) {
         st->floor_stop = 1;
         break;
       }
