@@ -719,7 +719,7 @@ inline int gsb(int64_t n) { return (int)std::min<int64_t>(kRedBlocks, std::max<i
 
 // ------------------------------------------------------------------ state
 struct NsState {
-  double *X = nullptr, *F = nullptr, *adv = nullptr, *hv = nullptr, *Dg = nullptr, *v3 = nullptr;
+  double *X = nullptr, *F = nullptr, *adv = nullptr, *hv = nullptr, *Dg = nullptr;
   float4* adv32 = nullptr;
   float* Dinv = nullptr;
   float4 *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *t = nullptr, *ph = nullptr, *sh = nullptr,
@@ -758,7 +758,7 @@ int ctx_ns_alloc(pnp_ctx* c) {
   };
   const size_t d4 = sizeof(double) * 4 * N, f4 = sizeof(float4) * N;
   bool ok = get((void**)&S->X, d4) && get((void**)&S->F, d4) && get((void**)&S->adv, d4) && get((void**)&S->hv, d4) &&
-            get((void**)&S->Dg, sizeof(double) * 16 * N) && get((void**)&S->v3, sizeof(double) * 3 * N) &&
+            get((void**)&S->Dg, sizeof(double) * 16 * N) &&
             get((void**)&S->adv32, f4) && get((void**)&S->Dinv, sizeof(float) * 16 * N) && get((void**)&S->r, f4) &&
             get((void**)&S->rh, f4) && get((void**)&S->p, f4) && get((void**)&S->v, f4) && get((void**)&S->t, f4) &&
             get((void**)&S->ph, f4) && get((void**)&S->sh, f4) && get((void**)&S->x, f4) &&
