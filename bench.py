@@ -64,7 +64,7 @@ BOUNDS = {"residual64": "fp32", "jv64": "fp64", "jv32": "fp32", "blockdiag": "fp
 # the Navier-Stokes block (the configurations give neither Sc nor kappa): Sc = 1, kappa = 0.5,
 # multigrid-preconditioned FP32 BiCGStab under FP64 refinement, App. A's tolerances
 NS_KW = dict(ns_Sc=1.0, ns_kappa=0.5, ns_mg_levels=8, mg_smooth=3, mg_omega=0.6, mg_coarse_its=32,
-             ns_rtol=1e-8, ns_atol=1e-10, ns_blocks=1)
+             ns_rtol=1e-8, ns_atol=1e-10, ns_blocks=1, ns_fgmres=50)
 
 WORKLOADS = {
     "electroconvection": {"eps": 5e-4, "V": 40.0, "dt": 5e-4,
@@ -370,7 +370,7 @@ def workload_config(name, mesh, coupled=True):
         cfg.update({"step": "NS-PNP block iteration (one pass): linear VMS Navier-Stokes, then PNP Newton",
                     "velocity": "Navier-Stokes block: Sc = 1, kappa = 0.5, no-slip walls, fluid at rest at t = 0",
                     "ns_dofs": 4 * mesh.n_nodes,
-                    "ns_solver": "FGMRES(30) in FP64 (basis, two-pass Gram-Schmidt, matrix action) right-"
+                    "ns_solver": "FGMRES(50) in FP64 (basis, two-pass Gram-Schmidt, matrix action) right-"
                                  "preconditioned by an FP32 multigrid V-cycle (8 coarser octrees, 3 block-Jacobi "
                                  "sweeps, damping 0.6, 32 on the coarsest), to 1e-8 relative / 1e-10 absolute"})
     else:
