@@ -59,7 +59,8 @@ def test_struct_layouts_match_header(pnp, tmp_path):
     p = pnp.default_params()
     assert p.C_I == 6.0 and p.gmres_restart == 30 and p.newton_rtol == 1e-8
     structs = (("pnp_params", pnp.pnp_params), ("pnp_solve_stats", pnp.pnp_solve_stats),
-               ("pnp_train_cfg", pnp.pnp_train_cfg), ("pnp_train_stats", pnp.pnp_train_stats))
+               ("pnp_ns_stats", pnp.pnp_ns_stats), ("pnp_train_cfg", pnp.pnp_train_cfg),
+               ("pnp_train_stats", pnp.pnp_train_stats))
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pnp.h"', 'int main(void){',
              'printf("PNP_MLP_PARAMS size %d\\n", PNP_MLP_PARAMS);']
     for cname, py in structs:
@@ -184,3 +185,19 @@ def test_membrane_band_mesh_counts(pnp):
     assert m.n_nodes == 257 * 257 * 15 + 129 * 129 + 2 * 65 * 65 + 33 * 33 * 29
     # hanging: level-8 nodes on z = 14/256 not on the level-7 lattice, etc.
     assert m.n_hanging == (257**2 - 129**2) + (129**2 - 65**2) + (65**2 - 33**2)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("eps", 0.0), ("dt", -1.0), ("gmres_restart", 0), ("gmres_restart", 201), ("precision", 7),
+    ("bdf_order", 3), ("mg_omega", 2.5), ("ns_blocks", 0), ("ns_blocks", 17), ("ns_Sc", 0.0),
+    ("ns_rtol", -1.0), ("ns_inner_rtol", 1.0), ("ns_max_it", 0), ("ns_pin", 2), ("ns_mg_levels", 17),
+    ("ns_inner_max_it", 0), ("ns_fgmres", -1), ("ns_fgmres", 201)])
+def test_context_rejects_out_of_range_params(pnp, field, value):
+    """Parameter checks run before any device call: no GPU is needed to see them fail."""
+    mesh = pnp.Mesh(W.uniform_octants(3, 2))
+    p = pnp.default_params(eps=1e-2, dt=1e-3)
+    setattr(p, field, value)
+    with pytest.raises(pnp.PnpError) as e:
+        pnp.Context(mesh, p)
+    assert e.value.code == pnp.PNP_ERR_ARG
+    mesh.close()
