@@ -187,10 +187,12 @@ typedef struct pnp_solve_stats {
 /* Statistics of one Navier-Stokes linear solve. */
 typedef struct pnp_ns_stats {
   int32_t status;        /* pnp_status of the solve */
-  int32_t refinements;   /* FP64 refinement steps (one FP32 BiCGStab each) */
-  int32_t inner_its;     /* total FP32 BiCGStab iterations */
-  int32_t matvecs32;     /* FP32 matrix applications (2 per BiCGStab iteration) */
-  int32_t matvecs64;     /* FP64 residual evaluations */
+  int32_t refinements;   /* FGMRES restart cycles, plus FP64 refinement steps (one FP32
+                            BiCGStab each) */
+  int32_t inner_its;     /* total Krylov iterations (FGMRES, then BiCGStab) */
+  int32_t matvecs32;     /* FP32 operator applications on the finest mesh: 2 per BiCGStab
+                            iteration and 2 mg_smooth per V-cycle */
+  int32_t matvecs64;     /* FP64 operator applications (FGMRES matrix actions and residuals) */
   int32_t singular_blocks; /* 1 when a 4x4 diagonal block was singular (replaced by I) */
   int32_t floor_stop;    /* 1 when the solve stopped at the rounding floor of the FP64 residual
                             (three refinement steps without progress, ||F|| <= 1e-9 ||F(X^0)||)

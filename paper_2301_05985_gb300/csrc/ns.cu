@@ -729,6 +729,7 @@ struct NsState {
   float4* mgAx = nullptr;   // [N] operator scratch of the finest multigrid level
   float4* xbest = nullptr;  // [N] BiCGStab's best iterate
   bool mg_off = false;      // this solve fell back from the V-cycle to the inverted blocks
+  int64_t fine32 = 0;       // finest-level FP32 operator applications of this solve's V-cycles
   // FGMRES(m): unnormalised FP64 basis [(m+1)][4N], FP32 preconditioned vectors [m][4N], an
   // FP64 scratch vector, reduction partials and device scalars
   double *Q = nullptr, *z64 = nullptr, *fpart = nullptr, *fsc = nullptr, *fsc2 = nullptr;
@@ -1035,8 +1036,13 @@ static int ns_mg_cycle(pnp_ctx* c, size_t l, const float4* b, float4* x) {
   cudaStream_t s = c->stream;
   const float om = (float)c->prm.mg_omega;
   const NsBc bc = ns_bc(lc);
+  auto apply = [&]() -> int {
+    RC(ctx_ns_apply32(lc, x, Ax));
+    if (l == 0) c->ns->fine32++;
+    return PNP_OK;
+  };
   auto smooth = [&](bool first) -> int {
-    if (!first) RC(ctx_ns_apply32(lc, x, Ax));
+    if (!first) RC(apply());
     ProfScope ps(c, l == 0 ? PNP_PROF_NS_KRYLOV : -1, 112.0 * N, 36.0 * N);
     k_ns_smooth<<<nblk(N, 256), 256, 0, s>>>(N, LS->Dinv, b, Ax, x, om, first ? 1 : 0);
     note_launch();
@@ -1050,7 +1056,7 @@ static int ns_mg_cycle(pnp_ctx* c, size_t l, const float4* b, float4* x) {
   }
   const int nu = std::max(1, c->prm.mg_smooth);
   for (int k = 0; k < nu; ++k) RC(smooth(k == 0));
-  RC(ctx_ns_apply32(lc, x, Ax));
+  RC(apply());
   pnp_ctx* cc = lv[l + 1].sub;
   const MgLevel& C = lv[l + 1];
   {
@@ -1323,7 +1329,6 @@ static int ns_fgmres(pnp_ctx* c, const double* Ubody, double target, double& f, 
   }
   st->inner_its = total;
   st->refinements = cycles;
-  st->matvecs32 = 0;
   return PNP_OK;
 }
 
@@ -1336,6 +1341,7 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
   const pnp_params& p = c->prm;
   const int64_t N = c->n_nodes;
   cudaStream_t s = c->stream;
+  S->fine32 = 0;
   RC(ctx_ns_block_diag(c, S->Dg));
   RC(ctx_ns_blocks_row_fix(c, S->Dg, S->Dinv));
   if (ns_mg_levels(c) > 0) RC(ctx_ns_mg_prepare(c));
@@ -1352,6 +1358,7 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
     const int rc = f > target ? ns_fgmres(c, Ubody, target, f, st) : PNP_OK;
     if (rc >= 0) {
       st->status = rc;
+      st->matvecs32 = (int32_t)S->fine32;
       st->res_final = f;
       st->wall_ms = now_ms() - t0;
       return rc;
@@ -1425,7 +1432,8 @@ int ctx_ns_solve(pnp_ctx* c, const double* Ubody, pnp_ns_stats* st) {
   CK(cudaStreamSynchronize(s));
   st->status = rc;
   st->refinements = ref;
-  st->matvecs32 += 2 * (inner_total - st->inner_its);  // BiCGStab: two per iteration
+  // BiCGStab: two per iteration, and the V-cycles' finest-level applications
+  st->matvecs32 += 2 * (inner_total - st->inner_its) + (int32_t)S->fine32;
   st->inner_its = inner_total;
   st->res_final = f;
   st->singular_blocks = (flag & 4) ? 1 : 0;
