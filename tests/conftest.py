@@ -9,7 +9,11 @@ for p in (ROOT, os.path.join(ROOT, "oracle")):
         sys.path.insert(0, p)
 
 
+@pytest.hookimpl(tryfirst=True)
 def pytest_configure(config):
+    # temporary files of the tests stay inside the repository (git-ignored)
+    if not config.option.basetemp:
+        config.option.basetemp = os.path.join(ROOT, ".pytest_tmp")
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built CUDA library")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
 
