@@ -577,9 +577,11 @@ enum {
   PNP_PROF_ORTHO_UPDATE = 7, /* Gram-Schmidt update: the multi-axpy + norm kernel */
   PNP_PROF_INNER = 8,      /* FP32 Gram-Schmidt of the inner GMRES (flexible mode) */
   PNP_PROF_MG = 9,         /* multigrid: everything on the coarse levels of a V-cycle */
-  PNP_PROF_NS = 10,        /* Navier-Stokes FP64 element kernels (residual, blocks) */
-  PNP_PROF_NS32 = 11,      /* Navier-Stokes FP32 matrix action */
-  PNP_PROF_NS_KRYLOV = 12, /* Navier-Stokes BiCGStab vector, dot and block-Jacobi kernels */
+  PNP_PROF_NS = 10,        /* Navier-Stokes FP64-data element kernels (residual, FGMRES matrix
+                              action, blocks) */
+  PNP_PROF_NS32 = 11,      /* Navier-Stokes FP32 matrix action (V-cycle, BiCGStab) */
+  PNP_PROF_NS_KRYLOV = 12, /* Navier-Stokes Krylov vector work (FGMRES Gram-Schmidt, BiCGStab),
+                              block-Jacobi and finest-level smoothing kernels */
   PNP_PROF_KINDS = 13
 };
 /* on != 0: clear the accumulated times and start recording; on == 0: stop. */
