@@ -1,6 +1,6 @@
 """FP64 reference of the learned Newton-start network (test infrastructure).
 
-Only tests, the smoke check and the benchmark's CPU-baseline leg import this module.
+Only the tests and the smoke check import this module.
 
 The paper has no learned component; this is the per-node multilayer perceptron the
 library adds as a Newton initial guess: input 216 features (a 3x3x3 stencil x 4 fields

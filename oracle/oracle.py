@@ -1,7 +1,7 @@
 """Python side of the FP64 CPU oracle (test infrastructure).
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
-import this module.  The library's product path never does.
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline and ``--impl reference``
+legs of ``bench.py`` import this module.  The library's product path never does.
 
 It wraps ``pnp_oracle.cpp`` (mesh, residual, analytic Jacobian, matrix-free Jv) and
 adds the solution algorithms of the paper written out plainly:

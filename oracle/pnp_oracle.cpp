@@ -1,8 +1,8 @@
 // pnp_oracle.cpp -- plain FP64 CPU oracle for the VMS-stabilised PNP block.
 //
 // TEST INFRASTRUCTURE.  This file is the independent reference that the CUDA path is
-// checked against.  Only the tests, the smoke check and the CPU-baseline leg of the
-// benchmark load it; the library's product path never calls, links or includes it,
+// checked against.  Only the tests, the smoke check and the CPU-baseline and reference
+// legs of the benchmark load it; the library's product path never calls, links or includes it,
 // and it shares no code, header or table with the CUDA sources.
 //
 // What it computes (Kim et al., "Direct numerical simulation of electrokinetic
