@@ -99,3 +99,30 @@ def test_clock_summary_reports_throttle_reasons():
     s = cs.summary()
     assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
     assert s["reasons"] == ["sw_power_cap"] and s["power_w_max"] == pytest.approx(1390.2)
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """The reference arm (the oracle on the host cores) on the small workload: one JSON line
+    with the contract's keys, its cpu_baseline and e2e describing the same value, and
+    ms_per_step x steps within the process's own wall time."""
+    import subprocess
+    import sys
+    import time
+    t0 = time.perf_counter()
+    r = subprocess.run([sys.executable, os.path.join(B.ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "small", "--steps", "2", "--warmup", "1"], cwd=B.ROOT, capture_output=True, text=True,
+                       timeout=600)
+    wall = time.perf_counter() - t0
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["unit"] == "s/step" and d["higher_is_better"] is False
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["ms_per_step"] * d["steps"] * 1e-3 <= wall
